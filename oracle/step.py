@@ -1,0 +1,113 @@
+"""One plain boundary-integral time step for a suspension (Algorithm 1 with exact operators).
+
+Test infrastructure only.
+
+Per step, in this order (Sec. 3.1, Algorithm 1, Sec. 4.2-4.3):
+1. force f^n = -kappa X_ssss + (sigma^n X_s)_s at X^n                         (Eq. elastic_force)
+2. u^n = U_far + U_near + u_inf at X^n                                       (Algorithm 4)
+3. advection  X* = X^n + dt (I - M^n) u^n                                    (Eq. advection_disc)
+4. relaxation (I - dt (I - M*) B*) X^{n+1} = X*                              (Eq. relaxation_disc)
+5. redistribution of X^{n+1} to equal arclength                               (Sec. 4.2)
+6. tension sigma^{n+1} = -L^{-1} P (B X^{n+1} + u^n), operators at the
+   redistributed X^{n+1}, u^n resampled at the new parameters                (Eq. tension_disc)
+7. area/length correction when either relative error exceeds corr_tol         (Sec. 4.3)
+
+Readings: Eq. tension_disc writes L^n, P^n while Algorithm 1-2 evaluate them at X^{n+1}; we
+use X^{n+1} after redistribution (step 6), and since redistribution re-indexes the material
+points, u^n is carried to the new points by its trigonometric interpolant. Algorithm 1
+computes the tension before the correction and so do we. One far-field evaluation per step
+(Algorithm 1 needs u^n once). Initial tension (not given in the paper):
+sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
+"""
+import numpy as np
+
+from . import correct as _corr
+from .farfield import far_field
+from .flows import background
+from .operators import Operators
+from .redistribute import redistribute
+from .spectral import Geometry, eval_interpolant, force
+
+
+class Params:
+    def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
+                 near_field=False, corr_tol=0.01):
+        self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
+        self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
+        self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
+
+
+def _tension(ops, x, y, ux, uy, kappa):
+    N = len(x)
+    rhs = ops.P @ (ops.B @ np.concatenate([x, y]) + np.concatenate([ux, uy]))
+    return -np.linalg.solve(ops.L, rhs)
+
+
+class Suspension:
+    """State (X, sigma, A_0, L_0) of M vesicles and the plain step (module header)."""
+
+    def __init__(self, xs, ys, params):
+        self.p = params
+        self.xs, self.ys, self.sig, self.A0, self.L0 = [], [], [], [], []
+        for x, y in zip(xs, ys):
+            xr, yr, _ = redistribute(np.asarray(x, float), np.asarray(y, float))
+            g = Geometry(xr, yr)
+            ops = Operators(xr, yr, params.kappa, params.mu)
+            ub = background(params.flow_kind, params.flow_p, xr, yr)
+            self.xs.append(xr)
+            self.ys.append(yr)
+            self.sig.append(_tension(ops, xr, yr, ub[0], ub[1], params.kappa))
+            self.A0.append(g.area)
+            self.L0.append(g.length)
+        self.velocity = [np.zeros(2 * len(x)) for x in self.xs]
+        self.corrections = 0
+        self.near_pairs = []
+
+    def interaction_velocity(self):
+        """u^n = U_far + U_near + u_inf at the current points (Algorithm 1, first line)."""
+        p = self.p
+        fx, fy = [], []
+        for x, y, s in zip(self.xs, self.ys, self.sig):
+            a, b = force(x, y, s, p.kappa)
+            fx.append(a)
+            fy.append(b)
+        ux, uy, near = far_field(self.xs, self.ys, fx, fy, p.mu, near_mask=p.near_field)
+        if p.near_field and near:
+            from .nearfield import near_correction
+            cx, cy = near_correction(self.xs, self.ys, fx, fy, p.mu, near)
+            ux = ux + cx
+            uy = uy + cy
+        self.near_pairs = near
+        out = []
+        o = 0
+        for x, y in zip(self.xs, self.ys):
+            n = len(x)
+            bx, by = background(p.flow_kind, p.flow_p, x, y)
+            out.append((ux[o:o + n] + bx, uy[o:o + n] + by))
+            o += n
+        return out
+
+    def step(self):
+        p = self.p
+        u = self.interaction_velocity()
+        nxs, nys, nsig, vel = [], [], [], []
+        for v, (x, y) in enumerate(zip(self.xs, self.ys)):
+            N = len(x)
+            ux, uy = u[v]
+            ubar = np.concatenate([ux, uy])
+            ops_n = Operators(x, y, p.kappa, p.mu)
+            zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
+            ops_s = Operators(zs[:N], zs[N:], p.kappa, p.mu)
+            A = np.eye(2 * N) - p.dt * (ops_s.B - ops_s.T @ np.linalg.solve(ops_s.L, ops_s.P @ ops_s.B))
+            z1 = np.linalg.solve(A, zs)
+            xr, yr, alpha = redistribute(z1[:N], z1[N:])
+            uxr, uyr = eval_interpolant(ux, alpha), eval_interpolant(uy, alpha)
+            ops_r = Operators(xr, yr, p.kappa, p.mu)
+            sig = _tension(ops_r, xr, yr, uxr, uyr, p.kappa)
+            xc, yc, fired, _ = _corr.correct(xr, yr, self.A0[v], self.L0[v], tol=p.corr_tol)
+            self.corrections += int(fired)
+            nxs.append(xc)
+            nys.append(yc)
+            nsig.append(sig)
+            vel.append(ubar)
+        self.xs, self.ys, self.sig, self.velocity = nxs, nys, nsig, vel
