@@ -1,0 +1,170 @@
+/*
+ * vesb300 -- C ABI of the B300 (sm_103a) vesicle-suspension time step.
+ *
+ * The method is the 2D boundary-integral vesicle scheme of VesNet (arXiv 2606.25569): the
+ * per-time-step hot path of Algorithm 1 with exact operators, i.e. the elastic force
+ * f = -kappa_b X_ssss + (sigma X_s)_s (Eq. elastic_force), the all-pairs far-field single layer
+ * with the 2D Stokeslet (Eqs. single_layer, Stokeslet; Sec. 2.2.2), the advection step
+ * (Eq. advection_disc), the implicit relaxation step (Eq. relaxation_disc), redistribution to
+ * equal arclength (Sec. 4.2), the tension update (Eq. tension_disc) and the area/length
+ * correction (Sec. 4.3). The problem statement of Algorithm 1 (Sec. 4.4) fixes the inputs: the
+ * vesicle points, the bending modulus kappa_b, the viscosity mu, the background flow and dt.
+ *
+ * Conventions shared by every entry point:
+ *  - Point layout ("CSR blocks"): vesicle v owns points offsets[v] .. offsets[v+1]-1
+ *    (N_v = offsets[v+1] - offsets[v], even, 8 <= N_v <= 128). A per-point 2-vector field
+ *    (positions, forces, velocities) is stored per vesicle as its N_v x-components followed by
+ *    its N_v y-components, starting at index 2*offsets[v]. Scalar fields (tension) start at
+ *    offsets[v]. Points run counter-clockwise.
+ *  - No exceptions cross the ABI; every call returns a vs_status. The message of the last
+ *    failure of a handle is kept per handle (vs_last_error).
+ *  - Handles are not thread-safe; separate handles are independent.
+ *  - All GPU work of a handle is enqueued on the CUDA stream given at creation. Errors found by
+ *    kernels (a zero pivot, a non-finite state, a correction that did not converge) are stored
+ *    on the device and reported by the next call that synchronises (vs_sync, vs_get_*).
+ *  - The library copies its inputs; output buffers belong to the caller.
+ *  - There is no CPU fallback: without a usable CUDA device every call fails with VS_ERR_CUDA.
+ */
+#ifndef VESB300_H
+#define VESB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VS_OK = 0,
+  VS_ERR_INVALID_ARG = 1,   /* bad sizes, layout, parameters or a null pointer */
+  VS_ERR_CUDA = 2,          /* a CUDA call failed (no device, launch error) */
+  VS_ERR_NOMEM = 3,         /* device allocation failed */
+  VS_ERR_NOT_CONVERGED = 4, /* area/length correction did not converge */
+  VS_ERR_UNSTABLE = 5,      /* non-finite state or a singular per-vesicle system */
+  VS_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
+  VS_ERR_NO_NETWORK = 7     /* reserved for the learned (hybrid) path */
+} vs_status;
+
+/* Background flow u_inf (Sec. 5.3-5.5): p[0], p[1] as listed. */
+typedef enum {
+  VS_FLOW_NONE = 0,
+  VS_FLOW_SHEAR = 1,        /* u = p0 (y, 0)                                        (Sec. 5.4) */
+  VS_FLOW_TAYLOR_GREEN = 2, /* u = p0 (sin(pi x/p1) cos(pi y/p1), -cos(pi x/p1) sin(pi y/p1))
+                                                                                  (Eq. tayGreenFlow) */
+  VS_FLOW_POISEUILLE = 3    /* u = p0 (1 - (y/p1)^2) e_x, walls at y = +-p1           (Sec. 5.3) */
+} vs_flow_kind;
+
+typedef struct {
+  int32_t kind;  /* vs_flow_kind */
+  int32_t pad_;
+  double p[4];
+} vs_flow;
+
+/* flags */
+#define VS_FLAG_FARFIELD_FP64 1ull /* far field in FP64 instead of compensated FP32 */
+
+typedef struct {
+  double kappa_b;    /* bending modulus, > 0 */
+  double mu;         /* viscosity, > 0 */
+  double dt;         /* time step, > 0 */
+  double corr_tol;   /* relative area/length error that triggers the correction (Sec. 4.3: 0.01) */
+  int32_t mode;      /* 0: plain boundary-integral step (the only mode of this version) */
+  int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
+  int32_t use_graph; /* reserved */
+  int32_t pad_;
+  uint64_t flags;    /* VS_FLAG_* */
+} vs_params;
+
+typedef struct vs_suspension vs_suspension;
+
+/*
+ * Create a suspension (Algorithm 1 input, Sec. 4.4).
+ *  xy       host, 2*offsets[M] doubles in CSR blocks: the initial points.
+ *  offsets  host, M+1 increasing int64, offsets[0] = 0.
+ *  params, flow  host structs, copied.
+ *  cuda_stream   cudaStream_t (NULL = legacy default stream) for all later work.
+ * The points are redistributed to equal arclength (Sec. 4.2); the resulting area and length
+ * become the reference A_0, L_0 of the correction (Sec. 4.3); the initial tension is
+ * sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) (self and background terms only).
+ * Returns VS_ERR_INVALID_ARG for M < 1, odd N, N outside [8, 128], non-finite points or bad
+ * parameters; VS_ERR_NOMEM / VS_ERR_CUDA on device failures. On success *out owns all device
+ * memory of the suspension until vs_destroy.
+ */
+vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const vs_params* params,
+                    const vs_flow* flow, void* cuda_stream, vs_suspension** out);
+
+/*
+ * Enqueue nsteps plain time steps (Algorithm 1 with exact operators): force, far field +
+ * u_inf, advection (Eq. advection_disc), relaxation (Eq. relaxation_disc), redistribution
+ * (Sec. 4.2), tension at the new points (Eq. tension_disc), correction (Sec. 4.3).
+ * Asynchronous: returns once the work is enqueued.
+ */
+vs_status vs_step(vs_suspension* s, int32_t nsteps);
+
+/* Wait for the handle's stream and report device-side errors of earlier steps. */
+vs_status vs_sync(vs_suspension* s);
+
+/*
+ * Replace positions and tension from host buffers (same layout as vs_create; sigma has
+ * offsets[M] doubles). The points are used as given (no redistribution); A_0, L_0 are kept.
+ */
+vs_status vs_set_state(vs_suspension* s, const double* xy, const double* sigma);
+
+/* Copy the state to caller-owned host buffers; cap = buffer length in doubles.
+ * positions: 2*P doubles (CSR blocks), tension: P, velocity: 2*P -- the velocity u^n of
+ * Algorithm 1 (far field + near-field exclusion + u_inf) at the points of the last step's start.
+ * Synchronises the stream. VS_ERR_INVALID_ARG when cap is too small. */
+vs_status vs_get_positions(vs_suspension* s, double* xy, int64_t cap);
+vs_status vs_get_tension(vs_suspension* s, double* sigma, int64_t cap);
+vs_status vs_get_velocity(vs_suspension* s, double* u, int64_t cap);
+
+/* Reference area/length (A_0, L_0) per vesicle: 2*M doubles, A_0 then L_0. */
+vs_status vs_get_reference(vs_suspension* s, double* a0l0, int64_t cap);
+
+/* Device pointers of positions (2P doubles) and tension (P doubles), borrowed: valid until the
+ * next vs_step / vs_set_state / vs_destroy. */
+vs_status vs_get_device_ptrs(const vs_suspension* s, const double** xy, const double** sigma);
+
+/* Counters: [0] steps taken, [1] corrections applied, [2] near (target, vesicle) pairs in the
+ * last far-field evaluation (when near_field), [3] device error bits. Synchronises. */
+vs_status vs_get_counters(vs_suspension* s, int64_t* out4);
+
+const char* vs_last_error(const vs_suspension* s);
+void vs_destroy(vs_suspension* s);
+
+/*
+ * Far-field single layer alone (Sec. 2.2.2; the "direct evaluation" of Table tab:timings):
+ *   u(x_i) = sum over vesicles v != vesicle(i) [not near x_i when near_mask] of
+ *            sum_j G(x_i - X_vj) f_vj |X_alpha|_vj (2 pi / N_v),
+ *   G = (1/4 pi mu)(-log|r| I + r r^T / |r|^2).
+ * A plan holds the layout and its device buffers.
+ *  offsets     host, M+1 int64 as in vs_create.
+ *  precision   0: compensated FP32 (vesicle-relative coordinates), 1: FP64.
+ * vs_farfield_eval takes DEVICE pointers in CSR blocks: xy (2P), f (2P); writes u (2P, device,
+ * overwritten) on the plan's stream. Asynchronous.
+ */
+typedef struct vs_farfield_plan vs_farfield_plan;
+vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, int32_t near_mask,
+                                  int32_t precision, void* cuda_stream, vs_farfield_plan** out);
+vs_status vs_farfield_eval(vs_farfield_plan* plan, const double* xy, const double* f, double* u);
+/* Device error bits of the last evaluation (near-list overflow) and the number of near pairs.
+ * Synchronises. */
+vs_status vs_farfield_counters(vs_farfield_plan* plan, int64_t* out2);
+const char* vs_farfield_last_error(const vs_farfield_plan* plan);
+void vs_farfield_plan_destroy(vs_farfield_plan* plan);
+
+/*
+ * Per-vesicle self single-layer matrices (Eq. single_layer with the Kress product rule for the
+ * log singularity, trapezoid weights otherwise; Sec. 2.2.2), for testing and for callers that
+ * build their own operators. xy: device, CSR blocks. S_out: device, sum_v (2 N_v)^2 doubles,
+ * vesicle v's row-major 2N_v x 2N_v matrix starting at 4 * sum_{u<v} N_u^2 (rows: u_x then u_y;
+ * columns: f_x then f_y). Synchronous.
+ */
+vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, double mu,
+                           double* S_out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VESB300_H */

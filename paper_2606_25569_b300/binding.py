@@ -1,0 +1,212 @@
+"""Thin ctypes binding of the vesb300 C ABI (include/vesb300.h): argument marshalling only.
+
+Every computation runs in libvesb300.so. Loading fails loudly when the library is missing;
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvesb300.so")
+
+VS_FLAG_FARFIELD_FP64 = 1
+
+STATUS = {0: "VS_OK", 1: "VS_ERR_INVALID_ARG", 2: "VS_ERR_CUDA", 3: "VS_ERR_NOMEM",
+          4: "VS_ERR_NOT_CONVERGED", 5: "VS_ERR_UNSTABLE", 6: "VS_ERR_TIMEOUT", 7: "VS_ERR_NO_NETWORK"}
+
+FUNCTIONS = {
+    "vs_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "vs_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "vs_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_get_positions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_get_tension": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_get_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_get_reference": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_get_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "vs_destroy": (None, [ctypes.c_void_p]),
+    "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_farfield_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_farfield_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_farfield_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "vs_farfield_plan_destroy": (None, [ctypes.c_void_p]),
+    "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libvesb300.so (built in-tree by paper_2606_25569_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libvesb300.so is not built: run python -m paper_2606_25569_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in FUNCTIONS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class VsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class VsParams(ctypes.Structure):
+    _fields_ = [("kappa_b", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
+                ("corr_tol", ctypes.c_double), ("mode", ctypes.c_int32), ("near_field", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("pad_", ctypes.c_int32), ("flags", ctypes.c_uint64)]
+
+
+class VsFlow(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("p", ctypes.c_double * 4)]
+
+
+def _ptr(a):
+    """Device/host address of a numpy array or a torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    return int(a)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Suspension:
+    """Owner of a vs_suspension handle (vs_create ... vs_destroy)."""
+
+    def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
+                 flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.M = len(off) - 1
+        self.P = int(off[-1])
+        p = VsParams(kappa, mu, dt, corr_tol, 0, 1 if near_field else 0, 0, 0,
+                     VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0)
+        f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
+        st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),
+                         ctypes.byref(self._h))
+        if st != 0:
+            raise VsError(st, L.vs_last_error(None).decode())
+
+    def _check(self, st):
+        if st != 0:
+            raise VsError(st, lib().vs_last_error(self._h).decode())
+
+    def step(self, n=1):
+        self._check(lib().vs_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(lib().vs_sync(self._h))
+
+    def set_state(self, xy, sigma):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        self._check(lib().vs_set_state(self._h, _ptr(xy), _ptr(sigma)))
+
+    def _get(self, fn, n):
+        out = np.empty(n)
+        self._check(fn(self._h, _ptr(out), n))
+        return out
+
+    def positions(self):
+        return self._get(lib().vs_get_positions, 2 * self.P)
+
+    def tension(self):
+        return self._get(lib().vs_get_tension, self.P)
+
+    def velocity(self):
+        return self._get(lib().vs_get_velocity, 2 * self.P)
+
+    def reference(self):
+        r = self._get(lib().vs_get_reference, 2 * self.M)
+        return r[:self.M], r[self.M:]
+
+    def counters(self):
+        out = np.zeros(4, dtype=np.int64)
+        self._check(lib().vs_get_counters(self._h, _ptr(out)))
+        return {"steps": int(out[0]), "corrections": int(out[1]), "near_pairs": int(out[2]), "err": int(out[3])}
+
+    def device_ptrs(self):
+        a, b = ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(lib().vs_get_device_ptrs(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if self._h:
+            lib().vs_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FarFieldPlan:
+    """vs_farfield_plan: far-field single layer of given densities at every point."""
+
+    def __init__(self, offsets, mu=1.0, near_mask=False, precision=0, stream=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        st = L.vs_farfield_plan_create(_ptr(off), len(off) - 1, float(mu), 1 if near_mask else 0, int(precision),
+                                       _stream(stream), ctypes.byref(self._h))
+        if st != 0:
+            raise VsError(st, L.vs_farfield_last_error(None).decode())
+
+    def eval(self, xy, f, u):
+        """xy, f, u: device tensors (float64, CSR blocks). u is overwritten."""
+        st = lib().vs_farfield_eval(self._h, _ptr(xy), _ptr(f), _ptr(u))
+        if st != 0:
+            raise VsError(st, lib().vs_farfield_last_error(self._h).decode())
+
+    def counters(self):
+        out = np.zeros(2, dtype=np.int64)
+        st = lib().vs_farfield_counters(self._h, _ptr(out))
+        if st != 0:
+            raise VsError(st, lib().vs_farfield_last_error(self._h).decode())
+        return {"err": int(out[0]), "near_pairs": int(out[1])}
+
+    def close(self):
+        if self._h:
+            lib().vs_farfield_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def self_matrices(xy_dev, offsets, mu, out_dev, stream=None):
+    """vs_self_matrices: xy_dev / out_dev device tensors (float64)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    st = lib().vs_self_matrices(_ptr(xy_dev), _ptr(off), len(off) - 1, float(mu), _ptr(out_dev), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_self_matrices failed")

@@ -1,0 +1,66 @@
+// Shared definitions for the vesicle-suspension kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#define VS_PI 3.14159265358979323846
+
+namespace vs {
+
+constexpr int NMAX = 128;          // largest points per vesicle handled by the per-vesicle kernels
+constexpr int TAB_STRIDE = 17;     // table doubles per N (see tables.cuh)
+constexpr int MAX_NEAR = 8;        // near source vesicles recorded per target point
+
+// Device-side error bits, OR-ed into one word per suspension and read back by the host.
+enum : unsigned {
+  ERR_PIVOT = 1u,        // zero pivot in a batched LU
+  ERR_NONFINITE = 2u,    // NaN / Inf in a state vector
+  ERR_CORRECTION = 4u,   // area/length correction did not converge
+  ERR_NEAR_OVERFLOW = 8u // a target had more than MAX_NEAR near vesicles
+};
+
+// Per-vesicle index arrays (device pointers, length M).
+struct VesIndex {
+  const int32_t* N;     // points of vesicle v (even, 8..NMAX)
+  const int64_t* off;   // first point of v in the point arrays
+  const int64_t* moff;  // first double of v's matrix scratch (25 N^2 doubles)
+  const int64_t* toff;  // first double of the tables for v's N
+};
+
+// Matrix scratch layout of one vesicle, in units of N^2 doubles from moff.
+struct MatLayout {
+  static __host__ __device__ inline int64_t slot(int s) { return s ? 7 : 0; }  // S 4, T 2, L 1
+  static constexpr int64_t S = 0, T = 4, L = 6;
+  static constexpr int64_t D4 = 14, B = 15, W = 19, A = 21, TOTAL = 25;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024). All threads get it.
+__device__ inline double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// out_i = sum_j c[(i - j) mod N] v_j : a circulant matrix-vector product (thread i).
+__device__ __forceinline__ double circ_row(const double* c, const double* v, int N, int i) {
+  double acc = 0.0;
+  int m = i;
+  for (int j = 0; j < N; ++j) {
+    acc = fma(c[m], v[j], acc);
+    m = (m == 0) ? N - 1 : m - 1;
+  }
+  return acc;
+}
+
+}  // namespace vs

@@ -1,0 +1,140 @@
+// Per-vesicle geometry, membrane force and background flow (Sec. 2.2.1, Eq. elastic_force,
+// Sec. 5.3-5.5). One CTA of NMAX threads per vesicle, thread j owns point j.
+#pragma once
+#include "common.cuh"
+
+namespace vs {
+
+struct FlowDev {
+  int kind;        // 0 none, 1 shear, 2 Taylor-Green, 3 Poiseuille
+  double p0, p1;
+};
+
+__device__ __forceinline__ double2 background_flow(const FlowDev& f, double x, double y) {
+  switch (f.kind) {
+    case 1: return make_double2(f.p0 * y, 0.0);
+    case 2: {
+      const double a = VS_PI * x / f.p1, b = VS_PI * y / f.p1;
+      return make_double2(f.p0 * sin(a) * cos(b), -f.p0 * cos(a) * sin(b));
+    }
+    case 3: {
+      const double r = y / f.p1;
+      return make_double2(f.p0 * (1.0 - r * r), 0.0);
+    }
+    default: return make_double2(0.0, 0.0);
+  }
+}
+
+// Geometry outputs at the N points of every vesicle.
+struct GeomOut {
+  double* sa;   // |X_alpha|
+  double* tx;   // X_s
+  double* ty;
+  double* bx;   // X_ssss
+  double* by;
+  double* area;    // [M]
+  double* length;  // [M]
+};
+
+// Force/source outputs (only written when `f` is non-null). With f_in non-null the density is
+// taken from f_in instead of the membrane force.
+struct ForceOut {
+  double* f;           // f = -kappa X_ssss + (sigma X_s)_s, CSR blocks [f_x(N), f_y(N)] per vesicle
+  double* u;           // velocity accumulator (CSR blocks): initialised to u_inf(X)
+  float4* src;         // (x - c_v, y - c_v, g_x, g_y), g = f |X_alpha| (2 pi/N) / (4 pi mu)
+  double2* centre;     // c_v (mean of the points) [M]
+  float4* centre32;    // (hi_x, hi_y, lo_x, lo_y) float split of c_v [M]
+  float* h2;           // (L_v/N_v)^2 [M]
+  double* g64;         // FP64 copy of g, CSR blocks (for the FP64 far-field variant)
+};
+
+__global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __restrict__ xy,
+                                                   const double* __restrict__ sigma,
+                                                   const double* __restrict__ tab, double kappa,
+                                                   double mu, FlowDev flow, GeomOut g,
+                                                   ForceOut fo, const double* __restrict__ f_in) {
+  __shared__ double d[NMAX], xs[NMAX], ys[NMAX], w1[NMAX], w2[NMAX], red[NMAX / 32];
+  const int v = blockIdx.x;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int i = threadIdx.x;
+  const bool act = i < N;
+  const double* T = tab + vi.toff[v];
+  if (act) {
+    d[i] = T[i];
+    xs[i] = xy[2 * o + i];
+    ys[i] = xy[2 * o + N + i];
+  }
+  __syncthreads();
+  double xa = 0.0, ya = 0.0;
+  if (act) {
+    xa = circ_row(d, xs, N, i);
+    ya = circ_row(d, ys, N, i);
+  }
+  const double sa = act ? sqrt(xa * xa + ya * ya) : 1.0;
+  const double tx = xa / sa, ty = ya / sa;
+  const double dal = 2.0 * VS_PI / N;
+  const double area = block_sum(act ? 0.5 * (xs[i] * ya - ys[i] * xa) * dal : 0.0, red);
+  const double length = block_sum(act ? sa * dal : 0.0, red);
+  const double cxs = block_sum(act ? xs[i] : 0.0, red);
+  const double cys = block_sum(act ? ys[i] : 0.0, red);
+  // X_ssss: four applications of D_s = diag(1/sa) D_alpha to each coordinate
+  double bx = act ? xs[i] : 0.0, by = act ? ys[i] : 0.0;
+  for (int r = 0; r < 4; ++r) {
+    __syncthreads();
+    if (act) { w1[i] = bx; w2[i] = by; }
+    __syncthreads();
+    if (act) {
+      bx = circ_row(d, w1, N, i) / sa;
+      by = circ_row(d, w2, N, i) / sa;
+    }
+  }
+  if (act) {
+    g.sa[o + i] = sa;
+    g.tx[o + i] = tx;
+    g.ty[o + i] = ty;
+    g.bx[o + i] = bx;
+    g.by[o + i] = by;
+  }
+  if (i == 0) {
+    g.area[v] = area;
+    g.length[v] = length;
+  }
+  if (fo.f == nullptr) return;
+  // force: f = -kappa X_ssss + D_s(sigma X_s)
+  const double sg = (act && sigma) ? sigma[o + i] : 0.0;  // sigma may be null with f_in
+  __syncthreads();
+  if (act) { w1[i] = sg * tx; w2[i] = sg * ty; }
+  __syncthreads();
+  double fx = 0.0, fy = 0.0;
+  if (act) {
+    if (f_in) {  // caller-supplied density (far-field evaluation of a given force)
+      fx = f_in[2 * o + i];
+      fy = f_in[2 * o + N + i];
+    } else {
+      fx = -kappa * bx + circ_row(d, w1, N, i) / sa;
+      fy = -kappa * by + circ_row(d, w2, N, i) / sa;
+    }
+  }
+  const double cx = cxs / N, cy = cys / N;
+  if (act) {
+    fo.f[2 * o + i] = fx;
+    fo.f[2 * o + N + i] = fy;
+    const double2 ub = background_flow(flow, xs[i], ys[i]);
+    fo.u[2 * o + i] = ub.x;
+    fo.u[2 * o + N + i] = ub.y;
+    const double c = sa * dal / (4.0 * VS_PI * mu);
+    fo.g64[2 * o + i] = fx * c;
+    fo.g64[2 * o + N + i] = fy * c;
+    fo.src[o + i] = make_float4((float)(xs[i] - cx), (float)(ys[i] - cy), (float)(fx * c), (float)(fy * c));
+  }
+  if (i == 0) {
+    fo.centre[v] = make_double2(cx, cy);
+    const float hx = (float)cx, hy = (float)cy;
+    fo.centre32[v] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
+    const double h = length / N;
+    fo.h2[v] = (float)(h * h);
+  }
+}
+
+}  // namespace vs

@@ -1,0 +1,595 @@
+// C ABI and host orchestration of the vesicle-suspension step (Algorithm 1 with exact operators).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vesb300.h"
+#include "common.cuh"
+#include "k_dense.cuh"
+#include "k_farfield.cuh"
+#include "k_geometry.cuh"
+#include "k_selfmat.cuh"
+#include "k_vesicle.cuh"
+#include "tables.cuh"
+
+using namespace vs;
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// layout shared by suspensions and far-field plans
+struct Layout {
+  int M = 0;
+  int64_t P = 0;
+  int nmax = 0;
+  std::vector<int32_t> N;
+  std::vector<int64_t> off, moff, toff;
+  std::vector<int32_t> owner, chunk;
+  std::vector<double> tab;
+};
+
+bool build_layout(const int64_t* offsets, int M, Layout& L, std::string& msg) {
+  if (M < 1 || offsets == nullptr) { msg = "M must be >= 1 and offsets non-null"; return false; }
+  if (offsets[0] != 0) { msg = "offsets[0] must be 0"; return false; }
+  L.M = M;
+  L.N.resize(M);
+  L.off.resize(M + 1);
+  L.moff.resize(M + 1);
+  L.toff.resize(M);
+  std::map<int, int64_t> tpos;
+  int64_t moff = 0;
+  for (int v = 0; v < M; ++v) {
+    const int64_t n = offsets[v + 1] - offsets[v];
+    if (n < 8 || n > NMAX || (n & 1)) {
+      char b[160];
+      snprintf(b, sizeof b, "vesicle %d has %lld points; need an even count in [8, %d]", v, (long long)n, NMAX);
+      msg = b;
+      return false;
+    }
+    L.N[v] = (int32_t)n;
+    L.off[v] = offsets[v];
+    L.moff[v] = moff;
+    moff += MatLayout::TOTAL * n * n;
+    if (!tpos.count((int)n)) {
+      tpos[(int)n] = (int64_t)L.tab.size();
+      L.tab.resize(L.tab.size() + TAB_STRIDE * n);
+      build_tables((int)n, L.tab.data() + tpos[(int)n]);
+    }
+    L.toff[v] = tpos[(int)n];
+    L.nmax = std::max(L.nmax, (int)n);
+  }
+  L.off[M] = offsets[M];
+  L.moff[M] = moff;
+  L.P = offsets[M];
+  L.owner.resize(L.P);
+  for (int v = 0; v < M; ++v)
+    for (int64_t p = L.off[v]; p < L.off[v + 1]; ++p) L.owner[p] = v;
+  L.chunk.clear();
+  L.chunk.push_back(0);
+  int64_t acc = 0;
+  for (int v = 0; v < M; ++v) {
+    if (acc + L.N[v] > FF_CHUNK) { L.chunk.push_back(v); acc = 0; }
+    acc += L.N[v];
+  }
+  L.chunk.push_back(M);
+  return true;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <class T>
+cudaError_t upload(T* d, const T* h, size_t n, cudaStream_t s) {
+  return cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+struct DevLayout {
+  int32_t* N = nullptr;
+  int64_t* off = nullptr;
+  int64_t* moff = nullptr;
+  int64_t* toff = nullptr;
+  int32_t* owner = nullptr;
+  int32_t* chunk = nullptr;
+  double* tab = nullptr;
+  VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
+  void release() {
+    cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
+    cudaFree(owner); cudaFree(chunk); cudaFree(tab);
+    *this = DevLayout{};
+  }
+};
+
+cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
+  cudaError_t e;
+#define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  VS_TRY(dalloc(&D.N, L.M));
+  VS_TRY(dalloc(&D.off, L.M + 1));
+  VS_TRY(dalloc(&D.moff, L.M + 1));
+  VS_TRY(dalloc(&D.toff, L.M));
+  VS_TRY(dalloc(&D.owner, L.P));
+  VS_TRY(dalloc(&D.chunk, L.chunk.size()));
+  VS_TRY(dalloc(&D.tab, L.tab.size()));
+  VS_TRY(upload(D.N, L.N.data(), L.M, s));
+  VS_TRY(upload(D.off, L.off.data(), L.M + 1, s));
+  VS_TRY(upload(D.moff, L.moff.data(), L.M + 1, s));
+  VS_TRY(upload(D.toff, L.toff.data(), L.M, s));
+  VS_TRY(upload(D.owner, L.owner.data(), L.P, s));
+  VS_TRY(upload(D.chunk, L.chunk.data(), L.chunk.size(), s));
+  VS_TRY(upload(D.tab, L.tab.data(), L.tab.size(), s));
+#undef VS_TRY
+  return cudaStreamSynchronize(s);
+}
+
+// Per-point and per-vesicle work buffers used by the force / far-field stage.
+struct SourceBufs {
+  double* f = nullptr;
+  double* g64 = nullptr;
+  float4* src = nullptr;
+  double2* centre = nullptr;
+  float4* centre32 = nullptr;
+  float* h2 = nullptr;
+  int* near_cnt = nullptr;
+  int* near_v = nullptr;
+  double *sa = nullptr, *tx = nullptr, *ty = nullptr, *bx = nullptr, *by = nullptr;
+  double *area = nullptr, *length = nullptr;
+  cudaError_t alloc(int64_t P, int M) {
+    cudaError_t e;
+#define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+    VS_TRY(dalloc(&f, 2 * P)); VS_TRY(dalloc(&g64, 2 * P)); VS_TRY(dalloc(&src, P));
+    VS_TRY(dalloc(&centre, M)); VS_TRY(dalloc(&centre32, M)); VS_TRY(dalloc(&h2, M));
+    VS_TRY(dalloc(&near_cnt, P)); VS_TRY(dalloc(&near_v, P * MAX_NEAR));
+    VS_TRY(dalloc(&sa, P)); VS_TRY(dalloc(&tx, P)); VS_TRY(dalloc(&ty, P));
+    VS_TRY(dalloc(&bx, P)); VS_TRY(dalloc(&by, P));
+    VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M));
+#undef VS_TRY
+    return cudaSuccess;
+  }
+  void release() {
+    cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
+    cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
+    cudaFree(by); cudaFree(area); cudaFree(length);
+    *this = SourceBufs{};
+  }
+  GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length}; }
+  PointGeom pg() const { return PointGeom{sa, tx, ty}; }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+struct vs_suspension {
+  Layout L;
+  DevLayout D;
+  SourceBufs B;
+  vs_params p{};
+  vs_flow flow{};
+  cudaStream_t stream = nullptr;
+  double *xy = nullptr, *xy_star = nullptr, *xy_next = nullptr, *sigma = nullptr;
+  double *u = nullptr, *u_r = nullptr, *A0 = nullptr, *L0 = nullptr, *scratch = nullptr;
+  int *piv = nullptr, *dirty = nullptr, *fired = nullptr;
+  unsigned* err = nullptr;
+  int cur = 0;
+  int64_t steps = 0;
+  std::string msg;
+};
+
+struct vs_farfield_plan {
+  Layout L;
+  DevLayout D;
+  SourceBufs B;
+  double mu = 1.0;
+  int near_mask = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  unsigned* err = nullptr;
+  std::string msg;
+};
+
+namespace {
+
+vs_status cuda_fail(std::string& msg, cudaError_t e, const char* where) {
+  msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? VS_ERR_NOMEM : VS_ERR_CUDA;
+}
+
+#define VS_CK(h, x, where)                          \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return cuda_fail((h)->msg, e_, where); \
+  } while (0)
+
+inline dim3 gemm_grid(int m, int n, int M) { return dim3((n + GT - 1) / GT, (m + GT - 1) / GT, M); }
+
+FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
+
+// S, T, L at slot s for the geometry currently in the SourceBufs, then LU of L.
+vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* active) {
+  const Layout& L = h->L;
+  const int M = L.M, n = L.nmax;
+  const VesIndex vi = h->D.vi();
+  k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                                     h->p.mu, h->scratch, s, active);
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
+  k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active);
+  k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active);
+  k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, h->piv, s, h->err, active);
+  VS_CK(h, cudaGetLastError(), "operator build");
+  return VS_OK;
+}
+
+vs_status geometry(vs_suspension* h, const double* xy, bool with_force) {
+  ForceOut fo{};
+  if (with_force)
+    fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
+  k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
+                                             flow_dev(h->flow), h->B.geom(), fo, nullptr);
+  VS_CK(h, cudaGetLastError(), "geometry");
+  return VS_OK;
+}
+
+vs_status far_field(vs_suspension* h) {
+  const Layout& L = h->L;
+  if (L.M < 2) return VS_OK;
+  FarFieldArgs a{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1,
+                 h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
+  const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
+  if (h->p.flags & VS_FLAG_FARFIELD_FP64)
+    k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N);
+  else
+    k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+  VS_CK(h, cudaGetLastError(), "far field");
+  return VS_OK;
+}
+
+vs_status step_once(vs_suspension* h) {
+  const Layout& L = h->L;
+  const int M = L.M, n = L.nmax;
+  const VesIndex vi = h->D.vi();
+  vs_status st;
+  const int cur = h->cur, nxt = 1 - h->cur;
+  // (1) geometry + force at X^n, u = u_inf(X^n)
+  if ((st = geometry(h, h->xy, true)) != VS_OK) return st;
+  // (2) operators at X^n where the cache is stale (first step, or after a correction)
+  if ((st = build_operators(h, h->xy, cur, h->dirty)) != VS_OK) return st;
+  // (3) u += far field
+  if ((st = far_field(h)) != VS_OK) return st;
+  // (4) advection
+  k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
+                                     h->xy_star);
+  VS_CK(h, cudaGetLastError(), "advection");
+  // (5) relaxation at X*
+  if ((st = geometry(h, h->xy_star, false)) != VS_OK) return st;
+  if ((st = build_operators(h, h->xy_star, nxt, nullptr)) != VS_OK) return st;
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
+  k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr);
+  k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr);
+  k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 0, h->p.kappa_b}, nullptr);
+  k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 1, h->p.kappa_b}, nullptr);
+  k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr);
+  k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, nxt, h->piv, nullptr);
+  k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, nxt, h->p.dt}, nullptr);
+  k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr);
+  k_relax_solve<<<M, 256, 0, h->stream>>>(vi, h->xy_star, h->scratch, h->piv, h->xy_next);
+  VS_CK(h, cudaGetLastError(), "relaxation");
+  // (6) redistribution of X^{n+1}; u carried to the new parameters
+  k_redistribute<<<M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r);
+  VS_CK(h, cudaGetLastError(), "redistribution");
+  // (7) tension at the redistributed X^{n+1}; operators cached in slot nxt for the next step
+  if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
+  if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
+  k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u_r, h->B.pg(), h->D.tab, h->scratch, nxt, h->piv,
+                                      h->p.kappa_b, h->sigma);
+  VS_CK(h, cudaGetLastError(), "tension");
+  // (8) area/length correction; marks the cached operators stale where it fires
+  k_correct<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab, h->dirty, h->fired, h->err);
+  VS_CK(h, cudaGetLastError(), "correction");
+  h->cur = nxt;
+  h->steps += 1;
+  return VS_OK;
+}
+
+vs_status read_err(vs_suspension* h) {
+  VS_CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+  unsigned e = 0;
+  VS_CK(h, cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost), "error word");
+  if (e & ERR_NONFINITE) { h->msg = "non-finite vesicle state"; return VS_ERR_UNSTABLE; }
+  if (e & ERR_PIVOT) { h->msg = "singular per-vesicle system (zero pivot)"; return VS_ERR_UNSTABLE; }
+  if (e & ERR_CORRECTION) { h->msg = "area/length correction did not converge"; return VS_ERR_NOT_CONVERGED; }
+  if (e & ERR_NEAR_OVERFLOW) { h->msg = "more near vesicles per target than recorded"; return VS_ERR_UNSTABLE; }
+  return VS_OK;
+}
+
+bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
+  if (!p || !f) { msg = "null params or flow"; return false; }
+  if (!(p->kappa_b > 0) || !(p->mu > 0) || !(p->dt > 0) || !(p->corr_tol >= 0) || !std::isfinite(p->dt)) {
+    msg = "kappa_b, mu, dt must be positive and corr_tol non-negative";
+    return false;
+  }
+  if (p->mode != 0) { msg = "only the plain mode (0) is available"; return false; }
+  if (f->kind < 0 || f->kind > 3) { msg = "unknown flow kind"; return false; }
+  if ((f->kind == 2 || f->kind == 3) && !(f->p[1] != 0.0)) { msg = "flow length scale p[1] must be non-zero"; return false; }
+  return true;
+}
+
+void free_suspension(vs_suspension* h) {
+  if (!h) return;
+  h->D.release();
+  h->B.release();
+  cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
+  cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
+  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err);
+}
+
+thread_local std::string g_create_msg;
+
+}  // namespace
+
+extern "C" {
+
+vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const vs_params* params,
+                    const vs_flow* flow, void* cuda_stream, vs_suspension** out) {
+  if (!out) return VS_ERR_INVALID_ARG;
+  *out = nullptr;
+  vs_suspension* h = new (std::nothrow) vs_suspension();
+  if (!h) return VS_ERR_NOMEM;
+  auto fail = [&](vs_status s) {
+    g_create_msg = h->msg;
+    free_suspension(h);
+    delete h;
+    return s;
+  };
+  if (!xy) { h->msg = "null xy"; return fail(VS_ERR_INVALID_ARG); }
+  if (!params_ok(params, flow, h->msg)) return fail(VS_ERR_INVALID_ARG);
+  if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
+  for (int64_t i = 0; i < 2 * h->L.P; ++i)
+    if (!std::isfinite(xy[i])) { h->msg = "non-finite input point"; return fail(VS_ERR_INVALID_ARG); }
+  h->p = *params;
+  h->flow = *flow;
+  h->stream = (cudaStream_t)cuda_stream;
+  const Layout& L = h->L;
+  cudaError_t e;
+#define VS_A(x) do { e = (x); if (e != cudaSuccess) { cuda_fail(h->msg, e, "vs_create"); return fail(e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA); } } while (0)
+  VS_A(upload_layout(L, h->D, h->stream));
+  VS_A(h->B.alloc(L.P, L.M));
+  VS_A(dalloc(&h->xy, 2 * L.P)); VS_A(dalloc(&h->xy_star, 2 * L.P)); VS_A(dalloc(&h->xy_next, 2 * L.P));
+  VS_A(dalloc(&h->sigma, L.P)); VS_A(dalloc(&h->u, 2 * L.P)); VS_A(dalloc(&h->u_r, 2 * L.P));
+  VS_A(dalloc(&h->A0, L.M)); VS_A(dalloc(&h->L0, L.M));
+  VS_A(dalloc(&h->scratch, L.moff[L.M])); VS_A(dalloc(&h->piv, 4 * L.P));
+  VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
+  VS_A(cudaMemsetAsync(h->fired, 0, sizeof(int), h->stream));
+  VS_A(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
+  VS_A(cudaMemsetAsync(h->sigma, 0, L.P * sizeof(double), h->stream));
+  VS_A(cudaMemsetAsync(h->u, 0, 2 * L.P * sizeof(double), h->stream));
+  VS_A(cudaMemsetAsync(h->B.near_cnt, 0, L.P * sizeof(int), h->stream));
+  VS_A(upload(h->xy_next, xy, 2 * L.P, h->stream));
+  {
+    std::vector<int> ones(L.M, 0);
+    VS_A(upload(h->dirty, ones.data(), L.M, h->stream));
+    VS_A(cudaStreamSynchronize(h->stream));
+  }
+  const VesIndex vi = h->D.vi();
+  // redistribute X^0, record A_0 and L_0, initial tension from self + background terms
+  k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r);
+  VS_A(cudaGetLastError());
+  if (geometry(h, h->xy, true) != VS_OK) return fail(VS_ERR_CUDA);
+  VS_A(cudaMemcpyAsync(h->A0, h->B.area, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VS_A(cudaMemcpyAsync(h->L0, h->B.length, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
+  k_tension<<<L.M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u, h->B.pg(), h->D.tab, h->scratch, 0, h->piv,
+                                        h->p.kappa_b, h->sigma);
+  VS_A(cudaGetLastError());
+  h->cur = 0;
+  VS_A(cudaStreamSynchronize(h->stream));
+#undef VS_A
+  const vs_status st = read_err(h);
+  if (st != VS_OK) return fail(st);
+  *out = h;
+  return VS_OK;
+}
+
+vs_status vs_step(vs_suspension* h, int32_t nsteps) {
+  if (!h || nsteps < 0) return VS_ERR_INVALID_ARG;
+  for (int32_t k = 0; k < nsteps; ++k) {
+    const vs_status st = step_once(h);
+    if (st != VS_OK) return st;
+  }
+  return VS_OK;
+}
+
+vs_status vs_sync(vs_suspension* h) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  return read_err(h);
+}
+
+vs_status vs_set_state(vs_suspension* h, const double* xy, const double* sigma) {
+  if (!h || !xy || !sigma) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  VS_CK(h, upload(h->xy, xy, 2 * L.P, h->stream), "set_state");
+  VS_CK(h, upload(h->sigma, sigma, L.P, h->stream), "set_state");
+  std::vector<int> ones(L.M, 1);
+  VS_CK(h, upload(h->dirty, ones.data(), L.M, h->stream), "set_state");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "set_state");
+  return VS_OK;
+}
+
+static vs_status copy_out(vs_suspension* h, const double* src, int64_t n, double* dst, int64_t cap) {
+  if (!h || !dst) return VS_ERR_INVALID_ARG;
+  if (cap < n) { h->msg = "output buffer too small"; return VS_ERR_INVALID_ARG; }
+  const vs_status st = read_err(h);
+  VS_CK(h, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy out");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "copy out");
+  return st;
+}
+
+vs_status vs_get_positions(vs_suspension* h, double* xy, int64_t cap) {
+  return h ? copy_out(h, h->xy, 2 * h->L.P, xy, cap) : VS_ERR_INVALID_ARG;
+}
+vs_status vs_get_tension(vs_suspension* h, double* sigma, int64_t cap) {
+  return h ? copy_out(h, h->sigma, h->L.P, sigma, cap) : VS_ERR_INVALID_ARG;
+}
+vs_status vs_get_velocity(vs_suspension* h, double* u, int64_t cap) {
+  return h ? copy_out(h, h->u, 2 * h->L.P, u, cap) : VS_ERR_INVALID_ARG;
+}
+vs_status vs_get_reference(vs_suspension* h, double* a0l0, int64_t cap) {
+  if (!h || !a0l0) return VS_ERR_INVALID_ARG;
+  if (cap < 2 * h->L.M) { h->msg = "output buffer too small"; return VS_ERR_INVALID_ARG; }
+  VS_CK(h, cudaStreamSynchronize(h->stream), "reference");
+  VS_CK(h, cudaMemcpy(a0l0, h->A0, h->L.M * sizeof(double), cudaMemcpyDeviceToHost), "reference");
+  VS_CK(h, cudaMemcpy(a0l0 + h->L.M, h->L0, h->L.M * sizeof(double), cudaMemcpyDeviceToHost), "reference");
+  return VS_OK;
+}
+
+vs_status vs_get_device_ptrs(const vs_suspension* h, const double** xy, const double** sigma) {
+  if (!h || !xy || !sigma) return VS_ERR_INVALID_ARG;
+  *xy = h->xy;
+  *sigma = h->sigma;
+  return VS_OK;
+}
+
+vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
+  if (!h || !out4) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaStreamSynchronize(h->stream), "counters");
+  int fired = 0;
+  unsigned e = 0;
+  VS_CK(h, cudaMemcpy(&fired, h->fired, sizeof fired, cudaMemcpyDeviceToHost), "counters");
+  VS_CK(h, cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost), "counters");
+  std::vector<int> nc(h->L.P);
+  VS_CK(h, cudaMemcpy(nc.data(), h->B.near_cnt, h->L.P * sizeof(int), cudaMemcpyDeviceToHost), "counters");
+  int64_t pairs = 0;
+  for (int c : nc) pairs += c;
+  out4[0] = h->steps;
+  out4[1] = fired;
+  out4[2] = pairs;
+  out4[3] = e;
+  return VS_OK;
+}
+
+const char* vs_last_error(const vs_suspension* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }
+
+void vs_destroy(vs_suspension* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_suspension(h);
+  delete h;
+}
+
+// ---------------------------------------------------------------------------------------------
+vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, int32_t near_mask,
+                                  int32_t precision, void* cuda_stream, vs_farfield_plan** out) {
+  if (!out) return VS_ERR_INVALID_ARG;
+  *out = nullptr;
+  vs_farfield_plan* h = new (std::nothrow) vs_farfield_plan();
+  if (!h) return VS_ERR_NOMEM;
+  auto fail = [&](vs_status s) {
+    g_create_msg = h->msg;
+    h->D.release();
+    h->B.release();
+    cudaFree(h->err);
+    delete h;
+    return s;
+  };
+  if (!(mu > 0) || (precision != 0 && precision != 1)) { h->msg = "mu must be > 0, precision 0 or 1"; return fail(VS_ERR_INVALID_ARG); }
+  if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
+  h->mu = mu;
+  h->near_mask = near_mask ? 1 : 0;
+  h->precision = precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if ((e = upload_layout(h->L, h->D, h->stream)) != cudaSuccess ||
+      (e = h->B.alloc(h->L.P, h->L.M)) != cudaSuccess || (e = dalloc(&h->err, 1)) != cudaSuccess ||
+      (e = cudaMemset(h->err, 0, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMemset(h->B.near_cnt, 0, h->L.P * sizeof(int))) != cudaSuccess) {
+    cuda_fail(h->msg, e, "vs_farfield_plan_create");
+    return fail(e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
+  }
+  *out = h;
+  return VS_OK;
+}
+
+vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* f, double* u) {
+  if (!h || !xy || !f || !u) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  ForceOut fo{h->B.f, u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
+  FlowDev none{0, 0.0, 0.0};
+  k_geometry<<<L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, nullptr, h->D.tab, 1.0, h->mu, none, h->B.geom(), fo, f);
+  VS_CK(h, cudaGetLastError(), "far-field sources");
+  if (L.M < 2) return VS_OK;
+  FarFieldArgs a{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1, h->near_mask, u,
+                 h->B.near_cnt, h->B.near_v, h->err};
+  const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
+  if (h->precision == 1)
+    k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
+  else
+    k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+  VS_CK(h, cudaGetLastError(), "far field");
+  return VS_OK;
+}
+
+vs_status vs_farfield_counters(vs_farfield_plan* h, int64_t* out2) {
+  if (!h || !out2) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaStreamSynchronize(h->stream), "counters");
+  unsigned e = 0;
+  VS_CK(h, cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost), "counters");
+  std::vector<int> nc(h->L.P);
+  VS_CK(h, cudaMemcpy(nc.data(), h->B.near_cnt, h->L.P * sizeof(int), cudaMemcpyDeviceToHost), "counters");
+  int64_t pairs = 0;
+  for (int c : nc) pairs += c;
+  out2[0] = e;
+  out2[1] = pairs;
+  return VS_OK;
+}
+
+const char* vs_farfield_last_error(const vs_farfield_plan* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }
+
+void vs_farfield_plan_destroy(vs_farfield_plan* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  h->D.release();
+  h->B.release();
+  cudaFree(h->err);
+  delete h;
+}
+
+// ---------------------------------------------------------------------------------------------
+vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, double mu, double* S_out,
+                           void* cuda_stream) {
+  if (!xy || !S_out || !(mu > 0)) return VS_ERR_INVALID_ARG;
+  Layout L;
+  std::string msg;
+  if (!build_layout(offsets, M, L, msg)) return VS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // a private layout whose matrix offsets are 4 N^2 apart (the output's packing)
+  std::vector<int64_t> moff(M + 1);
+  int64_t acc = 0;
+  for (int v = 0; v < M; ++v) { moff[v] = acc; acc += 4 * (int64_t)L.N[v] * L.N[v]; }
+  moff[M] = acc;
+  DevLayout D;
+  SourceBufs B;
+  cudaError_t e = upload_layout(L, D, s);
+  if (e == cudaSuccess) e = upload(D.moff, moff.data(), M + 1, s);
+  if (e == cudaSuccess) e = B.alloc(L.P, L.M);
+  if (e == cudaSuccess) {
+    FlowDev none{0, 0.0, 0.0};
+    k_geometry<<<M, NMAX, 0, s>>>(D.vi(), xy, nullptr, D.tab, 1.0, mu, none, B.geom(), ForceOut{}, nullptr);
+    const int n = L.nmax;
+    k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, 0,
+                                                               nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  D.release();
+  B.release();
+  return e == cudaSuccess ? VS_OK : (e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
+}
+
+}  // extern "C"

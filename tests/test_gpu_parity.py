@@ -1,0 +1,174 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 parts 1e-10 relative per vesicle (the stated bar for FP64 steps); the self
+matrix 1e-12 (a direct formula, no solve); FP32 compensated far field 1e-5 relative L2.
+"""
+import numpy as np
+import pytest
+
+from oracle.farfield import far_field
+from oracle.step import Params, Suspension as OracleSuspension
+from oracle.stokes import self_single_layer_matrix
+from paper_2606_25569_b300 import binding
+from paper_2606_25569_b300.workloads import farfield_box, single_shear, vesicle_outline
+
+from .gpu_util import csr, offsets, rel_err_per_vesicle, split
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _mixed(Ns, seed=0, spacing=3.0, R=1.0):
+    rng = np.random.default_rng(seed)
+    xs, ys = [], []
+    for v, N in enumerate(Ns):
+        x, y = vesicle_outline(N, float(rng.uniform(0.6, 0.9)), R, 2e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x + spacing * (v % 4))
+        ys.append(y + spacing * (v // 4))
+    return xs, ys
+
+
+def test_self_matrices_uneven_N():
+    Ns = [16, 32, 64, 128, 48, 8]
+    xs, ys = _mixed(Ns, 1)
+    off = offsets(xs)
+    out = torch.zeros(int(sum(4 * n * n for n in Ns)), dtype=torch.float64, device="cuda")
+    binding.self_matrices(_dev(csr(xs, ys)), off, 0.8, out)
+    got = out.cpu().numpy()
+    o = 0
+    for x, y in zip(xs, ys):
+        n = len(x)
+        S = got[o:o + 4 * n * n].reshape(2 * n, 2 * n)
+        ref = self_single_layer_matrix(x, y, 0.8)
+        assert np.max(np.abs(S - ref)) <= 1e-12 * np.max(np.abs(ref)), n
+        o += 4 * n * n
+
+
+def _ff_case(M, N, near, seed):
+    rng = np.random.default_rng(seed)
+    xs, ys = _mixed([N] * M, seed, spacing=2.3)
+    fx = [rng.standard_normal(N) for _ in range(M)]
+    fy = [rng.standard_normal(N) for _ in range(M)]
+    return xs, ys, fx, fy
+
+
+@pytest.mark.parametrize("near", [False, True])
+def test_farfield_fp64_matches_oracle(near):
+    xs, ys, fx, fy = _ff_case(9, 32, near, 2)
+    # pull one vesicle close to its neighbour so that the near mask has work
+    xs[1] = xs[1] - 0.25
+    off = offsets(xs)
+    plan = binding.FarFieldPlan(off, mu=1.3, near_mask=near, precision=1)
+    u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+    plan.eval(_dev(csr(xs, ys)), _dev(csr(fx, fy)), u)
+    c = plan.counters()
+    got = u.cpu().numpy()
+    ux, uy, pairs = far_field(xs, ys, fx, fy, 1.3, near_mask=near)
+    ref = csr(*_to_csr(ux, uy, xs))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert c["near_pairs"] == len(pairs)
+    if near:
+        assert len(pairs) > 0
+
+
+def _to_csr(ux, uy, xs):
+    out, o = [], 0
+    for x in xs:
+        n = len(x)
+        out.append(ux[o:o + n])
+        out.append(uy[o:o + n])
+        o += n
+    return [out[0::2], out[1::2]]
+
+
+def test_farfield_fp32_relative_l2():
+    wl, fx, fy = farfield_box(M=300, N=64, seed=3, box=20.0 * np.sqrt(300 / 2000.0))
+    off = wl.offsets
+    plan = binding.FarFieldPlan(off, mu=1.0, near_mask=False, precision=0)
+    u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+    plan.eval(_dev(wl.flat_xy()), _dev(csr(fx, fy)), u)
+    got = u.cpu().numpy()
+    rng = np.random.default_rng(0)
+    tgt = np.sort(rng.choice(off[-1], 1024, replace=False))
+    ux, uy, _ = far_field(wl.xs, wl.ys, fx, fy, 1.0, near_mask=False, targets=tgt)
+    owner = np.repeat(np.arange(wl.M), wl.counts)
+    loc = tgt - off[owner[tgt]]
+    gx = got[2 * off[owner[tgt]] + loc]
+    gy = got[2 * off[owner[tgt]] + wl.counts[owner[tgt]] + loc]
+    err = np.sqrt(np.sum((gx - ux) ** 2 + (gy - uy) ** 2) / np.sum(ux ** 2 + uy ** 2))
+    assert err <= 1e-5, err
+
+
+def _oracle_and_gpu(xs, ys, kappa, mu, dt, flow_kind, flow_p, corr_tol, fp64=True):
+    o = OracleSuspension(xs, ys, Params(kappa=kappa, mu=mu, dt=dt, flow_kind=flow_kind, flow_p=flow_p,
+                                        corr_tol=corr_tol))
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=kappa, mu=mu, dt=dt, corr_tol=corr_tol,
+                           flow_kind=flow_kind, flow_p=flow_p, farfield_fp64=fp64)
+    return o, g
+
+
+def _compare(o, g, tol_x=1e-10, tol_s=1e-8):
+    counts = [len(x) for x in o.xs]
+    gx, gy = split(g.positions(), counts)
+    ex = rel_err_per_vesicle(gx, gy, o.xs, o.ys)
+    sg = g.tension()
+    so = np.concatenate(o.sig)
+    es = np.max(np.abs(sg - so)) / np.max(np.abs(so))
+    assert ex <= tol_x, ex
+    assert es <= tol_s, es
+    return ex, es
+
+
+def test_create_matches_oracle_init():
+    wl = single_shear()
+    o, g = _oracle_and_gpu(wl.xs, wl.ys, 1.0, 1.0, 1e-4, 1, (1.0, 0, 0, 0), 0.01)
+    _compare(o, g, 1e-12, 1e-9)
+    A0, L0 = g.reference()
+    assert abs(A0[0] - o.A0[0]) <= 1e-13 * o.A0[0] and abs(L0[0] - o.L0[0]) <= 1e-13 * o.L0[0]
+
+
+def test_single_vesicle_steps_match_oracle():
+    wl = single_shear()
+    o, g = _oracle_and_gpu(wl.xs, wl.ys, 1.0, 1.0, 1e-4, 1, (1.0, 0, 0, 0), 0.01)
+    for k in range(5):
+        o.step()
+        g.step()
+        _compare(o, g)
+
+
+def test_uneven_suspension_fp64_farfield_matches_oracle():
+    xs, ys = _mixed([32, 64, 32, 16], 5, spacing=2.6)
+    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 1e-3, 2, (5.0, 8.0, 0, 0), 0.01)
+    for k in range(3):
+        o.step()
+        g.step()
+        _compare(o, g)
+    vg = g.velocity()
+    counts = [len(x) for x in xs]
+    vx, vy = split(vg, counts)
+    for v in range(len(xs)):
+        n = counts[v]
+        assert np.max(np.abs(vx[v] - o.velocity[v][:n])) <= 1e-10 * np.max(np.abs(o.velocity[v]))
+
+
+def test_forced_correction_matches_oracle():
+    xs, ys = _mixed([32, 32], 7, spacing=2.8)
+    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 5e-3, 1, (2.0, 0, 0, 0), 0.0)
+    for k in range(3):
+        o.step()
+        g.step()
+        _compare(o, g)
+    assert g.counters()["corrections"] == 6 and o.corrections == 6
+
+
+def test_fp32_farfield_step_close_to_oracle():
+    xs, ys = _mixed([32, 32, 32, 32], 9, spacing=2.6)
+    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 1e-3, 1, (1.0, 0, 0, 0), 0.01, fp64=False)
+    o.step()
+    g.step()
+    # FP32 velocities (relative 1e-5) enter X only through dt * u
+    _compare(o, g, tol_x=1e-7, tol_s=1e-3)
