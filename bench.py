@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the plain boundary-integral vesicle step on one B300 (vesicle-steps/s).
+
+Workload: the dense Poiseuille suspension of Sec. 5.5 -- 2000 vesicles x 64 points, 30% area
+fraction, channel of width 1, reduced area 0.65, Ca = 2, Cn = 0.025 -- drawn synthetically by
+paper_2606_25569_b300.workloads.poiseuille_dense (seed 5). One step = one pass of the whole
+hot path through libvesb300.so (force, far field with the near-field mask, advection,
+relaxation, redistribution, tension, correction).
+
+Prints one JSON line. Run as `python bench.py --gpus 1 --steps K --warmup W`, or under
+torch.distributed.run for N > 1 (independent replicas, weak scaling). `--impl reference`
+times the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+# the oracle baseline runs single-threaded: pin BLAS threads before numpy loads
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vesicle-steps/s: hybrid vs plain BIE on one B300 at shape error <=1e-2"
+UNIT = "vesicle-steps/s"
+MUFU_PER_CLK_SM = 16      # special-function results per clock per SM (4 per sub-partition)
+N_SM = 148
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vesb300", choices=["vesb300", "reference"])
+    ap.add_argument("--M", type=int, default=2000)
+    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    return poiseuille_dense(M=args.M, N=args.N, seed=5)
+
+
+def config_of(wl, args, extra=None):
+    c = {"workload": "dense Poiseuille suspension, %d vesicles x %d points, 30%% area fraction, "
+                     "channel width 1, reduced area 0.65, Ca 2, Cn 0.025" % (wl.M, args.N),
+         "mode": "plain BIE step (hybrid learned step not built)", "near_field": "mask only",
+         "dt": wl.dt, "farfield": "fp32 compensated", "l2": "working set > L2 (no flush needed)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------ roofline
+def kernel_flops(name, N, M):
+    """Algorithmic FP64 flops of one launch over M vesicles of N points (dense operator algebra)."""
+    n3 = float(N) ** 3
+    table = {
+        "k_bgemm<OpT>": 8 * n3, "k_bgemm<OpL>": 4 * n3, "k_bgemm<OpD2>": 2 * n3, "k_bgemm<OpD4>": 2 * n3,
+        "k_bgemm<OpB>": 4 * n3, "k_bgemm<OpPB>": 8 * n3, "k_bgemm<OpA>": 8 * n3,
+        "k_lu<A>": 2.0 / 3.0 * (2 * N) ** 3, "k_lu<L>": 2.0 / 3.0 * n3, "k_lu_solve_cols": 4 * n3,
+    }
+    return table.get(name, 0.0) * M
+
+
+def measured_fp64_tflops(torch):
+    """cuBLAS DGEMM rate measured here: the FP64 roofline denominator (no FP64 figure is
+    supplied with the machine's measured peaks)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------ oracle
+def oracle_sample(wl, n_ves=24, n_targets=2048, threads=1):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate one full step.
+
+    Per-vesicle part: an oracle step of the first n_ves vesicles (their mutual far field is
+    included, negligible). Far field: n_targets sampled targets against all sources. Full step
+    time = M * t_vesicle + P * t_target.
+    """
+    import contextlib
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:  # BLAS threads are already pinned through the environment
+        def threadpool_limits(limits):
+            return contextlib.nullcontext()
+    from oracle.farfield import far_field
+    from oracle.spectral import force
+    from oracle.step import Params, Suspension
+    with threadpool_limits(limits=threads):
+        p = Params(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True)
+        sub = Suspension(wl.xs[:n_ves], wl.ys[:n_ves], p)
+        t0 = time.perf_counter()
+        sub.step()
+        t_v = (time.perf_counter() - t0) / n_ves
+        fx, fy = [], []
+        for x, y in zip(wl.xs, wl.ys):
+            a, b = force(x, y, np.zeros(len(x)), wl.kappa)
+            fx.append(a)
+            fy.append(b)
+        P = int(sum(len(x) for x in wl.xs))
+        tg = np.linspace(0, P - 1, n_targets).astype(np.int64)
+        t0 = time.perf_counter()
+        far_field(wl.xs, wl.ys, fx, fy, wl.mu, near_mask=True, targets=tg)
+        t_t = (time.perf_counter() - t0) / n_targets
+    full = wl.M * t_v + P * t_t
+    return {"value": wl.M / full, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "FP64 numpy oracle: plain step of %d of the %d vesicles + far field at %d of %d targets "
+                      "against all sources; one full step extrapolated linearly (%.1f s)" % (n_ves, wl.M, n_targets,
+                                                                                           P, full)}
+
+
+# ------------------------------------------------------------------------------------------ main
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args)
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_ves=2, n_targets=64)
+    vals, times = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample(wl, n_ves=2, n_targets=96)
+        times.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.M / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, args, {"impl": "FP64 CPU oracle (numpy), sampled"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: oracle plain step of 2 vesicles + far field at 96 targets "
+                                       "against all sources, extrapolated to the full step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import torch
+    from paper_2606_25569_b300 import build as _build
+    _build.build()
+    from paper_2606_25569_b300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = workload(args)
+    stream = torch.cuda.current_stream()
+    s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream)
+    for _ in range(max(args.warmup, 3)):
+        s.step(1)
+    s.sync()
+    launches0 = s.counters()["launches"]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    s.step(args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    s.sync()
+    c = s.counters()
+    launches = c["launches"] - launches0
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * wl.M * args.steps / (ms * 1e-3)
+
+    # per-kernel CUDA-event breakdown over the same number of steps
+    s.profile(True)
+    s.step(args.steps)
+    prof = s.profile_read()
+    s.profile(False)
+    total_prof = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    peaks, peak_src = load_peaks()
+    fp64_peak = measured_fp64_tflops(torch)
+    avg_ms = dom_ms / dom_n
+    flops = kernel_flops(dom_name, args.N, wl.M)
+    if flops > 0:
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64: cuBLAS DGEMM 4096^3 measured in this run (of measured)",
+                "share_of_step": dom_ms / total_prof}
+    elif dom_name.startswith("k_farfield_f32"):
+        pairs = float(wl.offsets[-1]) ** 2 - float(np.sum(wl.counts.astype(np.float64) ** 2))
+        mhz = clocks.get("sm_mhz") or 1920.0
+        peak_mufu = MUFU_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
+        achieved = 2 * pairs / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_mufu, "unit": "Tmufu/s",
+                "frac": achieved / peak_mufu, "traffic": None,
+                "peak_source": "16 MUFU/clk/SM x 148 SMs x median SM clock (derived)",
+                "share_of_step": dom_ms / total_prof}
+    else:
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "share_of_step": dom_ms / total_prof}
+    breakdown = {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the C ABI with host buffers: upload state, step, read positions
+    e2e = None
+    if not args.no_e2e:
+        xy_h = torch.empty(2 * s.P, dtype=torch.float64).pin_memory()
+        sg_h = torch.empty(s.P, dtype=torch.float64).pin_memory()
+        xy_h.copy_(torch.from_numpy(s.positions()))
+        sg_h.copy_(torch.from_numpy(s.tension()))
+        L = binding.lib()
+        n_e2e = max(3, args.steps // 3)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(n_e2e):
+            assert L.vs_set_state(s._h, xy_h.data_ptr(), sg_h.data_ptr()) == 0
+            assert L.vs_step(s._h, 1) == 0
+            assert L.vs_get_positions(s._h, xy_h.data_ptr(), 2 * s.P) == 0
+            assert L.vs_get_tension(s._h, sg_h.data_ptr(), s.P) == 0
+        w1 = time.perf_counter()
+        e2e = {"value": world * wl.M * n_e2e / (w1 - w0), "unit": UNIT, "h2d_bytes_per_step": 24 * s.P,
+               "d2h_bytes_per_step": 24 * s.P, "steps": n_e2e,
+               "note": "per step: vs_set_state (positions + tension from pinned host), vs_step, "
+                       "vs_get_positions + vs_get_tension to pinned host; wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(wl)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU"}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "kernel_ms_per_launch": breakdown,
+                "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
+        print(json.dumps(line))
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

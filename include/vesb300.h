@@ -125,9 +125,19 @@ vs_status vs_get_reference(vs_suspension* s, double* a0l0, int64_t cap);
  * next vs_step / vs_set_state / vs_destroy. */
 vs_status vs_get_device_ptrs(const vs_suspension* s, const double** xy, const double** sigma);
 
-/* Counters: [0] steps taken, [1] corrections applied, [2] near (target, vesicle) pairs in the
- * last far-field evaluation (when near_field), [3] device error bits. Synchronises. */
-vs_status vs_get_counters(vs_suspension* s, int64_t* out4);
+/* Counters (out has 5 int64): [0] steps taken, [1] corrections applied, [2] near (target,
+ * vesicle) pairs in the last far-field evaluation (when near_field), [3] device error bits,
+ * [4] kernels launched by this handle so far. Synchronises. */
+vs_status vs_get_counters(vs_suspension* s, int64_t* out5);
+
+/* Per-kernel timing: while enabled, every kernel the handle launches is bracketed by CUDA
+ * events on its stream. vs_profile(s, 1) clears the totals and starts recording, 0 stops.
+ * vs_profile_read returns, for kernel name index idx (0, 1, ... until VS_ERR_INVALID_ARG), its
+ * name (NUL-terminated, truncated to name_cap), total milliseconds and launch count.
+ * Synchronises. */
+vs_status vs_profile(vs_suspension* s, int32_t enable);
+vs_status vs_profile_read(vs_suspension* s, int32_t idx, char* name, int32_t name_cap, double* total_ms,
+                          int64_t* launches);
 
 const char* vs_last_error(const vs_suspension* s);
 void vs_destroy(vs_suspension* s);

@@ -28,6 +28,9 @@ FUNCTIONS = {
     "vs_get_reference": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_get_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "vs_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -146,9 +149,25 @@ class Suspension:
         return r[:self.M], r[self.M:]
 
     def counters(self):
-        out = np.zeros(4, dtype=np.int64)
+        out = np.zeros(5, dtype=np.int64)
         self._check(lib().vs_get_counters(self._h, _ptr(out)))
-        return {"steps": int(out[0]), "corrections": int(out[1]), "near_pairs": int(out[2]), "err": int(out[3])}
+        return {"steps": int(out[0]), "corrections": int(out[1]), "near_pairs": int(out[2]), "err": int(out[3]),
+                "launches": int(out[4])}
+
+    def profile(self, enable):
+        self._check(lib().vs_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} recorded since profile(True)."""
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        i = 0
+        while lib().vs_profile_read(self._h, i, buf, 128, ctypes.byref(ms), ctypes.byref(n)) == 0:
+            out[buf.value.decode()] = (ms.value, n.value)
+            i += 1
+        return out
 
     def device_ptrs(self):
         a, b = ctypes.c_void_p(), ctypes.c_void_p()

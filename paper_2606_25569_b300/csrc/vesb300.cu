@@ -168,6 +168,24 @@ struct SourceBufs {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// Optional per-kernel CUDA-event timing on the handle's stream.
+struct Prof {
+  bool on = false;
+  std::vector<std::string> names;
+  std::vector<double> total_ms;
+  std::vector<int64_t> count;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> rec_id;  // name id per recorded pair (events 2k, 2k+1 of the pool)
+  int id(const char* n) {
+    for (size_t i = 0; i < names.size(); ++i)
+      if (names[i] == n) return (int)i;
+    names.push_back(n);
+    total_ms.push_back(0.0);
+    count.push_back(0);
+    return (int)names.size() - 1;
+  }
+};
+
 struct vs_suspension {
   Layout L;
   DevLayout D;
@@ -181,6 +199,8 @@ struct vs_suspension {
   unsigned* err = nullptr;
   int cur = 0;
   int64_t steps = 0;
+  int64_t launches = 0;
+  Prof prof;
   std::string msg;
 };
 
@@ -208,6 +228,48 @@ vs_status cuda_fail(std::string& msg, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((h)->msg, e_, where); \
   } while (0)
 
+// Record a CUDA event before a launch when profiling; returns the pool slot or -1.
+int prof_begin(vs_suspension* h, const char* name) {
+  h->launches += 1;
+  Prof& P = h->prof;
+  if (!P.on) return -1;
+  const size_t k = P.rec_id.size();
+  while (P.pool.size() < 2 * (k + 1)) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    P.pool.push_back(e);
+  }
+  P.rec_id.push_back(P.id(name));
+  cudaEventRecord(P.pool[2 * k], h->stream);
+  return (int)k;
+}
+
+void prof_end(vs_suspension* h, int k) {
+  if (k < 0) return;
+  cudaEventRecord(h->prof.pool[2 * k + 1], h->stream);
+}
+
+// Fold recorded event pairs into per-kernel totals (synchronises the stream).
+void prof_collect(vs_suspension* h) {
+  Prof& P = h->prof;
+  if (P.rec_id.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (size_t k = 0; k < P.rec_id.size(); ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.pool[2 * k], P.pool[2 * k + 1]);
+    P.total_ms[P.rec_id[k]] += ms;
+    P.count[P.rec_id[k]] += 1;
+  }
+  P.rec_id.clear();
+}
+
+#define VS_LAUNCH(h, name, ...)              \
+  do {                                      \
+    const int pk_ = prof_begin((h), (name)); \
+    __VA_ARGS__;                            \
+    prof_end((h), pk_);                     \
+  } while (0)
+
 inline dim3 gemm_grid(int m, int n, int M) { return dim3((n + GT - 1) / GT, (m + GT - 1) / GT, M); }
 
 FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
@@ -217,12 +279,12 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
   const VesIndex vi = h->D.vi();
-  k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                     h->p.mu, h->scratch, s, active);
+  VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                                     h->p.mu, h->scratch, s, active));
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
-  k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active);
-  k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active);
-  k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, h->piv, s, h->err, active);
+  VS_LAUNCH(h, "k_bgemm<OpT>", k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active));
+  VS_LAUNCH(h, "k_bgemm<OpL>", k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active));
+  VS_LAUNCH(h, "k_lu<L>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, h->piv, s, h->err, active));
   VS_CK(h, cudaGetLastError(), "operator build");
   return VS_OK;
 }
@@ -231,8 +293,8 @@ vs_status geometry(vs_suspension* h, const double* xy, bool with_force) {
   ForceOut fo{};
   if (with_force)
     fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
-  k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
-                                             flow_dev(h->flow), h->B.geom(), fo, nullptr);
+  VS_LAUNCH(h, "k_geometry", k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
+                                             flow_dev(h->flow), h->B.geom(), fo, nullptr));
   VS_CK(h, cudaGetLastError(), "geometry");
   return VS_OK;
 }
@@ -244,9 +306,9 @@ vs_status far_field(vs_suspension* h) {
                  h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
   const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
   if (h->p.flags & VS_FLAG_FARFIELD_FP64)
-    k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N);
+    VS_LAUNCH(h, "k_farfield_f64", k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N));
   else
-    k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+    VS_LAUNCH(h, "k_farfield_f32", k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2));
   VS_CK(h, cudaGetLastError(), "far field");
   return VS_OK;
 }
@@ -264,34 +326,34 @@ vs_status step_once(vs_suspension* h) {
   // (3) u += far field
   if ((st = far_field(h)) != VS_OK) return st;
   // (4) advection
-  k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
-                                     h->xy_star);
+  VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
+                                     h->xy_star));
   VS_CK(h, cudaGetLastError(), "advection");
   // (5) relaxation at X*
   if ((st = geometry(h, h->xy_star, false)) != VS_OK) return st;
   if ((st = build_operators(h, h->xy_star, nxt, nullptr)) != VS_OK) return st;
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
-  k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr);
-  k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr);
-  k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 0, h->p.kappa_b}, nullptr);
-  k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 1, h->p.kappa_b}, nullptr);
-  k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr);
-  k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, nxt, h->piv, nullptr);
-  k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, nxt, h->p.dt}, nullptr);
-  k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr);
-  k_relax_solve<<<M, 256, 0, h->stream>>>(vi, h->xy_star, h->scratch, h->piv, h->xy_next);
+  VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 0, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 1, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
+  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, nxt, h->piv, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, nxt, h->p.dt}, nullptr));
+  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr));
+  VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, h->xy_star, h->scratch, h->piv, h->xy_next));
   VS_CK(h, cudaGetLastError(), "relaxation");
   // (6) redistribution of X^{n+1}; u carried to the new parameters
-  k_redistribute<<<M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r);
+  VS_LAUNCH(h, "k_redistribute", k_redistribute<<<M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r));
   VS_CK(h, cudaGetLastError(), "redistribution");
   // (7) tension at the redistributed X^{n+1}; operators cached in slot nxt for the next step
   if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
   if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
-  k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u_r, h->B.pg(), h->D.tab, h->scratch, nxt, h->piv,
-                                      h->p.kappa_b, h->sigma);
+  VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u_r, h->B.pg(), h->D.tab, h->scratch, nxt, h->piv,
+                                      h->p.kappa_b, h->sigma));
   VS_CK(h, cudaGetLastError(), "tension");
   // (8) area/length correction; marks the cached operators stale where it fires
-  k_correct<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab, h->dirty, h->fired, h->err);
+  VS_LAUNCH(h, "k_correct", k_correct<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab, h->dirty, h->fired, h->err));
   VS_CK(h, cudaGetLastError(), "correction");
   h->cur = nxt;
   h->steps += 1;
@@ -379,14 +441,14 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   }
   const VesIndex vi = h->D.vi();
   // redistribute X^0, record A_0 and L_0, initial tension from self + background terms
-  k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r);
+  VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r));
   VS_A(cudaGetLastError());
   if (geometry(h, h->xy, true) != VS_OK) return fail(VS_ERR_CUDA);
   VS_A(cudaMemcpyAsync(h->A0, h->B.area, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   VS_A(cudaMemcpyAsync(h->L0, h->B.length, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
-  k_tension<<<L.M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u, h->B.pg(), h->D.tab, h->scratch, 0, h->piv,
-                                        h->p.kappa_b, h->sigma);
+  VS_LAUNCH(h, "k_tension", k_tension<<<L.M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u, h->B.pg(), h->D.tab, h->scratch, 0, h->piv,
+                                        h->p.kappa_b, h->sigma));
   VS_A(cudaGetLastError());
   h->cur = 0;
   VS_A(cudaStreamSynchronize(h->stream));
@@ -458,6 +520,7 @@ vs_status vs_get_device_ptrs(const vs_suspension* h, const double** xy, const do
 
 vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
   if (!h || !out4) return VS_ERR_INVALID_ARG;
+  prof_collect(h);
   VS_CK(h, cudaStreamSynchronize(h->stream), "counters");
   int fired = 0;
   unsigned e = 0;
@@ -471,6 +534,27 @@ vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
   out4[1] = fired;
   out4[2] = pairs;
   out4[3] = e;
+  out4[4] = h->launches;
+  return VS_OK;
+}
+
+vs_status vs_profile(vs_suspension* h, int32_t enable) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  prof_collect(h);
+  h->prof.on = enable != 0;
+  std::fill(h->prof.total_ms.begin(), h->prof.total_ms.end(), 0.0);
+  std::fill(h->prof.count.begin(), h->prof.count.end(), 0);
+  return VS_OK;
+}
+
+vs_status vs_profile_read(vs_suspension* h, int32_t idx, char* name, int32_t name_cap, double* total_ms,
+                          int64_t* launches) {
+  if (!h || !name || name_cap < 1 || !total_ms || !launches) return VS_ERR_INVALID_ARG;
+  prof_collect(h);
+  if (idx < 0 || idx >= (int32_t)h->prof.names.size()) return VS_ERR_INVALID_ARG;
+  snprintf(name, (size_t)name_cap, "%s", h->prof.names[idx].c_str());
+  *total_ms = h->prof.total_ms[idx];
+  *launches = h->prof.count[idx];
   return VS_OK;
 }
 
@@ -479,6 +563,7 @@ const char* vs_last_error(const vs_suspension* h) { return h ? h->msg.c_str() : 
 void vs_destroy(vs_suspension* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   free_suspension(h);
   delete h;
 }

@@ -12,6 +12,7 @@ a_k, b_k ~ N(0, 1), then a rotation. The points are not equally spaced in arclen
 library (and the oracle) redistribute them when a suspension is created.
 """
 from dataclasses import dataclass, field
+from functools import lru_cache
 
 import numpy as np
 
@@ -21,6 +22,7 @@ def _ellipse_perimeter(a, b, samples=8192):
     return float(np.sum(np.hypot(np.diff(a * np.cos(t)), np.diff(b * np.sin(t)))))
 
 
+@lru_cache(maxsize=4096)
 def ellipse_axes(nu, R):
     """Semi-axes (a, b), a >= b, of the ellipse with area pi R^2 and reduced area nu."""
     if not (0.0 < nu <= 1.0):
