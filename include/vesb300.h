@@ -173,6 +173,32 @@ void vs_farfield_plan_destroy(vs_farfield_plan* plan);
 vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, double mu,
                            double* S_out, void* cuda_stream);
 
+/*
+ * Far field without any device allocation (no counterpart in the paper; a deployment variant of
+ * vs_farfield_eval). Some callers cannot call cudaMalloc: code running inside another
+ * framework's memory pool or allocator, a host process that has handed all device memory to
+ * someone else, or a real-time loop that must not allocate. This entry point computes the same
+ * far-field sum as vs_farfield_eval with near_mask = 0 (every pair of different vesicles), but
+ * keeps all of its scratch in one static device array of fixed size that is part of the library
+ * image, so it calls no cudaMalloc / cudaFree and no allocating library routine.
+ *  offsets      host, M+1 int64 (as in vs_create); at most VS_STATIC_MAX_VESICLES vesicles and
+ *               VS_STATIC_MAX_POINTS points in total; N_v even in [8, 128].
+ *  precision    0: compensated FP32, 1: FP64.
+ *  xy, f        DEVICE, CSR blocks (2P doubles each); u DEVICE output (2P doubles, overwritten).
+ *  cuda_stream  stream for all work (NULL = legacy default stream). Asynchronous.
+ * Sizes beyond the limits, odd or out-of-range N, null pointers: VS_ERR_INVALID_ARG.
+ * The scratch array (about 13 MB) is reserved on every GPU that loads the library until the
+ * process exits. The first call on a device does a one-time set-up on that device (looks up the
+ * array's device address and fills its tables with one kernel); make that first call outside
+ * any stream capture. All calls share the one array and it keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, or another host thread) race on it and must
+ * be serialised by the caller.
+ */
+#define VS_STATIC_MAX_VESICLES 4096
+#define VS_STATIC_MAX_POINTS 131072
+vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, double mu, int32_t precision,
+                                  const double* xy, const double* f, double* u, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

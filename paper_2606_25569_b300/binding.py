@@ -39,6 +39,8 @@ FUNCTIONS = {
     "vs_farfield_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vs_farfield_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_farfield_plan_destroy": (None, [ctypes.c_void_p]),
+    "vs_farfield_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -229,3 +231,12 @@ def self_matrices(xy_dev, offsets, mu, out_dev, stream=None):
     st = lib().vs_self_matrices(_ptr(xy_dev), _ptr(off), len(off) - 1, float(mu), _ptr(out_dev), _stream(stream))
     if st != 0:
         raise VsError(st, "vs_self_matrices failed")
+
+
+def farfield_eval_static(offsets, mu, precision, xy_dev, f_dev, u_dev, stream=None):
+    """vs_farfield_eval_static: far field with the library's static scratch (no allocation)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    st = lib().vs_farfield_eval_static(_ptr(off), len(off) - 1, float(mu), int(precision), _ptr(xy_dev),
+                                       _ptr(f_dev), _ptr(u_dev), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_farfield_eval_static failed")

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -678,3 +679,138 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Far field with file-scope scratch: for callers that must not allocate device memory.
+//
+// Scratch lives in one static __device__ array (every GPU that loads this library holds it until
+// the process exits). Host code cannot use the array's name as a device address, so the first
+// call on each device looks the address up with cudaGetSymbolAddress (with that device current)
+// and fills the differentiation tables there; later calls reuse the address.
+namespace {
+
+constexpr int SF_MAX_M = VS_STATIC_MAX_VESICLES;
+constexpr int64_t SF_MAX_P = VS_STATIC_MAX_POINTS;
+constexpr int SF_NSLOTS = (NMAX - 8) / 2 + 1;            // even N in [8, NMAX]
+constexpr int64_t SF_TAB = (int64_t)TAB_STRIDE * (NMAX + 2 + 6) * (NMAX + 2 - 8) / 4;  // all N slots
+
+// byte offsets inside the scratch array (each region 256-byte aligned)
+constexpr int64_t sf_align(int64_t b) { return (b + 255) / 256 * 256; }
+constexpr int64_t SF_N = 0;
+constexpr int64_t SF_OFF = SF_N + sf_align(4 * SF_MAX_M);
+constexpr int64_t SF_TOFF = SF_OFF + sf_align(8 * (SF_MAX_M + 1));
+constexpr int64_t SF_OWNER = SF_TOFF + sf_align(8 * SF_MAX_M);
+constexpr int64_t SF_CHUNK = SF_OWNER + sf_align(4 * SF_MAX_P);
+constexpr int64_t SF_ERR = SF_CHUNK + sf_align(4 * (SF_MAX_M + 1));
+constexpr int64_t SF_TABLE = SF_ERR + 256;
+constexpr int64_t SF_GEOM = SF_TABLE + sf_align(8 * SF_TAB);        // sa, tx, ty, bx, by
+constexpr int64_t SF_AREA = SF_GEOM + sf_align(5 * 8 * SF_MAX_P);   // area, length
+constexpr int64_t SF_F = SF_AREA + sf_align(2 * 8 * SF_MAX_M);
+constexpr int64_t SF_G64 = SF_F + sf_align(16 * SF_MAX_P);
+constexpr int64_t SF_SRC = SF_G64 + sf_align(16 * SF_MAX_P);
+constexpr int64_t SF_CENTRE = SF_SRC + sf_align(16 * SF_MAX_P);
+constexpr int64_t SF_CENTRE32 = SF_CENTRE + sf_align(16 * SF_MAX_M);
+constexpr int64_t SF_H2 = SF_CENTRE32 + sf_align(16 * SF_MAX_M);
+constexpr int64_t SF_BYTES = SF_H2 + sf_align(4 * SF_MAX_M);
+
+__device__ __align__(256) static unsigned char g_ff_scratch[SF_BYTES];
+
+__host__ __device__ inline int64_t sf_tab_slot(int N) { return (int64_t)TAB_STRIDE * (N + 6) * (N - 8) / 4; }
+
+// Differentiation circulant d(m) = (-1)^m cot(pi m / N) / 2 of every even N (the only table
+// entries the source-preparation kernel reads).
+__global__ void k_static_tables(unsigned char* base) {
+  double* tab = (double*)(base + SF_TABLE);
+  for (int s = blockIdx.x; s < SF_NSLOTS; s += gridDim.x) {
+    const int N = 8 + 2 * s;
+    double* t = tab + sf_tab_slot(N);
+    for (int m = threadIdx.x; m < N; m += blockDim.x)
+      t[m] = (m == 0) ? 0.0 : 0.5 * ((m & 1) ? -1.0 : 1.0) / tan(VS_PI * m / N);
+  }
+}
+
+// Per-call layout from the offsets already copied into the scratch: N, table slots, owners,
+// and the same greedy source chunks the allocating path builds on the host.
+__global__ void k_static_layout(unsigned char* base, int M) {
+  const int64_t* off = (const int64_t*)(base + SF_OFF);
+  int32_t* N = (int32_t*)(base + SF_N);
+  int64_t* toff = (int64_t*)(base + SF_TOFF);
+  int32_t* owner = (int32_t*)(base + SF_OWNER);
+  for (int v = threadIdx.x; v < M; v += blockDim.x) {
+    const int n = (int)(off[v + 1] - off[v]);
+    N[v] = n;
+    toff[v] = sf_tab_slot(n);
+    for (int64_t p = off[v]; p < off[v + 1]; ++p) owner[p] = v;
+  }
+  if (threadIdx.x == 0) {
+    int32_t* chunk = (int32_t*)(base + SF_CHUNK);
+    int c = 0;
+    int64_t acc = 0;
+    chunk[c++] = 0;
+    for (int v = 0; v < M; ++v) {
+      const int n = (int)(off[v + 1] - off[v]);
+      if (acc + n > FF_CHUNK) { chunk[c++] = v; acc = 0; }
+      acc += n;
+    }
+    chunk[c] = M;
+    *(unsigned*)(base + SF_ERR) = 0u;
+  }
+}
+
+std::mutex g_sf_mutex;
+unsigned char* g_sf_ptr[256] = {};
+
+}  // namespace
+
+extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, double mu, int32_t precision,
+                                             const double* xy, const double* f, double* u, void* cuda_stream) {
+  if (!offsets || !xy || !f || !u || !(mu > 0) || (precision != 0 && precision != 1)) return VS_ERR_INVALID_ARG;
+  if (M < 1 || M > SF_MAX_M || offsets[0] != 0) return VS_ERR_INVALID_ARG;
+  int nchunk = 1;
+  int64_t acc = 0;
+  for (int v = 0; v < M; ++v) {
+    const int64_t n = offsets[v + 1] - offsets[v];
+    if (n < 8 || n > NMAX || (n & 1)) return VS_ERR_INVALID_ARG;
+    if (acc + n > FF_CHUNK) { ++nchunk; acc = 0; }
+    acc += n;
+  }
+  const int64_t P = offsets[M];
+  if (P > SF_MAX_P) return VS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return VS_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_sf_mutex);
+    if (!g_sf_ptr[dev]) {  // one-time set-up on this device
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_ff_scratch) != cudaSuccess || p == nullptr) return VS_ERR_CUDA;
+      k_static_tables<<<SF_NSLOTS, 128, 0, st>>>((unsigned char*)p);
+      if (cudaGetLastError() != cudaSuccess) return VS_ERR_CUDA;
+      g_sf_ptr[dev] = (unsigned char*)p;
+    }
+    base = g_sf_ptr[dev];
+  }
+  if (cudaMemcpyAsync(base + SF_OFF, offsets, (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return VS_ERR_CUDA;
+  k_static_layout<<<1, 256, 0, st>>>(base, M);
+  const int64_t* off = (const int64_t*)(base + SF_OFF);
+  const VesIndex vi{(const int32_t*)(base + SF_N), off, off, (const int64_t*)(base + SF_TOFF)};
+  double* geo = (double*)(base + SF_GEOM);
+  double* al = (double*)(base + SF_AREA);
+  const GeomOut g{geo, geo + SF_MAX_P, geo + 2 * SF_MAX_P, geo + 3 * SF_MAX_P, geo + 4 * SF_MAX_P, al, al + SF_MAX_M};
+  const ForceOut fo{(double*)(base + SF_F), u, (float4*)(base + SF_SRC), (double2*)(base + SF_CENTRE),
+                    (float4*)(base + SF_CENTRE32), (float*)(base + SF_H2), (double*)(base + SF_G64)};
+  const FlowDev none{0, 0.0, 0.0};
+  k_geometry<<<M, NMAX, 0, st>>>(vi, xy, nullptr, (const double*)(base + SF_TABLE), 1.0, mu, none, g, fo, f);
+  if (M >= 2) {
+    FarFieldArgs a{P, M, (const int32_t*)(base + SF_OWNER), off, (const int32_t*)(base + SF_CHUNK), nchunk, 0, u,
+                   nullptr, nullptr, (unsigned*)(base + SF_ERR)};
+    const int grid = (int)((P + FF_THREADS - 1) / FF_THREADS);
+    if (precision == 1)
+      k_farfield_f64<<<grid, FF_THREADS, 0, st>>>(a, xy, fo.g64, g.length, vi.N);
+    else
+      k_farfield_f32<<<grid, FF_THREADS, 0, st>>>(a, fo.src, fo.centre32, fo.h2);
+  }
+  return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ERR_CUDA;
+}
