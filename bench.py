@@ -56,7 +56,7 @@ def workload(args):
 def config_of(wl, args, extra=None):
     c = {"workload": "dense Poiseuille suspension, %d vesicles x %d points, 30%% area fraction, "
                      "channel width 1, reduced area 0.65, Ca 2, Cn 0.025" % (wl.M, args.N),
-         "mode": "plain BIE step (hybrid learned step not built)", "near_field": "mask only",
+         "mode": "plain BIE step (hybrid learned step not built)", "near_field": "mask + five-layer RBF correction (exact layer velocities)",
          "dt": wl.dt, "farfield": "fp32 compensated", "l2": "working set > L2 (no flush needed)"}
     if extra:
         c.update(extra)

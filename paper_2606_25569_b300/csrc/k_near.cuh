@@ -1,0 +1,273 @@
+// Near-field correction: five layers + Gaussian RBF (Sec. 3.3, Algorithm 4, App. A).
+//
+// For every source vesicle v with at least one near target (recorded by the far-field kernel):
+//  k_near_layers  the 5N layer points X + d h n, d in {-1, -1/2, 0, 1/2, 1}, and the exact
+//                 single layer S[X, f] there: on the curve S f with the cached self matrix, off the
+//                 curve the trapezoid rule on the curve upsampled by rho = ceil(sqrt(N)) (FP64);
+//  k_near_rbf     (Phi + lam I) w = u_layers, Phi_ab = exp(-|x_a - x_b|^2 / (c h)^2), c = 2,
+//                 lam = 1e-3, by an FP32 Cholesky (the paper's precision) in the vesicle's scratch;
+//  k_near_apply   u(x_t) += sum_b phi(|x_t - x_b|) w_b for each near (target, vesicle) pair.
+#pragma once
+#include "common.cuh"
+#include "k_dense.cuh"
+#include "k_vesicle.cuh"
+
+namespace vs {
+
+constexpr double NEAR_RBF_C = 2.0;
+constexpr double NEAR_RBF_NUGGET = 1e-3;
+constexpr int NEAR_LAYERS = 5;
+__device__ __constant__ double c_layer_d[NEAR_LAYERS] = {-1.0, -0.5, 0.0, 0.5, 1.0};
+
+__device__ __forceinline__ int near_rho(int N) { return (int)ceil(sqrt((double)N)); }
+
+// Mark source vesicles that have near targets.
+__global__ void k_near_mark(int64_t P, const int* __restrict__ near_cnt, const int* __restrict__ near_v,
+                            int* __restrict__ has_near) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int c = near_cnt[t];
+  for (int k = 0; k < c; ++k) has_near[near_v[t * MAX_NEAR + k]] = 1;
+}
+
+struct NearBufs {
+  double* layer;   // per vesicle at 30 off[v]: LX, LY, UX, UY, WX, WY (5N each)
+  float* phi;      // per vesicle at moff[v]: (5N)^2 floats
+};
+
+// Layer points and exact layer velocities. Dynamic shared memory: 12 * rho * N doubles.
+__global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __restrict__ has_near,
+                                                     const double* __restrict__ xy, const double* __restrict__ f,
+                                                     PointGeom g, const double* __restrict__ length,
+                                                     const double* __restrict__ tab,
+                                                     const double* __restrict__ scratch, int s, double mu,
+                                                     NearBufs nb) {
+  extern __shared__ double sm[];
+  const int v = blockIdx.x;
+  if (!has_near[v]) return;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int rho = near_rho(N), Nu = rho * N;
+  const int tid = threadIdx.x;
+  double* cs = sm;            // cos(2 pi q / Nu)
+  double* sn = cs + Nu;       // sin(2 pi q / Nu)
+  double* xu = sn + Nu;
+  double* yu = xu + Nu;
+  double* gx = yu + Nu;
+  double* gy = gx + Nu;
+  __shared__ double cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
+  __shared__ double fl[2 * NMAX];
+  const double* T = tab + vi.toff[v];
+  for (int q = tid; q < Nu; q += blockDim.x) sincospi(2.0 * q / Nu, &sn[q], &cs[q]);
+  for (int r = tid; r < 2 * N; r += blockDim.x) fl[r] = f[2 * o + r];
+  // Fourier coefficients of x, y, f_x, f_y (k = 0..N/2)
+  const int nk = N / 2 + 1;
+  for (int e = tid; e < 4 * nk; e += blockDim.x) {
+    const int comp = e / nk, k = e - comp * nk;
+    const double* src = (comp < 2) ? (xy + 2 * o + comp * N) : (f + 2 * o + (comp - 2) * N);
+    double re = 0.0, im = 0.0;
+    int m = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fma(src[j], T[15 * N + m], re);
+      im = fma(-src[j], T[16 * N + m], im);
+      m += k;
+      if (m >= N) m -= N;
+    }
+    cre[comp][k] = re / N;
+    cim[comp][k] = im / N;
+  }
+  __syncthreads();
+  // upsampled curve, its speed, and the scaled density g = f |X_alpha| (2 pi / Nu) / (4 pi mu)
+  const double cw = 2.0 * VS_PI / Nu / (4.0 * VS_PI * mu);
+  for (int q = tid; q < Nu; q += blockDim.x) {
+    double val[4], dx = 0.0, dy = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) val[c] = cre[c][0];
+    int idx = 0;
+    for (int k = 1; k < N / 2; ++k) {
+      idx += q;
+      if (idx >= Nu) idx %= Nu;
+      const double ck = cs[idx], sk = sn[idx];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) val[c] += 2.0 * (cre[c][k] * ck - cim[c][k] * sk);
+      dx -= 2.0 * k * (cre[0][k] * sk + cim[0][k] * ck);
+      dy -= 2.0 * k * (cre[1][k] * sk + cim[1][k] * ck);
+    }
+    const int iN = (int)(((int64_t)q * (N / 2)) % Nu);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) val[c] += cre[c][N / 2] * cs[iN];
+    dx -= cre[0][N / 2] * (N / 2) * sn[iN];
+    dy -= cre[1][N / 2] * (N / 2) * sn[iN];
+    const double w = sqrt(dx * dx + dy * dy) * cw;
+    xu[q] = val[0];
+    yu[q] = val[1];
+    gx[q] = val[2] * w;
+    gy[q] = val[3] * w;
+  }
+  __syncthreads();
+  const double h = length[v] / N;
+  double* L = nb.layer + 30 * o;
+  double* LX = L;
+  double* LY = L + 5 * N;
+  double* UX = L + 10 * N;
+  double* UY = L + 15 * N;
+  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * (int64_t)N * N;
+  for (int e = tid; e < 5 * N; e += blockDim.x) {
+    const int lay = e / N, j = e - lay * N;
+    const double d = c_layer_d[lay] * h;
+    const double nx = g.ty[o + j], ny = -g.tx[o + j];
+    const double px = xy[2 * o + j] + d * nx, py = xy[2 * o + N + j] + d * ny;
+    LX[e] = px;
+    LY[e] = py;
+    double ax = 0.0, ay = 0.0;
+    if (lay == 2) {  // on the curve: S f
+      for (int k = 0; k < 2 * N; ++k) {
+        ax = fma(S[(int64_t)j * 2 * N + k], fl[k], ax);
+        ay = fma(S[(int64_t)(N + j) * 2 * N + k], fl[k], ay);
+      }
+    } else {
+      for (int m = 0; m < Nu; ++m) {
+        const double rx = px - xu[m], ry = py - yu[m];
+        const double r2 = rx * rx + ry * ry;
+        const double lg = -0.5 * log(r2);
+        const double q = (rx * gx[m] + ry * gy[m]) / r2;
+        ax += lg * gx[m] + q * rx;
+        ay += lg * gy[m] + q * ry;
+      }
+    }
+    UX[e] = ax;
+    UY[e] = ay;
+  }
+}
+
+// FP32 Cholesky of (Phi + lam I) and the two RBF weight vectors. One CTA per near vesicle.
+__global__ void __launch_bounds__(256) k_near_rbf(VesIndex vi, const int* __restrict__ has_near,
+                                                  const double* __restrict__ length, NearBufs nb,
+                                                  unsigned* err) {
+  __shared__ float colk[5 * NMAX];
+  __shared__ float y1[5 * NMAX], y2[5 * NMAX];
+  __shared__ int bad;
+  const int v = blockIdx.x;
+  if (!has_near[v]) return;
+  const int N = vi.N[v];
+  const int n = 5 * N;
+  const int64_t o = vi.off[v];
+  const double h = length[v] / N;
+  const double ie2 = 1.0 / (NEAR_RBF_C * h * NEAR_RBF_C * h);
+  double* L = nb.layer + 30 * o;
+  const double* LX = L;
+  const double* LY = L + 5 * N;
+  float* A = nb.phi + vi.moff[v];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  for (int i = wid; i < n; i += nw)
+    for (int j = lane; j <= i; j += 32) {
+      const double dx = LX[i] - LX[j], dy = LY[i] - LY[j];
+      double p = exp(-(dx * dx + dy * dy) * ie2);
+      if (i == j) p += NEAR_RBF_NUGGET;
+      A[(int64_t)i * n + j] = (float)p;
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float dkk = A[(int64_t)k * n + k];
+    const float d = dkk > 0.f ? sqrtf(dkk) : 1.f;
+    if (tid == 0 && !(dkk > 0.f)) bad = 1;
+    const float inv = 1.f / d;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+      const float l = A[(int64_t)i * n + k] * inv;
+      A[(int64_t)i * n + k] = l;
+      colk[i] = l;
+    }
+    __syncthreads();
+    if (tid == 0) A[(int64_t)k * n + k] = d;
+    for (int i = k + 1 + wid; i < n; i += nw) {
+      const float li = colk[i];
+      for (int j = k + 1 + lane; j <= i; j += 32) A[(int64_t)i * n + j] = fmaf(-li, colk[j], A[(int64_t)i * n + j]);
+    }
+    __syncthreads();
+  }
+  if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
+  // forward L y = u, backward L^T w = y (warp 0, row dot products)
+  const double* UX = L + 10 * N;
+  const double* UY = L + 15 * N;
+  for (int i = tid; i < n; i += blockDim.x) { y1[i] = (float)UX[i]; y2[i] = (float)UY[i]; }
+  __syncthreads();
+  if (wid == 0) {
+    for (int i = 0; i < n; ++i) {
+      float s1 = 0.f, s2 = 0.f;
+      for (int k = lane; k < i; k += 32) {
+        const float a = A[(int64_t)i * n + k];
+        s1 = fmaf(a, y1[k], s1);
+        s2 = fmaf(a, y2[k], s2);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      }
+      if (lane == 0) {
+        const float di = A[(int64_t)i * n + i];
+        y1[i] = (y1[i] - s1) / di;
+        y2[i] = (y2[i] - s2) / di;
+      }
+      __syncwarp();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      float s1 = 0.f, s2 = 0.f;
+      for (int k = i + 1 + lane; k < n; k += 32) {
+        const float a = A[(int64_t)k * n + i];
+        s1 = fmaf(a, y1[k], s1);
+        s2 = fmaf(a, y2[k], s2);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      }
+      if (lane == 0) {
+        const float di = A[(int64_t)i * n + i];
+        y1[i] = (y1[i] - s1) / di;
+        y2[i] = (y2[i] - s2) / di;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double* WX = L + 20 * N;
+  double* WY = L + 25 * N;
+  for (int i = tid; i < n; i += blockDim.x) { WX[i] = y1[i]; WY[i] = y2[i]; }
+}
+
+// u(x_t) += RBF interpolant of each near vesicle's layer velocities.
+__global__ void __launch_bounds__(128) k_near_apply(int64_t P, const int32_t* __restrict__ owner,
+                                                    const int64_t* __restrict__ voff, const int32_t* __restrict__ Nv,
+                                                    const int* __restrict__ near_cnt, const int* __restrict__ near_v,
+                                                    const double* __restrict__ xy, const double* __restrict__ length,
+                                                    NearBufs nb, double* __restrict__ u) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int c = near_cnt[t];
+  if (c == 0) return;
+  const int tv = owner[t];
+  const int64_t to = voff[tv];
+  const int tN = Nv[tv];
+  const double px = xy[2 * to + (t - to)], py = xy[2 * to + tN + (t - to)];
+  double ax = 0.0, ay = 0.0;
+  for (int k = 0; k < c; ++k) {
+    const int v = near_v[t * MAX_NEAR + k];
+    const int N = Nv[v];
+    const double h = length[v] / N;
+    const double ie2 = 1.0 / (NEAR_RBF_C * h * NEAR_RBF_C * h);
+    const double* L = nb.layer + 30 * voff[v];
+    for (int b = 0; b < 5 * N; ++b) {
+      const double dx = px - L[b], dy = py - L[5 * N + b];
+      const double p = exp(-(dx * dx + dy * dy) * ie2);
+      ax = fma(p, L[20 * N + b], ax);
+      ay = fma(p, L[25 * N + b], ay);
+    }
+  }
+  u[2 * to + (t - to)] += ax;
+  u[2 * to + tN + (t - to)] += ay;
+}
+
+}  // namespace vs

@@ -16,6 +16,7 @@
 #include "k_dense.cuh"
 #include "k_farfield.cuh"
 #include "k_geometry.cuh"
+#include "k_near.cuh"
 #include "k_selfmat.cuh"
 #include "k_vesicle.cuh"
 #include "tables.cuh"
@@ -198,6 +199,8 @@ struct vs_suspension {
   double *u = nullptr, *u_r = nullptr, *A0 = nullptr, *L0 = nullptr, *scratch = nullptr;
   int *piv = nullptr, *dirty = nullptr, *fired = nullptr;
   unsigned* err = nullptr;
+  int* has_near = nullptr;
+  NearBufs nb{nullptr, nullptr};
   int cur = 0;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -314,6 +317,26 @@ vs_status far_field(vs_suspension* h) {
   return VS_OK;
 }
 
+// u += near-field correction of every (target, vesicle) pair the far field masked (Sec. 3.3).
+vs_status near_field(vs_suspension* h, int s) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  VS_CK(h, cudaMemsetAsync(h->has_near, 0, L.M * sizeof(int), h->stream), "near field");
+  const int tgrid = (int)((L.P + 127) / 128);
+  VS_LAUNCH(h, "k_near_mark", k_near_mark<<<tgrid, 128, 0, h->stream>>>(L.P, h->B.near_cnt, h->B.near_v, h->has_near));
+  const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
+  const size_t smem = 6 * (size_t)Nu * sizeof(double);
+  VS_LAUNCH(h, "k_near_layers", k_near_layers<<<L.M, 256, smem, h->stream>>>(vi, h->has_near, h->xy, h->B.f, h->B.pg(),
+                                                                            h->B.length, h->D.tab, h->scratch, s,
+                                                                            h->p.mu, h->nb));
+  VS_LAUNCH(h, "k_near_rbf", k_near_rbf<<<L.M, 256, 0, h->stream>>>(vi, h->has_near, h->B.length, h->nb, h->err));
+  VS_LAUNCH(h, "k_near_apply", k_near_apply<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->D.off, h->D.N,
+                                                                        h->B.near_cnt, h->B.near_v, h->xy,
+                                                                        h->B.length, h->nb, h->u));
+  VS_CK(h, cudaGetLastError(), "near field");
+  return VS_OK;
+}
+
 vs_status step_once(vs_suspension* h) {
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
@@ -324,8 +347,9 @@ vs_status step_once(vs_suspension* h) {
   if ((st = geometry(h, h->xy, true)) != VS_OK) return st;
   // (2) operators at X^n where the cache is stale (first step, or after a correction)
   if ((st = build_operators(h, h->xy, cur, h->dirty)) != VS_OK) return st;
-  // (3) u += far field
+  // (3) u += far field (near pairs masked) + near-field correction
   if ((st = far_field(h)) != VS_OK) return st;
+  if (h->p.near_field && L.M > 1 && (st = near_field(h, cur)) != VS_OK) return st;
   // (4) advection
   VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
                                      h->xy_star));
@@ -390,7 +414,8 @@ void free_suspension(vs_suspension* h) {
   h->B.release();
   cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
-  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err);
+  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near);
+  cudaFree(h->nb.layer); cudaFree(h->nb.phi);
 }
 
 thread_local std::string g_create_msg;
@@ -429,6 +454,14 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->A0, L.M)); VS_A(dalloc(&h->L0, L.M));
   VS_A(dalloc(&h->scratch, L.moff[L.M])); VS_A(dalloc(&h->piv, 4 * L.P));
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
+  VS_A(dalloc(&h->has_near, L.M));
+  if (h->p.near_field) {
+    VS_A(dalloc(&h->nb.layer, 30 * L.P));
+    VS_A(dalloc(&h->nb.phi, L.moff[L.M]));
+    const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
+    VS_A(cudaFuncSetAttribute(k_near_layers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(6 * (size_t)Nu * sizeof(double))));
+  }
   VS_A(cudaMemsetAsync(h->fired, 0, sizeof(int), h->stream));
   VS_A(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
   VS_A(cudaMemsetAsync(h->sigma, 0, L.P * sizeof(double), h->stream));

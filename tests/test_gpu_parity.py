@@ -172,3 +172,34 @@ def test_fp32_farfield_step_close_to_oracle():
     g.step()
     # FP32 velocities (relative 1e-5) enter X only through dt * u
     _compare(o, g, tol_x=1e-7, tol_s=1e-3)
+
+
+def _close_pair(N=32, gap_h=0.5, seed=3):
+    from oracle.spectral import Geometry
+    rng = np.random.default_rng(seed)
+    x0, y0 = vesicle_outline(N, 0.7, 1.0, 1e-2, rng, 0.0)
+    x1, y1 = vesicle_outline(N, 0.8, 0.8, 1e-2, rng, 0.4)
+    g0 = Geometry(x0, y0)
+    shift = x0.max() - x1.min() + gap_h * g0.h
+    x2, y2 = vesicle_outline(N, 0.75, 0.9, 1e-2, rng, 1.1)
+    return [x0, x1 + shift, x2], [y0, y1 + 0.1, y2 + 2.6]
+
+
+def test_near_field_step_matches_oracle():
+    # FP64 far field, near-field correction on: FP32 RBF Cholesky on the GPU vs FP64 in the oracle
+    xs, ys = _close_pair()
+    o = OracleSuspension(xs, ys, Params(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0, 0, 0),
+                                        near_field=True))
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1,
+                           flow_p=(0.5, 0, 0, 0), near_field=True, farfield_fp64=True)
+    for k in range(2):
+        o.step()
+        g.step()
+        assert len(o.near_pairs) > 0
+        assert g.counters()["near_pairs"] == len(o.near_pairs)
+        counts = [len(x) for x in xs]
+        vx, vy = split(g.velocity(), counts)
+        ref = np.concatenate(o.velocity)
+        got = np.concatenate([np.concatenate([a, b]) for a, b in zip(vx, vy)])
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+        _compare(o, g, tol_x=1e-8, tol_s=1e-4)
