@@ -1,0 +1,49 @@
+"""Pins for oracle.mlp (Sec. 3.4.2): finite-difference gradients, AdamW closed form, bf16 rounding."""
+import numpy as np
+
+from oracle.mlp import AdamW, bf16_round, init_params, loss_and_gradient, forward
+
+
+def test_gradient_matches_central_differences():
+    rng = np.random.default_rng(0)
+    dims = [8, 12, 10, 8]
+    p = init_params(dims, rng) + 0.01 * rng.standard_normal(sum(a * b + b for a, b in zip(dims[:-1], dims[1:])))
+    X = rng.standard_normal((5, 8))
+    Y = rng.standard_normal((5, 8))
+    loss, g = loss_and_gradient(p, dims, X, Y, beta=0.7, ncomp=2)
+    h = 1e-6
+    idx = rng.choice(len(p), 40, replace=False)
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (loss_and_gradient(p + e, dims, X, Y, 0.7, 2)[0] - loss_and_gradient(p - e, dims, X, Y, 0.7, 2)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def test_perfect_prediction_has_zero_loss():
+    rng = np.random.default_rng(1)
+    dims = [6, 9, 4]
+    p = init_params(dims, rng)
+    X = rng.standard_normal((3, 6))
+    Y, _ = forward(p, dims, X)
+    loss, g = loss_and_gradient(p, dims, X, Y, beta=1.0, ncomp=2)
+    assert loss == 0.0 and np.all(g == 0.0)
+
+
+def test_adamw_first_step_closed_form():
+    # first step: mhat = g, vhat = g^2, so w1 = w0 (1 - lr wd) - lr g / (|g| + eps)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal(50)
+    g = rng.standard_normal(50)
+    opt = AdamW(50, lr=1e-3, weight_decay=0.01)
+    w1 = opt.step(w, g)
+    assert np.allclose(w1, w * (1 - 1e-5) - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_bf16_rounding_ties_to_even():
+    # 1 + 2^-8 lies halfway between bf16 neighbours 1 and 1 + 2^-7: rounds to 1 (even)
+    assert bf16_round(np.array([1.0 + 2 ** -8]))[0] == 1.0
+    assert bf16_round(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
+    assert bf16_round(np.array([-2.5]))[0] == -2.5
+    x = np.array([3.14159265])
+    assert abs(bf16_round(x)[0] - x[0]) <= 2 ** -8 * 4
