@@ -174,6 +174,42 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
                            double* S_out, void* cuda_stream);
 
 /*
+ * Learned part (Sec. 3.2-3.4): a fully connected network (ReLU hidden layers, affine output)
+ * evaluated and trained on the tensor cores with BF16 operands and FP32 accumulation.
+ *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 4096]; d_L <= 1024.
+ *  max_batch   largest batch a call may pass.
+ *  ncomp, beta the loss ||Yhat - Y||/||Y|| + beta ||D(Yhat - Y)||/||D Y|| averaged over the batch,
+ *              D the periodic difference inside each of ncomp equal blocks of an output row
+ *              (Sec. 3.4.2).
+ * Parameters are one flat FP32 vector: every W_l (d_{l+1} x d_l, row-major), then every b_l.
+ * x, y are DEVICE row-major FP32 (batch x d_0, batch x d_L). vs_mlp_forward / vs_mlp_train_step
+ * are asynchronous on the handle's stream unless a host loss pointer is given. Errors: bad sizes
+ * VS_ERR_INVALID_ARG; a tensor-core wait that runs out VS_ERR_TIMEOUT (reported on the next
+ * synchronising call).
+ */
+typedef struct vs_mlp vs_mlp;
+typedef struct {
+  float lr, beta1, beta2, eps, weight_decay;  /* AdamW (Sec. 3.4.2: lr 1e-3) */
+} vs_adamw;
+vs_status vs_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_batch, int32_t ncomp, float beta,
+                        void* cuda_stream, vs_mlp** out);
+vs_status vs_mlp_num_params(const vs_mlp* m, int64_t* n);
+/* host FP32 parameters in / out; set also clears the AdamW moments */
+vs_status vs_mlp_set_params(vs_mlp* m, const float* params, int64_t n);
+vs_status vs_mlp_get_params(vs_mlp* m, float* params, int64_t n);
+/* y (device, batch x d_L) = network(x) */
+vs_status vs_mlp_forward(vs_mlp* m, const float* x, int32_t batch, float* y);
+/* loss (host) and, when grad (host, n floats) is non-null, its gradient; synchronises */
+vs_status vs_mlp_loss_grad(vs_mlp* m, const float* x, const float* y, int32_t batch, float* loss, float* grad,
+                           int64_t n);
+/* one AdamW step on the batch; loss (host) may be null to stay asynchronous */
+vs_status vs_mlp_train_step(vs_mlp* m, const float* x, const float* y, int32_t batch, const vs_adamw* opt,
+                            float* loss);
+vs_status vs_mlp_sync(vs_mlp* m);
+const char* vs_mlp_last_error(const vs_mlp* m);
+void vs_mlp_destroy(vs_mlp* m);
+
+/*
  * Far field without any device allocation (no counterpart in the paper; a deployment variant of
  * vs_farfield_eval). Some callers cannot call cudaMalloc: code running inside another
  * framework's memory pool or allocator, a host process that has handed all device memory to

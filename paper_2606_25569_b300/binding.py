@@ -41,6 +41,19 @@ FUNCTIONS = {
     "vs_farfield_plan_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_mlp_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "vs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_mlp_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "vs_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "vs_mlp_destroy": (None, [ctypes.c_void_p]),
     "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -240,3 +253,70 @@ def farfield_eval_static(offsets, mu, precision, xy_dev, f_dev, u_dev, stream=No
                                        _ptr(f_dev), _ptr(u_dev), _stream(stream))
     if st != 0:
         raise VsError(st, "vs_farfield_eval_static failed")
+
+
+class VsAdamW(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("weight_decay", ctypes.c_float)]
+
+
+class Mlp:
+    """vs_mlp: BF16 tensor-core MLP (ReLU hidden layers) with the paper's loss and AdamW."""
+
+    def __init__(self, dims, max_batch, ncomp=2, beta=1.0, stream=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        d = np.ascontiguousarray(dims, dtype=np.int32)
+        st = L.vs_mlp_create(_ptr(d), len(d) - 1, int(max_batch), int(ncomp), float(beta), _stream(stream),
+                             ctypes.byref(self._h))
+        if st != 0:
+            raise VsError(st, L.vs_mlp_last_error(None).decode())
+        n = ctypes.c_int64()
+        self._check(L.vs_mlp_num_params(self._h, ctypes.byref(n)))
+        self.nparam = n.value
+        self.dims = list(dims)
+
+    def _check(self, st):
+        if st != 0:
+            raise VsError(st, lib().vs_mlp_last_error(self._h).decode())
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().vs_mlp_set_params(self._h, _ptr(p), len(p)))
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        self._check(lib().vs_mlp_get_params(self._h, _ptr(p), len(p)))
+        return p
+
+    def forward(self, x_dev, y_dev, batch):
+        self._check(lib().vs_mlp_forward(self._h, _ptr(x_dev), int(batch), _ptr(y_dev)))
+
+    def loss_grad(self, x_dev, y_dev, batch, want_grad=True):
+        loss = ctypes.c_float()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grad else None
+        self._check(lib().vs_mlp_loss_grad(self._h, _ptr(x_dev), _ptr(y_dev), int(batch), ctypes.byref(loss),
+                                           _ptr(g) if want_grad else None, self.nparam))
+        return loss.value, g
+
+    def train_step(self, x_dev, y_dev, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01,
+                   want_loss=False):
+        opt = VsAdamW(lr, beta1, beta2, eps, weight_decay)
+        loss = ctypes.c_float()
+        self._check(lib().vs_mlp_train_step(self._h, _ptr(x_dev), _ptr(y_dev), int(batch), ctypes.byref(opt),
+                                            ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def sync(self):
+        self._check(lib().vs_mlp_sync(self._h))
+
+    def close(self):
+        if self._h:
+            lib().vs_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,6 +16,7 @@
 #include "k_dense.cuh"
 #include "k_farfield.cuh"
 #include "k_geometry.cuh"
+#include "k_mlp.cuh"
 #include "k_near.cuh"
 #include "k_selfmat.cuh"
 #include "k_vesicle.cuh"
@@ -709,6 +710,297 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
   D.release();
   B.release();
   return e == cudaSuccess ? VS_OK : (e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Learned part: MLP forward / backward / AdamW on the tensor cores.
+struct vs_mlp {
+  std::vector<int> dims;            // d_0 .. d_L
+  int L = 0, Bcap = 0, ncomp = 1;
+  float beta = 1.f;
+  int64_t nparam = 0;
+  std::vector<int64_t> woff, boff;  // offsets of W_l, b_l in the flat parameter vector
+  cudaStream_t stream = nullptr;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  std::vector<__nv_bfloat16*> Wb, WbT, H, HT;
+  float* yhat = nullptr;
+  float *g32[2] = {nullptr, nullptr};
+  __nv_bfloat16 *gbf[2] = {nullptr, nullptr}, *gbfT[2] = {nullptr, nullptr};
+  float *loss_b = nullptr, *loss = nullptr;
+  unsigned* err = nullptr;
+  int64_t t = 0;
+  int64_t launches = 0;
+  std::string msg;
+};
+
+namespace {
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+vs_status mlp_gemm(vs_mlp* h, const GemmArgs& a) {
+  const dim3 grid((a.N + MM_BN - 1) / MM_BN, (a.M + MM_BM - 1) / MM_BM);
+  k_gemm_bf16<<<grid, MM_THREADS, MM_SMEM, h->stream>>>(a);
+  h->launches += 1;
+  VS_CK(h, cudaGetLastError(), "mlp gemm");
+  return VS_OK;
+}
+
+GemmArgs gemm_args(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int M, int N, int K,
+                   unsigned* err) {
+  GemmArgs a{};
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.M = M; a.N = N; a.K = K; a.act = EPI_NONE; a.err = err;
+  return a;
+}
+
+vs_status mlp_refresh_bf16(vs_mlp* h) {
+  for (int l = 0; l < h->L; ++l) {
+    const int rows = h->dims[l + 1], cols = h->dims[l];
+    const int64_t n = (int64_t)rows * cols;
+    k_weights_bf16<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->w + h->woff[l], rows, cols, h->Wb[l],
+                                                                        h->WbT[l]);
+    h->launches += 1;
+  }
+  VS_CK(h, cudaGetLastError(), "mlp weights");
+  return VS_OK;
+}
+
+vs_status mlp_forward(vs_mlp* h, const float* x, int batch) {
+  const int Bp = round_up(batch, MM_BM);
+  const int64_t n0 = (int64_t)Bp * h->dims[0];
+  k_rows_to_bf16<<<(unsigned)((n0 + 255) / 256), 256, 0, h->stream>>>(x, batch, Bp, h->dims[0], h->H[0], h->HT[0]);
+  h->launches += 1;
+  VS_CK(h, cudaGetLastError(), "mlp input");
+  for (int l = 0; l < h->L; ++l) {
+    GemmArgs a = gemm_args(h->H[l], h->dims[l], h->Wb[l], h->dims[l], Bp, h->dims[l + 1], h->dims[l], h->err);
+    a.bias = h->w + h->boff[l];
+    if (l + 1 < h->L) {
+      a.act = EPI_RELU;
+      a.out_bf = h->H[l + 1];
+      a.ld_bf = h->dims[l + 1];
+      a.out_bfT = h->HT[l + 1];
+      a.ld_bfT = Bp;
+    } else {
+      a.out_f32 = h->yhat;
+      a.ld_f32 = h->dims[l + 1];
+    }
+    vs_status st = mlp_gemm(h, a);
+    if (st != VS_OK) return st;
+  }
+  return VS_OK;
+}
+
+// gradient of the loss into h->g (flat, same layout as the parameters); loss into h->loss
+vs_status mlp_backward(vs_mlp* h, const float* y, int batch) {
+  const int Bp = round_up(batch, MM_BM);
+  const int dL = h->dims[h->L];
+  k_mlp_loss<<<Bp, 128, 0, h->stream>>>(h->yhat, y, batch, dL, h->ncomp, h->beta, h->g32[0], h->gbf[0], h->gbfT[0], Bp,
+                                        h->loss_b);
+  k_mean<<<1, 32, 0, h->stream>>>(h->loss_b, batch, h->loss);
+  h->launches += 2;
+  VS_CK(h, cudaGetLastError(), "mlp loss");
+  int cur = 0;
+  for (int l = h->L - 1; l >= 0; --l) {
+    const int dout = h->dims[l + 1], din = h->dims[l];
+    // dW_l = G^T H_l  (d_out x d_in), reduction over the padded batch
+    GemmArgs a = gemm_args(h->gbfT[cur], Bp, h->HT[l], Bp, dout, din, Bp, h->err);
+    a.out_f32 = h->g + h->woff[l];
+    a.ld_f32 = din;
+    vs_status st = mlp_gemm(h, a);
+    if (st != VS_OK) return st;
+    k_colsum<<<(dout + 127) / 128, 128, 0, h->stream>>>(h->g32[cur], Bp, dout, h->g + h->boff[l]);
+    h->launches += 1;
+    if (l > 0) {
+      // dH_l = (G W_l) * (H_l > 0)
+      GemmArgs b = gemm_args(h->gbf[cur], dout, h->WbT[l], dout, Bp, din, dout, h->err);
+      b.act = EPI_MASK;
+      b.mask = h->H[l];
+      b.ld_mask = din;
+      b.out_f32 = h->g32[1 - cur];
+      b.ld_f32 = din;
+      b.out_bf = h->gbf[1 - cur];
+      b.ld_bf = din;
+      b.out_bfT = h->gbfT[1 - cur];
+      b.ld_bfT = Bp;
+      if ((st = mlp_gemm(h, b)) != VS_OK) return st;
+      cur = 1 - cur;
+    }
+  }
+  VS_CK(h, cudaGetLastError(), "mlp backward");
+  return VS_OK;
+}
+
+vs_status mlp_check_err(vs_mlp* h) {
+  unsigned e = 0;
+  VS_CK(h, cudaStreamSynchronize(h->stream), "mlp sync");
+  VS_CK(h, cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost), "mlp error word");
+  if (e & ERR_MMA_TIMEOUT) { h->msg = "tensor-core GEMM wait timed out"; return VS_ERR_TIMEOUT; }
+  return VS_OK;
+}
+
+void mlp_free(vs_mlp* h) {
+  cudaFree(h->w); cudaFree(h->g); cudaFree(h->m); cudaFree(h->v); cudaFree(h->yhat);
+  for (auto* p : h->Wb) cudaFree(p);
+  for (auto* p : h->WbT) cudaFree(p);
+  for (auto* p : h->H) cudaFree(p);
+  for (auto* p : h->HT) cudaFree(p);
+  for (int i = 0; i < 2; ++i) { cudaFree(h->g32[i]); cudaFree(h->gbf[i]); cudaFree(h->gbfT[i]); }
+  cudaFree(h->loss_b); cudaFree(h->loss); cudaFree(h->err);
+}
+
+}  // namespace
+
+extern "C" {
+
+vs_status vs_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_batch, int32_t ncomp, float beta,
+                        void* cuda_stream, vs_mlp** out) {
+  if (!out) return VS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dims || nlayers < 1 || max_batch < 1 || ncomp < 1 || !(beta >= 0.f)) {
+    g_create_msg = "bad MLP arguments";
+    return VS_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l <= nlayers; ++l)
+    if (dims[l] < 16 || dims[l] % 16 != 0 || dims[l] > 4096) {
+      g_create_msg = "MLP widths must be multiples of 16 in [16, 4096]";
+      return VS_ERR_INVALID_ARG;
+    }
+  if (dims[nlayers] > 1024 || dims[nlayers] % ncomp != 0) {
+    g_create_msg = "output width must be <= 1024 and divisible by ncomp";
+    return VS_ERR_INVALID_ARG;
+  }
+  vs_mlp* h = new (std::nothrow) vs_mlp();
+  if (!h) return VS_ERR_NOMEM;
+  h->dims.assign(dims, dims + nlayers + 1);
+  h->L = nlayers;
+  h->Bcap = round_up(max_batch, MM_BM);
+  h->ncomp = ncomp;
+  h->beta = beta;
+  h->stream = (cudaStream_t)cuda_stream;
+  int64_t o = 0;
+  for (int l = 0; l < h->L; ++l) { h->woff.push_back(o); o += (int64_t)h->dims[l] * h->dims[l + 1]; }
+  for (int l = 0; l < h->L; ++l) { h->boff.push_back(o); o += h->dims[l + 1]; }
+  h->nparam = o;
+  int dmax = 0;
+  for (int d : h->dims) dmax = std::max(dmax, d);
+  cudaError_t e;
+  auto fail = [&](cudaError_t ee) {
+    cuda_fail(g_create_msg, ee, "vs_mlp_create");
+    mlp_free(h);
+    delete h;
+    return ee == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA;
+  };
+#define VS_M(x) do { e = (x); if (e != cudaSuccess) return fail(e); } while (0)
+  VS_M(dalloc(&h->w, h->nparam)); VS_M(dalloc(&h->g, h->nparam));
+  VS_M(dalloc(&h->m, h->nparam)); VS_M(dalloc(&h->v, h->nparam));
+  h->Wb.assign(h->L, nullptr); h->WbT.assign(h->L, nullptr);
+  for (int l = 0; l < h->L; ++l) {
+    VS_M(dalloc(&h->Wb[l], (int64_t)h->dims[l] * h->dims[l + 1]));
+    VS_M(dalloc(&h->WbT[l], (int64_t)h->dims[l] * h->dims[l + 1]));
+  }
+  h->H.assign(h->L, nullptr); h->HT.assign(h->L, nullptr);
+  for (int l = 0; l < h->L; ++l) {
+    VS_M(dalloc(&h->H[l], (int64_t)h->Bcap * h->dims[l]));
+    VS_M(dalloc(&h->HT[l], (int64_t)h->Bcap * h->dims[l]));
+  }
+  VS_M(dalloc(&h->yhat, (int64_t)h->Bcap * h->dims[h->L]));
+  for (int i = 0; i < 2; ++i) {
+    VS_M(dalloc(&h->g32[i], (int64_t)h->Bcap * dmax));
+    VS_M(dalloc(&h->gbf[i], (int64_t)h->Bcap * dmax));
+    VS_M(dalloc(&h->gbfT[i], (int64_t)h->Bcap * dmax));
+  }
+  VS_M(dalloc(&h->loss_b, h->Bcap)); VS_M(dalloc(&h->loss, 1)); VS_M(dalloc(&h->err, 1));
+  VS_M(cudaMemset(h->err, 0, sizeof(unsigned)));
+  VS_M(cudaMemset(h->w, 0, h->nparam * sizeof(float)));
+  VS_M(cudaMemset(h->m, 0, h->nparam * sizeof(float)));
+  VS_M(cudaMemset(h->v, 0, h->nparam * sizeof(float)));
+  VS_M(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM));
+#undef VS_M
+  if (mlp_refresh_bf16(h) != VS_OK) return fail(cudaErrorUnknown);
+  *out = h;
+  return VS_OK;
+}
+
+vs_status vs_mlp_num_params(const vs_mlp* h, int64_t* n) {
+  if (!h || !n) return VS_ERR_INVALID_ARG;
+  *n = h->nparam;
+  return VS_OK;
+}
+
+vs_status vs_mlp_set_params(vs_mlp* h, const float* params, int64_t n) {
+  if (!h || !params || n != h->nparam) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaMemcpyAsync(h->w, params, n * sizeof(float), cudaMemcpyHostToDevice, h->stream), "set params");
+  VS_CK(h, cudaMemsetAsync(h->m, 0, n * sizeof(float), h->stream), "set params");
+  VS_CK(h, cudaMemsetAsync(h->v, 0, n * sizeof(float), h->stream), "set params");
+  h->t = 0;
+  vs_status st = mlp_refresh_bf16(h);
+  if (st != VS_OK) return st;
+  VS_CK(h, cudaStreamSynchronize(h->stream), "set params");
+  return VS_OK;
+}
+
+vs_status vs_mlp_get_params(vs_mlp* h, float* params, int64_t n) {
+  if (!h || !params || n != h->nparam) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaMemcpyAsync(params, h->w, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "get params");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "get params");
+  return VS_OK;
+}
+
+vs_status vs_mlp_forward(vs_mlp* h, const float* x, int32_t batch, float* y) {
+  if (!h || !x || !y || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
+  vs_status st = mlp_forward(h, x, batch);
+  if (st != VS_OK) return st;
+  const int dL = h->dims[h->L];
+  VS_CK(h, cudaMemcpyAsync(y, h->yhat, (size_t)batch * dL * sizeof(float), cudaMemcpyDeviceToDevice, h->stream),
+        "forward out");
+  return VS_OK;
+}
+
+vs_status vs_mlp_loss_grad(vs_mlp* h, const float* x, const float* y, int32_t batch, float* loss, float* grad,
+                           int64_t n) {
+  if (!h || !x || !y || !loss || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
+  if (grad && n != h->nparam) return VS_ERR_INVALID_ARG;
+  vs_status st = mlp_forward(h, x, batch);
+  if (st == VS_OK) st = mlp_backward(h, y, batch);
+  if (st != VS_OK) return st;
+  VS_CK(h, cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream), "loss");
+  if (grad) VS_CK(h, cudaMemcpyAsync(grad, h->g, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "grad");
+  return mlp_check_err(h);
+}
+
+vs_status vs_mlp_train_step(vs_mlp* h, const float* x, const float* y, int32_t batch, const vs_adamw* opt, float* loss) {
+  if (!h || !x || !y || !opt || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
+  vs_status st = mlp_forward(h, x, batch);
+  if (st == VS_OK) st = mlp_backward(h, y, batch);
+  if (st != VS_OK) return st;
+  h->t += 1;
+  const float c1 = 1.f - powf(opt->beta1, (float)h->t), c2 = 1.f - powf(opt->beta2, (float)h->t);
+  k_adamw<<<(unsigned)((h->nparam + 255) / 256), 256, 0, h->stream>>>(h->w, h->g, h->m, h->v, h->nparam, opt->lr,
+                                                                      opt->beta1, opt->beta2, opt->eps,
+                                                                      opt->weight_decay, c1, c2);
+  h->launches += 1;
+  VS_CK(h, cudaGetLastError(), "adamw");
+  if ((st = mlp_refresh_bf16(h)) != VS_OK) return st;
+  if (loss) {
+    VS_CK(h, cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream), "loss");
+    return mlp_check_err(h);
+  }
+  return VS_OK;
+}
+
+vs_status vs_mlp_sync(vs_mlp* h) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  return mlp_check_err(h);
+}
+
+const char* vs_mlp_last_error(const vs_mlp* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }
+
+void vs_mlp_destroy(vs_mlp* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  mlp_free(h);
+  delete h;
 }
 
 }  // extern "C"

@@ -1,0 +1,76 @@
+"""GPU parity of the tensor-core MLP (forward, gradients, AdamW) against the FP64 oracle with the
+same bfloat16 rounding points (oracle.mlp, bf16=True)."""
+import numpy as np
+import pytest
+
+from oracle.mlp import AdamW, forward, init_params, loss_and_gradient
+from paper_2606_25569_b300 import binding
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DIMS = [128, 512, 512, 512, 128]
+
+
+def _data(batch, seed):
+    rng = np.random.default_rng(seed)
+    p = init_params(DIMS, rng)
+    p[-sum(DIMS[1:]):] = 0.05 * rng.standard_normal(sum(DIMS[1:]))
+    X = rng.standard_normal((batch, DIMS[0]))
+    Y = rng.standard_normal((batch, DIMS[-1]))
+    return p, X, Y
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("batch", [300, 512])
+def test_forward_matches_oracle(batch):
+    p, X, _ = _data(batch, 1)
+    p32 = p.astype(np.float32).astype(np.float64)
+    net = binding.Mlp(DIMS, max_batch=batch)
+    net.set_params(p32)
+    y = torch.empty(batch, DIMS[-1], dtype=torch.float32, device="cuda")
+    net.forward(_dev(X), y, batch)
+    net.sync()
+    got = y.cpu().numpy().astype(np.float64)
+    ref, _ = forward(p32, DIMS, X.astype(np.float32).astype(np.float64), bf16=True)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-3, err
+
+
+def test_gradient_matches_oracle():
+    batch = 256
+    p, X, Y = _data(batch, 2)
+    p32 = p.astype(np.float32).astype(np.float64)
+    X32, Y32 = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    net = binding.Mlp(DIMS, max_batch=batch, ncomp=2, beta=0.5)
+    net.set_params(p32)
+    loss, g = net.loss_grad(_dev(X), _dev(Y), batch)
+    lo, go = loss_and_gradient(p32, DIMS, X32, Y32, beta=0.5, ncomp=2, bf16=True)
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    err = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert err <= 1e-2, err
+
+
+def test_adamw_step_and_training_reduces_loss():
+    batch = 512
+    rng = np.random.default_rng(3)
+    p = init_params(DIMS, rng)
+    X = rng.standard_normal((batch, DIMS[0]))
+    W = rng.standard_normal((DIMS[-1], DIMS[0])) / np.sqrt(DIMS[0])
+    Y = np.tanh(X @ W.T)
+    net = binding.Mlp(DIMS, max_batch=batch, ncomp=2, beta=0.1)
+    p32 = p.astype(np.float32)
+    net.set_params(p32)
+    xd, yd = _dev(X), _dev(Y)
+    # one step against the oracle's AdamW applied to the GPU gradient
+    _, g = net.loss_grad(xd, yd, batch)
+    opt = AdamW(net.nparam, lr=1e-3, weight_decay=0.01)
+    expect = opt.step(p32.astype(np.float64), g.astype(np.float64))
+    net.train_step(xd, yd, batch, lr=1e-3, weight_decay=0.01)
+    got = net.get_params().astype(np.float64)
+    assert np.max(np.abs(got - expect)) <= 2e-6
+    losses = [net.train_step(xd, yd, batch, want_loss=True) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
