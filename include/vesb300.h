@@ -68,7 +68,7 @@ typedef struct {
   double mu;         /* viscosity, > 0 */
   double dt;         /* time step, > 0 */
   double corr_tol;   /* relative area/length error that triggers the correction (Sec. 4.3: 0.01) */
-  int32_t mode;      /* 0: plain boundary-integral step (the only mode of this version) */
+  int32_t mode;      /* 0: plain boundary-integral step, 1: hybrid (learned relaxation, vs_set_network) */
   int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
   int32_t use_graph; /* reserved */
   int32_t pad_;
@@ -76,6 +76,7 @@ typedef struct {
 } vs_params;
 
 typedef struct vs_suspension vs_suspension;
+typedef struct vs_mlp vs_mlp;
 
 /*
  * Create a suspension (Algorithm 1 input, Sec. 4.4).
@@ -139,6 +140,22 @@ vs_status vs_profile(vs_suspension* s, int32_t enable);
 vs_status vs_profile_read(vs_suspension* s, int32_t idx, char* name, int32_t name_cap, double* total_ms,
                           int64_t* launches);
 
+/*
+ * Learned maps for the hybrid step (params.mode = 1; VesNet, Sec. 3.2 and Algorithm 1).
+ * which = 0: the relaxation flow map X_X (Eq. relaxation_disc replaced by a network): the step
+ * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the Fourier-filtered
+ * standardised shape and adds out_scale * output, mapped back from the standard frame, as
+ * X^{n+1} - X*. The network (borrowed, must outlive its use) needs widths 2N in and out, batch
+ * capacity >= M, the suspension's stream, and one N for all vesicles; otherwise
+ * VS_ERR_INVALID_ARG. net = NULL removes it; a hybrid step without it fails with VS_ERR_NO_NETWORK.
+ */
+vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double out_scale);
+
+/* Exact relaxation step (Eq. relaxation_disc) of the given DEVICE points (CSR blocks) into
+ * xy_out, with the suspension's kappa_b, mu and dt -- the map the learned relaxation is trained
+ * on. Does not change the suspension's state. Asynchronous. */
+vs_status vs_relax(vs_suspension* s, const double* xy_in, double* xy_out);
+
 const char* vs_last_error(const vs_suspension* s);
 void vs_destroy(vs_suspension* s);
 
@@ -174,6 +191,16 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
                            double* S_out, void* cuda_stream);
 
 /*
+ * Standardisation of every vesicle for the networks (Sec. 3.4.1): centroid, principal axis along
+ * +y, unit length, cyclic relabelling so that point 0 is the right-most upward crossing of the x
+ * axis, Fourier filter keeping modes |k| <= N/4. xy: device CSR blocks. xin: device FP32, row v =
+ * [x^o(N_max), y^o(N_max)] at offset 2 N_max v (first 2 N_v entries used). frames: device, 6 doubles
+ * per vesicle (c_x, c_y, cos t, sin t, 1/L, first-point label). Synchronous.
+ */
+vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, float* xin, double* frames,
+                         void* cuda_stream);
+
+/*
  * Learned part (Sec. 3.2-3.4): a fully connected network (ReLU hidden layers, affine output)
  * evaluated and trained on the tensor cores with BF16 operands and FP32 accumulation.
  *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 4096]; d_L <= 1024.
@@ -187,7 +214,6 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
  * VS_ERR_INVALID_ARG; a tensor-core wait that runs out VS_ERR_TIMEOUT (reported on the next
  * synchronising call).
  */
-typedef struct vs_mlp vs_mlp;
 typedef struct {
   float lr, beta1, beta2, eps, weight_decay;  /* AdamW (Sec. 3.4.2: lr 1e-3) */
 } vs_adamw;

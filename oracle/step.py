@@ -16,7 +16,8 @@ Readings: Eq. tension_disc writes L^n, P^n while Algorithm 1-2 evaluate them at 
 use X^{n+1} after redistribution (step 6), and since redistribution re-indexes the material
 points, u^n is carried to the new points by its trigonometric interpolant. Algorithm 1
 computes the tension before the correction and so do we. One far-field evaluation per step
-(Algorithm 1 needs u^n once). Initial tension (not given in the paper):
+(Algorithm 1 needs u^n once). With Params.relax_net set, step 4 is the learned relaxation of the
+hybrid step (relax_learned). Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -31,10 +32,37 @@ from .spectral import Geometry, eval_interpolant, force
 
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
-                 near_field=False, corr_tol=0.01):
+                 near_field=False, corr_tol=0.01, relax_net=None):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
+        # (dims, flat parameters, output scale): the learned relaxation map of the hybrid step
+        self.relax_net = relax_net
+
+
+def relax_learned(x, y, net):
+    """Hybrid relaxation (VesNet's X_X map, Sec. 3.2, 3.4.1): redistribute X* (Sec. 4.2),
+    standardise, evaluate the network on the Fourier-filtered standardised shape (bfloat16
+    operands as on the tensor cores, input first rounded to float32), scale its output and map it
+    back as the displacement X^{n+1} - X*_r."""
+    from .mlp import forward
+    from .standardize import destandardize_disp, fourier_filter, standardize
+    dims, params, scale = net
+    N = len(x)
+    xr, yr, _ = redistribute(x, y)
+    xo, yo, fr = standardize(xr, yr)
+    inp = np.concatenate([fourier_filter(xo), fourier_filter(yo)])[None, :]
+    out, _ = forward(params, dims, inp, bf16=True)
+    dx, dy = destandardize_disp(scale * out[0, :N], scale * out[0, N:], fr)
+    return np.concatenate([xr + dx, yr + dy])
+
+
+def relax_exact(x, y, p):
+    """Relaxation (Eq. relaxation_disc): solve (I - dt (I - M*) B*) X^{n+1} = X*."""
+    N = len(x)
+    ops_s = Operators(x, y, p.kappa, p.mu)
+    A = np.eye(2 * N) - p.dt * (ops_s.B - ops_s.T @ np.linalg.solve(ops_s.L, ops_s.P @ ops_s.B))
+    return np.linalg.solve(A, np.concatenate([x, y]))
 
 
 def _tension(ops, x, y, ux, uy, kappa):
@@ -97,9 +125,10 @@ class Suspension:
             ubar = np.concatenate([ux, uy])
             ops_n = Operators(x, y, p.kappa, p.mu)
             zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
-            ops_s = Operators(zs[:N], zs[N:], p.kappa, p.mu)
-            A = np.eye(2 * N) - p.dt * (ops_s.B - ops_s.T @ np.linalg.solve(ops_s.L, ops_s.P @ ops_s.B))
-            z1 = np.linalg.solve(A, zs)
+            if p.relax_net is not None:
+                z1 = relax_learned(zs[:N], zs[N:], p.relax_net)
+            else:
+                z1 = relax_exact(zs[:N], zs[N:], p)
             xr, yr, alpha = redistribute(z1[:N], z1[N:])
             uxr, uyr = eval_interpolant(ux, alpha), eval_interpolant(uy, alpha)
             ops_r = Operators(xr, yr, p.kappa, p.mu)

@@ -31,6 +31,8 @@ FUNCTIONS = {
     "vs_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "vs_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double]),
+    "vs_relax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -54,6 +56,8 @@ FUNCTIONS = {
     "vs_mlp_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "vs_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_mlp_destroy": (None, [ctypes.c_void_p]),
+    "vs_standardize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -115,14 +119,14 @@ class Suspension:
     """Owner of a vs_suspension handle (vs_create ... vs_destroy)."""
 
     def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
-                 flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None):
+                 flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0):
         L = lib()
         self._h = ctypes.c_void_p()
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self.M = len(off) - 1
         self.P = int(off[-1])
-        p = VsParams(kappa, mu, dt, corr_tol, 0, 1 if near_field else 0, 0, 0,
+        p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 0, 0,
                      VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0)
         f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
         st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),
@@ -183,6 +187,13 @@ class Suspension:
             out[buf.value.decode()] = (ms.value, n.value)
             i += 1
         return out
+
+    def set_network(self, net, out_scale, which=0):
+        self._net = net  # the library borrows it
+        self._check(lib().vs_set_network(self._h, int(which), net._h if net is not None else None, float(out_scale)))
+
+    def relax(self, xy_in_dev, xy_out_dev):
+        self._check(lib().vs_relax(self._h, _ptr(xy_in_dev), _ptr(xy_out_dev)))
 
     def device_ptrs(self):
         a, b = ctypes.c_void_p(), ctypes.c_void_p()
@@ -320,3 +331,11 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def standardize(xy_dev, offsets, xin_dev, frames_dev, stream=None):
+    """vs_standardize: FP32 network input rows and frames of every vesicle (device tensors)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    st = lib().vs_standardize(_ptr(xy_dev), _ptr(off), len(off) - 1, _ptr(xin_dev), _ptr(frames_dev), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_standardize failed")

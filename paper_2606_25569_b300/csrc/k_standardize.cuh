@@ -1,0 +1,152 @@
+// Standardisation for the networks (Sec. 3.4.1; Algorithms 2-4) and its inverse for displacements.
+//
+// k_standardize, one CTA (NMAX threads) per vesicle:
+//   centre c = (2/3) int X (X.n) ds / int X.n ds (the area centroid; the printed ratio lacks 2/3),
+//   J = 1/4 int (r.n)(|r|^2 I - r r^T) ds, principal axis = eigenvector of the smallest eigenvalue
+//   (y component >= 0), rotation taking it to +y, scale 1/L, cyclic shift so that point 0 is the
+//   right-most upward crossing of the x axis, then the Fourier filter (modes |k| <= N/4 kept).
+//   Writes the FP32 network input row [x^o(N), y^o(N)] and the frame parameters.
+// k_destandardize_add: X += R^T (out_scale * dX^o) / s, shifted back to the original labels.
+#pragma once
+#include "common.cuh"
+
+namespace vs {
+
+struct StdFrame {
+  double cx, cy, ct, st, s;
+  int j0;
+  int pad;
+};
+
+__global__ void __launch_bounds__(NMAX) k_standardize(VesIndex vi, const double* __restrict__ xy,
+                                                      const double* __restrict__ tab, float* __restrict__ xin,
+                                                      int64_t ld_in, StdFrame* __restrict__ frame) {
+  __shared__ double d[NMAX], xs[NMAX], ys[NMAX], xr[NMAX], yr[NMAX], red[NMAX / 32];
+  __shared__ double cre[2][NMAX / 4 + 1], cim[2][NMAX / 4 + 1];
+  __shared__ int sj0;
+  const int v = blockIdx.x;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int i = threadIdx.x;
+  const bool act = i < N;
+  const double* T = tab + vi.toff[v];
+  if (act) {
+    d[i] = T[i];
+    xs[i] = xy[2 * o + i];
+    ys[i] = xy[2 * o + N + i];
+  }
+  __syncthreads();
+  double xa = 0.0, ya = 0.0;
+  if (act) {
+    xa = circ_row(d, xs, N, i);
+    ya = circ_row(d, ys, N, i);
+  }
+  const double sa = act ? sqrt(xa * xa + ya * ya) : 1.0;
+  const double nx = ya / sa, ny = -xa / sa;  // outward normal (t_y, -t_x)
+  const double w = act ? sa * 2.0 * VS_PI / N : 0.0;
+  const double X = act ? xs[i] : 0.0, Y = act ? ys[i] : 0.0;
+  const double xn = X * nx + Y * ny;
+  const double den = block_sum(xn * w, red);
+  const double cx = block_sum(X * xn * w, red) / (1.5 * den);
+  const double cy = block_sum(Y * xn * w, red) / (1.5 * den);
+  const double L = block_sum(w, red);
+  const double rx = X - cx, ry = Y - cy;
+  const double rn = rx * nx + ry * ny, r2 = rx * rx + ry * ry;
+  const double Ja = 0.25 * block_sum(rn * (r2 - rx * rx) * w, red);
+  const double Jb = 0.25 * block_sum(rn * (-rx * ry) * w, red);
+  const double Jd = 0.25 * block_sum(rn * (r2 - ry * ry) * w, red);
+  // smallest eigenvalue and its eigenvector (the better conditioned of two equivalent forms)
+  const double hm = 0.5 * (Ja + Jd), hd = 0.5 * (Ja - Jd);
+  const double lam = hm - sqrt(hd * hd + Jb * Jb);
+  double px = lam - Jd, py = Jb;
+  const double qx = Jb, qy = lam - Ja;
+  if (qx * qx + qy * qy > px * px + py * py) { px = qx; py = qy; }
+  const double pn = sqrt(px * px + py * py);
+  px /= pn;
+  py /= pn;
+  if (py < 0.0 || (py == 0.0 && px < 0.0)) { px = -px; py = -py; }
+  const double ct = py, st = px, s = 1.0 / L;
+  if (act) {
+    xr[i] = s * (ct * rx - st * ry);
+    yr[i] = s * (st * rx + ct * ry);
+  }
+  __syncthreads();
+  // right-most upward crossing: y_{j-1} < 0 <= y_j (smallest index on ties)
+  double best = -1e300;
+  int bj = N;
+  if (act) {
+    const int jm = (i == 0) ? N - 1 : i - 1;
+    if (yr[jm] < 0.0 && yr[i] >= 0.0) { best = xr[i]; bj = i; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+    if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+  }
+  __shared__ double rb[NMAX / 32];
+  __shared__ int rj[NMAX / 32];
+  if ((i & 31) == 0) { rb[i >> 5] = best; rj[i >> 5] = bj; }
+  __syncthreads();
+  if (i == 0) {
+    double b = rb[0];
+    int j = rj[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      if (rb[k] > b || (rb[k] == b && rj[k] < j)) { b = rb[k]; j = rj[k]; }
+    sj0 = (j < N) ? j : 0;
+  }
+  __syncthreads();
+  const int j0 = sj0;
+  // Fourier coefficients k = 0..N/4 of the shifted curve
+  const int nk = N / 4 + 1;
+  for (int e = i; e < 2 * nk; e += blockDim.x) {
+    const int comp = e / nk, k = e - comp * nk;
+    const double* src = comp ? yr : xr;
+    double re = 0.0, im = 0.0;
+    int m = 0;
+    for (int j = 0; j < N; ++j) {
+      const double val = src[(j + j0) % N];
+      re = fma(val, T[15 * N + m], re);
+      im = fma(-val, T[16 * N + m], im);
+      m += k;
+      if (m >= N) m -= N;
+    }
+    cre[comp][k] = re / N;
+    cim[comp][k] = im / N;
+  }
+  __syncthreads();
+  if (act) {
+    double fx = cre[0][0], fy = cre[1][0];
+    int m = 0;
+    for (int k = 1; k < nk; ++k) {
+      m += i;
+      if (m >= N) m -= N;
+      const double c = T[15 * N + m], sn = T[16 * N + m];
+      fx += 2.0 * (cre[0][k] * c - cim[0][k] * sn);
+      fy += 2.0 * (cre[1][k] * c - cim[1][k] * sn);
+    }
+    xin[(int64_t)v * ld_in + i] = (float)fx;
+    xin[(int64_t)v * ld_in + N + i] = (float)fy;
+  }
+  if (i == 0) frame[v] = StdFrame{cx, cy, ct, st, s, j0, 0};
+}
+
+// xy[v] += R^T (scale * dX^o) / s with the labels shifted back by j0.
+__global__ void __launch_bounds__(NMAX) k_destandardize_add(VesIndex vi, const float* __restrict__ yout,
+                                                            int64_t ld_out, double scale,
+                                                            const StdFrame* __restrict__ frame,
+                                                            double* __restrict__ xy) {
+  const int v = blockIdx.x;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int k = threadIdx.x;
+  if (k >= N) return;
+  const StdFrame f = frame[v];
+  const double dx = scale * (double)yout[(int64_t)v * ld_out + k] / f.s;
+  const double dy = scale * (double)yout[(int64_t)v * ld_out + N + k] / f.s;
+  const int i = (k + f.j0) % N;
+  xy[2 * o + i] += f.ct * dx + f.st * dy;
+  xy[2 * o + N + i] += -f.st * dx + f.ct * dy;
+}
+
+}  // namespace vs

@@ -19,6 +19,7 @@
 #include "k_mlp.cuh"
 #include "k_near.cuh"
 #include "k_selfmat.cuh"
+#include "k_standardize.cuh"
 #include "k_vesicle.cuh"
 #include "tables.cuh"
 
@@ -189,6 +190,25 @@ struct Prof {
   }
 };
 
+struct vs_mlp {
+  std::vector<int> dims;            // d_0 .. d_L
+  int L = 0, Bcap = 0, ncomp = 1;
+  float beta = 1.f;
+  int64_t nparam = 0;
+  std::vector<int64_t> woff, boff;  // offsets of W_l, b_l in the flat parameter vector
+  cudaStream_t stream = nullptr;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  std::vector<__nv_bfloat16*> Wb, WbT, H, HT;
+  float* yhat = nullptr;
+  float *g32[2] = {nullptr, nullptr};
+  __nv_bfloat16 *gbf[2] = {nullptr, nullptr}, *gbfT[2] = {nullptr, nullptr};
+  float *loss_b = nullptr, *loss = nullptr;
+  unsigned* err = nullptr;
+  int64_t t = 0;
+  int64_t launches = 0;
+  std::string msg;
+};
+
 struct vs_suspension {
   Layout L;
   DevLayout D;
@@ -202,6 +222,10 @@ struct vs_suspension {
   unsigned* err = nullptr;
   int* has_near = nullptr;
   NearBufs nb{nullptr, nullptr};
+  float* xin = nullptr;            // network input rows (M x 2N)
+  StdFrame* frames = nullptr;      // standardisation frames (M)
+  struct vs_mlp* net = nullptr;    // learned relaxation map (hybrid mode), borrowed
+  double net_scale = 1.0;
   int cur = 0;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -318,6 +342,47 @@ vs_status far_field(vs_suspension* h) {
   return VS_OK;
 }
 
+vs_status mlp_forward(vs_mlp* h, const float* x, int batch);
+const float* mlp_output(const vs_mlp* h);
+
+// Exact relaxation (Eq. relaxation_disc) of the points xs into xo, operators built in slot s.
+vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
+  const Layout& L = h->L;
+  const int M = L.M, n = L.nmax;
+  const VesIndex vi = h->D.vi();
+  vs_status st;
+  if ((st = geometry(h, xs, false)) != VS_OK) return st;
+  if ((st = build_operators(h, xs, s, nullptr)) != VS_OK) return st;
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
+  VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 0, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 1, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
+  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
+  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr));
+  VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo));
+  VS_CK(h, cudaGetLastError(), "relaxation");
+  return VS_OK;
+}
+
+// Learned relaxation (VesNet's X_X map): X*_r = redistribute(X*), X^{n+1} = X*_r + destandardise(net(standardise(X*_r))).
+vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  if (!h->net) { h->msg = "hybrid mode needs a relaxation network (vs_set_network)"; return VS_ERR_NO_NETWORK; }
+  VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, xs, h->u, h->D.tab, xo, h->u_r));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, 2 * L.nmax, h->frames));
+  VS_CK(h, cudaGetLastError(), "standardise");
+  vs_status st = mlp_forward(h->net, h->xin, L.M);
+  if (st != VS_OK) { h->msg = "network forward failed"; return st; }
+  VS_LAUNCH(h, "k_destandardize_add", k_destandardize_add<<<L.M, NMAX, 0, h->stream>>>(vi, mlp_output(h->net), 2 * L.nmax,
+                                                                                       h->net_scale, h->frames, xo));
+  VS_CK(h, cudaGetLastError(), "destandardise");
+  return VS_OK;
+}
+
 // u += near-field correction of every (target, vesicle) pair the far field masked (Sec. 3.3).
 vs_status near_field(vs_suspension* h, int s) {
   const Layout& L = h->L;
@@ -355,20 +420,12 @@ vs_status step_once(vs_suspension* h) {
   VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
                                      h->xy_star));
   VS_CK(h, cudaGetLastError(), "advection");
-  // (5) relaxation at X*
-  if ((st = geometry(h, h->xy_star, false)) != VS_OK) return st;
-  if ((st = build_operators(h, h->xy_star, nxt, nullptr)) != VS_OK) return st;
-  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
-  VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 0, h->p.kappa_b}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, nxt, 1, h->p.kappa_b}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
-  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, nxt, h->piv, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, nxt, h->p.dt}, nullptr));
-  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr));
-  VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, h->xy_star, h->scratch, h->piv, h->xy_next));
-  VS_CK(h, cudaGetLastError(), "relaxation");
+  // (5) relaxation at X*: exact (plain) or the learned map (hybrid)
+  if (h->p.mode == 1) {
+    if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
+  } else {
+    if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt)) != VS_OK) return st;
+  }
   // (6) redistribution of X^{n+1}; u carried to the new parameters
   VS_LAUNCH(h, "k_redistribute", k_redistribute<<<M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r));
   VS_CK(h, cudaGetLastError(), "redistribution");
@@ -403,7 +460,7 @@ bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
     msg = "kappa_b, mu, dt must be positive and corr_tol non-negative";
     return false;
   }
-  if (p->mode != 0) { msg = "only the plain mode (0) is available"; return false; }
+  if (p->mode != 0 && p->mode != 1) { msg = "mode must be 0 (plain) or 1 (hybrid)"; return false; }
   if (f->kind < 0 || f->kind > 3) { msg = "unknown flow kind"; return false; }
   if ((f->kind == 2 || f->kind == 3) && !(f->p[1] != 0.0)) { msg = "flow length scale p[1] must be non-zero"; return false; }
   return true;
@@ -416,7 +473,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
   cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near);
-  cudaFree(h->nb.layer); cudaFree(h->nb.phi);
+  cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
 }
 
 thread_local std::string g_create_msg;
@@ -456,6 +513,8 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->scratch, L.moff[L.M])); VS_A(dalloc(&h->piv, 4 * L.P));
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
+  VS_A(dalloc(&h->xin, 2 * (int64_t)L.nmax * L.M));
+  VS_A(dalloc(&h->frames, L.M));
   if (h->p.near_field) {
     VS_A(dalloc(&h->nb.layer, 30 * L.P));
     VS_A(dalloc(&h->nb.phi, L.moff[L.M]));
@@ -593,6 +652,29 @@ vs_status vs_profile_read(vs_suspension* h, int32_t idx, char* name, int32_t nam
   return VS_OK;
 }
 
+
+vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double out_scale) {
+  if (!h || which != 0) return VS_ERR_INVALID_ARG;
+  if (!net) { h->net = nullptr; return VS_OK; }
+  const Layout& L = h->L;
+  for (int v = 0; v < L.M; ++v)
+    if (L.N[v] != L.nmax) { h->msg = "the learned relaxation needs one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
+  if (net->dims.front() != 2 * L.nmax || net->dims.back() != 2 * L.nmax || net->Bcap < L.M) {
+    h->msg = "network widths must be 2N in and out and its batch capacity at least M";
+    return VS_ERR_INVALID_ARG;
+  }
+  if (net->stream != h->stream) { h->msg = "network and suspension must share one stream"; return VS_ERR_INVALID_ARG; }
+  if (!(out_scale > 0)) return VS_ERR_INVALID_ARG;
+  h->net = net;
+  h->net_scale = out_scale;
+  return VS_OK;
+}
+
+vs_status vs_relax(vs_suspension* h, const double* xy_in, double* xy_out) {
+  if (!h || !xy_in || !xy_out || xy_in == xy_out) return VS_ERR_INVALID_ARG;
+  return relax_exact(h, xy_in, xy_out, 1 - h->cur);
+}
+
 const char* vs_last_error(const vs_suspension* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }
 
 void vs_destroy(vs_suspension* h) {
@@ -681,6 +763,38 @@ void vs_farfield_plan_destroy(vs_farfield_plan* h) {
 }
 
 // ---------------------------------------------------------------------------------------------
+
+vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, float* xin, double* frames,
+                         void* cuda_stream) {
+  if (!xy || !xin || !frames) return VS_ERR_INVALID_ARG;
+  Layout L;
+  std::string msg;
+  if (!build_layout(offsets, M, L, msg)) return VS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  DevLayout D;
+  StdFrame* fr = nullptr;
+  cudaError_t e = upload_layout(L, D, s);
+  if (e == cudaSuccess) e = dalloc(&fr, L.M);
+  if (e == cudaSuccess) {
+    k_standardize<<<M, NMAX, 0, s>>>(D.vi(), xy, D.tab, xin, 2 * L.nmax, fr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    std::vector<StdFrame> hf(M);
+    e = cudaMemcpy(hf.data(), fr, M * sizeof(StdFrame), cudaMemcpyDeviceToHost);
+    std::vector<double> out(6 * (size_t)M);
+    for (int v = 0; v < M; ++v) {
+      out[6 * v + 0] = hf[v].cx; out[6 * v + 1] = hf[v].cy; out[6 * v + 2] = hf[v].ct;
+      out[6 * v + 3] = hf[v].st; out[6 * v + 4] = hf[v].s; out[6 * v + 5] = hf[v].j0;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(frames, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  cudaFree(fr);
+  D.release();
+  return e == cudaSuccess ? VS_OK : (e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
+}
+
 vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, double mu, double* S_out,
                            void* cuda_stream) {
   if (!xy || !S_out || !(mu > 0)) return VS_ERR_INVALID_ARG;
@@ -716,24 +830,7 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
 
 // ---------------------------------------------------------------------------------------------
 // Learned part: MLP forward / backward / AdamW on the tensor cores.
-struct vs_mlp {
-  std::vector<int> dims;            // d_0 .. d_L
-  int L = 0, Bcap = 0, ncomp = 1;
-  float beta = 1.f;
-  int64_t nparam = 0;
-  std::vector<int64_t> woff, boff;  // offsets of W_l, b_l in the flat parameter vector
-  cudaStream_t stream = nullptr;
-  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
-  std::vector<__nv_bfloat16*> Wb, WbT, H, HT;
-  float* yhat = nullptr;
-  float *g32[2] = {nullptr, nullptr};
-  __nv_bfloat16 *gbf[2] = {nullptr, nullptr}, *gbfT[2] = {nullptr, nullptr};
-  float *loss_b = nullptr, *loss = nullptr;
-  unsigned* err = nullptr;
-  int64_t t = 0;
-  int64_t launches = 0;
-  std::string msg;
-};
+
 
 namespace {
 
@@ -830,6 +927,8 @@ vs_status mlp_backward(vs_mlp* h, const float* y, int batch) {
   VS_CK(h, cudaGetLastError(), "mlp backward");
   return VS_OK;
 }
+
+const float* mlp_output(const vs_mlp* h) { return h->yhat; }
 
 vs_status mlp_check_err(vs_mlp* h) {
   unsigned e = 0;

@@ -1,0 +1,81 @@
+"""GPU parity of standardisation, the exact relaxation map and the hybrid (learned relaxation)
+step against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle.mlp import init_params
+from oracle.standardize import fourier_filter, standardize
+from oracle.step import Params, Suspension as OracleSuspension, relax_exact
+from paper_2606_25569_b300 import binding
+from paper_2606_25569_b300.workloads import vesicle_outline
+
+from .gpu_util import csr, offsets, rel_err_per_vesicle, split
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _shapes(M, N, seed, spacing=3.0):
+    rng = np.random.default_rng(seed)
+    xs, ys = [], []
+    for v in range(M):
+        x, y = vesicle_outline(N, 0.65, 1.0, 3e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x + spacing * (v % 4))
+        ys.append(y + spacing * (v // 4))
+    return xs, ys
+
+
+def test_standardize_matches_oracle():
+    xs, ys = _shapes(6, 64, 1)
+    off = offsets(xs)
+    xy = torch.as_tensor(csr(xs, ys), device="cuda")
+    xin = torch.zeros(6, 128, dtype=torch.float32, device="cuda")
+    fr = torch.zeros(6, 6, dtype=torch.float64, device="cuda")
+    binding.standardize(xy, off, xin, fr)
+    got, frames = xin.cpu().numpy(), fr.cpu().numpy()
+    for v in range(6):
+        xo, yo, p = standardize(xs[v], ys[v])
+        ref = np.concatenate([fourier_filter(xo), fourier_filter(yo)])
+        assert np.max(np.abs(got[v] - ref)) <= 1e-6 * np.max(np.abs(ref))
+        assert int(frames[v, 5]) == p.j0
+        assert np.max(np.abs(frames[v, :5] - [p.c[0], p.c[1], p.cos_t, p.sin_t, p.s])) <= 1e-12 * max(1.0, abs(p.s))
+
+
+def test_relax_map_matches_oracle():
+    xs, ys = _shapes(5, 64, 2)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.0, dt=2e-3)
+    xin = torch.as_tensor(csr(xs, ys), device="cuda")
+    out = torch.empty_like(xin)
+    g.relax(xin, out)
+    torch.cuda.synchronize()
+    gx, gy = split(out.cpu().numpy(), [64] * 5)
+    p = Params(kappa=1.0, mu=1.0, dt=2e-3)
+    rx, ry = [], []
+    for x, y in zip(xs, ys):
+        z = relax_exact(x, y, p)
+        rx.append(z[:64])
+        ry.append(z[64:])
+    assert rel_err_per_vesicle(gx, gy, rx, ry) <= 1e-10
+
+
+def test_hybrid_step_matches_oracle():
+    N, M = 64, 4
+    xs, ys = _shapes(M, N, 3)
+    dims = [2 * N, 256, 256, 2 * N]
+    rng = np.random.default_rng(4)
+    params = init_params(dims, rng).astype(np.float32).astype(np.float64)
+    scale = 1e-3
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(1.0, 0.0, 0.0, 0.0))
+    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale), **kw))
+    stream = torch.cuda.current_stream()
+    net = binding.Mlp(dims, max_batch=M, stream=stream)
+    net.set_params(params)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
+    g.set_network(net, scale)
+    for _ in range(3):
+        o.step()
+        g.step()
+        gx, gy = split(g.positions(), [N] * M)
+        err = rel_err_per_vesicle(gx, gy, o.xs, o.ys)
+        # bf16 network output (relative ~1e-3) enters X through scale * output only
+        assert err <= 1e-8, err
