@@ -33,6 +33,8 @@ FUNCTIONS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double]),
     "vs_relax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_training_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double]),
     "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -194,6 +196,9 @@ class Suspension:
 
     def relax(self, xy_in_dev, xy_out_dev):
         self._check(lib().vs_relax(self._h, _ptr(xy_in_dev), _ptr(xy_out_dev)))
+
+    def training_pairs(self, xy_in_dev, xin_dev, yout_dev, out_scale):
+        self._check(lib().vs_training_pairs(self._h, _ptr(xy_in_dev), _ptr(xin_dev), _ptr(yout_dev), float(out_scale)))
 
     def device_ptrs(self):
         a, b = ctypes.c_void_p(), ctypes.c_void_p()

@@ -192,22 +192,34 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
     }
 }
 
-// In-place LU with partial pivoting (first maximum |a| wins) of the n x n matrix at `sub`
-// (units of N^2 doubles), n = dm N. Pivot k swaps rows k and piv[k]. One CTA per vesicle.
-// Pivots of a vesicle live at piv[4 off + pivsub N ...]: L of slot s at pivsub = s, A at 2.
-__global__ void __launch_bounds__(256) k_lu(VesIndex vi, double* scratch, int64_t sub, int dm,
-                                            int* piv, int pivsub, unsigned* err,
-                                            const int* __restrict__ active) {
-  __shared__ double colk[2 * NMAX], rowk[2 * NMAX];
+// Where the per-vesicle LU finds its matrix: the n x n matrix at `sub` (units of N^2 doubles) of the
+// vesicle's scratch with n = dm N + extra, pivots at piv + pbase(v).
+struct LuGeo {
+  VesIndex vi;
+  double* scratch;
+  int64_t sub;
+  int dm, extra;
+  int* piv;
+  int pivsub;      // >= 0: pivots at 4 off + pivsub N;  < 0: at 2 off + 2 v (correction systems)
+  __device__ int n(int v) const { return dm * vi.N[v] + extra; }
+  __device__ double* A(int v) const { return scratch + vi.moff[v] + sub * (int64_t)vi.N[v] * vi.N[v]; }
+  __device__ int* p(int v) const {
+    return pivsub >= 0 ? piv + 4 * vi.off[v] + pivsub * vi.N[v] : piv + 2 * vi.off[v] + 2 * v;
+  }
+};
+
+// In-place LU with partial pivoting (first maximum |a| wins) of an n x n row-major matrix, n <= 2 NMAX + 8.
+// Pivot k swaps rows k and piv[k]. One CTA per vesicle.
+__global__ void __launch_bounds__(256) k_lu(LuGeo geo, unsigned* err, const int* __restrict__ active) {
+  __shared__ double colk[2 * NMAX + 8], rowk[2 * NMAX + 8];
   __shared__ double rv[8];
   __shared__ int ri[8];
   __shared__ int sp;
   const int v = blockIdx.x;
   if (active && !active[v]) return;
-  const int N = vi.N[v];
-  const int n = dm * N;
-  double* A = scratch + vi.moff[v] + sub * (int64_t)N * N;
-  int* p = piv + 4 * vi.off[v] + pivsub * N;
+  const int n = geo.n(v);
+  double* A = geo.A(v);
+  int* p = geo.p(v);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;

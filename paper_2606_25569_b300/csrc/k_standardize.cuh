@@ -149,4 +149,22 @@ __global__ void __launch_bounds__(NMAX) k_destandardize_add(VesIndex vi, const f
   xy[2 * o + N + i] += -f.st * dx + f.ct * dy;
 }
 
+// Training targets: the displacement X_out - X_in of each vesicle expressed in the standard frame of
+// X_in (rotation, unit length, relabelling), divided by out_scale, as an FP32 row [dx^o(N), dy^o(N)].
+__global__ void __launch_bounds__(NMAX) k_to_frame_rows(VesIndex vi, const double* __restrict__ xin,
+                                                        const double* __restrict__ xout,
+                                                        const StdFrame* __restrict__ frame, double inv_scale,
+                                                        float* __restrict__ rows, int64_t ld) {
+  const int v = blockIdx.x;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int k = threadIdx.x;
+  if (k >= N) return;
+  const StdFrame f = frame[v];
+  const int i = (k + f.j0) % N;
+  const double dx = xout[2 * o + i] - xin[2 * o + i], dy = xout[2 * o + N + i] - xin[2 * o + N + i];
+  rows[(int64_t)v * ld + k] = (float)(f.s * (f.ct * dx - f.st * dy) * inv_scale);
+  rows[(int64_t)v * ld + N + k] = (float)(f.s * (f.st * dx + f.ct * dy) * inv_scale);
+}
+
 }  // namespace vs

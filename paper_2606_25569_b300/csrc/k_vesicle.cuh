@@ -190,137 +190,203 @@ __global__ void __launch_bounds__(256) k_tension(VesIndex vi, const double* __re
   if (i < N) sigma[o + i] = -rhs[i];
 }
 
-// Area and length (Green formula / trapezoid of |X_alpha|) and their gradients at z.
-struct AL { double A, L; };
+// Area/length correction (Sec. 4.3) as the exact constrained minimiser of ||X~ - X||^2 subject to
+// A(X~) = A_0, L(X~) = L_0, found by Newton's method on its KKT system
+//   [ I - lam_A H_A - lam_L H_L   -J^T ] [dz  ]     [ z - X - J^T lam ]
+//   [ J                            0   ] [dlam] = - [ c(z)            ]
+// with the discrete A = (2 pi/N) sum 1/2 (x y' - y x'), L = (2 pi/N) sum |X'|, X' = D X, their
+// gradients J = (grad A, grad L) and exact Hessians H_A = (2 pi/N)[[0, D], [D^T, 0]],
+// H_L = (2 pi/N) blockdiag(D, D)^T Q blockdiag(D, D), Q = (I - t t^T)/|X'| per point. Coordinates are
+// taken relative to the mean point. Per vesicle state (6 N + 16 doubles at 6 off + 16 v): X0 (2N),
+// z (2N), rhs (2N + 2), then lam_A, lam_L, mean_x, mean_y, size, converged. The (2N+2)^2 system
+// lives in the vesicle's matrix scratch from MatLayout::B (free at this point of the step).
 
-__device__ AL area_length_grad(const double* d, const double* zx, const double* zy, int N,
-                               double* gAx, double* gAy, double* gLx, double* gLy, double* tmpx,
-                               double* tmpy, double* red) {
-  const int i = threadIdx.x;
-  const bool act = i < N;
-  const double dal = 2.0 * VS_PI / N;
-  double xa = 0.0, ya = 0.0, s = 1.0;
-  if (act) {
-    xa = circ_row(d, zx, N, i);
-    ya = circ_row(d, zy, N, i);
-    s = sqrt(xa * xa + ya * ya);
-  }
-  const double A = block_sum(act ? dal * 0.5 * (zx[i] * ya - zy[i] * xa) : 0.0, red);
-  const double L = block_sum(act ? dal * s : 0.0, red);
-  __syncthreads();
-  if (act) { tmpx[i] = xa / s; tmpy[i] = ya / s; }
-  __syncthreads();
-  if (act) {
-    gAx[i] = dal * ya;
-    gAy[i] = -dal * xa;
-    gLx[i] = -dal * circ_row(d, tmpx, N, i);
-    gLy[i] = -dal * circ_row(d, tmpy, N, i);
-  }
-  __syncthreads();
-  return AL{A, L};
+__device__ __forceinline__ double* corr_state(double* corr, const VesIndex& vi, int v) {
+  return corr + 6 * vi.off[v] + 16 * (int64_t)v;
 }
 
-// Block-wide max of one double (all threads get it).
-__device__ inline double block_max(double v, double* red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double m = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-  return m;
-}
-
-// Area/length correction (Sec. 4.3): when a relative error exceeds tol, replace X by the
-// minimiser of ||X~ - X||^2 subject to A = A_0, L = L_0. The KKT point X~ = X + J(X~)^T lam,
-// c(X~) = 0 is reached by the fixed-point iteration z <- X + J(z)^T lam, lam solving
-// c(X + J(z)^T lam) = 0 by 2x2 Newton steps. Sets dirty[v] when it fires, clears it otherwise.
-__global__ void __launch_bounds__(NMAX) k_correct(VesIndex vi, double* __restrict__ xy,
-                                                  const double* __restrict__ A0, const double* __restrict__ L0,
-                                                  double tol, const double* __restrict__ tab, int* __restrict__ dirty,
-                                                  int* __restrict__ fired, unsigned* err) {
-  __shared__ double d[NMAX], X0x[NMAX], X0y[NMAX], zx[NMAX], zy[NMAX], yx[NMAX], yy[NMAX];
-  __shared__ double jAx[NMAX], jAy[NMAX], jLx[NMAX], jLy[NMAX];
-  __shared__ double hAx[NMAX], hAy[NMAX], hLx[NMAX], hLy[NMAX], t1[NMAX], t2[NMAX], red[NMAX / 32];
+// Trigger test (relative error of A or L above tol) and Newton start z = X, lam = 0.
+__global__ void __launch_bounds__(NMAX) k_corr_init(VesIndex vi, const double* __restrict__ xy,
+                                                    const double* __restrict__ A0, const double* __restrict__ L0,
+                                                    double tol, const double* __restrict__ tab,
+                                                    double* __restrict__ corr, int* __restrict__ active,
+                                                    int* __restrict__ dirty, unsigned* err) {
+  __shared__ double d[NMAX], xs[NMAX], ys[NMAX], red[NMAX / 32];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
   const bool act = i < N;
+  const double px = act ? xy[2 * o + i] : 0.0, py = act ? xy[2 * o + N + i] : 0.0;
+  if (__syncthreads_or(act && !(isfinite(px) && isfinite(py)))) {
+    if (i == 0) { atomicOr(err, ERR_NONFINITE); active[v] = 0; dirty[v] = 0; }
+    return;
+  }
+  const double mx = block_sum(px, red) / N, my = block_sum(py, red) / N;
   if (act) {
     d[i] = tab[vi.toff[v] + i];
-    X0x[i] = xy[2 * o + i];
-    X0y[i] = xy[2 * o + N + i];
-    zx[i] = X0x[i];
-    zy[i] = X0y[i];
+    xs[i] = px - mx;
+    ys[i] = py - my;
   }
-  const int bad = __syncthreads_or(act && !(isfinite(X0x[i]) && isfinite(X0y[i])));
-  if (bad) {
-    if (i == 0) atomicOr(err, ERR_NONFINITE);
-    return;
-  }
-  const double a0 = A0[v], l0 = L0[v];
-  const AL c0 = area_length_grad(d, zx, zy, N, jAx, jAy, jLx, jLy, t1, t2, red);
-  if (!(fabs(c0.A - a0) / fabs(a0) > tol || fabs(c0.L - l0) / fabs(l0) > tol)) {
-    if (i == 0) dirty[v] = 0;
-    return;
-  }
-  const double xmax = block_max(act ? fmax(fabs(X0x[i]), fabs(X0y[i])) : 0.0, red);
-  double la = 0.0, ll = 0.0;
-  bool converged = false;
-  for (int outer = 0; outer < 60 && !converged; ++outer) {
-    // jA, jL hold the constraint gradients at the current iterate z
-    for (int inner = 0; inner < 40; ++inner) {
-      __syncthreads();
-      if (act) {
-        yx[i] = X0x[i] + la * jAx[i] + ll * jLx[i];
-        yy[i] = X0y[i] + la * jAy[i] + ll * jLy[i];
-      }
-      __syncthreads();
-      const AL cy = area_length_grad(d, yx, yy, N, hAx, hAy, hLx, hLy, t1, t2, red);
-      const double FA = cy.A - a0, FL = cy.L - l0;
-      const double J11 = block_sum(act ? hAx[i] * jAx[i] + hAy[i] * jAy[i] : 0.0, red);
-      const double J12 = block_sum(act ? hAx[i] * jLx[i] + hAy[i] * jLy[i] : 0.0, red);
-      const double J21 = block_sum(act ? hLx[i] * jAx[i] + hLy[i] * jAy[i] : 0.0, red);
-      const double J22 = block_sum(act ? hLx[i] * jLx[i] + hLy[i] * jLy[i] : 0.0, red);
-      if (fabs(FA) <= 1e-15 * fabs(a0) && fabs(FL) <= 1e-15 * fabs(l0)) break;
-      const double det = J11 * J22 - J12 * J21;
-      const double nrm = J11 * J11 + J12 * J12 + J21 * J21 + J22 * J22;
-      double dA, dL;
-      if (fabs(det) > 1e-12 * nrm) {
-        dA = (J22 * FA - J12 * FL) / det;
-        dL = (-J21 * FA + J11 * FL) / det;
-      } else {  // rank-one J (a circle): minimum-norm step
-        dA = (J11 * FA + J21 * FL) / nrm;
-        dL = (J12 * FA + J22 * FL) / nrm;
-      }
-      la -= dA;
-      ll -= dL;
-    }
-    __syncthreads();
-    double dz = 0.0;
-    if (act) {
-      const double nx = X0x[i] + la * jAx[i] + ll * jLx[i];
-      const double ny = X0y[i] + la * jAy[i] + ll * jLy[i];
-      dz = fmax(fabs(nx - zx[i]), fabs(ny - zy[i]));
-      yx[i] = nx;
-      yy[i] = ny;
-    }
-    const double step = block_max(dz, red);
-    if (act) { zx[i] = yx[i]; zy[i] = yy[i]; }
-    __syncthreads();
-    converged = step <= 1e-15 * xmax;
-    if (!converged) area_length_grad(d, zx, zy, N, jAx, jAy, jLx, jLy, t1, t2, red);
-  }
-  if (!converged && i == 0) atomicOr(err, ERR_CORRECTION);
+  __syncthreads();
+  double xa = 0.0, ya = 0.0;
   if (act) {
-    xy[2 * o + i] = zx[i];
-    xy[2 * o + N + i] = zy[i];
+    xa = circ_row(d, xs, N, i);
+    ya = circ_row(d, ys, N, i);
+  }
+  const double dal = 2.0 * VS_PI / N;
+  const double A = block_sum(act ? dal * 0.5 * (xs[i] * ya - ys[i] * xa) : 0.0, red);
+  const double L = block_sum(act ? dal * sqrt(xa * xa + ya * ya) : 0.0, red);
+  double size = act ? fmax(fabs(xs[i]), fabs(ys[i])) : 0.0;
+  for (int off = 16; off > 0; off >>= 1) size = fmax(size, __shfl_xor_sync(0xffffffffu, size, off));
+  __syncthreads();
+  if ((i & 31) == 0) red[i >> 5] = size;
+  __syncthreads();
+  size = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) size = fmax(size, red[w]);
+  const bool fire = fabs(A - A0[v]) / fabs(A0[v]) > tol || fabs(L - L0[v]) / fabs(L0[v]) > tol;
+  double* st = corr_state(corr, vi, v);
+  if (fire && act) {
+    st[i] = xs[i];
+    st[N + i] = ys[i];
+    st[2 * N + i] = xs[i];
+    st[3 * N + i] = ys[i];
   }
   if (i == 0) {
-    dirty[v] = 1;
+    active[v] = fire ? 1 : 0;
+    dirty[v] = fire ? 1 : 0;
+    double* sc = st + 6 * N + 2;
+    sc[0] = 0.0; sc[1] = 0.0; sc[2] = mx; sc[3] = my; sc[4] = size; sc[5] = 0.0;
+  }
+}
+
+// Assemble the KKT matrix and right-hand side at the current iterate.
+__global__ void __launch_bounds__(256) k_corr_build(VesIndex vi, const double* __restrict__ tab,
+                                                    const double* __restrict__ A0, const double* __restrict__ L0,
+                                                    double* __restrict__ corr, double* __restrict__ scratch,
+                                                    const int* __restrict__ active) {
+  __shared__ double d[NMAX], zx[NMAX], zy[NMAX], tx[NMAX], ty[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX];
+  __shared__ double gA[2 * NMAX], gL[2 * NMAX], red[8];
+  const int v = blockIdx.x;
+  if (!active[v]) return;
+  const int N = vi.N[v];
+  const int n = 2 * N + 2;
+  const int tid = threadIdx.x;
+  double* st = corr_state(corr, vi, v);
+  const double la = st[6 * N + 2], ll = st[6 * N + 3];
+  for (int i = tid; i < N; i += blockDim.x) {
+    d[i] = tab[vi.toff[v] + i];
+    zx[i] = st[2 * N + i];
+    zy[i] = st[3 * N + i];
+  }
+  __syncthreads();
+  const double dal = 2.0 * VS_PI / N;
+  double pa = 0.0, pl = 0.0;
+  for (int i = tid; i < N; i += blockDim.x) {
+    const double xa = circ_row(d, zx, N, i), ya = circ_row(d, zy, N, i);
+    const double sp = sqrt(xa * xa + ya * ya);
+    tx[i] = xa / sp;
+    ty[i] = ya / sp;
+    qxx[i] = ty[i] * ty[i] / sp;
+    qxy[i] = -tx[i] * ty[i] / sp;
+    qyy[i] = tx[i] * tx[i] / sp;
+    gA[i] = dal * ya;
+    gA[N + i] = -dal * xa;
+    pa += dal * 0.5 * (zx[i] * ya - zy[i] * xa);
+    pl += dal * sp;
+  }
+  const double Acur = block_sum(pa, red), Lcur = block_sum(pl, red);
+  __syncthreads();
+  for (int i = tid; i < N; i += blockDim.x) {
+    gL[i] = -dal * circ_row(d, tx, N, i);
+    gL[N + i] = -dal * circ_row(d, ty, N, i);
+  }
+  __syncthreads();
+  double* K = scratch + vi.moff[v] + MatLayout::B * (int64_t)N * N;
+  for (int e = tid; e < 2 * N * 2 * N; e += blockDim.x) {
+    const int a = e / (2 * N), b = e - a * (2 * N);
+    const int p = a / N, i = a - p * N, q = b / N, j = b - q * N;
+    double hl = 0.0;
+    for (int k = 0; k < N; ++k) {
+      int ki = k - i, kj = k - j;
+      ki += (ki < 0) ? N : 0;
+      kj += (kj < 0) ? N : 0;
+      const double qq = (p == 0) ? ((q == 0) ? qxx[k] : qxy[k]) : ((q == 0) ? qxy[k] : qyy[k]);
+      hl = fma(d[ki] * d[kj], qq, hl);
+    }
+    double ha = 0.0;
+    if (p == 0 && q == 1) { int m = i - j; m += (m < 0) ? N : 0; ha = d[m]; }
+    if (p == 1 && q == 0) { int m = j - i; m += (m < 0) ? N : 0; ha = d[m]; }
+    K[(int64_t)a * n + b] = ((a == b) ? 1.0 : 0.0) - la * dal * ha - ll * dal * hl;
+  }
+  for (int a = tid; a < 2 * N; a += blockDim.x) {
+    K[(int64_t)a * n + 2 * N] = -gA[a];
+    K[(int64_t)a * n + 2 * N + 1] = -gL[a];
+    K[(int64_t)(2 * N) * n + a] = gA[a];
+    K[(int64_t)(2 * N + 1) * n + a] = gL[a];
+    const double z = (a < N) ? zx[a] : zy[a - N];
+    st[4 * N + a] = -(z - st[a] - la * gA[a] - ll * gL[a]);
+  }
+  if (tid == 0) {
+    K[(int64_t)(2 * N) * n + 2 * N] = 0.0;
+    K[(int64_t)(2 * N) * n + 2 * N + 1] = 0.0;
+    K[(int64_t)(2 * N + 1) * n + 2 * N] = 0.0;
+    K[(int64_t)(2 * N + 1) * n + 2 * N + 1] = 0.0;
+    st[6 * N] = -(Acur - A0[v]);
+    st[6 * N + 1] = -(Lcur - L0[v]);
+  }
+}
+
+// Solve the factored KKT system, update (z, lam), retire converged vesicles.
+__global__ void __launch_bounds__(256) k_corr_update(VesIndex vi, const double* __restrict__ scratch,
+                                                     const int* __restrict__ cpiv, double* __restrict__ corr,
+                                                     int* __restrict__ active) {
+  __shared__ double b[2 * NMAX + 8], red[8];
+  const int v = blockIdx.x;
+  if (!active[v]) return;
+  const int N = vi.N[v];
+  const int n = 2 * N + 2;
+  double* st = corr_state(corr, vi, v);
+  for (int a = threadIdx.x; a < n; a += blockDim.x) b[a] = st[4 * N + a];
+  __syncthreads();
+  lu_solve_vec(scratch + vi.moff[v] + MatLayout::B * (int64_t)N * N, cpiv + 2 * vi.off[v] + 2 * v, n, b);
+  double dm = 0.0;
+  for (int a = threadIdx.x; a < 2 * N; a += blockDim.x) {
+    st[2 * N + a] += b[a];
+    dm = fmax(dm, fabs(b[a]));
+  }
+  for (int off = 16; off > 0; off >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    st[6 * N + 2] += b[2 * N];
+    st[6 * N + 3] += b[2 * N + 1];
+    if (m <= 1e-14 * st[6 * N + 6]) {
+      st[6 * N + 7] = 1.0;
+      active[v] = 0;
+    }
+  }
+}
+
+// Write corrected points back (plus the mean) and flag vesicles that did not converge.
+__global__ void __launch_bounds__(NMAX) k_corr_finish(VesIndex vi, const double* __restrict__ corr,
+                                                      const int* __restrict__ dirty, double* __restrict__ xy,
+                                                      int* __restrict__ fired, unsigned* err) {
+  const int v = blockIdx.x;
+  if (!dirty[v]) return;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const double* st = corr + 6 * o + 16 * (int64_t)v;
+  const int i = threadIdx.x;
+  if (i < N) {
+    xy[2 * o + i] = st[2 * N + i] + st[6 * N + 4];
+    xy[2 * o + N + i] = st[3 * N + i] + st[6 * N + 5];
+  }
+  if (i == 0) {
     atomicAdd(fired, 1);
+    if (st[6 * N + 7] == 0.0) atomicOr(err, ERR_CORRECTION);
   }
 }
 

@@ -25,6 +25,8 @@
 
 using namespace vs;
 
+constexpr int CORR_NEWTON_ITERS = 8;  // Newton steps on the KKT system (quadratic convergence)
+
 namespace {
 
 // ---------------------------------------------------------------------------------------------
@@ -222,6 +224,8 @@ struct vs_suspension {
   unsigned* err = nullptr;
   int* has_near = nullptr;
   NearBufs nb{nullptr, nullptr};
+  double* corr = nullptr;          // correction state (6 N + 16 doubles per vesicle)
+  int *cactive = nullptr, *cpiv = nullptr;
   float* xin = nullptr;            // network input rows (M x 2N)
   StdFrame* frames = nullptr;      // standardisation frames (M)
   struct vs_mlp* net = nullptr;    // learned relaxation map (hybrid mode), borrowed
@@ -313,7 +317,7 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
   VS_LAUNCH(h, "k_bgemm<OpT>", k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active));
   VS_LAUNCH(h, "k_bgemm<OpL>", k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active));
-  VS_LAUNCH(h, "k_lu<L>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, h->piv, s, h->err, active));
+  VS_LAUNCH(h, "k_lu<L>", k_lu<<<M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv, s}, h->err, active));
   VS_CK(h, cudaGetLastError(), "operator build");
   return VS_OK;
 }
@@ -361,7 +365,7 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
   VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
   VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
-  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(vi, h->scratch, MatLayout::A, 2, h->piv, 2, h->err, nullptr));
+  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, h->err, nullptr));
   VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo));
   VS_CK(h, cudaGetLastError(), "relaxation");
   return VS_OK;
@@ -403,6 +407,26 @@ vs_status near_field(vs_suspension* h, int s) {
   return VS_OK;
 }
 
+// Area/length correction of every vesicle whose relative error exceeds corr_tol (Sec. 4.3).
+vs_status correction(vs_suspension* h) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  VS_LAUNCH(h, "k_corr_init", k_corr_init<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab,
+                                                                       h->corr, h->cactive, h->dirty, h->err));
+  for (int it = 0; it < CORR_NEWTON_ITERS; ++it) {
+    VS_LAUNCH(h, "k_corr_build", k_corr_build<<<L.M, 256, 0, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
+                                                                          h->scratch, h->cactive));
+    VS_LAUNCH(h, "k_lu<KKT>", k_lu<<<L.M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::B, 2, 2, h->cpiv, -1},
+                                                                h->err, h->cactive));
+    VS_LAUNCH(h, "k_corr_update", k_corr_update<<<L.M, 256, 0, h->stream>>>(vi, h->scratch, h->cpiv, h->corr,
+                                                                            h->cactive));
+  }
+  VS_LAUNCH(h, "k_corr_finish", k_corr_finish<<<L.M, NMAX, 0, h->stream>>>(vi, h->corr, h->dirty, h->xy, h->fired,
+                                                                           h->err));
+  VS_CK(h, cudaGetLastError(), "correction");
+  return VS_OK;
+}
+
 vs_status step_once(vs_suspension* h) {
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
@@ -435,9 +459,8 @@ vs_status step_once(vs_suspension* h) {
   VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u_r, h->B.pg(), h->D.tab, h->scratch, nxt, h->piv,
                                       h->p.kappa_b, h->sigma));
   VS_CK(h, cudaGetLastError(), "tension");
-  // (8) area/length correction; marks the cached operators stale where it fires
-  VS_LAUNCH(h, "k_correct", k_correct<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab, h->dirty, h->fired, h->err));
-  VS_CK(h, cudaGetLastError(), "correction");
+  // (8) area/length correction (Newton on the KKT system); marks the cached operators stale where it fires
+  if ((st = correction(h)) != VS_OK) return st;
   h->cur = nxt;
   h->steps += 1;
   return VS_OK;
@@ -474,6 +497,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
   cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
+  cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
 }
 
 thread_local std::string g_create_msg;
@@ -513,6 +537,9 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->scratch, L.moff[L.M])); VS_A(dalloc(&h->piv, 4 * L.P));
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
+  VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
+  VS_A(dalloc(&h->cactive, L.M));
+  VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
   VS_A(dalloc(&h->xin, 2 * (int64_t)L.nmax * L.M));
   VS_A(dalloc(&h->frames, L.M));
   if (h->p.near_field) {
@@ -673,6 +700,22 @@ vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double ou
 vs_status vs_relax(vs_suspension* h, const double* xy_in, double* xy_out) {
   if (!h || !xy_in || !xy_out || xy_in == xy_out) return VS_ERR_INVALID_ARG;
   return relax_exact(h, xy_in, xy_out, 1 - h->cur);
+}
+
+
+vs_status vs_training_pairs(vs_suspension* h, const double* xy_in, float* xin, float* yout, double out_scale) {
+  if (!h || !xy_in || !xin || !yout || !(out_scale > 0)) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  for (int v = 0; v < L.M; ++v)
+    if (L.N[v] != L.nmax) { h->msg = "training pairs need one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
+  const VesIndex vi = h->D.vi();
+  vs_status st = relax_exact(h, xy_in, h->xy_next, 1 - h->cur);
+  if (st != VS_OK) return st;
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->D.tab, xin, 2 * L.nmax, h->frames));
+  VS_LAUNCH(h, "k_to_frame_rows", k_to_frame_rows<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->xy_next, h->frames,
+                                                                             1.0 / out_scale, yout, 2 * L.nmax));
+  VS_CK(h, cudaGetLastError(), "training pairs");
+  return VS_OK;
 }
 
 const char* vs_last_error(const vs_suspension* h) { return h ? h->msg.c_str() : g_create_msg.c_str(); }

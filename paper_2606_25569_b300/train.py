@@ -1,0 +1,109 @@
+"""Learned relaxation map: data generation on the GPU, training with the library's tensor-core MLP,
+and the shape-error comparison of the hybrid step against the plain step (Sec. 3.2-3.4, App. B).
+
+Data: a plain suspension is stepped with libvesb300; every `every` steps each vesicle's current
+(equal-arclength) shape is taken as an input and the library's exact relaxation map gives the
+target (vs_training_pairs: network input = filtered standardised shape, target = relaxation
+displacement in the standard frame). Training: relative L2 loss with the derivative term and
+AdamW at learning rate 1e-3 (Sec. 3.4.2), all in libvesb300 (vs_mlp_*). This module only
+arranges calls, draws the initial weights and copies data.
+"""
+import time
+
+import numpy as np
+
+from . import binding
+
+
+def he_uniform(dims, rng):
+    """Initial flat parameters: He-uniform weights, zero biases (layout of vs_mlp)."""
+    ws, bs = [], []
+    for a, b in zip(dims[:-1], dims[1:]):
+        lim = np.sqrt(6.0 / a)
+        ws.append(rng.uniform(-lim, lim, size=(b, a)).ravel())
+        bs.append(np.zeros(b))
+    return np.concatenate(ws + bs).astype(np.float32)
+
+
+def relaxation_samples(wl, snapshots, every, stream, near_field=None):
+    """(X, Y): FP32 device tensors (snapshots * M, 2N) of network inputs and raw targets."""
+    import torch
+    nf = wl.near_field if near_field is None else near_field
+    s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=nf, stream=stream)
+    M, N2 = wl.M, 2 * len(wl.xs[0])
+    X = torch.empty(snapshots * M, N2, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    for k in range(snapshots):
+        xy = torch.as_tensor(s.positions(), device="cuda")
+        s.training_pairs(xy, X[k * M:(k + 1) * M], Y[k * M:(k + 1) * M], 1.0)
+        s.sync()
+        if k + 1 < snapshots:
+            s.step(every)
+    s.sync()
+    s.close()
+    return X, Y
+
+
+def relative_errors(net, X, Y, batch):
+    """Per-sample ||Yhat - Y|| / ||Y|| of the network on (X, Y) (device tensors)."""
+    import torch
+    out = torch.empty_like(Y)
+    for a in range(0, X.shape[0], batch):
+        b = min(a + batch, X.shape[0])
+        net.forward(X[a:b], out[a:b], b - a)
+    net.sync()
+    return (torch.linalg.norm(out - Y, dim=1) / torch.linalg.norm(Y, dim=1)).cpu().numpy()
+
+
+def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, beta=0.1, holdout=0.1,
+                     seed=0, stream=None, ncomp=2):
+    """Train on (X, Y); the last `holdout` fraction is held out. Returns a dict with the network,
+    its output scale, the loss history, held-out errors and timings."""
+    import torch
+    n = X.shape[0]
+    nh = int(round(holdout * n))
+    ntr = n - nh
+    scale = float(torch.sqrt(torch.mean(Y[:ntr].double() ** 2)).item())
+    Yn = (Y / scale).contiguous()
+    dims = [X.shape[1]] + list(hidden) + [Y.shape[1]]
+    net = binding.Mlp(dims, max_batch=batch, ncomp=ncomp, beta=beta, stream=stream)
+    net.set_params(he_uniform(dims, np.random.default_rng(seed)))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    hist = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    for ep in range(epochs):
+        perm = torch.randperm(ntr, device="cuda", generator=gen)
+        Xs, Ys = X[perm].contiguous(), Yn[perm].contiguous()
+        for a in range(0, ntr - batch + 1, batch):
+            want = (a == 0)
+            lo = net.train_step(Xs[a:a + batch], Ys[a:a + batch], batch, lr=lr, want_loss=want)
+            steps += 1
+            if want:
+                hist.append(lo)
+    net.sync()
+    t_train = time.perf_counter() - t0
+    err_tr = relative_errors(net, X[:ntr], Yn[:ntr], batch)
+    err_ho = relative_errors(net, X[ntr:], Yn[ntr:], batch) if nh else np.array([])
+    return {"net": net, "scale": scale, "dims": dims, "history": hist, "train_err": err_tr,
+            "holdout_err": err_ho, "train_seconds": t_train, "steps": steps}
+
+
+def centred_shape_error(xy_a, xy_b, counts):
+    """Per-vesicle ||(X_a - c_a) - (X_b - c_b)|| / ||X_b - c_b|| (App. B error on centred shapes),
+    with c the mean of the points, and the centre distance over the vesicle's radius of gyration."""
+    out, cen = [], []
+    o = 0
+    for n in counts:
+        xa, ya = xy_a[2 * o:2 * o + n], xy_a[2 * o + n:2 * o + 2 * n]
+        xb, yb = xy_b[2 * o:2 * o + n], xy_b[2 * o + n:2 * o + 2 * n]
+        ca, cb = np.array([xa.mean(), ya.mean()]), np.array([xb.mean(), yb.mean()])
+        da = np.concatenate([xa - ca[0], ya - ca[1]])
+        db = np.concatenate([xb - cb[0], yb - cb[1]])
+        out.append(np.linalg.norm(da - db) / np.linalg.norm(db))
+        cen.append(np.linalg.norm(ca - cb) / (np.linalg.norm(db) / np.sqrt(n)))
+        o += n
+    return np.array(out), np.array(cen)
