@@ -143,18 +143,25 @@ vs_status vs_profile_read(vs_suspension* s, int32_t idx, char* name, int32_t nam
 /*
  * Learned maps for the hybrid step (params.mode = 1; VesNet, Sec. 3.2 and Algorithm 1).
  * which = 0: the relaxation flow map X_X (Eq. relaxation_disc replaced by a network): the step
- * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the Fourier-filtered
- * standardised shape and adds out_scale * output, mapped back from the standard frame, as
+ * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the standardised shape
+ * with its Fourier modes |k| > filter_kmax removed (the Nyquist mode always is) and adds
+ * out_scale * output, mapped back from the standard frame, as
  * X^{n+1} - X*. The network (borrowed, must outlive its use) needs widths 2N in and out, batch
  * capacity >= M, the suspension's stream, and one N for all vesicles; otherwise
  * VS_ERR_INVALID_ARG. net = NULL removes it; a hybrid step without it fails with VS_ERR_NO_NETWORK.
  */
-vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double out_scale);
+vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double out_scale, int32_t filter_kmax);
 
 /* Exact relaxation step (Eq. relaxation_disc) of the given DEVICE points (CSR blocks) into
  * xy_out, with the suspension's kappa_b, mu and dt -- the map the learned relaxation is trained
  * on. Does not change the suspension's state. Asynchronous. */
 vs_status vs_relax(vs_suspension* s, const double* xy_in, double* xy_out);
+
+/* Training pairs of the relaxation map: for DEVICE points xy_in (CSR blocks, equal N), xin (device
+ * FP32, M x 2N) = the network input of vs_set_network's map and yout (device FP32, M x 2N) =
+ * (relax(xy_in) - xy_in) in each vesicle's standard frame, divided by out_scale. Asynchronous. */
+vs_status vs_training_pairs(vs_suspension* s, const double* xy_in, float* xin, float* yout, double out_scale,
+                            int32_t filter_kmax);
 
 const char* vs_last_error(const vs_suspension* s);
 void vs_destroy(vs_suspension* s);
@@ -193,12 +200,12 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
 /*
  * Standardisation of every vesicle for the networks (Sec. 3.4.1): centroid, principal axis along
  * +y, unit length, cyclic relabelling so that point 0 is the right-most upward crossing of the x
- * axis, Fourier filter keeping modes |k| <= N/4. xy: device CSR blocks. xin: device FP32, row v =
+ * axis, Fourier filter keeping modes |k| <= kmax (< N/2). xy: device CSR blocks. xin: device FP32, row v =
  * [x^o(N_max), y^o(N_max)] at offset 2 N_max v (first 2 N_v entries used). frames: device, 6 doubles
  * per vesicle (c_x, c_y, cos t, sin t, 1/L, first-point label). Synchronous.
  */
-vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, float* xin, double* frames,
-                         void* cuda_stream);
+vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, int32_t kmax, float* xin,
+                         double* frames, void* cuda_stream);
 
 /*
  * Learned part (Sec. 3.2-3.4): a fully connected network (ReLU hidden layers, affine output)

@@ -11,8 +11,8 @@ standardize(X) -> (X^o, params):
 4. reorder: the first point is the right-most of the points j with y_{j-1} < 0 <= y_j (an upward
    crossing of the x axis, i.e. on or just above it, points counter-clockwise) -- reading of
    "the first point lies on or just above the x-axis".
-The networks see the Fourier-filtered standardised shape: modes |k| > N/4 and the Nyquist mode
-zeroed (reading; the paper names no filter). Displacements map back with destandardize_disp.
+The networks see the Fourier-filtered standardised shape: modes |k| > kmax and the Nyquist mode
+zeroed (reading; the paper names no cut-off, the library takes kmax as a parameter). Displacements map back with destandardize_disp.
 
 Pins (tests/test_oracle_standardize.py): invariance of X^o to translation, rotation and scaling of
 the input; J of an ellipse in closed form; the centroid against the polygon centroid; exact
@@ -90,10 +90,11 @@ def to_frame_disp(dx, dy, p):
     return np.roll(p.s * rx, -p.j0), np.roll(p.s * ry, -p.j0)
 
 
-def fourier_filter(v):
-    """Zero the modes |k| > N/4 and the Nyquist mode of real samples v."""
+def fourier_filter(v, kmax=None):
+    """Zero the modes |k| > kmax (default N/4) and the Nyquist mode of real samples v."""
     N = len(v)
+    kmax = N // 4 if kmax is None else min(kmax, N // 2 - 1)
     c = np.fft.fft(v)
     k = np.abs(np.fft.fftfreq(N, d=1.0 / N))
-    c[k > N // 4] = 0.0
+    c[k > kmax] = 0.0
     return np.fft.ifft(c).real

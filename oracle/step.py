@@ -36,7 +36,7 @@ class Params:
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
-        # (dims, flat parameters, output scale): the learned relaxation map of the hybrid step
+        # (dims, flat parameters, output scale, filter kmax): the learned relaxation of the hybrid step
         self.relax_net = relax_net
 
 
@@ -47,11 +47,11 @@ def relax_learned(x, y, net):
     back as the displacement X^{n+1} - X*_r."""
     from .mlp import forward
     from .standardize import destandardize_disp, fourier_filter, standardize
-    dims, params, scale = net
+    dims, params, scale, kmax = net
     N = len(x)
     xr, yr, _ = redistribute(x, y)
     xo, yo, fr = standardize(xr, yr)
-    inp = np.concatenate([fourier_filter(xo), fourier_filter(yo)])[None, :]
+    inp = np.concatenate([fourier_filter(xo, kmax), fourier_filter(yo, kmax)])[None, :]
     out, _ = forward(params, dims, inp, bf16=True)
     dx, dy = destandardize_disp(scale * out[0, :N], scale * out[0, N:], fr)
     return np.concatenate([xr + dx, yr + dy])

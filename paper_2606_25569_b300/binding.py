@@ -31,10 +31,11 @@ FUNCTIONS = {
     "vs_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "vs_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p]),
-    "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double]),
+    "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_int32]),
     "vs_relax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_training_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_double]),
+                                         ctypes.c_double, ctypes.c_int32]),
     "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -58,8 +59,8 @@ FUNCTIONS = {
     "vs_mlp_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "vs_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_mlp_destroy": (None, [ctypes.c_void_p]),
-    "vs_standardize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
-                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_standardize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -190,15 +191,17 @@ class Suspension:
             i += 1
         return out
 
-    def set_network(self, net, out_scale, which=0):
+    def set_network(self, net, out_scale, filter_kmax, which=0):
         self._net = net  # the library borrows it
-        self._check(lib().vs_set_network(self._h, int(which), net._h if net is not None else None, float(out_scale)))
+        self._check(lib().vs_set_network(self._h, int(which), net._h if net is not None else None, float(out_scale),
+                                         int(filter_kmax)))
 
     def relax(self, xy_in_dev, xy_out_dev):
         self._check(lib().vs_relax(self._h, _ptr(xy_in_dev), _ptr(xy_out_dev)))
 
-    def training_pairs(self, xy_in_dev, xin_dev, yout_dev, out_scale):
-        self._check(lib().vs_training_pairs(self._h, _ptr(xy_in_dev), _ptr(xin_dev), _ptr(yout_dev), float(out_scale)))
+    def training_pairs(self, xy_in_dev, xin_dev, yout_dev, out_scale, filter_kmax):
+        self._check(lib().vs_training_pairs(self._h, _ptr(xy_in_dev), _ptr(xin_dev), _ptr(yout_dev), float(out_scale),
+                                            int(filter_kmax)))
 
     def device_ptrs(self):
         a, b = ctypes.c_void_p(), ctypes.c_void_p()
@@ -338,9 +341,10 @@ class Mlp:
             pass
 
 
-def standardize(xy_dev, offsets, xin_dev, frames_dev, stream=None):
+def standardize(xy_dev, offsets, kmax, xin_dev, frames_dev, stream=None):
     """vs_standardize: FP32 network input rows and frames of every vesicle (device tensors)."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
-    st = lib().vs_standardize(_ptr(xy_dev), _ptr(off), len(off) - 1, _ptr(xin_dev), _ptr(frames_dev), _stream(stream))
+    st = lib().vs_standardize(_ptr(xy_dev), _ptr(off), len(off) - 1, int(kmax), _ptr(xin_dev), _ptr(frames_dev),
+                              _stream(stream))
     if st != 0:
         raise VsError(st, "vs_standardize failed")

@@ -4,7 +4,8 @@
 //   centre c = (2/3) int X (X.n) ds / int X.n ds (the area centroid; the printed ratio lacks 2/3),
 //   J = 1/4 int (r.n)(|r|^2 I - r r^T) ds, principal axis = eigenvector of the smallest eigenvalue
 //   (y component >= 0), rotation taking it to +y, scale 1/L, cyclic shift so that point 0 is the
-//   right-most upward crossing of the x axis, then the Fourier filter (modes |k| <= N/4 kept).
+//   right-most upward crossing of the x axis, then the Fourier filter (modes |k| <= kmax kept,
+//   kmax < N/2, so the Nyquist mode is always removed).
 //   Writes the FP32 network input row [x^o(N), y^o(N)] and the frame parameters.
 // k_destandardize_add: X += R^T (out_scale * dX^o) / s, shifted back to the original labels.
 #pragma once
@@ -20,9 +21,9 @@ struct StdFrame {
 
 __global__ void __launch_bounds__(NMAX) k_standardize(VesIndex vi, const double* __restrict__ xy,
                                                       const double* __restrict__ tab, float* __restrict__ xin,
-                                                      int64_t ld_in, StdFrame* __restrict__ frame) {
+                                                      int64_t ld_in, StdFrame* __restrict__ frame, int kmax) {
   __shared__ double d[NMAX], xs[NMAX], ys[NMAX], xr[NMAX], yr[NMAX], red[NMAX / 32];
-  __shared__ double cre[2][NMAX / 4 + 1], cim[2][NMAX / 4 + 1];
+  __shared__ double cre[2][NMAX / 2], cim[2][NMAX / 2];
   __shared__ int sj0;
   const int v = blockIdx.x;
   const int N = vi.N[v];
@@ -97,8 +98,8 @@ __global__ void __launch_bounds__(NMAX) k_standardize(VesIndex vi, const double*
   }
   __syncthreads();
   const int j0 = sj0;
-  // Fourier coefficients k = 0..N/4 of the shifted curve
-  const int nk = N / 4 + 1;
+  // Fourier coefficients k = 0..kmax of the shifted curve (kmax < N/2)
+  const int nk = min(kmax, N / 2 - 1) + 1;
   for (int e = i; e < 2 * nk; e += blockDim.x) {
     const int comp = e / nk, k = e - comp * nk;
     const double* src = comp ? yr : xr;

@@ -230,6 +230,7 @@ struct vs_suspension {
   StdFrame* frames = nullptr;      // standardisation frames (M)
   struct vs_mlp* net = nullptr;    // learned relaxation map (hybrid mode), borrowed
   double net_scale = 1.0;
+  int net_kmax = 0;
   int cur = 0;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -377,7 +378,7 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   const VesIndex vi = h->D.vi();
   if (!h->net) { h->msg = "hybrid mode needs a relaxation network (vs_set_network)"; return VS_ERR_NO_NETWORK; }
   VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, xs, h->u, h->D.tab, xo, h->u_r));
-  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, 2 * L.nmax, h->frames));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, 2 * L.nmax, h->frames, h->net_kmax));
   VS_CK(h, cudaGetLastError(), "standardise");
   vs_status st = mlp_forward(h->net, h->xin, L.M);
   if (st != VS_OK) { h->msg = "network forward failed"; return st; }
@@ -680,7 +681,7 @@ vs_status vs_profile_read(vs_suspension* h, int32_t idx, char* name, int32_t nam
 }
 
 
-vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double out_scale) {
+vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double out_scale, int32_t filter_kmax) {
   if (!h || which != 0) return VS_ERR_INVALID_ARG;
   if (!net) { h->net = nullptr; return VS_OK; }
   const Layout& L = h->L;
@@ -691,9 +692,10 @@ vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double ou
     return VS_ERR_INVALID_ARG;
   }
   if (net->stream != h->stream) { h->msg = "network and suspension must share one stream"; return VS_ERR_INVALID_ARG; }
-  if (!(out_scale > 0)) return VS_ERR_INVALID_ARG;
+  if (!(out_scale > 0) || filter_kmax < 0) return VS_ERR_INVALID_ARG;
   h->net = net;
   h->net_scale = out_scale;
+  h->net_kmax = filter_kmax;
   return VS_OK;
 }
 
@@ -703,15 +705,16 @@ vs_status vs_relax(vs_suspension* h, const double* xy_in, double* xy_out) {
 }
 
 
-vs_status vs_training_pairs(vs_suspension* h, const double* xy_in, float* xin, float* yout, double out_scale) {
-  if (!h || !xy_in || !xin || !yout || !(out_scale > 0)) return VS_ERR_INVALID_ARG;
+vs_status vs_training_pairs(vs_suspension* h, const double* xy_in, float* xin, float* yout, double out_scale,
+                            int32_t kmax) {
+  if (!h || !xy_in || !xin || !yout || !(out_scale > 0) || kmax < 0) return VS_ERR_INVALID_ARG;
   const Layout& L = h->L;
   for (int v = 0; v < L.M; ++v)
     if (L.N[v] != L.nmax) { h->msg = "training pairs need one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
   const VesIndex vi = h->D.vi();
   vs_status st = relax_exact(h, xy_in, h->xy_next, 1 - h->cur);
   if (st != VS_OK) return st;
-  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->D.tab, xin, 2 * L.nmax, h->frames));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->D.tab, xin, 2 * L.nmax, h->frames, kmax));
   VS_LAUNCH(h, "k_to_frame_rows", k_to_frame_rows<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->xy_next, h->frames,
                                                                              1.0 / out_scale, yout, 2 * L.nmax));
   VS_CK(h, cudaGetLastError(), "training pairs");
@@ -807,9 +810,9 @@ void vs_farfield_plan_destroy(vs_farfield_plan* h) {
 
 // ---------------------------------------------------------------------------------------------
 
-vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, float* xin, double* frames,
-                         void* cuda_stream) {
-  if (!xy || !xin || !frames) return VS_ERR_INVALID_ARG;
+vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, int32_t kmax, float* xin,
+                         double* frames, void* cuda_stream) {
+  if (!xy || !xin || !frames || kmax < 0) return VS_ERR_INVALID_ARG;
   Layout L;
   std::string msg;
   if (!build_layout(offsets, M, L, msg)) return VS_ERR_INVALID_ARG;
@@ -819,7 +822,7 @@ vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, fl
   cudaError_t e = upload_layout(L, D, s);
   if (e == cudaSuccess) e = dalloc(&fr, L.M);
   if (e == cudaSuccess) {
-    k_standardize<<<M, NMAX, 0, s>>>(D.vi(), xy, D.tab, xin, 2 * L.nmax, fr);
+    k_standardize<<<M, NMAX, 0, s>>>(D.vi(), xy, D.tab, xin, 2 * L.nmax, fr, kmax);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

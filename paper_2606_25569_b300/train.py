@@ -25,18 +25,21 @@ def he_uniform(dims, rng):
     return np.concatenate(ws + bs).astype(np.float32)
 
 
-def relaxation_samples(wl, snapshots, every, stream, near_field=None):
-    """(X, Y): FP32 device tensors (snapshots * M, 2N) of network inputs and raw targets."""
+def relaxation_samples(wl, snapshots, every, stream, kmax, near_field=None, skip=0):
+    """(X, Y): FP32 device tensors (snapshots * M, 2N) of network inputs (filter cut-off kmax) and
+    raw targets, taken every `every` steps after `skip` initial steps."""
     import torch
     nf = wl.near_field if near_field is None else near_field
     s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
                            flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=nf, stream=stream)
     M, N2 = wl.M, 2 * len(wl.xs[0])
+    if skip:
+        s.step(skip)
     X = torch.empty(snapshots * M, N2, dtype=torch.float32, device="cuda")
     Y = torch.empty_like(X)
     for k in range(snapshots):
         xy = torch.as_tensor(s.positions(), device="cuda")
-        s.training_pairs(xy, X[k * M:(k + 1) * M], Y[k * M:(k + 1) * M], 1.0)
+        s.training_pairs(xy, X[k * M:(k + 1) * M], Y[k * M:(k + 1) * M], 1.0, kmax)
         s.sync()
         if k + 1 < snapshots:
             s.step(every)
@@ -56,10 +59,11 @@ def relative_errors(net, X, Y, batch):
     return (torch.linalg.norm(out - Y, dim=1) / torch.linalg.norm(Y, dim=1)).cpu().numpy()
 
 
-def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, beta=0.1, holdout=0.1,
-                     seed=0, stream=None, ncomp=2):
-    """Train on (X, Y); the last `holdout` fraction is held out. Returns a dict with the network,
-    its output scale, the loss history, held-out errors and timings."""
+def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, lr_min=1e-5, beta=0.1,
+                     holdout=0.1, seed=0, stream=None, ncomp=2):
+    """Train on (X, Y); the last `holdout` fraction is held out. AdamW starts at lr (Sec. 3.4.2:
+    1e-3) and decays on a cosine to lr_min over the epochs. Returns a dict with the network, its
+    output scale, the loss history, held-out errors and timings."""
     import torch
     n = X.shape[0]
     nh = int(round(holdout * n))
@@ -76,11 +80,12 @@ def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e
     t0 = time.perf_counter()
     steps = 0
     for ep in range(epochs):
+        lr_ep = lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * ep / max(1, epochs)))
         perm = torch.randperm(ntr, device="cuda", generator=gen)
         Xs, Ys = X[perm].contiguous(), Yn[perm].contiguous()
         for a in range(0, ntr - batch + 1, batch):
             want = (a == 0)
-            lo = net.train_step(Xs[a:a + batch], Ys[a:a + batch], batch, lr=lr, want_loss=want)
+            lo = net.train_step(Xs[a:a + batch], Ys[a:a + batch], batch, lr=lr_ep, want_loss=want)
             steps += 1
             if want:
                 hist.append(lo)

@@ -31,11 +31,11 @@ def test_standardize_matches_oracle():
     xy = torch.as_tensor(csr(xs, ys), device="cuda")
     xin = torch.zeros(6, 128, dtype=torch.float32, device="cuda")
     fr = torch.zeros(6, 6, dtype=torch.float64, device="cuda")
-    binding.standardize(xy, off, xin, fr)
+    binding.standardize(xy, off, 16, xin, fr)
     got, frames = xin.cpu().numpy(), fr.cpu().numpy()
     for v in range(6):
         xo, yo, p = standardize(xs[v], ys[v])
-        ref = np.concatenate([fourier_filter(xo), fourier_filter(yo)])
+        ref = np.concatenate([fourier_filter(xo, 16), fourier_filter(yo, 16)])
         assert np.max(np.abs(got[v] - ref)) <= 1e-6 * np.max(np.abs(ref))
         assert int(frames[v, 5]) == p.j0
         assert np.max(np.abs(frames[v, :5] - [p.c[0], p.c[1], p.cos_t, p.sin_t, p.s])) <= 1e-12 * max(1.0, abs(p.s))
@@ -66,12 +66,12 @@ def test_hybrid_step_matches_oracle():
     params = init_params(dims, rng).astype(np.float32).astype(np.float64)
     scale = 1e-3
     kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(1.0, 0.0, 0.0, 0.0))
-    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale), **kw))
+    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale, 31), **kw))
     stream = torch.cuda.current_stream()
     net = binding.Mlp(dims, max_batch=M, stream=stream)
     net.set_params(params)
     g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
-    g.set_network(net, scale)
+    g.set_network(net, scale, 31)
     for _ in range(3):
         o.step()
         g.step()
