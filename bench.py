@@ -57,7 +57,8 @@ def config_of(wl, args, extra=None):
     c = {"workload": "dense Poiseuille suspension, %d vesicles x %d points, 30%% area fraction, "
                      "channel width 1, reduced area 0.65, Ca 2, Cn 0.025" % (wl.M, args.N),
          "mode": "plain BIE step (hybrid learned step not built)", "near_field": "mask + five-layer RBF correction (exact layer velocities)",
-         "dt": wl.dt, "farfield": "fp32 compensated", "l2": "working set > L2 (no flush needed)"}
+         "dt": wl.dt, "farfield": "fp32 compensated", "l2": "working set > L2 (no flush needed)",
+         "launch": "each step replayed from a captured CUDA graph"}
     if extra:
         c.update(extra)
     return c
@@ -230,7 +231,7 @@ def run_gpu(args):
     wl = workload(args)
     stream = torch.cuda.current_stream()
     s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
-                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream)
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True)
     for _ in range(max(args.warmup, 3)):
         s.step(1)
     s.sync()

@@ -70,7 +70,8 @@ typedef struct {
   double corr_tol;   /* relative area/length error that triggers the correction (Sec. 4.3: 0.01) */
   int32_t mode;      /* 0: plain boundary-integral step, 1: hybrid (learned relaxation, vs_set_network) */
   int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
-  int32_t use_graph; /* reserved */
+  int32_t use_graph; /* 1: replay each step from a captured CUDA graph (needs a non-NULL stream and
+                        profiling off; otherwise steps are launched one kernel at a time) */
   int32_t pad_;
   uint64_t flags;    /* VS_FLAG_* */
 } vs_params;

@@ -122,14 +122,15 @@ class Suspension:
     """Owner of a vs_suspension handle (vs_create ... vs_destroy)."""
 
     def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
-                 flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0):
+                 flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0,
+                 use_graph=False):
         L = lib()
         self._h = ctypes.c_void_p()
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self.M = len(off) - 1
         self.P = int(off[-1])
-        p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 0, 0,
+        p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0, 0,
                      VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0)
         f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
         st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),

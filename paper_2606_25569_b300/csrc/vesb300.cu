@@ -235,6 +235,8 @@ struct vs_suspension {
   int64_t steps = 0;
   int64_t launches = 0;
   Prof prof;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one captured step per operator-slot parity
+  int64_t graph_launches[2] = {0, 0};
   std::string msg;
 };
 
@@ -478,6 +480,42 @@ vs_status read_err(vs_suspension* h) {
   return VS_OK;
 }
 
+void drop_graphs(vs_suspension* h) {
+  for (int c = 0; c < 2; ++c)
+    if (h->graph[c]) {
+      cudaGraphExecDestroy(h->graph[c]);
+      h->graph[c] = nullptr;
+    }
+}
+
+// One step replayed from a CUDA graph captured on first use (per slot parity). The step's kernels
+// read every per-step decision (dirty operator slots, near lists, correction triggers) from device
+// flags, so the captured sequence is valid for every later step with the same parity.
+vs_status step_graph(vs_suspension* h) {
+  const int c = h->cur;
+  if (!h->graph[c]) {
+    cudaGraph_t g = nullptr;
+    VS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    const int64_t l0 = h->launches, s0 = h->steps;
+    const vs_status st = step_once(h);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->graph_launches[c] = h->launches - l0;
+    h->launches = l0;
+    h->steps = s0;
+    h->cur = c;
+    if (st != VS_OK) { if (g) cudaGraphDestroy(g); return st; }
+    VS_CK(h, e, "graph capture");
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph[c], g, 0);
+    cudaGraphDestroy(g);
+    VS_CK(h, ei, "graph instantiate");
+  }
+  VS_CK(h, cudaGraphLaunch(h->graph[c], h->stream), "graph launch");
+  h->cur = 1 - c;
+  h->steps += 1;
+  h->launches += h->graph_launches[c];
+  return VS_OK;
+}
+
 bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
   if (!p || !f) { msg = "null params or flow"; return false; }
   if (!(p->kappa_b > 0) || !(p->mu > 0) || !(p->dt > 0) || !(p->corr_tol >= 0) || !std::isfinite(p->dt)) {
@@ -583,8 +621,9 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
 
 vs_status vs_step(vs_suspension* h, int32_t nsteps) {
   if (!h || nsteps < 0) return VS_ERR_INVALID_ARG;
+  const bool graphs = h->p.use_graph && h->stream != nullptr && !h->prof.on;
   for (int32_t k = 0; k < nsteps; ++k) {
-    const vs_status st = step_once(h);
+    const vs_status st = graphs ? step_graph(h) : step_once(h);
     if (st != VS_OK) return st;
   }
   return VS_OK;
@@ -683,7 +722,7 @@ vs_status vs_profile_read(vs_suspension* h, int32_t idx, char* name, int32_t nam
 
 vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double out_scale, int32_t filter_kmax) {
   if (!h || which != 0) return VS_ERR_INVALID_ARG;
-  if (!net) { h->net = nullptr; return VS_OK; }
+  if (!net) { drop_graphs(h); h->net = nullptr; return VS_OK; }
   const Layout& L = h->L;
   for (int v = 0; v < L.M; ++v)
     if (L.N[v] != L.nmax) { h->msg = "the learned relaxation needs one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
@@ -693,6 +732,7 @@ vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double ou
   }
   if (net->stream != h->stream) { h->msg = "network and suspension must share one stream"; return VS_ERR_INVALID_ARG; }
   if (!(out_scale > 0) || filter_kmax < 0) return VS_ERR_INVALID_ARG;
+  drop_graphs(h);
   h->net = net;
   h->net_scale = out_scale;
   h->net_kmax = filter_kmax;
@@ -726,6 +766,7 @@ const char* vs_last_error(const vs_suspension* h) { return h ? h->msg.c_str() : 
 void vs_destroy(vs_suspension* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   free_suspension(h);
   delete h;
