@@ -146,8 +146,9 @@ vs_status vs_profile_read(vs_suspension* s, int32_t idx, char* name, int32_t nam
  * which = 0: the relaxation flow map X_X (Eq. relaxation_disc replaced by a network): the step
  * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the standardised shape
  * with its Fourier modes |k| > filter_kmax removed (the Nyquist mode always is) and adds
- * out_scale * output, mapped back from the standard frame, as
- * X^{n+1} - X*. The network (borrowed, must outlive its use) needs widths 2N in and out, batch
+ * out_scale * output, mapped back from the standard frame, to the redistributed X*; the result,
+ * with its modes |k| > filter_kmax removed (the network does not represent them; the exact
+ * relaxation leaves them at their tiny size), is X^{n+1}. The network (borrowed, must outlive its use) needs widths 2N in and out, batch
  * capacity >= M, the suspension's stream, and one N for all vesicles; otherwise
  * VS_ERR_INVALID_ARG. net = NULL removes it; a hybrid step without it fails with VS_ERR_NO_NETWORK.
  */

@@ -43,8 +43,9 @@ class Params:
 def relax_learned(x, y, net):
     """Hybrid relaxation (VesNet's X_X map, Sec. 3.2, 3.4.1): redistribute X* (Sec. 4.2),
     standardise, evaluate the network on the Fourier-filtered standardised shape (bfloat16
-    operands as on the tensor cores, input first rounded to float32), scale its output and map it
-    back as the displacement X^{n+1} - X*_r."""
+    operands as on the tensor cores, input first rounded to float32), scale its output, map it
+    back to the original frame, add it to X*_r and remove the modes |k| > kmax of the result (the
+    network represents only those modes)."""
     from .mlp import forward
     from .standardize import destandardize_disp, fourier_filter, standardize
     dims, params, scale, kmax = net
@@ -54,7 +55,7 @@ def relax_learned(x, y, net):
     inp = np.concatenate([fourier_filter(xo, kmax), fourier_filter(yo, kmax)])[None, :]
     out, _ = forward(params, dims, inp, bf16=True)
     dx, dy = destandardize_disp(scale * out[0, :N], scale * out[0, N:], fr)
-    return np.concatenate([xr + dx, yr + dy])
+    return np.concatenate([fourier_filter(xr + dx, kmax), fourier_filter(yr + dy, kmax)])
 
 
 def relax_exact(x, y, p):

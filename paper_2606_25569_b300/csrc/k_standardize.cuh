@@ -168,4 +168,52 @@ __global__ void __launch_bounds__(NMAX) k_to_frame_rows(VesIndex vi, const doubl
   rows[(int64_t)v * ld + N + k] = (float)(f.s * (f.st * dx + f.ct * dy) * inv_scale);
 }
 
+// Low-pass of each vesicle's points along the curve parameter: modes |k| > kmax (and the Nyquist
+// mode) removed from x and y. The learned relaxation ends with it, so modes the network does not
+// represent are not carried (the exact relaxation leaves them at their tiny size).
+__global__ void __launch_bounds__(NMAX) k_lowpass(VesIndex vi, const double* __restrict__ tab, int kmax,
+                                                  double* __restrict__ xy) {
+  __shared__ double xs[NMAX], ys[NMAX];
+  __shared__ double cre[2][NMAX / 2], cim[2][NMAX / 2];
+  const int v = blockIdx.x;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int i = threadIdx.x;
+  const double* T = tab + vi.toff[v];
+  if (i < N) {
+    xs[i] = xy[2 * o + i];
+    ys[i] = xy[2 * o + N + i];
+  }
+  __syncthreads();
+  const int nk = min(kmax, N / 2 - 1) + 1;
+  for (int e = i; e < 2 * nk; e += blockDim.x) {
+    const int comp = e / nk, k = e - comp * nk;
+    const double* src = comp ? ys : xs;
+    double re = 0.0, im = 0.0;
+    int m = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fma(src[j], T[15 * N + m], re);
+      im = fma(-src[j], T[16 * N + m], im);
+      m += k;
+      if (m >= N) m -= N;
+    }
+    cre[comp][k] = re / N;
+    cim[comp][k] = im / N;
+  }
+  __syncthreads();
+  if (i < N) {
+    double fx = cre[0][0], fy = cre[1][0];
+    int m = 0;
+    for (int k = 1; k < nk; ++k) {
+      m += i;
+      if (m >= N) m -= N;
+      const double c = T[15 * N + m], sn = T[16 * N + m];
+      fx += 2.0 * (cre[0][k] * c - cim[0][k] * sn);
+      fy += 2.0 * (cre[1][k] * c - cim[1][k] * sn);
+    }
+    xy[2 * o + i] = fx;
+    xy[2 * o + N + i] = fy;
+  }
+}
+
 }  // namespace vs

@@ -374,7 +374,8 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
   return VS_OK;
 }
 
-// Learned relaxation (VesNet's X_X map): X*_r = redistribute(X*), X^{n+1} = X*_r + destandardise(net(standardise(X*_r))).
+// Learned relaxation (VesNet's X_X map): X*_r = redistribute(X*),
+// X^{n+1} = lowpass_kmax(X*_r + destandardise(net(standardise(X*_r)))).
 vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   const Layout& L = h->L;
   const VesIndex vi = h->D.vi();
@@ -386,6 +387,7 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   if (st != VS_OK) { h->msg = "network forward failed"; return st; }
   VS_LAUNCH(h, "k_destandardize_add", k_destandardize_add<<<L.M, NMAX, 0, h->stream>>>(vi, mlp_output(h->net), 2 * L.nmax,
                                                                                        h->net_scale, h->frames, xo));
+  VS_LAUNCH(h, "k_lowpass", k_lowpass<<<L.M, NMAX, 0, h->stream>>>(vi, h->D.tab, h->net_kmax, xo));
   VS_CK(h, cudaGetLastError(), "destandardise");
   return VS_OK;
 }
