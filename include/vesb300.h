@@ -62,6 +62,10 @@ typedef struct {
 
 /* flags */
 #define VS_FLAG_FARFIELD_FP64 1ull /* far field in FP64 instead of compensated FP32 */
+/* Per-vesicle solves with FP64 dense operator products and FP64 LU instead of the default mixed
+ * precision (FP32 products and factorisations refined to FP64 accuracy by matrix-free FP64
+ * residuals). Both give the FP64 solution; the default is several times faster on B300. */
+#define VS_FLAG_DIRECT_FP64 2ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */

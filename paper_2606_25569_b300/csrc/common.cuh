@@ -34,6 +34,10 @@ struct MatLayout {
   static constexpr int64_t D4 = 14, B = 15, W = 19, A = 21, TOTAL = 25;
 };
 
+// Fused multiply-add in the operands' own precision (a plain fma() on floats would promote to FP64).
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

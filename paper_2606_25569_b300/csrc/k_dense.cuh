@@ -8,6 +8,7 @@
 //   D4 = (D_s D_s)(D_s D_s)                                               (N x N)
 //   B  = -kappa S blockdiag(D4, D4)                                       (2N x 2N)
 //   W  = P B, then W <- L^{-1} W                                          (N x 2N)
+// (FP32 path: W = L^{-1} (P B) with the explicit FP32 inverse of L, see k_gj_inverse)
 //   A  = I - dt (B - T W) = I - dt (I - T L^{-1} P) B                     (2N x 2N)
 // with D_s = diag(1/|X_alpha|) D_alpha.
 #pragma once
@@ -22,18 +23,34 @@ struct OpCtx {
   const double* tx;
   const double* ty;
   double* scratch;
+  float* scratch32;  // FP32 copies with the same per-vesicle layout (mixed-precision path)
+  const float* tab32;   // FP32 copy of tab
+  const float4* g32;    // FP32 (1/|X_alpha|, x_s, y_s, 0) per point
   __device__ __forceinline__ double* mat(int v, int N, int64_t sub) const {
     return scratch + vi.moff[v] + sub * (int64_t)N * N;
+  }
+  __device__ __forceinline__ float* mat32(int v, int N, int64_t sub) const {
+    return scratch32 + vi.moff[v] + sub * (int64_t)N * N;
   }
   __device__ __forceinline__ double dcirc(int v, int N, int m) const {
     m %= N;
     if (m < 0) m += N;
     return tab[vi.toff[v] + m];
   }
+  // FP32 circulant entry d(m) for m in (-N, N)
+  __device__ __forceinline__ float dcirc32(int v, int N, int m) const { return tab32[vi.toff[v] + (m < 0 ? m + N : m)]; }
 };
+
+// FP32 entry (i, k) of P = [diag(x_s) D_s, diag(y_s) D_s] (N x 2N), all arithmetic in FP32
+__device__ __forceinline__ float p_entry32(const OpCtx& c, int v, int N, int i, int k) {
+  const float4 g = c.g32[c.vi.off[v] + i];
+  const int kk = (k < N) ? k : k - N;
+  return ((k < N) ? g.y : g.z) * g.x * c.dcirc32(v, N, i - kk);
+}
 
 // T = S Ten at slot s.
 struct OpT {
+  using T = double;
   OpCtx c; int s;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = N; k = 2 * N; }
   __device__ double a(int v, int N, int i, int k) const {
@@ -59,6 +76,7 @@ __device__ __forceinline__ double p_entry(const OpCtx& c, int v, int N, int i, i
 
 // L = P T at slot s.
 struct OpL {
+  using T = double;
   OpCtx c; int s;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = 2 * N; }
   __device__ double a(int v, int N, int i, int k) const { return p_entry(c, v, N, i, k); }
@@ -72,6 +90,7 @@ struct OpL {
 
 // D2 = D_s D_s, written to the A region (scratch).
 struct OpD2 {
+  using T = double;
   OpCtx c;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = N; }
   __device__ double a(int v, int N, int i, int k) const {
@@ -87,6 +106,7 @@ struct OpD2 {
 
 // D4 = D2 D2.
 struct OpD4 {
+  using T = double;
   OpCtx c;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = N; }
   __device__ double a(int v, int N, int i, int k) const { return c.mat(v, N, MatLayout::A)[(int64_t)i * N + k]; }
@@ -98,6 +118,7 @@ struct OpD4 {
 
 // B[:, h N + j] = -kappa sum_k S[i][h N + k] D4[k][j] with S from slot s.
 struct OpB {
+  using T = double;
   OpCtx c; int s; int h; double kappa;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = N; k = N; }
   __device__ double a(int v, int N, int i, int k) const {
@@ -111,6 +132,7 @@ struct OpB {
 
 // W = P B (N x 2N).
 struct OpPB {
+  using T = double;
   OpCtx c;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = 2 * N; k = 2 * N; }
   __device__ double a(int v, int N, int i, int k) const { return p_entry(c, v, N, i, k); }
@@ -122,6 +144,7 @@ struct OpPB {
 
 // A = I - dt (B - T W) with T from slot s.
 struct OpA {
+  using T = double;
   OpCtx c; int s; double dt;
   __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = 2 * N; k = N; }
   __device__ double a(int v, int N, int i, int k) const {
@@ -134,14 +157,114 @@ struct OpA {
   }
 };
 
+// ---- FP32 operator products (mixed-precision path): the same products from the FP32 copy of S,
+// used only to build factorisations that precondition FP64 matrix-free refinement.
+struct OpT32 {
+  using T = float;
+  OpCtx c; int s;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = N; k = 2 * N; }
+  __device__ float a(int v, int N, int i, int k) const {
+    return c.mat32(v, N, MatLayout::slot(s) + MatLayout::S)[(int64_t)i * 2 * N + k] *
+           c.g32[c.vi.off[v] + ((k < N) ? k : k - N)].x;
+  }
+  __device__ float b(int v, int N, int k, int j) const {
+    const float4 g = c.g32[c.vi.off[v] + j];
+    return c.dcirc32(v, N, ((k < N) ? k : k - N) - j) * ((k < N) ? g.y : g.z);
+  }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::slot(s) + MatLayout::T)[(int64_t)i * N + j] = acc;
+  }
+};
+struct OpL32 {
+  using T = float;
+  OpCtx c; int s;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = 2 * N; }
+  __device__ float a(int v, int N, int i, int k) const { return p_entry32(c, v, N, i, k); }
+  __device__ float b(int v, int N, int k, int j) const {
+    return c.mat32(v, N, MatLayout::slot(s) + MatLayout::T)[(int64_t)k * N + j];
+  }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::slot(s) + MatLayout::L)[(int64_t)i * N + j] = acc;
+  }
+};
+struct OpD2_32 {
+  using T = float;
+  OpCtx c;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const { return c.dcirc32(v, N, i - k) * c.g32[c.vi.off[v] + i].x; }
+  __device__ float b(int v, int N, int k, int j) const { return c.dcirc32(v, N, k - j) * c.g32[c.vi.off[v] + k].x; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::A)[(int64_t)i * N + j] = acc;
+  }
+};
+struct OpD4_32 {
+  using T = float;
+  OpCtx c;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const { return c.mat32(v, N, MatLayout::A)[(int64_t)i * N + k]; }
+  __device__ float b(int v, int N, int k, int j) const { return c.mat32(v, N, MatLayout::A)[(int64_t)k * N + j]; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::D4)[(int64_t)i * N + j] = acc;
+  }
+};
+struct OpB32 {
+  using T = float;
+  OpCtx c; int s; int h; double kappa;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const {
+    return c.mat32(v, N, MatLayout::slot(s) + MatLayout::S)[(int64_t)i * 2 * N + h * N + k];
+  }
+  __device__ float b(int v, int N, int k, int j) const { return c.mat32(v, N, MatLayout::D4)[(int64_t)k * N + j]; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::B)[(int64_t)i * 2 * N + h * N + j] = (float)(-kappa) * acc;
+  }
+};
+struct OpPB32 {
+  using T = float;
+  OpCtx c;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = 2 * N; k = 2 * N; }
+  __device__ float a(int v, int N, int i, int k) const { return p_entry32(c, v, N, i, k); }
+  __device__ float b(int v, int N, int k, int j) const { return c.mat32(v, N, MatLayout::B)[(int64_t)k * 2 * N + j]; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {  // P B parked in the A block
+    c.mat32(v, N, MatLayout::A)[(int64_t)i * 2 * N + j] = acc;
+  }
+};
+// W = L^{-1} (P B) with the FP32 inverse of L (held in the L block of slot s).
+struct OpW32 {
+  using T = float;
+  OpCtx c; int s;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = 2 * N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const {
+    return c.mat32(v, N, MatLayout::slot(s) + MatLayout::L)[(int64_t)i * N + k];
+  }
+  __device__ float b(int v, int N, int k, int j) const { return c.mat32(v, N, MatLayout::A)[(int64_t)k * 2 * N + j]; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    c.mat32(v, N, MatLayout::W)[(int64_t)i * 2 * N + j] = acc;
+  }
+};
+struct OpA32 {
+  using T = float;
+  OpCtx c; int s; double dt;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = 2 * N; n = 2 * N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const {
+    return c.mat32(v, N, MatLayout::slot(s) + MatLayout::T)[(int64_t)i * N + k];
+  }
+  __device__ float b(int v, int N, int k, int j) const { return c.mat32(v, N, MatLayout::W)[(int64_t)k * 2 * N + j]; }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    const float bij = c.mat32(v, N, MatLayout::B)[(int64_t)i * 2 * N + j];
+    c.mat32(v, N, MatLayout::A)[(int64_t)i * 2 * N + j] = ((i == j) ? 1.f : 0.f) - (float)dt * (bij - acc);
+  }
+};
+
 constexpr int GT = 64;   // output tile
 constexpr int GK = 16;   // k tile
 
 // C = A B per vesicle; grid (ceil(n/64), ceil(m/64), M), 256 threads, 4x4 outputs per thread.
 template <class Op>
 __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ active) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
+  using T = typename Op::T;
+  __shared__ T As[GK][GT + 1];
+  __shared__ T Bs[GK][GT + 1];
   const int v = blockIdx.z;
   if (active && !active[v]) return;
   const int N = op.c.vi.N[v];
@@ -151,27 +274,27 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
   if (r0 >= m || c0 >= n) return;
   const int tid = threadIdx.x;
   const int tr = tid / 16, tc = tid % 16;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int e = tid; e < GK * GT; e += 256) {
       // A is row-major in its k index: let consecutive threads walk k
       const int kk = e % GK, rr = e / GK;
       const int gi = r0 + rr, gk = k0 + kk;
-      As[kk][rr] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : 0.0;
+      As[kk][rr] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
     }
     for (int e = tid; e < GK * GT; e += 256) {
       const int kk = e / GT, cc = e % GT;
       const int gj = c0 + cc, gk = k0 + kk;
-      Bs[kk][cc] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : 0.0;
+      Bs[kk][cc] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = As[kk][tr + 16 * a];
 #pragma unroll
@@ -179,7 +302,7 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma_t(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
@@ -194,54 +317,56 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
 
 // Where the per-vesicle LU finds its matrix: the n x n matrix at `sub` (units of N^2 doubles) of the
 // vesicle's scratch with n = dm N + extra, pivots at piv + pbase(v).
-struct LuGeo {
+template <class E>
+struct LuGeoT {
+  using T = E;
   VesIndex vi;
-  double* scratch;
+  E* scratch;
   int64_t sub;
   int dm, extra;
   int* piv;
   int pivsub;      // >= 0: pivots at 4 off + pivsub N;  < 0: at 2 off + 2 v (correction systems)
   __device__ int n(int v) const { return dm * vi.N[v] + extra; }
-  __device__ double* A(int v) const { return scratch + vi.moff[v] + sub * (int64_t)vi.N[v] * vi.N[v]; }
+  __device__ E* A(int v) const { return scratch + vi.moff[v] + sub * (int64_t)vi.N[v] * vi.N[v]; }
   __device__ int* p(int v) const {
     return pivsub >= 0 ? piv + 4 * vi.off[v] + pivsub * vi.N[v] : piv + 2 * vi.off[v] + 2 * v;
   }
 };
+using LuGeo = LuGeoT<double>;
+using LuGeo32 = LuGeoT<float>;
 
 // In-place LU with partial pivoting (first maximum |a| wins) of an n x n row-major matrix, n <= 2 NMAX + 8.
 // Pivot k swaps rows k and piv[k]. One CTA per vesicle.
-__global__ void __launch_bounds__(256) k_lu(LuGeo geo, unsigned* err, const int* __restrict__ active) {
-  __shared__ double colk[2 * NMAX + 8], rowk[2 * NMAX + 8];
-  __shared__ double rv[8];
+template <class Geo>
+__device__ void lu_factor(typename Geo::T* A, int n, int* p, unsigned* err) {
+  using E = typename Geo::T;
+  __shared__ E colk[2 * NMAX + 8], rowk[2 * NMAX + 8];
+  __shared__ E rv[8];
   __shared__ int ri[8];
   __shared__ int sp;
-  const int v = blockIdx.x;
-  if (active && !active[v]) return;
-  const int n = geo.n(v);
-  double* A = geo.A(v);
-  int* p = geo.p(v);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
+    // pivot search in the matrix's own precision (FP64 compares are slow on this part)
+    E best = E(-1);
     int idx = n;
     for (int r = k + tid; r < n; r += blockDim.x) {
-      const double a = fabs(A[(int64_t)r * n + k]);
+      const E a = fabs(A[(int64_t)r * n + k]);
       if (a > best) { best = a; idx = r; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const E ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
       if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
     }
     if (lane == 0) { rv[wid] = best; ri[wid] = idx; }
     __syncthreads();
     if (tid == 0) {
-      double b = rv[0];
+      E b = rv[0];
       int id = ri[0];
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
         if (rv[w] > b || (rv[w] == b && ri[w] < id)) { b = rv[w]; id = ri[w]; }
-      if (!(b > 0.0)) { atomicOr(err, ERR_PIVOT); id = k; }
+      if (!(b > E(0))) { atomicOr(err, ERR_PIVOT); id = k; }
       sp = id;
       p[k] = id;
     }
@@ -249,33 +374,209 @@ __global__ void __launch_bounds__(256) k_lu(LuGeo geo, unsigned* err, const int*
     const int pr = sp;
     if (pr != k) {
       for (int j = tid; j < n; j += blockDim.x) {
-        const double t = A[(int64_t)k * n + j];
+        const E t = A[(int64_t)k * n + j];
         A[(int64_t)k * n + j] = A[(int64_t)pr * n + j];
         A[(int64_t)pr * n + j] = t;
       }
       __syncthreads();
     }
-    const double piv_v = A[(int64_t)k * n + k];
-    const double inv = (piv_v != 0.0) ? 1.0 / piv_v : 0.0;
+    const E piv_v = A[(int64_t)k * n + k];
+    const E inv = (piv_v != E(0)) ? E(1) / piv_v : E(0);
     for (int j = k + 1 + tid; j < n; j += blockDim.x) rowk[j] = A[(int64_t)k * n + j];
     for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-      const double l = A[(int64_t)i * n + k] * inv;
+      const E l = A[(int64_t)i * n + k] * inv;
       A[(int64_t)i * n + k] = l;
       colk[i] = l;
     }
     __syncthreads();
-    const int rem = n - k - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      A[(int64_t)i * n + j] = fma(-colk[i], rowk[j], A[(int64_t)i * n + j]);
+    const int nw = blockDim.x >> 5;
+    for (int i = k + 1 + wid; i < n; i += nw) {  // rows by warps, columns by lanes
+      const E li = colk[i];
+      E* Ai = A + (int64_t)i * n;
+      for (int j = k + 1 + lane; j < n; j += 32) Ai[j] = fma_t(-li, rowk[j], Ai[j]);
     }
     __syncthreads();
   }
 }
 
+template <class Geo>
+__global__ void __launch_bounds__(256) k_lu(Geo geo, unsigned* err, const int* __restrict__ active) {
+  const int v = blockIdx.x;
+  if (active && !active[v]) return;
+  lu_factor<Geo>(geo.A(v), geo.n(v), geo.p(v), err);
+}
+
+// The same factorisation staged through shared memory (dynamic, n^2 elements): for matrices that
+// fit, the elimination's many passes over the trailing block stay on chip.
+template <class Geo>
+__global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const int* __restrict__ active) {
+  using E = typename Geo::T;
+  extern __shared__ unsigned char lu_raw[];
+  E* As = reinterpret_cast<E*>(lu_raw);
+  const int v = blockIdx.x;
+  if (active && !active[v]) return;
+  const int n = geo.n(v);
+  E* A = geo.A(v);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) As[e] = A[e];
+  __syncthreads();
+  lu_factor<Geo>(As, n, geo.p(v), err);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = As[e];
+}
+
+// In-place FP32 inverse of the n x n matrix at geo (n <= 16 R) by Gauss-Jordan exchange steps with
+// partial pivoting: step k takes as pivot p the row not yet used with the largest |T[p][k]| (first
+// wins) and exchanges equation p with unknown k,
+//   T[p][k] <- 1/t,  T[p][j] <- -T[p][j]/t,  T[i][k] <- T[i][k]/t,  T[i][j] <- T[i][j] - T[i][k] T[p][j]/t
+// (t = T[p][k]). After n steps row i expresses unknown step(i) through the right-hand-side entries
+// pivot(j) of the columns, so inv[step(i)][pivot(j)] = T[i][j]; no rows move. 256 threads form a
+// 16 x 16 grid and thread (tr, tc) keeps T[tr + 16a][tc + 16b] (a, b < R) in registers: a step
+// costs two barriers, and the column of step k sits in register b = k / 16 of every thread.
+template <int R>
+__global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
+  constexpr int NP = 16 * R;
+  __shared__ float colb[2][NP], rowb[2][NP], redv[2][16];
+  __shared__ int redi[2][16], pk[NP], rstep[NP];
+  const int v = blockIdx.x;
+  if (active && !active[v]) return;
+  const int n = geo.n(v);
+  float* A = geo.A(v);
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  float T[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int i = tr + 16 * a, j = tc + 16 * b;
+      T[a][b] = (i < n && j < n) ? A[(int64_t)i * n + j] : 0.f;
+    }
+  for (int e = tid; e < 2 * NP; e += blockDim.x) {
+    (&colb[0][0])[e] = 0.f;
+    (&rowb[0][0])[e] = 0.f;
+  }
+  __syncthreads();
+  unsigned used = 0u;  // bit a: row tr + 16 a has been a pivot
+  bool bad = false;
+#pragma unroll
+  for (int kb = 0; kb < R; ++kb) {
+    for (int kc = 0; kc < 16; ++kc) {
+      const int k = 16 * kb + kc;
+      if (k >= n) break;
+      const int buf = k & 1;  // double-buffered broadcasts: two barriers per step suffice
+      if (tc == kc) {
+        float best = -1.f;
+        int bi = NP;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          const int i = tr + 16 * a;
+          const float val = T[a][kb];
+          if (i < n) {
+            colb[buf][i] = val;
+            // (bi == NP: the first unused row is always a candidate, so a NaN column still yields a row)
+            if (!((used >> a) & 1u) && (fabsf(val) > best || bi == NP)) { best = fabsf(val); bi = i; }
+          }
+        }
+        redv[buf][tr] = best;
+        redi[buf][tr] = bi;
+      }
+      __syncthreads();
+      float best = redv[buf][0];
+      int p = redi[buf][0];
+#pragma unroll
+      for (int t = 1; t < 16; ++t) {
+        const float bv = redv[buf][t];
+        const int bi = redi[buf][t];
+        if (bi < NP && (p == NP || bv > best || (bv == best && bi < p))) { best = bv; p = bi; }
+      }
+      if (p >= n) { p = n - 1; best = 0.f; }  // unreachable (k < n rows are used); keeps indices in range
+      const int pr = p & 15, pa = p >> 4;
+      if (tr == pr) {
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+          if (a == pa) {
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+              const int j = tc + 16 * b;
+              if (j < n) rowb[buf][j] = T[a][b];
+            }
+            used |= 1u << a;
+          }
+      }
+      if (tid == 0) { pk[k] = p; rstep[p] = k; }
+      __syncthreads();
+      float pv = colb[buf][p];
+      if (!(best > 0.f)) { bad = true; pv = 1.f; }
+      const float ip = 1.f / pv;
+      float c[R], u[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) c[a] = colb[buf][tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < R; ++b) u[b] = (b == kb && tc == kc) ? 1.f - ip : rowb[buf][tc + 16 * b] * ip;
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) T[a][b] = fmaf(-c[a], u[b], T[a][b]);
+      if (tr == pr) {
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+          if (a == pa) {
+#pragma unroll
+            for (int b = 0; b < R; ++b) T[a][b] = (b == kb && tc == kc) ? ip : -u[b];
+          }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int i = tr + 16 * a, j = tc + 16 * b;
+      if (i < n && j < n) A[(int64_t)rstep[i] * n + pk[j]] = T[a][b];
+    }
+  if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
+}
+
+// Inverse from a batched LU (pivots applied) for matrices too large for k_gj_inverse: column j of
+// the inverse solves A x = e_j, thread per column, written to the block at `dsub` of the vesicle's
+// scratch (row-major n x n).
+template <class Geo>
+__global__ void __launch_bounds__(256) k_lu_inverse(Geo geo, int64_t dsub, const int* __restrict__ active) {
+  using E = typename Geo::T;
+  const int v = blockIdx.x;
+  if (active && !active[v]) return;
+  const int N = geo.vi.N[v];
+  const int n = geo.n(v);
+  const E* LU = geo.A(v);
+  const int* p = geo.p(v);
+  E* X = geo.scratch + geo.vi.moff[v] + dsub * (int64_t)N * N;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int i = 0; i < n; ++i) X[(int64_t)i * n + j] = (i == j) ? E(1) : E(0);
+    for (int k = 0; k < n; ++k) {
+      const int q = p[k];
+      if (q != k) {
+        const E t = X[(int64_t)k * n + j];
+        X[(int64_t)k * n + j] = X[(int64_t)q * n + j];
+        X[(int64_t)q * n + j] = t;
+      }
+    }
+    for (int i = 1; i < n; ++i) {
+      E s2 = X[(int64_t)i * n + j];
+      for (int k = 0; k < i; ++k) s2 = fma_t(-LU[(int64_t)i * n + k], X[(int64_t)k * n + j], s2);
+      X[(int64_t)i * n + j] = s2;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      E s2 = X[(int64_t)i * n + j];
+      for (int k = i + 1; k < n; ++k) s2 = fma_t(-LU[(int64_t)i * n + k], X[(int64_t)k * n + j], s2);
+      X[(int64_t)i * n + j] = s2 / LU[(int64_t)i * n + i];
+    }
+  }
+}
+
 // Solve LU x = b in place for one vector b in shared memory (length n); warp 0 works, the
 // block synchronises on exit. Row-oriented substitution with warp dot products.
-__device__ void lu_solve_vec(const double* LU, const int* p, int n, double* b) {
+template <class F>
+__device__ void lu_solve_vec(const F* LU, const int* p, int n, double* b) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (lane == 0)
@@ -286,16 +587,16 @@ __device__ void lu_solve_vec(const double* LU, const int* p, int n, double* b) {
     __syncwarp();
     for (int i = 1; i < n; ++i) {
       double s = 0.0;
-      for (int k = lane; k < i; k += 32) s = fma(LU[(int64_t)i * n + k], b[k], s);
+      for (int k = lane; k < i; k += 32) s = fma((double)LU[(int64_t)i * n + k], b[k], s);
       s = warp_sum(s);
       if (lane == 0) b[i] -= s;
       __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {
       double s = 0.0;
-      for (int k = i + 1 + lane; k < n; k += 32) s = fma(LU[(int64_t)i * n + k], b[k], s);
+      for (int k = i + 1 + lane; k < n; k += 32) s = fma((double)LU[(int64_t)i * n + k], b[k], s);
       s = warp_sum(s);
-      if (lane == 0) b[i] = (b[i] - s) / LU[(int64_t)i * n + i];
+      if (lane == 0) b[i] = (b[i] - s) / (double)LU[(int64_t)i * n + i];
       __syncwarp();
     }
   }
@@ -303,7 +604,8 @@ __device__ void lu_solve_vec(const double* LU, const int* p, int n, double* b) {
 }
 
 // W <- L^{-1} W for the N x 2N block W using the LU of L at slot s; thread per column.
-__global__ void __launch_bounds__(256) k_lu_solve_cols(VesIndex vi, double* scratch, int s,
+template <class E>
+__global__ void __launch_bounds__(256) k_lu_solve_cols(VesIndex vi, E* scratch, int s,
                                                        const int* piv, const int* __restrict__ active) {
   const int v = blockIdx.x;
   if (active && !active[v]) return;
@@ -311,25 +613,25 @@ __global__ void __launch_bounds__(256) k_lu_solve_cols(VesIndex vi, double* scra
   const int nc = 2 * N;
   const int col = threadIdx.x;
   if (col >= nc) return;
-  const double* LU = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::L) * (int64_t)N * N;
-  double* W = scratch + vi.moff[v] + MatLayout::W * (int64_t)N * N;
+  const E* LU = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::L) * (int64_t)N * N;
+  E* W = scratch + vi.moff[v] + MatLayout::W * (int64_t)N * N;
   const int* p = piv + 4 * vi.off[v] + s * N;
   for (int k = 0; k < N; ++k) {
     const int q = p[k];
     if (q != k) {
-      const double t = W[(int64_t)k * nc + col];
+      const E t = W[(int64_t)k * nc + col];
       W[(int64_t)k * nc + col] = W[(int64_t)q * nc + col];
       W[(int64_t)q * nc + col] = t;
     }
   }
   for (int i = 1; i < N; ++i) {
-    double s2 = W[(int64_t)i * nc + col];
-    for (int k = 0; k < i; ++k) s2 = fma(-LU[(int64_t)i * N + k], W[(int64_t)k * nc + col], s2);
+    E s2 = W[(int64_t)i * nc + col];
+    for (int k = 0; k < i; ++k) s2 = fma_t(-LU[(int64_t)i * N + k], W[(int64_t)k * nc + col], s2);
     W[(int64_t)i * nc + col] = s2;
   }
   for (int i = N - 1; i >= 0; --i) {
-    double s2 = W[(int64_t)i * nc + col];
-    for (int k = i + 1; k < N; ++k) s2 = fma(-LU[(int64_t)i * N + k], W[(int64_t)k * nc + col], s2);
+    E s2 = W[(int64_t)i * nc + col];
+    for (int k = i + 1; k < N; ++k) s2 = fma_t(-LU[(int64_t)i * N + k], W[(int64_t)k * nc + col], s2);
     W[(int64_t)i * nc + col] = s2 / LU[(int64_t)i * N + i];
   }
 }

@@ -34,6 +34,7 @@ struct GeomOut {
   double* by;
   double* area;    // [M]
   double* length;  // [M]
+  float4* g32;     // FP32 (1/|X_alpha|, x_s, y_s, 0) for the FP32 operator products (may be null)
 };
 
 // Force/source outputs (only written when `f` is non-null). With f_in non-null the density is
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     g.ty[o + i] = ty;
     g.bx[o + i] = bx;
     g.by[o + i] = by;
+    if (g.g32) g.g32[o + i] = make_float4((float)(1.0 / sa), (float)tx, (float)ty, 0.f);
   }
   if (i == 0) {
     g.area[v] = area;

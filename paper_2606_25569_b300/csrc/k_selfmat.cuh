@@ -6,54 +6,92 @@
 //   rr_ij = r r^T / |r|^2 (i != j),  rr_ii = X_s X_s^T
 // i.e. the Kress product rule for the log singularity of -log|r| and the trapezoid rule for the
 // smooth remainder, with the standard 2D Stokeslet (1/4 pi mu)(-log|r| I + r r^T/|r|^2).
-// Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y].
+// Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y]. With scratch32 set,
+// an FP32 copy is written at the same place of the FP32 scratch.
 #pragma once
 #include "common.cuh"
 
 namespace vs {
+
+// The kernel of S is symmetric in (i, j) apart from the column factor sa_j, so each CTA evaluates
+// one 16 x 16 tile (bi <= bj) of the symmetric part (the FP64 logarithm dominates the cost) and
+// writes the tile and its mirror image (bj, bi). Grid: (nt (nt + 1) / 2, M), nt = ceil(N / 16).
+constexpr int SM_TILE = 16;
+
+__device__ __forceinline__ void self_store(double* S, float* S32, int n2, int N, int i, int j, double c, double lp,
+                                           double dal, double axx, double axy, double ayy) {
+  const double sxx = c * (lp + dal * axx), sxy = c * dal * axy, syy = c * (lp + dal * ayy);
+  S[(int64_t)i * n2 + j] = sxx;
+  S[(int64_t)i * n2 + N + j] = sxy;
+  S[(int64_t)(N + i) * n2 + j] = sxy;
+  S[(int64_t)(N + i) * n2 + N + j] = syy;
+  if (S32) {  // FP32 copy for the mixed-precision factorisations
+    S32[(int64_t)i * n2 + j] = (float)sxx;
+    S32[(int64_t)i * n2 + N + j] = (float)sxy;
+    S32[(int64_t)(N + i) * n2 + j] = (float)sxy;
+    S32[(int64_t)(N + i) * n2 + N + j] = (float)syy;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* __restrict__ xy,
                                                      const double* __restrict__ sa,
                                                      const double* __restrict__ tx,
                                                      const double* __restrict__ ty,
                                                      const double* __restrict__ tab, double mu,
-                                                     double* __restrict__ scratch, int slot,
-                                                     const int* __restrict__ active) {
+                                                     double* __restrict__ scratch, float* __restrict__ scratch32,
+                                                     int slot, const int* __restrict__ active) {
   const int v = blockIdx.y;
   if (active && !active[v]) return;
   const int N = vi.N[v];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N * N) return;
-  const int i = p / N, j = p - (p / N) * N;
+  const int nt = (N + SM_TILE - 1) / SM_TILE;
+  int t = blockIdx.x, bi = 0;
+  if (t >= nt * (nt + 1) / 2) return;
+  while (t >= nt - bi) { t -= nt - bi; ++bi; }
+  const int bj = bi + t;
+  __shared__ double kl[SM_TILE][SM_TILE + 1], kxx[SM_TILE][SM_TILE + 1], kxy[SM_TILE][SM_TILE + 1],
+      kyy[SM_TILE][SM_TILE + 1];
+  const int li = threadIdx.x / SM_TILE, lj = threadIdx.x % SM_TILE;
   const int64_t o = vi.off[v];
   const double* T = tab + vi.toff[v];
-  const int m = (i - j < 0) ? i - j + N : i - j;
-  const double R = T[N + m];
   const double dal = 2.0 * VS_PI / N;
-  double lp, axx, axy, ayy;
-  if (i != j) {
-    const double rx = xy[2 * o + i] - xy[2 * o + j];
-    const double ry = xy[2 * o + N + i] - xy[2 * o + N + j];
-    const double r2 = rx * rx + ry * ry;
-    lp = -0.5 * R - 0.5 * dal * log(r2 / T[2 * N + m]);
-    const double ir2 = 1.0 / r2;
-    axx = rx * rx * ir2;
-    axy = rx * ry * ir2;
-    ayy = ry * ry * ir2;
-  } else {
-    lp = -0.5 * R - dal * log(sa[o + i]);
-    const double a = tx[o + i], b = ty[o + i];
-    axx = a * a;
-    axy = a * b;
-    ayy = b * b;
-  }
-  const double c = sa[o + j] / (4.0 * VS_PI * mu);
+  const double c0 = 1.0 / (4.0 * VS_PI * mu);
   double* S = scratch + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N;
+  float* S32 = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N : nullptr;
   const int n2 = 2 * N;
-  S[(int64_t)i * n2 + j] = c * (lp + dal * axx);
-  S[(int64_t)i * n2 + N + j] = c * dal * axy;
-  S[(int64_t)(N + i) * n2 + j] = c * dal * axy;
-  S[(int64_t)(N + i) * n2 + N + j] = c * (lp + dal * ayy);
+  int i = bi * SM_TILE + li, j = bj * SM_TILE + lj;
+  if (i < N && j < N) {
+    const int m = (i - j < 0) ? i - j + N : i - j;
+    const double R = T[N + m];
+    double lp, axx, axy, ayy;
+    if (i != j) {
+      const double rx = xy[2 * o + i] - xy[2 * o + j];
+      const double ry = xy[2 * o + N + i] - xy[2 * o + N + j];
+      const double r2 = rx * rx + ry * ry;
+      lp = -0.5 * R - 0.5 * dal * log(r2 / T[2 * N + m]);
+      const double ir2 = 1.0 / r2;
+      axx = rx * rx * ir2;
+      axy = rx * ry * ir2;
+      ayy = ry * ry * ir2;
+    } else {
+      lp = -0.5 * R - dal * log(sa[o + i]);
+      const double a = tx[o + i], b = ty[o + i];
+      axx = a * a;
+      axy = a * b;
+      ayy = b * b;
+    }
+    kl[li][lj] = lp;
+    kxx[li][lj] = axx;
+    kxy[li][lj] = axy;
+    kyy[li][lj] = ayy;
+    self_store(S, S32, n2, N, i, j, sa[o + j] * c0, lp, dal, axx, axy, ayy);
+  }
+  if (bi == bj) return;
+  __syncthreads();
+  // mirror tile: entry (i, j) = (bj*16 + li, bi*16 + lj) has the symmetric part of (j, i)
+  i = bj * SM_TILE + li;
+  j = bi * SM_TILE + lj;
+  if (i < N && j < N)
+    self_store(S, S32, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
 }
 
 }  // namespace vs

@@ -17,6 +17,7 @@
 #include "k_farfield.cuh"
 #include "k_geometry.cuh"
 #include "k_mlp.cuh"
+#include "k_mp.cuh"
 #include "k_near.cuh"
 #include "k_selfmat.cuh"
 #include "k_standardize.cuh"
@@ -108,10 +109,11 @@ struct DevLayout {
   int32_t* owner = nullptr;
   int32_t* chunk = nullptr;
   double* tab = nullptr;
+  float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
   VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
-    cudaFree(owner); cudaFree(chunk); cudaFree(tab);
+    cudaFree(owner); cudaFree(chunk); cudaFree(tab); cudaFree(tab32);
     *this = DevLayout{};
   }
 };
@@ -133,6 +135,9 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   VS_TRY(upload(D.owner, L.owner.data(), L.P, s));
   VS_TRY(upload(D.chunk, L.chunk.data(), L.chunk.size(), s));
   VS_TRY(upload(D.tab, L.tab.data(), L.tab.size(), s));
+  std::vector<float> t32(L.tab.begin(), L.tab.end());
+  VS_TRY(dalloc(&D.tab32, t32.size()));
+  VS_TRY(upload(D.tab32, t32.data(), t32.size(), s));
 #undef VS_TRY
   return cudaStreamSynchronize(s);
 }
@@ -149,6 +154,7 @@ struct SourceBufs {
   int* near_v = nullptr;
   double *sa = nullptr, *tx = nullptr, *ty = nullptr, *bx = nullptr, *by = nullptr;
   double *area = nullptr, *length = nullptr;
+  float4* g32 = nullptr;
   cudaError_t alloc(int64_t P, int M) {
     cudaError_t e;
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -157,17 +163,17 @@ struct SourceBufs {
     VS_TRY(dalloc(&near_cnt, P)); VS_TRY(dalloc(&near_v, P * MAX_NEAR));
     VS_TRY(dalloc(&sa, P)); VS_TRY(dalloc(&tx, P)); VS_TRY(dalloc(&ty, P));
     VS_TRY(dalloc(&bx, P)); VS_TRY(dalloc(&by, P));
-    VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M));
+    VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M)); VS_TRY(dalloc(&g32, P));
 #undef VS_TRY
     return cudaSuccess;
   }
   void release() {
     cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
-    cudaFree(by); cudaFree(area); cudaFree(length);
+    cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32);
     *this = SourceBufs{};
   }
-  GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length}; }
+  GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32}; }
   PointGeom pg() const { return PointGeom{sa, tx, ty}; }
 };
 
@@ -220,6 +226,8 @@ struct vs_suspension {
   cudaStream_t stream = nullptr;
   double *xy = nullptr, *xy_star = nullptr, *xy_next = nullptr, *sigma = nullptr;
   double *u = nullptr, *u_r = nullptr, *A0 = nullptr, *L0 = nullptr, *scratch = nullptr;
+  float* scratch32 = nullptr;      // FP32 operator copies / factorisations (mixed-precision path)
+  int* piv32 = nullptr;
   int *piv = nullptr, *dirty = nullptr, *fired = nullptr;
   unsigned* err = nullptr;
   int* has_near = nullptr;
@@ -306,21 +314,66 @@ void prof_collect(vs_suspension* h) {
     prof_end((h), pk_);                     \
   } while (0)
 
+constexpr size_t LU_SMEM_MAX = 200 * 1024;  // dynamic shared memory granted to k_lu_smem
+
+// Batched LU: staged through shared memory when the largest matrix fits, else in global memory.
+template <class Geo>
+void launch_lu(vs_suspension* h, const char* name, const Geo& geo, int nmax_dim, const int* active) {
+  const size_t bytes = (size_t)nmax_dim * nmax_dim * sizeof(typename Geo::T);
+  if (bytes <= LU_SMEM_MAX) {
+    VS_LAUNCH(h, name, k_lu_smem<Geo><<<h->L.M, 256, bytes, h->stream>>>(geo, h->err, active));
+  } else {
+    VS_LAUNCH(h, name, k_lu<Geo><<<h->L.M, 256, 0, h->stream>>>(geo, h->err, active));
+  }
+}
+
+// In-place FP32 inverses by Gauss-Jordan in registers (k_gj_inverse) for matrices up to 128 x 128;
+// false when nmax_dim is larger (nothing launched).
+bool launch_gj32(vs_suspension* h, const char* name, const LuGeo32& geo, int nmax_dim, const int* active) {
+  const int M = h->L.M;
+  if (nmax_dim <= 32) {
+    VS_LAUNCH(h, name, k_gj_inverse<2><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+  } else if (nmax_dim <= 64) {
+    VS_LAUNCH(h, name, k_gj_inverse<4><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+  } else if (nmax_dim <= 128) {
+    VS_LAUNCH(h, name, k_gj_inverse<8><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// k_self_matrix: one CTA per 16 x 16 tile of the upper triangle of the largest vesicle
+inline dim3 self_grid(int nmax, int M) {
+  const int nt = (nmax + SM_TILE - 1) / SM_TILE;
+  return dim3(nt * (nt + 1) / 2, M);
+}
+
 inline dim3 gemm_grid(int m, int n, int M) { return dim3((n + GT - 1) / GT, (m + GT - 1) / GT, M); }
 
 FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
+
+// Mixed precision (default): FP32 operator products and factorisations refined in FP64.
+inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
 
 // S, T, L at slot s for the geometry currently in the SourceBufs, then LU of L.
 vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* active) {
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
   const VesIndex vi = h->D.vi();
-  VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                     h->p.mu, h->scratch, s, active));
-  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
-  VS_LAUNCH(h, "k_bgemm<OpT>", k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active));
-  VS_LAUNCH(h, "k_bgemm<OpL>", k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active));
-  VS_LAUNCH(h, "k_lu<L>", k_lu<<<M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv, s}, h->err, active));
+  VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                                     h->p.mu, h->scratch, mixed(h) ? h->scratch32 : nullptr, s, active));
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_bgemm<OpT32>", k_bgemm<OpT32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT32{c, s}, active));
+    VS_LAUNCH(h, "k_bgemm<OpL32>", k_bgemm<OpL32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL32{c, s}, active));
+    static_assert(NMAX <= 128, "the FP32 inverse of L is formed in registers");
+    launch_gj32(h, "k_gj_inverse<L>", LuGeo32{vi, h->scratch32, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv32, s}, n, active);
+  } else {
+    VS_LAUNCH(h, "k_bgemm<OpT>", k_bgemm<OpT><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT{c, s}, active));
+    VS_LAUNCH(h, "k_bgemm<OpL>", k_bgemm<OpL><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL{c, s}, active));
+    launch_lu(h, "k_lu<L>", LuGeo{vi, h->scratch, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv, s}, n, active);
+  }
   VS_CK(h, cudaGetLastError(), "operator build");
   return VS_OK;
 }
@@ -360,17 +413,54 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
   vs_status st;
   if ((st = geometry(h, xs, false)) != VS_OK) return st;
   if ((st = build_operators(h, xs, s, nullptr)) != VS_OK) return st;
-  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch};
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_bgemm<OpD2_32>", k_bgemm<OpD2_32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2_32{c}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpD4_32>", k_bgemm<OpD4_32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4_32{c}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpB32>", k_bgemm<OpB32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB32{c, s, 0, h->p.kappa_b}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpB32>", k_bgemm<OpB32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB32{c, s, 1, h->p.kappa_b}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpPB32>", k_bgemm<OpPB32><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB32{c}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpW32>", k_bgemm<OpW32><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpW32{c, s}, nullptr));
+    VS_LAUNCH(h, "k_bgemm<OpA32>", k_bgemm<OpA32><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA32{c, s, h->p.dt}, nullptr));
+    const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
+    int64_t ainv = MatLayout::A;
+    if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, nullptr)) {
+      // too large for registers: LU, then the inverse by substitution into the (now free) B block
+      launch_lu(h, "k_lu32<A>", ga, 2 * n, nullptr);
+      VS_LAUNCH(h, "k_lu_inverse32<A>", k_lu_inverse<LuGeo32><<<M, 256, 0, h->stream>>>(ga, MatLayout::B, nullptr));
+      ainv = MatLayout::B;
+    }
+    VS_LAUNCH(h, "k_relax_mp", k_relax_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch,
+                                                                   h->scratch32, s, ainv, h->p.kappa_b, h->p.dt, xo, h->err));
+    VS_CK(h, cudaGetLastError(), "relaxation");
+    return VS_OK;
+  }
   VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 0, h->p.kappa_b}, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 1, h->p.kappa_b}, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
-  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
+  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<double><<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
-  VS_LAUNCH(h, "k_lu<A>", k_lu<<<M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, h->err, nullptr));
+  launch_lu(h, "k_lu<A>", LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, 2 * n, nullptr);
   VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo));
   VS_CK(h, cudaGetLastError(), "relaxation");
+  return VS_OK;
+}
+
+// sigma at the points whose operators sit in slot s (geometry in the SourceBufs), velocity u.
+vs_status tension(vs_suspension* h, const double* u, int s) {
+  const VesIndex vi = h->D.vi();
+  const int M = h->L.M;
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_tension_mp", k_tension_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty,
+                                                                       h->D.tab, h->scratch, h->scratch32, s,
+                                                                       h->p.kappa_b, h->sigma, h->err));
+  } else {
+    VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
+                                                                 h->piv, h->p.kappa_b, h->sigma));
+  }
+  VS_CK(h, cudaGetLastError(), "tension");
   return VS_OK;
 }
 
@@ -421,8 +511,7 @@ vs_status correction(vs_suspension* h) {
   for (int it = 0; it < CORR_NEWTON_ITERS; ++it) {
     VS_LAUNCH(h, "k_corr_build", k_corr_build<<<L.M, 256, 0, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
                                                                           h->scratch, h->cactive));
-    VS_LAUNCH(h, "k_lu<KKT>", k_lu<<<L.M, 256, 0, h->stream>>>(LuGeo{vi, h->scratch, MatLayout::B, 2, 2, h->cpiv, -1},
-                                                                h->err, h->cactive));
+    launch_lu(h, "k_lu<KKT>", LuGeo{vi, h->scratch, MatLayout::B, 2, 2, h->cpiv, -1}, 2 * L.nmax + 2, h->cactive);
     VS_LAUNCH(h, "k_corr_update", k_corr_update<<<L.M, 256, 0, h->stream>>>(vi, h->scratch, h->cpiv, h->corr,
                                                                             h->cactive));
   }
@@ -446,8 +535,14 @@ vs_status step_once(vs_suspension* h) {
   if ((st = far_field(h)) != VS_OK) return st;
   if (h->p.near_field && L.M > 1 && (st = near_field(h, cur)) != VS_OK) return st;
   // (4) advection
-  VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
-                                     h->xy_star));
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_advect_mp", k_advect_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                                     h->scratch, h->scratch32, cur, h->p.dt,
+                                                                     h->xy_star, h->err));
+  } else {
+    VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
+                                                               h->xy_star));
+  }
   VS_CK(h, cudaGetLastError(), "advection");
   // (5) relaxation at X*: exact (plain) or the learned map (hybrid)
   if (h->p.mode == 1) {
@@ -461,9 +556,7 @@ vs_status step_once(vs_suspension* h) {
   // (7) tension at the redistributed X^{n+1}; operators cached in slot nxt for the next step
   if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
   if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
-  VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u_r, h->B.pg(), h->D.tab, h->scratch, nxt, h->piv,
-                                      h->p.kappa_b, h->sigma));
-  VS_CK(h, cudaGetLastError(), "tension");
+  if ((st = tension(h, h->u_r, nxt)) != VS_OK) return st;
   // (8) area/length correction (Newton on the KKT system); marks the cached operators stale where it fires
   if ((st = correction(h)) != VS_OK) return st;
   h->cur = nxt;
@@ -478,6 +571,7 @@ vs_status read_err(vs_suspension* h) {
   if (e & ERR_NONFINITE) { h->msg = "non-finite vesicle state"; return VS_ERR_UNSTABLE; }
   if (e & ERR_PIVOT) { h->msg = "singular per-vesicle system (zero pivot)"; return VS_ERR_UNSTABLE; }
   if (e & ERR_CORRECTION) { h->msg = "area/length correction did not converge"; return VS_ERR_NOT_CONVERGED; }
+  if (e & ERR_REFINE) { h->msg = "mixed-precision refinement did not converge"; return VS_ERR_NOT_CONVERGED; }
   if (e & ERR_NEAR_OVERFLOW) { h->msg = "more near vesicles per target than recorded"; return VS_ERR_UNSTABLE; }
   return VS_OK;
 }
@@ -536,6 +630,7 @@ void free_suspension(vs_suspension* h) {
   h->B.release();
   cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
+  cudaFree(h->scratch32); cudaFree(h->piv32);
   cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
@@ -576,8 +671,11 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->sigma, L.P)); VS_A(dalloc(&h->u, 2 * L.P)); VS_A(dalloc(&h->u_r, 2 * L.P));
   VS_A(dalloc(&h->A0, L.M)); VS_A(dalloc(&h->L0, L.M));
   VS_A(dalloc(&h->scratch, L.moff[L.M])); VS_A(dalloc(&h->piv, 4 * L.P));
+  VS_A(dalloc(&h->scratch32, L.moff[L.M])); VS_A(dalloc(&h->piv32, 4 * L.P));
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
+  VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
+  VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
@@ -609,8 +707,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(cudaMemcpyAsync(h->A0, h->B.area, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   VS_A(cudaMemcpyAsync(h->L0, h->B.length, L.M * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
-  VS_LAUNCH(h, "k_tension", k_tension<<<L.M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, h->u, h->B.pg(), h->D.tab, h->scratch, 0, h->piv,
-                                        h->p.kappa_b, h->sigma));
+  if (tension(h, h->u, 0) != VS_OK) return fail(VS_ERR_CUDA);
   VS_A(cudaGetLastError());
   h->cur = 0;
   VS_A(cudaStreamSynchronize(h->stream));
@@ -905,8 +1002,8 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
     FlowDev none{0, 0.0, 0.0};
     k_geometry<<<M, NMAX, 0, s>>>(D.vi(), xy, nullptr, D.tab, 1.0, mu, none, B.geom(), ForceOut{}, nullptr);
     const int n = L.nmax;
-    k_self_matrix<<<dim3((n * n + 255) / 256, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, 0,
-                                                               nullptr);
+    k_self_matrix<<<self_grid(n, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, nullptr,
+                                                               0, nullptr);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }

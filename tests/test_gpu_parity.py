@@ -103,11 +103,11 @@ def test_farfield_fp32_relative_l2():
     assert err <= 1e-5, err
 
 
-def _oracle_and_gpu(xs, ys, kappa, mu, dt, flow_kind, flow_p, corr_tol, fp64=True):
+def _oracle_and_gpu(xs, ys, kappa, mu, dt, flow_kind, flow_p, corr_tol, fp64=True, direct=False):
     o = OracleSuspension(xs, ys, Params(kappa=kappa, mu=mu, dt=dt, flow_kind=flow_kind, flow_p=flow_p,
                                         corr_tol=corr_tol))
     g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=kappa, mu=mu, dt=dt, corr_tol=corr_tol,
-                           flow_kind=flow_kind, flow_p=flow_p, farfield_fp64=fp64)
+                           flow_kind=flow_kind, flow_p=flow_p, farfield_fp64=fp64, direct_fp64=direct)
     return o, g
 
 
@@ -131,18 +131,21 @@ def test_create_matches_oracle_init():
     assert abs(A0[0] - o.A0[0]) <= 1e-13 * o.A0[0] and abs(L0[0] - o.L0[0]) <= 1e-13 * o.L0[0]
 
 
-def test_single_vesicle_steps_match_oracle():
+@pytest.mark.parametrize("direct", [False, True])
+def test_single_vesicle_steps_match_oracle(direct):
+    # default: FP32 factorisations refined to FP64 accuracy; direct: FP64 products and LU
     wl = single_shear()
-    o, g = _oracle_and_gpu(wl.xs, wl.ys, 1.0, 1.0, 1e-4, 1, (1.0, 0, 0, 0), 0.01)
+    o, g = _oracle_and_gpu(wl.xs, wl.ys, 1.0, 1.0, 1e-4, 1, (1.0, 0, 0, 0), 0.01, direct=direct)
     for k in range(5):
         o.step()
         g.step()
         _compare(o, g)
 
 
-def test_uneven_suspension_fp64_farfield_matches_oracle():
+@pytest.mark.parametrize("direct", [False, True])
+def test_uneven_suspension_fp64_farfield_matches_oracle(direct):
     xs, ys = _mixed([32, 64, 32, 16], 5, spacing=2.6)
-    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 1e-3, 2, (5.0, 8.0, 0, 0), 0.01)
+    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 1e-3, 2, (5.0, 8.0, 0, 0), 0.01, direct=direct)
     for k in range(3):
         o.step()
         g.step()
