@@ -56,6 +56,18 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
+__device__ inline double block_max(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = red[0];
+  for (int w = 1; w < nw; ++w) t = fmax(t, red[w]);
+  return t;
+}
+
 // out_i = sum_j c[(i - j) mod N] v_j : a circulant matrix-vector product (thread i).
 __device__ __forceinline__ double circ_row(const double* c, const double* v, int N, int i) {
   double acc = 0.0;

@@ -429,26 +429,31 @@ __global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const i
 // wins) and exchanges equation p with unknown k,
 //   T[p][k] <- 1/t,  T[p][j] <- -T[p][j]/t,  T[i][k] <- T[i][k]/t,  T[i][j] <- T[i][j] - T[i][k] T[p][j]/t
 // (t = T[p][k]). After n steps row i expresses unknown step(i) through the right-hand-side entries
-// pivot(j) of the columns, so inv[step(i)][pivot(j)] = T[i][j]; no rows move. 256 threads form a
-// 16 x 16 grid and thread (tr, tc) keeps T[tr + 16a][tc + 16b] (a, b < R) in registers: a step
-// costs two barriers, and the column of step k sits in register b = k / 16 of every thread.
+// pivot(j) of the columns, so inv[step(i)][pivot(j)] = T[i][j]; no rows move.
+// 256 threads form a 16 x 16 grid, thread (tr, tc) = (tid % 16, tid / 16) keeping
+// T[tr + 16a][tc + 16b] (a, b < R) in registers as pairs over b for the paired FP32 update. The
+// column of step k sits in register b = k / 16 of the half-warp tc = k % 16, which also finds the
+// pivot by shuffles; column k and row p are broadcast through shared memory laid out per owner
+// ([tr][a] and [tc][b]) so that each thread reads its R values as 128-bit words. Two barriers a step.
 template <int R>
 __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
-  constexpr int NP = 16 * R;
-  __shared__ float colb[2][NP], rowb[2][NP], redv[2][16];
-  __shared__ int redi[2][16], pk[NP], rstep[NP];
+  static_assert(R % 2 == 0 && R >= 2 && R <= 8, "R even, at most 8");
+  constexpr int NP = 16 * R, H = R / 2;
+  __shared__ __align__(16) float colb[2][NP], rowb[2][NP];  // colb[tr * R + a], rowb[tc * R + b]
+  __shared__ int psel[2], pk[NP], rstep[NP];
   const int v = blockIdx.x;
   if (active && !active[v]) return;
   const int n = geo.n(v);
   float* A = geo.A(v);
-  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
-  float T[R][R];
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  float2 T[R][H];
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < R; ++b) {
-      const int i = tr + 16 * a, j = tc + 16 * b;
-      T[a][b] = (i < n && j < n) ? A[(int64_t)i * n + j] : 0.f;
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 32 * h, j1 = j0 + 16;
+      T[a][h].x = (i < n && j0 < n) ? A[(int64_t)i * n + j0] : 0.f;
+      T[a][h].y = (i < n && j1 < n) ? A[(int64_t)i * n + j1] : 0.f;
     }
   for (int e = tid; e < 2 * NP; e += blockDim.x) {
     (&colb[0][0])[e] = 0.f;
@@ -457,71 +462,93 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
   __syncthreads();
   unsigned used = 0u;  // bit a: row tr + 16 a has been a pivot
   bool bad = false;
+  const unsigned half = (tc & 1) ? 0xffff0000u : 0x0000ffffu;
 #pragma unroll
   for (int kb = 0; kb < R; ++kb) {
     for (int kc = 0; kc < 16; ++kc) {
       const int k = 16 * kb + kc;
       if (k >= n) break;
       const int buf = k & 1;  // double-buffered broadcasts: two barriers per step suffice
-      if (tc == kc) {
+      if (tc == kc) {         // the half-warp holding column k: publish it and find the pivot
         float best = -1.f;
         int bi = NP;
+        float cv[R];
 #pragma unroll
         for (int a = 0; a < R; ++a) {
           const int i = tr + 16 * a;
-          const float val = T[a][kb];
-          if (i < n) {
-            colb[buf][i] = val;
-            // (bi == NP: the first unused row is always a candidate, so a NaN column still yields a row)
-            if (!((used >> a) & 1u) && (fabsf(val) > best || bi == NP)) { best = fabsf(val); bi = i; }
-          }
+          cv[a] = (kb & 1) ? T[a][kb >> 1].y : T[a][kb >> 1].x;
+          // the first unused row is always a candidate, so a NaN column still yields a row
+          if (i < n && !((used >> a) & 1u) && (fabsf(cv[a]) > best || bi == NP)) { best = fabsf(cv[a]); bi = i; }
         }
-        redv[buf][tr] = best;
-        redi[buf][tr] = bi;
+        if constexpr (R >= 4) {
+#pragma unroll
+          for (int a = 0; a < R; a += 4)
+            *reinterpret_cast<float4*>(&colb[buf][tr * R + a]) = make_float4(cv[a], cv[a + 1], cv[a + 2], cv[a + 3]);
+        } else {
+          *reinterpret_cast<float2*>(&colb[buf][tr * R]) = make_float2(cv[0], cv[1]);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(half, best, o);
+          const int oi = __shfl_xor_sync(half, bi, o);
+          if (oi < NP && (bi == NP || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+        }
+        if (tr == 0) psel[buf] = (bi < n && best > 0.f) ? bi : -1 - (bi < n ? bi : n - 1);
       }
       __syncthreads();
-      float best = redv[buf][0];
-      int p = redi[buf][0];
-#pragma unroll
-      for (int t = 1; t < 16; ++t) {
-        const float bv = redv[buf][t];
-        const int bi = redi[buf][t];
-        if (bi < NP && (p == NP || bv > best || (bv == best && bi < p))) { best = bv; p = bi; }
-      }
-      if (p >= n) { p = n - 1; best = 0.f; }  // unreachable (k < n rows are used); keeps indices in range
+      int p = psel[buf];
+      if (p < 0) { bad = true; p = -1 - p; }  // zero or NaN pivot column
       const int pr = p & 15, pa = p >> 4;
-      if (tr == pr) {
+      if (tr == pr) {  // owners of row p publish it
 #pragma unroll
         for (int a = 0; a < R; ++a)
           if (a == pa) {
+            if constexpr (H == 1) {
+              *reinterpret_cast<float2*>(&rowb[buf][tc * R]) = T[a][0];
+            } else {
 #pragma unroll
-            for (int b = 0; b < R; ++b) {
-              const int j = tc + 16 * b;
-              if (j < n) rowb[buf][j] = T[a][b];
+              for (int h = 0; h < H; h += 2)
+                *reinterpret_cast<float4*>(&rowb[buf][tc * R + 2 * h]) =
+                    make_float4(T[a][h].x, T[a][h].y, T[a][h + 1].x, T[a][h + 1].y);
             }
             used |= 1u << a;
           }
       }
       if (tid == 0) { pk[k] = p; rstep[p] = k; }
       __syncthreads();
-      float pv = colb[buf][p];
-      if (!(best > 0.f)) { bad = true; pv = 1.f; }
+      float pv = colb[buf][pr * R + pa];
+      if (bad || !(pv != 0.f)) { bad = true; pv = 1.f; }
       const float ip = 1.f / pv;
-      float c[R], u[R];
+      float c[R];
+      float2 u[H];
+      if constexpr (R >= 4) {
 #pragma unroll
-      for (int a = 0; a < R; ++a) c[a] = colb[buf][tr + 16 * a];
+        for (int a = 0; a < R; a += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(&colb[buf][tr * R + a]);
+          c[a] = w.x; c[a + 1] = w.y; c[a + 2] = w.z; c[a + 3] = w.w;
+        }
+      } else {
+        const float2 w = *reinterpret_cast<const float2*>(&colb[buf][tr * R]);
+        c[0] = w.x; c[1] = w.y;
+      }
 #pragma unroll
-      for (int b = 0; b < R; ++b) u[b] = (b == kb && tc == kc) ? 1.f - ip : rowb[buf][tc + 16 * b] * ip;
+      for (int h = 0; h < H; ++h) u[h] = __fmul2_rn(*reinterpret_cast<const float2*>(&rowb[buf][tc * R + 2 * h]), make_float2(ip, ip));
+      if (tc == kc) {  // column k itself: T[i][k] <- T[i][k] / t
+        if (kb & 1) u[kb >> 1].y = 1.f - ip; else u[kb >> 1].x = 1.f - ip;
+      }
 #pragma unroll
       for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < R; ++b) T[a][b] = fmaf(-c[a], u[b], T[a][b]);
-      if (tr == pr) {
+        for (int h = 0; h < H; ++h) T[a][h] = __ffma2_rn(make_float2(-c[a], -c[a]), u[h], T[a][h]);
+      if (tr == pr) {  // row p: T[p][j] <- -T[p][j] / t, T[p][k] <- 1 / t
 #pragma unroll
         for (int a = 0; a < R; ++a)
           if (a == pa) {
 #pragma unroll
-            for (int b = 0; b < R; ++b) T[a][b] = (b == kb && tc == kc) ? ip : -u[b];
+            for (int h = 0; h < H; ++h) T[a][h] = make_float2(-u[h].x, -u[h].y);
+            if (tc == kc) {
+              if (kb & 1) T[a][kb >> 1].y = ip; else T[a][kb >> 1].x = ip;
+            }
           }
       }
     }
@@ -530,9 +557,10 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < R; ++b) {
-      const int i = tr + 16 * a, j = tc + 16 * b;
-      if (i < n && j < n) A[(int64_t)rstep[i] * n + pk[j]] = T[a][b];
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 32 * h, j1 = j0 + 16;
+      if (i < n && j0 < n) A[(int64_t)rstep[i] * n + pk[j0]] = T[a][h].x;
+      if (i < n && j1 < n) A[(int64_t)rstep[i] * n + pk[j1]] = T[a][h].y;
     }
   if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
 }

@@ -4,7 +4,8 @@
 //           sum_j [ -log|r| g_j + (r . g_j) r / |r|^2 ],  r = x_i - X_vj,
 // g_j = f_j |X_alpha|_j (2 pi / N_v) / (4 pi mu) (trapezoid rule with the 2D Stokeslet).
 // x_i is near v when min_j |r|^2 <= h_v^2, h_v = L_v / N_v; its pair is then skipped and the
-// source vesicle recorded in the target's near list (ascending v, at most MAX_NEAR).
+// source vesicle recorded in the target's near list (ascending v, at most MAX_NEAR). The minimum is
+// only tracked for targets inside a conservative reach circle of v (a bound from its radius).
 //
 // FP32 path: each source carries its offset from its vesicle's centre c_v; per (target, source
 // vesicle) the centre difference is formed once from float hi/lo splits, so |r| keeps relative
@@ -39,6 +40,27 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float p) {
   s = t;
 }
 
+// Sum over the sources j0..j1-1 (shared memory) of one vesicle for the target at (qx, qy) in the
+// vesicle's frame; with MIN the smallest |r|^2 is tracked too.
+template <bool MIN>
+__device__ __forceinline__ void ff_sum(const float4* sh, int j0, int j1, float qx, float qy, float& ax, float& ay,
+                                       float& lx, float& ly, float& mn) {
+#pragma unroll 4
+  for (int j = j0; j < j1; ++j) {
+    const float4 s = sh[j];
+    const float rx = qx - s.x, ry = qy - s.y;
+    const float r2 = fmaf(rx, rx, ry * ry);
+    if (MIN) mn = fminf(mn, r2);
+    const float lg = fast_lg2(r2);
+    const float inv = fast_rcp(r2);
+    lx = fmaf(lg, s.z, lx);
+    ly = fmaf(lg, s.w, ly);
+    const float q = fmaf(rx, s.z, ry * s.w) * inv;
+    ax = fmaf(q, rx, ax);
+    ay = fmaf(q, ry, ay);
+  }
+}
+
 struct FarFieldArgs {
   int64_t P;                 // total points (targets = sources)
   int M;
@@ -55,7 +77,7 @@ struct FarFieldArgs {
 
 __global__ void __launch_bounds__(FF_THREADS) k_farfield_f32(FarFieldArgs a, const float4* __restrict__ src,
                                                              const float4* __restrict__ centre32,
-                                                             const float* __restrict__ h2) {
+                                                             const float2* __restrict__ h2) {
   __shared__ float4 sh[FF_CHUNK];
   const int64_t t = (int64_t)blockIdx.x * FF_THREADS + threadIdx.x;
   const bool valid = t < a.P;
@@ -78,22 +100,15 @@ __global__ void __launch_bounds__(FF_THREADS) k_farfield_f32(FarFieldArgs a, con
       const float qx = ((tc.x - sc.x) + (tc.z - sc.z)) + ts.x;
       const float qy = ((tc.y - sc.y) + (tc.w - sc.w)) + ts.y;
       const int j0 = (int)(a.voff[sv] - p0), j1 = (int)(a.voff[sv + 1] - p0);
+      const float2 nr = h2[sv];
+      // the minimum distance is only needed when the target lies within reach of the vesicle
+      const bool test = a.near_mask && fmaf(qx, qx, qy * qy) <= nr.y;
       float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
-#pragma unroll 4
-      for (int j = j0; j < j1; ++j) {
-        const float4 s = sh[j];
-        const float rx = qx - s.x, ry = qy - s.y;
-        const float r2 = fmaf(rx, rx, ry * ry);
-        mn = fminf(mn, r2);
-        const float lg = fast_lg2(r2);
-        const float inv = fast_rcp(r2);
-        lx = fmaf(lg, s.z, lx);
-        ly = fmaf(lg, s.w, ly);
-        const float q = fmaf(rx, s.z, ry * s.w) * inv;
-        ax = fmaf(q, rx, ax);
-        ay = fmaf(q, ry, ay);
-      }
-      if (a.near_mask && mn <= h2[sv]) {
+      if (test)
+        ff_sum<true>(sh, j0, j1, qx, qy, ax, ay, lx, ly, mn);
+      else
+        ff_sum<false>(sh, j0, j1, qx, qy, ax, ay, lx, ly, mn);
+      if (test && mn <= nr.x) {
         if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
         else atomicOr(a.err, ERR_NEAR_OVERFLOW);
         ++ncnt;

@@ -45,7 +45,8 @@ struct ForceOut {
   float4* src;         // (x - c_v, y - c_v, g_x, g_y), g = f |X_alpha| (2 pi/N) / (4 pi mu)
   double2* centre;     // c_v (mean of the points) [M]
   float4* centre32;    // (hi_x, hi_y, lo_x, lo_y) float split of c_v [M]
-  float* h2;           // (L_v/N_v)^2 [M]
+  float2* h2;          // ((L_v/N_v)^2, reach^2) [M]: reach = (max_j |X_vj - c_v| + L_v/N_v)(1 + 1e-3), a
+                       // bound beyond which no point of v is within L_v/N_v
   double* g64;         // FP64 copy of g, CSR blocks (for the FP64 far-field variant)
 };
 
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     }
   }
   const double cx = cxs / N, cy = cys / N;
+  const double rho2 = block_max(act ? (xs[i] - cx) * (xs[i] - cx) + (ys[i] - cy) * (ys[i] - cy) : 0.0, red);
   if (act) {
     fo.f[2 * o + i] = fx;
     fo.f[2 * o + N + i] = fy;
@@ -135,7 +137,8 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     const float hx = (float)cx, hy = (float)cy;
     fo.centre32[v] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
     const double h = length / N;
-    fo.h2[v] = (float)(h * h);
+    const double reach = (sqrt(rho2) + h) * (1.0 + 1e-3);
+    fo.h2[v] = make_float2((float)(h * h), (float)(reach * reach));
   }
 }
 

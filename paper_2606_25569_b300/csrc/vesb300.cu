@@ -149,7 +149,7 @@ struct SourceBufs {
   float4* src = nullptr;
   double2* centre = nullptr;
   float4* centre32 = nullptr;
-  float* h2 = nullptr;
+  float2* h2 = nullptr;
   int* near_cnt = nullptr;
   int* near_v = nullptr;
   double *sa = nullptr, *tx = nullptr, *ty = nullptr, *bx = nullptr, *by = nullptr;
@@ -1321,7 +1321,7 @@ constexpr int64_t SF_SRC = SF_G64 + sf_align(16 * SF_MAX_P);
 constexpr int64_t SF_CENTRE = SF_SRC + sf_align(16 * SF_MAX_P);
 constexpr int64_t SF_CENTRE32 = SF_CENTRE + sf_align(16 * SF_MAX_M);
 constexpr int64_t SF_H2 = SF_CENTRE32 + sf_align(16 * SF_MAX_M);
-constexpr int64_t SF_BYTES = SF_H2 + sf_align(4 * SF_MAX_M);
+constexpr int64_t SF_BYTES = SF_H2 + sf_align(8 * SF_MAX_M);
 
 __device__ __align__(256) static unsigned char g_ff_scratch[SF_BYTES];
 
@@ -1410,7 +1410,7 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
   double* al = (double*)(base + SF_AREA);
   const GeomOut g{geo, geo + SF_MAX_P, geo + 2 * SF_MAX_P, geo + 3 * SF_MAX_P, geo + 4 * SF_MAX_P, al, al + SF_MAX_M};
   const ForceOut fo{(double*)(base + SF_F), u, (float4*)(base + SF_SRC), (double2*)(base + SF_CENTRE),
-                    (float4*)(base + SF_CENTRE32), (float*)(base + SF_H2), (double*)(base + SF_G64)};
+                    (float4*)(base + SF_CENTRE32), (float2*)(base + SF_H2), (double*)(base + SF_G64)};
   const FlowDev none{0, 0.0, 0.0};
   k_geometry<<<M, NMAX, 0, st>>>(vi, xy, nullptr, (const double*)(base + SF_TABLE), 1.0, mu, none, g, fo, f);
   if (M >= 2) {
