@@ -23,15 +23,17 @@ enum : unsigned {
 struct VesIndex {
   const int32_t* N;     // points of vesicle v (even, 8..NMAX)
   const int64_t* off;   // first point of v in the point arrays
-  const int64_t* moff;  // first double of v's matrix scratch (25 N^2 doubles)
+  const int64_t* moff;  // first element of v's matrix scratch (MatLayout::TOTAL N^2 elements)
   const int64_t* toff;  // first double of the tables for v's N
 };
 
 // Matrix scratch layout of one vesicle, in units of N^2 doubles from moff.
+// Two operator slots of S (2N x 2N), T (2N x N), L (N x N) and SL (2N x 2N: in the FP32 scratch the low
+// part S - S_hi of the FP64 S; unused in the FP64 scratch), then D4, B, W, A.
 struct MatLayout {
-  static __host__ __device__ inline int64_t slot(int s) { return s ? 7 : 0; }  // S 4, T 2, L 1
-  static constexpr int64_t S = 0, T = 4, L = 6;
-  static constexpr int64_t D4 = 14, B = 15, W = 19, A = 21, TOTAL = 25;
+  static __host__ __device__ inline int64_t slot(int s) { return s ? 11 : 0; }
+  static constexpr int64_t S = 0, T = 4, L = 6, SL = 7;
+  static constexpr int64_t D4 = 22, B = 23, W = 27, A = 29, TOTAL = 33;
 };
 
 // Fused multiply-add in the operands' own precision (a plain fma() on floats would promote to FP64).

@@ -1,20 +1,23 @@
-// Mixed-precision per-vesicle solves: FP32 factorisations precondition FP64 iterative refinement
-// whose residuals apply the FP64 operators without forming them (Eqs. advection_disc,
-// relaxation_disc, tension_disc). One CTA per vesicle.
+// Mixed-precision per-vesicle solves: explicit FP32 inverses precondition iterative refinement whose
+// residuals apply the operators of Eqs. advection_disc, relaxation_disc and tension_disc without
+// forming them, in double-float arithmetic (FP64 runs at 1/64 of the FP32 rate on this part). One CTA
+// per vesicle.
 //
-// FP64 operator actions (vectors in shared memory):
+// Operator actions (vectors in shared memory, double-float):
 //   D_s u = diag(1/|X_alpha|) D_alpha u          (circulant, Sec. 2.2.1)
 //   Ten s = [D_s(s x_s); D_s(s y_s)],  T s = S Ten s,  P v = x_s D_s v_x + y_s D_s v_y,  L s = P T s
 //   B x = -kappa S [D_s^4 x_x; D_s^4 x_y]
+// with S = S_hi + S_lo, the FP64 self matrix split into two FP32 matrices by k_self_matrix.
 // Solves:
 //   L s = g        s <- s + Li32 (g - L s)
 //   relaxation, coupled in (x, sigma):  x - dt (B x + T sigma) = X*,  P (B x + T sigma) = 0;
 //     with v = S(-kappa D^4 x + Ten sigma): r1 = X* - x + dt v, r2 = -P v,
 //     y = Li32 r2, dx = Ai32 (r1 + dt T32 y), dsigma = y - W32 dx   (W32 = Li32 P B32,
 //     A32 = I - dt (B32 - T32 W32)): the exact block elimination of the FP32 system.
-// Li32 and Ai32 are explicit FP32 inverses (k_gj_inverse), so every correction is a few FP32
-// mat-vecs that all warps share. Each refinement stops at the rounding floor of its iterate
-// (mp_done; at most MP_MAXIT steps); an update above 1e-11 of the iterate at the end sets ERR_REFINE.
+// Li32 and Ai32 are explicit FP32 inverses (k_gj_inverse), so every correction is a few FP32 mat-vecs
+// that all warps share. Iterates are kept in FP64. Each refinement stops at the rounding floor of the
+// residual arithmetic (mp_done; at most MP_MAXIT steps); an update above MP_FAIL of the iterate at the
+// end sets ERR_REFINE.
 #pragma once
 #include "common.cuh"
 #include "k_dense.cuh"
@@ -23,7 +26,78 @@ namespace vs {
 
 constexpr int MP_MAXIT = 10;
 constexpr int MP_THREADS = 128;  // small CTAs: many vesicles per SM hide the global-memory latency
+constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10;
 enum : unsigned { ERR_REFINE = 32u };
+
+// ---- double-float arithmetic: a value is the unevaluated sum x + y of two floats with |y| <= ulp(x)/2
+// (about 48 significant bits). Error-free transformations: TwoSum (Knuth), Fast2Sum (Dekker), the exact
+// product error by FMA; dot products follow the compensated scheme Dot2 of Ogita, Rump and Oishi (2005),
+// extended by the cross terms of double-float operands and folded into a double-float total every
+// DF_CHUNK terms. The _rn intrinsics keep the compiler from contracting the transformations into FMAs.
+constexpr int DF_CHUNK = 8;
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+
+// Compensated accumulator: s the running FP32 sum, c the sum of its rounding errors and of the
+// low-order product terms.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float t = __fadd_rn(s, p), z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)), e));
+    s = t;
+  }
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    const float2 t = two_sum(s, s2);
+    s = t.x;
+    c = __fadd_rn(c, __fadd_rn(c2, t.y));
+  }
+  __device__ __forceinline__ float2 value() const { return two_sum(s, c); }
+};
+
+// out_i = sum_j d[(i - j) mod N] v_j in double-float (d and v in shared memory); the compensated
+// partial sums are folded into a double-float total every DF_CHUNK terms (the last chunk may be short)
+__device__ __forceinline__ float2 circ_df(const float2* d, const float2* v, int N, int i) {
+  float2 tot = make_float2(0.f, 0.f);
+  int m = i;
+  for (int j0 = 0; j0 < N; j0 += DF_CHUNK) {
+    Dot2 a;
+    const int j1 = min(j0 + DF_CHUNK, N);
+    for (int j = j0; j < j1; ++j) {
+      a.add(d[m], v[j]);
+      m = (m == 0) ? N - 1 : m - 1;
+    }
+    tot = df_add(tot, a.value());
+  }
+  return tot;
+}
 
 __device__ inline double block_max_abs(double v, double* red) {
   v = fabs(v);
@@ -38,27 +112,46 @@ __device__ inline double block_max_abs(double v, double* red) {
 }
 
 struct MpShared {
-  double d[NMAX], sa[NMAX], tx[NMAX], ty[NMAX];
-  double t0[2 * NMAX], t1[2 * NMAX], t2[2 * NMAX], red[8];
-  float f0[2 * NMAX], f1[2 * NMAX];
+  float2 d[NMAX], is[NMAX], tx[NMAX], ty[NMAX];   // D_alpha circulant, 1/|X_alpha|, x_s, y_s
+  float2 u0[2 * NMAX], u1[2 * NMAX], u2[2 * NMAX]; // double-float work vectors
+  double red[8];
+  __align__(16) float f0[2 * NMAX];                // FP32 corrections
+  __align__(16) float f1[2 * NMAX];
 };
 
-// y (+)= alpha M x in FP32 for a rows x cols row-major FP32 matrix (global, read-only): each warp
-// takes four rows at a time so that their loads are in flight together; ends synchronised.
+// y (+)= alpha M x in FP32 for a rows x cols row-major FP32 matrix (global, read-only; cols even, at most
+// MP_COLS). Each warp takes MV_ROWS rows at a time and each lane two adjacent columns per 64, all loads
+// of a pass issued before the arithmetic so that enough bytes are in flight to cover the memory latency;
+// ends synchronised. x must be 8-byte aligned.
+constexpr int MV_ROWS = 4, MP_COLS = 2 * NMAX;
 __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols, const float* x, float* y,
                                  float alpha, bool add) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r0 = 4 * wid; r0 < rows; r0 += 4 * nw) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-    for (int k = lane; k < cols; k += 32) {
-      const float xk = x[k];
+  for (int r0 = MV_ROWS * wid; r0 < rows; r0 += MV_ROWS * nw) {
+    float2 mv[MP_COLS / 64][MV_ROWS];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (r0 + q < rows) acc[q] = fmaf(__ldg(M + (int64_t)(r0 + q) * cols + k), xk, acc[q]);
+    for (int t = 0; t < MP_COLS / 64; ++t) {
+      const int k = 2 * lane + 64 * t;
+#pragma unroll
+      for (int q = 0; q < MV_ROWS; ++q)
+        mv[t][q] = (k < cols && r0 + q < rows)
+                       ? __ldg(reinterpret_cast<const float2*>(M + (int64_t)(r0 + q) * cols + k))
+                       : make_float2(0.f, 0.f);
+    }
+    float acc[MV_ROWS];
+#pragma unroll
+    for (int q = 0; q < MV_ROWS; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int t = 0; t < MP_COLS / 64; ++t) {
+      const int k = 2 * lane + 64 * t;
+      if (k < cols) {
+        const float2 xk = *reinterpret_cast<const float2*>(x + k);
+#pragma unroll
+        for (int q = 0; q < MV_ROWS; ++q) acc[q] = fmaf(mv[t][q].y, xk.y, fmaf(mv[t][q].x, xk.x, acc[q]));
+      }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < MV_ROWS; ++q) {
       float a = acc[q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -68,95 +161,130 @@ __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols
   __syncthreads();
 }
 
-// Convergence test of a refinement: stop once the update is at the rounding floor of the iterate
-// (below 4e-15 of it) or has stopped shrinking after falling below 1e-12 of it.
+// Convergence test of a refinement: stop once the update is at the rounding floor of the residual
+// arithmetic, or has stopped shrinking after falling below MP_STALL of the iterate.
 __device__ __forceinline__ bool mp_done(double upd, double prev, double top) {
-  return upd <= 4e-15 * top || (upd <= 1e-12 * top && upd >= 0.5 * prev);
+  return upd <= MP_FLOOR * top || (upd <= MP_STALL * top && upd >= 0.5 * prev);
 }
 
 __device__ inline void mp_load_geom(MpShared& sh, const double* tab, const double* sa, const double* tx,
                                     const double* ty, int N, int64_t o) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sh.d[i] = tab[i];
-    sh.sa[i] = sa[o + i];
-    sh.tx[i] = tx[o + i];
-    sh.ty[i] = ty[o + i];
+    sh.d[i] = df_of(tab[i]);
+    sh.is[i] = df_of(1.0 / sa[o + i]);
+    sh.tx[i] = df_of(tx[o + i]);
+    sh.ty[i] = df_of(ty[o + i]);
   }
   __syncthreads();
 }
 
-// out[i] = D_s in (i < N); in and out distinct; ends synchronised
-__device__ inline void mp_ds(const MpShared& sh, const double* in, double* out, int N) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = circ_row(sh.d, in, N, i) / sh.sa[i];
-  __syncthreads();
-}
-
-// w = S u for the 2N x 2N row-major FP64 matrix S (global, read-only), four rows per warp pass;
-// ends synchronised
-__device__ inline void mp_smatvec(const double* __restrict__ S, const double* u, double* w, int n2) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r0 = 4 * wid; r0 < n2; r0 += 4 * nw) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 2
-    for (int k = lane; k < n2; k += 32) {
-      const double uk = u[k];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (r0 + q < n2) acc[q] = fma(__ldg(S + (int64_t)(r0 + q) * n2 + k), uk, acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double a = warp_sum(acc[q]);
-      if (lane == 0 && r0 + q < n2) w[r0 + q] = a;
-    }
-  }
-  __syncthreads();
-}
-
-// out[c N + i] = D_s in[c N + i] for both components c = 0, 1 at once; ends synchronised
-__device__ inline void mp_ds2(const MpShared& sh, const double* in, double* out, int N) {
+// out[c N + i] = D_s in[c N + i] for both components c = 0, 1; in and out distinct; ends synchronised
+__device__ inline void mp_ds2(const MpShared& sh, const float2* in, float2* out, int N) {
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) {
     const int c = (r >= N) ? 1 : 0, i = r - c * N;
-    out[r] = circ_row(sh.d, in + c * N, N, i) / sh.sa[i];
+    out[r] = df_mul(circ_df(sh.d, in + c * N, N, i), sh.is[i]);
   }
   __syncthreads();
 }
 
-// out (2N) = Ten s; uses sh.t2 as scratch
-__device__ inline void mp_ten(MpShared& sh, const double* s, double* out, int N) {
+// out (2N) = Ten s; uses sh.u2 as scratch
+__device__ inline void mp_ten(MpShared& sh, const float2* s, float2* out, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sh.t2[i] = s[i] * sh.tx[i];
-    sh.t2[N + i] = s[i] * sh.ty[i];
+    sh.u2[i] = df_mul(s[i], sh.tx[i]);
+    sh.u2[N + i] = df_mul(s[i], sh.ty[i]);
   }
   __syncthreads();
-  mp_ds2(sh, sh.t2, out, N);
+  mp_ds2(sh, sh.u2, out, N);
 }
 
-// out (N) = P v
-__device__ inline void mp_p(const MpShared& sh, const double* v, double* out, int N) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    out[i] = (sh.tx[i] * circ_row(sh.d, v, N, i) + sh.ty[i] * circ_row(sh.d, v + N, N, i)) / sh.sa[i];
+// out (N) = P v; ends synchronised
+__device__ inline void mp_p(const MpShared& sh, const float2* v, float2* out, int N) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float2 a = df_mul(sh.tx[i], circ_df(sh.d, v, N, i));
+    const float2 b = df_mul(sh.ty[i], circ_df(sh.d, v + N, N, i));
+    out[i] = df_mul(df_add(a, b), sh.is[i]);
+  }
   __syncthreads();
 }
 
-// Solve L s = g (FP64 accuracy) with the FP32 inverse of L and FP64 matrix-free L. g is read only.
-// s, e (N each), q, w (2N each) are caller shared arrays; uses sh.t2.
-__device__ bool mp_solve_L(MpShared& sh, const double* S, const float* Linv, const double* g, double* s,
-                           double* e, double* q, double* w, int N) {
+// w = S u for the 2N x 2N matrix S = Sh + Sl (two row-major FP32 matrices in global memory): MV_ROWS
+// rows per warp pass, each lane two adjacent columns per 64 (all loads of a pass issued first), partial
+// sums merged across the warp; ends synchronised
+__device__ inline void mp_smatvec(const float* __restrict__ Sh, const float* __restrict__ Sl, const float2* u,
+                                  float2* w, int n2) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r0 = MV_ROWS * wid; r0 < n2; r0 += MV_ROWS * nw) {
+    float2 hv[MP_COLS / 64][MV_ROWS], lv[MP_COLS / 64][MV_ROWS];
+#pragma unroll
+    for (int t = 0; t < MP_COLS / 64; ++t) {
+      const int k = 2 * lane + 64 * t;
+#pragma unroll
+      for (int q = 0; q < MV_ROWS; ++q) {
+        const bool in = k < n2 && r0 + q < n2;
+        const int64_t e = (int64_t)(r0 + q) * n2 + k;
+        hv[t][q] = in ? __ldg(reinterpret_cast<const float2*>(Sh + e)) : make_float2(0.f, 0.f);
+        lv[t][q] = in ? __ldg(reinterpret_cast<const float2*>(Sl + e)) : make_float2(0.f, 0.f);
+      }
+    }
+    Dot2 acc[MV_ROWS];
+#pragma unroll
+    for (int t = 0; t < MP_COLS / 64; ++t) {
+      const int k = 2 * lane + 64 * t;
+      if (k < n2) {
+        const float2 u0 = u[k], u1 = u[k + 1];
+#pragma unroll
+        for (int q = 0; q < MV_ROWS; ++q) {
+          acc[q].add(make_float2(hv[t][q].x, lv[t][q].x), u0);
+          acc[q].add(make_float2(hv[t][q].y, lv[t][q].y), u1);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MV_ROWS; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, acc[q].s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, acc[q].c, o);
+        acc[q].merge(s2, c2);
+      }
+      if (lane == 0 && r0 + q < n2) w[r0 + q] = acc[q].value();
+    }
+  }
+  __syncthreads();
+}
+
+// The FP32 blocks of vesicle v at slot s: S_hi, S_lo, T32, Li32
+struct MpMats {
+  const float *sh, *sl, *t32, *li;
+};
+__device__ __forceinline__ MpMats mp_mats(const VesIndex& vi, const float* scratch32, int v, int s) {
+  const int N = vi.N[v];
+  const int64_t NN = (int64_t)N * N;
+  const float* b = scratch32 + vi.moff[v];
+  return MpMats{b + (MatLayout::slot(s) + MatLayout::S) * NN, b + (MatLayout::slot(s) + MatLayout::SL) * NN,
+                b + (MatLayout::slot(s) + MatLayout::T) * NN, b + (MatLayout::slot(s) + MatLayout::L) * NN};
+}
+
+// Solve L s = g (s FP64, g double-float and read only) with Li32 and the matrix-free L.
+// e (N) and q, w (2N) are caller shared double-float arrays; uses sh.u2, sh.f0, sh.f1.
+__device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, double* s, float2* e, float2* q,
+                           float2* w, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) { s[i] = 0.0; e[i] = g[i]; }
   __syncthreads();
   double upd = 1e300, top = 0.0;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it > 0) {
-      mp_ten(sh, s, q, N);
-      mp_smatvec(S, q, w, 2 * N);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = df_of(s[i]);
+      __syncthreads();
+      mp_ten(sh, w, q, N);
+      mp_smatvec(m.sh, m.sl, q, w, 2 * N);
       mp_p(sh, w, e, N);
-      for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = g[i] - e[i];
+      for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = df_add(g[i], make_float2(-e[i].x, -e[i].y));
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f1[i] = (float)e[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f1[i] = e[i].x;
     __syncthreads();
-    matvec32f(Linv, N, N, sh.f1, sh.f0, 1.f, false);
+    matvec32f(m.li, N, N, sh.f1, sh.f0, 1.f, false);
     double du = 0.0, sv = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       s[i] += (double)sh.f0[i];
@@ -168,32 +296,34 @@ __device__ bool mp_solve_L(MpShared& sh, const double* S, const float* Linv, con
     top = block_max_abs(sv, sh.red);
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
-  return upd <= 1e-11 * top || top == 0.0;
+  return upd <= MP_FAIL * top || top == 0.0;
 }
 
-// X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with S (FP64) and Li32 cached at slot s.
+// X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s.
 __global__ void __launch_bounds__(MP_THREADS) k_advect_mp(VesIndex vi, const double* __restrict__ xy,
                                                    const double* __restrict__ u, const double* __restrict__ sa,
                                                    const double* __restrict__ tx, const double* __restrict__ ty,
-                                                   const double* __restrict__ tab, const double* __restrict__ scratch,
+                                                   const double* __restrict__ tab,
                                                    const float* __restrict__ scratch32, int s, double dt,
                                                    double* __restrict__ xy_out, unsigned* err) {
   __shared__ MpShared sh;
-  __shared__ double ub[2 * NMAX], g[NMAX], sg[NMAX], e[NMAX];
+  __shared__ float2 g[NMAX], e[NMAX];
+  __shared__ double sg[NMAX];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
-  const int64_t NN = (int64_t)N * N;
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
-  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) ub[r] = u[2 * o + r];
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u0[r] = df_of(u[2 * o + r]);
   __syncthreads();
-  mp_p(sh, ub, g, N);
-  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN;
-  const float* Linv = scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::L) * NN;
-  const bool ok = mp_solve_L(sh, S, Linv, g, sg, e, sh.t0, sh.t1, N);
-  mp_ten(sh, sg, sh.t0, N);
-  mp_smatvec(S, sh.t0, sh.t1, 2 * N);
-  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) xy_out[2 * o + r] = xy[2 * o + r] + dt * (ub[r] - sh.t1[r]);
+  mp_p(sh, sh.u0, g, N);
+  const MpMats m = mp_mats(vi, scratch32, v, s);
+  const bool ok = mp_solve_L(sh, m, g, sg, e, sh.u1, sh.u0, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = df_of(sg[i]);
+  __syncthreads();
+  mp_ten(sh, e, sh.u1, N);
+  mp_smatvec(m.sh, m.sl, sh.u1, sh.u0, 2 * N);
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x)
+    xy_out[2 * o + r] = xy[2 * o + r] + dt * (u[2 * o + r] - df_val(sh.u0[r]));
   if (!ok && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
@@ -202,85 +332,98 @@ __global__ void __launch_bounds__(MP_THREADS) k_tension_mp(VesIndex vi, const do
                                                     const double* __restrict__ by, const double* __restrict__ u,
                                                     const double* __restrict__ sa, const double* __restrict__ tx,
                                                     const double* __restrict__ ty, const double* __restrict__ tab,
-                                                    const double* __restrict__ scratch,
                                                     const float* __restrict__ scratch32, int s, double kappa,
                                                     double* __restrict__ sigma, unsigned* err) {
   __shared__ MpShared sh;
-  __shared__ double b2[2 * NMAX], g[NMAX], sg[NMAX], e[NMAX];
+  __shared__ float2 g[NMAX], e[NMAX];
+  __shared__ double sg[NMAX];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
-  const int64_t NN = (int64_t)N * N;
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    b2[i] = bx[o + i];
-    b2[N + i] = by[o + i];
+    sh.u0[i] = df_of(bx[o + i]);
+    sh.u0[N + i] = df_of(by[o + i]);
   }
   __syncthreads();
-  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN;
-  mp_smatvec(S, b2, sh.t0, 2 * N);
-  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.t0[r] = -kappa * sh.t0[r] + u[2 * o + r];
+  const MpMats m = mp_mats(vi, scratch32, v, s);
+  mp_smatvec(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
+  const float2 mk = df_of(-kappa);
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u1[r] = df_add(df_mul(mk, sh.u1[r]), df_of(u[2 * o + r]));
   __syncthreads();
-  mp_p(sh, sh.t0, g, N);
-  const float* Linv = scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::L) * NN;
-  const bool ok = mp_solve_L(sh, S, Linv, g, sg, e, sh.t0, sh.t1, N);
+  mp_p(sh, sh.u1, g, N);
+  const bool ok = mp_solve_L(sh, m, g, sg, e, sh.u1, sh.u0, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sigma[o + i] = -sg[i];
   if (!ok && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
-// Relaxation (Eq. relaxation_disc) by refinement of the coupled (x, sigma) system at slot s.
+// Relaxation (Eq. relaxation_disc) by refinement of the coupled (x, sigma) system at slot s. The
+// iterate x is kept relative to the mean point of X* (the operators only see its derivatives).
 __global__ void __launch_bounds__(MP_THREADS) k_relax_mp(VesIndex vi, const double* __restrict__ xy_star,
                                                   const double* __restrict__ sa, const double* __restrict__ tx,
                                                   const double* __restrict__ ty, const double* __restrict__ tab,
-                                                  const double* __restrict__ scratch,
                                                   const float* __restrict__ scratch32, int s, int64_t ainv_sub,
                                                   double kappa, double dt, double* __restrict__ xy_out,
                                                   unsigned* err) {
   __shared__ MpShared sh;
-  __shared__ double b[2 * NMAX], x[2 * NMAX], sg[NMAX], r1[2 * NMAX], y2[NMAX];
-  __shared__ float fy[NMAX], fr[2 * NMAX], fdx[2 * NMAX], fw[NMAX];
+  __shared__ double b[2 * NMAX], x[2 * NMAX], sg[NMAX], r1[2 * NMAX], cen[2];
+  __shared__ float2 y2[NMAX];
+  __shared__ __align__(16) float fy[NMAX], fr[2 * NMAX], fdx[2 * NMAX], fw[NMAX];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int64_t NN = (int64_t)N * N;
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
-  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) { b[r] = xy_star[2 * o + r]; x[r] = 0.0; }
+  double mx = 0.0, my = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    mx += xy_star[2 * o + i];
+    my += xy_star[2 * o + N + i];
+  }
+  mx = block_sum(mx, sh.red) / N;
+  my = block_sum(my, sh.red) / N;
+  if (threadIdx.x == 0) { cen[0] = mx; cen[1] = my; }
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) {
+    b[r] = xy_star[2 * o + r] - ((r < N) ? mx : my);  // X* relative to its mean point
+    x[r] = 0.0;
+  }
   for (int i = threadIdx.x; i < N; i += blockDim.x) sg[i] = 0.0;
   __syncthreads();
-  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN;
+  const MpMats m = mp_mats(vi, scratch32, v, s);
   const float* base32 = scratch32 + vi.moff[v];
-  const float* T32 = base32 + (MatLayout::slot(s) + MatLayout::T) * NN;
-  const float* Linv = base32 + (MatLayout::slot(s) + MatLayout::L) * NN;  // Li32
   const float* W32 = base32 + MatLayout::W * NN;
-  const float* Ainv = base32 + ainv_sub * NN;                              // Ai32
+  const float* Ainv = base32 + ainv_sub * NN;  // Ai32
+  const float2 mk = df_of(-kappa);
   double upd = 1e300, top = 0.0;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it == 0) {
       for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r];
-      for (int i = threadIdx.x; i < N; i += blockDim.x) y2[i] = 0.0;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) y2[i] = make_float2(0.f, 0.f);
       __syncthreads();
     } else {
-      // q = -kappa D^4 x + Ten sigma  (into sh.t0), v = S q (into sh.t1)
-      mp_ds2(sh, x, sh.t1, N);
-      mp_ds2(sh, sh.t1, sh.t2, N);
-      mp_ds2(sh, sh.t2, sh.t1, N);
-      mp_ds2(sh, sh.t1, sh.t0, N);
-      mp_ten(sh, sg, sh.t1, N);
-      for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.t0[r] = -kappa * sh.t0[r] + sh.t1[r];
+      // q = -kappa D^4 x + Ten sigma (into u0), v = S q (into u1)
+      for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u0[r] = df_of(x[r]);
       __syncthreads();
-      mp_smatvec(S, sh.t0, sh.t1, 2 * N);
-      for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r] - x[r] + dt * sh.t1[r];
+      mp_ds2(sh, sh.u0, sh.u1, N);
+      mp_ds2(sh, sh.u1, sh.u2, N);
+      mp_ds2(sh, sh.u2, sh.u1, N);
+      mp_ds2(sh, sh.u1, sh.u0, N);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) sh.u1[i] = df_of(sg[i]);
       __syncthreads();
-      mp_p(sh, sh.t1, y2, N);
-      for (int i = threadIdx.x; i < N; i += blockDim.x) y2[i] = -y2[i];
+      float2* tsg = reinterpret_cast<float2*>(r1);  // r1 is free until the residual: Ten sigma (2N) into it
+      mp_ten(sh, sh.u1, tsg, N);
+      for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u0[r] = df_add(df_mul(mk, sh.u0[r]), tsg[r]);
       __syncthreads();
+      mp_smatvec(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
+      for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r] - x[r] + dt * df_val(sh.u1[r]);
+      __syncthreads();
+      mp_p(sh, sh.u1, y2, N);
     }
-    // correction in FP32: y = Li32 r2, dx = Ai32 (r1 + dt T32 y), dsigma = y - W32 dx
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f0[i] = (float)y2[i];
+    // correction in FP32: y = Li32 r2 (r2 = -P v), dx = Ai32 (r1 + dt T32 y), dsigma = y - W32 dx
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f0[i] = -y2[i].x;
     for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) fr[r] = (float)r1[r];
     __syncthreads();
-    matvec32f(Linv, N, N, sh.f0, fy, 1.f, false);
-    matvec32f(T32, 2 * N, N, fy, fr, (float)dt, true);
+    matvec32f(m.li, N, N, sh.f0, fy, 1.f, false);
+    matvec32f(m.t32, 2 * N, N, fy, fr, (float)dt, true);
     matvec32f(Ainv, 2 * N, 2 * N, fr, fdx, 1.f, false);
     matvec32f(W32, N, 2 * N, fdx, fw, 1.f, false);
     double du = 0.0, xv = 0.0;
@@ -295,8 +438,8 @@ __global__ void __launch_bounds__(MP_THREADS) k_relax_mp(VesIndex vi, const doub
     top = block_max_abs(xv, sh.red);
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
-  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) xy_out[2 * o + r] = x[r];
-  if (!(upd <= 1e-11 * top) && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) xy_out[2 * o + r] = x[r] + cen[r < N ? 0 : 1];
+  if (!(upd <= MP_FAIL * top) && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
 }  // namespace vs

@@ -7,7 +7,7 @@
 // i.e. the Kress product rule for the log singularity of -log|r| and the trapezoid rule for the
 // smooth remainder, with the standard 2D Stokeslet (1/4 pi mu)(-log|r| I + r r^T/|r|^2).
 // Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y]. With scratch32 set,
-// an FP32 copy is written at the same place of the FP32 scratch.
+// the FP32 split S = S_hi + S_lo is written to the S and SL blocks of the FP32 scratch.
 #pragma once
 #include "common.cuh"
 
@@ -18,18 +18,20 @@ namespace vs {
 // writes the tile and its mirror image (bj, bi). Grid: (nt (nt + 1) / 2, M), nt = ceil(N / 16).
 constexpr int SM_TILE = 16;
 
-__device__ __forceinline__ void self_store(double* S, float* S32, int n2, int N, int i, int j, double c, double lp,
-                                           double dal, double axx, double axy, double ayy) {
+__device__ __forceinline__ void self_store(double* S, float* S32, float* SL32, int n2, int N, int i, int j,
+                                           double c, double lp, double dal, double axx, double axy, double ayy) {
   const double sxx = c * (lp + dal * axx), sxy = c * dal * axy, syy = c * (lp + dal * ayy);
-  S[(int64_t)i * n2 + j] = sxx;
-  S[(int64_t)i * n2 + N + j] = sxy;
-  S[(int64_t)(N + i) * n2 + j] = sxy;
-  S[(int64_t)(N + i) * n2 + N + j] = syy;
-  if (S32) {  // FP32 copy for the mixed-precision factorisations
-    S32[(int64_t)i * n2 + j] = (float)sxx;
-    S32[(int64_t)i * n2 + N + j] = (float)sxy;
-    S32[(int64_t)(N + i) * n2 + j] = (float)sxy;
-    S32[(int64_t)(N + i) * n2 + N + j] = (float)syy;
+  const int64_t e[4] = {(int64_t)i * n2 + j, (int64_t)i * n2 + N + j, (int64_t)(N + i) * n2 + j,
+                        (int64_t)(N + i) * n2 + N + j};
+  const double val[4] = {sxx, sxy, sxy, syy};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    S[e[q]] = val[q];
+    if (S32) {  // FP32 split S = S_hi + S_lo for the mixed-precision path
+      const float hi = __double2float_rn(val[q]);
+      S32[e[q]] = hi;
+      SL32[e[q]] = __double2float_rn(val[q] - (double)hi);
+    }
   }
 }
 
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
   const double c0 = 1.0 / (4.0 * VS_PI * mu);
   double* S = scratch + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N;
   float* S32 = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N : nullptr;
+  float* SL32 = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::SL) * (int64_t)N * N : nullptr;
   const int n2 = 2 * N;
   int i = bi * SM_TILE + li, j = bj * SM_TILE + lj;
   if (i < N && j < N) {
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
     kxx[li][lj] = axx;
     kxy[li][lj] = axy;
     kyy[li][lj] = ayy;
-    self_store(S, S32, n2, N, i, j, sa[o + j] * c0, lp, dal, axx, axy, ayy);
+    self_store(S, S32, SL32, n2, N, i, j, sa[o + j] * c0, lp, dal, axx, axy, ayy);
   }
   if (bi == bj) return;
   __syncthreads();
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
   i = bj * SM_TILE + li;
   j = bi * SM_TILE + lj;
   if (i < N && j < N)
-    self_store(S, S32, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
+    self_store(S, S32, SL32, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
 }
 
 }  // namespace vs

@@ -430,7 +430,7 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
       VS_LAUNCH(h, "k_lu_inverse32<A>", k_lu_inverse<LuGeo32><<<M, 256, 0, h->stream>>>(ga, MatLayout::B, nullptr));
       ainv = MatLayout::B;
     }
-    VS_LAUNCH(h, "k_relax_mp", k_relax_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch,
+    VS_LAUNCH(h, "k_relax_mp", k_relax_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
                                                                    h->scratch32, s, ainv, h->p.kappa_b, h->p.dt, xo, h->err));
     VS_CK(h, cudaGetLastError(), "relaxation");
     return VS_OK;
@@ -454,7 +454,7 @@ vs_status tension(vs_suspension* h, const double* u, int s) {
   const int M = h->L.M;
   if (mixed(h)) {
     VS_LAUNCH(h, "k_tension_mp", k_tension_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty,
-                                                                       h->D.tab, h->scratch, h->scratch32, s,
+                                                                       h->D.tab, h->scratch32, s,
                                                                        h->p.kappa_b, h->sigma, h->err));
   } else {
     VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
@@ -537,7 +537,7 @@ vs_status step_once(vs_suspension* h) {
   // (4) advection
   if (mixed(h)) {
     VS_LAUNCH(h, "k_advect_mp", k_advect_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                     h->scratch, h->scratch32, cur, h->p.dt,
+                                                                     h->scratch32, cur, h->p.dt,
                                                                      h->xy_star, h->err));
   } else {
     VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
