@@ -8,7 +8,7 @@
 namespace vs {
 
 constexpr int NMAX = 128;          // largest points per vesicle handled by the per-vesicle kernels
-constexpr int TAB_STRIDE = 17;     // table doubles per N (see tables.cuh)
+constexpr int TAB_STRIDE = 18;     // table doubles per N (see tables.cuh)
 constexpr int MAX_NEAR = 8;        // near source vesicles recorded per target point
 
 // Device-side error bits, OR-ed into one word per suspension and read back by the host.

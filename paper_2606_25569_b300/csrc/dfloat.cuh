@@ -1,0 +1,70 @@
+// Double-float arithmetic for the mixed-precision kernels (FP64 runs at 1/64 of the FP32 rate on
+// this part).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace vs {
+
+// A double-float value is the unevaluated sum x + y of two floats with |y| <= ulp(x)/2
+// (about 48 significant bits). Error-free transformations: TwoSum (Knuth), Fast2Sum (Dekker), the exact
+// product error by FMA; dot products follow the compensated scheme Dot2 of Ogita, Rump and Oishi (2005),
+// extended by the cross terms of double-float operands and folded into a double-float total every
+// DF_CHUNK terms. The _rn intrinsics keep the compiler from contracting the transformations into FMAs.
+constexpr int DF_CHUNK = 8;
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+
+// Compensated accumulator: s the running FP32 sum, c the sum of its rounding errors and of the
+// low-order product terms.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float t = __fadd_rn(s, p), z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)), e));
+    s = t;
+  }
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    const float2 t = two_sum(s, s2);
+    s = t.x;
+    c = __fadd_rn(c, __fadd_rn(c2, t.y));
+  }
+  __device__ __forceinline__ float2 value() const { return two_sum(s, c); }
+};
+
+
+// 1/a in double-float: the FP32 reciprocal refined by one Newton step carried out in double-float
+__device__ __forceinline__ float2 df_rcp(float2 a) {
+  const float2 y0 = make_float2(__frcp_rn(a.x), 0.f);
+  const float2 p = df_mul(a, y0);
+  const float2 e = df_add(make_float2(1.f, 0.f), make_float2(-p.x, -p.y));
+  return df_add(y0, df_mul(y0, e));
+}
+
+}  // namespace vs

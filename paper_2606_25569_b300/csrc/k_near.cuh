@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
                                                      const double* __restrict__ xy, const double* __restrict__ f,
                                                      PointGeom g, const double* __restrict__ length,
                                                      const double* __restrict__ tab,
-                                                     const double* __restrict__ scratch, int s, double mu,
+                                                     const double* __restrict__ scratch,
+                                                     const float* __restrict__ scratch32, int s, double mu,
                                                      NearBufs nb) {
   extern __shared__ double sm[];
   const int v = blockIdx.x;
@@ -111,7 +112,11 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
   double* LY = L + 5 * N;
   double* UX = L + 10 * N;
   double* UY = L + 15 * N;
-  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * (int64_t)N * N;
+  // S at slot s: FP64, or (mixed-precision path, scratch32 set) the FP32 split S_hi + S_lo
+  const int64_t NN = (int64_t)N * N;
+  const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN;
+  const float* Sh = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN : nullptr;
+  const float* Sl = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::SL) * NN : nullptr;
   for (int e = tid; e < 5 * N; e += blockDim.x) {
     const int lay = e / N, j = e - lay * N;
     const double d = c_layer_d[lay] * h;
@@ -122,8 +127,11 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
     double ax = 0.0, ay = 0.0;
     if (lay == 2) {  // on the curve: S f
       for (int k = 0; k < 2 * N; ++k) {
-        ax = fma(S[(int64_t)j * 2 * N + k], fl[k], ax);
-        ay = fma(S[(int64_t)(N + j) * 2 * N + k], fl[k], ay);
+        const int64_t ex = (int64_t)j * 2 * N + k, ey = (int64_t)(N + j) * 2 * N + k;
+        const double sx = Sh ? (double)Sh[ex] + (double)Sl[ex] : S[ex];
+        const double sy = Sh ? (double)Sh[ey] + (double)Sl[ey] : S[ey];
+        ax = fma(sx, fl[k], ax);
+        ay = fma(sy, fl[k], ay);
       }
     } else {
       for (int m = 0; m < Nu; ++m) {

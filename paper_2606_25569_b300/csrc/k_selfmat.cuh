@@ -6,10 +6,12 @@
 //   rr_ij = r r^T / |r|^2 (i != j),  rr_ii = X_s X_s^T
 // i.e. the Kress product rule for the log singularity of -log|r| and the trapezoid rule for the
 // smooth remainder, with the standard 2D Stokeslet (1/4 pi mu)(-log|r| I + r r^T/|r|^2).
-// Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y]. With scratch32 set,
-// the FP32 split S = S_hi + S_lo is written to the S and SL blocks of the FP32 scratch.
+// Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y]. k_self_matrix writes
+// FP64 S; k_self_matrix_df writes the split S = S_hi + S_lo (two FP32 matrices, the S and SL blocks of
+// the FP32 scratch) for the mixed-precision path, with everything after the logarithm in double-float.
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace vs {
 
@@ -18,21 +20,13 @@ namespace vs {
 // writes the tile and its mirror image (bj, bi). Grid: (nt (nt + 1) / 2, M), nt = ceil(N / 16).
 constexpr int SM_TILE = 16;
 
-__device__ __forceinline__ void self_store(double* S, float* S32, float* SL32, int n2, int N, int i, int j,
-                                           double c, double lp, double dal, double axx, double axy, double ayy) {
+__device__ __forceinline__ void self_store(double* S, int n2, int N, int i, int j, double c, double lp, double dal,
+                                           double axx, double axy, double ayy) {
   const double sxx = c * (lp + dal * axx), sxy = c * dal * axy, syy = c * (lp + dal * ayy);
-  const int64_t e[4] = {(int64_t)i * n2 + j, (int64_t)i * n2 + N + j, (int64_t)(N + i) * n2 + j,
-                        (int64_t)(N + i) * n2 + N + j};
-  const double val[4] = {sxx, sxy, sxy, syy};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    S[e[q]] = val[q];
-    if (S32) {  // FP32 split S = S_hi + S_lo for the mixed-precision path
-      const float hi = __double2float_rn(val[q]);
-      S32[e[q]] = hi;
-      SL32[e[q]] = __double2float_rn(val[q] - (double)hi);
-    }
-  }
+  S[(int64_t)i * n2 + j] = sxx;
+  S[(int64_t)i * n2 + N + j] = sxy;
+  S[(int64_t)(N + i) * n2 + j] = sxy;
+  S[(int64_t)(N + i) * n2 + N + j] = syy;
 }
 
 __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* __restrict__ xy,
@@ -40,8 +34,8 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
                                                      const double* __restrict__ tx,
                                                      const double* __restrict__ ty,
                                                      const double* __restrict__ tab, double mu,
-                                                     double* __restrict__ scratch, float* __restrict__ scratch32,
-                                                     int slot, const int* __restrict__ active) {
+                                                     double* __restrict__ scratch, int slot,
+                                                     const int* __restrict__ active) {
   const int v = blockIdx.y;
   if (active && !active[v]) return;
   const int N = vi.N[v];
@@ -58,8 +52,6 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
   const double dal = 2.0 * VS_PI / N;
   const double c0 = 1.0 / (4.0 * VS_PI * mu);
   double* S = scratch + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N;
-  float* S32 = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * (int64_t)N * N : nullptr;
-  float* SL32 = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::SL) * (int64_t)N * N : nullptr;
   const int n2 = 2 * N;
   int i = bi * SM_TILE + li, j = bj * SM_TILE + lj;
   if (i < N && j < N) {
@@ -86,7 +78,7 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
     kxx[li][lj] = axx;
     kxy[li][lj] = axy;
     kyy[li][lj] = ayy;
-    self_store(S, S32, SL32, n2, N, i, j, sa[o + j] * c0, lp, dal, axx, axy, ayy);
+    self_store(S, n2, N, i, j, sa[o + j] * c0, lp, dal, axx, axy, ayy);
   }
   if (bi == bj) return;
   __syncthreads();
@@ -94,7 +86,91 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
   i = bj * SM_TILE + li;
   j = bi * SM_TILE + lj;
   if (i < N && j < N)
-    self_store(S, S32, SL32, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
+    self_store(S, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
+}
+
+__device__ __forceinline__ void self_store_df(float* Sh, float* Sl, int n2, int N, int i, int j, float2 c, float2 lp,
+                                              float2 dal, float2 axx, float2 axy, float2 ayy) {
+  const float2 sxx = df_mul(c, df_add(lp, df_mul(dal, axx)));
+  const float2 sxy = df_mul(c, df_mul(dal, axy));
+  const float2 syy = df_mul(c, df_add(lp, df_mul(dal, ayy)));
+  const int64_t e0 = (int64_t)i * n2 + j, e1 = (int64_t)i * n2 + N + j, e2 = (int64_t)(N + i) * n2 + j,
+                e3 = (int64_t)(N + i) * n2 + N + j;
+  Sh[e0] = sxx.x; Sl[e0] = sxx.y;
+  Sh[e1] = sxy.x; Sl[e1] = sxy.y;
+  Sh[e2] = sxy.x; Sl[e2] = sxy.y;
+  Sh[e3] = syy.x; Sl[e3] = syy.y;
+}
+
+// The same matrix as k_self_matrix, as S_hi + S_lo: the log term lp in FP64 (log|r|^2 minus the tabulated
+// log 4 sin^2), then the r r^T/|r|^2 terms and the products in double-float. Same grid and tiling.
+__global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const double* __restrict__ xy,
+                                                        const double* __restrict__ sa,
+                                                        const double* __restrict__ tx,
+                                                        const double* __restrict__ ty,
+                                                        const double* __restrict__ tab, double mu,
+                                                        float* __restrict__ scratch32, int slot,
+                                                        const int* __restrict__ active) {
+  const int v = blockIdx.y;
+  if (active && !active[v]) return;
+  const int N = vi.N[v];
+  const int nt = (N + SM_TILE - 1) / SM_TILE;
+  int t = blockIdx.x, bi = 0;
+  if (t >= nt * (nt + 1) / 2) return;
+  while (t >= nt - bi) { t -= nt - bi; ++bi; }
+  const int bj = bi + t;
+  __shared__ float2 kl[SM_TILE][SM_TILE + 1], kxx[SM_TILE][SM_TILE + 1], kxy[SM_TILE][SM_TILE + 1],
+      kyy[SM_TILE][SM_TILE + 1];
+  __shared__ float2 cc[2][SM_TILE];  // sa_j / (4 pi mu) for the tile's columns (0) and its mirror's (1)
+  const int li = threadIdx.x / SM_TILE, lj = threadIdx.x % SM_TILE;
+  const int64_t o = vi.off[v];
+  const double* T = tab + vi.toff[v];
+  const double dal64 = 2.0 * VS_PI / N;
+  const float2 dal = df_of(dal64);
+  if (threadIdx.x < 2 * SM_TILE) {
+    const int w = threadIdx.x / SM_TILE, jj = (w ? bi : bj) * SM_TILE + threadIdx.x % SM_TILE;
+    cc[w][threadIdx.x % SM_TILE] = (jj < N) ? df_of(sa[o + jj] / (4.0 * VS_PI * mu)) : make_float2(0.f, 0.f);
+  }
+  const int64_t NN = (int64_t)N * N;
+  float* Sh = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * NN;
+  float* Sl = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::SL) * NN;
+  const int n2 = 2 * N;
+  int i = bi * SM_TILE + li, j = bj * SM_TILE + lj;
+  float2 lp, axx, axy, ayy;
+  const bool in = i < N && j < N;
+  if (in) {
+    const int m = (i - j < 0) ? i - j + N : i - j;
+    const double R = T[N + m];
+    if (i != j) {
+      const double rx = xy[2 * o + i] - xy[2 * o + j];
+      const double ry = xy[2 * o + N + i] - xy[2 * o + N + j];
+      lp = df_of(-0.5 * R - 0.5 * dal64 * (log(rx * rx + ry * ry) - T[17 * N + m]));
+      const float2 rxd = df_of(rx), ryd = df_of(ry);
+      const float2 xx = df_mul(rxd, rxd), xy2 = df_mul(rxd, ryd), yy = df_mul(ryd, ryd);
+      const float2 ir2 = df_rcp(df_add(xx, yy));
+      axx = df_mul(xx, ir2);
+      axy = df_mul(xy2, ir2);
+      ayy = df_mul(yy, ir2);
+    } else {
+      lp = df_of(-0.5 * R - dal64 * log(sa[o + i]));
+      const float2 a = df_of(tx[o + i]), b = df_of(ty[o + i]);
+      axx = df_mul(a, a);
+      axy = df_mul(a, b);
+      ayy = df_mul(b, b);
+    }
+    kl[li][lj] = lp;
+    kxx[li][lj] = axx;
+    kxy[li][lj] = axy;
+    kyy[li][lj] = ayy;
+  }
+  __syncthreads();
+  if (in) self_store_df(Sh, Sl, n2, N, i, j, cc[0][lj], lp, dal, axx, axy, ayy);
+  if (bi == bj) return;
+  // mirror tile: entry (i, j) = (bj*16 + li, bi*16 + lj) has the symmetric part of (j, i)
+  i = bj * SM_TILE + li;
+  j = bi * SM_TILE + lj;
+  if (i < N && j < N)
+    self_store_df(Sh, Sl, n2, N, i, j, cc[1][lj], kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
 }
 
 }  // namespace vs

@@ -361,8 +361,13 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
   const VesIndex vi = h->D.vi();
-  VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                     h->p.mu, h->scratch, mixed(h) ? h->scratch32 : nullptr, s, active));
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_self_matrix_df", k_self_matrix_df<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
+                                                                      h->D.tab, h->p.mu, h->scratch32, s, active));
+  } else {
+    VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
+                                                                      h->D.tab, h->p.mu, h->scratch, s, active));
+  }
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
   if (mixed(h)) {
     VS_LAUNCH(h, "k_bgemm<OpT32>", k_bgemm<OpT32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT32{c, s}, active));
@@ -492,7 +497,8 @@ vs_status near_field(vs_suspension* h, int s) {
   const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
   const size_t smem = 6 * (size_t)Nu * sizeof(double);
   VS_LAUNCH(h, "k_near_layers", k_near_layers<<<L.M, 256, smem, h->stream>>>(vi, h->has_near, h->xy, h->B.f, h->B.pg(),
-                                                                            h->B.length, h->D.tab, h->scratch, s,
+                                                                            h->B.length, h->D.tab, h->scratch,
+                                                                            mixed(h) ? h->scratch32 : nullptr, s,
                                                                             h->p.mu, h->nb));
   VS_LAUNCH(h, "k_near_rbf", k_near_rbf<<<L.M, 256, 0, h->stream>>>(vi, h->has_near, h->B.length, h->nb, h->err));
   VS_LAUNCH(h, "k_near_apply", k_near_apply<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->D.off, h->D.N,
@@ -1002,8 +1008,7 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
     FlowDev none{0, 0.0, 0.0};
     k_geometry<<<M, NMAX, 0, s>>>(D.vi(), xy, nullptr, D.tab, 1.0, mu, none, B.geom(), ForceOut{}, nullptr);
     const int n = L.nmax;
-    k_self_matrix<<<self_grid(n, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, nullptr,
-                                                               0, nullptr);
+    k_self_matrix<<<self_grid(n, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, 0, nullptr);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
