@@ -260,15 +260,12 @@ __global__ void __launch_bounds__(NMAX) k_corr_init(VesIndex vi, const double* _
   }
 }
 
-// Assemble the KKT matrix and right-hand side at the current iterate.
-__global__ void __launch_bounds__(256) k_corr_build(VesIndex vi, const double* __restrict__ tab,
-                                                    const double* __restrict__ A0, const double* __restrict__ L0,
-                                                    double* __restrict__ corr, double* __restrict__ scratch,
-                                                    const int* __restrict__ active) {
+// Assemble the KKT matrix K (n x n, n = 2N + 2, in the B block of the scratch) and the right-hand side
+// at the current iterate of vesicle v.
+__device__ void corr_build(int v, VesIndex vi, const double* __restrict__ tab, const double* __restrict__ A0,
+                           const double* __restrict__ L0, double* __restrict__ corr, double* __restrict__ scratch) {
   __shared__ double d[NMAX], zx[NMAX], zy[NMAX], tx[NMAX], ty[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX];
   __shared__ double gA[2 * NMAX], gL[2 * NMAX], red[8];
-  const int v = blockIdx.x;
-  if (!active[v]) return;
   const int N = vi.N[v];
   const int n = 2 * N + 2;
   const int tid = threadIdx.x;
@@ -337,19 +334,16 @@ __global__ void __launch_bounds__(256) k_corr_build(VesIndex vi, const double* _
   }
 }
 
-// Solve the factored KKT system, update (z, lam), retire converged vesicles.
-__global__ void __launch_bounds__(256) k_corr_update(VesIndex vi, const double* __restrict__ scratch,
-                                                     const int* __restrict__ cpiv, double* __restrict__ corr,
-                                                     int* __restrict__ active) {
+// Solve the KKT system factored in LU (pivots p), update (z, lam), retire the vesicle once converged.
+__device__ void corr_update(int v, VesIndex vi, const double* LU, const int* p, double* __restrict__ corr,
+                            int* __restrict__ active) {
   __shared__ double b[2 * NMAX + 8], red[8];
-  const int v = blockIdx.x;
-  if (!active[v]) return;
   const int N = vi.N[v];
   const int n = 2 * N + 2;
   double* st = corr_state(corr, vi, v);
   for (int a = threadIdx.x; a < n; a += blockDim.x) b[a] = st[4 * N + a];
   __syncthreads();
-  lu_solve_vec(scratch + vi.moff[v] + MatLayout::B * (int64_t)N * N, cpiv + 2 * vi.off[v] + 2 * v, n, b);
+  lu_solve_vec(LU, p, n, b);
   double dm = 0.0;
   for (int a = threadIdx.x; a < 2 * N; a += blockDim.x) {
     st[2 * N + a] += b[a];
@@ -370,13 +364,38 @@ __global__ void __launch_bounds__(256) k_corr_update(VesIndex vi, const double* 
   }
 }
 
-// Write corrected points back (plus the mean) and flag vesicles that did not converge.
-__global__ void __launch_bounds__(NMAX) k_corr_finish(VesIndex vi, const double* __restrict__ corr,
-                                                      const int* __restrict__ dirty, double* __restrict__ xy,
-                                                      int* __restrict__ fired, unsigned* err) {
+// Newton iterations of the correction for every vesicle flagged by k_corr_init (dirty), at most `iters`
+// steps: assemble K, factor it (in dynamic shared memory when SMEM, else in place), solve, update; then
+// write the corrected points back (plus the mean) and flag vesicles that did not converge. One CTA of
+// 256 threads per vesicle.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_corr_newton(VesIndex vi, const double* __restrict__ tab,
+                                                     const double* __restrict__ A0, const double* __restrict__ L0,
+                                                     double* __restrict__ corr, double* __restrict__ scratch,
+                                                     int* __restrict__ cpiv, int* __restrict__ active,
+                                                     const int* __restrict__ dirty, int iters,
+                                                     double* __restrict__ xy, int* __restrict__ fired, unsigned* err) {
+  extern __shared__ unsigned char corr_raw[];
   const int v = blockIdx.x;
   if (!dirty[v]) return;
   const int N = vi.N[v];
+  const int n = 2 * N + 2;
+  double* K = scratch + vi.moff[v] + MatLayout::B * (int64_t)N * N;
+  double* F = SMEM ? reinterpret_cast<double*>(corr_raw) : K;
+  int* p = cpiv + 2 * vi.off[v] + 2 * v;
+  for (int it = 0; it < iters; ++it) {
+    __syncthreads();
+    if (!active[v]) break;  // uniform: written by thread 0 of this CTA before the barrier
+    corr_build(v, vi, tab, A0, L0, corr, scratch);
+    __syncthreads();
+    if (SMEM)
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) F[e] = K[e];
+    __syncthreads();
+    lu_factor<LuGeo>(F, n, p, err);
+    __syncthreads();
+    corr_update(v, vi, F, p, corr, active);
+  }
+  __syncthreads();
   const int64_t o = vi.off[v];
   const double* st = corr + 6 * o + 16 * (int64_t)v;
   const int i = threadIdx.x;

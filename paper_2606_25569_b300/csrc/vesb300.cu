@@ -514,15 +514,19 @@ vs_status correction(vs_suspension* h) {
   const VesIndex vi = h->D.vi();
   VS_LAUNCH(h, "k_corr_init", k_corr_init<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->A0, h->L0, h->p.corr_tol, h->D.tab,
                                                                        h->corr, h->cactive, h->dirty, h->err));
-  for (int it = 0; it < CORR_NEWTON_ITERS; ++it) {
-    VS_LAUNCH(h, "k_corr_build", k_corr_build<<<L.M, 256, 0, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
-                                                                          h->scratch, h->cactive));
-    launch_lu(h, "k_lu<KKT>", LuGeo{vi, h->scratch, MatLayout::B, 2, 2, h->cpiv, -1}, 2 * L.nmax + 2, h->cactive);
-    VS_LAUNCH(h, "k_corr_update", k_corr_update<<<L.M, 256, 0, h->stream>>>(vi, h->scratch, h->cpiv, h->corr,
-                                                                            h->cactive));
+  const int n = 2 * L.nmax + 2;
+  const size_t bytes = (size_t)n * n * sizeof(double);
+  if (bytes <= LU_SMEM_MAX) {
+    VS_LAUNCH(h, "k_corr_newton", k_corr_newton<true><<<L.M, 256, bytes, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
+                                                                                    h->scratch, h->cpiv, h->cactive,
+                                                                                    h->dirty, CORR_NEWTON_ITERS, h->xy,
+                                                                                    h->fired, h->err));
+  } else {
+    VS_LAUNCH(h, "k_corr_newton", k_corr_newton<false><<<L.M, 256, 0, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
+                                                                                  h->scratch, h->cpiv, h->cactive,
+                                                                                  h->dirty, CORR_NEWTON_ITERS, h->xy,
+                                                                                  h->fired, h->err));
   }
-  VS_LAUNCH(h, "k_corr_finish", k_corr_finish<<<L.M, NMAX, 0, h->stream>>>(vi, h->corr, h->dirty, h->xy, h->fired,
-                                                                           h->err));
   VS_CK(h, cudaGetLastError(), "correction");
   return VS_OK;
 }
@@ -682,6 +686,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->has_near, L.M));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
+  VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
