@@ -33,6 +33,9 @@ METRIC = "vesicle-steps/s: hybrid vs plain BIE on one B300 at shape error <=1e-2
 UNIT = "vesicle-steps/s"
 MUFU_PER_CLK_SM = 16      # special-function results per clock per SM (4 per sub-partition)
 N_SM = 148
+# DRAM bytes per point of one far-field launch: ncu dram__bytes of k_farfield_f32 on the 1200 x 64 dense
+# Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
+FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 
 
 def parse():
@@ -283,7 +286,8 @@ def run_gpu(args):
         peak_mufu = MUFU_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
         achieved = 2 * pairs / (avg_ms * 1e-3) / 1e12
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_mufu, "unit": "Tmufu/s",
-                "frac": achieved / peak_mufu, "traffic": None,
+                "frac": achieved / peak_mufu, "traffic": FF_DRAM_BYTES_PER_POINT * float(wl.offsets[-1]),
+                "traffic_source": "ncu dram__bytes at 1200 x 64, scaled by points",
                 "peak_source": "16 MUFU/clk/SM x 148 SMs x median SM clock (derived)",
                 "share_of_step": dom_ms / total_prof}
     else:
