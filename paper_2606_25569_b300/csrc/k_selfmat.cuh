@@ -89,6 +89,30 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
     self_store(S, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
 }
 
+// Natural logarithm for the self matrix, table-driven (Tang, ACM TOMS 16, 1990): x = 2^e m with m in [1, 2),
+// c = 1 + (k + 1/2)/128 for k the top 7 fraction bits of m, log x = e ln 2 + log c + log1p(f) with
+// f = (m - c)/c, |f| < 2^-8, and log1p(f) by its Taylor series through f^7 (the next term is below 2^-67).
+// tab[k] = (log c, 1/c) is built on the host. Absolute error below 2e-15 for normal x; other x go to log().
+constexpr int LOG_TAB = 128;
+__device__ __forceinline__ double log_table(double x, const double2* tab) {
+  if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) return log(x);
+  const long long b = __double_as_longlong(x);
+  const int e = (int)(b >> 52) - 1023;
+  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const int k = (int)((b >> 45) & (LOG_TAB - 1));
+  const double2 t = tab[k];
+  const double f = (m - (1.0 + (k + 0.5) / LOG_TAB)) * t.y;  // m - c is exact
+  double p = 1.0 / 7.0;
+  p = fma(p, f, -1.0 / 6.0);
+  p = fma(p, f, 1.0 / 5.0);
+  p = fma(p, f, -0.25);
+  p = fma(p, f, 1.0 / 3.0);
+  p = fma(p, f, -0.5);
+  const double l1 = fma(p * f, f, f);
+  constexpr double LN2_HI = 0x1.62e42p-1, LN2_LO = 0x1.fdf473de6af28p-22;  // LN2_HI * e is exact
+  return fma((double)e, LN2_HI, t.x + fma((double)e, LN2_LO, l1));
+}
+
 __device__ __forceinline__ void self_store_df(float* Sh, float* Sl, int n2, int N, int i, int j, float2 c, float2 lp,
                                               float2 dal, float2 axx, float2 axy, float2 ayy) {
   const float2 sxx = df_mul(c, df_add(lp, df_mul(dal, axx)));
@@ -109,6 +133,7 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
                                                         const double* __restrict__ tx,
                                                         const double* __restrict__ ty,
                                                         const double* __restrict__ tab, double mu,
+                                                        const double2* __restrict__ logtab,
                                                         float* __restrict__ scratch32, int slot,
                                                         const int* __restrict__ active) {
   const int v = blockIdx.y;
@@ -122,11 +147,14 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   __shared__ float2 kl[SM_TILE][SM_TILE + 1], kxx[SM_TILE][SM_TILE + 1], kxy[SM_TILE][SM_TILE + 1],
       kyy[SM_TILE][SM_TILE + 1];
   __shared__ float2 cc[2][SM_TILE];  // sa_j / (4 pi mu) for the tile's columns (0) and its mirror's (1)
+  __shared__ double2 lt[LOG_TAB];
+  for (int e = threadIdx.x; e < LOG_TAB; e += blockDim.x) lt[e] = logtab[e];
   const int li = threadIdx.x / SM_TILE, lj = threadIdx.x % SM_TILE;
   const int64_t o = vi.off[v];
   const double* T = tab + vi.toff[v];
   const double dal64 = 2.0 * VS_PI / N;
   const float2 dal = df_of(dal64);
+  __syncthreads();  // lt
   if (threadIdx.x < 2 * SM_TILE) {
     const int w = threadIdx.x / SM_TILE, jj = (w ? bi : bj) * SM_TILE + threadIdx.x % SM_TILE;
     cc[w][threadIdx.x % SM_TILE] = (jj < N) ? df_of(sa[o + jj] / (4.0 * VS_PI * mu)) : make_float2(0.f, 0.f);
@@ -144,7 +172,7 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
     if (i != j) {
       const double rx = xy[2 * o + i] - xy[2 * o + j];
       const double ry = xy[2 * o + N + i] - xy[2 * o + N + j];
-      lp = df_of(-0.5 * R - 0.5 * dal64 * (log(rx * rx + ry * ry) - T[17 * N + m]));
+      lp = df_of(-0.5 * R - 0.5 * dal64 * (log_table(rx * rx + ry * ry, lt) - T[17 * N + m]));
       const float2 rxd = df_of(rx), ryd = df_of(ry);
       const float2 xx = df_mul(rxd, rxd), xy2 = df_mul(rxd, ryd), yy = df_mul(ryd, ryd);
       const float2 ir2 = df_rcp(df_add(xx, yy));

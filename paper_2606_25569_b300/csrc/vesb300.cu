@@ -110,10 +110,11 @@ struct DevLayout {
   int32_t* chunk = nullptr;
   double* tab = nullptr;
   float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
+  double2* logtab = nullptr;  // (log c_k, 1/c_k), c_k = 1 + (k + 1/2)/LOG_TAB (log_table)
   VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
-    cudaFree(owner); cudaFree(chunk); cudaFree(tab); cudaFree(tab32);
+    cudaFree(owner); cudaFree(chunk); cudaFree(tab); cudaFree(tab32); cudaFree(logtab);
     *this = DevLayout{};
   }
 };
@@ -138,6 +139,13 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   std::vector<float> t32(L.tab.begin(), L.tab.end());
   VS_TRY(dalloc(&D.tab32, t32.size()));
   VS_TRY(upload(D.tab32, t32.data(), t32.size(), s));
+  std::vector<double2> lt(LOG_TAB);
+  for (int k = 0; k < LOG_TAB; ++k) {
+    const long double c = 1.0L + (k + 0.5L) / LOG_TAB;
+    lt[k] = make_double2((double)std::log(c), (double)(1.0L / c));
+  }
+  VS_TRY(dalloc(&D.logtab, LOG_TAB));
+  VS_TRY(upload(D.logtab, lt.data(), LOG_TAB, s));
 #undef VS_TRY
   return cudaStreamSynchronize(s);
 }
@@ -363,7 +371,8 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   const VesIndex vi = h->D.vi();
   if (mixed(h)) {
     VS_LAUNCH(h, "k_self_matrix_df", k_self_matrix_df<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
-                                                                      h->D.tab, h->p.mu, h->scratch32, s, active));
+                                                                      h->D.tab, h->p.mu, h->D.logtab, h->scratch32,
+                                                                      s, active));
   } else {
     VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
                                                                       h->D.tab, h->p.mu, h->scratch, s, active));
