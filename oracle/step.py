@@ -121,23 +121,30 @@ class Suspension:
         u = self.interaction_velocity()
         nxs, nys, nsig, vel = [], [], [], []
         for v, (x, y) in enumerate(zip(self.xs, self.ys)):
-            N = len(x)
             ux, uy = u[v]
-            ubar = np.concatenate([ux, uy])
-            ops_n = Operators(x, y, p.kappa, p.mu)
-            zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
-            if p.relax_net is not None:
-                z1 = relax_learned(zs[:N], zs[N:], p.relax_net)
-            else:
-                z1 = relax_exact(zs[:N], zs[N:], p)
-            xr, yr, alpha = redistribute(z1[:N], z1[N:])
-            uxr, uyr = eval_interpolant(ux, alpha), eval_interpolant(uy, alpha)
-            ops_r = Operators(xr, yr, p.kappa, p.mu)
-            sig = _tension(ops_r, xr, yr, uxr, uyr, p.kappa)
-            xc, yc, fired, _ = _corr.correct(xr, yr, self.A0[v], self.L0[v], tol=p.corr_tol)
+            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], p)
             self.corrections += int(fired)
             nxs.append(xc)
             nys.append(yc)
             nsig.append(sig)
-            vel.append(ubar)
+            vel.append(np.concatenate([ux, uy]))
         self.xs, self.ys, self.sig, self.velocity = nxs, nys, nsig, vel
+
+
+def advance_vesicle(x, y, ux, uy, A0, L0, p):
+    """Steps 3-7 of the module header for one vesicle at X^n = (x, y) given its velocity u^n = (ux, uy):
+    returns (x^{n+1}, y^{n+1}, sigma^{n+1}, correction fired)."""
+    N = len(x)
+    ubar = np.concatenate([ux, uy])
+    ops_n = Operators(x, y, p.kappa, p.mu)
+    zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
+    if p.relax_net is not None:
+        z1 = relax_learned(zs[:N], zs[N:], p.relax_net)
+    else:
+        z1 = relax_exact(zs[:N], zs[N:], p)
+    xr, yr, alpha = redistribute(z1[:N], z1[N:])
+    uxr, uyr = eval_interpolant(ux, alpha), eval_interpolant(uy, alpha)
+    ops_r = Operators(xr, yr, p.kappa, p.mu)
+    sig = _tension(ops_r, xr, yr, uxr, uyr, p.kappa)
+    xc, yc, fired, _ = _corr.correct(xr, yr, A0, L0, tol=p.corr_tol)
+    return xc, yc, sig, fired

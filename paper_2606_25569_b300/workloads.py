@@ -17,28 +17,33 @@ from functools import lru_cache
 import numpy as np
 
 
-def _ellipse_perimeter(a, b, samples=8192):
-    t = np.linspace(0.0, 2.0 * np.pi, samples + 1)
-    return float(np.sum(np.hypot(np.diff(a * np.cos(t)), np.diff(b * np.sin(t)))))
+def _ellipse_perimeter(a, b):
+    """Perimeter 4 a E(1 - b^2/a^2) of the ellipse with semi-axes a >= b (complete elliptic integral)."""
+    from scipy.special import ellipe
+    return float(4.0 * a * ellipe(1.0 - (b / a) ** 2))
 
 
-@lru_cache(maxsize=4096)
+@lru_cache(maxsize=65536)
+def _aspect(nu):
+    """q = a/b of the ellipse with reduced area nu (nu does not depend on the size), by bisection."""
+    lo, hi = 1.0, 400.0
+    for _ in range(80):
+        q = 0.5 * (lo + hi)
+        L = _ellipse_perimeter(np.sqrt(q), 1.0 / np.sqrt(q))
+        if 4.0 * np.pi * np.pi / (L * L) > nu:
+            lo = q
+        else:
+            hi = q
+    return 0.5 * (lo + hi)
+
+
 def ellipse_axes(nu, R):
     """Semi-axes (a, b), a >= b, of the ellipse with area pi R^2 and reduced area nu."""
     if not (0.0 < nu <= 1.0):
         raise ValueError("reduced area must be in (0, 1]")
     if nu == 1.0:
         return R, R
-    lo, hi = 1.0, 400.0
-    for _ in range(80):
-        q = 0.5 * (lo + hi)
-        a, b = R * np.sqrt(q), R / np.sqrt(q)
-        L = _ellipse_perimeter(a, b)
-        if 4.0 * np.pi * np.pi * R * R / (L * L) > nu:
-            lo = q
-        else:
-            hi = q
-    q = 0.5 * (lo + hi)
+    q = _aspect(float(nu))
     return R * np.sqrt(q), R / np.sqrt(q)
 
 
