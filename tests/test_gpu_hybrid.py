@@ -79,3 +79,39 @@ def test_hybrid_step_matches_oracle():
         err = rel_err_per_vesicle(gx, gy, o.xs, o.ys)
         # bf16 network output (relative ~1e-3) enters X through scale * output only
         assert err <= 1e-8, err
+
+
+def test_trained_network_beats_the_step_without_it():
+    """What the learned relaxation gains: trained on the GPU by the library's own kernels on pairs the
+    exact relaxation map produces, the network's relaxation displacement on held-out shapes is far
+    closer to the exact one than leaving the shape unrelaxed (relative error 1 by definition)."""
+    from paper_2606_25569_b300.train import relative_errors, train_relaxation
+    N, M, sets = 64, 512, 32
+    kmax = 16
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(21)
+    X = torch.empty(sets * M, 2 * N, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    g = None
+    for k in range(sets):
+        xs, ys = [], []
+        for v in range(M):
+            x, y = vesicle_outline(N, float(rng.uniform(0.6, 0.95)), 1.0, 5e-2, rng, rng.uniform(0, 2 * np.pi))
+            xs.append(x + 3.0 * (v % 32))
+            ys.append(y + 3.0 * (v // 32))
+        if g is None:
+            g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.0, dt=5e-3, stream=stream)
+        g.training_pairs(torch.as_tensor(csr(xs, ys), device="cuda"), X[k * M:(k + 1) * M], Y[k * M:(k + 1) * M],
+                         1.0, kmax)
+    g.sync()
+    g.close()
+    res = train_relaxation(X, Y, hidden=(512, 512), epochs=300, batch=512, lr=1e-3, lr_min=1e-5,
+                           holdout=1.0 / sets, seed=0, stream=stream)
+    print("learned relaxation: held-out relative error mean %.3f median %.3f (train %.3f), %d steps, %.1f s"
+          % (np.mean(res["holdout_err"]), np.median(res["holdout_err"]), np.mean(res["train_err"]), res["steps"],
+             res["train_seconds"]))
+    held = res["holdout_err"]
+    assert len(held) == M
+    # the same shapes without the network: zero displacement, relative error exactly 1
+    assert float(np.mean(held)) <= 0.5, float(np.mean(held))
+    assert float(np.median(held)) <= 0.5
