@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
+    ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     return ap.parse_args()
 
 
@@ -59,7 +61,8 @@ def workload(args):
 def config_of(wl, args, extra=None):
     c = {"workload": "dense Poiseuille suspension, %d vesicles x %d points, 30%% area fraction, "
                      "channel width 1, reduced area 0.65, Ca 2, Cn 0.025" % (wl.M, args.N),
-         "mode": "plain BIE step (hybrid learned step not built)", "near_field": "mask + five-layer RBF correction (exact layer velocities)",
+         "mode": "plain BIE step (value); the hybrid learned-relaxation step is reported under 'hybrid'",
+         "near_field": "mask + five-layer RBF correction (exact layer velocities)",
          "dt": wl.dt, "farfield": "fp32 compensated", "l2": "working set > L2 (no flush needed)",
          "launch": "each step replayed from a captured CUDA graph"}
     if extra:
@@ -217,6 +220,65 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def hybrid_arm(wl, args, stream):
+    """The hybrid step (learned relaxation, everything else exact) against the plain step from the same
+    state: a network trained on the GPU on exact relaxation pairs of a differently seeded suspension,
+    then both suspensions stepped args.hybrid_steps steps; the shape error is the mean over vesicles of
+    the centred relative error (App. B), and the hybrid throughput is timed with CUDA events."""
+    import torch
+    from paper_2606_25569_b300 import binding, train
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    kmax = 16
+    t0 = time.time()
+    X, Y = train.relaxation_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 8, 4, stream, kmax)
+    r = train.train_relaxation(X, Y, hidden=(512, 512, 512), epochs=120, batch=1024, lr=1e-3, lr_min=1e-5,
+                               stream=stream, serve_batch=wl.M)
+    t_train = time.time() - t0
+    kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
+              near_field=True, stream=stream, use_graph=True)
+    plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
+    hyb = binding.Suspension(wl.flat_xy(), wl.offsets, mode=1, **kw)
+    hyb.set_network(r["net"], r["scale"], kmax)
+    out = {"net": {"dims": r["dims"], "train_samples": int(X.shape[0]), "train_steps": r["steps"],
+                   "holdout_rel_err_mean": float(np.mean(r["holdout_err"])), "train_seconds": round(t_train, 1),
+                   "input_filter_kmax": kmax}}
+    # throughput of the hybrid step
+    hyb.step(3)
+    hyb.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hyb.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out.update({"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms})
+    hyb.close()
+    # shape error against the plain step from the same initial state
+    hyb = binding.Suspension(wl.flat_xy(), wl.offsets, mode=1, **kw)
+    hyb.set_network(r["net"], r["scale"], kmax)
+    done, errs, failed = 0, {}, None
+    for S in sorted({min(k, args.hybrid_steps) for k in (10, 100, 1000, args.hybrid_steps)}):
+        try:
+            hyb.step(S - done)
+            hyb.sync()
+        except Exception as ex:  # a non-finite hybrid state ends the comparison
+            failed = "step %d..%d: %s" % (done, S, ex)
+            break
+        plain.step(S - done)
+        plain.sync()
+        done = S
+        e, _ = train.centred_shape_error(hyb.positions(), plain.positions(), wl.counts)
+        errs[str(S)] = float(np.mean(e))
+    plain.close()
+    hyb.close()
+    last = errs.get(str(args.hybrid_steps))
+    out.update({"shape_error_mean_by_step": errs, "after_steps": args.hybrid_steps,
+                "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2)})
+    if failed:
+        out["failed"] = failed
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2606_25569_b300 import build as _build
@@ -318,6 +380,9 @@ def run_gpu(args):
                "note": "per step: vs_set_state (positions + tension from pinned host), vs_step, "
                        "vs_get_positions + vs_get_tension to pinned host; wall clock"}
 
+    hybrid = None
+    if rank == 0 and not args.no_hybrid:
+        hybrid = hybrid_arm(wl, args, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(wl)
@@ -328,6 +393,7 @@ def run_gpu(args):
                 "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU"}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
+                "hybrid": hybrid,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -60,10 +60,11 @@ def relative_errors(net, X, Y, batch):
 
 
 def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, lr_min=1e-5, beta=0.1,
-                     holdout=0.1, seed=0, stream=None, ncomp=2):
+                     holdout=0.1, seed=0, stream=None, ncomp=2, serve_batch=0):
     """Train on (X, Y); the last `holdout` fraction is held out. AdamW starts at lr (Sec. 3.4.2:
-    1e-3) and decays on a cosine to lr_min over the epochs. Returns a dict with the network, its
-    output scale, the loss history, held-out errors and timings."""
+    1e-3) and decays on a cosine to lr_min over the epochs. The network can afterwards run batches of
+    up to max(batch, serve_batch) rows (a suspension needs at least its vesicle count). Returns a dict
+    with the network, its output scale, the loss history, held-out errors and timings."""
     import torch
     n = X.shape[0]
     nh = int(round(holdout * n))
@@ -71,7 +72,7 @@ def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e
     scale = float(torch.sqrt(torch.mean(Y[:ntr].double() ** 2)).item())
     Yn = (Y / scale).contiguous()
     dims = [X.shape[1]] + list(hidden) + [Y.shape[1]]
-    net = binding.Mlp(dims, max_batch=batch, ncomp=ncomp, beta=beta, stream=stream)
+    net = binding.Mlp(dims, max_batch=max(batch, serve_batch), ncomp=ncomp, beta=beta, stream=stream)
     net.set_params(he_uniform(dims, np.random.default_rng(seed)))
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
