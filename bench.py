@@ -297,6 +297,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
                            flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True)
+    fv = s.farfield_variant()
     for _ in range(max(args.warmup, 3)):
         s.step(1)
     s.sync()
@@ -390,7 +391,9 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU"}),
+                "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU",
+                                               "farfield_launch": "%d threads x %d staged source points per CTA "
+                                                                  "(autotuned at create)" % (fv[1], fv[2])}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
                 "hybrid": hybrid,

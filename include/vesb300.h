@@ -66,6 +66,9 @@ typedef struct {
  * precision (FP32 products and factorisations refined to FP64 accuracy by matrix-free FP64
  * residuals). Both give the FP64 solution; the default is several times faster on B300. */
 #define VS_FLAG_DIRECT_FP64 2ull
+/* Keep the default FP32 far-field launch shape instead of timing the shapes at vs_create
+ * (vs_farfield_variant). */
+#define VS_FLAG_NO_AUTOTUNE 4ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */
@@ -135,6 +138,16 @@ vs_status vs_get_device_ptrs(const vs_suspension* s, const double** xy, const do
  * vesicle) pairs in the last far-field evaluation (when near_field), [3] device error bits,
  * [4] kernels launched by this handle so far. Synchronises. */
 vs_status vs_get_counters(vs_suspension* s, int64_t* out5);
+
+/* FP32 far-field launch shape; the paper has no counterpart (a tuning control). vs_create times the
+ * far-field kernel in each of its launch shapes (threads per CTA x source points staged per chunk)
+ * on the suspension's own sources and keeps the fastest, unless VS_FLAG_NO_AUTOTUNE is set; the
+ * choice is cached per (device name, M, points, near mask) in the process, and in the text file
+ * named by the environment variable VS_TUNE_CACHE when it is set. Every shape gives bitwise
+ * identical velocities. set >= 0 selects shape `set` (captured step graphs are dropped), set < 0
+ * leaves it. On return *index, *threads and *chunk (each may be null) describe the shape in use.
+ * VS_ERR_INVALID_ARG for a null handle or set beyond the last shape. */
+vs_status vs_farfield_variant(vs_suspension* s, int32_t set, int32_t* index, int32_t* threads, int32_t* chunk);
 
 /* Per-kernel timing: while enabled, every kernel the handle launches is bracketed by CUDA
  * events on its stream. vs_profile(s, 1) clears the totals and starts recording, 0 stops.

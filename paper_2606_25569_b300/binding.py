@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libvesb300.so")
 
 VS_FLAG_FARFIELD_FP64 = 1
 VS_FLAG_DIRECT_FP64 = 2
+VS_FLAG_NO_AUTOTUNE = 4
 
 STATUS = {0: "VS_OK", 1: "VS_ERR_INVALID_ARG", 2: "VS_ERR_CUDA", 3: "VS_ERR_NOMEM",
           4: "VS_ERR_NOT_CONVERGED", 5: "VS_ERR_UNSTABLE", 6: "VS_ERR_TIMEOUT", 7: "VS_ERR_NO_NETWORK"}
@@ -30,6 +31,8 @@ FUNCTIONS = {
     "vs_get_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vs_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "vs_farfield_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "vs_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double,
@@ -124,14 +127,15 @@ class Suspension:
 
     def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
                  flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0,
-                 use_graph=False, direct_fp64=False):
+                 use_graph=False, direct_fp64=False, autotune=True):
         L = lib()
         self._h = ctypes.c_void_p()
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self.M = len(off) - 1
         self.P = int(off[-1])
-        flags = (VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0) | (VS_FLAG_DIRECT_FP64 if direct_fp64 else 0)
+        flags = ((VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0) | (VS_FLAG_DIRECT_FP64 if direct_fp64 else 0)
+                 | (0 if autotune else VS_FLAG_NO_AUTOTUNE))
         p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0, 0, flags)
         f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
         st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),
@@ -171,6 +175,13 @@ class Suspension:
     def reference(self):
         r = self._get(lib().vs_get_reference, 2 * self.M)
         return r[:self.M], r[self.M:]
+
+    def farfield_variant(self, set=-1):
+        """(index, threads per CTA, staged points) of the FP32 far-field launch shape; set >= 0 selects one."""
+        idx, thr, chk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().vs_farfield_variant(self._h, int(set), ctypes.byref(idx), ctypes.byref(thr),
+                                              ctypes.byref(chk)))
+        return idx.value, thr.value, chk.value
 
     def counters(self):
         out = np.zeros(5, dtype=np.int64)

@@ -256,6 +256,38 @@ struct OpA32 {
   }
 };
 
+// N x N blocks inside the FP32 scratch, for the 2 x 2 block inverse of A when 2N exceeds the register
+// Gauss-Jordan: the block starts at `sub` (units of N^2 floats) of the vesicle's scratch, rows are
+// `ld` N floats apart (1: a contiguous N x N matrix, 2: a block of a 2N x 2N matrix), and (bi, bj)
+// selects the block in units of N.
+struct BlkView {
+  int64_t sub;
+  int ld, bi, bj;
+  __device__ __forceinline__ float* at(const OpCtx& c, int v, int N, int i, int j) const {
+    return c.mat32(v, N, sub) + ((int64_t)(bi * N + i) * ld + bj) * N + j;
+  }
+};
+// C = alpha A B (+ D when hasD), all N x N views.
+struct OpBlk32 {
+  using T = float;
+  OpCtx c; BlkView A, B, C, D; float alpha; int hasD;
+  __device__ void dims(int N, int& m, int& n, int& k) const { m = N; n = N; k = N; }
+  __device__ float a(int v, int N, int i, int k) const { return *A.at(c, v, N, i, k); }
+  __device__ float b(int v, int N, int k, int j) const { return *B.at(c, v, N, k, j); }
+  __device__ void store(int v, int N, int i, int j, float acc) const {
+    *C.at(c, v, N, i, j) = hasD ? fmaf(alpha, acc, *D.at(c, v, N, i, j)) : alpha * acc;
+  }
+};
+// dst = src for N x N views; grid (ceil(N^2 / 256), M)
+__global__ void __launch_bounds__(256) k_blk_copy(OpCtx c, BlkView src, BlkView dst) {
+  const int v = blockIdx.y;
+  const int N = c.vi.N[v];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int i = e / N, j = e - (e / N) * N;
+  *dst.at(c, v, N, i, j) = *src.at(c, v, N, i, j);
+}
+
 constexpr int GT = 64;   // output tile
 constexpr int GK = 16;   // k tile
 
@@ -563,42 +595,6 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
       if (i < n && j1 < n) A[(int64_t)rstep[i] * n + pk[j1]] = T[a][h].y;
     }
   if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
-}
-
-// Inverse from a batched LU (pivots applied) for matrices too large for k_gj_inverse: column j of
-// the inverse solves A x = e_j, thread per column, written to the block at `dsub` of the vesicle's
-// scratch (row-major n x n).
-template <class Geo>
-__global__ void __launch_bounds__(256) k_lu_inverse(Geo geo, int64_t dsub, const int* __restrict__ active) {
-  using E = typename Geo::T;
-  const int v = blockIdx.x;
-  if (active && !active[v]) return;
-  const int N = geo.vi.N[v];
-  const int n = geo.n(v);
-  const E* LU = geo.A(v);
-  const int* p = geo.p(v);
-  E* X = geo.scratch + geo.vi.moff[v] + dsub * (int64_t)N * N;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    for (int i = 0; i < n; ++i) X[(int64_t)i * n + j] = (i == j) ? E(1) : E(0);
-    for (int k = 0; k < n; ++k) {
-      const int q = p[k];
-      if (q != k) {
-        const E t = X[(int64_t)k * n + j];
-        X[(int64_t)k * n + j] = X[(int64_t)q * n + j];
-        X[(int64_t)q * n + j] = t;
-      }
-    }
-    for (int i = 1; i < n; ++i) {
-      E s2 = X[(int64_t)i * n + j];
-      for (int k = 0; k < i; ++k) s2 = fma_t(-LU[(int64_t)i * n + k], X[(int64_t)k * n + j], s2);
-      X[(int64_t)i * n + j] = s2;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      E s2 = X[(int64_t)i * n + j];
-      for (int k = i + 1; k < n; ++k) s2 = fma_t(-LU[(int64_t)i * n + k], X[(int64_t)k * n + j], s2);
-      X[(int64_t)i * n + j] = s2 / LU[(int64_t)i * n + i];
-    }
-  }
 }
 
 // Solve LU x = b in place for one vector b in shared memory (length n); warp 0 works, the

@@ -14,13 +14,15 @@
 // the special-function unit.
 //
 // One thread per target; source vesicles are staged through shared memory in chunks of whole
-// vesicles (chunk boundaries precomputed on the host, at most FF_CHUNK points each).
+// vesicles (chunk boundaries precomputed on the host, at most CHUNK points each). THREADS and CHUNK
+// only change the launch shape and the staging: every target sums the same terms in the same order
+// (vesicles ascending), so all instantiations give bitwise identical results (autotuned per suspension).
 #pragma once
 #include "common.cuh"
 
 namespace vs {
 
-constexpr int FF_THREADS = 128;
+constexpr int FF_THREADS = 128;  // default launch shape (far-field plans, the allocation-free entry point)
 constexpr int FF_CHUNK = 2048;
 
 __device__ __forceinline__ float fast_lg2(float x) {
@@ -75,11 +77,12 @@ struct FarFieldArgs {
   unsigned* err;
 };
 
-__global__ void __launch_bounds__(FF_THREADS) k_farfield_f32(FarFieldArgs a, const float4* __restrict__ src,
-                                                             const float4* __restrict__ centre32,
-                                                             const float2* __restrict__ h2) {
-  __shared__ float4 sh[FF_CHUNK];
-  const int64_t t = (int64_t)blockIdx.x * FF_THREADS + threadIdx.x;
+template <int THREADS, int CHUNK>
+__global__ void __launch_bounds__(THREADS) k_farfield_f32(FarFieldArgs a, const float4* __restrict__ src,
+                                                          const float4* __restrict__ centre32,
+                                                          const float2* __restrict__ h2) {
+  __shared__ float4 sh[CHUNK];
+  const int64_t t = (int64_t)blockIdx.x * THREADS + threadIdx.x;
   const bool valid = t < a.P;
   const int tv = valid ? a.owner[t] : -1;
   const float4 ts = valid ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(FF_THREADS) k_farfield_f32(FarFieldArgs a, con
     const int v0 = a.chunk[c], v1 = a.chunk[c + 1];
     const int64_t p0 = a.voff[v0], p1 = a.voff[v1];
     __syncthreads();
-    for (int64_t q = p0 + threadIdx.x; q < p1; q += FF_THREADS) sh[q - p0] = src[q];
+    for (int64_t q = p0 + threadIdx.x; q < p1; q += THREADS) sh[q - p0] = src[q];
     __syncthreads();
     if (!valid) continue;
     for (int sv = v0; sv < v1; ++sv) {

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -38,9 +39,21 @@ struct Layout {
   int nmax = 0;
   std::vector<int32_t> N;
   std::vector<int64_t> off, moff, toff;
-  std::vector<int32_t> owner, chunk;
+  std::vector<int32_t> owner, chunk, chunk1k;  // far-field source chunks of at most 2048 / 1024 points
   std::vector<double> tab;
 };
+
+// Greedy chunks of whole vesicles with at most `limit` points each: boundaries in vesicles.
+std::vector<int32_t> source_chunks(const std::vector<int32_t>& N, int limit) {
+  std::vector<int32_t> c{0};
+  int64_t acc = 0;
+  for (int v = 0; v < (int)N.size(); ++v) {
+    if (acc + N[v] > limit) { c.push_back(v); acc = 0; }
+    acc += N[v];
+  }
+  c.push_back((int32_t)N.size());
+  return c;
+}
 
 bool build_layout(const int64_t* offsets, int M, Layout& L, std::string& msg) {
   if (M < 1 || offsets == nullptr) { msg = "M must be >= 1 and offsets non-null"; return false; }
@@ -78,14 +91,8 @@ bool build_layout(const int64_t* offsets, int M, Layout& L, std::string& msg) {
   L.owner.resize(L.P);
   for (int v = 0; v < M; ++v)
     for (int64_t p = L.off[v]; p < L.off[v + 1]; ++p) L.owner[p] = v;
-  L.chunk.clear();
-  L.chunk.push_back(0);
-  int64_t acc = 0;
-  for (int v = 0; v < M; ++v) {
-    if (acc + L.N[v] > FF_CHUNK) { L.chunk.push_back(v); acc = 0; }
-    acc += L.N[v];
-  }
-  L.chunk.push_back(M);
+  L.chunk = source_chunks(L.N, FF_CHUNK);
+  L.chunk1k = source_chunks(L.N, 1024);
   return true;
 }
 
@@ -108,13 +115,14 @@ struct DevLayout {
   int64_t* toff = nullptr;
   int32_t* owner = nullptr;
   int32_t* chunk = nullptr;
+  int32_t* chunk1k = nullptr;
   double* tab = nullptr;
   float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
   double2* logtab = nullptr;  // (log c_k, 1/c_k), c_k = 1 + (k + 1/2)/LOG_TAB (log_table)
   VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
-    cudaFree(owner); cudaFree(chunk); cudaFree(tab); cudaFree(tab32); cudaFree(logtab);
+    cudaFree(owner); cudaFree(chunk); cudaFree(chunk1k); cudaFree(tab); cudaFree(tab32); cudaFree(logtab);
     *this = DevLayout{};
   }
 };
@@ -128,6 +136,8 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   VS_TRY(dalloc(&D.toff, L.M));
   VS_TRY(dalloc(&D.owner, L.P));
   VS_TRY(dalloc(&D.chunk, L.chunk.size()));
+  VS_TRY(dalloc(&D.chunk1k, L.chunk1k.size()));
+  VS_TRY(upload(D.chunk1k, L.chunk1k.data(), L.chunk1k.size(), s));
   VS_TRY(dalloc(&D.tab, L.tab.size()));
   VS_TRY(upload(D.N, L.N.data(), L.M, s));
   VS_TRY(upload(D.off, L.off.data(), L.M + 1, s));
@@ -253,6 +263,7 @@ struct vs_suspension {
   Prof prof;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one captured step per operator-slot parity
   int64_t graph_launches[2] = {0, 0};
+  int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
   std::string msg;
 };
 
@@ -402,17 +413,119 @@ vs_status geometry(vs_suspension* h, const double* xy, bool with_force) {
   return VS_OK;
 }
 
+// Launch shapes of the FP32 far field (threads per CTA, source points staged per chunk). All give the
+// same result bit for bit; the fastest for a suspension is picked by tune_far_field.
+struct FfVariant {
+  int threads, chunk;
+};
+constexpr FfVariant FF_VARIANTS[] = {{128, 2048}, {64, 2048}, {256, 2048}, {128, 1024}, {64, 1024}, {32, 1024}};
+constexpr int FF_NVARIANTS = (int)(sizeof(FF_VARIANTS) / sizeof(FF_VARIANTS[0]));
+
+void launch_far_field_f32(const vs_suspension* h, int var, FarFieldArgs a) {
+  const FfVariant fv = FF_VARIANTS[var];
+  const bool big = fv.chunk == 2048;
+  a.chunk = big ? h->D.chunk : h->D.chunk1k;
+  a.nchunk = (int)(big ? h->L.chunk.size() : h->L.chunk1k.size()) - 1;
+  const int grid = (int)((h->L.P + fv.threads - 1) / fv.threads);
+  const float4* src = h->B.src;
+  const float4* c32 = h->B.centre32;
+  const float2* h2 = h->B.h2;
+  cudaStream_t st = h->stream;
+  switch (var) {
+    case 0: k_farfield_f32<128, 2048><<<grid, 128, 0, st>>>(a, src, c32, h2); break;
+    case 1: k_farfield_f32<64, 2048><<<grid, 64, 0, st>>>(a, src, c32, h2); break;
+    case 2: k_farfield_f32<256, 2048><<<grid, 256, 0, st>>>(a, src, c32, h2); break;
+    case 3: k_farfield_f32<128, 1024><<<grid, 128, 0, st>>>(a, src, c32, h2); break;
+    case 4: k_farfield_f32<64, 1024><<<grid, 64, 0, st>>>(a, src, c32, h2); break;
+    default: k_farfield_f32<32, 1024><<<grid, 32, 0, st>>>(a, src, c32, h2); break;
+  }
+}
+
+FarFieldArgs far_field_args(vs_suspension* h) {
+  const Layout& L = h->L;
+  return FarFieldArgs{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1,
+                      h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
+}
+
 vs_status far_field(vs_suspension* h) {
   const Layout& L = h->L;
   if (L.M < 2) return VS_OK;
-  FarFieldArgs a{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1,
-                 h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
-  const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
-  if (h->p.flags & VS_FLAG_FARFIELD_FP64)
+  const FarFieldArgs a = far_field_args(h);
+  if (h->p.flags & VS_FLAG_FARFIELD_FP64) {
+    const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
     VS_LAUNCH(h, "k_farfield_f64", k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N));
-  else
-    VS_LAUNCH(h, "k_farfield_f32", k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2));
+  } else {
+    VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
+  }
   VS_CK(h, cudaGetLastError(), "far field");
+  return VS_OK;
+}
+
+// Autotuner of the FP32 far-field launch shape: every variant timed on the suspension's own sources
+// (CUDA events, best of two launches after one warm-up), the fastest kept. Results are cached per
+// (device name, M, points, near mask) for the process, and in the text file named by VS_TUNE_CACHE
+// when that variable is set (one "key variant" line per entry). The far field writes only the
+// velocity accumulator and near lists, which every step rebuilds; the caller refreshes them.
+std::map<std::string, int>& tune_cache() {
+  static std::map<std::string, int> c;
+  return c;
+}
+
+vs_status tune_far_field(vs_suspension* h) {
+  const Layout& L = h->L;
+  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE))) return VS_OK;
+  int dev = 0;
+  VS_CK(h, cudaGetDevice(&dev), "autotune");
+  cudaDeviceProp prop;
+  VS_CK(h, cudaGetDeviceProperties(&prop, dev), "autotune");
+  char key[512];
+  snprintf(key, sizeof key, "%s|M=%d|P=%lld|near=%d", prop.name, L.M, (long long)L.P, h->p.near_field ? 1 : 0);
+  for (char* c = key; *c; ++c)
+    if (*c == ' ') *c = '_';
+  auto& cache = tune_cache();
+  const char* path = std::getenv("VS_TUNE_CACHE");
+  if (!cache.count(key) && path) {
+    if (FILE* f = std::fopen(path, "r")) {
+      char k[512];
+      int var = 0;
+      while (std::fscanf(f, "%511s %d", k, &var) == 2)
+        if (var >= 0 && var < FF_NVARIANTS) cache[k] = var;
+      std::fclose(f);
+    }
+  }
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    h->ff_variant = it->second;
+    return VS_OK;
+  }
+  const FarFieldArgs a = far_field_args(h);
+  cudaEvent_t e0, e1;
+  VS_CK(h, cudaEventCreate(&e0), "autotune");
+  VS_CK(h, cudaEventCreate(&e1), "autotune");
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int var = 0; var < FF_NVARIANTS; ++var) {
+    launch_far_field_f32(h, var, a);
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      launch_far_field_f32(h, var, a);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = var; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  VS_CK(h, cudaGetLastError(), "autotune");
+  h->ff_variant = best;
+  cache[key] = best;
+  if (path)
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d\n", key, best);
+      std::fclose(f);
+    }
   return VS_OK;
 }
 
@@ -437,12 +550,25 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
     VS_LAUNCH(h, "k_bgemm<OpW32>", k_bgemm<OpW32><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpW32{c, s}, nullptr));
     VS_LAUNCH(h, "k_bgemm<OpA32>", k_bgemm<OpA32><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA32{c, s, h->p.dt}, nullptr));
     const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
-    int64_t ainv = MatLayout::A;
+    const int64_t ainv = MatLayout::A;
     if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, nullptr)) {
-      // too large for registers: LU, then the inverse by substitution into the (now free) B block
-      launch_lu(h, "k_lu32<A>", ga, 2 * n, nullptr);
-      VS_LAUNCH(h, "k_lu_inverse32<A>", k_lu_inverse<LuGeo32><<<M, 256, 0, h->stream>>>(ga, MatLayout::B, nullptr));
-      ainv = MatLayout::B;
+      // 2N beyond the register Gauss-Jordan: the 2 x 2 block (Schur complement) inverse in place,
+      // A = [A11 A12; A21 A22], X1 = A11^{-1}, Y = X1 A12, Z = A21 X1, S = A22 - A21 Y,
+      // A^{-1} = [X1 - C12 Z, C12; -S^{-1} Z, S^{-1}] with C12 = -Y S^{-1}; X1, Y, Z, S^{-1} in the free B block
+      const int64_t Bq = MatLayout::B;
+      const BlkView A11{MatLayout::A, 2, 0, 0}, A12{MatLayout::A, 2, 0, 1}, A21{MatLayout::A, 2, 1, 0},
+          A22{MatLayout::A, 2, 1, 1}, X1{Bq, 1, 0, 0}, Y{Bq + 1, 1, 0, 0}, Z{Bq + 2, 1, 0, 0}, Si{Bq + 3, 1, 0, 0};
+      const dim3 gcopy((n * n + 255) / 256, M), gb = gemm_grid(n, n, M);
+      VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, A11, X1));
+      launch_gj32(h, "k_gj_inverse<A11>", LuGeo32{vi, h->scratch32, Bq, 1, 0, h->piv32, 2}, n, nullptr);
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, X1, A12, Y, Y, 1.f, 0}, nullptr));
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A21, X1, Z, Z, 1.f, 0}, nullptr));
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A21, Y, Si, A22, -1.f, 1}, nullptr));
+      launch_gj32(h, "k_gj_inverse<S>", LuGeo32{vi, h->scratch32, Bq + 3, 1, 0, h->piv32, 2}, n, nullptr);
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, Y, Si, A12, A12, -1.f, 0}, nullptr));
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, Si, Z, A21, A21, -1.f, 0}, nullptr));
+      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, nullptr));
+      VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
     }
     VS_LAUNCH(h, "k_relax_mp", k_relax_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
                                                                    h->scratch32, s, ainv, h->p.kappa_b, h->p.dt, xo, h->err));
@@ -694,7 +820,6 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
-  VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
@@ -729,6 +854,8 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
   if (tension(h, h->u, 0) != VS_OK) return fail(VS_ERR_CUDA);
   VS_A(cudaGetLastError());
+  if (tune_far_field(h) != VS_OK) return fail(VS_ERR_CUDA);
+  if (geometry(h, h->xy, true) != VS_OK) return fail(VS_ERR_CUDA);  // u back to u_inf after tuning
   h->cur = 0;
   VS_A(cudaStreamSynchronize(h->stream));
 #undef VS_A
@@ -815,6 +942,18 @@ vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
   out4[2] = pairs;
   out4[3] = e;
   out4[4] = h->launches;
+  return VS_OK;
+}
+
+vs_status vs_farfield_variant(vs_suspension* h, int32_t set, int32_t* index, int32_t* threads, int32_t* chunk) {
+  if (!h || set >= FF_NVARIANTS) return VS_ERR_INVALID_ARG;
+  if (set >= 0 && set != h->ff_variant) {
+    h->ff_variant = set;
+    drop_graphs(h);
+  }
+  if (index) *index = h->ff_variant;
+  if (threads) *threads = FF_VARIANTS[h->ff_variant].threads;
+  if (chunk) *chunk = FF_VARIANTS[h->ff_variant].chunk;
   return VS_OK;
 }
 
@@ -938,7 +1077,7 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
   if (h->precision == 1)
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
   else
-    k_farfield_f32<<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+    k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
   VS_CK(h, cudaGetLastError(), "far field");
   return VS_OK;
 }
@@ -1439,7 +1578,7 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
     if (precision == 1)
       k_farfield_f64<<<grid, FF_THREADS, 0, st>>>(a, xy, fo.g64, g.length, vi.N);
     else
-      k_farfield_f32<<<grid, FF_THREADS, 0, st>>>(a, fo.src, fo.centre32, fo.h2);
+      k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, st>>>(a, fo.src, fo.centre32, fo.h2);
   }
   return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ERR_CUDA;
 }
