@@ -26,7 +26,9 @@
 namespace vs {
 
 constexpr int MP_MAXIT = 10;
-constexpr int MP_THREADS = 128;  // small CTAs: many vesicles per SM hide the global-memory latency
+// CTA sizes of the refinement kernels: 128 threads when there are many vesicles per SM to hide the
+// memory latency, 256 when a few large vesicles leave the SMs short of work (mp_threads)
+constexpr int MP_THREADS = 128, MP_THREADS_WIDE = 256;
 constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10;
 enum : unsigned { ERR_REFINE = 32u };
 
@@ -248,7 +250,8 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
 }
 
 // X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s.
-__global__ void __launch_bounds__(MP_THREADS) k_advect_mp(VesIndex vi, const double* __restrict__ xy,
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_advect_mp(VesIndex vi, const double* __restrict__ xy,
                                                    const double* __restrict__ u, const double* __restrict__ sa,
                                                    const double* __restrict__ tx, const double* __restrict__ ty,
                                                    const double* __restrict__ tab,
@@ -276,7 +279,8 @@ __global__ void __launch_bounds__(MP_THREADS) k_advect_mp(VesIndex vi, const dou
 }
 
 // sigma = -L^{-1} P (B X + u) at slot s (Eq. tension_disc), B X = -kappa S X_ssss.
-__global__ void __launch_bounds__(MP_THREADS) k_tension_mp(VesIndex vi, const double* __restrict__ bx,
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tension_mp(VesIndex vi, const double* __restrict__ bx,
                                                     const double* __restrict__ by, const double* __restrict__ u,
                                                     const double* __restrict__ sa, const double* __restrict__ tx,
                                                     const double* __restrict__ ty, const double* __restrict__ tab,
@@ -307,7 +311,8 @@ __global__ void __launch_bounds__(MP_THREADS) k_tension_mp(VesIndex vi, const do
 
 // Relaxation (Eq. relaxation_disc) by refinement of the coupled (x, sigma) system at slot s. The
 // iterate x is kept relative to the mean point of X* (the operators only see its derivatives).
-__global__ void __launch_bounds__(MP_THREADS) k_relax_mp(VesIndex vi, const double* __restrict__ xy_star,
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double* __restrict__ xy_star,
                                                   const double* __restrict__ sa, const double* __restrict__ tx,
                                                   const double* __restrict__ ty, const double* __restrict__ tab,
                                                   const float* __restrict__ scratch32, int s, int64_t ainv_sub,

@@ -372,6 +372,10 @@ inline dim3 gemm_grid(int m, int n, int M) { return dim3((n + GT - 1) / GT, (m +
 
 FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
 
+// Refinement kernels: 256 threads per vesicle when the vesicles are large or too few to give every SM
+// several, else 128.
+inline bool mp_wide(const vs_suspension* h) { return h->L.nmax > 64 || h->L.M < 4 * 148; }
+
 // Mixed precision (default): FP32 operator products and factorisations refined in FP64.
 inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
 
@@ -570,8 +574,14 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
       VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, nullptr));
       VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
     }
-    VS_LAUNCH(h, "k_relax_mp", k_relax_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                   h->scratch32, s, ainv, h->p.kappa_b, h->p.dt, xo, h->err));
+    if (mp_wide(h))
+      VS_LAUNCH(h, "k_relax_mp", k_relax_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
+                                     vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv, h->p.kappa_b,
+                                     h->p.dt, xo, h->err));
+    else
+      VS_LAUNCH(h, "k_relax_mp", k_relax_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
+                                     vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv, h->p.kappa_b,
+                                     h->p.dt, xo, h->err));
     VS_CK(h, cudaGetLastError(), "relaxation");
     return VS_OK;
   }
@@ -593,9 +603,14 @@ vs_status tension(vs_suspension* h, const double* u, int s) {
   const VesIndex vi = h->D.vi();
   const int M = h->L.M;
   if (mixed(h)) {
-    VS_LAUNCH(h, "k_tension_mp", k_tension_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty,
-                                                                       h->D.tab, h->scratch32, s,
-                                                                       h->p.kappa_b, h->sigma, h->err));
+    if (mp_wide(h))
+      VS_LAUNCH(h, "k_tension_mp", k_tension_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
+                                       vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
+                                       h->p.kappa_b, h->sigma, h->err));
+    else
+      VS_LAUNCH(h, "k_tension_mp", k_tension_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
+                                       vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
+                                       h->p.kappa_b, h->sigma, h->err));
   } else {
     VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
                                                                  h->piv, h->p.kappa_b, h->sigma));
@@ -681,9 +696,14 @@ vs_status step_once(vs_suspension* h) {
   if (h->p.near_field && L.M > 1 && (st = near_field(h, cur)) != VS_OK) return st;
   // (4) advection
   if (mixed(h)) {
-    VS_LAUNCH(h, "k_advect_mp", k_advect_mp<<<M, MP_THREADS, 0, h->stream>>>(vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                                     h->scratch32, cur, h->p.dt,
-                                                                     h->xy_star, h->err));
+    if (mp_wide(h))
+      VS_LAUNCH(h, "k_advect_mp", k_advect_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
+                                      vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, cur, h->p.dt,
+                                      h->xy_star, h->err));
+    else
+      VS_LAUNCH(h, "k_advect_mp", k_advect_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
+                                      vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, cur, h->p.dt,
+                                      h->xy_star, h->err));
   } else {
     VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
                                                                h->xy_star));
