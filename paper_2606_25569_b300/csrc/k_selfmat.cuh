@@ -89,28 +89,30 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
     self_store(S, n2, N, i, j, sa[o + j] * c0, kl[lj][li], dal, kxx[lj][li], kxy[lj][li], kyy[lj][li]);
 }
 
-// Natural logarithm for the self matrix, table-driven (Tang, ACM TOMS 16, 1990): x = 2^e m with m in [1, 2),
-// c = 1 + (k + 1/2)/128 for k the top 7 fraction bits of m, log x = e ln 2 + log c + log1p(f) with
-// f = (m - c)/c, |f| < 2^-8, and log1p(f) by its Taylor series through f^7 (the next term is below 2^-67).
-// tab[k] = (log c, 1/c) is built on the host. Absolute error below 2e-15 for normal x; other x go to log().
-constexpr int LOG_TAB = 128;
-__device__ __forceinline__ double log_table(double x, const double2* tab) {
-  if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) return log(x);
-  const long long b = __double_as_longlong(x);
-  const int e = (int)(b >> 52) - 1023;
-  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
-  const int k = (int)((b >> 45) & (LOG_TAB - 1));
-  const double2 t = tab[k];
-  const double f = (m - (1.0 + (k + 0.5) / LOG_TAB)) * t.y;  // m - c is exact
-  double p = 1.0 / 7.0;
-  p = fma(p, f, -1.0 / 6.0);
-  p = fma(p, f, 1.0 / 5.0);
-  p = fma(p, f, -0.25);
-  p = fma(p, f, 1.0 / 3.0);
-  p = fma(p, f, -0.5);
-  const double l1 = fma(p * f, f, f);
-  constexpr double LN2_HI = 0x1.62e42p-1, LN2_LO = 0x1.fdf473de6af28p-22;  // LN2_HI * e is exact
-  return fma((double)e, LN2_HI, t.x + fma((double)e, LN2_LO, l1));
+constexpr int LOG_TAB = 512;
+
+// Natural logarithm of a double-float x = (hi, lo) > 0 with a normal hi, table-driven (Tang, ACM TOMS 16,
+// 1990): x = 2^e (m_hi + m_lo) with m_hi in [1, 2) the scaled hi, c = 1 + (k + 1/2)/LOG_TAB for k the top
+// 9 fraction bits of m_hi, log x = e ln 2 + log c + log1p(f) with f = (m - c)/c in double-float
+// (|f| <= 2^-10) and log1p(f) = f - f^2/2 + f^3 (1/3 - f/4 + f^2/5): the cubic part is below 2^-30, so
+// plain FP32 carries it, and the next term is below 2^-62. ltd[k] = (log c hi, log c lo, 1/c hi,
+// 1/c lo) is built on the host. About 47 significant bits.
+__device__ __forceinline__ float2 log_df(float2 x, const float4* ltd) {
+  const unsigned b = __float_as_uint(x.x);
+  const int e = (int)((b >> 23) & 255u) - 127;
+  const int k = (int)((b >> 14) & (unsigned)(LOG_TAB - 1));
+  const float mh = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+  const float ml = ldexpf(x.y, -e);
+  const float c = 1.0f + (k + 0.5f) / LOG_TAB;  // exact: 10 fraction bits
+  const float4 t = ltd[k];
+  const float2 f = df_mul(two_sum(__fsub_rn(mh, c), ml), make_float2(t.z, t.w));  // mh - c is exact
+  const float fx = f.x;
+  const float cubic = fx * fx * fx * fmaf(fx, fmaf(fx, 0.2f, -0.25f), 1.0f / 3.0f);
+  const float2 f2 = df_mul(f, f);
+  const float2 l1 = df_add(f, two_sum(-0.5f * f2.x, fmaf(-0.5f, f2.y, cubic)));
+  constexpr float LN2_H = (float)0.69314718055994530942, LN2_L = (float)(0.69314718055994530942 - (double)LN2_H);
+  const float2 eln2 = df_mul(make_float2((float)e, 0.f), make_float2(LN2_H, LN2_L));
+  return df_add(df_add(eln2, make_float2(t.x, t.y)), l1);
 }
 
 __device__ __forceinline__ void self_store_df(float* Sh, float* Sl, int n2, int N, int i, int j, float2 c, float2 lp,
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
                                                         const double* __restrict__ tx,
                                                         const double* __restrict__ ty,
                                                         const double* __restrict__ tab, double mu,
-                                                        const double2* __restrict__ logtab,
+                                                        const float4* __restrict__ logtab,
                                                         float* __restrict__ scratch32, int slot,
                                                         const int* __restrict__ active) {
   const int v = blockIdx.y;
@@ -147,7 +149,9 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   __shared__ float2 kl[SM_TILE][SM_TILE + 1], kxx[SM_TILE][SM_TILE + 1], kxy[SM_TILE][SM_TILE + 1],
       kyy[SM_TILE][SM_TILE + 1];
   __shared__ float2 cc[2][SM_TILE];  // sa_j / (4 pi mu) for the tile's columns (0) and its mirror's (1)
-  __shared__ double2 lt[LOG_TAB];
+  __shared__ float2 pr[2][2][SM_TILE];  // [rows, cols][x, y]: points of the tile relative to point 0
+  __shared__ float4 lt[LOG_TAB];
+  __shared__ float2 am[2 * SM_TILE];  // the table's log constant at m = (bi - bj) 16 + d, d = -15..16
   for (int e = threadIdx.x; e < LOG_TAB; e += blockDim.x) lt[e] = logtab[e];
   const int li = threadIdx.x / SM_TILE, lj = threadIdx.x % SM_TILE;
   const int64_t o = vi.off[v];
@@ -158,7 +162,18 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   if (threadIdx.x < 2 * SM_TILE) {
     const int w = threadIdx.x / SM_TILE, jj = (w ? bi : bj) * SM_TILE + threadIdx.x % SM_TILE;
     cc[w][threadIdx.x % SM_TILE] = (jj < N) ? df_of(sa[o + jj] / (4.0 * VS_PI * mu)) : make_float2(0.f, 0.f);
+  } else if (threadIdx.x < 6 * SM_TILE) {
+    const int e = threadIdx.x - 2 * SM_TILE, w = e / (2 * SM_TILE), comp = (e / SM_TILE) & 1, l = e % SM_TILE;
+    const int k = (w ? bj : bi) * SM_TILE + l;
+    const double* X = xy + 2 * o + comp * N;
+    pr[w][comp][l] = (k < N) ? df_of(X[k] - X[0]) : make_float2(0.f, 0.f);
+  } else if (threadIdx.x < 8 * SM_TILE) {
+    const int d = threadIdx.x - 6 * SM_TILE - (SM_TILE - 1);
+    int m = ((bi - bj) * SM_TILE + d) % N;
+    if (m < 0) m += N;
+    am[d + SM_TILE - 1] = df_of(T[17 * N + m]);
   }
+  __syncthreads();
   const int64_t NN = (int64_t)N * N;
   float* Sh = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * NN;
   float* Sl = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::SL) * NN;
@@ -170,12 +185,12 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
     const int m = (i - j < 0) ? i - j + N : i - j;
     const double R = T[N + m];
     if (i != j) {
-      const double rx = xy[2 * o + i] - xy[2 * o + j];
-      const double ry = xy[2 * o + N + i] - xy[2 * o + N + j];
-      lp = df_of(-0.5 * R - 0.5 * dal64 * (log_table(rx * rx + ry * ry, lt) - T[17 * N + m]));
-      const float2 rxd = df_of(rx), ryd = df_of(ry);
+      const float2 rxd = df_add(pr[0][0][li], make_float2(-pr[1][0][lj].x, -pr[1][0][lj].y));
+      const float2 ryd = df_add(pr[0][1][li], make_float2(-pr[1][1][lj].x, -pr[1][1][lj].y));
       const float2 xx = df_mul(rxd, rxd), xy2 = df_mul(rxd, ryd), yy = df_mul(ryd, ryd);
-      const float2 ir2 = df_rcp(df_add(xx, yy));
+      const float2 r2 = df_add(xx, yy);
+      lp = df_add(am[li - lj + SM_TILE - 1], df_mul(df_of(-0.5 * dal64), log_df(r2, lt)));
+      const float2 ir2 = df_rcp(r2);
       axx = df_mul(xx, ir2);
       axy = df_mul(xy2, ir2);
       ayy = df_mul(yy, ir2);

@@ -10,7 +10,8 @@
 //                    K0 = (1/N)[1 + 2 sum_{k=1}^{N/2-1} cos(k theta) + cos(N theta/2)]
 //   [9N,15N)  K1(q)  its derivative in theta.
 //   [15N,16N) cos(2 pi m / N),  [16N,17N) sin(2 pi m / N).
-//   [17N,18N) log(4 sin^2(pi m / N)) (0 at m = 0).
+//   [17N,18N) -R(m)/2 + (pi/N) log(4 sin^2(pi m / N)) (m >= 1; 0 at m = 0): with it the log part of the
+//             self single layer off the diagonal is this minus (pi/N) log|r|^2.
 #pragma once
 #include <cmath>
 #include <vector>
@@ -45,7 +46,7 @@ inline void build_tables(int N, double* t) {
   for (int m = 0; m < N; ++m) {
     t[15 * N + m] = std::cos(2.0 * VS_PI * m / N);
     t[16 * N + m] = std::sin(2.0 * VS_PI * m / N);
-    t[17 * N + m] = (m == 0) ? 0.0 : std::log(t[2 * N + m]);
+    t[17 * N + m] = (m == 0) ? 0.0 : -0.5 * t[N + m] + (VS_PI / N) * std::log(t[2 * N + m]);
   }
 }
 

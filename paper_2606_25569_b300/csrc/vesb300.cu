@@ -118,7 +118,7 @@ struct DevLayout {
   int32_t* chunk1k = nullptr;
   double* tab = nullptr;
   float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
-  double2* logtab = nullptr;  // (log c_k, 1/c_k), c_k = 1 + (k + 1/2)/LOG_TAB (log_table)
+  float4* logtab = nullptr;  // (log c_k, 1/c_k) as FP32 pairs, c_k = 1 + (k + 1/2)/LOG_TAB (log_df)
   VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
@@ -149,10 +149,11 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   std::vector<float> t32(L.tab.begin(), L.tab.end());
   VS_TRY(dalloc(&D.tab32, t32.size()));
   VS_TRY(upload(D.tab32, t32.data(), t32.size(), s));
-  std::vector<double2> lt(LOG_TAB);
+  std::vector<float4> lt(LOG_TAB);
   for (int k = 0; k < LOG_TAB; ++k) {
-    const long double c = 1.0L + (k + 0.5L) / LOG_TAB;
-    lt[k] = make_double2((double)std::log(c), (double)(1.0L / c));
+    const long double c = 1.0L + (k + 0.5L) / LOG_TAB, lc = std::log(c), rc = 1.0L / c;
+    const float lh = (float)lc, rh = (float)rc;
+    lt[k] = make_float4(lh, (float)(lc - lh), rh, (float)(rc - rh));
   }
   VS_TRY(dalloc(&D.logtab, LOG_TAB));
   VS_TRY(upload(D.logtab, lt.data(), LOG_TAB, s));
