@@ -70,17 +70,18 @@ struct MpShared {
 };
 
 // y (+)= alpha M x in FP32 for a rows x cols row-major FP32 matrix (global, read-only; cols even, at most
-// MP_COLS). Each warp takes MV_ROWS rows at a time and each lane two adjacent columns per 64, all loads
+// COLS, 128 or 256). Each warp takes MV_ROWS rows at a time and each lane two adjacent columns per 64, all loads
 // of a pass issued before the arithmetic so that enough bytes are in flight to cover the memory latency;
 // ends synchronised. x must be 8-byte aligned.
-constexpr int MV_ROWS = 4, MP_COLS = 2 * NMAX;
+constexpr int MV_ROWS = 4;
+template <int COLS>
 __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols, const float* x, float* y,
                                  float alpha, bool add) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r0 = MV_ROWS * wid; r0 < rows; r0 += MV_ROWS * nw) {
-    float2 mv[MP_COLS / 64][MV_ROWS];
+    float2 mv[COLS / 64][MV_ROWS];
 #pragma unroll
-    for (int t = 0; t < MP_COLS / 64; ++t) {
+    for (int t = 0; t < COLS / 64; ++t) {
       const int k = 2 * lane + 64 * t;
 #pragma unroll
       for (int q = 0; q < MV_ROWS; ++q)
@@ -92,7 +93,7 @@ __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols
 #pragma unroll
     for (int q = 0; q < MV_ROWS; ++q) acc[q] = 0.f;
 #pragma unroll
-    for (int t = 0; t < MP_COLS / 64; ++t) {
+    for (int t = 0; t < COLS / 64; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k < cols) {
         const float2 xk = *reinterpret_cast<const float2*>(x + k);
@@ -160,13 +161,14 @@ __device__ inline void mp_p(const MpShared& sh, const float2* v, float2* out, in
 // w = S u for the 2N x 2N matrix S = Sh + Sl (two row-major FP32 matrices in global memory): MV_ROWS
 // rows per warp pass, each lane two adjacent columns per 64 (all loads of a pass issued first), partial
 // sums merged across the warp; ends synchronised
+template <int COLS>
 __device__ inline void mp_smatvec(const float* __restrict__ Sh, const float* __restrict__ Sl, const float2* u,
                                   float2* w, int n2) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r0 = MV_ROWS * wid; r0 < n2; r0 += MV_ROWS * nw) {
-    float2 hv[MP_COLS / 64][MV_ROWS], lv[MP_COLS / 64][MV_ROWS];
+    float2 hv[COLS / 64][MV_ROWS], lv[COLS / 64][MV_ROWS];
 #pragma unroll
-    for (int t = 0; t < MP_COLS / 64; ++t) {
+    for (int t = 0; t < COLS / 64; ++t) {
       const int k = 2 * lane + 64 * t;
 #pragma unroll
       for (int q = 0; q < MV_ROWS; ++q) {
@@ -178,7 +180,7 @@ __device__ inline void mp_smatvec(const float* __restrict__ Sh, const float* __r
     }
     Dot2 acc[MV_ROWS];
 #pragma unroll
-    for (int t = 0; t < MP_COLS / 64; ++t) {
+    for (int t = 0; t < COLS / 64; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k < n2) {
         const float2 u0 = u[k], u1 = u[k + 1];
@@ -217,6 +219,7 @@ __device__ __forceinline__ MpMats mp_mats(const VesIndex& vi, const float* scrat
 
 // Solve L s = g (s FP64, g double-float and read only) with Li32 and the matrix-free L.
 // e (N) and q, w (2N) are caller shared double-float arrays; uses sh.u2, sh.f0, sh.f1.
+template <int COLS>
 __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, double* s, float2* e, float2* q,
                            float2* w, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) { s[i] = 0.0; e[i] = g[i]; }
@@ -227,14 +230,14 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
       for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = df_of(s[i]);
       __syncthreads();
       mp_ten(sh, w, q, N);
-      mp_smatvec(m.sh, m.sl, q, w, 2 * N);
+      mp_smatvec<COLS>(m.sh, m.sl, q, w, 2 * N);
       mp_p(sh, w, e, N);
       for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = df_add(g[i], make_float2(-e[i].x, -e[i].y));
       __syncthreads();
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f1[i] = e[i].x;
     __syncthreads();
-    matvec32f(m.li, N, N, sh.f1, sh.f0, 1.f, false);
+    matvec32f<COLS>(m.li, N, N, sh.f1, sh.f0, 1.f, false);
     double du = 0.0, sv = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       s[i] += (double)sh.f0[i];
@@ -250,7 +253,7 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
 }
 
 // X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s.
-template <int THREADS>
+template <int THREADS, int COLS>
 __global__ void __launch_bounds__(THREADS) k_advect_mp(VesIndex vi, const double* __restrict__ xy,
                                                    const double* __restrict__ u, const double* __restrict__ sa,
                                                    const double* __restrict__ tx, const double* __restrict__ ty,
@@ -268,18 +271,18 @@ __global__ void __launch_bounds__(THREADS) k_advect_mp(VesIndex vi, const double
   __syncthreads();
   mp_p(sh, sh.u0, g, N);
   const MpMats m = mp_mats(vi, scratch32, v, s);
-  const bool ok = mp_solve_L(sh, m, g, sg, e, sh.u1, sh.u0, N);
+  const bool ok = mp_solve_L<COLS>(sh, m, g, sg, e, sh.u1, sh.u0, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) e[i] = df_of(sg[i]);
   __syncthreads();
   mp_ten(sh, e, sh.u1, N);
-  mp_smatvec(m.sh, m.sl, sh.u1, sh.u0, 2 * N);
+  mp_smatvec<COLS>(m.sh, m.sl, sh.u1, sh.u0, 2 * N);
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x)
     xy_out[2 * o + r] = xy[2 * o + r] + dt * (u[2 * o + r] - df_val(sh.u0[r]));
   if (!ok && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
 // sigma = -L^{-1} P (B X + u) at slot s (Eq. tension_disc), B X = -kappa S X_ssss.
-template <int THREADS>
+template <int THREADS, int COLS>
 __global__ void __launch_bounds__(THREADS) k_tension_mp(VesIndex vi, const double* __restrict__ bx,
                                                     const double* __restrict__ by, const double* __restrict__ u,
                                                     const double* __restrict__ sa, const double* __restrict__ tx,
@@ -299,19 +302,19 @@ __global__ void __launch_bounds__(THREADS) k_tension_mp(VesIndex vi, const doubl
   }
   __syncthreads();
   const MpMats m = mp_mats(vi, scratch32, v, s);
-  mp_smatvec(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
+  mp_smatvec<COLS>(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
   const float2 mk = df_of(-kappa);
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u1[r] = df_add(df_mul(mk, sh.u1[r]), df_of(u[2 * o + r]));
   __syncthreads();
   mp_p(sh, sh.u1, g, N);
-  const bool ok = mp_solve_L(sh, m, g, sg, e, sh.u1, sh.u0, N);
+  const bool ok = mp_solve_L<COLS>(sh, m, g, sg, e, sh.u1, sh.u0, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sigma[o + i] = -sg[i];
   if (!ok && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
 // Relaxation (Eq. relaxation_disc) by refinement of the coupled (x, sigma) system at slot s. The
 // iterate x is kept relative to the mean point of X* (the operators only see its derivatives).
-template <int THREADS>
+template <int THREADS, int COLS>
 __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double* __restrict__ xy_star,
                                                   const double* __restrict__ sa, const double* __restrict__ tx,
                                                   const double* __restrict__ ty, const double* __restrict__ tab,
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
       mp_ten(sh, sh.u1, tsg, N);
       for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) sh.u0[r] = df_add(df_mul(mk, sh.u0[r]), tsg[r]);
       __syncthreads();
-      mp_smatvec(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
+      mp_smatvec<COLS>(m.sh, m.sl, sh.u0, sh.u1, 2 * N);
       for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r] - x[r] + dt * df_val(sh.u1[r]);
       __syncthreads();
       mp_p(sh, sh.u1, y2, N);
@@ -375,10 +378,10 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
     for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f0[i] = -y2[i].x;
     for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) fr[r] = (float)r1[r];
     __syncthreads();
-    matvec32f(m.li, N, N, sh.f0, fy, 1.f, false);
-    matvec32f(m.t32, 2 * N, N, fy, fr, (float)dt, true);
-    matvec32f(Ainv, 2 * N, 2 * N, fr, fdx, 1.f, false);
-    matvec32f(W32, N, 2 * N, fdx, fw, 1.f, false);
+    matvec32f<COLS>(m.li, N, N, sh.f0, fy, 1.f, false);
+    matvec32f<COLS>(m.t32, 2 * N, N, fy, fr, (float)dt, true);
+    matvec32f<COLS>(Ainv, 2 * N, 2 * N, fr, fdx, 1.f, false);
+    matvec32f<COLS>(W32, N, 2 * N, fdx, fw, 1.f, false);
     double du = 0.0, xv = 0.0;
     for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) {
       x[r] += (double)fdx[r];

@@ -377,6 +377,21 @@ FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
 // several, else 128.
 inline bool mp_wide(const vs_suspension* h) { return h->L.nmax > 64 || h->L.M < 4 * 148; }
 
+// Launch a refinement kernel with the CTA size of mp_wide and the mat-vec column capacity (128 or 256)
+// that covers 2 nmax.
+#define MP_DISPATCH(h, name, kern, grid, args)                                                              \
+  do {                                                                                                      \
+    const bool wide_ = mp_wide(h), small_ = 2 * (h)->L.nmax <= 128;                                          \
+    if (wide_ && small_)                                                                                     \
+      VS_LAUNCH(h, name, kern<MP_THREADS_WIDE, 128><<<grid, MP_THREADS_WIDE, 0, (h)->stream>>> args);         \
+    else if (wide_)                                                                                          \
+      VS_LAUNCH(h, name, kern<MP_THREADS_WIDE, 256><<<grid, MP_THREADS_WIDE, 0, (h)->stream>>> args);         \
+    else if (small_)                                                                                         \
+      VS_LAUNCH(h, name, kern<MP_THREADS, 128><<<grid, MP_THREADS, 0, (h)->stream>>> args);                   \
+    else                                                                                                     \
+      VS_LAUNCH(h, name, kern<MP_THREADS, 256><<<grid, MP_THREADS, 0, (h)->stream>>> args);                   \
+  } while (0)
+
 // Mixed precision (default): FP32 operator products and factorisations refined in FP64.
 inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
 
@@ -575,14 +590,8 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
       VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, nullptr));
       VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
     }
-    if (mp_wide(h))
-      VS_LAUNCH(h, "k_relax_mp", k_relax_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
-                                     vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv, h->p.kappa_b,
-                                     h->p.dt, xo, h->err));
-    else
-      VS_LAUNCH(h, "k_relax_mp", k_relax_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
-                                     vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv, h->p.kappa_b,
-                                     h->p.dt, xo, h->err));
+    MP_DISPATCH(h, "k_relax_mp", k_relax_mp, M, (vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv,
+                                                    h->p.kappa_b, h->p.dt, xo, h->err));
     VS_CK(h, cudaGetLastError(), "relaxation");
     return VS_OK;
   }
@@ -604,14 +613,8 @@ vs_status tension(vs_suspension* h, const double* u, int s) {
   const VesIndex vi = h->D.vi();
   const int M = h->L.M;
   if (mixed(h)) {
-    if (mp_wide(h))
-      VS_LAUNCH(h, "k_tension_mp", k_tension_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
-                                       vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
-                                       h->p.kappa_b, h->sigma, h->err));
-    else
-      VS_LAUNCH(h, "k_tension_mp", k_tension_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
-                                       vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
-                                       h->p.kappa_b, h->sigma, h->err));
+    MP_DISPATCH(h, "k_tension_mp", k_tension_mp, M, (vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                        h->scratch32, s, h->p.kappa_b, h->sigma, h->err));
   } else {
     VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
                                                                  h->piv, h->p.kappa_b, h->sigma));
@@ -697,14 +700,8 @@ vs_status step_once(vs_suspension* h) {
   if (h->p.near_field && L.M > 1 && (st = near_field(h, cur)) != VS_OK) return st;
   // (4) advection
   if (mixed(h)) {
-    if (mp_wide(h))
-      VS_LAUNCH(h, "k_advect_mp", k_advect_mp<MP_THREADS_WIDE><<<M, MP_THREADS_WIDE, 0, h->stream>>>(
-                                      vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, cur, h->p.dt,
-                                      h->xy_star, h->err));
-    else
-      VS_LAUNCH(h, "k_advect_mp", k_advect_mp<MP_THREADS><<<M, MP_THREADS, 0, h->stream>>>(
-                                      vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, cur, h->p.dt,
-                                      h->xy_star, h->err));
+    MP_DISPATCH(h, "k_advect_mp", k_advect_mp, M, (vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32,
+                                                      cur, h->p.dt, h->xy_star, h->err));
   } else {
     VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, h->xy, h->u, h->B.pg(), h->D.tab, h->scratch, cur, h->piv, h->p.dt,
                                                                h->xy_star));
