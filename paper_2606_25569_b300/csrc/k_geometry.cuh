@@ -2,6 +2,7 @@
 // Sec. 5.3-5.5). One CTA of NMAX threads per vesicle, thread j owns point j.
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace vs {
 
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
                                                    const double* __restrict__ tab, double kappa,
                                                    double mu, FlowDev flow, GeomOut g,
                                                    ForceOut fo, const double* __restrict__ f_in) {
-  __shared__ double d[NMAX], xs[NMAX], ys[NMAX], w1[NMAX], w2[NMAX], red[NMAX / 32];
+  // the circulant products run in double-float (FP64 is 1/64 of the FP32 rate on this part), on the
+  // positions relative to point 0 (the derivatives do not see the constant)
+  __shared__ double xs[NMAX], ys[NMAX], red[NMAX / 32];
+  __shared__ float2 dd[NMAX], w1[NMAX], w2[NMAX];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
@@ -63,34 +67,42 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
   const bool act = i < N;
   const double* T = tab + vi.toff[v];
   if (act) {
-    d[i] = T[i];
+    dd[i] = df_of(T[i]);
     xs[i] = xy[2 * o + i];
     ys[i] = xy[2 * o + N + i];
   }
   __syncthreads();
+  if (act) {
+    w1[i] = df_of(xs[i] - xs[0]);
+    w2[i] = df_of(ys[i] - ys[0]);
+  }
+  __syncthreads();
   double xa = 0.0, ya = 0.0;
   if (act) {
-    xa = circ_row(d, xs, N, i);
-    ya = circ_row(d, ys, N, i);
+    xa = df_val(circ_df(dd, w1, N, i));
+    ya = df_val(circ_df(dd, w2, N, i));
   }
   const double sa = act ? sqrt(xa * xa + ya * ya) : 1.0;
-  const double tx = xa / sa, ty = ya / sa;
+  const double isa = 1.0 / sa;
+  const float2 isd = df_of(isa);
+  const double tx = xa * isa, ty = ya * isa;
   const double dal = 2.0 * VS_PI / N;
   const double area = block_sum(act ? 0.5 * (xs[i] * ya - ys[i] * xa) * dal : 0.0, red);
   const double length = block_sum(act ? sa * dal : 0.0, red);
   const double cxs = block_sum(act ? xs[i] : 0.0, red);
   const double cys = block_sum(act ? ys[i] : 0.0, red);
   // X_ssss: four applications of D_s = diag(1/sa) D_alpha to each coordinate
-  double bx = act ? xs[i] : 0.0, by = act ? ys[i] : 0.0;
+  float2 bxd = act ? w1[i] : make_float2(0.f, 0.f), byd = act ? w2[i] : make_float2(0.f, 0.f);
   for (int r = 0; r < 4; ++r) {
     __syncthreads();
-    if (act) { w1[i] = bx; w2[i] = by; }
+    if (act) { w1[i] = bxd; w2[i] = byd; }
     __syncthreads();
     if (act) {
-      bx = circ_row(d, w1, N, i) / sa;
-      by = circ_row(d, w2, N, i) / sa;
+      bxd = df_mul(circ_df(dd, w1, N, i), isd);
+      byd = df_mul(circ_df(dd, w2, N, i), isd);
     }
   }
+  const double bx = df_val(bxd), by = df_val(byd);
   if (act) {
     g.sa[o + i] = sa;
     g.tx[o + i] = tx;
@@ -107,7 +119,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
   // force: f = -kappa X_ssss + D_s(sigma X_s)
   const double sg = (act && sigma) ? sigma[o + i] : 0.0;  // sigma may be null with f_in
   __syncthreads();
-  if (act) { w1[i] = sg * tx; w2[i] = sg * ty; }
+  if (act) { w1[i] = df_of(sg * tx); w2[i] = df_of(sg * ty); }
   __syncthreads();
   double fx = 0.0, fy = 0.0;
   if (act) {
@@ -115,8 +127,8 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
       fx = f_in[2 * o + i];
       fy = f_in[2 * o + N + i];
     } else {
-      fx = -kappa * bx + circ_row(d, w1, N, i) / sa;
-      fy = -kappa * by + circ_row(d, w2, N, i) / sa;
+      fx = -kappa * bx + df_val(df_mul(circ_df(dd, w1, N, i), isd));
+      fy = -kappa * by + df_val(df_mul(circ_df(dd, w2, N, i), isd));
     }
   }
   const double cx = cxs / N, cy = cys / N;

@@ -32,23 +32,6 @@ constexpr int MP_THREADS = 128, MP_THREADS_WIDE = 256;
 constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10;
 enum : unsigned { ERR_REFINE = 32u };
 
-// out_i = sum_j d[(i - j) mod N] v_j in double-float (d and v in shared memory); the compensated
-// partial sums are folded into a double-float total every DF_CHUNK terms (the last chunk may be short)
-__device__ __forceinline__ float2 circ_df(const float2* d, const float2* v, int N, int i) {
-  float2 tot = make_float2(0.f, 0.f);
-  int m = i;
-  for (int j0 = 0; j0 < N; j0 += DF_CHUNK) {
-    Dot2 a;
-    const int j1 = min(j0 + DF_CHUNK, N);
-    for (int j = j0; j < j1; ++j) {
-      a.add(d[m], v[j]);
-      m = (m == 0) ? N - 1 : m - 1;
-    }
-    tot = df_add(tot, a.value());
-  }
-  return tot;
-}
-
 __device__ inline double block_max_abs(double v, double* red) {
   v = fabs(v);
 #pragma unroll
