@@ -2,6 +2,7 @@
 // (Eqs. advection_disc, relaxation_disc, tension_disc; Sec. 4.2, 4.3). One CTA per vesicle.
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "k_dense.cuh"
 
 namespace vs {
@@ -63,61 +64,92 @@ __global__ void __launch_bounds__(256) k_relax_solve(VesIndex vi, const double* 
 __global__ void __launch_bounds__(256) k_redistribute(VesIndex vi, const double* __restrict__ xy_in,
                                                       const double* __restrict__ u, const double* __restrict__ tab,
                                                       double* __restrict__ xy_out, double* __restrict__ u_out) {
-  __shared__ double val[4][NMAX];
+  // sums of products run in double-float (FP64 is 1/64 of the FP32 rate on this part); the positions
+  // enter relative to point 0 and the mean is restored on output
+  __shared__ float2 val[4][NMAX];
+  __shared__ float2 k1[6 * NMAX], cs[NMAX], sn[NMAX];
   __shared__ double sp[6 * NMAX];
   __shared__ double l[6 * NMAX + 1];
-  __shared__ double cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
+  __shared__ float2 cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
+  __shared__ double base[2];
   const int v = blockIdx.x;
   const int N = vi.N[v];
   const int Nu = 6 * N;
   const int64_t o = vi.off[v];
   const double* T = tab + vi.toff[v];
   const int tid = threadIdx.x;
+  if (tid < 2) base[tid] = xy_in[2 * o + tid * N];
+  __syncthreads();
   for (int i = tid; i < N; i += blockDim.x) {
-    val[0][i] = xy_in[2 * o + i];
-    val[1][i] = xy_in[2 * o + N + i];
-    val[2][i] = u[2 * o + i];
-    val[3][i] = u[2 * o + N + i];
+    val[0][i] = df_of(xy_in[2 * o + i] - base[0]);
+    val[1][i] = df_of(xy_in[2 * o + N + i] - base[1]);
+    val[2][i] = df_of(u[2 * o + i]);
+    val[3][i] = df_of(u[2 * o + N + i]);
+    cs[i] = df_of(T[15 * N + i]);
+    sn[i] = df_of(T[16 * N + i]);
   }
+  for (int q = tid; q < Nu; q += blockDim.x) k1[q] = df_of(T[9 * N + q]);
   __syncthreads();
-  const double* K1 = T + 9 * N;
+  // speed |X_alpha| on the 6x finer grid from the interpolation kernel's derivative
   for (int q = tid; q < Nu; q += blockDim.x) {
-    double xp = 0.0, yp = 0.0;
+    float2 xp = make_float2(0.f, 0.f), yp = xp;
     int m = q;  // (q - 6 j) mod Nu
-    for (int j = 0; j < N; ++j) {
-      xp = fma(val[0][j], K1[m], xp);
-      yp = fma(val[1][j], K1[m], yp);
-      m -= 6;
-      if (m < 0) m += Nu;
+    for (int j0 = 0; j0 < N; j0 += DF_CHUNK) {
+      Dot2 ax, ay;
+      const int j1 = min(j0 + DF_CHUNK, N);
+      for (int j = j0; j < j1; ++j) {
+        ax.add(val[0][j], k1[m]);
+        ay.add(val[1][j], k1[m]);
+        m -= 6;
+        if (m < 0) m += Nu;
+      }
+      xp = df_add(xp, ax.value());
+      yp = df_add(yp, ay.value());
     }
-    sp[q] = sqrt(xp * xp + yp * yp);
+    const double x = df_val(xp), y = df_val(yp);
+    sp[q] = sqrt(x * x + y * y);
   }
   __syncthreads();
+  // cumulative trapezoid of the speed: warp 0, each lane a contiguous segment, then a shuffle scan
   const double dal = 2.0 * VS_PI / Nu;
-  if (tid == 0) {
+  if (tid < 32) {
+    const int seg = (Nu + 31) / 32, q0 = tid * seg, q1 = min(q0 + seg, Nu);
     double acc = 0.0;
-    l[0] = 0.0;
-    for (int q = 0; q < Nu; ++q) {
-      acc += 0.5 * dal * (sp[q] + sp[(q + 1 == Nu) ? 0 : q + 1]);
-      l[q + 1] = acc;
+    for (int q = q0; q < q1; ++q) acc += 0.5 * dal * (sp[q] + sp[(q + 1 == Nu) ? 0 : q + 1]);
+    double incl = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (tid >= off) incl += t;
+    }
+    double run = incl - acc;
+    if (tid == 0) l[0] = 0.0;
+    for (int q = q0; q < q1; ++q) {
+      run += 0.5 * dal * (sp[q] + sp[(q + 1 == Nu) ? 0 : q + 1]);
+      l[q + 1] = run;
     }
   }
   // Fourier coefficients c_k = (1/N) sum_j v_j e^{-2 pi i k j / N}, k = 0..N/2, of the 4 fields
-  const double* C = T + 15 * N;
-  const double* Sn = T + 16 * N;
   const int nk = N / 2 + 1;
+  const float2 invN = df_of(1.0 / N);
   for (int e = tid; e < 4 * nk; e += blockDim.x) {
     const int comp = e / nk, k = e - comp * nk;
-    double re = 0.0, im = 0.0;
+    float2 re = make_float2(0.f, 0.f), im = re;
     int m = 0;
-    for (int j = 0; j < N; ++j) {
-      re = fma(val[comp][j], C[m], re);
-      im = fma(-val[comp][j], Sn[m], im);
-      m += k;
-      if (m >= N) m -= N;
+    for (int j0 = 0; j0 < N; j0 += DF_CHUNK) {
+      Dot2 ar, ai;
+      const int j1 = min(j0 + DF_CHUNK, N);
+      for (int j = j0; j < j1; ++j) {
+        ar.add(val[comp][j], cs[m]);
+        ai.add(val[comp][j], sn[m]);
+        m += k;
+        if (m >= N) m -= N;
+      }
+      re = df_add(re, ar.value());
+      im = df_add(im, ai.value());
     }
-    cre[comp][k] = re / N;
-    cim[comp][k] = im / N;
+    cre[comp][k] = df_mul(re, invN);
+    cim[comp][k] = df_mul(make_float2(-im.x, -im.y), invN);
   }
   __syncthreads();
   const double total = l[Nu];
@@ -134,26 +166,45 @@ __global__ void __launch_bounds__(256) k_redistribute(VesIndex vi, const double*
       const double frac = (target - l[m0]) / (l[m1] - l[m0]);
       alpha = dal * m0 + frac * dal;
     }
-    double c1, s1;
-    sincos(alpha, &s1, &c1);
-    double out[4];
+    double c1d, s1d;
+    sincos(alpha, &s1d, &c1d);
+    const float2 c1 = df_of(c1d), s1 = df_of(s1d);
+    // trigonometric interpolant: c_0 + 2 sum_{m < N/2} Re(c_m e^{i m alpha}) + c_{N/2} cos(N alpha / 2)
+    float2 out[4];
+    Dot2 acc[4];
 #pragma unroll
     for (int comp = 0; comp < 4; ++comp) out[comp] = cre[comp][0];
-    double cm = c1, sm = s1;
+    float2 cm = c1, sm = s1;
     for (int mm = 1; mm < N / 2; ++mm) {
 #pragma unroll
-      for (int comp = 0; comp < 4; ++comp) out[comp] += 2.0 * (cre[comp][mm] * cm - cim[comp][mm] * sm);
-      const double cn = cm * c1 - sm * s1;
-      sm = sm * c1 + cm * s1;
+      for (int comp = 0; comp < 4; ++comp) {
+        acc[comp].add(cre[comp][mm], cm);
+        acc[comp].add(make_float2(-cim[comp][mm].x, -cim[comp][mm].y), sm);
+      }
+      const float2 cn = df_add(df_mul(cm, c1), make_float2(-df_mul(sm, s1).x, -df_mul(sm, s1).y));
+      sm = df_add(df_mul(sm, c1), df_mul(cm, s1));
       cm = cn;
+      if ((mm & (DF_CHUNK - 1)) == 0) {
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp) {
+          const float2 a = acc[comp].value();
+          out[comp] = df_add(out[comp], make_float2(2.f * a.x, 2.f * a.y));
+          acc[comp] = Dot2();
+        }
+      }
     }
     const double cN = cos((N / 2) * alpha);
+    double res[4];
 #pragma unroll
-    for (int comp = 0; comp < 4; ++comp) out[comp] += cre[comp][N / 2] * cN;
-    xy_out[2 * o + k] = out[0];
-    xy_out[2 * o + N + k] = out[1];
-    u_out[2 * o + k] = out[2];
-    u_out[2 * o + N + k] = out[3];
+    for (int comp = 0; comp < 4; ++comp) {
+      const float2 a = acc[comp].value();
+      out[comp] = df_add(out[comp], make_float2(2.f * a.x, 2.f * a.y));
+      res[comp] = df_val(out[comp]) + df_val(cre[comp][N / 2]) * cN;
+    }
+    xy_out[2 * o + k] = res[0] + base[0];
+    xy_out[2 * o + N + k] = res[1] + base[1];
+    u_out[2 * o + k] = res[2];
+    u_out[2 * o + N + k] = res[3];
   }
 }
 
