@@ -212,7 +212,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.M / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, args, {"impl": "FP64 CPU oracle (numpy), sampled"}),
+            "config": config_of(wl, args, {"impl": "FP64 CPU oracle (numpy), sampled", "mode": "plain BIE step",
+                                           "farfield": "fp64 brute force (oracle)",
+                                           "launch": "numpy on the host cores, one vesicle at a time"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "per step: oracle plain step of 2 vesicles + far field at 96 targets "
                                        "against all sources, extrapolated to the full step"},

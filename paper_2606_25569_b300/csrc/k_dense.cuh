@@ -456,34 +456,34 @@ __global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const i
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = As[e];
 }
 
-// In-place FP32 inverse of the n x n matrix at geo (n <= 16 R) by Gauss-Jordan exchange steps with
-// partial pivoting: step k takes as pivot p the row not yet used with the largest |T[p][k]| (first
+// In-place FP32 inverse of the n x n matrix at geo (n <= 16 RA = TC RB) by Gauss-Jordan exchange steps
+// with partial pivoting: step k takes as pivot p the row not yet used with the largest |T[p][k]| (first
 // wins) and exchanges equation p with unknown k,
 //   T[p][k] <- 1/t,  T[p][j] <- -T[p][j]/t,  T[i][k] <- T[i][k]/t,  T[i][j] <- T[i][j] - T[i][k] T[p][j]/t
 // (t = T[p][k]). After n steps row i expresses unknown step(i) through the right-hand-side entries
 // pivot(j) of the columns, so inv[step(i)][pivot(j)] = T[i][j]; no rows move.
-// 256 threads form a 16 x 16 grid, thread (tr, tc) = (tid % 16, tid / 16) keeping
-// T[tr + 16a][tc + 16b] (a, b < R) in registers as pairs over b for the paired FP32 update. The
-// column of step k sits in register b = k / 16 of the half-warp tc = k % 16, which also finds the
-// pivot by shuffles; column k and row p are broadcast through shared memory laid out per owner
-// ([tr][a] and [tc][b]) so that each thread reads its R values as 128-bit words. Two barriers a step.
-template <int R>
-__global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
-  static_assert(R % 2 == 0 && R >= 2 && R <= 8, "R even, at most 8");
-  constexpr int NP = 16 * R, H = R / 2;
-  __shared__ __align__(16) float colb[2][NP], rowb[2][NP];  // colb[tr * R + a], rowb[tc * R + b]
+// 16 TC threads form a 16 x TC grid, thread (tr, tc) = (tid % 16, tid / 16) keeping T[tr + 16a][tc + TC b]
+// (a < RA, b < RB) in registers as pairs over b for the paired FP32 update. The column of step k sits in
+// register b = k / TC of the half-warp tc = k % TC, which also finds the pivot by shuffles; column k and
+// row p are broadcast through shared memory laid out per owner ([tr][a] and [tc][b]) so that each thread
+// reads its values as vectors. Two barriers a step.
+template <int RA, int RB, int TC>
+__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
+  static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB, "square grid of pairs");
+  constexpr int NP = 16 * RA, H = RB / 2;
+  __shared__ __align__(16) float colb[2][NP], rowb[2][NP];  // colb[tr * RA + a], rowb[tc * RB + b]
   __shared__ int psel[2], pk[NP], rstep[NP];
   const int v = blockIdx.x;
   if (active && !active[v]) return;
   const int n = geo.n(v);
   float* A = geo.A(v);
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
-  float2 T[R][H];
+  float2 T[RA][H];
 #pragma unroll
-  for (int a = 0; a < R; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
     for (int h = 0; h < H; ++h) {
-      const int i = tr + 16 * a, j0 = tc + 32 * h, j1 = j0 + 16;
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
       T[a][h].x = (i < n && j0 < n) ? A[(int64_t)i * n + j0] : 0.f;
       T[a][h].y = (i < n && j1 < n) ? A[(int64_t)i * n + j1] : 0.f;
     }
@@ -496,28 +496,28 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
   bool bad = false;
   const unsigned half = (tc & 1) ? 0xffff0000u : 0x0000ffffu;
 #pragma unroll
-  for (int kb = 0; kb < R; ++kb) {
-    for (int kc = 0; kc < 16; ++kc) {
-      const int k = 16 * kb + kc;
+  for (int kb = 0; kb < RB; ++kb) {
+    for (int kc = 0; kc < TC; ++kc) {
+      const int k = TC * kb + kc;
       if (k >= n) break;
       const int buf = k & 1;  // double-buffered broadcasts: two barriers per step suffice
       if (tc == kc) {         // the half-warp holding column k: publish it and find the pivot
         float best = -1.f;
         int bi = NP;
-        float cv[R];
+        float cv[RA];
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
+        for (int a = 0; a < RA; ++a) {
           const int i = tr + 16 * a;
           cv[a] = (kb & 1) ? T[a][kb >> 1].y : T[a][kb >> 1].x;
           // the first unused row is always a candidate, so a NaN column still yields a row
           if (i < n && !((used >> a) & 1u) && (fabsf(cv[a]) > best || bi == NP)) { best = fabsf(cv[a]); bi = i; }
         }
-        if constexpr (R >= 4) {
+        if constexpr (RA >= 4) {
 #pragma unroll
-          for (int a = 0; a < R; a += 4)
-            *reinterpret_cast<float4*>(&colb[buf][tr * R + a]) = make_float4(cv[a], cv[a + 1], cv[a + 2], cv[a + 3]);
+          for (int a = 0; a < RA; a += 4)
+            *reinterpret_cast<float4*>(&colb[buf][tr * RA + a]) = make_float4(cv[a], cv[a + 1], cv[a + 2], cv[a + 3]);
         } else {
-          *reinterpret_cast<float2*>(&colb[buf][tr * R]) = make_float2(cv[0], cv[1]);
+          *reinterpret_cast<float2*>(&colb[buf][tr * RA]) = make_float2(cv[0], cv[1]);
         }
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) {
@@ -533,14 +533,14 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
       const int pr = p & 15, pa = p >> 4;
       if (tr == pr) {  // owners of row p publish it
 #pragma unroll
-        for (int a = 0; a < R; ++a)
+        for (int a = 0; a < RA; ++a)
           if (a == pa) {
             if constexpr (H == 1) {
-              *reinterpret_cast<float2*>(&rowb[buf][tc * R]) = T[a][0];
+              *reinterpret_cast<float2*>(&rowb[buf][tc * RB]) = T[a][0];
             } else {
 #pragma unroll
               for (int h = 0; h < H; h += 2)
-                *reinterpret_cast<float4*>(&rowb[buf][tc * R + 2 * h]) =
+                *reinterpret_cast<float4*>(&rowb[buf][tc * RB + 2 * h]) =
                     make_float4(T[a][h].x, T[a][h].y, T[a][h + 1].x, T[a][h + 1].y);
             }
             used |= 1u << a;
@@ -548,33 +548,33 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
       }
       if (tid == 0) { pk[k] = p; rstep[p] = k; }
       __syncthreads();
-      float pv = colb[buf][pr * R + pa];
+      float pv = colb[buf][pr * RA + pa];
       if (bad || !(pv != 0.f)) { bad = true; pv = 1.f; }
       const float ip = 1.f / pv;
-      float c[R];
+      float c[RA];
       float2 u[H];
-      if constexpr (R >= 4) {
+      if constexpr (RA >= 4) {
 #pragma unroll
-        for (int a = 0; a < R; a += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(&colb[buf][tr * R + a]);
+        for (int a = 0; a < RA; a += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(&colb[buf][tr * RA + a]);
           c[a] = w.x; c[a + 1] = w.y; c[a + 2] = w.z; c[a + 3] = w.w;
         }
       } else {
-        const float2 w = *reinterpret_cast<const float2*>(&colb[buf][tr * R]);
+        const float2 w = *reinterpret_cast<const float2*>(&colb[buf][tr * RA]);
         c[0] = w.x; c[1] = w.y;
       }
 #pragma unroll
-      for (int h = 0; h < H; ++h) u[h] = __fmul2_rn(*reinterpret_cast<const float2*>(&rowb[buf][tc * R + 2 * h]), make_float2(ip, ip));
+      for (int h = 0; h < H; ++h) u[h] = __fmul2_rn(*reinterpret_cast<const float2*>(&rowb[buf][tc * RB + 2 * h]), make_float2(ip, ip));
       if (tc == kc) {  // column k itself: T[i][k] <- T[i][k] / t
         if (kb & 1) u[kb >> 1].y = 1.f - ip; else u[kb >> 1].x = 1.f - ip;
       }
 #pragma unroll
-      for (int a = 0; a < R; ++a)
+      for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int h = 0; h < H; ++h) T[a][h] = __ffma2_rn(make_float2(-c[a], -c[a]), u[h], T[a][h]);
       if (tr == pr) {  // row p: T[p][j] <- -T[p][j] / t, T[p][k] <- 1 / t
 #pragma unroll
-        for (int a = 0; a < R; ++a)
+        for (int a = 0; a < RA; ++a)
           if (a == pa) {
 #pragma unroll
             for (int h = 0; h < H; ++h) T[a][h] = make_float2(-u[h].x, -u[h].y);
@@ -587,10 +587,10 @@ __global__ void __launch_bounds__(256, 2) k_gj_inverse(LuGeo32 geo, unsigned* er
   }
   __syncthreads();
 #pragma unroll
-  for (int a = 0; a < R; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
     for (int h = 0; h < H; ++h) {
-      const int i = tr + 16 * a, j0 = tc + 32 * h, j1 = j0 + 16;
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
       if (i < n && j0 < n) A[(int64_t)rstep[i] * n + pk[j0]] = T[a][h].x;
       if (i < n && j1 < n) A[(int64_t)rstep[i] * n + pk[j1]] = T[a][h].y;
     }

@@ -352,11 +352,11 @@ void launch_lu(vs_suspension* h, const char* name, const Geo& geo, int nmax_dim,
 bool launch_gj32(vs_suspension* h, const char* name, const LuGeo32& geo, int nmax_dim, const int* active) {
   const int M = h->L.M;
   if (nmax_dim <= 32) {
-    VS_LAUNCH(h, name, k_gj_inverse<2><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+    VS_LAUNCH(h, name, (k_gj_inverse<2, 2, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
   } else if (nmax_dim <= 64) {
-    VS_LAUNCH(h, name, k_gj_inverse<4><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+    VS_LAUNCH(h, name, (k_gj_inverse<4, 4, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
   } else if (nmax_dim <= 128) {
-    VS_LAUNCH(h, name, k_gj_inverse<8><<<M, 256, 0, h->stream>>>(geo, h->err, active));
+    VS_LAUNCH(h, name, (k_gj_inverse<8, 8, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
   } else {
     return false;
   }
