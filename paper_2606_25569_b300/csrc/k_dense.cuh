@@ -467,16 +467,15 @@ __global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const i
 // register b = k / TC of the half-warp tc = k % TC, which also finds the pivot by shuffles; column k and
 // row p are broadcast through shared memory laid out per owner ([tr][a] and [tc][b]) so that each thread
 // reads its values as vectors. Two barriers a step.
+// The elimination as a device function of the whole CTA (16 TC threads): src and dst (global or shared
+// memory, row-major n x n, possibly the same) are read before and written after the elimination.
 template <int RA, int RB, int TC>
-__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
+__device__ void gj_invert(const float* src, float* dst, int n, unsigned* err) {
   static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB, "square grid of pairs");
   constexpr int NP = 16 * RA, H = RB / 2;
   __shared__ __align__(16) float colb[2][NP], rowb[2][NP];  // colb[tr * RA + a], rowb[tc * RB + b]
   __shared__ int psel[2], pk[NP], rstep[NP];
-  const int v = blockIdx.x;
-  if (active && !active[v]) return;
-  const int n = geo.n(v);
-  float* A = geo.A(v);
+  const float* A = src;
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
   float2 T[RA][H];
 #pragma unroll
@@ -591,10 +590,19 @@ __global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
-      if (i < n && j0 < n) A[(int64_t)rstep[i] * n + pk[j0]] = T[a][h].x;
-      if (i < n && j1 < n) A[(int64_t)rstep[i] * n + pk[j1]] = T[a][h].y;
+      if (i < n && j0 < n) dst[(int64_t)rstep[i] * n + pk[j0]] = T[a][h].x;
+      if (i < n && j1 < n) dst[(int64_t)rstep[i] * n + pk[j1]] = T[a][h].y;
     }
   if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
+  __syncthreads();
+}
+
+template <int RA, int RB, int TC>
+__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
+  const int v = blockIdx.x;
+  if (active && !active[v]) return;
+  float* A = geo.A(v);
+  gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
 }
 
 // Solve LU x = b in place for one vector b in shared memory (length n); warp 0 works, the

@@ -415,6 +415,176 @@ __device__ void corr_update(int v, VesIndex vi, const double* LU, const int* p, 
   }
 }
 
+// Newton iterations of the correction with an FP32 Jacobian (2N <= 16 RA): per step the FP64 residual
+// (z - X - J^T lam, c(z)) as in corr_build, the 2N x 2N block M = I - lam_A H_A - lam_L H_L assembled in
+// FP32 in dynamic shared memory and inverted in registers (gj_invert), and the KKT system
+//   [M  -G; G^T  0] [dz; dlam] = [r1; r2],  G = (grad A, grad L)
+// solved through its 2 x 2 Schur complement: y = M^{-1} r1, Y = M^{-1} G, (G^T Y) dlam = r2 - G^T y,
+// dz = y + Y dlam. The FP32 Jacobian makes the iteration converge linearly (factor about 1e-6) to the
+// same KKT point that the FP64 residual defines; the same stopping test as corr_update. 256 threads.
+template <int RA>
+__global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double* __restrict__ tab,
+                                                       const double* __restrict__ A0, const double* __restrict__ L0,
+                                                       double* __restrict__ corr, int* __restrict__ active,
+                                                       const int* __restrict__ dirty, int iters,
+                                                       double* __restrict__ xy, int* __restrict__ fired, unsigned* err) {
+  extern __shared__ __align__(16) float Mg[];  // (2N)^2
+  __shared__ double d[NMAX], zx[NMAX], zy[NMAX], gA[2 * NMAX], gL[2 * NMAX], r1[2 * NMAX], red[8];
+  __shared__ float dq[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX], f1[2 * NMAX];
+  __shared__ float yv[3][2 * NMAX];
+  __shared__ double sol[3];
+  const int v = blockIdx.x;
+  if (!dirty[v]) return;
+  const int N = vi.N[v];
+  const int n2 = 2 * N;
+  const int tid = threadIdx.x;
+  double* st = corr_state(corr, vi, v);
+  const double dal = 2.0 * VS_PI / N;
+  for (int i = tid; i < N; i += blockDim.x) {
+    d[i] = tab[vi.toff[v] + i];
+    dq[i] = (float)d[i];
+  }
+  for (int it = 0; it < iters; ++it) {
+    __syncthreads();
+    if (!active[v]) break;  // uniform: written by thread 0 of this CTA before the barrier
+    const double la = st[6 * N + 2], ll = st[6 * N + 3];
+    for (int i = tid; i < N; i += blockDim.x) {
+      zx[i] = st[2 * N + i];
+      zy[i] = st[3 * N + i];
+    }
+    __syncthreads();
+    // geometry of z and the FP64 residual (same formulas as corr_build)
+    double pa = 0.0, pl = 0.0;
+    __shared__ double txs[NMAX], tys[NMAX];
+    for (int i = tid; i < N; i += blockDim.x) {
+      const double xa = circ_row(d, zx, N, i), ya = circ_row(d, zy, N, i);
+      const double sp = sqrt(xa * xa + ya * ya);
+      txs[i] = xa / sp;
+      tys[i] = ya / sp;
+      qxx[i] = (float)(tys[i] * tys[i] / sp);
+      qxy[i] = (float)(-txs[i] * tys[i] / sp);
+      qyy[i] = (float)(txs[i] * txs[i] / sp);
+      gA[i] = dal * ya;
+      gA[N + i] = -dal * xa;
+      pa += dal * 0.5 * (zx[i] * ya - zy[i] * xa);
+      pl += dal * sp;
+    }
+    const double Acur = block_sum(pa, red), Lcur = block_sum(pl, red);
+    __syncthreads();
+    for (int i = tid; i < N; i += blockDim.x) {
+      gL[i] = -dal * circ_row(d, txs, N, i);
+      gL[N + i] = -dal * circ_row(d, tys, N, i);
+    }
+    __syncthreads();
+    for (int a = tid; a < n2; a += blockDim.x) {
+      const double z = (a < N) ? zx[a] : zy[a - N];
+      r1[a] = -(z - st[a] - la * gA[a] - ll * gL[a]);
+    }
+    // M = I - la dal H_A - ll dal H_L in FP32
+    const float fa = (float)(la * dal), fl = (float)(ll * dal);
+    for (int e = tid; e < n2 * n2; e += blockDim.x) {
+      const int a = e / n2, b = e - a * n2;
+      const int p = a / N, i = a - p * N, q = b / N, j = b - q * N;
+      const float* qq = (p == 0) ? ((q == 0) ? qxx : qxy) : ((q == 0) ? qxy : qyy);
+      float hl = 0.f;
+      int ki = N - i, kj = N - j;  // (k - i) mod N at k = 0
+      if (ki == N) ki = 0;
+      if (kj == N) kj = 0;
+      for (int k = 0; k < N; ++k) {
+        hl = fmaf(dq[ki] * dq[kj], qq[k], hl);
+        if (++ki == N) ki = 0;
+        if (++kj == N) kj = 0;
+      }
+      float ha = 0.f;
+      if (p == 0 && q == 1) { int m = i - j; m += (m < 0) ? N : 0; ha = dq[m]; }
+      if (p == 1 && q == 0) { int m = j - i; m += (m < 0) ? N : 0; ha = dq[m]; }
+      Mg[e] = ((a == b) ? 1.f : 0.f) - fa * ha - fl * hl;
+    }
+    __syncthreads();
+    gj_invert<RA, RA, 16>(Mg, Mg, n2, err);
+    // y = M^{-1} r1, Y = M^{-1} (gA, gL): warp per row
+    {
+      const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+      for (int a = wid; a < n2; a += nw) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int b = lane; b < n2; b += 32) {
+          const float m = Mg[a * n2 + b];
+          s0 = fmaf(m, (float)r1[b], s0);
+          s1 = fmaf(m, (float)gA[b], s1);
+          s2 = fmaf(m, (float)gL[b], s2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) { yv[0][a] = s0; yv[1][a] = s1; yv[2][a] = s2; }
+      }
+    }
+    __syncthreads();
+    // 2 x 2 Schur system (G^T Y) dlam = r2 - G^T y in FP64 (warp 0)
+    if (tid < 32) {
+      double gy[2] = {0.0, 0.0}, S[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+      for (int a = tid; a < n2; a += 32) {
+        const double y0 = yv[0][a], ya = yv[1][a], yl = yv[2][a];
+        gy[0] += gA[a] * y0;
+        gy[1] += gL[a] * y0;
+        S[0][0] += gA[a] * ya;
+        S[0][1] += gA[a] * yl;
+        S[1][0] += gL[a] * ya;
+        S[1][1] += gL[a] * yl;
+      }
+      gy[0] = warp_sum(gy[0]);
+      gy[1] = warp_sum(gy[1]);
+      S[0][0] = warp_sum(S[0][0]);
+      S[0][1] = warp_sum(S[0][1]);
+      S[1][0] = warp_sum(S[1][0]);
+      S[1][1] = warp_sum(S[1][1]);
+      if (tid == 0) {
+        const double b0 = -(Acur - A0[v]) - gy[0], b1 = -(Lcur - L0[v]) - gy[1];
+        const double det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+        const double idet = (det != 0.0) ? 1.0 / det : 0.0;
+        sol[0] = (b0 * S[1][1] - b1 * S[0][1]) * idet;
+        sol[1] = (S[0][0] * b1 - S[1][0] * b0) * idet;
+        if (det == 0.0) atomicOr(err, ERR_PIVOT);
+      }
+    }
+    __syncthreads();
+    const double dla = sol[0], dll = sol[1];
+    double dm = 0.0;
+    for (int a = tid; a < n2; a += blockDim.x) {
+      const double dz = (double)yv[0][a] + (double)yv[1][a] * dla + (double)yv[2][a] * dll;
+      st[2 * N + a] += dz;
+      dm = fmax(dm, fabs(dz));
+    }
+    for (int off = 16; off > 0; off >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, off));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dm;
+    __syncthreads();
+    if (tid == 0) {
+      double m = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      st[6 * N + 2] += dla;
+      st[6 * N + 3] += dll;
+      if (m <= 1e-14 * st[6 * N + 6]) {
+        st[6 * N + 7] = 1.0;
+        active[v] = 0;
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t o = vi.off[v];
+  for (int i = tid; i < N; i += blockDim.x) {
+    xy[2 * o + i] = st[2 * N + i] + st[6 * N + 4];
+    xy[2 * o + N + i] = st[3 * N + i] + st[6 * N + 5];
+  }
+  if (tid == 0) {
+    atomicAdd(fired, 1);
+    if (st[6 * N + 7] == 0.0) atomicOr(err, ERR_CORRECTION);
+  }
+}
+
 // Newton iterations of the correction for every vesicle flagged by k_corr_init (dirty), at most `iters`
 // steps: assemble K, factor it (in dynamic shared memory when SMEM, else in place), solve, update; then
 // write the corrected points back (plus the mean) and flag vesicles that did not converge. One CTA of

@@ -670,7 +670,23 @@ vs_status correction(vs_suspension* h) {
                                                                        h->corr, h->cactive, h->dirty, h->err));
   const int n = 2 * L.nmax + 2;
   const size_t bytes = (size_t)n * n * sizeof(double);
-  if (bytes <= LU_SMEM_MAX) {
+  const size_t bytes32 = (size_t)4 * L.nmax * L.nmax * sizeof(float);
+  if (2 * L.nmax <= 32) {
+    VS_LAUNCH(h, "k_corr_newton32", k_corr_newton32<2><<<L.M, 256, bytes32, h->stream>>>(vi, h->D.tab, h->A0, h->L0,
+                                                                                     h->corr, h->cactive, h->dirty,
+                                                                                     CORR_NEWTON_ITERS, h->xy,
+                                                                                     h->fired, h->err));
+  } else if (2 * L.nmax <= 64) {
+    VS_LAUNCH(h, "k_corr_newton32", k_corr_newton32<4><<<L.M, 256, bytes32, h->stream>>>(vi, h->D.tab, h->A0, h->L0,
+                                                                                     h->corr, h->cactive, h->dirty,
+                                                                                     CORR_NEWTON_ITERS, h->xy,
+                                                                                     h->fired, h->err));
+  } else if (2 * L.nmax <= 128) {
+    VS_LAUNCH(h, "k_corr_newton32", k_corr_newton32<8><<<L.M, 256, bytes32, h->stream>>>(vi, h->D.tab, h->A0, h->L0,
+                                                                                     h->corr, h->cactive, h->dirty,
+                                                                                     CORR_NEWTON_ITERS, h->xy,
+                                                                                     h->fired, h->err));
+  } else if (bytes <= LU_SMEM_MAX) {
     VS_LAUNCH(h, "k_corr_newton", k_corr_newton<true><<<L.M, 256, bytes, h->stream>>>(vi, h->D.tab, h->A0, h->L0, h->corr,
                                                                                     h->scratch, h->cpiv, h->cactive,
                                                                                     h->dirty, CORR_NEWTON_ITERS, h->xy,
@@ -839,6 +855,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->has_near, L.M));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
+  VS_A(cudaFuncSetAttribute(k_corr_newton32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
