@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
+    ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -361,6 +362,22 @@ def run_gpu(args):
     breakdown = {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     per_step = {k: round(v[0] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
+    # steady state: after a burn-in the area/length correction fires for a few vesicles every step
+    steady = None
+    if args.burn_in > 0:
+        s.step(args.burn_in)
+        s.sync()
+        c0 = s.counters()["corrections"]
+        t2, t3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t2.record(stream)
+        s.step(args.steps)
+        t3.record(stream)
+        torch.cuda.synchronize()
+        ms_ss = t2.elapsed_time(t3) / args.steps
+        steady = {"after_steps": args.burn_in + max(args.warmup, 3) + args.steps, "steps": args.steps,
+                  "ms_per_step": ms_ss, "value": world * wl.M / (ms_ss * 1e-3), "unit": UNIT,
+                  "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
+
     # end to end through the C ABI with host buffers: upload state, step, read positions
     e2e = None
     if not args.no_e2e:
@@ -398,7 +415,7 @@ def run_gpu(args):
                                                                   "(autotuned at create)" % (fv[1], fv[2])}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
-                "hybrid": hybrid,
+                "steady_state": steady, "hybrid": hybrid,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()
