@@ -157,8 +157,13 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   const int64_t o = vi.off[v];
   const double* T = tab + vi.toff[v];
   const double dal64 = 2.0 * VS_PI / N;
-  const float2 dal = df_of(dal64);
-  __syncthreads();  // lt
+  __shared__ float2 kc[2];  // 2 pi / N and -pi / N in double-float, converted once per CTA
+  if (threadIdx.x == 0) {
+    kc[0] = df_of(dal64);
+    kc[1] = df_of(-0.5 * dal64);
+  }
+  __syncthreads();  // lt, kc
+  const float2 dal = kc[0];
   if (threadIdx.x < 2 * SM_TILE) {
     const int w = threadIdx.x / SM_TILE, jj = (w ? bi : bj) * SM_TILE + threadIdx.x % SM_TILE;
     cc[w][threadIdx.x % SM_TILE] = (jj < N) ? df_of(sa[o + jj] / (4.0 * VS_PI * mu)) : make_float2(0.f, 0.f);
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
       const float2 ryd = df_add(pr[0][1][li], make_float2(-pr[1][1][lj].x, -pr[1][1][lj].y));
       const float2 xx = df_mul(rxd, rxd), xy2 = df_mul(rxd, ryd), yy = df_mul(ryd, ryd);
       const float2 r2 = df_add(xx, yy);
-      lp = df_add(am[li - lj + SM_TILE - 1], df_mul(df_of(-0.5 * dal64), log_df(r2, lt)));
+      lp = df_add(am[li - lj + SM_TILE - 1], df_mul(kc[1], log_df(r2, lt)));
       const float2 ir2 = df_rcp(r2);
       axx = df_mul(xx, ir2);
       axy = df_mul(xy2, ir2);
