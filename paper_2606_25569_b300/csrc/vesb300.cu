@@ -354,7 +354,7 @@ bool launch_gj32(vs_suspension* h, const char* name, const LuGeo32& geo, int nma
   if (nmax_dim <= 32) {
     VS_LAUNCH(h, name, (k_gj_inverse<2, 2, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
   } else if (nmax_dim <= 64) {
-    VS_LAUNCH(h, name, (k_gj_inverse<4, 4, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
+    VS_LAUNCH(h, name, (k_gj_inverse<4, 8, 8><<<M, 128, 0, h->stream>>>(geo, h->err, active)));
   } else if (nmax_dim <= 128) {
     VS_LAUNCH(h, name, (k_gj_inverse<8, 8, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
   } else {
