@@ -69,6 +69,10 @@ typedef struct {
 /* Keep the default FP32 far-field launch shape instead of timing the shapes at vs_create
  * (vs_farfield_variant). */
 #define VS_FLAG_NO_AUTOTUNE 4ull
+/* Build the FP32 operator products of the mixed-precision path on the tensor cores (each FP32 operand
+ * split into three BF16 parts, FP32 accumulation) instead of with FP32 FMAs; both give FP32-quality
+ * preconditioners and the same FP64-accurate results. At N <= 128 the FMA kernels are faster. */
+#define VS_FLAG_TC_GEMM 8ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */

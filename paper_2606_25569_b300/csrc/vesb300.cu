@@ -22,6 +22,7 @@
 #include "k_near.cuh"
 #include "k_selfmat.cuh"
 #include "k_standardize.cuh"
+#include "k_tcgemm.cuh"
 #include "k_vesicle.cuh"
 #include "tables.cuh"
 
@@ -371,6 +372,18 @@ inline dim3 self_grid(int nmax, int M) {
 
 inline dim3 gemm_grid(int m, int n, int M) { return dim3((n + GT - 1) / GT, (m + GT - 1) / GT, M); }
 
+// FP32 operator product C = A B of every vesicle (Op: operand functors, m x n output): with FP32 FMAs
+// (k_bgemm), or on the tensor cores with the three-part BF16 split (k_bgemm_tc) under VS_FLAG_TC_GEMM.
+template <class Op>
+void gemm32(vs_suspension* h, const char* name, const Op& op, int m, int n, const int* active) {
+  if (h->p.flags & VS_FLAG_TC_GEMM) {
+    const dim3 grid((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM, h->L.M);
+    VS_LAUNCH(h, name, k_bgemm_tc<Op><<<grid, TC_THREADS, TC_SMEM, h->stream>>>(op, active, h->err));
+  } else {
+    VS_LAUNCH(h, name, k_bgemm<Op><<<gemm_grid(m, n, h->L.M), 256, 0, h->stream>>>(op, active));
+  }
+}
+
 FlowDev flow_dev(const vs_flow& f) { return FlowDev{f.kind, f.p[0], f.p[1]}; }
 
 // Refinement kernels: 256 threads per vesicle when the vesicles are large or too few to give every SM
@@ -410,8 +423,8 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   }
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
   if (mixed(h)) {
-    VS_LAUNCH(h, "k_bgemm<OpT32>", k_bgemm<OpT32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpT32{c, s}, active));
-    VS_LAUNCH(h, "k_bgemm<OpL32>", k_bgemm<OpL32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpL32{c, s}, active));
+    gemm32(h, "k_bgemm<OpT32>", OpT32{c, s}, 2 * n, n, active);
+    gemm32(h, "k_bgemm<OpL32>", OpL32{c, s}, n, n, active);
     static_assert(NMAX <= 128, "the FP32 inverse of L is formed in registers");
     launch_gj32(h, "k_gj_inverse<L>", LuGeo32{vi, h->scratch32, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv32, s}, n, active);
   } else {
@@ -562,13 +575,13 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
   if ((st = build_operators(h, xs, s, nullptr)) != VS_OK) return st;
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
   if (mixed(h)) {
-    VS_LAUNCH(h, "k_bgemm<OpD2_32>", k_bgemm<OpD2_32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2_32{c}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpD4_32>", k_bgemm<OpD4_32><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4_32{c}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpB32>", k_bgemm<OpB32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB32{c, s, 0, h->p.kappa_b}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpB32>", k_bgemm<OpB32><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB32{c, s, 1, h->p.kappa_b}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpPB32>", k_bgemm<OpPB32><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB32{c}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpW32>", k_bgemm<OpW32><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpW32{c, s}, nullptr));
-    VS_LAUNCH(h, "k_bgemm<OpA32>", k_bgemm<OpA32><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA32{c, s, h->p.dt}, nullptr));
+    gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, nullptr);
+    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 1, h->p.kappa_b}, 2 * n, n, nullptr);
+    gemm32(h, "k_bgemm<OpPB32>", OpPB32{c}, n, 2 * n, nullptr);
+    gemm32(h, "k_bgemm<OpW32>", OpW32{c, s}, n, 2 * n, nullptr);
+    gemm32(h, "k_bgemm<OpA32>", OpA32{c, s, h->p.dt}, 2 * n, 2 * n, nullptr);
     const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
     const int64_t ainv = MatLayout::A;
     if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, nullptr)) {
@@ -578,16 +591,16 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
       const int64_t Bq = MatLayout::B;
       const BlkView A11{MatLayout::A, 2, 0, 0}, A12{MatLayout::A, 2, 0, 1}, A21{MatLayout::A, 2, 1, 0},
           A22{MatLayout::A, 2, 1, 1}, X1{Bq, 1, 0, 0}, Y{Bq + 1, 1, 0, 0}, Z{Bq + 2, 1, 0, 0}, Si{Bq + 3, 1, 0, 0};
-      const dim3 gcopy((n * n + 255) / 256, M), gb = gemm_grid(n, n, M);
+      const dim3 gcopy((n * n + 255) / 256, M);
       VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, A11, X1));
       launch_gj32(h, "k_gj_inverse<A11>", LuGeo32{vi, h->scratch32, Bq, 1, 0, h->piv32, 2}, n, nullptr);
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, X1, A12, Y, Y, 1.f, 0}, nullptr));
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A21, X1, Z, Z, 1.f, 0}, nullptr));
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A21, Y, Si, A22, -1.f, 1}, nullptr));
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, X1, A12, Y, Y, 1.f, 0}, n, n, nullptr);
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, X1, Z, Z, 1.f, 0}, n, n, nullptr);
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, Y, Si, A22, -1.f, 1}, n, n, nullptr);
       launch_gj32(h, "k_gj_inverse<S>", LuGeo32{vi, h->scratch32, Bq + 3, 1, 0, h->piv32, 2}, n, nullptr);
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, Y, Si, A12, A12, -1.f, 0}, nullptr));
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, Si, Z, A21, A21, -1.f, 0}, nullptr));
-      VS_LAUNCH(h, "k_bgemm<OpBlk32>", k_bgemm<OpBlk32><<<gb, 256, 0, h->stream>>>(OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, nullptr));
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Y, Si, A12, A12, -1.f, 0}, n, n, nullptr);
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Si, Z, A21, A21, -1.f, 0}, n, n, nullptr);
+      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, n, n, nullptr);
       VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
     }
     MP_DISPATCH(h, "k_relax_mp", k_relax_mp, M, (vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv,
@@ -856,6 +869,15 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpT32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpD2_32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpD4_32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpPB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpW32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpA32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpBlk32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));

@@ -250,3 +250,22 @@ def test_farfield_launch_shapes_bitwise_identical():
         k += 1
     assert k >= 4
     g.close()
+
+
+@pytest.mark.parametrize("Ns", [[64, 32, 64, 48, 64, 32, 64, 64], [128, 96, 128]])
+def test_tensor_core_and_fma_operator_products_agree(Ns):
+    # the preconditioners built on the tensor cores (three-part BF16 split, VS_FLAG_TC_GEMM) and with FP32
+    # FMAs lead to the same FP64-accurate step (N = 128 also takes the 2 x 2 block inverse of A)
+    xs, ys = _mixed(Ns, 10, spacing=2.6)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=2, flow_p=(5.0, 8.0, 0, 0), farfield_fp64=True)
+    a = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    b = binding.Suspension(csr(xs, ys), offsets(xs), tc_gemm=True, **kw)
+    a.step(3)
+    b.step(3)
+    counts = [len(x) for x in xs]
+    ax, ay = split(a.positions(), counts)
+    bx, by = split(b.positions(), counts)
+    assert rel_err_per_vesicle(ax, ay, bx, by) <= 1e-12
+    assert np.max(np.abs(a.tension() - b.tension())) <= 1e-10 * np.max(np.abs(b.tension()))
+    a.close()
+    b.close()
