@@ -253,7 +253,22 @@ vs_status vs_mlp_num_params(const vs_mlp* m, int64_t* n);
 /* host FP32 parameters in / out; set also clears the AdamW moments */
 vs_status vs_mlp_set_params(vs_mlp* m, const float* params, int64_t n);
 vs_status vs_mlp_get_params(vs_mlp* m, float* params, int64_t n);
-/* y (device, batch x d_L) = network(x) */
+/*
+ * Per-feature affine maps around the layers (feature normalisation of the training data, Sec. 3.4.2):
+ * the first layer sees (x_j - in_shift_j) in_scale_j (FP32, then BF16), and the output is
+ * z_j out_scale_j + out_shift_j for the last layer's value z. Training compares z with the targets
+ * mapped the other way, (y_j - out_shift_j) (1/out_scale_j) in FP32, so the loss above is taken in
+ * the normalised output coordinates. set: host arrays of d_0, d_0, d_L, d_L floats; a NULL shift
+ * is 0 and a NULL scale 1; all four NULL removes both maps; a zero or non-finite value is
+ * VS_ERR_INVALID_ARG. get: host arrays (each may be NULL). fit: in_shift / out_shift = column means
+ * and in_scale = 1/sd, out_scale = sd (1 for a constant column) of the DEVICE FP32 rows x (rows x
+ * d_0) and y (rows x d_L), FP64 sums; synchronises.
+ */
+vs_status vs_mlp_set_affine(vs_mlp* m, const float* in_shift, const float* in_scale, const float* out_shift,
+                            const float* out_scale);
+vs_status vs_mlp_get_affine(vs_mlp* m, float* in_shift, float* in_scale, float* out_shift, float* out_scale);
+vs_status vs_mlp_fit_affine(vs_mlp* m, const float* x, const float* y, int32_t rows);
+/* y (device, batch x d_L) = network(x), output map included */
 vs_status vs_mlp_forward(vs_mlp* m, const float* x, int32_t batch, float* y);
 /* loss (host) and, when grad (host, n floats) is non-null, its gradient; synchronises */
 vs_status vs_mlp_loss_grad(vs_mlp* m, const float* x, const float* y, int32_t batch, float* loss, float* grad,

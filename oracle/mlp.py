@@ -9,12 +9,19 @@ with the decoupled weight decay w <- w (1 - lr wd) - lr mhat / (sqrt(vhat) + eps
 Parameters of layer l: W_l (d_{l+1} x d_l, row-major) and b_l (d_{l+1}); the flat parameter
 vector is every W_l then every b_l, in layer order.
 
+Optional per-feature affine maps (feature normalisation of the data): affine = (in_shift, in_scale,
+out_shift, out_scale); the first layer sees (x - in_shift) * in_scale and the output is
+z * out_scale + out_shift for the last layer's value z; the loss compares z with the mapped targets
+(y - out_shift) / out_scale. With bf16=True the two maps of the inputs and targets are taken in
+float32 as the GPU does (subtract, then multiply by the float32 scale or float32 reciprocal).
+
 bf16=True rounds the GEMM operands (inputs, hidden activations, weights) to bfloat16 (round to
 nearest even) where the tensor-core path does, accumulating in FP64; gradients are then those of
 the rounded forward pass (straight-through), as the GPU computes them.
 
 Pins (tests/test_oracle_mlp.py): gradients against central finite differences (FP64, rel 1e-7),
-AdamW's first step in closed form, the loss of a perfect prediction is zero.
+AdamW's first step in closed form, the loss of a perfect prediction is zero, and the affine maps
+against the same network with the maps folded into its first and last layers.
 """
 import numpy as np
 
@@ -50,11 +57,37 @@ def unpack(params, dims):
     return ws, bs
 
 
-def forward(params, dims, X, bf16=False):
-    """Returns (Y, cache). X: (batch, d0)."""
+def map_inputs(X, affine, bf16):
+    """(X - in_shift) * in_scale (float32 arithmetic when bf16, else FP64)."""
+    X = np.asarray(X, dtype=np.float64)
+    if affine is None:
+        return X
+    sh, sc = affine[0], affine[1]
+    if bf16:
+        f32 = np.float32
+        return ((X.astype(f32) - np.asarray(sh, f32)) * np.asarray(sc, f32)).astype(np.float64)
+    return (X - np.asarray(sh, np.float64)) * np.asarray(sc, np.float64)
+
+
+def map_targets(Y, affine, bf16):
+    """(Y - out_shift) / out_scale, as (Y - out_shift) * float32(1/out_scale) in float32 when bf16."""
+    Y = np.asarray(Y, dtype=np.float64)
+    if affine is None:
+        return Y
+    sh, sc = affine[2], affine[3]
+    if bf16:
+        f32 = np.float32
+        inv = (f32(1.0) / np.asarray(sc, f32)).astype(f32)
+        return ((Y.astype(f32) - np.asarray(sh, f32)) * inv).astype(np.float64)
+    return (Y - np.asarray(sh, np.float64)) / np.asarray(sc, np.float64)
+
+
+def forward(params, dims, X, bf16=False, affine=None, out_map=True):
+    """Returns (Y, cache). X: (batch, d0). With affine, out_map=False returns the last layer's value
+    before the output map (the quantity the loss sees)."""
     ws, bs = unpack(params, dims)
     rd = bf16_round if bf16 else (lambda a: a)
-    H = [rd(np.asarray(X, dtype=np.float64))]
+    H = [rd(map_inputs(X, affine, bf16))]
     L = len(ws)
     for l in range(L):
         Z = H[-1] @ rd(ws[l]).T + bs[l]
@@ -62,6 +95,8 @@ def forward(params, dims, X, bf16=False):
             H.append(rd(np.maximum(Z, 0.0)))
         else:
             Y = Z
+    if affine is not None and out_map:
+        Y = Y * np.asarray(affine[3], np.float64) + np.asarray(affine[2], np.float64)
     return Y, H
 
 
@@ -111,9 +146,9 @@ def backward(params, dims, cache, dY, bf16=False):
     return np.concatenate([g.ravel() for g in gws] + gbs)
 
 
-def loss_and_gradient(params, dims, X, Y, beta=1.0, ncomp=2, bf16=False):
-    Yhat, cache = forward(params, dims, X, bf16)
-    loss, dY = loss_and_grad_output(Yhat, Y, beta, ncomp)
+def loss_and_gradient(params, dims, X, Y, beta=1.0, ncomp=2, bf16=False, affine=None):
+    Yhat, cache = forward(params, dims, X, bf16, affine, out_map=False)
+    loss, dY = loss_and_grad_output(Yhat, map_targets(Y, affine, bf16), beta, ncomp)
     return loss, backward(params, dims, cache, dY, bf16)
 
 

@@ -45,15 +45,17 @@ def relax_learned(x, y, net):
     standardise, evaluate the network on the Fourier-filtered standardised shape (bfloat16
     operands as on the tensor cores, input first rounded to float32), scale its output, map it
     back to the original frame, add it to X*_r and remove the modes |k| > kmax of the result (the
-    network represents only those modes)."""
+    network represents only those modes). net = (dims, params, scale, kmax[, affine]), affine the
+    network's per-feature input and output maps (oracle.mlp)."""
     from .mlp import forward
     from .standardize import destandardize_disp, fourier_filter, standardize
-    dims, params, scale, kmax = net
+    dims, params, scale, kmax = net[:4]
+    affine = net[4] if len(net) > 4 else None
     N = len(x)
     xr, yr, _ = redistribute(x, y)
     xo, yo, fr = standardize(xr, yr)
     inp = np.concatenate([fourier_filter(xo, kmax), fourier_filter(yo, kmax)])[None, :]
-    out, _ = forward(params, dims, inp, bf16=True)
+    out, _ = forward(params, dims, inp, bf16=True, affine=affine)
     dx, dy = destandardize_disp(scale * out[0, :N], scale * out[0, N:], fr)
     return np.concatenate([fourier_filter(xr + dx, kmax), fourier_filter(yr + dy, kmax)])
 

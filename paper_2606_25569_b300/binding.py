@@ -55,6 +55,11 @@ FUNCTIONS = {
                                      ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_mlp_set_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "vs_mlp_get_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "vs_mlp_fit_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "vs_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "vs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
@@ -321,6 +326,27 @@ class Mlp:
         p = np.empty(self.nparam, dtype=np.float32)
         self._check(lib().vs_mlp_get_params(self._h, _ptr(p), len(p)))
         return p
+
+    def set_affine(self, in_shift=None, in_scale=None, out_shift=None, out_scale=None):
+        """Per-feature input and output maps (vs_mlp_set_affine); None is the identity part."""
+        arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+               for a in (in_shift, in_scale, out_shift, out_scale)]
+        for a, d in zip(arr, (self.dims[0], self.dims[0], self.dims[-1], self.dims[-1])):
+            if a is not None and a.shape != (d,):
+                raise ValueError("affine map of width %d expected" % d)
+        self._check(lib().vs_mlp_set_affine(self._h, *[None if a is None else _ptr(a) for a in arr]))
+
+    def get_affine(self):
+        """(in_shift, in_scale, out_shift, out_scale) as FP32 host arrays."""
+        d0, dL = self.dims[0], self.dims[-1]
+        out = [np.empty(d0, np.float32), np.empty(d0, np.float32), np.empty(dL, np.float32),
+               np.empty(dL, np.float32)]
+        self._check(lib().vs_mlp_get_affine(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def fit_affine(self, x_dev, y_dev, rows):
+        """Maps from the column means and deviations of device rows x, y (vs_mlp_fit_affine)."""
+        self._check(lib().vs_mlp_fit_affine(self._h, _ptr(x_dev), _ptr(y_dev), int(rows)))
 
     def forward(self, x_dev, y_dev, batch):
         self._check(lib().vs_mlp_forward(self._h, _ptr(x_dev), int(batch), _ptr(y_dev)))

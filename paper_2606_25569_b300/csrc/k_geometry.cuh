@@ -36,6 +36,8 @@ struct GeomOut {
   double* area;    // [M]
   double* length;  // [M]
   float4* g32;     // FP32 (1/|X_alpha|, x_s, y_s, 0) for the FP32 operator products (may be null)
+  float4* sdf;     // 3 per point, double-float pairs for the self matrix (may be null):
+                   //   (x - x_0, y - y_0), (|X_alpha| / (4 pi mu), -R(0)/2 - (2 pi/N) log|X_alpha|), (x_s, y_s)
 };
 
 // Force/source outputs (only written when `f` is non-null). With f_in non-null the density is
@@ -72,9 +74,10 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     ys[i] = xy[2 * o + N + i];
   }
   __syncthreads();
+  float2 px = make_float2(0.f, 0.f), py = px;
   if (act) {
-    w1[i] = df_of(xs[i] - xs[0]);
-    w2[i] = df_of(ys[i] - ys[0]);
+    px = w1[i] = df_of(xs[i] - xs[0]);
+    py = w2[i] = df_of(ys[i] - ys[0]);
   }
   __syncthreads();
   double xa = 0.0, ya = 0.0;
@@ -110,6 +113,14 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     g.bx[o + i] = bx;
     g.by[o + i] = by;
     if (g.g32) g.g32[o + i] = make_float4((float)(1.0 / sa), (float)tx, (float)ty, 0.f);
+    if (g.sdf) {  // once per point here instead of once per tile in the self matrix (FP64 is slow)
+      const float2 c = df_of(sa / (4.0 * VS_PI * mu)), lpd = df_of(-0.5 * T[N] - dal * log(sa));
+      const float2 a = df_of(tx), b = df_of(ty);
+      float4* q = g.sdf + 3 * (o + i);
+      q[0] = make_float4(px.x, px.y, py.x, py.y);
+      q[1] = make_float4(c.x, c.y, lpd.x, lpd.y);
+      q[2] = make_float4(a.x, a.y, b.x, b.y);
+    }
   }
   if (i == 0) {
     g.area[v] = area;

@@ -24,8 +24,9 @@ constexpr uint32_t MM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(M
 constexpr long long MM_WAIT_LIMIT = 1ll << 26;
 enum : unsigned { ERR_MMA_TIMEOUT = 16u };
 
-// epilogue: v = acc (+ bias[n]); RELU: max(v, 0); MASK: v * (mask[m][n] > 0);
-// then write whichever of out_f32 [m][n], out_bf [m][n], out_bfT [n][m] is non-null.
+// epilogue: v = acc (+ bias[n]); RELU: max(v, 0); MASK: v * (mask[m][n] > 0); with oscale non-null
+// v = v oscale[n] + oshift[n] (the network's output map); then write whichever of out_f32 [m][n],
+// out_bf [m][n], out_bfT [n][m] is non-null.
 enum : int { EPI_NONE = 0, EPI_RELU = 1, EPI_MASK = 2 };
 
 struct GemmArgs {
@@ -38,6 +39,7 @@ struct GemmArgs {
   __nv_bfloat16* out_bf; int64_t ld_bf;
   __nv_bfloat16* out_bfT; int64_t ld_bfT;
   const __nv_bfloat16* mask; int64_t ld_mask;
+  const float* oscale; const float* oshift;  // [N] each, or both null
   unsigned* err;
 };
 
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
           if (g.bias) x += g.bias[gn];
           if (g.act == EPI_RELU) x = fmaxf(x, 0.f);
           if (g.act == EPI_MASK && !(__bfloat162float(g.mask[(int64_t)gm * g.ld_mask + gn]) > 0.f)) x = 0.f;
+          if (g.oscale) x = fmaf(x, g.oscale[gn], g.oshift[gn]);
           if (g.out_f32) g.out_f32[(int64_t)gm * g.ld_f32 + gn] = x;
           const __nv_bfloat16 b = __float2bfloat16_rn(x);
           if (g.out_bf) g.out_bf[(int64_t)gm * g.ld_bf + gn] = b;
@@ -161,21 +164,30 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
 }
 
 // FP32 rows (batch x d) -> BF16 rows and BF16 transposed (d x Bp), zero rows for batch <= b < Bp.
-__global__ void k_rows_to_bf16(const float* __restrict__ x, int batch, int Bp, int d, __nv_bfloat16* __restrict__ out,
+// With shift non-null each feature is first mapped to (x[j] - shift[j]) scale[j] in FP32 (the network's
+// input map).
+__global__ void k_rows_to_bf16(const float* __restrict__ x, int batch, int Bp, int d, const float* __restrict__ shift,
+                               const float* __restrict__ scale, __nv_bfloat16* __restrict__ out,
                                __nv_bfloat16* __restrict__ outT) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)Bp * d) return;
   const int b = (int)(e / d), j = (int)(e - (int64_t)b * d);
-  const __nv_bfloat16 v = __float2bfloat16_rn(b < batch ? x[e] : 0.f);
+  float xv = b < batch ? x[e] : 0.f;
+  if (shift && b < batch) xv = __fmul_rn(__fsub_rn(xv, shift[j]), scale[j]);
+  const __nv_bfloat16 v = __float2bfloat16_rn(xv);
   out[e] = v;
   outT[(int64_t)j * Bp + b] = v;
 }
 
 // Per-sample loss (Sec. 3.4.2) and its gradient: one CTA per sample row b.
 //   loss_b = ||e|| / ||y|| + beta ||D e|| / ||D y||,  e = yhat - y,
+// where, with yshift non-null, y is the target in the network's output coordinates,
+// (target[j] - yshift[j]) yinv[j] in FP32, and yhat is the output before the output map.
 //   D = periodic forward difference inside each of ncomp equal blocks of the row;
 //   dL/dyhat = (e / (||e|| ||y||) + beta D^T D e / (||D e|| ||D y||)) / batch.
-__global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat, const float* __restrict__ y, int batch,
+__global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat, const float* __restrict__ yraw,
+                                                  const float* __restrict__ yshift, const float* __restrict__ yinv,
+                                                  float* __restrict__ y, int batch,
                                                   int d, int ncomp, float beta, float* __restrict__ g_f32,
                                                   __nv_bfloat16* __restrict__ g_bf, __nv_bfloat16* __restrict__ g_bfT,
                                                   int Bp, float* __restrict__ loss_b) {
@@ -191,6 +203,14 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
       g_bfT[(int64_t)j * Bp + b] = __float2bfloat16_rn(0.f);
     }
     return;
+  }
+  // y: the row's targets in output coordinates (a scratch row when yshift is set, else yraw itself)
+  if (yshift) {
+    for (int j = tid; j < d; j += blockDim.x)
+      y[(int64_t)b * d + j] = __fmul_rn(__fsub_rn(yraw[(int64_t)b * d + j], yshift[j]), yinv[j]);
+    __syncthreads();
+  } else {
+    y = const_cast<float*>(yraw);
   }
   double se = 0.0, sy = 0.0;
   for (int j = tid; j < d; j += blockDim.x) {
@@ -224,6 +244,24 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
     g_bf[(int64_t)b * d + j] = bv;
     g_bfT[(int64_t)j * Bp + b] = bv;
   }
+}
+
+// Column mean and standard deviation of a row-major FP32 matrix (rows x cols), FP64 sums in a fixed
+// order, one thread per column: mean[c], and sd[c] = sqrt(mean of squared deviations).
+__global__ void k_colstats(const float* __restrict__ X, int rows, int cols, double* __restrict__ mean,
+                           double* __restrict__ sd) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0;
+  for (int r = 0; r < rows; ++r) s += X[(int64_t)r * cols + c];
+  const double m = s / rows;
+  double q = 0.0;
+  for (int r = 0; r < rows; ++r) {
+    const double d = X[(int64_t)r * cols + c] - m;
+    q += d * d;
+  }
+  mean[c] = m;
+  sd[c] = sqrt(q / rows);
 }
 
 // Mean of the per-sample losses (fixed order, one thread).

@@ -8,7 +8,7 @@
 // smooth remainder, with the standard 2D Stokeslet (1/4 pi mu)(-log|r| I + r r^T/|r|^2).
 // Row-major, rows [x-velocity(0..N-1), y-velocity(0..N-1)], columns [f_x, f_y]. k_self_matrix writes
 // FP64 S; k_self_matrix_df writes the split S = S_hi + S_lo (two FP32 matrices, the S and SL blocks of
-// the FP32 scratch) for the mixed-precision path, with everything after the logarithm in double-float.
+// the FP32 scratch) for the mixed-precision path, entirely in double-float.
 #pragma once
 #include "common.cuh"
 #include "dfloat.cuh"
@@ -128,13 +128,13 @@ __device__ __forceinline__ void self_store_df(float* Sh, float* Sl, int n2, int 
   Sh[e3] = syy.x; Sl[e3] = syy.y;
 }
 
-// The same matrix as k_self_matrix, as S_hi + S_lo: the log term lp in FP64 (log|r|^2 minus the tabulated
-// log 4 sin^2), then the r r^T/|r|^2 terms and the products in double-float. Same grid and tiling.
-__global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const double* __restrict__ xy,
-                                                        const double* __restrict__ sa,
-                                                        const double* __restrict__ tx,
-                                                        const double* __restrict__ ty,
-                                                        const double* __restrict__ tab, double mu,
+// The same matrix as k_self_matrix, as S_hi + S_lo, entirely in double-float: log|r|^2 by log_df minus the
+// tabulated log 4 sin^2, the r r^T/|r|^2 terms and the products. The per-point inputs (positions relative
+// to point 0, weights |X_alpha|/(4 pi mu), the diagonal log term and the tangents) come as double-float
+// pairs from k_geometry and the table in double-float, so no FP64 arithmetic is left here. Same grid and
+// tiling as k_self_matrix.
+__global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const float4* __restrict__ sdf,
+                                                        const float2* __restrict__ tabdf,
                                                         const float4* __restrict__ logtab,
                                                         float* __restrict__ scratch32, int slot,
                                                         const int* __restrict__ active) {
@@ -148,37 +148,32 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   const int bj = bi + t;
   __shared__ float2 kl[SM_TILE][SM_TILE + 1], kxx[SM_TILE][SM_TILE + 1], kxy[SM_TILE][SM_TILE + 1],
       kyy[SM_TILE][SM_TILE + 1];
-  __shared__ float2 cc[2][SM_TILE];  // sa_j / (4 pi mu) for the tile's columns (0) and its mirror's (1)
-  __shared__ float2 pr[2][2][SM_TILE];  // [rows, cols][x, y]: points of the tile relative to point 0
+  __shared__ float2 cc[2][SM_TILE];     // |X_alpha|_j / (4 pi mu) for the tile's columns (0) and its mirror's (1)
+  __shared__ float4 pr[2][SM_TILE];     // [rows, cols]: points of the tile relative to point 0 (x, y pairs)
   __shared__ float4 lt[LOG_TAB];
   __shared__ float2 am[2 * SM_TILE];  // the table's log constant at m = (bi - bj) 16 + d, d = -15..16
+  __shared__ float2 kc[2];            // 2 pi / N and -pi / N in double-float
   for (int e = threadIdx.x; e < LOG_TAB; e += blockDim.x) lt[e] = logtab[e];
   const int li = threadIdx.x / SM_TILE, lj = threadIdx.x % SM_TILE;
   const int64_t o = vi.off[v];
-  const double* T = tab + vi.toff[v];
-  const double dal64 = 2.0 * VS_PI / N;
-  __shared__ float2 kc[2];  // 2 pi / N and -pi / N in double-float, converted once per CTA
-  if (threadIdx.x == 0) {
+  const float4* P = sdf + 3 * o;
+  if (threadIdx.x < 2 * SM_TILE) {
+    const int w = threadIdx.x / SM_TILE, l = threadIdx.x % SM_TILE;
+    const int jj = (w ? bi : bj) * SM_TILE + l, k = (w ? bj : bi) * SM_TILE + l;
+    cc[w][l] = (jj < N) ? make_float2(P[3 * jj + 1].x, P[3 * jj + 1].y) : make_float2(0.f, 0.f);
+    pr[w][l] = (k < N) ? P[3 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if (threadIdx.x < 4 * SM_TILE) {
+    const int d = threadIdx.x - 2 * SM_TILE - (SM_TILE - 1);
+    int m = ((bi - bj) * SM_TILE + d) % N;
+    if (m < 0) m += N;
+    am[d + SM_TILE - 1] = tabdf[vi.toff[v] + 17 * N + m];
+  } else if (threadIdx.x == 4 * SM_TILE) {
+    const double dal64 = 2.0 * VS_PI / N;
     kc[0] = df_of(dal64);
     kc[1] = df_of(-0.5 * dal64);
   }
-  __syncthreads();  // lt, kc
-  const float2 dal = kc[0];
-  if (threadIdx.x < 2 * SM_TILE) {
-    const int w = threadIdx.x / SM_TILE, jj = (w ? bi : bj) * SM_TILE + threadIdx.x % SM_TILE;
-    cc[w][threadIdx.x % SM_TILE] = (jj < N) ? df_of(sa[o + jj] / (4.0 * VS_PI * mu)) : make_float2(0.f, 0.f);
-  } else if (threadIdx.x < 6 * SM_TILE) {
-    const int e = threadIdx.x - 2 * SM_TILE, w = e / (2 * SM_TILE), comp = (e / SM_TILE) & 1, l = e % SM_TILE;
-    const int k = (w ? bj : bi) * SM_TILE + l;
-    const double* X = xy + 2 * o + comp * N;
-    pr[w][comp][l] = (k < N) ? df_of(X[k] - X[0]) : make_float2(0.f, 0.f);
-  } else if (threadIdx.x < 8 * SM_TILE) {
-    const int d = threadIdx.x - 6 * SM_TILE - (SM_TILE - 1);
-    int m = ((bi - bj) * SM_TILE + d) % N;
-    if (m < 0) m += N;
-    am[d + SM_TILE - 1] = df_of(T[17 * N + m]);
-  }
   __syncthreads();
+  const float2 dal = kc[0];
   const int64_t NN = (int64_t)N * N;
   float* Sh = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::S) * NN;
   float* Sl = scratch32 + vi.moff[v] + (MatLayout::slot(slot) + MatLayout::SL) * NN;
@@ -187,11 +182,10 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
   float2 lp, axx, axy, ayy;
   const bool in = i < N && j < N;
   if (in) {
-    const int m = (i - j < 0) ? i - j + N : i - j;
-    const double R = T[N + m];
     if (i != j) {
-      const float2 rxd = df_add(pr[0][0][li], make_float2(-pr[1][0][lj].x, -pr[1][0][lj].y));
-      const float2 ryd = df_add(pr[0][1][li], make_float2(-pr[1][1][lj].x, -pr[1][1][lj].y));
+      const float4 pi = pr[0][li], pj = pr[1][lj];
+      const float2 rxd = df_add(make_float2(pi.x, pi.y), make_float2(-pj.x, -pj.y));
+      const float2 ryd = df_add(make_float2(pi.z, pi.w), make_float2(-pj.z, -pj.w));
       const float2 xx = df_mul(rxd, rxd), xy2 = df_mul(rxd, ryd), yy = df_mul(ryd, ryd);
       const float2 r2 = df_add(xx, yy);
       lp = df_add(am[li - lj + SM_TILE - 1], df_mul(kc[1], log_df(r2, lt)));
@@ -200,8 +194,9 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const doubl
       axy = df_mul(xy2, ir2);
       ayy = df_mul(yy, ir2);
     } else {
-      lp = df_of(-0.5 * R - dal64 * log(sa[o + i]));
-      const float2 a = df_of(tx[o + i]), b = df_of(ty[o + i]);
+      const float4 q = P[3 * i + 1], tg = P[3 * i + 2];
+      lp = make_float2(q.z, q.w);
+      const float2 a = make_float2(tg.x, tg.y), b = make_float2(tg.z, tg.w);
       axx = df_mul(a, a);
       axy = df_mul(a, b);
       ayy = df_mul(b, b);

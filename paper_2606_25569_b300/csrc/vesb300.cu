@@ -120,10 +120,12 @@ struct DevLayout {
   double* tab = nullptr;
   float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
   float4* logtab = nullptr;  // (log c_k, 1/c_k) as FP32 pairs, c_k = 1 + (k + 1/2)/LOG_TAB (log_df)
+  float2* tabdf = nullptr;   // double-float copy of tab (hi, lo)
   VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
     cudaFree(owner); cudaFree(chunk); cudaFree(chunk1k); cudaFree(tab); cudaFree(tab32); cudaFree(logtab);
+    cudaFree(tabdf);
     *this = DevLayout{};
   }
 };
@@ -150,6 +152,13 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   std::vector<float> t32(L.tab.begin(), L.tab.end());
   VS_TRY(dalloc(&D.tab32, t32.size()));
   VS_TRY(upload(D.tab32, t32.data(), t32.size(), s));
+  std::vector<float2> tdf(L.tab.size());
+  for (size_t k = 0; k < L.tab.size(); ++k) {
+    const float hi = (float)L.tab[k];
+    tdf[k] = make_float2(hi, (float)(L.tab[k] - (double)hi));
+  }
+  VS_TRY(dalloc(&D.tabdf, tdf.size()));
+  VS_TRY(upload(D.tabdf, tdf.data(), tdf.size(), s));
   std::vector<float4> lt(LOG_TAB);
   for (int k = 0; k < LOG_TAB; ++k) {
     const long double c = 1.0L + (k + 0.5L) / LOG_TAB, lc = std::log(c), rc = 1.0L / c;
@@ -175,6 +184,7 @@ struct SourceBufs {
   double *sa = nullptr, *tx = nullptr, *ty = nullptr, *bx = nullptr, *by = nullptr;
   double *area = nullptr, *length = nullptr;
   float4* g32 = nullptr;
+  float4* sdf = nullptr;
   cudaError_t alloc(int64_t P, int M) {
     cudaError_t e;
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -184,16 +194,17 @@ struct SourceBufs {
     VS_TRY(dalloc(&sa, P)); VS_TRY(dalloc(&tx, P)); VS_TRY(dalloc(&ty, P));
     VS_TRY(dalloc(&bx, P)); VS_TRY(dalloc(&by, P));
     VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M)); VS_TRY(dalloc(&g32, P));
+    VS_TRY(dalloc(&sdf, 3 * P));
 #undef VS_TRY
     return cudaSuccess;
   }
   void release() {
     cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
-    cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32);
+    cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32); cudaFree(sdf);
     *this = SourceBufs{};
   }
-  GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32}; }
+  GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32, sdf}; }
   PointGeom pg() const { return PointGeom{sa, tx, ty}; }
 };
 
@@ -231,6 +242,11 @@ struct vs_mlp {
   float *g32[2] = {nullptr, nullptr};
   __nv_bfloat16 *gbf[2] = {nullptr, nullptr}, *gbfT[2] = {nullptr, nullptr};
   float *loss_b = nullptr, *loss = nullptr;
+  // per-feature affine maps: [in_shift d_0 | in_scale d_0 | out_shift d_L | out_scale d_L | 1/out_scale d_L]
+  float* aff = nullptr;
+  bool has_in = false, has_out = false;
+  float* ynorm = nullptr;             // targets in output coordinates (Bcap x d_L)
+  double* stats = nullptr;            // column means and deviations (2 max(d_0, d_L))
   unsigned* err = nullptr;
   int64_t t = 0;
   int64_t launches = 0;
@@ -414,9 +430,8 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   const int M = L.M, n = L.nmax;
   const VesIndex vi = h->D.vi();
   if (mixed(h)) {
-    VS_LAUNCH(h, "k_self_matrix_df", k_self_matrix_df<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
-                                                                      h->D.tab, h->p.mu, h->D.logtab, h->scratch32,
-                                                                      s, active));
+    VS_LAUNCH(h, "k_self_matrix_df", k_self_matrix_df<<<self_grid(n, M), 256, 0, h->stream>>>(vi, h->B.sdf, h->D.tabdf,
+                                                                      h->D.logtab, h->scratch32, s, active));
   } else {
     VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(n, M), 256, 0, h->stream>>>(vi, xy, h->B.sa, h->B.tx, h->B.ty,
                                                                       h->D.tab, h->p.mu, h->scratch, s, active));
@@ -562,7 +577,7 @@ vs_status tune_far_field(vs_suspension* h) {
   return VS_OK;
 }
 
-vs_status mlp_forward(vs_mlp* h, const float* x, int batch);
+vs_status mlp_forward(vs_mlp* h, const float* x, int batch, bool out_map);
 const float* mlp_output(const vs_mlp* h);
 
 // Exact relaxation (Eq. relaxation_disc) of the points xs into xo, operators built in slot s.
@@ -645,7 +660,7 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, xs, h->u, h->D.tab, xo, h->u_r));
   VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, 2 * L.nmax, h->frames, h->net_kmax));
   VS_CK(h, cudaGetLastError(), "standardise");
-  vs_status st = mlp_forward(h->net, h->xin, L.M);
+  vs_status st = mlp_forward(h->net, h->xin, L.M, true);
   if (st != VS_OK) { h->msg = "network forward failed"; return st; }
   VS_LAUNCH(h, "k_destandardize_add", k_destandardize_add<<<L.M, NMAX, 0, h->stream>>>(vi, mlp_output(h->net), 2 * L.nmax,
                                                                                        h->net_scale, h->frames, xo));
@@ -1264,10 +1279,14 @@ vs_status mlp_refresh_bf16(vs_mlp* h) {
   return VS_OK;
 }
 
-vs_status mlp_forward(vs_mlp* h, const float* x, int batch) {
+// out_map: apply the output map (inference); training compares the output before it with the mapped
+// targets.
+vs_status mlp_forward(vs_mlp* h, const float* x, int batch, bool out_map) {
   const int Bp = round_up(batch, MM_BM);
-  const int64_t n0 = (int64_t)Bp * h->dims[0];
-  k_rows_to_bf16<<<(unsigned)((n0 + 255) / 256), 256, 0, h->stream>>>(x, batch, Bp, h->dims[0], h->H[0], h->HT[0]);
+  const int d0 = h->dims[0], dL = h->dims[h->L];
+  const int64_t n0 = (int64_t)Bp * d0;
+  k_rows_to_bf16<<<(unsigned)((n0 + 255) / 256), 256, 0, h->stream>>>(x, batch, Bp, d0, h->has_in ? h->aff : nullptr,
+                                                                      h->aff + d0, h->H[0], h->HT[0]);
   h->launches += 1;
   VS_CK(h, cudaGetLastError(), "mlp input");
   for (int l = 0; l < h->L; ++l) {
@@ -1282,6 +1301,10 @@ vs_status mlp_forward(vs_mlp* h, const float* x, int batch) {
     } else {
       a.out_f32 = h->yhat;
       a.ld_f32 = h->dims[l + 1];
+      if (out_map && h->has_out) {
+        a.oshift = h->aff + 2 * d0;
+        a.oscale = h->aff + 2 * d0 + dL;
+      }
     }
     vs_status st = mlp_gemm(h, a);
     if (st != VS_OK) return st;
@@ -1293,7 +1316,10 @@ vs_status mlp_forward(vs_mlp* h, const float* x, int batch) {
 vs_status mlp_backward(vs_mlp* h, const float* y, int batch) {
   const int Bp = round_up(batch, MM_BM);
   const int dL = h->dims[h->L];
-  k_mlp_loss<<<Bp, 128, 0, h->stream>>>(h->yhat, y, batch, dL, h->ncomp, h->beta, h->g32[0], h->gbf[0], h->gbfT[0], Bp,
+  const int d0 = h->dims[0];
+  const float* ysh = h->has_out ? h->aff + 2 * d0 : nullptr;
+  k_mlp_loss<<<Bp, 128, 0, h->stream>>>(h->yhat, y, ysh, h->aff + 2 * d0 + 2 * dL, h->ynorm, batch, dL, h->ncomp, h->beta,
+                                        h->g32[0], h->gbf[0], h->gbfT[0], Bp,
                                         h->loss_b);
   k_mean<<<1, 32, 0, h->stream>>>(h->loss_b, batch, h->loss);
   h->launches += 2;
@@ -1347,6 +1373,7 @@ void mlp_free(vs_mlp* h) {
   for (auto* p : h->HT) cudaFree(p);
   for (int i = 0; i < 2; ++i) { cudaFree(h->g32[i]); cudaFree(h->gbf[i]); cudaFree(h->gbfT[i]); }
   cudaFree(h->loss_b); cudaFree(h->loss); cudaFree(h->err);
+  cudaFree(h->aff); cudaFree(h->ynorm); cudaFree(h->stats);
 }
 
 }  // namespace
@@ -1411,6 +1438,9 @@ vs_status vs_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_batch,
     VS_M(dalloc(&h->gbfT[i], (int64_t)h->Bcap * dmax));
   }
   VS_M(dalloc(&h->loss_b, h->Bcap)); VS_M(dalloc(&h->loss, 1)); VS_M(dalloc(&h->err, 1));
+  VS_M(dalloc(&h->aff, 2 * (int64_t)h->dims[0] + 3 * (int64_t)h->dims[h->L]));
+  VS_M(dalloc(&h->ynorm, (int64_t)h->Bcap * h->dims[h->L]));
+  VS_M(dalloc(&h->stats, 2 * (int64_t)std::max(h->dims[0], h->dims[h->L])));
   VS_M(cudaMemset(h->err, 0, sizeof(unsigned)));
   VS_M(cudaMemset(h->w, 0, h->nparam * sizeof(float)));
   VS_M(cudaMemset(h->m, 0, h->nparam * sizeof(float)));
@@ -1447,9 +1477,80 @@ vs_status vs_mlp_get_params(vs_mlp* h, float* params, int64_t n) {
   return VS_OK;
 }
 
+vs_status vs_mlp_set_affine(vs_mlp* h, const float* in_shift, const float* in_scale, const float* out_shift,
+                            const float* out_scale) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  const int d0 = h->dims[0], dL = h->dims[h->L];
+  std::vector<float> a(2 * d0 + 3 * dL);
+  for (int j = 0; j < d0; ++j) {
+    a[j] = in_shift ? in_shift[j] : 0.f;
+    a[d0 + j] = in_scale ? in_scale[j] : 1.f;
+  }
+  for (int j = 0; j < dL; ++j) {
+    a[2 * d0 + j] = out_shift ? out_shift[j] : 0.f;
+    const float t = out_scale ? out_scale[j] : 1.f;
+    if (!(t != 0.f) || !std::isfinite(t)) return VS_ERR_INVALID_ARG;
+    a[2 * d0 + dL + j] = t;
+    a[2 * d0 + 2 * dL + j] = 1.f / t;
+  }
+  for (float x : a)
+    if (!std::isfinite(x)) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaMemcpyAsync(h->aff, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream), "set affine");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "set affine");
+  h->has_in = in_shift || in_scale;
+  h->has_out = out_shift || out_scale;
+  return VS_OK;
+}
+
+vs_status vs_mlp_get_affine(vs_mlp* h, float* in_shift, float* in_scale, float* out_shift, float* out_scale) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  const int d0 = h->dims[0], dL = h->dims[h->L];
+  std::vector<float> a(2 * d0 + 3 * dL);
+  VS_CK(h, cudaMemcpyAsync(a.data(), h->aff, a.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "get affine");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "get affine");
+  for (int j = 0; j < d0; ++j) {
+    if (in_shift) in_shift[j] = h->has_in ? a[j] : 0.f;
+    if (in_scale) in_scale[j] = h->has_in ? a[d0 + j] : 1.f;
+  }
+  for (int j = 0; j < dL; ++j) {
+    if (out_shift) out_shift[j] = h->has_out ? a[2 * d0 + j] : 0.f;
+    if (out_scale) out_scale[j] = h->has_out ? a[2 * d0 + dL + j] : 1.f;
+  }
+  return VS_OK;
+}
+
+vs_status vs_mlp_fit_affine(vs_mlp* h, const float* x, const float* y, int32_t rows) {
+  if (!h || !x || !y || rows < 1) return VS_ERR_INVALID_ARG;
+  const int d0 = h->dims[0], dL = h->dims[h->L];
+  std::vector<double> st(2 * (size_t)std::max(d0, dL));
+  std::vector<float> sh_in(d0), sc_in(d0), sh_out(dL), sc_out(dL);
+  const int dmx = std::max(d0, dL);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int d = pass ? dL : d0;
+    k_colstats<<<(d + 127) / 128, 128, 0, h->stream>>>(pass ? y : x, rows, d, h->stats, h->stats + dmx);
+    h->launches += 1;
+    VS_CK(h, cudaGetLastError(), "fit affine");
+    VS_CK(h, cudaMemcpyAsync(st.data(), h->stats, 2 * dmx * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+          "fit affine");
+    VS_CK(h, cudaStreamSynchronize(h->stream), "fit affine");
+    for (int j = 0; j < d; ++j) {
+      const double m = st[j], sd = st[dmx + j];
+      const bool flat = !(sd > 0.0) || !std::isfinite(sd);
+      if (pass) {
+        sh_out[j] = (float)m;
+        sc_out[j] = flat ? 1.f : (float)sd;
+      } else {
+        sh_in[j] = (float)m;
+        sc_in[j] = flat ? 1.f : (float)(1.0 / sd);
+      }
+    }
+  }
+  return vs_mlp_set_affine(h, sh_in.data(), sc_in.data(), sh_out.data(), sc_out.data());
+}
+
 vs_status vs_mlp_forward(vs_mlp* h, const float* x, int32_t batch, float* y) {
   if (!h || !x || !y || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
-  vs_status st = mlp_forward(h, x, batch);
+  vs_status st = mlp_forward(h, x, batch, true);
   if (st != VS_OK) return st;
   const int dL = h->dims[h->L];
   VS_CK(h, cudaMemcpyAsync(y, h->yhat, (size_t)batch * dL * sizeof(float), cudaMemcpyDeviceToDevice, h->stream),
@@ -1461,7 +1562,7 @@ vs_status vs_mlp_loss_grad(vs_mlp* h, const float* x, const float* y, int32_t ba
                            int64_t n) {
   if (!h || !x || !y || !loss || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
   if (grad && n != h->nparam) return VS_ERR_INVALID_ARG;
-  vs_status st = mlp_forward(h, x, batch);
+  vs_status st = mlp_forward(h, x, batch, false);
   if (st == VS_OK) st = mlp_backward(h, y, batch);
   if (st != VS_OK) return st;
   VS_CK(h, cudaMemcpyAsync(loss, h->loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream), "loss");
@@ -1471,7 +1572,7 @@ vs_status vs_mlp_loss_grad(vs_mlp* h, const float* x, const float* y, int32_t ba
 
 vs_status vs_mlp_train_step(vs_mlp* h, const float* x, const float* y, int32_t batch, const vs_adamw* opt, float* loss) {
   if (!h || !x || !y || !opt || batch < 1 || batch > h->Bcap) return VS_ERR_INVALID_ARG;
-  vs_status st = mlp_forward(h, x, batch);
+  vs_status st = mlp_forward(h, x, batch, false);
   if (st == VS_OK) st = mlp_backward(h, y, batch);
   if (st != VS_OK) return st;
   h->t += 1;

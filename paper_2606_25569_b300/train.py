@@ -60,20 +60,31 @@ def relative_errors(net, X, Y, batch):
 
 
 def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, lr_min=1e-5, beta=0.1,
-                     holdout=0.1, seed=0, stream=None, ncomp=2, serve_batch=0):
+                     holdout=0.1, seed=0, stream=None, ncomp=2, serve_batch=0, normalise=True):
     """Train on (X, Y); the last `holdout` fraction is held out. AdamW starts at lr (Sec. 3.4.2:
     1e-3) and decays on a cosine to lr_min over the epochs. The network can afterwards run batches of
-    up to max(batch, serve_batch) rows (a suspension needs at least its vesicle count). Returns a dict
-    with the network, its output scale, the loss history, held-out errors and timings."""
+    up to max(batch, serve_batch) rows (a suspension needs at least its vesicle count).
+
+    normalise: every input and output feature is mapped to zero mean and unit deviation over the
+    training rows (vs_mlp_fit_affine; the maps are part of the network, so the output scale is 1).
+    This matters here: the standardised shapes differ from each other by ~1e-2 of their size, below
+    what a bfloat16 input resolves next to the shape itself. Otherwise the targets are divided by
+    their RMS (the returned scale). Returns a dict with the network, its output scale, the loss
+    history, held-out errors and timings."""
     import torch
     n = X.shape[0]
     nh = int(round(holdout * n))
     ntr = n - nh
-    scale = float(torch.sqrt(torch.mean(Y[:ntr].double() ** 2)).item())
-    Yn = (Y / scale).contiguous()
     dims = [X.shape[1]] + list(hidden) + [Y.shape[1]]
     net = binding.Mlp(dims, max_batch=max(batch, serve_batch), ncomp=ncomp, beta=beta, stream=stream)
     net.set_params(he_uniform(dims, np.random.default_rng(seed)))
+    if normalise:
+        scale = 1.0
+        Yn = Y
+        net.fit_affine(X[:ntr].contiguous(), Y[:ntr].contiguous(), ntr)
+    else:
+        scale = float(torch.sqrt(torch.mean(Y[:ntr].double() ** 2)).item())
+        Yn = (Y / scale).contiguous()
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
     hist = []

@@ -58,7 +58,8 @@ def test_relax_map_matches_oracle():
     assert rel_err_per_vesicle(gx, gy, rx, ry) <= 1e-10
 
 
-def test_hybrid_step_matches_oracle():
+@pytest.mark.parametrize("with_affine", [False, True])
+def test_hybrid_step_matches_oracle(with_affine):
     N, M = 64, 4
     xs, ys = _shapes(M, N, 3)
     dims = [2 * N, 256, 256, 2 * N]
@@ -66,10 +67,17 @@ def test_hybrid_step_matches_oracle():
     params = init_params(dims, rng).astype(np.float32).astype(np.float64)
     scale = 1e-3
     kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(1.0, 0.0, 0.0, 0.0))
-    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale, 31), **kw))
     stream = torch.cuda.current_stream()
     net = binding.Mlp(dims, max_batch=M, stream=stream)
     net.set_params(params)
+    relax_net = (dims, params, scale, 31)
+    if with_affine:
+        f32 = lambda a: a.astype(np.float32).astype(np.float64)
+        aff = (f32(0.05 * rng.standard_normal(2 * N)), f32(rng.uniform(1.0, 20.0, 2 * N)),
+               f32(0.1 * rng.standard_normal(2 * N)), f32(rng.uniform(0.2, 1.0, 2 * N)))
+        net.set_affine(*aff)
+        relax_net = relax_net + (aff,)
+    o = OracleSuspension(xs, ys, Params(relax_net=relax_net, **kw))
     g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
     g.set_network(net, scale, 31)
     for _ in range(3):

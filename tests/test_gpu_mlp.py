@@ -74,3 +74,60 @@ def test_adamw_step_and_training_reduces_loss():
     assert np.max(np.abs(got - expect)) <= 2e-6
     losses = [net.train_step(xd, yd, batch, want_loss=True) for _ in range(60)]
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def _affine(rng):
+    return (0.3 * rng.standard_normal(DIMS[0]), rng.uniform(0.5, 4.0, DIMS[0]), 0.2 * rng.standard_normal(DIMS[-1]),
+            rng.uniform(0.05, 2.0, DIMS[-1]))
+
+
+def test_forward_and_gradient_with_affine_maps_match_oracle():
+    batch = 256
+    p, X, Y = _data(batch, 7)
+    rng = np.random.default_rng(8)
+    aff = tuple(a.astype(np.float32).astype(np.float64) for a in _affine(rng))
+    p32 = p.astype(np.float32).astype(np.float64)
+    X32, Y32 = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    net = binding.Mlp(DIMS, max_batch=batch, ncomp=2, beta=0.5)
+    net.set_params(p32)
+    net.set_affine(*aff)
+    back = net.get_affine()
+    for a, b in zip(aff, back):
+        assert np.array_equal(a.astype(np.float32), b)
+    y = torch.empty(batch, DIMS[-1], dtype=torch.float32, device="cuda")
+    net.forward(_dev(X), y, batch)
+    net.sync()
+    ref, _ = forward(p32, DIMS, X32, bf16=True, affine=aff)
+    err = np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= 1e-3, err
+    loss, g = net.loss_grad(_dev(X), _dev(Y), batch)
+    lo, go = loss_and_gradient(p32, DIMS, X32, Y32, beta=0.5, ncomp=2, bf16=True, affine=aff)
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    err = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert err <= 1e-2, err
+    # removing the maps restores the plain network
+    net.set_affine()
+    net.forward(_dev(X), y, batch)
+    net.sync()
+    ref, _ = forward(p32, DIMS, X32, bf16=True)
+    assert np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-3
+
+
+def test_fit_affine_column_statistics():
+    rows = 1000
+    rng = np.random.default_rng(9)
+    X = (rng.standard_normal((rows, DIMS[0])) * rng.uniform(1e-3, 10.0, DIMS[0]) + rng.standard_normal(DIMS[0]))
+    Y = rng.standard_normal((rows, DIMS[-1])) * rng.uniform(1e-4, 1.0, DIMS[-1])
+    X[:, 3] = 2.5  # a constant column keeps scale 1
+    X, Y = X.astype(np.float32), Y.astype(np.float32)
+    net = binding.Mlp(DIMS, max_batch=128)
+    net.fit_affine(_dev(X), _dev(Y), rows)
+    ish, isc, osh, osc = net.get_affine()
+    Xd, Yd = X.astype(np.float64), Y.astype(np.float64)
+    sdx = Xd.std(axis=0)
+    assert np.allclose(ish, Xd.mean(axis=0), rtol=1e-6, atol=1e-6)
+    expect = np.where(sdx > 0, 1.0 / np.where(sdx > 0, sdx, 1.0), 1.0)
+    assert np.allclose(isc, expect, rtol=1e-5)
+    assert isc[3] == 1.0
+    assert np.allclose(osh, Yd.mean(axis=0), rtol=1e-6, atol=1e-7)
+    assert np.allclose(osc, Yd.std(axis=0), rtol=1e-5)
