@@ -233,8 +233,8 @@ def hybrid_arm(wl, args, stream):
     from paper_2606_25569_b300.workloads import poiseuille_dense
     kmax = 16
     t0 = time.time()
-    X, Y = train.relaxation_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 8, 4, stream, kmax)
-    r = train.train_relaxation(X, Y, hidden=(512, 512, 512), epochs=120, batch=1024, lr=1e-3, lr_min=1e-5,
+    X, Y = train.relaxation_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 16, 4, stream, kmax)
+    r = train.train_relaxation(X, Y, hidden=(512, 512, 512), epochs=60, batch=1024, lr=1e-3, lr_min=1e-5,
                                stream=stream, serve_batch=wl.M)
     t_train = time.time() - t0
     kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,

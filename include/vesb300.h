@@ -165,12 +165,15 @@ vs_status vs_profile_read(vs_suspension* s, int32_t idx, char* name, int32_t nam
 /*
  * Learned maps for the hybrid step (params.mode = 1; VesNet, Sec. 3.2 and Algorithm 1).
  * which = 0: the relaxation flow map X_X (Eq. relaxation_disc replaced by a network): the step
- * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the standardised shape
- * with its Fourier modes |k| > filter_kmax removed (the Nyquist mode always is) and adds
- * out_scale * output, mapped back from the standard frame, to the redistributed X*; the result,
- * with its modes |k| > filter_kmax removed (the network does not represent them; the exact
- * relaxation leaves them at their tiny size), is X^{n+1}. The network (borrowed, must outlive its use) needs widths 2N in and out, batch
- * capacity >= M, the suspension's stream, and one N for all vesicles; otherwise
+ * redistributes X* (Sec. 4.2), standardises it (Sec. 3.4.1), evaluates net on the Fourier features of the
+ * standardised shape and adds out_scale * (the displacement synthesised from the output's features),
+ * mapped back from the standard frame, to the redistributed X*; the result, with its modes |k| > K
+ * removed (the network does not represent them; the exact relaxation leaves them at their tiny size),
+ * is X^{n+1}. Features, K = min(filter_kmax, N/2 - 1): with a_k = (1/N) sum_j v_j cos(2 pi k j/N) and
+ * b_k = -(1/N) sum_j v_j sin(2 pi k j/N) of v = x^o then y^o, a row is [a_0..a_K, b_1..b_K (x);
+ * a_0..a_K, b_1..b_K (y); zeros] of width W = 16 ceil((4K + 2)/16); outputs use the same layout
+ * (v_j = a_0 + 2 sum_k (a_k cos - b_k sin)). The network (borrowed, must outlive its use) needs widths W
+ * in and out, batch capacity >= M, the suspension's stream, and one N for all vesicles; otherwise
  * VS_ERR_INVALID_ARG. net = NULL removes it; a hybrid step without it fails with VS_ERR_NO_NETWORK.
  */
 vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double out_scale, int32_t filter_kmax);
@@ -181,8 +184,9 @@ vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double ou
 vs_status vs_relax(vs_suspension* s, const double* xy_in, double* xy_out);
 
 /* Training pairs of the relaxation map: for DEVICE points xy_in (CSR blocks, equal N), xin (device
- * FP32, M x 2N) = the network input of vs_set_network's map and yout (device FP32, M x 2N) =
- * (relax(xy_in) - xy_in) in each vesicle's standard frame, divided by out_scale. Asynchronous. */
+ * FP32, M x W) = the network input of vs_set_network's map and yout (device FP32, M x W) = the
+ * features of (relax(xy_in) - xy_in) in each vesicle's standard frame, divided by out_scale; W and the
+ * features as for vs_set_network with the same filter_kmax. Asynchronous. */
 vs_status vs_training_pairs(vs_suspension* s, const double* xy_in, float* xin, float* yout, double out_scale,
                             int32_t filter_kmax);
 
@@ -261,13 +265,14 @@ vs_status vs_mlp_get_params(vs_mlp* m, float* params, int64_t n);
  * the normalised output coordinates. set: host arrays of d_0, d_0, d_L, d_L floats; a NULL shift
  * is 0 and a NULL scale 1; all four NULL removes both maps; a zero or non-finite value is
  * VS_ERR_INVALID_ARG. get: host arrays (each may be NULL). fit: in_shift / out_shift = column means
- * and in_scale = 1/sd, out_scale = sd (1 for a constant column) of the DEVICE FP32 rows x (rows x
- * d_0) and y (rows x d_L), FP64 sums; synchronises.
+ * and in_scale = 1/sd, out_scale = sd of the DEVICE FP32 rows x (rows x d_0) and y (rows x d_L), FP64
+ * sums, with sd raised to rel_floor times the largest deviation of its matrix (rel_floor >= 0; columns
+ * whose spread is rounding noise then stay small) and 1 for a constant column; synchronises.
  */
 vs_status vs_mlp_set_affine(vs_mlp* m, const float* in_shift, const float* in_scale, const float* out_shift,
                             const float* out_scale);
 vs_status vs_mlp_get_affine(vs_mlp* m, float* in_shift, float* in_scale, float* out_shift, float* out_scale);
-vs_status vs_mlp_fit_affine(vs_mlp* m, const float* x, const float* y, int32_t rows);
+vs_status vs_mlp_fit_affine(vs_mlp* m, const float* x, const float* y, int32_t rows, double rel_floor);
 /* y (device, batch x d_L) = network(x), output map included */
 vs_status vs_mlp_forward(vs_mlp* m, const float* x, int32_t batch, float* y);
 /* loss (host) and, when grad (host, n floats) is non-null, its gradient; synchronises */

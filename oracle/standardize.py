@@ -13,10 +13,16 @@ standardize(X) -> (X^o, params):
    "the first point lies on or just above the x-axis".
 The networks see the Fourier-filtered standardised shape: modes |k| > kmax and the Nyquist mode
 zeroed (reading; the paper names no cut-off, the library takes kmax as a parameter). Displacements map back with destandardize_disp.
+The network input and output are the Fourier coefficients of the standardised shape and of the
+relaxation displacement (fourier_features / features_to_samples): a_k = (1/N) sum_j v_j cos(2 pi k j/N),
+b_k = -(1/N) sum_j v_j sin(2 pi k j/N), k = 0..K, laid out as [a_0..a_K, b_1..b_K] for x, then for y
+(reading: the paper feeds point coordinates to its convolutional networks; coefficients normalised per
+mode let a fully connected network resolve the small high modes that the bending force amplifies).
 
 Pins (tests/test_oracle_standardize.py): invariance of X^o to translation, rotation and scaling of
 the input; J of an ellipse in closed form; the centroid against the polygon centroid; exact
-round trip of points and displacements.
+round trip of points and displacements; the features of single cosine and sine modes in closed
+form and the synthesis of features against the FFT low-pass.
 """
 import numpy as np
 
@@ -98,3 +104,32 @@ def fourier_filter(v, kmax=None):
     k = np.abs(np.fft.fftfreq(N, d=1.0 / N))
     c[k > kmax] = 0.0
     return np.fft.ifft(c).real
+
+
+def feature_count(K):
+    return 4 * K + 2
+
+
+def fourier_features(vx, vy, K):
+    """[a_0..a_K, b_1..b_K] of vx, then of vy (module header), written out as the DFT sums."""
+    N = len(vx)
+    j = np.arange(N)
+    out = []
+    for v in (np.asarray(vx, float), np.asarray(vy, float)):
+        a = [np.sum(v * np.cos(2.0 * np.pi * k * j / N)) / N for k in range(K + 1)]
+        b = [-np.sum(v * np.sin(2.0 * np.pi * k * j / N)) / N for k in range(1, K + 1)]
+        out += a + b
+    return np.array(out)
+
+
+def features_to_samples(f, K, N):
+    """The samples v_j = a_0 + 2 sum_{k=1..K} (a_k cos(2 pi k j/N) - b_k sin(2 pi k j/N)) of x and y."""
+    j = np.arange(N)
+    res = []
+    for c in range(2):
+        g = f[c * (2 * K + 1):(c + 1) * (2 * K + 1)]
+        v = np.full(N, g[0])
+        for k in range(1, K + 1):
+            v = v + 2.0 * (g[k] * np.cos(2.0 * np.pi * k * j / N) - g[K + k] * np.sin(2.0 * np.pi * k * j / N))
+        res.append(v)
+    return res[0], res[1]

@@ -42,21 +42,26 @@ class Params:
 
 def relax_learned(x, y, net):
     """Hybrid relaxation (VesNet's X_X map, Sec. 3.2, 3.4.1): redistribute X* (Sec. 4.2),
-    standardise, evaluate the network on the Fourier-filtered standardised shape (bfloat16
-    operands as on the tensor cores, input first rounded to float32), scale its output, map it
-    back to the original frame, add it to X*_r and remove the modes |k| > kmax of the result (the
-    network represents only those modes). net = (dims, params, scale, kmax[, affine]), affine the
-    network's per-feature input and output maps (oracle.mlp)."""
+    standardise, evaluate the network on the Fourier features of the standardised shape (modes
+    k <= K = min(kmax, N/2 - 1), zero-padded to the width 16 ceil((4K + 2)/16); bfloat16 operands as on
+    the tensor cores, input first rounded to float32), synthesise the displacement from the scaled
+    output's features, map it back to the original frame, add it to X*_r and remove the modes |k| > K
+    of the result (the network represents only those modes). net = (dims, params, scale, kmax[, affine]),
+    affine the network's per-feature input and output maps (oracle.mlp)."""
     from .mlp import forward
-    from .standardize import destandardize_disp, fourier_filter, standardize
+    from .standardize import (destandardize_disp, feature_count, features_to_samples, fourier_features,
+                              fourier_filter, standardize)
     dims, params, scale, kmax = net[:4]
     affine = net[4] if len(net) > 4 else None
     N = len(x)
+    K = min(kmax, N // 2 - 1)
     xr, yr, _ = redistribute(x, y)
     xo, yo, fr = standardize(xr, yr)
-    inp = np.concatenate([fourier_filter(xo, kmax), fourier_filter(yo, kmax)])[None, :]
+    inp = np.zeros((1, dims[0]))
+    inp[0, :feature_count(K)] = fourier_features(xo, yo, K)
     out, _ = forward(params, dims, inp, bf16=True, affine=affine)
-    dx, dy = destandardize_disp(scale * out[0, :N], scale * out[0, N:], fr)
+    ddx, ddy = features_to_samples(scale * out[0, :feature_count(K)], K, N)
+    dx, dy = destandardize_disp(ddx, ddy, fr)
     return np.concatenate([fourier_filter(xr + dx, kmax), fourier_filter(yr + dy, kmax)])
 
 

@@ -59,7 +59,8 @@ FUNCTIONS = {
                                          ctypes.c_void_p]),
     "vs_mlp_get_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
-    "vs_mlp_fit_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "vs_mlp_fit_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_double]),
     "vs_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "vs_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
@@ -298,6 +299,13 @@ class VsAdamW(ctypes.Structure):
                 ("weight_decay", ctypes.c_float)]
 
 
+def feature_width(N, kmax):
+    """Width of the relaxation network's feature rows (vs_set_network): 16 ceil((4K + 2)/16),
+    K = min(kmax, N/2 - 1)."""
+    K = min(int(kmax), int(N) // 2 - 1)
+    return (4 * K + 2 + 15) // 16 * 16
+
+
 class Mlp:
     """vs_mlp: BF16 tensor-core MLP (ReLU hidden layers) with the paper's loss and AdamW."""
 
@@ -344,9 +352,9 @@ class Mlp:
         self._check(lib().vs_mlp_get_affine(self._h, *[_ptr(a) for a in out]))
         return tuple(out)
 
-    def fit_affine(self, x_dev, y_dev, rows):
+    def fit_affine(self, x_dev, y_dev, rows, rel_floor=0.0):
         """Maps from the column means and deviations of device rows x, y (vs_mlp_fit_affine)."""
-        self._check(lib().vs_mlp_fit_affine(self._h, _ptr(x_dev), _ptr(y_dev), int(rows)))
+        self._check(lib().vs_mlp_fit_affine(self._h, _ptr(x_dev), _ptr(y_dev), int(rows), float(rel_floor)))
 
     def forward(self, x_dev, y_dev, batch):
         self._check(lib().vs_mlp_forward(self._h, _ptr(x_dev), int(batch), _ptr(y_dev)))

@@ -270,7 +270,7 @@ struct vs_suspension {
   NearBufs nb{nullptr, nullptr};
   double* corr = nullptr;          // correction state (6 N + 16 doubles per vesicle)
   int *cactive = nullptr, *cpiv = nullptr;
-  float* xin = nullptr;            // network input rows (M x 2N)
+  float* xin = nullptr;            // network input rows (M x feature width)
   StdFrame* frames = nullptr;      // standardisation frames (M)
   struct vs_mlp* net = nullptr;    // learned relaxation map (hybrid mode), borrowed
   double net_scale = 1.0;
@@ -657,13 +657,16 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   const Layout& L = h->L;
   const VesIndex vi = h->D.vi();
   if (!h->net) { h->msg = "hybrid mode needs a relaxation network (vs_set_network)"; return VS_ERR_NO_NETWORK; }
+  const int W = feat_width(feat_kmax(h->net_kmax, L.nmax));
   VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, xs, h->u, h->D.tab, xo, h->u_r));
-  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, 2 * L.nmax, h->frames, h->net_kmax));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xo, h->D.tab, h->xin, W, h->frames,
+                                                                           h->net_kmax, true));
   VS_CK(h, cudaGetLastError(), "standardise");
   vs_status st = mlp_forward(h->net, h->xin, L.M, true);
   if (st != VS_OK) { h->msg = "network forward failed"; return st; }
-  VS_LAUNCH(h, "k_destandardize_add", k_destandardize_add<<<L.M, NMAX, 0, h->stream>>>(vi, mlp_output(h->net), 2 * L.nmax,
-                                                                                       h->net_scale, h->frames, xo));
+  VS_LAUNCH(h, "k_destandardize_add", k_destandardize_add<<<L.M, NMAX, 0, h->stream>>>(vi, mlp_output(h->net), W,
+                                                                                       h->net_scale, h->net_kmax,
+                                                                                       h->D.tab, h->frames, xo));
   VS_LAUNCH(h, "k_lowpass", k_lowpass<<<L.M, NMAX, 0, h->stream>>>(vi, h->D.tab, h->net_kmax, xo));
   VS_CK(h, cudaGetLastError(), "destandardise");
   return VS_OK;
@@ -896,7 +899,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
-  VS_A(dalloc(&h->xin, 2 * (int64_t)L.nmax * L.M));
+  VS_A(dalloc(&h->xin, (int64_t)std::max(2 * L.nmax, feat_width(feat_kmax(L.nmax, L.nmax))) * L.M));
   VS_A(dalloc(&h->frames, L.M));
   if (h->p.near_field) {
     VS_A(dalloc(&h->nb.layer, 30 * L.P));
@@ -1056,12 +1059,14 @@ vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double ou
   const Layout& L = h->L;
   for (int v = 0; v < L.M; ++v)
     if (L.N[v] != L.nmax) { h->msg = "the learned relaxation needs one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
-  if (net->dims.front() != 2 * L.nmax || net->dims.back() != 2 * L.nmax || net->Bcap < L.M) {
-    h->msg = "network widths must be 2N in and out and its batch capacity at least M";
+  if (!(out_scale > 0) || filter_kmax < 0) return VS_ERR_INVALID_ARG;
+  const int W = feat_width(feat_kmax(filter_kmax, L.nmax));
+  if (net->dims.front() != W || net->dims.back() != W || net->Bcap < L.M) {
+    h->msg = "network widths must be the feature width 16 ceil((4K + 2)/16), K = min(filter_kmax, N/2 - 1), in "
+             "and out, and its batch capacity at least M";
     return VS_ERR_INVALID_ARG;
   }
   if (net->stream != h->stream) { h->msg = "network and suspension must share one stream"; return VS_ERR_INVALID_ARG; }
-  if (!(out_scale > 0) || filter_kmax < 0) return VS_ERR_INVALID_ARG;
   drop_graphs(h);
   h->net = net;
   h->net_scale = out_scale;
@@ -1084,9 +1089,11 @@ vs_status vs_training_pairs(vs_suspension* h, const double* xy_in, float* xin, f
   const VesIndex vi = h->D.vi();
   vs_status st = relax_exact(h, xy_in, h->xy_next, 1 - h->cur);
   if (st != VS_OK) return st;
-  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->D.tab, xin, 2 * L.nmax, h->frames, kmax));
+  const int W = feat_width(feat_kmax(kmax, L.nmax));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->D.tab, xin, W, h->frames, kmax,
+                                                                           true));
   VS_LAUNCH(h, "k_to_frame_rows", k_to_frame_rows<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->xy_next, h->frames,
-                                                                             1.0 / out_scale, yout, 2 * L.nmax));
+                                                                             1.0 / out_scale, h->D.tab, kmax, yout, W));
   VS_CK(h, cudaGetLastError(), "training pairs");
   return VS_OK;
 }
@@ -1193,7 +1200,7 @@ vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, in
   cudaError_t e = upload_layout(L, D, s);
   if (e == cudaSuccess) e = dalloc(&fr, L.M);
   if (e == cudaSuccess) {
-    k_standardize<<<M, NMAX, 0, s>>>(D.vi(), xy, D.tab, xin, 2 * L.nmax, fr, kmax);
+    k_standardize<<<M, NMAX, 0, s>>>(D.vi(), xy, D.tab, xin, 2 * L.nmax, fr, kmax, false);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1519,8 +1526,8 @@ vs_status vs_mlp_get_affine(vs_mlp* h, float* in_shift, float* in_scale, float* 
   return VS_OK;
 }
 
-vs_status vs_mlp_fit_affine(vs_mlp* h, const float* x, const float* y, int32_t rows) {
-  if (!h || !x || !y || rows < 1) return VS_ERR_INVALID_ARG;
+vs_status vs_mlp_fit_affine(vs_mlp* h, const float* x, const float* y, int32_t rows, double rel_floor) {
+  if (!h || !x || !y || rows < 1 || !(rel_floor >= 0.0)) return VS_ERR_INVALID_ARG;
   const int d0 = h->dims[0], dL = h->dims[h->L];
   std::vector<double> st(2 * (size_t)std::max(d0, dL));
   std::vector<float> sh_in(d0), sc_in(d0), sh_out(dL), sc_out(dL);
@@ -1533,8 +1540,11 @@ vs_status vs_mlp_fit_affine(vs_mlp* h, const float* x, const float* y, int32_t r
     VS_CK(h, cudaMemcpyAsync(st.data(), h->stats, 2 * dmx * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
           "fit affine");
     VS_CK(h, cudaStreamSynchronize(h->stream), "fit affine");
+    double sdmax = 0.0;
+    for (int j = 0; j < d; ++j)
+      if (std::isfinite(st[dmx + j])) sdmax = std::max(sdmax, st[dmx + j]);
     for (int j = 0; j < d; ++j) {
-      const double m = st[j], sd = st[dmx + j];
+      const double m = st[j], sd = std::max(st[dmx + j], rel_floor * sdmax);
       const bool flat = !(sd > 0.0) || !std::isfinite(sd);
       if (pass) {
         sh_out[j] = (float)m;

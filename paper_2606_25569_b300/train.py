@@ -26,16 +26,17 @@ def he_uniform(dims, rng):
 
 
 def relaxation_samples(wl, snapshots, every, stream, kmax, near_field=None, skip=0):
-    """(X, Y): FP32 device tensors (snapshots * M, 2N) of network inputs (filter cut-off kmax) and
-    raw targets, taken every `every` steps after `skip` initial steps."""
+    """(X, Y): FP32 device tensors (snapshots * M, W) of network inputs and raw targets (Fourier
+    features up to mode kmax, W = binding.feature_width), taken every `every` steps after `skip`
+    initial steps."""
     import torch
     nf = wl.near_field if near_field is None else near_field
     s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
                            flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=nf, stream=stream)
-    M, N2 = wl.M, 2 * len(wl.xs[0])
+    M, W = wl.M, binding.feature_width(len(wl.xs[0]), kmax)
     if skip:
         s.step(skip)
-    X = torch.empty(snapshots * M, N2, dtype=torch.float32, device="cuda")
+    X = torch.empty(snapshots * M, W, dtype=torch.float32, device="cuda")
     Y = torch.empty_like(X)
     for k in range(snapshots):
         xy = torch.as_tensor(s.positions(), device="cuda")
@@ -60,13 +61,14 @@ def relative_errors(net, X, Y, batch):
 
 
 def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e-3, lr_min=1e-5, beta=0.1,
-                     holdout=0.1, seed=0, stream=None, ncomp=2, serve_batch=0, normalise=True):
+                     holdout=0.1, seed=0, stream=None, ncomp=2, serve_batch=0, normalise=True, rel_floor=1e-3):
     """Train on (X, Y); the last `holdout` fraction is held out. AdamW starts at lr (Sec. 3.4.2:
     1e-3) and decays on a cosine to lr_min over the epochs. The network can afterwards run batches of
     up to max(batch, serve_batch) rows (a suspension needs at least its vesicle count).
 
     normalise: every input and output feature is mapped to zero mean and unit deviation over the
-    training rows (vs_mlp_fit_affine; the maps are part of the network, so the output scale is 1).
+    training rows (vs_mlp_fit_affine; the maps are part of the network, so the output scale is 1),
+    deviations below rel_floor times the largest one raised to it.
     This matters here: the standardised shapes differ from each other by ~1e-2 of their size, below
     what a bfloat16 input resolves next to the shape itself. Otherwise the targets are divided by
     their RMS (the returned scale). Returns a dict with the network, its output scale, the loss
@@ -81,7 +83,7 @@ def train_relaxation(X, Y, hidden=(512, 512, 512), epochs=100, batch=4096, lr=1e
     if normalise:
         scale = 1.0
         Yn = Y
-        net.fit_affine(X[:ntr].contiguous(), Y[:ntr].contiguous(), ntr)
+        net.fit_affine(X[:ntr].contiguous(), Y[:ntr].contiguous(), ntr, rel_floor)
     else:
         scale = float(torch.sqrt(torch.mean(Y[:ntr].double() ** 2)).item())
         Yn = (Y / scale).contiguous()

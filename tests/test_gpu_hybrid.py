@@ -41,6 +41,30 @@ def test_standardize_matches_oracle():
         assert np.max(np.abs(frames[v, :5] - [p.c[0], p.c[1], p.cos_t, p.sin_t, p.s])) <= 1e-12 * max(1.0, abs(p.s))
 
 
+def test_training_pairs_are_oracle_features():
+    from oracle.standardize import feature_count, fourier_features, to_frame_disp
+    N, M, kmax = 64, 5, 12
+    xs, ys = _shapes(M, N, 7)
+    W = binding.feature_width(N, kmax)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.0, dt=2e-3)
+    X = torch.zeros(M, W, dtype=torch.float32, device="cuda")
+    Y = torch.zeros(M, W, dtype=torch.float32, device="cuda")
+    g.training_pairs(torch.as_tensor(csr(xs, ys), device="cuda"), X, Y, 0.5, kmax)
+    g.sync()
+    gX, gY = X.cpu().numpy(), Y.cpu().numpy()
+    p = Params(kappa=1.0, mu=1.0, dt=2e-3)
+    F = feature_count(kmax)
+    for v in range(M):
+        xo, yo, fr = standardize(xs[v], ys[v])
+        fx = fourier_features(xo, yo, kmax)
+        assert np.max(np.abs(gX[v, :F] - fx)) <= 1e-6 * np.max(np.abs(fx))
+        z = relax_exact(xs[v], ys[v], p)
+        dx, dy = to_frame_disp(z[:N] - xs[v], z[N:] - ys[v], fr)
+        fy = fourier_features(dx, dy, kmax) / 0.5
+        assert np.max(np.abs(gY[v, :F] - fy)) <= 1e-5 * np.max(np.abs(fy))
+        assert np.all(gX[v, F:] == 0) and np.all(gY[v, F:] == 0)
+
+
 def test_relax_map_matches_oracle():
     xs, ys = _shapes(5, 64, 2)
     g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.0, dt=2e-3)
@@ -62,10 +86,13 @@ def test_relax_map_matches_oracle():
 def test_hybrid_step_matches_oracle(with_affine):
     N, M = 64, 4
     xs, ys = _shapes(M, N, 3)
-    dims = [2 * N, 256, 256, 2 * N]
+    W = binding.feature_width(N, 31)
+    dims = [W, 256, 256, W]
     rng = np.random.default_rng(4)
     params = init_params(dims, rng).astype(np.float32).astype(np.float64)
-    scale = 1e-3
+    # the random network's outputs are O(1); scale 2e-4 keeps the synthesised displacement (a sum over
+    # 4K + 2 = 126 features, times 1/s = L) near the size of a real relaxation step
+    scale = 2e-4
     kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(1.0, 0.0, 0.0, 0.0))
     stream = torch.cuda.current_stream()
     net = binding.Mlp(dims, max_batch=M, stream=stream)
@@ -73,8 +100,8 @@ def test_hybrid_step_matches_oracle(with_affine):
     relax_net = (dims, params, scale, 31)
     if with_affine:
         f32 = lambda a: a.astype(np.float32).astype(np.float64)
-        aff = (f32(0.05 * rng.standard_normal(2 * N)), f32(rng.uniform(1.0, 20.0, 2 * N)),
-               f32(0.1 * rng.standard_normal(2 * N)), f32(rng.uniform(0.2, 1.0, 2 * N)))
+        aff = (f32(0.02 * rng.standard_normal(W)), f32(rng.uniform(1.0, 20.0, W)),
+               f32(0.1 * rng.standard_normal(W)), f32(rng.uniform(0.2, 1.0, W)))
         net.set_affine(*aff)
         relax_net = relax_net + (aff,)
     o = OracleSuspension(xs, ys, Params(relax_net=relax_net, **kw))
@@ -98,7 +125,7 @@ def test_trained_network_beats_the_step_without_it():
     kmax = 16
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(21)
-    X = torch.empty(sets * M, 2 * N, dtype=torch.float32, device="cuda")
+    X = torch.empty(sets * M, binding.feature_width(N, kmax), dtype=torch.float32, device="cuda")
     Y = torch.empty_like(X)
     g = None
     for k in range(sets):

@@ -131,3 +131,16 @@ def test_fit_affine_column_statistics():
     assert isc[3] == 1.0
     assert np.allclose(osh, Yd.mean(axis=0), rtol=1e-6, atol=1e-7)
     assert np.allclose(osc, Yd.std(axis=0), rtol=1e-5)
+
+
+def test_fit_affine_relative_floor():
+    rows = 500
+    rng = np.random.default_rng(10)
+    X = (rng.standard_normal((rows, DIMS[0])) * np.logspace(-6, 0, DIMS[0])).astype(np.float32)
+    Y = (rng.standard_normal((rows, DIMS[-1])) * np.logspace(-8, 0, DIMS[-1])).astype(np.float32)
+    net = binding.Mlp(DIMS, max_batch=128)
+    net.fit_affine(_dev(X), _dev(Y), rows, rel_floor=1e-2)
+    _, isc, _, osc = net.get_affine()
+    sdx, sdy = X.astype(np.float64).std(axis=0), Y.astype(np.float64).std(axis=0)
+    assert np.allclose(isc, 1.0 / np.maximum(sdx, 1e-2 * sdx.max()), rtol=1e-5)
+    assert np.allclose(osc, np.maximum(sdy, 1e-2 * sdy.max()), rtol=1e-5)

@@ -65,3 +65,26 @@ def test_filter_keeps_low_modes_only():
     t = 2 * np.pi * np.arange(N) / N
     v = np.cos(3 * t) + 0.5 * np.sin(16 * t) + 0.2 * np.cos(17 * t) + 0.1 * np.cos(32 * t)
     assert np.max(np.abs(fourier_filter(v) - (np.cos(3 * t) + 0.5 * np.sin(16 * t)))) < 1e-13
+
+
+def test_fourier_features_of_single_modes_closed_form():
+    from oracle.standardize import fourier_features
+    N, K = 32, 7
+    j = np.arange(N)
+    # x = 3 + 2 cos(2 pi 3 j/N) - 5 sin(2 pi 5 j/N) has a_0 = 3, a_3 = 1, b_5 = 5/2 (v = a_0 + 2(a cos - b sin))
+    vx = 3.0 + 2.0 * np.cos(2 * np.pi * 3 * j / N) - 5.0 * np.sin(2 * np.pi * 5 * j / N)
+    vy = np.sin(2 * np.pi * 1 * j / N)
+    f = fourier_features(vx, vy, K)
+    expect = np.zeros(4 * K + 2)
+    expect[0], expect[3], expect[K + 5] = 3.0, 1.0, 2.5
+    expect[(2 * K + 1) + K + 1] = -0.5
+    assert np.max(np.abs(f - expect)) < 1e-13
+
+
+def test_feature_synthesis_equals_fft_lowpass():
+    from oracle.standardize import features_to_samples, fourier_features
+    x, y = _shape(64, 3)
+    for K in (5, 16, 31):
+        sx, sy = features_to_samples(fourier_features(x, y, K), K, 64)
+        assert np.max(np.abs(sx - fourier_filter(x, K))) < 1e-13
+        assert np.max(np.abs(sy - fourier_filter(y, K))) < 1e-13
