@@ -597,12 +597,133 @@ __device__ void gj_invert(const float* src, float* dst, int n, unsigned* err) {
   __syncthreads();
 }
 
+// The same exchange steps without pivoting: step k takes row k, so the row and the column of a step are
+// known in advance and their owners publish both before a single barrier (one barrier a step instead of
+// two, and no pivot search). A pivot with |t| <= GJ_NP_TOL max|A| ends the attempt: it returns false and
+// writes nothing (uniformly across the CTA), and the caller runs the pivoting elimination. Otherwise the
+// result is the inverse in place (inv[i][j] = T[i][j], no permutation).
+constexpr float GJ_NP_TOL = 1e-4f;
+template <int RA, int RB, int TC>
+__device__ bool gj_invert_np(const float* src, float* dst, int n) {
+  static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB, "square grid of pairs");
+  constexpr int NP = 16 * RA, H = RB / 2, NW = 16 * TC / 32;
+  __shared__ __align__(16) float colb[2][NP], rowb[2][NP];
+  __shared__ float wmax[NW];
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  float2 T[RA][H];
+  float mx = 0.f;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
+      T[a][h].x = (i < n && j0 < n) ? src[(int64_t)i * n + j0] : 0.f;
+      T[a][h].y = (i < n && j1 < n) ? src[(int64_t)i * n + j1] : 0.f;
+      mx = fmaxf(mx, fmaxf(fabsf(T[a][h].x), fabsf(T[a][h].y)));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = mx;
+  __syncthreads();
+  mx = wmax[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) mx = fmaxf(mx, wmax[w]);
+  const float thr = GJ_NP_TOL * mx;
+  bool ok = mx > 0.f;
+#pragma unroll
+  for (int kb = 0; kb < RB; ++kb) {
+#pragma unroll 1
+    for (int kc = 0; kc < TC; ++kc) {
+      const int k = TC * kb + kc;
+      if (k >= n) break;
+      const int buf = k & 1;
+      const int pr = k & 15, pa = k >> 4;
+      if (tc == kc) {  // column k
+        float cv[RA];
+#pragma unroll
+        for (int a = 0; a < RA; ++a) cv[a] = (kb & 1) ? T[a][kb >> 1].y : T[a][kb >> 1].x;
+        if constexpr (RA >= 4) {
+#pragma unroll
+          for (int a = 0; a < RA; a += 4)
+            *reinterpret_cast<float4*>(&colb[buf][tr * RA + a]) = make_float4(cv[a], cv[a + 1], cv[a + 2], cv[a + 3]);
+        } else {
+          *reinterpret_cast<float2*>(&colb[buf][tr * RA]) = make_float2(cv[0], cv[1]);
+        }
+      }
+      if (tr == pr) {  // row k
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+          if (a == pa) {
+            if constexpr (H == 1) {
+              *reinterpret_cast<float2*>(&rowb[buf][tc * RB]) = T[a][0];
+            } else {
+#pragma unroll
+              for (int h = 0; h < H; h += 2)
+                *reinterpret_cast<float4*>(&rowb[buf][tc * RB + 2 * h]) =
+                    make_float4(T[a][h].x, T[a][h].y, T[a][h + 1].x, T[a][h + 1].y);
+            }
+          }
+      }
+      __syncthreads();
+      float pv = colb[buf][pr * RA + pa];
+      if (!(fabsf(pv) > thr)) { ok = false; pv = 1.f; }
+      const float ip = 1.f / pv;
+      float c[RA];
+      float2 u[H];
+      if constexpr (RA >= 4) {
+#pragma unroll
+        for (int a = 0; a < RA; a += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(&colb[buf][tr * RA + a]);
+          c[a] = w.x; c[a + 1] = w.y; c[a + 2] = w.z; c[a + 3] = w.w;
+        }
+      } else {
+        const float2 w = *reinterpret_cast<const float2*>(&colb[buf][tr * RA]);
+        c[0] = w.x; c[1] = w.y;
+      }
+#pragma unroll
+      for (int h = 0; h < H; ++h) u[h] = __fmul2_rn(*reinterpret_cast<const float2*>(&rowb[buf][tc * RB + 2 * h]), make_float2(ip, ip));
+      if (tc == kc) {
+        if (kb & 1) u[kb >> 1].y = 1.f - ip; else u[kb >> 1].x = 1.f - ip;
+      }
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int h = 0; h < H; ++h) T[a][h] = __ffma2_rn(make_float2(-c[a], -c[a]), u[h], T[a][h]);
+      if (tr == pr) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+          if (a == pa) {
+#pragma unroll
+            for (int h = 0; h < H; ++h) T[a][h] = make_float2(-u[h].x, -u[h].y);
+            if (tc == kc) {
+              if (kb & 1) T[a][kb >> 1].y = ip; else T[a][kb >> 1].x = ip;
+            }
+          }
+      }
+    }
+  }
+  // every thread took the same decisions from the same shared values; the barrier also ends the reads
+  // of src before dst (possibly the same memory) is written
+  __syncthreads();
+  if (!ok) return false;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
+      if (i < n && j0 < n) dst[(int64_t)i * n + j0] = T[a][h].x;
+      if (i < n && j1 < n) dst[(int64_t)i * n + j1] = T[a][h].y;
+    }
+  __syncthreads();
+  return true;
+}
+
 template <int RA, int RB, int TC>
 __global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
   const int v = blockIdx.x;
   if (active && !active[v]) return;
   float* A = geo.A(v);
-  gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
+  if (!gj_invert_np<RA, RB, TC>(A, A, geo.n(v))) gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
 }
 
 // Solve LU x = b in place for one vector b in shared memory (length n); warp 0 works, the
