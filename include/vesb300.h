@@ -225,6 +225,16 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
                            double* S_out, void* cuda_stream);
 
 /*
+ * Batched FP32 inverse (the preconditioners of the mixed-precision solves are built with it): a_inv[v] =
+ * a[v]^{-1} for batch row-major n x n DEVICE matrices (n <= 128; a and a_inv may be the same memory) by
+ * register Gauss-Jordan exchange steps, first without pivoting and, for a matrix where a pivot falls to
+ * 1e-4 of its largest entry or below, again with partial pivoting; *fallbacks (host, may be NULL) gets
+ * the number of such matrices. A zero pivot column under pivoting is VS_ERR_UNSTABLE. Synchronous.
+ */
+vs_status vs_batched_inverse32(const float* a, float* a_inv, int32_t n, int32_t batch, int32_t* fallbacks,
+                               void* cuda_stream);
+
+/*
  * Standardisation of every vesicle for the networks (Sec. 3.4.1): centroid, principal axis along
  * +y, unit length, cyclic relabelling so that point 0 is the right-most upward crossing of the x
  * axis, Fourier filter keeping modes |k| <= kmax (< N/2). xy: device CSR blocks. xin: device FP32, row v =

@@ -51,6 +51,8 @@ FUNCTIONS = {
     "vs_farfield_plan_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_batched_inverse32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                      ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -297,6 +299,15 @@ def farfield_eval_static(offsets, mu, precision, xy_dev, f_dev, u_dev, stream=No
 class VsAdamW(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("weight_decay", ctypes.c_float)]
+
+
+def batched_inverse32(a_dev, out_dev, n, batch, stream=None):
+    """vs_batched_inverse32 on device FP32 tensors; returns the number of pivoting fallbacks."""
+    fb = ctypes.c_int32()
+    st = lib().vs_batched_inverse32(_ptr(a_dev), _ptr(out_dev), int(n), int(batch), ctypes.byref(fb), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_batched_inverse32 failed")
+    return fb.value
 
 
 def feature_width(N, kmax):

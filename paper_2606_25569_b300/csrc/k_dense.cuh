@@ -718,12 +718,26 @@ __device__ bool gj_invert_np(const float* src, float* dst, int n) {
   return true;
 }
 
-template <int RA, int RB, int TC>
-__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(LuGeo32 geo, unsigned* err, const int* __restrict__ active) {
+// A dense batch of n x n row-major FP32 matrices, matrix v at base + v n^2.
+struct DenseGeo32 {
+  float* base;
+  int nn;
+  __device__ int n(int) const { return nn; }
+  __device__ float* A(int v) const { return base + (int64_t)v * nn * nn; }
+};
+
+// In-place inverse of matrix blockIdx.x of geo; fallbacks (may be null) counts the matrices that needed
+// the pivoting elimination.
+template <int RA, int RB, int TC, class Geo>
+__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(Geo geo, unsigned* err, const int* __restrict__ active,
+                                                           int* fallbacks) {
   const int v = blockIdx.x;
   if (active && !active[v]) return;
   float* A = geo.A(v);
-  if (!gj_invert_np<RA, RB, TC>(A, A, geo.n(v))) gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
+  if (!gj_invert_np<RA, RB, TC>(A, A, geo.n(v))) {
+    if (fallbacks && threadIdx.x == 0) atomicAdd(fallbacks, 1);
+    gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
+  }
 }
 
 // Solve LU x = b in place for one vector b in shared memory (length n); warp 0 works, the

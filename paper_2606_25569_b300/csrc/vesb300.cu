@@ -366,17 +366,25 @@ void launch_lu(vs_suspension* h, const char* name, const Geo& geo, int nmax_dim,
 
 // In-place FP32 inverses by Gauss-Jordan in registers (k_gj_inverse) for matrices up to 128 x 128;
 // false when nmax_dim is larger (nothing launched).
-bool launch_gj32(vs_suspension* h, const char* name, const LuGeo32& geo, int nmax_dim, const int* active) {
-  const int M = h->L.M;
+// The FP32 Gauss-Jordan inverse shape for matrices of order <= nmax_dim, on M matrices of geo.
+template <class Geo>
+cudaError_t gj32_launch(const Geo& geo, int nmax_dim, int M, cudaStream_t st, unsigned* err, const int* active,
+                        int* fallbacks) {
   if (nmax_dim <= 32) {
-    VS_LAUNCH(h, name, (k_gj_inverse<2, 2, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
+    k_gj_inverse<2, 2, 16><<<M, 256, 0, st>>>(geo, err, active, fallbacks);
   } else if (nmax_dim <= 64) {
-    VS_LAUNCH(h, name, (k_gj_inverse<4, 8, 8><<<M, 128, 0, h->stream>>>(geo, h->err, active)));
+    k_gj_inverse<4, 8, 8><<<M, 128, 0, st>>>(geo, err, active, fallbacks);
   } else if (nmax_dim <= 128) {
-    VS_LAUNCH(h, name, (k_gj_inverse<8, 8, 16><<<M, 256, 0, h->stream>>>(geo, h->err, active)));
+    k_gj_inverse<8, 8, 16><<<M, 256, 0, st>>>(geo, err, active, fallbacks);
   } else {
-    return false;
+    return cudaErrorInvalidValue;
   }
+  return cudaSuccess;  // launch errors stay pending for the caller's check
+}
+
+bool launch_gj32(vs_suspension* h, const char* name, const LuGeo32& geo, int nmax_dim, const int* active) {
+  if (nmax_dim > 128) return false;
+  VS_LAUNCH(h, name, gj32_launch(geo, nmax_dim, h->L.M, h->stream, h->err, active, nullptr));
   return true;
 }
 
@@ -1187,6 +1195,32 @@ void vs_farfield_plan_destroy(vs_farfield_plan* h) {
 }
 
 // ---------------------------------------------------------------------------------------------
+
+vs_status vs_batched_inverse32(const float* a, float* a_inv, int32_t n, int32_t batch, int32_t* fallbacks,
+                               void* cuda_stream) {
+  if (!a || !a_inv || n < 1 || n > 128 || batch < 1) return VS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned* err = nullptr;
+  int* fb = nullptr;
+  cudaError_t e = dalloc(&err, 1);
+  if (e == cudaSuccess) e = dalloc(&fb, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fb, 0, sizeof(int), s);
+  const size_t bytes = (size_t)batch * n * n * sizeof(float);
+  if (e == cudaSuccess && a != a_inv) e = cudaMemcpyAsync(a_inv, a, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = gj32_launch(DenseGeo32{a_inv, n}, n, batch, s, err, nullptr, fb);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  unsigned he = 0;
+  int hf = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&he, err, sizeof he, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, fb, sizeof hf, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  cudaFree(fb);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA;
+  if (fallbacks) *fallbacks = hf;
+  return (he & ERR_PIVOT) ? VS_ERR_UNSTABLE : VS_OK;
+}
 
 vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, int32_t kmax, float* xin,
                          double* frames, void* cuda_stream) {
