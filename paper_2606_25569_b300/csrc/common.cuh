@@ -25,6 +25,9 @@ struct VesIndex {
   const int64_t* off;   // first point of v in the point arrays
   const int64_t* moff;  // first element of v's matrix scratch (MatLayout::TOTAL N^2 elements)
   const int64_t* toff;  // first double of the tables for v's N
+  const int32_t* order; // CTA b of a per-vesicle launch works on vesicle order[b] (point counts descending,
+                        // so the largest vesicles start first); null: vesicle b
+  __device__ int vid(int b) const { return order ? order[b] : b; }
 };
 
 // Matrix scratch layout of one vesicle, in units of N^2 doubles from moff.

@@ -280,7 +280,7 @@ struct OpBlk32 {
 };
 // dst = src for N x N views; grid (ceil(N^2 / 256), M)
 __global__ void __launch_bounds__(256) k_blk_copy(OpCtx c, BlkView src, BlkView dst) {
-  const int v = blockIdx.y;
+  const int v = c.vi.vid(blockIdx.y);
   const int N = c.vi.N[v];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
   using T = typename Op::T;
   __shared__ T As[GK][GT + 1];
   __shared__ T Bs[GK][GT + 1];
-  const int v = blockIdx.z;
+  const int v = op.c.vi.vid(blockIdx.z);
   if (active && !active[v]) return;
   const int N = op.c.vi.N[v];
   int m, n, K;
@@ -358,6 +358,7 @@ struct LuGeoT {
   int dm, extra;
   int* piv;
   int pivsub;      // >= 0: pivots at 4 off + pivsub N;  < 0: at 2 off + 2 v (correction systems)
+  __device__ int vid(int b) const { return vi.vid(b); }
   __device__ int n(int v) const { return dm * vi.N[v] + extra; }
   __device__ E* A(int v) const { return scratch + vi.moff[v] + sub * (int64_t)vi.N[v] * vi.N[v]; }
   __device__ int* p(int v) const {
@@ -433,7 +434,7 @@ __device__ void lu_factor(typename Geo::T* A, int n, int* p, unsigned* err) {
 
 template <class Geo>
 __global__ void __launch_bounds__(256) k_lu(Geo geo, unsigned* err, const int* __restrict__ active) {
-  const int v = blockIdx.x;
+  const int v = geo.vid(blockIdx.x);
   if (active && !active[v]) return;
   lu_factor<Geo>(geo.A(v), geo.n(v), geo.p(v), err);
 }
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const i
   using E = typename Geo::T;
   extern __shared__ unsigned char lu_raw[];
   E* As = reinterpret_cast<E*>(lu_raw);
-  const int v = blockIdx.x;
+  const int v = geo.vid(blockIdx.x);
   if (active && !active[v]) return;
   const int n = geo.n(v);
   E* A = geo.A(v);
@@ -722,6 +723,7 @@ __device__ bool gj_invert_np(const float* src, float* dst, int n) {
 struct DenseGeo32 {
   float* base;
   int nn;
+  __device__ int vid(int b) const { return b; }
   __device__ int n(int) const { return nn; }
   __device__ float* A(int v) const { return base + (int64_t)v * nn * nn; }
 };
@@ -731,7 +733,7 @@ struct DenseGeo32 {
 template <int RA, int RB, int TC, class Geo>
 __global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(Geo geo, unsigned* err, const int* __restrict__ active,
                                                            int* fallbacks) {
-  const int v = blockIdx.x;
+  const int v = geo.vid(blockIdx.x);
   if (active && !active[v]) return;
   float* A = geo.A(v);
   if (!gj_invert_np<RA, RB, TC>(A, A, geo.n(v))) {
@@ -774,7 +776,7 @@ __device__ void lu_solve_vec(const F* LU, const int* p, int n, double* b) {
 template <class E>
 __global__ void __launch_bounds__(256) k_lu_solve_cols(VesIndex vi, E* scratch, int s,
                                                        const int* piv, const int* __restrict__ active) {
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   if (active && !active[v]) return;
   const int N = vi.N[v];
   const int nc = 2 * N;

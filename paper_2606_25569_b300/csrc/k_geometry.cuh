@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
   // positions relative to point 0 (the derivatives do not see the constant)
   __shared__ double xs[NMAX], ys[NMAX], red[NMAX / 32];
   __shared__ float2 dd[NMAX], w1[NMAX], w2[NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;

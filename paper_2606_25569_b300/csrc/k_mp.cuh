@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(THREADS) k_advect_mp(VesIndex vi, const double
   __shared__ MpShared sh;
   __shared__ float2 g[NMAX], e[NMAX];
   __shared__ double sg[NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(THREADS) k_tension_mp(VesIndex vi, const doubl
   __shared__ MpShared sh;
   __shared__ float2 g[NMAX], e[NMAX];
   __shared__ double sg[NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
   __shared__ double b[2 * NMAX], x[2 * NMAX], sg[NMAX], r1[2 * NMAX], cen[2];
   __shared__ float2 y2[NMAX];
   __shared__ __align__(16) float fy[NMAX], fr[2 * NMAX], fdx[2 * NMAX], fw[NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int64_t NN = (int64_t)N * N;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
                                                      const float* __restrict__ scratch32, int s, double mu,
                                                      NearBufs nb) {
   extern __shared__ double sm[];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   if (!has_near[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_near_rbf(VesIndex vi, const int* __rest
   __shared__ float colk[5 * NMAX];
   __shared__ float y1[5 * NMAX], y2[5 * NMAX];
   __shared__ int bad;
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   if (!has_near[v]) return;
   const int N = vi.N[v];
   const int n = 5 * N;

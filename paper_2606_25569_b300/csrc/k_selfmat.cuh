@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_self_matrix(VesIndex vi, const double* 
                                                      const double* __restrict__ tab, double mu,
                                                      double* __restrict__ scratch, int slot,
                                                      const int* __restrict__ active) {
-  const int v = blockIdx.y;
+  const int v = vi.vid(blockIdx.y);
   if (active && !active[v]) return;
   const int N = vi.N[v];
   const int nt = (N + SM_TILE - 1) / SM_TILE;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_self_matrix_df(VesIndex vi, const float
                                                         const float4* __restrict__ logtab,
                                                         float* __restrict__ scratch32, int slot,
                                                         const int* __restrict__ active) {
-  const int v = blockIdx.y;
+  const int v = vi.vid(blockIdx.y);
   if (active && !active[v]) return;
   const int N = vi.N[v];
   const int nt = (N + SM_TILE - 1) / SM_TILE;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NMAX) k_standardize(VesIndex vi, const double*
   __shared__ double d[NMAX], xs[NMAX], ys[NMAX], xr[NMAX], yr[NMAX], red[NMAX / 32];
   __shared__ double cre[2][NMAX / 2], cim[2][NMAX / 2];
   __shared__ int sj0;
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NMAX) k_destandardize_add(VesIndex vi, const f
                                                             const double* __restrict__ tab,
                                                             const StdFrame* __restrict__ frame,
                                                             double* __restrict__ xy) {
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int k = threadIdx.x;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(NMAX) k_to_frame_rows(VesIndex vi, const doubl
                                                         float* __restrict__ rows, int64_t ld) {
   __shared__ double d[2][NMAX];
   __shared__ double cre[2][NMAX / 2], cim[2][NMAX / 2];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int k = threadIdx.x;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(NMAX) k_lowpass(VesIndex vi, const double* __r
                                                   double* __restrict__ xy) {
   __shared__ double xs[NMAX], ys[NMAX];
   __shared__ double cre[2][NMAX / 2], cim[2][NMAX / 2];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_bgemm_tc(Op op, const int* __res
   extern __shared__ unsigned char tc_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  const int v = blockIdx.z;
+  const int v = op.c.vi.vid(blockIdx.z);
   if (active && !active[v]) return;
   const int N = op.c.vi.N[v];
   int m, n, K;

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_advect(VesIndex vi, const double* __res
                                                 const double* __restrict__ scratch, int s, const int* __restrict__ piv,
                                                 double dt, double* __restrict__ xy_out) {
   __shared__ double d[NMAX], u1[NMAX], u2[NMAX], b[2 * NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_relax_solve(VesIndex vi, const double* 
                                                      const double* __restrict__ scratch, const int* __restrict__ piv,
                                                      double* __restrict__ xy_out) {
   __shared__ double b[2 * NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) b[r] = xy_star[2 * o + r];
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_redistribute(VesIndex vi, const double*
   __shared__ double l[6 * NMAX + 1];
   __shared__ float2 cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
   __shared__ double base[2];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int Nu = 6 * N;
   const int64_t o = vi.off[v];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_tension(VesIndex vi, const double* __re
                                                  int s, const int* __restrict__ piv, double kappa,
                                                  double* __restrict__ sigma) {
   __shared__ double d[NMAX], b[2 * NMAX], w[2 * NMAX], rhs[NMAX];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NMAX) k_corr_init(VesIndex vi, const double* _
                                                     double* __restrict__ corr, int* __restrict__ active,
                                                     int* __restrict__ dirty, unsigned* err) {
   __shared__ double d[NMAX], xs[NMAX], ys[NMAX], red[NMAX / 32];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double
   __shared__ float dq[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX], f1[2 * NMAX];
   __shared__ float yv[3][2 * NMAX];
   __shared__ double sol[3];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   if (!dirty[v]) return;
   const int N = vi.N[v];
   const int n2 = 2 * N;
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) k_corr_newton(VesIndex vi, const double* 
                                                      const int* __restrict__ dirty, int iters,
                                                      double* __restrict__ xy, int* __restrict__ fired, unsigned* err) {
   extern __shared__ unsigned char corr_raw[];
-  const int v = blockIdx.x;
+  const int v = vi.vid(blockIdx.x);
   if (!dirty[v]) return;
   const int N = vi.N[v];
   const int n = 2 * N + 2;

@@ -42,6 +42,7 @@ struct Layout {
   std::vector<int64_t> off, moff, toff;
   std::vector<int32_t> owner, chunk, chunk1k;  // far-field source chunks of at most 2048 / 1024 points
   std::vector<double> tab;
+  std::vector<int32_t> order;  // vesicles by point count, descending (empty when all counts are equal)
 };
 
 // Greedy chunks of whole vesicles with at most `limit` points each: boundaries in vesicles.
@@ -94,6 +95,13 @@ bool build_layout(const int64_t* offsets, int M, Layout& L, std::string& msg) {
     for (int64_t p = L.off[v]; p < L.off[v + 1]; ++p) L.owner[p] = v;
   L.chunk = source_chunks(L.N, FF_CHUNK);
   L.chunk1k = source_chunks(L.N, 1024);
+  // per-vesicle launches take the largest vesicles first (longest work first shortens the tail)
+  L.order.clear();
+  if (*std::min_element(L.N.begin(), L.N.end()) != L.nmax) {
+    L.order.resize(M);
+    for (int v = 0; v < M; ++v) L.order[v] = v;
+    std::stable_sort(L.order.begin(), L.order.end(), [&](int a, int b) { return L.N[a] > L.N[b]; });
+  }
   return true;
 }
 
@@ -121,11 +129,12 @@ struct DevLayout {
   float* tab32 = nullptr;  // FP32 copy of tab (FP32 operator products)
   float4* logtab = nullptr;  // (log c_k, 1/c_k) as FP32 pairs, c_k = 1 + (k + 1/2)/LOG_TAB (log_df)
   float2* tabdf = nullptr;   // double-float copy of tab (hi, lo)
-  VesIndex vi() const { return VesIndex{N, off, moff, toff}; }
+  int32_t* order = nullptr;
+  VesIndex vi() const { return VesIndex{N, off, moff, toff, order}; }
   void release() {
     cudaFree(N); cudaFree(off); cudaFree(moff); cudaFree(toff);
     cudaFree(owner); cudaFree(chunk); cudaFree(chunk1k); cudaFree(tab); cudaFree(tab32); cudaFree(logtab);
-    cudaFree(tabdf);
+    cudaFree(tabdf); cudaFree(order);
     *this = DevLayout{};
   }
 };
@@ -137,6 +146,10 @@ cudaError_t upload_layout(const Layout& L, DevLayout& D, cudaStream_t s) {
   VS_TRY(dalloc(&D.off, L.M + 1));
   VS_TRY(dalloc(&D.moff, L.M + 1));
   VS_TRY(dalloc(&D.toff, L.M));
+  if (!L.order.empty()) {
+    VS_TRY(dalloc(&D.order, L.M));
+    VS_TRY(upload(D.order, L.order.data(), L.M, s));
+  }
   VS_TRY(dalloc(&D.owner, L.P));
   VS_TRY(dalloc(&D.chunk, L.chunk.size()));
   VS_TRY(dalloc(&D.chunk1k, L.chunk1k.size()));
