@@ -119,7 +119,9 @@ vs_status vs_sync(vs_suspension* s);
 
 /*
  * Replace positions and tension from host buffers (same layout as vs_create; sigma has
- * offsets[M] doubles). The points are used as given (no redistribution); A_0, L_0 are kept.
+ * offsets[M] doubles). The points are used as given (no redistribution); A_0, L_0 are kept. The
+ * operators cached for a vesicle stay valid when its points are bitwise unchanged (state read back with
+ * vs_get_positions and passed in again); vesicles with any changed coordinate rebuild them. Synchronous.
  */
 vs_status vs_set_state(vs_suspension* s, const double* xy, const double* sigma);
 

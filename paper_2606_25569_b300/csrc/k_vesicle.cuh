@@ -630,4 +630,20 @@ __global__ void __launch_bounds__(256) k_corr_newton(VesIndex vi, const double* 
   }
 }
 
+// New positions for every vesicle: xy <- xy_new, and dirty[v] = 1 where any coordinate of v changed
+// (bitwise), so the operators cached for unchanged vesicles stay valid. One CTA of NMAX threads per vesicle.
+__global__ void __launch_bounds__(NMAX) k_state_update(VesIndex vi, const double* __restrict__ xy_new,
+                                                       double* __restrict__ xy, int* __restrict__ dirty) {
+  const int v = vi.vid(blockIdx.x);
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  bool changed = false;
+  for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) {
+    const double a = xy_new[2 * o + r];
+    changed |= __double_as_longlong(a) != __double_as_longlong(xy[2 * o + r]);
+    xy[2 * o + r] = a;
+  }
+  if (__syncthreads_or(changed) && threadIdx.x == 0) dirty[v] = 1;
+}
+
 }  // namespace vs

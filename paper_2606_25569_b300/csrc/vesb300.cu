@@ -979,10 +979,11 @@ vs_status vs_sync(vs_suspension* h) {
 vs_status vs_set_state(vs_suspension* h, const double* xy, const double* sigma) {
   if (!h || !xy || !sigma) return VS_ERR_INVALID_ARG;
   const Layout& L = h->L;
-  VS_CK(h, upload(h->xy, xy, 2 * L.P, h->stream), "set_state");
+  // staged in xy_star (free between steps); only vesicles whose points changed lose their cached operators
+  VS_CK(h, upload(h->xy_star, xy, 2 * L.P, h->stream), "set_state");
   VS_CK(h, upload(h->sigma, sigma, L.P, h->stream), "set_state");
-  std::vector<int> ones(L.M, 1);
-  VS_CK(h, upload(h->dirty, ones.data(), L.M, h->stream), "set_state");
+  VS_LAUNCH(h, "k_state_update", k_state_update<<<L.M, NMAX, 0, h->stream>>>(h->D.vi(), h->xy_star, h->xy, h->dirty));
+  VS_CK(h, cudaGetLastError(), "set_state");
   VS_CK(h, cudaStreamSynchronize(h->stream), "set_state");
   return VS_OK;
 }

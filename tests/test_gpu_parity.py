@@ -269,3 +269,33 @@ def test_tensor_core_and_fma_operator_products_agree(Ns):
     assert np.max(np.abs(a.tension() - b.tension())) <= 1e-10 * np.max(np.abs(b.tension()))
     a.close()
     b.close()
+
+
+def test_set_state_keeps_operators_of_unchanged_vesicles():
+    # vs_set_state only invalidates the cached operators of vesicles whose points changed; rebuilding the
+    # others would give the same bits, so a suspension whose every vesicle was invalidated must agree
+    xs, ys = _mixed([32, 64, 32, 48], 11, spacing=2.6)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, corr_tol=0.01, flow_kind=1, flow_p=(0.5, 0, 0, 0), use_graph=True)
+    a = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    b = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    a.step(2)
+    b.step(2)
+    xy, sg = a.positions(), a.tension()
+    # unchanged state: stepping on from the cache equals stepping without the call
+    b.set_state(xy, sg)
+    a.step(1)
+    b.step(1)
+    assert np.array_equal(a.positions(), b.positions()) and np.array_equal(a.tension(), b.tension())
+    # one vesicle moved: only its operators are rebuilt, with the same result as rebuilding all
+    xy, sg = a.positions(), a.tension()
+    new = xy.copy()
+    o, n = 32, 64
+    new[2 * o:2 * o + n] = 1.0001 * (new[2 * o:2 * o + n] - new[2 * o:2 * o + n].mean()) + new[2 * o:2 * o + n].mean()
+    a.set_state(new, sg)
+    b.set_state(xy + 1e-3, sg)  # every vesicle changed ...
+    b.set_state(new, sg)        # ... and then set to the same state as a
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.positions(), b.positions()) and np.array_equal(a.tension(), b.tension())
+    a.close()
+    b.close()
