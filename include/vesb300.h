@@ -83,7 +83,8 @@ typedef struct {
   int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
   int32_t use_graph; /* 1: replay each step from a captured CUDA graph (needs a non-NULL stream and
                         profiling off; otherwise steps are launched one kernel at a time) */
-  int32_t pad_;
+  int32_t exact_every; /* hybrid only: every exact_every-th step (counting from 1) takes the exact
+                          relaxation instead of the learned one; 0: never */
   uint64_t flags;    /* VS_FLAG_* */
 } vs_params;
 

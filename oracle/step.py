@@ -17,7 +17,10 @@ use X^{n+1} after redistribution (step 6), and since redistribution re-indexes t
 points, u^n is carried to the new points by its trigonometric interpolant. Algorithm 1
 computes the tension before the correction and so do we. One far-field evaluation per step
 (Algorithm 1 needs u^n once). With Params.relax_net set, step 4 is the learned relaxation of the
-hybrid step (relax_learned). Initial tension (not given in the paper):
+hybrid step (relax_learned), except for vesicles in a near pair this step (the target's owner or the
+source vesicle) and, with exact_every = m > 0, on every m-th step: those relax exactly, the plain step
+serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
+too; here they keep the exact relaxation). Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -32,12 +35,14 @@ from .spectral import Geometry, eval_interpolant, force
 
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
-                 near_field=False, corr_tol=0.01, relax_net=None):
+                 near_field=False, corr_tol=0.01, relax_net=None, exact_every=0):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
-        # (dims, flat parameters, output scale, filter kmax): the learned relaxation of the hybrid step
+        # (dims, flat parameters, output scale, filter kmax[, affine]): the learned relaxation of the hybrid
+        # step; with exact_every = m > 0 every m-th step (counting from 1) relaxes exactly instead
         self.relax_net = relax_net
+        self.exact_every = int(exact_every)
 
 
 def relax_learned(x, y, net):
@@ -125,11 +130,27 @@ class Suspension:
 
     def step(self):
         p = self.p
+        self.nstep = getattr(self, "nstep", 0) + 1
+        if p.relax_net is not None and p.exact_every > 0 and self.nstep % p.exact_every == 0:
+            import copy
+            p = copy.copy(p)
+            p.relax_net = None
         u = self.interaction_velocity()
+        # in a learned step, vesicles in a near pair (as the target's owner or as the source) relax exactly
+        exact = set()
+        if p.relax_net is not None:
+            owner = np.repeat(np.arange(len(self.xs)), [len(x) for x in self.xs])
+            for t, v in self.near_pairs:
+                exact.update((int(owner[t]), int(v)))
         nxs, nys, nsig, vel = [], [], [], []
         for v, (x, y) in enumerate(zip(self.xs, self.ys)):
             ux, uy = u[v]
-            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], p)
+            pv = p
+            if v in exact:
+                import copy
+                pv = copy.copy(p)
+                pv.relax_net = None
+            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], pv)
             self.corrections += int(fired)
             nxs.append(xc)
             nys.append(yc)

@@ -105,7 +105,7 @@ class VsError(RuntimeError):
 class VsParams(ctypes.Structure):
     _fields_ = [("kappa_b", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
                 ("corr_tol", ctypes.c_double), ("mode", ctypes.c_int32), ("near_field", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("pad_", ctypes.c_int32), ("flags", ctypes.c_uint64)]
+                ("use_graph", ctypes.c_int32), ("exact_every", ctypes.c_int32), ("flags", ctypes.c_uint64)]
 
 
 class VsFlow(ctypes.Structure):
@@ -136,7 +136,7 @@ class Suspension:
 
     def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
                  flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0,
-                 use_graph=False, direct_fp64=False, autotune=True, tc_gemm=False):
+                 use_graph=False, direct_fp64=False, autotune=True, tc_gemm=False, exact_every=0):
         L = lib()
         self._h = ctypes.c_void_p()
         xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -145,7 +145,8 @@ class Suspension:
         self.P = int(off[-1])
         flags = ((VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0) | (VS_FLAG_DIRECT_FP64 if direct_fp64 else 0)
                  | (0 if autotune else VS_FLAG_NO_AUTOTUNE) | (VS_FLAG_TC_GEMM if tc_gemm else 0))
-        p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0, 0, flags)
+        p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0,
+                     int(exact_every), flags)
         f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
         st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),
                          ctypes.byref(self._h))

@@ -38,6 +38,7 @@ struct GeomOut {
   float4* g32;     // FP32 (1/|X_alpha|, x_s, y_s, 0) for the FP32 operator products (may be null)
   float4* sdf;     // 3 per point, double-float pairs for the self matrix (may be null):
                    //   (x - x_0, y - y_0), (|X_alpha| / (4 pi mu), -R(0)/2 - (2 pi/N) log|X_alpha|), (x_s, y_s)
+  const int* active;  // null, or only vesicles with active[v] != 0 are processed
 };
 
 // Force/source outputs (only written when `f` is non-null). With f_in non-null the density is
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
   __shared__ double xs[NMAX], ys[NMAX], red[NMAX / 32];
   __shared__ float2 dd[NMAX], w1[NMAX], w2[NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (g.active && !g.active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;

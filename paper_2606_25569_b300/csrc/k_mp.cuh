@@ -303,12 +303,13 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
                                                   const double* __restrict__ ty, const double* __restrict__ tab,
                                                   const float* __restrict__ scratch32, int s, int64_t ainv_sub,
                                                   double kappa, double dt, double* __restrict__ xy_out,
-                                                  unsigned* err) {
+                                                  unsigned* err, const int* __restrict__ active) {
   __shared__ MpShared sh;
   __shared__ double b[2 * NMAX], x[2 * NMAX], sg[NMAX], r1[2 * NMAX], cen[2];
   __shared__ float2 y2[NMAX];
   __shared__ __align__(16) float fy[NMAX], fr[2 * NMAX], fdx[2 * NMAX], fw[NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int64_t NN = (int64_t)N * N;

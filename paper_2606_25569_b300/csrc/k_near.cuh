@@ -30,6 +30,17 @@ __global__ void k_near_mark(int64_t P, const int* __restrict__ near_cnt, const i
   for (int k = 0; k < c; ++k) has_near[near_v[t * MAX_NEAR + k]] = 1;
 }
 
+// involved[v] = 1 for every vesicle in a near pair: the owner of a target with near vesicles and each
+// of those vesicles.
+__global__ void k_near_involved(int64_t P, const int32_t* __restrict__ owner, const int* __restrict__ near_cnt,
+                                const int* __restrict__ near_v, int* __restrict__ involved) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int c = near_cnt[t];
+  if (c > 0) involved[owner[t]] = 1;
+  for (int k = 0; k < c; ++k) involved[near_v[t * MAX_NEAR + k]] = 1;
+}
+
 struct NearBufs {
   double* layer;   // per vesicle at 30 off[v]: LX, LY, UX, UY, WX, WY (5N each)
   float* phi;      // per vesicle at moff[v]: (5N)^2 floats

@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) k_advect(VesIndex vi, const double* __res
 // X^{n+1} = A^{-1} X*, A = I - dt (I - M*) B* factored in place (Eq. relaxation_disc).
 __global__ void __launch_bounds__(256) k_relax_solve(VesIndex vi, const double* __restrict__ xy_star,
                                                      const double* __restrict__ scratch, const int* __restrict__ piv,
-                                                     double* __restrict__ xy_out) {
+                                                     double* __restrict__ xy_out, const int* __restrict__ active) {
   __shared__ double b[2 * NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) b[r] = xy_star[2 * o + r];

@@ -28,7 +28,7 @@
 
 using namespace vs;
 
-constexpr int CORR_NEWTON_ITERS = 8;  // Newton steps on the KKT system (quadratic convergence)
+constexpr int CORR_NEWTON_ITERS = 16;  // Newton steps on the KKT system (linear convergence with the FP32 Jacobian)
 
 namespace {
 
@@ -280,6 +280,7 @@ struct vs_suspension {
   int *piv = nullptr, *dirty = nullptr, *fired = nullptr;
   unsigned* err = nullptr;
   int* has_near = nullptr;
+  int* involved = nullptr;         // vesicles in a near pair this step (hybrid: they relax exactly)
   NearBufs nb{nullptr, nullptr};
   double* corr = nullptr;          // correction state (6 N + 16 doubles per vesicle)
   int *cactive = nullptr, *cpiv = nullptr;
@@ -292,8 +293,9 @@ struct vs_suspension {
   int64_t steps = 0;
   int64_t launches = 0;
   Prof prof;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one captured step per operator-slot parity
-  int64_t graph_launches[2] = {0, 0};
+  // one captured step per (operator-slot parity, relaxation kind: learned 0 / exact 1)
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t graph_launches[4] = {0, 0, 0, 0};
   int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
   std::string msg;
 };
@@ -472,12 +474,17 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   return VS_OK;
 }
 
-vs_status geometry(vs_suspension* h, const double* xy, bool with_force) {
+inline GeomOut geom_active(GeomOut g, const int* active) {
+  g.active = active;
+  return g;
+}
+
+vs_status geometry(vs_suspension* h, const double* xy, bool with_force, const int* active = nullptr) {
   ForceOut fo{};
   if (with_force)
     fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
   VS_LAUNCH(h, "k_geometry", k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
-                                             flow_dev(h->flow), h->B.geom(), fo, nullptr));
+                                             flow_dev(h->flow), geom_active(h->B.geom(), active), fo, nullptr));
   VS_CK(h, cudaGetLastError(), "geometry");
   return VS_OK;
 }
@@ -602,25 +609,27 @@ vs_status mlp_forward(vs_mlp* h, const float* x, int batch, bool out_map);
 const float* mlp_output(const vs_mlp* h);
 
 // Exact relaxation (Eq. relaxation_disc) of the points xs into xo, operators built in slot s.
-vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
+// Exact relaxation (Eq. relaxation_disc) of xs into xo with the operators at slot s; with active non-null
+// only the vesicles with active[v] != 0 are processed and written.
+vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s, const int* active = nullptr) {
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
   const VesIndex vi = h->D.vi();
   vs_status st;
-  if ((st = geometry(h, xs, false)) != VS_OK) return st;
-  if ((st = build_operators(h, xs, s, nullptr)) != VS_OK) return st;
+  if ((st = geometry(h, xs, false, active)) != VS_OK) return st;
+  if ((st = build_operators(h, xs, s, active)) != VS_OK) return st;
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
   if (mixed(h)) {
-    gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, nullptr);
-    gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, nullptr);
-    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, nullptr);
-    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 1, h->p.kappa_b}, 2 * n, n, nullptr);
-    gemm32(h, "k_bgemm<OpPB32>", OpPB32{c}, n, 2 * n, nullptr);
-    gemm32(h, "k_bgemm<OpW32>", OpW32{c, s}, n, 2 * n, nullptr);
-    gemm32(h, "k_bgemm<OpA32>", OpA32{c, s, h->p.dt}, 2 * n, 2 * n, nullptr);
+    gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, active);
+    gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, active);
+    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, active);
+    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 1, h->p.kappa_b}, 2 * n, n, active);
+    gemm32(h, "k_bgemm<OpPB32>", OpPB32{c}, n, 2 * n, active);
+    gemm32(h, "k_bgemm<OpW32>", OpW32{c, s}, n, 2 * n, active);
+    gemm32(h, "k_bgemm<OpA32>", OpA32{c, s, h->p.dt}, 2 * n, 2 * n, active);
     const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
     const int64_t ainv = MatLayout::A;
-    if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, nullptr)) {
+    if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, active)) {
       // 2N beyond the register Gauss-Jordan: the 2 x 2 block (Schur complement) inverse in place,
       // A = [A11 A12; A21 A22], X1 = A11^{-1}, Y = X1 A12, Z = A21 X1, S = A22 - A21 Y,
       // A^{-1} = [X1 - C12 Z, C12; -S^{-1} Z, S^{-1}] with C12 = -Y S^{-1}; X1, Y, Z, S^{-1} in the free B block
@@ -640,7 +649,7 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
       VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
     }
     MP_DISPATCH(h, "k_relax_mp", k_relax_mp, M, (vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv,
-                                                    h->p.kappa_b, h->p.dt, xo, h->err));
+                                                    h->p.kappa_b, h->p.dt, xo, h->err, active));
     VS_CK(h, cudaGetLastError(), "relaxation");
     return VS_OK;
   }
@@ -652,7 +661,7 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s) {
   VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<double><<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
   VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
   launch_lu(h, "k_lu<A>", LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, 2 * n, nullptr);
-  VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo));
+  VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo, active));
   VS_CK(h, cudaGetLastError(), "relaxation");
   return VS_OK;
 }
@@ -753,6 +762,13 @@ vs_status correction(vs_suspension* h) {
   return VS_OK;
 }
 
+// Hybrid steps use the learned relaxation except every exact_every-th step (counting from 1), which takes
+// the exact one.
+inline bool learned_step(const vs_suspension* h) {
+  if (h->p.mode != 1) return false;
+  return !(h->p.exact_every > 0 && (h->steps + 1) % h->p.exact_every == 0);
+}
+
 vs_status step_once(vs_suspension* h) {
   const Layout& L = h->L;
   const int M = L.M, n = L.nmax;
@@ -776,8 +792,16 @@ vs_status step_once(vs_suspension* h) {
   }
   VS_CK(h, cudaGetLastError(), "advection");
   // (5) relaxation at X*: exact (plain) or the learned map (hybrid)
-  if (h->p.mode == 1) {
+  if (learned_step(h)) {
     if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
+    if (h->p.near_field && M > 1) {
+      // the plain step is the fallback of the learned one: vesicles in a near pair relax exactly
+      VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
+      const int tgrid = (int)((L.P + 127) / 128);
+      VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
+                                                                                     h->B.near_v, h->involved));
+      if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
+    }
   } else {
     if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt)) != VS_OK) return st;
   }
@@ -808,7 +832,7 @@ vs_status read_err(vs_suspension* h) {
 }
 
 void drop_graphs(vs_suspension* h) {
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < 4; ++c)
     if (h->graph[c]) {
       cudaGraphExecDestroy(h->graph[c]);
       h->graph[c] = nullptr;
@@ -819,7 +843,7 @@ void drop_graphs(vs_suspension* h) {
 // read every per-step decision (dirty operator slots, near lists, correction triggers) from device
 // flags, so the captured sequence is valid for every later step with the same parity.
 vs_status step_graph(vs_suspension* h) {
-  const int c = h->cur;
+  const int c = h->cur + (learned_step(h) ? 0 : 2);
   if (!h->graph[c]) {
     cudaGraph_t g = nullptr;
     VS_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
@@ -829,7 +853,7 @@ vs_status step_graph(vs_suspension* h) {
     h->graph_launches[c] = h->launches - l0;
     h->launches = l0;
     h->steps = s0;
-    h->cur = c;
+    h->cur = c & 1;
     if (st != VS_OK) { if (g) cudaGraphDestroy(g); return st; }
     VS_CK(h, e, "graph capture");
     const cudaError_t ei = cudaGraphInstantiate(&h->graph[c], g, 0);
@@ -837,7 +861,7 @@ vs_status step_graph(vs_suspension* h) {
     VS_CK(h, ei, "graph instantiate");
   }
   VS_CK(h, cudaGraphLaunch(h->graph[c], h->stream), "graph launch");
-  h->cur = 1 - c;
+  h->cur = 1 - (c & 1);
   h->steps += 1;
   h->launches += h->graph_launches[c];
   return VS_OK;
@@ -850,6 +874,7 @@ bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
     return false;
   }
   if (p->mode != 0 && p->mode != 1) { msg = "mode must be 0 (plain) or 1 (hybrid)"; return false; }
+  if (p->exact_every < 0) { msg = "exact_every must be >= 0"; return false; }
   if (f->kind < 0 || f->kind > 3) { msg = "unknown flow kind"; return false; }
   if ((f->kind == 2 || f->kind == 3) && !(f->p[1] != 0.0)) { msg = "flow length scale p[1] must be non-zero"; return false; }
   return true;
@@ -862,7 +887,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
   cudaFree(h->scratch32); cudaFree(h->piv32);
-  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near);
+  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near); cudaFree(h->involved);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
 }
@@ -905,6 +930,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->scratch32, L.moff[L.M])); VS_A(dalloc(&h->piv32, 4 * L.P));
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
+  VS_A(dalloc(&h->involved, L.M));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));

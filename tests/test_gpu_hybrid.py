@@ -82,8 +82,8 @@ def test_relax_map_matches_oracle():
     assert rel_err_per_vesicle(gx, gy, rx, ry) <= 1e-10
 
 
-@pytest.mark.parametrize("with_affine", [False, True])
-def test_hybrid_step_matches_oracle(with_affine):
+@pytest.mark.parametrize("with_affine,exact_every", [(False, 0), (True, 0), (True, 2)])
+def test_hybrid_step_matches_oracle(with_affine, exact_every):
     N, M = 64, 4
     xs, ys = _shapes(M, N, 3)
     W = binding.feature_width(N, 31)
@@ -104,8 +104,9 @@ def test_hybrid_step_matches_oracle(with_affine):
                f32(0.1 * rng.standard_normal(W)), f32(rng.uniform(0.2, 1.0, W)))
         net.set_affine(*aff)
         relax_net = relax_net + (aff,)
-    o = OracleSuspension(xs, ys, Params(relax_net=relax_net, **kw))
-    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
+    o = OracleSuspension(xs, ys, Params(relax_net=relax_net, exact_every=exact_every, **kw))
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1,
+                           exact_every=exact_every, use_graph=exact_every > 0, **kw)
     g.set_network(net, scale, 31)
     for _ in range(3):
         o.step()
@@ -150,3 +151,32 @@ def test_trained_network_beats_the_step_without_it():
     # the same shapes without the network: zero displacement, relative error exactly 1
     assert float(np.mean(held)) <= 0.5, float(np.mean(held))
     assert float(np.median(held)) <= 0.5
+
+
+def test_hybrid_near_pairs_fall_back_to_exact_relaxation():
+    # vesicles in a near pair relax exactly, the rest with the network, on both sides; FP64 far field and
+    # the near-field correction on (its FP32 RBF solve sets the tolerances, as in the plain near-field test)
+    from .test_gpu_parity import _close_pair
+    xs, ys = _close_pair()
+    N, M = 32, 3
+    W = binding.feature_width(N, 15)
+    dims = [W, 128, W]
+    rng = np.random.default_rng(8)
+    params = init_params(dims, rng).astype(np.float32).astype(np.float64)
+    scale = 2e-4
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0.0, 0.0, 0.0), near_field=True)
+    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale, 15), **kw))
+    stream = torch.cuda.current_stream()
+    net = binding.Mlp(dims, max_batch=M, stream=stream)
+    net.set_params(params)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
+    g.set_network(net, scale, 15)
+    for _ in range(2):
+        o.step()
+        g.step()
+        assert len(o.near_pairs) > 0
+        owner = np.repeat(np.arange(M), N)
+        assert {int(owner[t]) for t, _ in o.near_pairs} | {v for _, v in o.near_pairs} == {0, 1}
+        gx, gy = split(g.positions(), [N] * M)
+        assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-8
+    g.close()
