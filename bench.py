@@ -280,7 +280,9 @@ def hybrid_arm(wl, args, stream):
     hyb.close()
     last = errs.get(str(args.hybrid_steps))
     out.update({"shape_error_mean_by_step": errs, "after_steps": args.hybrid_steps,
-                "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2)})
+                "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2),
+                "fallback": "exact relaxation on every %d-th step and for vesicles within 3 spacings h of "
+                            "another vesicle" % exact_every})
     if failed:
         out["failed"] = failed
     return out
@@ -407,6 +409,7 @@ def run_gpu(args):
     hybrid = None
     if rank == 0 and not args.no_hybrid:
         hybrid = hybrid_arm(wl, args, stream)
+        hybrid["vs_plain"] = hybrid["value"] / (value / world)  # both single-GPU throughputs
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(wl)

@@ -18,8 +18,8 @@ points, u^n is carried to the new points by its trigonometric interpolant. Algor
 computes the tension before the correction and so do we. One far-field evaluation per step
 (Algorithm 1 needs u^n once). With Params.relax_net set, step 4 is the learned relaxation of the
 hybrid step (relax_learned), except for vesicles in a near pair this step (the target's owner or the
-source vesicle) and, with exact_every = m > 0, on every m-th step: those relax exactly, the plain step
-serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
+source vesicle) or within HYBRID_EXACT_GAP spacings of another vesicle, and, with exact_every = m > 0,
+on every m-th step: those relax exactly, the plain step serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
 too; here they keep the exact relaxation). Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
@@ -142,6 +142,7 @@ class Suspension:
             owner = np.repeat(np.arange(len(self.xs)), [len(x) for x in self.xs])
             for t, v in self.near_pairs:
                 exact.update((int(owner[t]), int(v)))
+            exact.update(close_vesicles(self.xs, self.ys, HYBRID_EXACT_GAP))
         nxs, nys, nsig, vel = [], [], [], []
         for v, (x, y) in enumerate(zip(self.xs, self.ys)):
             ux, uy = u[v]
@@ -157,6 +158,22 @@ class Suspension:
             nsig.append(sig)
             vel.append(np.concatenate([ux, uy]))
         self.xs, self.ys, self.sig, self.velocity = nxs, nys, nsig, vel
+
+
+HYBRID_EXACT_GAP = 3.0
+
+
+def close_vesicles(xs, ys, gap_h):
+    """Vesicles with a point within gap_h * max(h_a, h_b) of a point of another vesicle b, h = L/N
+    (brute force over all pairs of points)."""
+    hs = [Geometry(x, y).length / len(x) for x, y in zip(xs, ys)]
+    out = set()
+    for a in range(len(xs)):
+        for b in range(a + 1, len(xs)):
+            d2 = (xs[a][:, None] - xs[b][None, :]) ** 2 + (ys[a][:, None] - ys[b][None, :]) ** 2
+            if d2.min() <= (gap_h * max(hs[a], hs[b])) ** 2:
+                out.update((a, b))
+    return out
 
 
 def advance_vesicle(x, y, ux, uy, A0, L0, p):

@@ -41,6 +41,63 @@ __global__ void k_near_involved(int64_t P, const int32_t* __restrict__ owner, co
   for (int k = 0; k < c; ++k) involved[near_v[t * MAX_NEAR + k]] = 1;
 }
 
+// involved[a] = 1 when a point of vesicle a lies within gap_h times the larger spacing h = L/N of the two
+// vesicles from a point of another vesicle b. One CTA per vesicle a: the threads screen the other vesicles
+// by their bounding circles (centre, reach = largest distance to the centre plus h) and collect the
+// candidates, which are then compared point by point. More than PROX_CAND candidates counts as a hit.
+constexpr int PROX_CAND = 64;
+__global__ void __launch_bounds__(128) k_proximity(VesIndex vi, const double* __restrict__ xy,
+                                                   const double2* __restrict__ centre, const float2* __restrict__ h2,
+                                                   int M, double gap_h, int* __restrict__ involved) {
+  __shared__ float px[NMAX], py[NMAX];
+  __shared__ int cand[PROX_CAND];
+  __shared__ int nc, hit;
+  const int a = vi.vid(blockIdx.x);
+  const int Na = vi.N[a];
+  const int64_t oa = vi.off[a];
+  const double2 ca = centre[a];
+  const float2 ha = h2[a];
+  for (int i = threadIdx.x; i < Na; i += blockDim.x) {
+    px[i] = (float)(xy[2 * oa + i] - ca.x);
+    py[i] = (float)(xy[2 * oa + Na + i] - ca.y);
+  }
+  if (threadIdx.x == 0) { nc = 0; hit = 0; }
+  __syncthreads();
+  const float ra = sqrtf(ha.y), hA = sqrtf(ha.x);
+  for (int b = threadIdx.x; b < M; b += blockDim.x) {
+    if (b == a) continue;
+    const float2 hb = h2[b];
+    const double2 cb = centre[b];
+    const float dx = (float)(cb.x - ca.x), dy = (float)(cb.y - ca.y);
+    const float lim = ra + sqrtf(hb.y) + (float)gap_h * fmaxf(hA, sqrtf(hb.x));
+    if (dx * dx + dy * dy <= lim * lim) {
+      const int k = atomicAdd(&nc, 1);
+      if (k < PROX_CAND) cand[k] = b;
+    }
+  }
+  __syncthreads();
+  const int n = min(nc, PROX_CAND);
+  if (nc > PROX_CAND && threadIdx.x == 0) hit = 1;
+  __syncthreads();
+  for (int c = 0; c < n && !hit; ++c) {  // hit is read after a barrier: uniform
+    const int b = cand[c];
+    const int Nb = vi.N[b];
+    const int64_t ob = vi.off[b];
+    const float gap = (float)gap_h * fmaxf(hA, sqrtf(h2[b].x));
+    float mn = 3.0e38f;
+    for (int j = threadIdx.x; j < Nb; j += blockDim.x) {
+      const float qx = (float)(xy[2 * ob + j] - ca.x), qy = (float)(xy[2 * ob + Nb + j] - ca.y);
+      for (int i = 0; i < Na; ++i) {
+        const float rx = qx - px[i], ry = qy - py[i];
+        mn = fminf(mn, rx * rx + ry * ry);
+      }
+    }
+    if (mn <= gap * gap) hit = 1;  // every writer stores 1
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && hit) involved[a] = 1;
+}
+
 struct NearBufs {
   double* layer;   // per vesicle at 30 off[v]: LX, LY, UX, UY, WX, WY (5N each)
   float* phi;      // per vesicle at moff[v]: (5N)^2 floats

@@ -28,6 +28,9 @@
 
 using namespace vs;
 
+// Hybrid steps relax exactly every vesicle within this many point spacings h = L/N (the larger of the two
+// vesicles') of another vesicle.
+constexpr double HYBRID_EXACT_GAP = 3.0;
 constexpr int CORR_NEWTON_ITERS = 16;  // Newton steps on the KKT system (linear convergence with the FP32 Jacobian)
 
 namespace {
@@ -795,11 +798,14 @@ vs_status step_once(vs_suspension* h) {
   if (learned_step(h)) {
     if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
     if (h->p.near_field && M > 1) {
-      // the plain step is the fallback of the learned one: vesicles in a near pair relax exactly
+      // the plain step is the fallback of the learned one: vesicles in a near pair, or closer to another
+      // vesicle than HYBRID_EXACT_GAP spacings, relax exactly
       VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
       const int tgrid = (int)((L.P + 127) / 128);
       VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
                                                                                      h->B.near_v, h->involved));
+      VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
+                                                                         HYBRID_EXACT_GAP, h->involved));
       if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
     }
   } else {

@@ -180,3 +180,31 @@ def test_hybrid_near_pairs_fall_back_to_exact_relaxation():
         gx, gy = split(g.positions(), [N] * M)
         assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-8
     g.close()
+
+
+def test_hybrid_close_vesicles_relax_exactly():
+    # two vesicles about two spacings apart (no near pair, within three spacings) and a far one
+    from .test_gpu_parity import _close_pair
+    xs, ys = _close_pair(gap_h=2.0)
+    N, M = 32, 3
+    W = binding.feature_width(N, 15)
+    dims = [W, 128, W]
+    rng = np.random.default_rng(9)
+    params = init_params(dims, rng).astype(np.float32).astype(np.float64)
+    scale = 2e-4
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0.0, 0.0, 0.0), near_field=True)
+    o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale, 15), **kw))
+    from oracle.step import close_vesicles
+    assert close_vesicles(o.xs, o.ys, 3.0) == {0, 1}
+    stream = torch.cuda.current_stream()
+    net = binding.Mlp(dims, max_batch=M, stream=stream)
+    net.set_params(params)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
+    g.set_network(net, scale, 15)
+    for _ in range(2):
+        o.step()
+        g.step()
+        assert len(o.near_pairs) == 0
+        gx, gy = split(g.positions(), [N] * M)
+        assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-8
+    g.close()

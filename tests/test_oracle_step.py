@@ -80,3 +80,16 @@ def test_advection_moves_with_uniform_background():
     s0.step()
     assert np.max(np.abs(s.xs[0] - s0.xs[0] - 2e-3)) < 1e-10
     assert np.max(np.abs(s.ys[0] - s0.ys[0])) < 1e-10
+
+
+def test_close_vesicles_against_circles_at_known_gaps():
+    # two unit circles whose nearest points (angles 0 and pi, both sampled) are `gap` apart; h = 2 pi / N
+    from oracle.step import close_vesicles
+    N = 32
+    t = 2 * np.pi * np.arange(N) / N
+    h = 2 * np.pi / N
+    far = (np.cos(t) + 40.0, np.sin(t))
+    for gap, expect in ((2.9 * h, {0, 1}), (3.1 * h, set())):
+        xs = [np.cos(t), np.cos(t) + 2.0 + gap, far[0]]
+        ys = [np.sin(t), np.sin(t), far[1]]
+        assert close_vesicles(xs, ys, 3.0) == expect
