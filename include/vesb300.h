@@ -146,7 +146,21 @@ vs_status vs_get_device_ptrs(const vs_suspension* s, const double** xy, const do
  * [4] kernels launched by this handle so far. Synchronises. */
 vs_status vs_get_counters(vs_suspension* s, int64_t* out5);
 
-/* FP32 far-field launch shape; the paper has no counterpart (a tuning control). vs_create times the
+/*
+ * Checkpoint and resume (no counterpart in the paper). A checkpoint holds what a later run needs to
+ * continue bit for bit: positions, tension, A_0 and L_0, the step count and the correction counter, with
+ * kappa_b, mu, dt, mode and a hash of the point counts, in a versioned layout of
+ * vs_checkpoint_size bytes of caller-owned HOST memory. vs_restore loads one into a suspension created
+ * with the same offsets and parameters (otherwise VS_ERR_INVALID_ARG); its cached operators are rebuilt
+ * from the restored points at the next step, which gives the same bits as the uninterrupted run. A
+ * hybrid suspension needs its network set again. Both synchronise; vs_checkpoint reports pending
+ * device errors.
+ */
+vs_status vs_checkpoint_size(vs_suspension* s, int64_t* bytes);
+vs_status vs_checkpoint(vs_suspension* s, void* buf, int64_t cap);
+vs_status vs_restore(vs_suspension* s, const void* buf, int64_t size);
+
+/* FP32 far-field launch shape; the paper has no counterpart/* FP32 far-field launch shape; the paper has no counterpart (a tuning control). vs_create times the
  * far-field kernel in each of its launch shapes (threads per CTA x source points staged per chunk)
  * on the suspension's own sources and keeps the fastest, unless VS_FLAG_NO_AUTOTUNE is set; the
  * choice is cached per (device name, M, points, near mask) in the process, and in the text file

@@ -41,6 +41,9 @@ FUNCTIONS = {
     "vs_relax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_training_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, ctypes.c_int32]),
+    "vs_checkpoint_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_restore": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_destroy": (None, [ctypes.c_void_p]),
     "vs_farfield_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -225,6 +228,19 @@ class Suspension:
     def training_pairs(self, xy_in_dev, xin_dev, yout_dev, out_scale, filter_kmax):
         self._check(lib().vs_training_pairs(self._h, _ptr(xy_in_dev), _ptr(xin_dev), _ptr(yout_dev), float(out_scale),
                                             int(filter_kmax)))
+
+    def checkpoint(self):
+        """The suspension's checkpoint (vs_checkpoint) as bytes."""
+        n = ctypes.c_int64()
+        self._check(lib().vs_checkpoint_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(lib().vs_checkpoint(self._h, buf, n.value))
+        return buf.raw
+
+    def restore(self, data):
+        """Load a checkpoint made by checkpoint() (vs_restore)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._check(lib().vs_restore(self._h, buf, len(data)))
 
     def device_ptrs(self):
         a, b = ctypes.c_void_p(), ctypes.c_void_p()

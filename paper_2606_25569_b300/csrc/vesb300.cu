@@ -1054,6 +1054,29 @@ vs_status vs_get_device_ptrs(const vs_suspension* h, const double** xy, const do
   return VS_OK;
 }
 
+// Checkpoint format (little-endian host memory): CkptHeader, then xy (2P), sigma (P), A_0 (M), L_0 (M)
+// as doubles.
+struct CkptHeader {
+  char magic[8];       // "VSCKPT\0\1"
+  int64_t M, P;
+  uint64_t layout;     // FNV-1a hash of the point counts
+  int64_t steps;
+  int32_t fired, mode;
+  double kappa_b, mu, dt;
+};
+constexpr char CKPT_MAGIC[8] = {'V', 'S', 'C', 'K', 'P', 'T', 0, 1};
+
+uint64_t layout_hash(const Layout& L) {
+  uint64_t x = 1469598103934665603ull;
+  for (int32_t n : L.N) {
+    x ^= (uint64_t)(uint32_t)n;
+    x *= 1099511628211ull;
+  }
+  return x;
+}
+
+int64_t ckpt_bytes(const Layout& L) { return (int64_t)sizeof(CkptHeader) + (3 * L.P + 2 * (int64_t)L.M) * 8; }
+
 vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
   if (!h || !out4) return VS_ERR_INVALID_ARG;
   prof_collect(h);
@@ -1149,6 +1172,69 @@ vs_status vs_training_pairs(vs_suspension* h, const double* xy_in, float* xin, f
   VS_LAUNCH(h, "k_to_frame_rows", k_to_frame_rows<<<L.M, NMAX, 0, h->stream>>>(vi, xy_in, h->xy_next, h->frames,
                                                                              1.0 / out_scale, h->D.tab, kmax, yout, W));
   VS_CK(h, cudaGetLastError(), "training pairs");
+  return VS_OK;
+}
+
+vs_status vs_checkpoint_size(vs_suspension* h, int64_t* bytes) {
+  if (!h || !bytes) return VS_ERR_INVALID_ARG;
+  *bytes = ckpt_bytes(h->L);
+  return VS_OK;
+}
+
+vs_status vs_checkpoint(vs_suspension* h, void* buf, int64_t cap) {
+  if (!h || !buf) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  if (cap < ckpt_bytes(L)) { h->msg = "checkpoint buffer too small"; return VS_ERR_INVALID_ARG; }
+  const vs_status st = read_err(h);
+  if (st != VS_OK) return st;
+  int fired = 0;
+  VS_CK(h, cudaMemcpy(&fired, h->fired, sizeof fired, cudaMemcpyDeviceToHost), "checkpoint");
+  CkptHeader hd{};
+  std::memcpy(hd.magic, CKPT_MAGIC, 8);
+  hd.M = L.M;
+  hd.P = L.P;
+  hd.layout = layout_hash(L);
+  hd.steps = h->steps;
+  hd.fired = fired;
+  hd.mode = h->p.mode;
+  hd.kappa_b = h->p.kappa_b;
+  hd.mu = h->p.mu;
+  hd.dt = h->p.dt;
+  unsigned char* b = static_cast<unsigned char*>(buf);
+  std::memcpy(b, &hd, sizeof hd);
+  double* d = reinterpret_cast<double*>(b + sizeof hd);
+  VS_CK(h, cudaMemcpy(d, h->xy, 2 * L.P * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint");
+  VS_CK(h, cudaMemcpy(d + 2 * L.P, h->sigma, L.P * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint");
+  VS_CK(h, cudaMemcpy(d + 3 * L.P, h->A0, L.M * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint");
+  VS_CK(h, cudaMemcpy(d + 3 * L.P + L.M, h->L0, L.M * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint");
+  return VS_OK;
+}
+
+vs_status vs_restore(vs_suspension* h, const void* buf, int64_t size) {
+  if (!h || !buf) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  CkptHeader hd;
+  if (size < (int64_t)sizeof hd) { h->msg = "checkpoint too short"; return VS_ERR_INVALID_ARG; }
+  std::memcpy(&hd, buf, sizeof hd);
+  if (std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0) { h->msg = "not a checkpoint of this format"; return VS_ERR_INVALID_ARG; }
+  if (hd.M != L.M || hd.P != L.P || hd.layout != layout_hash(L) || size < ckpt_bytes(L)) {
+    h->msg = "checkpoint of a suspension with other point counts";
+    return VS_ERR_INVALID_ARG;
+  }
+  if (hd.kappa_b != h->p.kappa_b || hd.mu != h->p.mu || hd.dt != h->p.dt || hd.mode != h->p.mode) {
+    h->msg = "checkpoint of a suspension with other parameters (kappa_b, mu, dt, mode)";
+    return VS_ERR_INVALID_ARG;
+  }
+  const double* d = reinterpret_cast<const double*>(static_cast<const unsigned char*>(buf) + sizeof hd);
+  VS_CK(h, cudaStreamSynchronize(h->stream), "restore");
+  VS_CK(h, cudaMemcpy(h->xy, d, 2 * L.P * sizeof(double), cudaMemcpyHostToDevice), "restore");
+  VS_CK(h, cudaMemcpy(h->sigma, d + 2 * L.P, L.P * sizeof(double), cudaMemcpyHostToDevice), "restore");
+  VS_CK(h, cudaMemcpy(h->A0, d + 3 * L.P, L.M * sizeof(double), cudaMemcpyHostToDevice), "restore");
+  VS_CK(h, cudaMemcpy(h->L0, d + 3 * L.P + L.M, L.M * sizeof(double), cudaMemcpyHostToDevice), "restore");
+  VS_CK(h, cudaMemcpy(h->fired, &hd.fired, sizeof hd.fired, cudaMemcpyHostToDevice), "restore");
+  std::vector<int> ones(L.M, 1);  // every cached operator is rebuilt from the restored points
+  VS_CK(h, cudaMemcpy(h->dirty, ones.data(), L.M * sizeof(int), cudaMemcpyHostToDevice), "restore");
+  h->steps = hd.steps;
   return VS_OK;
 }
 

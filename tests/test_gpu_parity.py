@@ -299,3 +299,32 @@ def test_set_state_keeps_operators_of_unchanged_vesicles():
     assert np.array_equal(a.positions(), b.positions()) and np.array_equal(a.tension(), b.tension())
     a.close()
     b.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    # a run resumed from a checkpoint continues with the same bits as the uninterrupted one
+    xs, ys = _mixed([32, 64, 32, 48, 64, 32], 12, spacing=2.5)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, corr_tol=0.0, flow_kind=1, flow_p=(0.5, 0, 0, 0), near_field=True,
+              use_graph=True)
+    a = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    a.step(3)
+    ck = a.checkpoint()
+    a.step(4)
+    b = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    b.step(1)  # a different state, replaced by the restore
+    b.restore(ck)
+    b.step(4)
+    assert np.array_equal(a.positions(), b.positions()) and np.array_equal(a.tension(), b.tension())
+    ca, cb = a.counters(), b.counters()
+    assert ca["steps"] == cb["steps"] == 7 and ca["corrections"] == cb["corrections"] > 0
+    # a checkpoint of other point counts or parameters is refused
+    c = binding.Suspension(csr(xs[:5], ys[:5]), offsets(xs[:5]), **kw)
+    with pytest.raises(binding.VsError):
+        c.restore(ck)
+    d = binding.Suspension(csr(xs, ys), offsets(xs), **dict(kw, dt=2e-3))
+    with pytest.raises(binding.VsError):
+        d.restore(ck)
+    with pytest.raises(binding.VsError):
+        b.restore(ck[:100])
+    for s in (a, b, c, d):
+        s.close()
