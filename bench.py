@@ -328,11 +328,9 @@ def run_gpu(args):
     s.sync()
     c = s.counters()
     launches = c["launches"] - launches0
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * wl.M * args.steps / (ms * 1e-3)
+    # whole job: every rank's vesicle-steps over the slowest rank's time (replicas: weak scaling)
+    from paper_2606_25569_b300.shard import job_throughput
+    value, ms = job_throughput(wl.M * args.steps, ms)
 
     # per-kernel CUDA-event breakdown over the same number of steps
     s.profile(True)
