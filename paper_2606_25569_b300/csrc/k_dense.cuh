@@ -292,6 +292,17 @@ constexpr int GT = 64;   // output tile
 constexpr int GK = 16;   // k tile
 
 // C = A B per vesicle; grid (ceil(n/64), ceil(m/64), M), 256 threads, 4x4 outputs per thread.
+// Whether k_bgemm fetches the next K chunk's operands during the current chunk's products (measured per
+// operator: it helps where the operand functors are cheap; OpT32's costlier functors run faster without).
+template <class Op>
+struct GemmPrefetch {
+  static constexpr bool value = true;
+};
+template <>
+struct GemmPrefetch<OpT32> {
+  static constexpr bool value = false;
+};
+
 template <class Op>
 __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ active) {
   using T = typename Op::T;
@@ -311,19 +322,54 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = tid; e < GK * GT; e += 256) {
-      // A is row-major in its k index: let consecutive threads walk k
-      const int kk = e % GK, rr = e / GK;
-      const int gi = r0 + rr, gk = k0 + kk;
-      As[kk][rr] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
+  // the next K chunk's operands are fetched into registers while the current one is multiplied
+  constexpr int PER = GK * GT / 256;
+  T ra[PER], rb[PER];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      {  // A is row-major in its k index: let consecutive threads walk k
+        const int kk = e % GK, rr = e / GK;
+        const int gi = r0 + rr, gk = k0 + kk;
+        ra[q] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
+      }
+      {
+        const int kk = e / GT, cc = e % GT;
+        const int gj = c0 + cc, gk = k0 + kk;
+        rb[q] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
+      }
     }
-    for (int e = tid; e < GK * GT; e += 256) {
-      const int kk = e / GT, cc = e % GT;
-      const int gj = c0 + cc, gk = k0 + kk;
-      Bs[kk][cc] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      As[e % GK][e / GK] = ra[q];
+      Bs[e / GT][e % GT] = rb[q];
+    }
+  };
+  constexpr bool PF = GemmPrefetch<Op>::value;
+  if constexpr (PF) fetch(0);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    if constexpr (PF) {
+      stash();
+    } else {  // operands formed straight into shared memory
+      for (int e = tid; e < GK * GT; e += 256) {
+        const int kk = e % GK, rr = e / GK;
+        const int gi = r0 + rr, gk = k0 + kk;
+        As[kk][rr] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
+      }
+      for (int e = tid; e < GK * GT; e += 256) {
+        const int kk = e / GT, cc = e % GT;
+        const int gj = c0 + cc, gk = k0 + kk;
+        Bs[kk][cc] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
+      }
     }
     __syncthreads();
+    if constexpr (PF) {
+      if (k0 + GK < K) fetch(k0 + GK);
+    }
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
       T av[4], bv[4];
