@@ -47,7 +47,7 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float p) {
 template <bool MIN>
 __device__ __forceinline__ void ff_sum(const float4* sh, int j0, int j1, float qx, float qy, float& ax, float& ay,
                                        float& lx, float& ly, float& mn) {
-#pragma unroll 4
+#pragma unroll 16
   for (int j = j0; j < j1; ++j) {
     const float4 s = sh[j];
     const float rx = qx - s.x, ry = qy - s.y;
