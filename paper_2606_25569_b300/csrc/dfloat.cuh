@@ -84,4 +84,30 @@ __device__ __forceinline__ float2 circ_df(const float2* d, const float2* v, int 
   return tot;
 }
 
+constexpr int LOG_TAB = 512;
+
+// Natural logarithm of a double-float x = (hi, lo) > 0 with a normal hi, table-driven (Tang, ACM TOMS 16,
+// 1990): x = 2^e (m_hi + m_lo) with m_hi in [1, 2) the scaled hi, c = 1 + (k + 1/2)/LOG_TAB for k the top
+// 9 fraction bits of m_hi, log x = e ln 2 + log c + log1p(f) with f = (m - c)/c in double-float
+// (|f| <= 2^-10) and log1p(f) = f - f^2/2 + f^3 (1/3 - f/4 + f^2/5): the cubic part is below 2^-30, so
+// plain FP32 carries it, and the next term is below 2^-62. ltd[k] = (log c hi, log c lo, 1/c hi,
+// 1/c lo) is built on the host. About 47 significant bits.
+__device__ __forceinline__ float2 log_df(float2 x, const float4* ltd) {
+  const unsigned b = __float_as_uint(x.x);
+  const int e = (int)((b >> 23) & 255u) - 127;
+  const int k = (int)((b >> 14) & (unsigned)(LOG_TAB - 1));
+  const float mh = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+  const float ml = ldexpf(x.y, -e);
+  const float c = 1.0f + (k + 0.5f) / LOG_TAB;  // exact: 10 fraction bits
+  const float4 t = ltd[k];
+  const float2 f = df_mul(two_sum(__fsub_rn(mh, c), ml), make_float2(t.z, t.w));  // mh - c is exact
+  const float fx = f.x;
+  const float cubic = fx * fx * fx * fmaf(fx, fmaf(fx, 0.2f, -0.25f), 1.0f / 3.0f);
+  const float2 f2 = df_mul(f, f);
+  const float2 l1 = df_add(f, two_sum(-0.5f * f2.x, fmaf(-0.5f, f2.y, cubic)));
+  constexpr float LN2_H = (float)0.69314718055994530942, LN2_L = (float)(0.69314718055994530942 - (double)LN2_H);
+  const float2 eln2 = df_mul(make_float2((float)e, 0.f), make_float2(LN2_H, LN2_L));
+  return df_add(df_add(eln2, make_float2(t.x, t.y)), l1);
+}
+
 }  // namespace vs

@@ -39,6 +39,8 @@ struct GeomOut {
   float4* sdf;     // 3 per point, double-float pairs for the self matrix (may be null):
                    //   (x - x_0, y - y_0), (|X_alpha| / (4 pi mu), -R(0)/2 - (2 pi/N) log|X_alpha|), (x_s, y_s)
   const int* active;  // null, or only vesicles with active[v] != 0 are processed
+  const float4* logtab;  // the double-float logarithm's table (log_df) for the self-matrix diagonal, or null
+                         // (then an FP64 logarithm)
 };
 
 // Force/source outputs (only written when `f` is non-null). With f_in non-null the density is
@@ -116,7 +118,9 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     g.by[o + i] = by;
     if (g.g32) g.g32[o + i] = make_float4((float)(1.0 / sa), (float)tx, (float)ty, 0.f);
     if (g.sdf) {  // once per point here instead of once per tile in the self matrix (FP64 is slow)
-      const float2 c = df_of(sa / (4.0 * VS_PI * mu)), lpd = df_of(-0.5 * T[N] - dal * log(sa));
+      const float2 c = df_of(sa / (4.0 * VS_PI * mu));
+      const float2 lpd = g.logtab ? df_add(df_of(-0.5 * T[N]), df_mul(df_of(-dal), log_df(df_of(sa), g.logtab)))
+                                  : df_of(-0.5 * T[N] - dal * log(sa));
       const float2 a = df_of(tx), b = df_of(ty);
       float4* q = g.sdf + 3 * (o + i);
       q[0] = make_float4(px.x, px.y, py.x, py.y);

@@ -477,8 +477,9 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
   return VS_OK;
 }
 
-inline GeomOut geom_active(GeomOut g, const int* active) {
+inline GeomOut geom_active(GeomOut g, const int* active, const float4* logtab) {
   g.active = active;
+  g.logtab = logtab;
   return g;
 }
 
@@ -487,7 +488,7 @@ vs_status geometry(vs_suspension* h, const double* xy, bool with_force, const in
   if (with_force)
     fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
   VS_LAUNCH(h, "k_geometry", k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
-                                             flow_dev(h->flow), geom_active(h->B.geom(), active), fo, nullptr));
+                                             flow_dev(h->flow), geom_active(h->B.geom(), active, h->D.logtab), fo, nullptr));
   VS_CK(h, cudaGetLastError(), "geometry");
   return VS_OK;
 }
