@@ -60,6 +60,27 @@ constexpr int MV_ROWS = 4;
 template <int COLS>
 __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols, const float* x, float* y,
                                  float alpha, bool add) {
+  if ((cols & 3) == 0 && ((reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(x)) & 15) == 0) {
+    // one row per thread, the row read as float4 and x broadcast from shared memory: no cross-lane reduction
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      const float4* Mr = reinterpret_cast<const float4*>(M + (int64_t)r * cols);
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < cols / 4; ++k) {
+        const float4 m = __ldg(Mr + k);
+        const float4 xv = x4[k];
+        a0 = fmaf(m.x, xv.x, a0);
+        a1 = fmaf(m.y, xv.y, a1);
+        a0 = fmaf(m.z, xv.z, a0);
+        a1 = fmaf(m.w, xv.w, a1);
+      }
+      const float a = a0 + a1;
+      y[r] = add ? y[r] + alpha * a : alpha * a;
+    }
+    __syncthreads();
+    return;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r0 = MV_ROWS * wid; r0 < rows; r0 += MV_ROWS * nw) {
     float2 mv[COLS / 64][MV_ROWS];
