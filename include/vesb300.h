@@ -73,6 +73,11 @@ typedef struct {
  * split into three BF16 parts, FP32 accumulation) instead of with FP32 FMAs; both give FP32-quality
  * preconditioners and the same FP64-accurate results. At N <= 128 the FMA kernels are faster. */
 #define VS_FLAG_TC_GEMM 8ull
+/* Far field through vesicle multipole expansions (order 12 about each vesicle's centre) for source
+ * vesicles farther than three reach radii from the target, point sums for the rest (near test and lists
+ * unchanged): an approximation of the all-pairs sum (the paper names FMM as the route to O(M) cost) whose
+ * truncation error is below 3^-13 of a vesicle's density scale; FP32 with compensated accumulation. */
+#define VS_FLAG_FARFIELD_MULTIPOLE 16ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */
@@ -217,7 +222,8 @@ void vs_destroy(vs_suspension* s);
  *   G = (1/4 pi mu)(-log|r| I + r r^T / |r|^2).
  * A plan holds the layout and its device buffers.
  *  offsets     host, M+1 int64 as in vs_create.
- *  precision   0: compensated FP32 (vesicle-relative coordinates), 1: FP64.
+ *  precision   0: compensated FP32 (vesicle-relative coordinates), 1: FP64, 2: FP32 with vesicle
+ *              multipole expansions for far source vesicles (VS_FLAG_FARFIELD_MULTIPOLE).
  * vs_farfield_eval takes DEVICE pointers in CSR blocks: xy (2P), f (2P); writes u (2P, device,
  * overwritten) on the plan's stream. Asynchronous.
  */

@@ -174,4 +174,167 @@ __global__ void __launch_bounds__(FF_THREADS) k_farfield_f64(FarFieldArgs a, con
   if (a.near_mask) a.near_cnt[t] = ncnt < MAX_NEAR ? ncnt : MAX_NEAR;
 }
 
+// ---- Vesicle multipole far field (FP32; opt-in). A source vesicle far from the target (|q| > 3 R_v,
+// q = target - c_v, R_v the reach radius) contributes through a truncated expansion of its Stokeslet sum
+// about its centre instead of its N point terms; nearer vesicles are summed point by point exactly as in
+// k_farfield_f32 (near-pair test and lists included). With s_j = X_vj - c_v, g_j as above, complex numbers
+// for 2-vectors and zeta = 1/q, the pair term -g log|w| + (w . g) w / |w|^2, w = q - s_j, equals
+// -g log|w| + g/2 + (w / conj(w)) conj(g)/2; expanding log(1 - s/q) and 1/conj(w) in powers of s/q gives
+//   u = -A_0 log|q| + A_0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2,
+//   T1 = sum_{k=1..P} (A_k/k) zeta^k,  S_A = sum_{k=1..P+1} A_{k-1} zeta^k,
+//   E  = sum_{k=1..P+1} (conj(B_k)/k [k <= P] - conj(D_{k-1})) zeta^k,
+// A_k = sum_j g_j s_j^k, B_k = sum_j g_j conj(s_j)^k, D_k = sum_j conj(g_j) s_j conj(s_j)^k (moments in FP64,
+// stored in FP32). The truncation error is below (R_v/|q|)^(P+1) ~ 1/3^(P+1) of the vesicle's density scale.
+constexpr int FF_MP_P = 12;            // expansion order
+constexpr float FF_MP_THETA2 = 9.0f;   // far when |q|^2 > 9 R_v^2
+
+// Moments of every vesicle: one CTA per vesicle, one thread per point; each thread forms s^k (k = 0..P+1)
+// by repeated products and its terms of A_k, B_k, D_k in FP64, and the block sums them (warp shuffles,
+// then the warps' partial sums in fixed order). coef[v][k - 1], k = 1..P+1: (A_k/k [k <= P], A_{k-1}) and
+// (E_k, 0, 0) as float4 pairs; a0[v] = A_0.
+template <int P>
+__global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__ voff, const float4* __restrict__ src,
+                                                     float4* __restrict__ coef, float2* __restrict__ a0) {
+  constexpr int K = P + 2;
+  __shared__ double part[NMAX / 32][3 * K][2];
+  __shared__ double2 sA[K], sB[K], sD[K];
+  const int v = blockIdx.x, j = threadIdx.x, lane = j & 31, w = j >> 5;
+  const int64_t o = voff[v], n = voff[v + 1] - o;
+  double sx = 0.0, sy = 0.0, gx = 0.0, gy = 0.0;
+  if (j < n) {
+    const float4 q = src[o + j];
+    sx = q.x; sy = q.y; gx = q.z; gy = q.w;
+  }
+  double pr = 1.0, pi = 0.0;  // s^k
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t[6];
+    t[0] = gx * pr - gy * pi;  // g s^k
+    t[1] = gx * pi + gy * pr;
+    t[2] = gx * pr + gy * pi;  // g conj(s)^k = g conj(s^k)
+    t[3] = gy * pr - gx * pi;
+    const double wr = sx * pr + sy * pi, wi = sy * pr - sx * pi;  // s conj(s^k)
+    t[4] = gx * wr + gy * wi;  // conj(g) s conj(s^k)
+    t[5] = gx * wi - gy * wr;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      double x = t[e];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane == 0) part[w][(e >> 1) * K + k][e & 1] = x;
+    }
+    const double nr = pr * sx - pi * sy;
+    pi = pr * sy + pi * sx;
+    pr = nr;
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int e = j; e < 3 * K; e += blockDim.x) {
+    double x = 0.0, y = 0.0;
+    for (int q = 0; q < nw; ++q) { x += part[q][e][0]; y += part[q][e][1]; }
+    const int set = e / K, k = e - set * K;
+    (set == 0 ? sA : set == 1 ? sB : sD)[k] = make_double2(x, y);
+  }
+  __syncthreads();
+  const int k = j;
+  if (k >= 1 && k <= P + 1) {
+    const double ik = 1.0 / k;
+    const double2 c1 = (k <= P) ? make_double2(sA[k].x * ik, sA[k].y * ik) : make_double2(0.0, 0.0);
+    const double2 cA = sA[k - 1];
+    double er = -sD[k - 1].x, ei = sD[k - 1].y;  // -conj(D_{k-1})
+    if (k <= P) {
+      er += sB[k].x * ik;   // conj(B_k)/k
+      ei -= sB[k].y * ik;
+    }
+    float4* c = coef + ((int64_t)v * (P + 1) + (k - 1)) * 2;
+    c[0] = make_float4((float)c1.x, (float)c1.y, (float)cA.x, (float)cA.y);
+    c[1] = make_float4((float)er, (float)ei, 0.f, 0.f);
+  }
+  if (k == 0) a0[v] = make_float2((float)sA[0].x, (float)sA[0].y);
+}
+
+// One thread per target over every source vesicle in ascending order: the expansion for far vesicles,
+// the point sum (k_farfield_f32's, with the near test) for the rest; per-vesicle results added with
+// Neumaier compensation.
+template <int THREADS, int P>
+__global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const float4* __restrict__ src,
+                                                         const float4* __restrict__ centre32,
+                                                         const float2* __restrict__ h2,
+                                                         const float4* __restrict__ coef,
+                                                         const float2* __restrict__ a0) {
+  const int64_t t = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+  if (t >= a.P) return;
+  const int tv = a.owner[t];
+  const float4 ts = src[t];
+  const float4 tc = centre32[tv];
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+  int ncnt = 0;
+  const float hl2 = -0.34657359027997264f;  // -ln(2)/2
+  for (int sv = 0; sv < a.M; ++sv) {
+    if (sv == tv) continue;
+    const float4 sc = centre32[sv];
+    const float qx = ((tc.x - sc.x) + (tc.z - sc.z)) + ts.x;
+    const float qy = ((tc.y - sc.y) + (tc.w - sc.w)) + ts.y;
+    const float2 nr = h2[sv];
+    const float d2 = fmaf(qx, qx, qy * qy);
+    float ux, uy;
+    if (d2 > FF_MP_THETA2 * nr.y) {
+      const float inv = fast_rcp(d2);
+      const float zr = qx * inv, zi = -qy * inv;  // zeta = 1/q
+      const float4* c = coef + (int64_t)sv * (P + 1) * 2;
+      float t1r = 0.f, t1i = 0.f, sar = 0.f, sai = 0.f, er = 0.f, ei = 0.f;
+#pragma unroll
+      for (int k = P; k >= 0; --k) {  // Horner from the top coefficient (index k = power - 1)
+        const float4 c0 = __ldg(c + 2 * k), c1 = __ldg(c + 2 * k + 1);
+        float r;
+        r = fmaf(t1r, zr, fmaf(-t1i, zi, c0.x)); t1i = fmaf(t1r, zi, fmaf(t1i, zr, c0.y)); t1r = r;
+        r = fmaf(sar, zr, fmaf(-sai, zi, c0.z)); sai = fmaf(sar, zi, fmaf(sai, zr, c0.w)); sar = r;
+        r = fmaf(er, zr, fmaf(-ei, zi, c1.x)); ei = fmaf(er, zi, fmaf(ei, zr, c1.y)); er = r;
+      }
+      // the series start at zeta^1: one more factor zeta
+      float r;
+      r = t1r * zr - t1i * zi; t1i = t1r * zi + t1i * zr; t1r = r;
+      r = sar * zr - sai * zi; sai = sar * zi + sai * zr; sar = r;
+      r = er * zr - ei * zi; ei = er * zi + ei * zr; er = r;
+      const float2 A0 = a0[sv];
+      const float lq = hl2 * fast_lg2(d2);  // -log|q|
+      // u = -A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
+      ux = fmaf(A0.x, lq + 0.5f, 0.5f * (t1r + er + (qx * sar + qy * sai)));
+      uy = fmaf(A0.y, lq + 0.5f, 0.5f * (t1i - ei + (qy * sar - qx * sai)));
+    } else {
+      const bool test = a.near_mask && d2 <= nr.y;
+      float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
+      const int64_t j0 = a.voff[sv], j1 = a.voff[sv + 1];
+      for (int64_t j = j0; j < j1; ++j) {
+        const float4 s = __ldg(src + j);
+        const float rx = qx - s.x, ry = qy - s.y;
+        const float r2 = fmaf(rx, rx, ry * ry);
+        if (test) mn = fminf(mn, r2);
+        const float lg = fast_lg2(r2);
+        const float iv = fast_rcp(r2);
+        lx = fmaf(lg, s.z, lx);
+        ly = fmaf(lg, s.w, ly);
+        const float q = fmaf(rx, s.z, ry * s.w) * iv;
+        ax = fmaf(q, rx, ax);
+        ay = fmaf(q, ry, ay);
+      }
+      if (test && mn <= nr.x) {
+        if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
+        else atomicOr(a.err, ERR_NEAR_OVERFLOW);
+        ++ncnt;
+        continue;
+      }
+      ux = fmaf(hl2, lx, ax);
+      uy = fmaf(hl2, ly, ay);
+    }
+    neumaier_add(sx, cx, ux);
+    neumaier_add(sy, cy, uy);
+  }
+  const int64_t to = a.voff[tv];
+  const int tN = (int)(a.voff[tv + 1] - to);
+  a.u[2 * to + (t - to)] += (double)sx + (double)cx;
+  a.u[2 * to + tN + (t - to)] += (double)sy + (double)cy;
+  if (a.near_mask) a.near_cnt[t] = ncnt < MAX_NEAR ? ncnt : MAX_NEAR;
+}
+
 }  // namespace vs

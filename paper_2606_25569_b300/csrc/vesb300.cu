@@ -201,6 +201,8 @@ struct SourceBufs {
   double *area = nullptr, *length = nullptr;
   float4* g32 = nullptr;
   float4* sdf = nullptr;
+  float4* mpcoef = nullptr;  // multipole far field: per vesicle (FF_MP_P + 1) x 2 float4 coefficients
+  float2* mpa0 = nullptr;    // and its total density A_0
   cudaError_t alloc(int64_t P, int M) {
     cudaError_t e;
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -211,6 +213,7 @@ struct SourceBufs {
     VS_TRY(dalloc(&bx, P)); VS_TRY(dalloc(&by, P));
     VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M)); VS_TRY(dalloc(&g32, P));
     VS_TRY(dalloc(&sdf, 3 * P));
+    VS_TRY(dalloc(&mpcoef, (int64_t)M * (FF_MP_P + 1) * 2)); VS_TRY(dalloc(&mpa0, M));
 #undef VS_TRY
     return cudaSuccess;
   }
@@ -218,6 +221,7 @@ struct SourceBufs {
     cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
     cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32); cudaFree(sdf);
+    cudaFree(mpcoef); cudaFree(mpa0);
     *this = SourceBufs{};
   }
   GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32, sdf}; }
@@ -521,6 +525,9 @@ void launch_far_field_f32(const vs_suspension* h, int var, FarFieldArgs a) {
   }
 }
 
+// k_ff_moments: one thread per point of the largest vesicle, whole warps
+inline int ff_moment_threads(const Layout& L) { return (L.nmax + 31) / 32 * 32; }
+
 FarFieldArgs far_field_args(vs_suspension* h) {
   const Layout& L = h->L;
   return FarFieldArgs{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1,
@@ -534,6 +541,13 @@ vs_status far_field(vs_suspension* h) {
   if (h->p.flags & VS_FLAG_FARFIELD_FP64) {
     const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
     VS_LAUNCH(h, "k_farfield_f64", k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N));
+  } else if (h->p.flags & VS_FLAG_FARFIELD_MULTIPOLE) {
+    VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef,
+                                                                                   h->B.mpa0));
+    const int grid = (int)((L.P + 127) / 128);
+    VS_LAUNCH(h, "k_farfield_mp", (k_farfield_mp<128, FF_MP_P><<<grid, 128, 0, h->stream>>>(a, h->B.src, h->B.centre32,
+                                                                                          h->B.h2, h->B.mpcoef,
+                                                                                          h->B.mpa0)));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -553,7 +567,7 @@ std::map<std::string, int>& tune_cache() {
 
 vs_status tune_far_field(vs_suspension* h) {
   const Layout& L = h->L;
-  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE))) return VS_OK;
+  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE))) return VS_OK;
   int dev = 0;
   VS_CK(h, cudaGetDevice(&dev), "autotune");
   cudaDeviceProp prop;
@@ -1265,7 +1279,7 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
     delete h;
     return s;
   };
-  if (!(mu > 0) || (precision != 0 && precision != 1)) { h->msg = "mu must be > 0, precision 0 or 1"; return fail(VS_ERR_INVALID_ARG); }
+  if (!(mu > 0) || precision < 0 || precision > 2) { h->msg = "mu must be > 0, precision 0, 1 or 2"; return fail(VS_ERR_INVALID_ARG); }
   if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
   h->mu = mu;
   h->near_mask = near_mask ? 1 : 0;
@@ -1294,10 +1308,15 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
   FarFieldArgs a{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1, h->near_mask, u,
                  h->B.near_cnt, h->B.near_v, h->err};
   const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
-  if (h->precision == 1)
+  if (h->precision == 1) {
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
-  else
+  } else if (h->precision == 2) {
+    k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
+    k_farfield_mp<128, FF_MP_P><<<(int)((L.P + 127) / 128), 128, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2,
+                                                                                 h->B.mpcoef, h->B.mpa0);
+  } else {
     k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+  }
   VS_CK(h, cudaGetLastError(), "far field");
   return VS_OK;
 }

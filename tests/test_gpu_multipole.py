@@ -1,0 +1,82 @@
+"""GPU checks of the multipole far field (VS_FLAG_FARFIELD_MULTIPOLE / plan precision 2) against the FP64
+oracle's all-pairs sum and against the point-sum FP32 far field."""
+import numpy as np
+import pytest
+
+from oracle.farfield import far_field
+from oracle.flows import background
+from oracle.spectral import force
+from paper_2606_25569_b300 import binding
+from paper_2606_25569_b300.workloads import farfield_box, poiseuille_dense
+
+from .gpu_util import csr, split
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def test_multipole_far_field_2000x128_sampled_targets():
+    wl, fx, fy = farfield_box()
+    off = wl.offsets
+    got = {}
+    for prec in (0, 2):
+        plan = binding.FarFieldPlan(off, mu=1.0, near_mask=False, precision=prec)
+        u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+        plan.eval(_dev(wl.flat_xy()), _dev(csr(fx, fy)), u)
+        got[prec] = u.cpu().numpy()
+        plan.close()
+    rng = np.random.default_rng(21)
+    tgt = np.sort(rng.choice(off[-1], 256, replace=False))
+    ux, uy, _ = far_field(wl.xs, wl.ys, fx, fy, 1.0, near_mask=False, targets=tgt)
+    owner = np.repeat(np.arange(wl.M), wl.counts)
+    loc = tgt - off[owner[tgt]]
+    for prec in (0, 2):
+        gx = got[prec][2 * off[owner[tgt]] + loc]
+        gy = got[prec][2 * off[owner[tgt]] + wl.counts[owner[tgt]] + loc]
+        err = np.sqrt(np.sum((gx - ux) ** 2 + (gy - uy) ** 2) / np.sum(ux ** 2 + uy ** 2))
+        print("far field 2000x128 precision %d: relative L2 error %.3e" % (prec, err))
+        assert err <= 1e-5, (prec, err)
+
+
+def test_multipole_suspension_poiseuille_2000x64():
+    wl = poiseuille_dense(2000, 64, seed=5)
+    stream = torch.cuda.current_stream()
+    kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
+              near_field=True, stream=stream, use_graph=True)
+    g = binding.Suspension(wl.flat_xy(), wl.offsets, farfield_multipole=True, **kw)
+    d = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
+    counts = list(wl.counts)
+    off = wl.offsets
+    x0s, y0s = split(g.positions(), counts)
+    s0 = g.tension()
+    g.step(1)
+    d.step(1)
+    g.sync()
+    u_mp, u_pt = g.velocity(), d.velocity()
+    assert g.counters()["near_pairs"] == d.counters()["near_pairs"]
+    # against the oracle's all-pairs sum at sampled targets (same tolerance as the point-sum FP32 kernel)
+    fx, fy = [], []
+    for v in range(wl.M):
+        a, b = force(x0s[v], y0s[v], s0[off[v]:off[v + 1]], wl.kappa)
+        fx.append(a)
+        fy.append(b)
+    rng = np.random.default_rng(22)
+    tgt = np.sort(rng.choice(off[-1], 256, replace=False))
+    ux, uy, near = far_field(x0s, y0s, fx, fy, wl.mu, near_mask=True, targets=tgt)
+    assert not near
+    owner = np.repeat(np.arange(wl.M), wl.counts)
+    loc = tgt - off[owner[tgt]]
+    X, Y = np.concatenate(x0s), np.concatenate(y0s)
+    bx, by = background(wl.flow_kind, wl.flow_p, X[tgt], Y[tgt])
+    for name, u0 in (("multipole", u_mp), ("point sums", u_pt)):
+        gx = u0[2 * off[owner[tgt]] + loc] - bx
+        gy = u0[2 * off[owner[tgt]] + wl.counts[owner[tgt]] + loc] - by
+        err = np.sqrt(np.sum((gx - ux) ** 2 + (gy - uy) ** 2) / np.sum(ux ** 2 + uy ** 2))
+        print("poiseuille 2000x64 far-field velocity, %s: relative L2 error %.3e" % (name, err))
+        assert err <= 2e-5, (name, err)
+    g.close()
+    d.close()
