@@ -255,81 +255,100 @@ __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__
 
 // One thread per target over every source vesicle in ascending order: the expansion for far vesicles,
 // the point sum (k_farfield_f32's, with the near test) for the rest; per-vesicle results added with
-// Neumaier compensation.
+// Neumaier compensation. The vesicles' centres, reach and expansion coefficients are staged through shared
+// memory FF_MP_CHUNK vesicles at a time.
+constexpr int FF_MP_CHUNK = 32;
 template <int THREADS, int P>
 __global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const float4* __restrict__ src,
                                                          const float4* __restrict__ centre32,
                                                          const float2* __restrict__ h2,
                                                          const float4* __restrict__ coef,
                                                          const float2* __restrict__ a0) {
+  constexpr int NC = 2 * (P + 1);  // coefficient float4s per vesicle
+  __shared__ float4 scoef[FF_MP_CHUNK * NC];
+  __shared__ float4 scen[FF_MP_CHUNK];
+  __shared__ float4 sh2a0[FF_MP_CHUNK];  // (h^2, reach^2, A0.x, A0.y)
   const int64_t t = (int64_t)blockIdx.x * THREADS + threadIdx.x;
-  if (t >= a.P) return;
-  const int tv = a.owner[t];
-  const float4 ts = src[t];
-  const float4 tc = centre32[tv];
+  const bool valid = t < a.P;
+  const int tv = valid ? a.owner[t] : -1;
+  const float4 ts = valid ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 tc = valid ? centre32[tv] : make_float4(0.f, 0.f, 0.f, 0.f);
   float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
   int ncnt = 0;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2
-  for (int sv = 0; sv < a.M; ++sv) {
-    if (sv == tv) continue;
-    const float4 sc = centre32[sv];
-    const float qx = ((tc.x - sc.x) + (tc.z - sc.z)) + ts.x;
-    const float qy = ((tc.y - sc.y) + (tc.w - sc.w)) + ts.y;
-    const float2 nr = h2[sv];
-    const float d2 = fmaf(qx, qx, qy * qy);
-    float ux, uy;
-    if (d2 > FF_MP_THETA2 * nr.y) {
-      const float inv = fast_rcp(d2);
-      const float zr = qx * inv, zi = -qy * inv;  // zeta = 1/q
-      const float4* c = coef + (int64_t)sv * (P + 1) * 2;
-      float t1r = 0.f, t1i = 0.f, sar = 0.f, sai = 0.f, er = 0.f, ei = 0.f;
-#pragma unroll
-      for (int k = P; k >= 0; --k) {  // Horner from the top coefficient (index k = power - 1)
-        const float4 c0 = __ldg(c + 2 * k), c1 = __ldg(c + 2 * k + 1);
-        float r;
-        r = fmaf(t1r, zr, fmaf(-t1i, zi, c0.x)); t1i = fmaf(t1r, zi, fmaf(t1i, zr, c0.y)); t1r = r;
-        r = fmaf(sar, zr, fmaf(-sai, zi, c0.z)); sai = fmaf(sar, zi, fmaf(sai, zr, c0.w)); sar = r;
-        r = fmaf(er, zr, fmaf(-ei, zi, c1.x)); ei = fmaf(er, zi, fmaf(ei, zr, c1.y)); er = r;
-      }
-      // the series start at zeta^1: one more factor zeta
-      float r;
-      r = t1r * zr - t1i * zi; t1i = t1r * zi + t1i * zr; t1r = r;
-      r = sar * zr - sai * zi; sai = sar * zi + sai * zr; sar = r;
-      r = er * zr - ei * zi; ei = er * zi + ei * zr; er = r;
-      const float2 A0 = a0[sv];
-      const float lq = hl2 * fast_lg2(d2);  // -log|q|
-      // u = -A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
-      ux = fmaf(A0.x, lq + 0.5f, 0.5f * (t1r + er + (qx * sar + qy * sai)));
-      uy = fmaf(A0.y, lq + 0.5f, 0.5f * (t1i - ei + (qy * sar - qx * sai)));
-    } else {
-      const bool test = a.near_mask && d2 <= nr.y;
-      float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
-      const int64_t j0 = a.voff[sv], j1 = a.voff[sv + 1];
-      for (int64_t j = j0; j < j1; ++j) {
-        const float4 s = __ldg(src + j);
-        const float rx = qx - s.x, ry = qy - s.y;
-        const float r2 = fmaf(rx, rx, ry * ry);
-        if (test) mn = fminf(mn, r2);
-        const float lg = fast_lg2(r2);
-        const float iv = fast_rcp(r2);
-        lx = fmaf(lg, s.z, lx);
-        ly = fmaf(lg, s.w, ly);
-        const float q = fmaf(rx, s.z, ry * s.w) * iv;
-        ax = fmaf(q, rx, ax);
-        ay = fmaf(q, ry, ay);
-      }
-      if (test && mn <= nr.x) {
-        if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
-        else atomicOr(a.err, ERR_NEAR_OVERFLOW);
-        ++ncnt;
-        continue;
-      }
-      ux = fmaf(hl2, lx, ax);
-      uy = fmaf(hl2, ly, ay);
+  for (int v0 = 0; v0 < a.M; v0 += FF_MP_CHUNK) {
+    const int nv = min(FF_MP_CHUNK, a.M - v0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nv * NC; e += THREADS) scoef[e] = coef[(int64_t)v0 * NC + e];
+    for (int e = threadIdx.x; e < nv; e += THREADS) {
+      scen[e] = centre32[v0 + e];
+      const float2 hh = h2[v0 + e], A = a0[v0 + e];
+      sh2a0[e] = make_float4(hh.x, hh.y, A.x, A.y);
     }
-    neumaier_add(sx, cx, ux);
-    neumaier_add(sy, cy, uy);
+    __syncthreads();
+    if (!valid) continue;
+    for (int l = 0; l < nv; ++l) {
+      const int sv = v0 + l;
+      if (sv == tv) continue;
+      const float4 sc = scen[l];
+      const float qx = ((tc.x - sc.x) + (tc.z - sc.z)) + ts.x;
+      const float qy = ((tc.y - sc.y) + (tc.w - sc.w)) + ts.y;
+      const float4 na = sh2a0[l];
+      const float d2 = fmaf(qx, qx, qy * qy);
+      float ux, uy;
+      if (d2 > FF_MP_THETA2 * na.y) {
+        const float inv = fast_rcp(d2);
+        const float zr = qx * inv, zi = -qy * inv;  // zeta = 1/q
+        const float4* c = scoef + l * NC;
+        float t1r = 0.f, t1i = 0.f, sar = 0.f, sai = 0.f, er = 0.f, ei = 0.f;
+#pragma unroll
+        for (int k = P; k >= 0; --k) {  // Horner from the top coefficient (index k = power - 1)
+          const float4 c0 = c[2 * k], c1 = c[2 * k + 1];
+          float r;
+          r = fmaf(t1r, zr, fmaf(-t1i, zi, c0.x)); t1i = fmaf(t1r, zi, fmaf(t1i, zr, c0.y)); t1r = r;
+          r = fmaf(sar, zr, fmaf(-sai, zi, c0.z)); sai = fmaf(sar, zi, fmaf(sai, zr, c0.w)); sar = r;
+          r = fmaf(er, zr, fmaf(-ei, zi, c1.x)); ei = fmaf(er, zi, fmaf(ei, zr, c1.y)); er = r;
+        }
+        // the series start at zeta^1: one more factor zeta
+        float r;
+        r = t1r * zr - t1i * zi; t1i = t1r * zi + t1i * zr; t1r = r;
+        r = sar * zr - sai * zi; sai = sar * zi + sai * zr; sar = r;
+        r = er * zr - ei * zi; ei = er * zi + ei * zr; er = r;
+        const float lq = hl2 * fast_lg2(d2);  // -log|q|
+        // u = -A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
+        ux = fmaf(na.z, lq + 0.5f, 0.5f * (t1r + er + (qx * sar + qy * sai)));
+        uy = fmaf(na.w, lq + 0.5f, 0.5f * (t1i - ei + (qy * sar - qx * sai)));
+      } else {
+        const bool test = a.near_mask && d2 <= na.y;
+        float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
+        const int64_t j0 = a.voff[sv], j1 = a.voff[sv + 1];
+        for (int64_t j = j0; j < j1; ++j) {
+          const float4 s = __ldg(src + j);
+          const float rx = qx - s.x, ry = qy - s.y;
+          const float r2 = fmaf(rx, rx, ry * ry);
+          if (test) mn = fminf(mn, r2);
+          const float lg = fast_lg2(r2);
+          const float iv = fast_rcp(r2);
+          lx = fmaf(lg, s.z, lx);
+          ly = fmaf(lg, s.w, ly);
+          const float q = fmaf(rx, s.z, ry * s.w) * iv;
+          ax = fmaf(q, rx, ax);
+          ay = fmaf(q, ry, ay);
+        }
+        if (test && mn <= na.x) {
+          if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
+          else atomicOr(a.err, ERR_NEAR_OVERFLOW);
+          ++ncnt;
+          continue;
+        }
+        ux = fmaf(hl2, lx, ax);
+        uy = fmaf(hl2, ly, ay);
+      }
+      neumaier_add(sx, cx, ux);
+      neumaier_add(sy, cy, uy);
+    }
   }
+  if (!valid) return;
   const int64_t to = a.voff[tv];
   const int tN = (int)(a.voff[tv + 1] - to);
   a.u[2 * to + (t - to)] += (double)sx + (double)cx;
