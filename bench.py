@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-multipole", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
@@ -221,6 +222,41 @@ def run_reference(args):
                                        "against all sources, extrapolated to the full step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def multipole_arm(wl, args, stream):
+    """The plain step with the vesicle-multipole far field (VS_FLAG_FARFIELD_MULTIPOLE): throughput timed
+    with CUDA events, and its far-field velocity at the first step against the all-pairs point sums of the
+    same state (relative L2 over every point)."""
+    import torch
+    from paper_2606_25569_b300 import binding
+    kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
+              near_field=True, stream=stream, use_graph=True)
+    m = binding.Suspension(wl.flat_xy(), wl.offsets, farfield_multipole=True, **kw)
+    d = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
+    m.step(1)
+    d.step(1)
+    um, ud = m.velocity(), d.velocity()
+    diff = float(np.linalg.norm(um - ud) / np.linalg.norm(ud))
+    d.close()
+    m.step(max(args.warmup, 3))
+    m.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    m.profile(True)
+    m.step(2)
+    prof = m.profile_read()
+    m.profile(False)
+    m.close()
+    ff = sum(v[0] for k, v in prof.items() if k in ("k_farfield_mp", "k_ff_moments")) / 2
+    return {"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "far_field_ms_per_step": ff,
+            "velocity_rel_l2_vs_point_sums": diff,
+            "method": "order-12 expansions about each vesicle's centre beyond three reach radii, point sums "
+                      "(with the near test) inside; an approximation of the all-pairs sum (not the headline)"}
 
 
 def hybrid_arm(wl, args, stream):
@@ -404,6 +440,9 @@ def run_gpu(args):
                "note": "per step: vs_set_state (positions + tension from pinned host), vs_step, "
                        "vs_get_positions + vs_get_tension to pinned host; wall clock"}
 
+    multipole = None
+    if rank == 0 and not args.no_multipole:
+        multipole = multipole_arm(wl, args, stream)
     hybrid = None
     if rank == 0 and not args.no_hybrid:
         hybrid = hybrid_arm(wl, args, stream)
@@ -420,7 +459,7 @@ def run_gpu(args):
                                                                   "(autotuned at create)" % (fv[1], fv[2])}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
-                "steady_state": steady, "hybrid": hybrid,
+                "steady_state": steady, "hybrid": hybrid, "farfield_multipole": multipole,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()
