@@ -48,7 +48,6 @@ def parse():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-multipole", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
@@ -224,48 +223,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def multipole_arm(wl, args, stream):
-    """The plain step with the vesicle-multipole far field (VS_FLAG_FARFIELD_MULTIPOLE): throughput timed
-    with CUDA events, and its far-field velocity at the first step against the all-pairs point sums of the
-    same state (relative L2 over every point)."""
+def _time_steps(sus, n, stream):
     import torch
-    from paper_2606_25569_b300 import binding
-    kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
-              near_field=True, stream=stream, use_graph=True)
-    m = binding.Suspension(wl.flat_xy(), wl.offsets, farfield_multipole=True, **kw)
-    d = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
-    m.step(1)
-    d.step(1)
-    um, ud = m.velocity(), d.velocity()
-    diff = float(np.linalg.norm(um - ud) / np.linalg.norm(ud))
-    d.close()
-    m.step(max(args.warmup, 3))
-    m.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    m.step(args.steps)
+    sus.step(n)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    m.profile(True)
-    m.step(2)
-    prof = m.profile_read()
-    m.profile(False)
-    m.close()
-    ff = sum(v[0] for k, v in prof.items() if k in ("k_farfield_mp", "k_ff_moments")) / 2
-    return {"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "far_field_ms_per_step": ff,
-            "velocity_rel_l2_vs_point_sums": diff,
-            "method": "order-12 expansions about each vesicle's centre beyond three reach radii, point sums "
-                      "(with the near test) inside; an approximation of the all-pairs sum (not the headline)"}
+    return e0.elapsed_time(e1) / n
 
 
-def hybrid_arm(wl, args, stream):
-    """The hybrid step (learned relaxation on every other step, exact relaxation on the others and for
-    vesicles in near pairs; everything else exact) against the plain step from the same state: a network
-    trained on the GPU on exact relaxation pairs of a differently seeded suspension (64 snapshots 15 steps
-    apart), then both suspensions stepped args.hybrid_steps steps; the shape error is the mean over
-    vesicles of the centred relative error (App. B), and the hybrid throughput is timed with CUDA events."""
-    import torch
+def long_run_arms(wl, args, stream):
+    """Variants of the step against the plain step (all-pairs point sums) from the same state:
+    * hybrid: learned relaxation on every other step, exact relaxation on the others and for vesicles in
+      near pairs or within three spacings of another vesicle; the network trained on the GPU on exact
+      relaxation pairs of a differently seeded suspension (64 snapshots 15 steps apart);
+    * farfield_multipole: the plain step with the vesicle-multipole far field;
+    * hybrid_multipole: both.
+    Each reports its throughput (CUDA events) and the mean over vesicles of the centred relative shape
+    error (App. B) against the plain step after 10 .. args.hybrid_steps steps."""
     from paper_2606_25569_b300 import binding, train
     from paper_2606_25569_b300.workloads import poiseuille_dense
     kmax, exact_every, width = 16, 2, 1024
@@ -275,52 +251,78 @@ def hybrid_arm(wl, args, stream):
     r = train.train_relaxation(X, Y, hidden=(width, width, width), epochs=40, batch=1024, lr=1e-3, lr_min=1e-5,
                                stream=stream, serve_batch=wl.M)
     t_train = time.time() - t0 - t_data
+    net = {"dims": r["dims"], "train_samples": int(X.shape[0]), "train_steps": r["steps"],
+           "holdout_rel_err_mean": float(np.mean(r["holdout_err"])), "data_seconds": round(t_data, 1),
+           "train_seconds": round(t_train, 1), "input_filter_kmax": kmax, "features": "Fourier, normalised"}
     kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
               near_field=True, stream=stream, use_graph=True)
-    plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
-    hyb = binding.Suspension(wl.flat_xy(), wl.offsets, mode=1, exact_every=exact_every, **kw)
-    hyb.set_network(r["net"], r["scale"], kmax)
-    out = {"net": {"dims": r["dims"], "train_samples": int(X.shape[0]), "train_steps": r["steps"],
-                   "holdout_rel_err_mean": float(np.mean(r["holdout_err"])), "data_seconds": round(t_data, 1),
-                   "train_seconds": round(t_train, 1), "input_filter_kmax": kmax, "features": "Fourier, normalised"},
-           "exact_every": exact_every}
-    # throughput of the hybrid step (an even number of steps: learned and exact alternate)
-    hyb.step(4)
-    hyb.sync()
-    n = 2 * max(2, args.steps // 2)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    hyb.step(n)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / n
-    out.update({"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_timed": n})
-    hyb.close()
+    variants = {"hybrid": dict(mode=1, exact_every=exact_every),
+                "farfield_multipole": dict(farfield_multipole=True),
+                "hybrid_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True)}
+
+    def make(cfg):
+        sus = binding.Suspension(wl.flat_xy(), wl.offsets, **cfg, **kw)
+        if cfg.get("mode", 0) == 1:
+            sus.set_network(r["net"], r["scale"], kmax)
+        return sus
+
+    out = {}
+    for name, cfg in variants.items():
+        sus = make(cfg)
+        sus.step(4)
+        sus.sync()
+        n = 2 * max(2, args.steps // 2)  # even: learned and exact relaxation alternate
+        ms = _time_steps(sus, n, stream)
+        prof = {}
+        if "multipole" in name:
+            sus.profile(True)
+            sus.step(2)
+            prof = sus.profile_read()
+            sus.profile(False)
+        sus.close()
+        out[name] = {"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_timed": n}
+        if prof:
+            out[name]["far_field_ms_per_step"] = sum(v[0] for k, v in prof.items()
+                                                     if k in ("k_farfield_mp", "k_ff_moments")) / 2
+        if cfg.get("mode", 0) == 1:
+            out[name]["net"] = net
+            out[name]["exact_every"] = exact_every
+            out[name]["fallback"] = ("exact relaxation on every %d-th step and for vesicles within 3 spacings h of "
+                                     "another vesicle" % exact_every)
+        if cfg.get("farfield_multipole"):
+            out[name]["far_field"] = ("order-12 expansions about each vesicle's centre beyond three reach radii, "
+                                      "point sums (with the near test) inside: an approximation of the all-pairs sum")
     # shape error against the plain step from the same initial state
-    hyb = binding.Suspension(wl.flat_xy(), wl.offsets, mode=1, exact_every=exact_every, **kw)
-    hyb.set_network(r["net"], r["scale"], kmax)
-    done, errs, failed = 0, {}, None
+    plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
+    runs = {name: make(cfg) for name, cfg in variants.items()}
+    errs = {name: {} for name in variants}
+    failed = {}
+    done = 0
     for S in sorted({min(k, args.hybrid_steps) for k in (10, 100, 300, 500, 800, 1000, args.hybrid_steps)}):
-        try:
-            hyb.step(S - done)
-            hyb.sync()
-        except Exception as ex:  # a non-finite hybrid state ends the comparison
-            failed = "step %d..%d: %s" % (done, S, ex)
-            break
         plain.step(S - done)
         plain.sync()
+        ref = plain.positions()
+        for name, sus in runs.items():
+            if name in failed:
+                continue
+            try:
+                sus.step(S - done)
+                sus.sync()
+            except Exception as ex:  # a non-finite state ends that comparison
+                failed[name] = "step %d..%d: %s" % (done, S, ex)
+                continue
+            e, _ = train.centred_shape_error(sus.positions(), ref, wl.counts)
+            errs[name][str(S)] = float(np.mean(e))
         done = S
-        e, _ = train.centred_shape_error(hyb.positions(), plain.positions(), wl.counts)
-        errs[str(S)] = float(np.mean(e))
     plain.close()
-    hyb.close()
-    last = errs.get(str(args.hybrid_steps))
-    out.update({"shape_error_mean_by_step": errs, "after_steps": args.hybrid_steps,
-                "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2),
-                "fallback": "exact relaxation on every %d-th step and for vesicles within 3 spacings h of "
-                            "another vesicle" % exact_every})
-    if failed:
-        out["failed"] = failed
+    for name, sus in runs.items():
+        sus.close()
+        last = errs[name].get(str(args.hybrid_steps))
+        out[name].update({"shape_error_mean_by_step": errs[name], "after_steps": args.hybrid_steps,
+                          "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2)})
+        if name in failed:
+            out[name]["failed"] = failed[name]
+    r["net"].close()
     return out
 
 
@@ -440,13 +442,11 @@ def run_gpu(args):
                "note": "per step: vs_set_state (positions + tension from pinned host), vs_step, "
                        "vs_get_positions + vs_get_tension to pinned host; wall clock"}
 
-    multipole = None
-    if rank == 0 and not args.no_multipole:
-        multipole = multipole_arm(wl, args, stream)
-    hybrid = None
+    arms = {}
     if rank == 0 and not args.no_hybrid:
-        hybrid = hybrid_arm(wl, args, stream)
-        hybrid["vs_plain"] = hybrid["value"] / (value / world)  # both single-GPU throughputs
+        arms = long_run_arms(wl, args, stream)
+        for v in arms.values():
+            v["vs_plain"] = v["value"] / (value / world)  # both single-GPU throughputs
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(wl)
@@ -459,7 +459,8 @@ def run_gpu(args):
                                                                   "(autotuned at create)" % (fv[1], fv[2])}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
-                "steady_state": steady, "hybrid": hybrid, "farfield_multipole": multipole,
+                "steady_state": steady, "hybrid": arms.get("hybrid"),
+                "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()
