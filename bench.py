@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--farfield-multipole", action="store_true",
+                    help="time the plain step with the vesicle-multipole far field (not the headline configuration)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
@@ -343,7 +345,8 @@ def run_gpu(args):
     wl = workload(args)
     stream = torch.cuda.current_stream()
     s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
-                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True)
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True,
+                           farfield_multipole=args.farfield_multipole)
     fv = s.farfield_variant()
     for _ in range(max(args.warmup, 3)):
         s.step(1)
@@ -456,7 +459,11 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU",
                                                "farfield_launch": "%d threads x %d staged source points per CTA "
-                                                                  "(autotuned at create)" % (fv[1], fv[2])}),
+                                                                  "(autotuned at create)" % (fv[1], fv[2])}
+                                    if not args.farfield_multipole else
+                                    {"parallelism": "replicas" if world > 1 else "single GPU",
+                                     "farfield": "fp32 vesicle multipole beyond three reach radii, point sums "
+                                                 "inside (not the headline configuration)"}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
                 "steady_state": steady, "hybrid": arms.get("hybrid"),
