@@ -80,3 +80,35 @@ def test_multipole_suspension_poiseuille_2000x64():
         assert err <= 2e-5, (name, err)
     g.close()
     d.close()
+
+
+def test_multipole_far_field_uneven_vesicles_and_near_lists():
+    # point counts 16..128 in one box, some vesicles close (point sums and near test), most far
+    from paper_2606_25569_b300.workloads import vesicle_outline
+    rng = np.random.default_rng(23)
+    xs, ys, fx, fy = [], [], [], []
+    Ns = rng.choice([16, 32, 48, 64, 128], size=60)
+    for v, N in enumerate(Ns):
+        x, y = vesicle_outline(int(N), float(rng.uniform(0.6, 0.9)), 0.1, 1e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x + 0.25 * (v % 8) + 0.02 * rng.standard_normal())
+        ys.append(y + 0.25 * (v // 8))
+        fx.append(rng.standard_normal(int(N)))
+        fy.append(rng.standard_normal(int(N)))
+    off = np.concatenate([[0], np.cumsum(Ns)]).astype(np.int64)
+    xy = np.concatenate([np.concatenate([a, b]) for a, b in zip(xs, ys)])
+    f = np.concatenate([np.concatenate([a, b]) for a, b in zip(fx, fy)])
+    got, counts = {}, {}
+    for prec in (0, 2):
+        plan = binding.FarFieldPlan(off, mu=1.0, near_mask=True, precision=prec)
+        u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+        plan.eval(_dev(xy), _dev(f), u)
+        got[prec] = u.cpu().numpy()
+        counts[prec] = plan.counters()
+        plan.close()
+    assert counts[0] == counts[2] and counts[2]["near_pairs"] > 0 and counts[2]["err"] == 0  # same near pairs
+    ux, uy, near = far_field(xs, ys, fx, fy, 1.0, near_mask=True)
+    assert len(near) == counts[2]["near_pairs"]
+    ref = np.concatenate([np.concatenate([ux[off[v]:off[v + 1]], uy[off[v]:off[v + 1]]]) for v in range(len(Ns))])
+    err = np.linalg.norm(got[2] - ref) / np.linalg.norm(ref)
+    print("uneven box, multipole: relative L2 error %.3e" % err)
+    assert err <= 1e-5, err
