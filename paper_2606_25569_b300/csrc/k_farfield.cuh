@@ -253,12 +253,83 @@ __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__
   if (k == 0) a0[v] = make_float2((float)sA[0].x, (float)sA[0].y);
 }
 
-// One thread per target over every source vesicle in ascending order: the expansion for far vesicles,
-// the point sum (k_farfield_f32's, with the near test) for the rest; per-vesicle results added with
-// Neumaier compensation. The vesicles' centres, reach and expansion coefficients are staged through shared
-// memory FF_MP_CHUNK vesicles at a time.
+// Horner evaluation of a far vesicle's expansion (coefficients c in shared memory, (h^2, reach^2, A0) in na)
+// for E targets at once (q_e = (qx[e], qy[e]), |q_e|^2 = d2[e]): every coefficient load serves all E.
+template <int P, int E>
+__device__ __forceinline__ void mp_far(const float4* c, float4 na, const float* qx, const float* qy, const float* d2,
+                                       float* ux, float* uy) {
+  const float hl2 = -0.34657359027997264f;  // -ln(2)/2
+  float zr[E], zi[E], t1r[E], t1i[E], sar[E], sai[E], er[E], ei[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const float inv = fast_rcp(d2[e]);
+    zr[e] = qx[e] * inv;
+    zi[e] = -qy[e] * inv;  // zeta = 1/q
+    t1r[e] = t1i[e] = sar[e] = sai[e] = er[e] = ei[e] = 0.f;
+  }
+#pragma unroll
+  for (int k = P; k >= 0; --k) {  // Horner from the top coefficient (index k = power - 1)
+    const float4 c0 = c[2 * k], c1 = c[2 * k + 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      float r;
+      r = fmaf(t1r[e], zr[e], fmaf(-t1i[e], zi[e], c0.x)); t1i[e] = fmaf(t1r[e], zi[e], fmaf(t1i[e], zr[e], c0.y)); t1r[e] = r;
+      r = fmaf(sar[e], zr[e], fmaf(-sai[e], zi[e], c0.z)); sai[e] = fmaf(sar[e], zi[e], fmaf(sai[e], zr[e], c0.w)); sar[e] = r;
+      r = fmaf(er[e], zr[e], fmaf(-ei[e], zi[e], c1.x)); ei[e] = fmaf(er[e], zi[e], fmaf(ei[e], zr[e], c1.y)); er[e] = r;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    // the series start at zeta^1: one more factor zeta
+    float r;
+    r = t1r[e] * zr[e] - t1i[e] * zi[e]; t1i[e] = t1r[e] * zi[e] + t1i[e] * zr[e]; t1r[e] = r;
+    r = sar[e] * zr[e] - sai[e] * zi[e]; sai[e] = sar[e] * zi[e] + sai[e] * zr[e]; sar[e] = r;
+    r = er[e] * zr[e] - ei[e] * zi[e]; ei[e] = er[e] * zi[e] + ei[e] * zr[e]; er[e] = r;
+    const float lq = hl2 * fast_lg2(d2[e]);  // -log|q|
+    // u = -A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
+    ux[e] = fmaf(na.z, lq + 0.5f, 0.5f * (t1r[e] + er[e] + (qx[e] * sar[e] + qy[e] * sai[e])));
+    uy[e] = fmaf(na.w, lq + 0.5f, 0.5f * (t1i[e] - ei[e] + (qy[e] * sar[e] - qx[e] * sai[e])));
+  }
+}
+
+// Point sum over vesicle sv's sources (global memory) for the target at q, with the near test when the
+// target is within reach; returns false (and records sv in the target's near list) for a near pair.
+__device__ __forceinline__ bool mp_points(const FarFieldArgs& a, const float4* __restrict__ src, int64_t t, int sv,
+                                          float qx, float qy, float d2, float4 na, int& ncnt, float& ux, float& uy) {
+  const float hl2 = -0.34657359027997264f;
+  const bool test = a.near_mask && d2 <= na.y;
+  float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
+  const int64_t j0 = a.voff[sv], j1 = a.voff[sv + 1];
+  for (int64_t j = j0; j < j1; ++j) {
+    const float4 s = __ldg(src + j);
+    const float rx = qx - s.x, ry = qy - s.y;
+    const float r2 = fmaf(rx, rx, ry * ry);
+    if (test) mn = fminf(mn, r2);
+    const float lg = fast_lg2(r2);
+    const float iv = fast_rcp(r2);
+    lx = fmaf(lg, s.z, lx);
+    ly = fmaf(lg, s.w, ly);
+    const float q = fmaf(rx, s.z, ry * s.w) * iv;
+    ax = fmaf(q, rx, ax);
+    ay = fmaf(q, ry, ay);
+  }
+  if (test && mn <= na.x) {
+    if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
+    else atomicOr(a.err, ERR_NEAR_OVERFLOW);
+    ++ncnt;
+    return false;
+  }
+  ux = fmaf(hl2, lx, ax);
+  uy = fmaf(hl2, ly, ay);
+  return true;
+}
+
+// TPT consecutive targets per thread over every source vesicle in ascending order: the expansion for far
+// vesicles (one coefficient pass for all of a thread's targets when every one of them is far), the point
+// sum with the near test for the rest; per-vesicle results added with Neumaier compensation. The vesicles'
+// centres, reach and coefficients are staged through shared memory FF_MP_CHUNK vesicles at a time.
 constexpr int FF_MP_CHUNK = 32;
-template <int THREADS, int P>
+template <int THREADS, int P, int TPT>
 __global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const float4* __restrict__ src,
                                                          const float4* __restrict__ centre32,
                                                          const float2* __restrict__ h2,
@@ -268,14 +339,22 @@ __global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const f
   __shared__ float4 scoef[FF_MP_CHUNK * NC];
   __shared__ float4 scen[FF_MP_CHUNK];
   __shared__ float4 sh2a0[FF_MP_CHUNK];  // (h^2, reach^2, A0.x, A0.y)
-  const int64_t t = (int64_t)blockIdx.x * THREADS + threadIdx.x;
-  const bool valid = t < a.P;
-  const int tv = valid ? a.owner[t] : -1;
-  const float4 ts = valid ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 tc = valid ? centre32[tv] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-  int ncnt = 0;
-  const float hl2 = -0.34657359027997264f;  // -ln(2)/2
+  int64_t t[TPT];
+  int tv[TPT], ncnt[TPT];
+  float4 ts[TPT], tc[TPT];
+  float sx[TPT], cx[TPT], sy[TPT], cy[TPT];
+  bool any = false;
+#pragma unroll
+  for (int e = 0; e < TPT; ++e) {
+    t[e] = ((int64_t)blockIdx.x * THREADS + threadIdx.x) * TPT + e;
+    const bool ok = t[e] < a.P;
+    any |= ok;
+    tv[e] = ok ? a.owner[t[e]] : -1;
+    ts[e] = ok ? src[t[e]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    tc[e] = ok ? centre32[tv[e]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sx[e] = cx[e] = sy[e] = cy[e] = 0.f;
+    ncnt[e] = 0;
+  }
   for (int v0 = 0; v0 < a.M; v0 += FF_MP_CHUNK) {
     const int nv = min(FF_MP_CHUNK, a.M - v0);
     __syncthreads();
@@ -286,74 +365,53 @@ __global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const f
       sh2a0[e] = make_float4(hh.x, hh.y, A.x, A.y);
     }
     __syncthreads();
-    if (!valid) continue;
+    if (!any) continue;
     for (int l = 0; l < nv; ++l) {
       const int sv = v0 + l;
-      if (sv == tv) continue;
       const float4 sc = scen[l];
-      const float qx = ((tc.x - sc.x) + (tc.z - sc.z)) + ts.x;
-      const float qy = ((tc.y - sc.y) + (tc.w - sc.w)) + ts.y;
       const float4 na = sh2a0[l];
-      const float d2 = fmaf(qx, qx, qy * qy);
-      float ux, uy;
-      if (d2 > FF_MP_THETA2 * na.y) {
-        const float inv = fast_rcp(d2);
-        const float zr = qx * inv, zi = -qy * inv;  // zeta = 1/q
-        const float4* c = scoef + l * NC;
-        float t1r = 0.f, t1i = 0.f, sar = 0.f, sai = 0.f, er = 0.f, ei = 0.f;
+      float qx[TPT], qy[TPT], d2[TPT];
+      bool far_all = true;
 #pragma unroll
-        for (int k = P; k >= 0; --k) {  // Horner from the top coefficient (index k = power - 1)
-          const float4 c0 = c[2 * k], c1 = c[2 * k + 1];
-          float r;
-          r = fmaf(t1r, zr, fmaf(-t1i, zi, c0.x)); t1i = fmaf(t1r, zi, fmaf(t1i, zr, c0.y)); t1r = r;
-          r = fmaf(sar, zr, fmaf(-sai, zi, c0.z)); sai = fmaf(sar, zi, fmaf(sai, zr, c0.w)); sar = r;
-          r = fmaf(er, zr, fmaf(-ei, zi, c1.x)); ei = fmaf(er, zi, fmaf(ei, zr, c1.y)); er = r;
+      for (int e = 0; e < TPT; ++e) {
+        qx[e] = ((tc[e].x - sc.x) + (tc[e].z - sc.z)) + ts[e].x;
+        qy[e] = ((tc[e].y - sc.y) + (tc[e].w - sc.w)) + ts[e].y;
+        d2[e] = fmaf(qx[e], qx[e], qy[e] * qy[e]);
+        far_all = far_all && tv[e] >= 0 && sv != tv[e] && d2[e] > FF_MP_THETA2 * na.y;
+      }
+      if (far_all) {
+        float ux[TPT], uy[TPT];
+        mp_far<P, TPT>(scoef + l * NC, na, qx, qy, d2, ux, uy);
+#pragma unroll
+        for (int e = 0; e < TPT; ++e) {
+          neumaier_add(sx[e], cx[e], ux[e]);
+          neumaier_add(sy[e], cy[e], uy[e]);
         }
-        // the series start at zeta^1: one more factor zeta
-        float r;
-        r = t1r * zr - t1i * zi; t1i = t1r * zi + t1i * zr; t1r = r;
-        r = sar * zr - sai * zi; sai = sar * zi + sai * zr; sar = r;
-        r = er * zr - ei * zi; ei = er * zi + ei * zr; er = r;
-        const float lq = hl2 * fast_lg2(d2);  // -log|q|
-        // u = -A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
-        ux = fmaf(na.z, lq + 0.5f, 0.5f * (t1r + er + (qx * sar + qy * sai)));
-        uy = fmaf(na.w, lq + 0.5f, 0.5f * (t1i - ei + (qy * sar - qx * sai)));
-      } else {
-        const bool test = a.near_mask && d2 <= na.y;
-        float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
-        const int64_t j0 = a.voff[sv], j1 = a.voff[sv + 1];
-        for (int64_t j = j0; j < j1; ++j) {
-          const float4 s = __ldg(src + j);
-          const float rx = qx - s.x, ry = qy - s.y;
-          const float r2 = fmaf(rx, rx, ry * ry);
-          if (test) mn = fminf(mn, r2);
-          const float lg = fast_lg2(r2);
-          const float iv = fast_rcp(r2);
-          lx = fmaf(lg, s.z, lx);
-          ly = fmaf(lg, s.w, ly);
-          const float q = fmaf(rx, s.z, ry * s.w) * iv;
-          ax = fmaf(q, rx, ax);
-          ay = fmaf(q, ry, ay);
-        }
-        if (test && mn <= na.x) {
-          if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
-          else atomicOr(a.err, ERR_NEAR_OVERFLOW);
-          ++ncnt;
+        continue;
+      }
+#pragma unroll
+      for (int e = 0; e < TPT; ++e) {
+        if (tv[e] < 0 || sv == tv[e]) continue;
+        float ux, uy;
+        if (d2[e] > FF_MP_THETA2 * na.y) {
+          mp_far<P, 1>(scoef + l * NC, na, &qx[e], &qy[e], &d2[e], &ux, &uy);
+        } else if (!mp_points(a, src, t[e], sv, qx[e], qy[e], d2[e], na, ncnt[e], ux, uy)) {
           continue;
         }
-        ux = fmaf(hl2, lx, ax);
-        uy = fmaf(hl2, ly, ay);
+        neumaier_add(sx[e], cx[e], ux);
+        neumaier_add(sy[e], cy[e], uy);
       }
-      neumaier_add(sx, cx, ux);
-      neumaier_add(sy, cy, uy);
     }
   }
-  if (!valid) return;
-  const int64_t to = a.voff[tv];
-  const int tN = (int)(a.voff[tv + 1] - to);
-  a.u[2 * to + (t - to)] += (double)sx + (double)cx;
-  a.u[2 * to + tN + (t - to)] += (double)sy + (double)cy;
-  if (a.near_mask) a.near_cnt[t] = ncnt < MAX_NEAR ? ncnt : MAX_NEAR;
+#pragma unroll
+  for (int e = 0; e < TPT; ++e) {
+    if (tv[e] < 0) continue;
+    const int64_t to = a.voff[tv[e]];
+    const int tN = (int)(a.voff[tv[e] + 1] - to);
+    a.u[2 * to + (t[e] - to)] += (double)sx[e] + (double)cx[e];
+    a.u[2 * to + tN + (t[e] - to)] += (double)sy[e] + (double)cy[e];
+    if (a.near_mask) a.near_cnt[t[e]] = ncnt[e] < MAX_NEAR ? ncnt[e] : MAX_NEAR;
+  }
 }
 
 }  // namespace vs

@@ -545,9 +545,9 @@ vs_status far_field(vs_suspension* h) {
     VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef,
                                                                                    h->B.mpa0));
     const int grid = (int)((L.P + 127) / 128);
-    VS_LAUNCH(h, "k_farfield_mp", (k_farfield_mp<128, FF_MP_P><<<grid, 128, 0, h->stream>>>(a, h->B.src, h->B.centre32,
-                                                                                          h->B.h2, h->B.mpcoef,
-                                                                                          h->B.mpa0)));
+    VS_LAUNCH(h, "k_farfield_mp", (k_farfield_mp<128, FF_MP_P, 1><<<grid, 128, 0, h->stream>>>(a, h->B.src,
+                                                                                             h->B.centre32, h->B.h2,
+                                                                                             h->B.mpcoef, h->B.mpa0)));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -1312,8 +1312,8 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
   } else if (h->precision == 2) {
     k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
-    k_farfield_mp<128, FF_MP_P><<<(int)((L.P + 127) / 128), 128, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2,
-                                                                                 h->B.mpcoef, h->B.mpa0);
+    k_farfield_mp<128, FF_MP_P, 1><<<(int)((L.P + 127) / 128), 128, 0, h->stream>>>(a, h->B.src, h->B.centre32,
+                                                                                    h->B.h2, h->B.mpcoef, h->B.mpa0);
   } else {
     k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
   }
