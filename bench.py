@@ -407,23 +407,8 @@ def run_gpu(args):
     breakdown = {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     per_step = {k: round(v[0] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
-    # steady state: after a burn-in the area/length correction fires for a few vesicles every step
-    steady = None
-    if args.burn_in > 0:
-        s.step(args.burn_in)
-        s.sync()
-        c0 = s.counters()["corrections"]
-        t2, t3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t2.record(stream)
-        s.step(args.steps)
-        t3.record(stream)
-        torch.cuda.synchronize()
-        ms_ss = t2.elapsed_time(t3) / args.steps
-        steady = {"after_steps": args.burn_in + max(args.warmup, 3) + args.steps, "steps": args.steps,
-                  "ms_per_step": ms_ss, "value": world * wl.M / (ms_ss * 1e-3), "unit": UNIT,
-                  "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
-
-    # end to end through the C ABI with host buffers: upload state, step, read positions
+    # end to end through the C ABI with host buffers: upload state, step, read positions (right after the
+    # timed region, so at the same stage of the run as the device-timed value)
     e2e = None
     if not args.no_e2e:
         xy_h = torch.empty(2 * s.P, dtype=torch.float64).pin_memory()
@@ -444,6 +429,22 @@ def run_gpu(args):
                "d2h_bytes_per_step": 24 * s.P, "steps": n_e2e,
                "note": "per step: vs_set_state (positions + tension from pinned host), vs_step, "
                        "vs_get_positions + vs_get_tension to pinned host; wall clock"}
+
+    # steady state: after a burn-in the area/length correction fires for a few vesicles every step
+    steady = None
+    if args.burn_in > 0:
+        s.step(args.burn_in)
+        s.sync()
+        c0 = s.counters()["corrections"]
+        t2, t3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t2.record(stream)
+        s.step(args.steps)
+        t3.record(stream)
+        torch.cuda.synchronize()
+        ms_ss = t2.elapsed_time(t3) / args.steps
+        steady = {"after_steps": args.burn_in + max(args.warmup, 3) + args.steps, "steps": args.steps,
+                  "ms_per_step": ms_ss, "value": world * wl.M / (ms_ss * 1e-3), "unit": UNIT,
+                  "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
 
     arms = {}
     if rank == 0 and not args.no_hybrid:

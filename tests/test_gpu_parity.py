@@ -328,3 +328,20 @@ def test_checkpoint_resume_is_bitwise():
         b.restore(ck[:100])
     for s in (a, b, c, d):
         s.close()
+
+
+@pytest.mark.parametrize("multipole", [False, True])
+def test_two_runs_are_bitwise_identical(multipole):
+    # fixed-order reductions and no floating-point atomics: the same input gives the same bits
+    xs, ys = _mixed([64, 32, 64, 48, 64, 32, 64, 64, 16, 128], 13, spacing=2.4)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, corr_tol=0.0, flow_kind=1, flow_p=(0.5, 0, 0, 0), near_field=True,
+              use_graph=True, farfield_multipole=multipole)
+    runs = []
+    for _ in range(2):
+        s = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+        s.step(4)
+        runs.append((s.positions(), s.tension(), s.velocity(), s.counters()))
+        s.close()
+    (pa, ta, va, ca), (pb, tb, vb, cb) = runs
+    assert np.array_equal(pa, pb) and np.array_equal(ta, tb) and np.array_equal(va, vb)
+    assert ca["corrections"] == cb["corrections"] > 0 and ca["near_pairs"] == cb["near_pairs"]
