@@ -418,11 +418,12 @@ __device__ void corr_update(int v, VesIndex vi, const double* LU, const int* p, 
 
 // Newton iterations of the correction with an FP32 Jacobian (2N <= 16 RA): per step the FP64 residual
 // (z - X - J^T lam, c(z)) as in corr_build, the 2N x 2N block M = I - lam_A H_A - lam_L H_L assembled in
-// FP32 in dynamic shared memory and inverted in registers (gj_invert), and the KKT system
+// FP32 in dynamic shared memory and inverted in registers (gj_invert_np, else gj_invert), and the KKT system
 //   [M  -G; G^T  0] [dz; dlam] = [r1; r2],  G = (grad A, grad L)
 // solved through its 2 x 2 Schur complement: y = M^{-1} r1, Y = M^{-1} G, (G^T Y) dlam = r2 - G^T y,
 // dz = y + Y dlam. The FP32 Jacobian makes the iteration converge linearly (factor about 1e-6) to the
-// same KKT point that the FP64 residual defines; the same stopping test as corr_update. 256 threads.
+// same KKT point that the FP64 residual defines, and so does keeping M's inverse from one step to the
+// next (chord steps) while the updates keep shrinking; the same stopping test as corr_update. 256 threads.
 template <int RA>
 __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double* __restrict__ tab,
                                                        const double* __restrict__ A0, const double* __restrict__ L0,
@@ -445,6 +446,11 @@ __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double
     d[i] = tab[vi.toff[v] + i];
     dq[i] = (float)d[i];
   }
+  // the inverse of M is formed on the first step (M = I at lam = 0), re-formed on the second and kept
+  // while each update shrinks by 10x or more (a chord iteration on the Jacobian of the second step)
+  __shared__ int reinv;
+  __shared__ double mprev;
+  if (tid == 0) { reinv = 1; mprev = 1e300; }
   for (int it = 0; it < iters; ++it) {
     __syncthreads();
     if (!active[v]) break;  // uniform: written by thread 0 of this CTA before the barrier
@@ -483,26 +489,31 @@ __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double
     }
     // M = I - la dal H_A - ll dal H_L in FP32
     const float fa = (float)(la * dal), fl = (float)(ll * dal);
-    for (int e = tid; e < n2 * n2; e += blockDim.x) {
-      const int a = e / n2, b = e - a * n2;
-      const int p = a / N, i = a - p * N, q = b / N, j = b - q * N;
-      const float* qq = (p == 0) ? ((q == 0) ? qxx : qxy) : ((q == 0) ? qxy : qyy);
-      float hl = 0.f;
-      int ki = N - i, kj = N - j;  // (k - i) mod N at k = 0
-      if (ki == N) ki = 0;
-      if (kj == N) kj = 0;
-      for (int k = 0; k < N; ++k) {
-        hl = fmaf(dq[ki] * dq[kj], qq[k], hl);
-        if (++ki == N) ki = 0;
-        if (++kj == N) kj = 0;
+    if (reinv && it == 0 && la == 0.0 && ll == 0.0) {
+      for (int e = tid; e < n2 * n2; e += blockDim.x) Mg[e] = (e / n2 == e % n2) ? 1.f : 0.f;
+    } else if (reinv) {
+      for (int e = tid; e < n2 * n2; e += blockDim.x) {
+        const int a = e / n2, b = e - a * n2;
+        const int p = a / N, i = a - p * N, q = b / N, j = b - q * N;
+        const float* qq = (p == 0) ? ((q == 0) ? qxx : qxy) : ((q == 0) ? qxy : qyy);
+        float hl = 0.f;
+        int ki = N - i, kj = N - j;  // (k - i) mod N at k = 0
+        if (ki == N) ki = 0;
+        if (kj == N) kj = 0;
+        for (int k = 0; k < N; ++k) {
+          hl = fmaf(dq[ki] * dq[kj], qq[k], hl);
+          if (++ki == N) ki = 0;
+          if (++kj == N) kj = 0;
+        }
+        float ha = 0.f;
+        if (p == 0 && q == 1) { int m = i - j; m += (m < 0) ? N : 0; ha = dq[m]; }
+        if (p == 1 && q == 0) { int m = j - i; m += (m < 0) ? N : 0; ha = dq[m]; }
+        Mg[e] = ((a == b) ? 1.f : 0.f) - fa * ha - fl * hl;
       }
-      float ha = 0.f;
-      if (p == 0 && q == 1) { int m = i - j; m += (m < 0) ? N : 0; ha = dq[m]; }
-      if (p == 1 && q == 0) { int m = j - i; m += (m < 0) ? N : 0; ha = dq[m]; }
-      Mg[e] = ((a == b) ? 1.f : 0.f) - fa * ha - fl * hl;
+      __syncthreads();
+      if (!gj_invert_np<RA, RA, 16>(Mg, Mg, n2)) gj_invert<RA, RA, 16>(Mg, Mg, n2, err);
     }
     __syncthreads();
-    gj_invert<RA, RA, 16>(Mg, Mg, n2, err);
     // y = M^{-1} r1, Y = M^{-1} (gA, gL): warp per row
     {
       const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -572,6 +583,8 @@ __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double
         st[6 * N + 7] = 1.0;
         active[v] = 0;
       }
+      reinv = (it == 0) || !(m <= 0.1 * mprev);
+      mprev = m;
     }
   }
   __syncthreads();
