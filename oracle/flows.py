@@ -5,6 +5,9 @@ kind codes match the library's flow enumeration: 0 none, 1 shear, 2 Taylor-Green
 * Taylor-Green: u = U (sin(pi x/W) cos(pi y/W), -cos(pi x/W) sin(pi y/W)) (Eq. tayGreenFlow),
                 p = (U, W)
 * Poiseuille:   u = u_max (1 - (y/W)^2) e_x, walls at y = +-W       (Sec. 5.3), p = (u_max, W)
+
+Pins (tests/test_oracle_flows.py): every flow divergence-free by finite differences, the shear rate, the
+Poiseuille no-slip walls, axis velocity and wall shear rate, the Taylor-Green stagnation points and speed.
 """
 import numpy as np
 

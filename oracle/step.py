@@ -12,6 +12,10 @@ Per step, in this order (Sec. 3.1, Algorithm 1, Sec. 4.2-4.3):
    redistributed X^{n+1}, u^n resampled at the new parameters                (Eq. tension_disc)
 7. area/length correction when either relative error exceeds corr_tol         (Sec. 4.3)
 
+Pins (tests/test_oracle_step.py): relaxation lowers the bending energy, area and length drift first
+order in dt, translation/rotation equivariance, first-order convergence in time, a uniform background
+translates a vesicle rigidly, the proximity rule on circles at known gaps.
+
 Readings: Eq. tension_disc writes L^n, P^n while Algorithm 1-2 evaluate them at X^{n+1}; we
 use X^{n+1} after redistribution (step 6), and since redistribution re-indexes the material
 points, u^n is carried to the new points by its trigonometric interpolant. Algorithm 1
