@@ -345,3 +345,26 @@ def test_two_runs_are_bitwise_identical(multipole):
     (pa, ta, va, ca), (pb, tb, vb, cb) = runs
     assert np.array_equal(pa, pb) and np.array_equal(ta, tb) and np.array_equal(va, vb)
     assert ca["corrections"] == cb["corrections"] > 0 and ca["near_pairs"] == cb["near_pairs"]
+
+
+def test_extreme_point_counts_step():
+    # the smallest (8) and largest (128) point counts in one suspension, through the default path
+    xs, ys = _mixed([8, 128, 8, 128], 14, spacing=2.6)
+    o, g = _oracle_and_gpu(xs, ys, 1.0, 1.0, 1e-3, 1, (0.5, 0, 0, 0), 0.01)
+    for _ in range(3):
+        o.step()
+        g.step()
+        _compare(o, g)
+    g.close()
+
+
+def test_circle_makes_the_tension_system_singular_and_is_reported():
+    # degenerate case of the method: on a circle a uniform tension gives a uniform normal force c n, and
+    # S[c n] = 0, so the tension operator L = P S Ten annihilates constants and sigma is fixed only up to
+    # one. The mixed-precision refinement notices (it cannot converge in the null direction) and the
+    # suspension is refused with VS_ERR_NOT_CONVERGED instead of returning an arbitrary tension.
+    N, R = 64, 0.7
+    t = 2 * np.pi * np.arange(N) / N
+    xs, ys = [R * np.cos(t)], [R * np.sin(t)]
+    with pytest.raises(binding.VsError, match="NOT_CONVERGED"):
+        binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.3, mu=1.0, dt=1e-2, corr_tol=0.01, flow_kind=0)
