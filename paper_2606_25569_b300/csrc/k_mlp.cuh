@@ -3,12 +3,14 @@
 //
 // k_gemm_bf16 computes D[m][n] = sum_k A[m][k] B[n][k] (both operands K-major, BF16) with
 // tcgen05.mma (kind::f16, cta_group::1, M = 128, N = 128, K = 16 per instruction). One CTA per
-// 128 x 128 output tile; its K loop stages 128 x 64 slices of A and B through two shared-memory
-// buffers in the canonical no-swizzle K-major layout (8 x 8 core matrices, core (g, c) of row
-// group g and K-chunk c at byte (8 g + c) * 128, so LBO = 128 B, SBO = 1024 B), one elected thread
-// issues the MMAs and commits them to an mbarrier, and the accumulator stays in 128 TMEM columns
-// until the epilogue reads it back with tcgen05.ld. Every mbarrier wait has an iteration bound
-// after which the kernel records an error and skips the epilogue.
+// 128 x 128 output tile; its K loop stages 128 x 64 slices of A and B through a ring of MM_STAGES
+// shared-memory buffers in the canonical no-swizzle K-major layout (8 x 8 core matrices, core (g, c)
+// of row group g and K-chunk c at byte (8 g + c) * 128, so LBO = 128 B, SBO = 1024 B), filled by
+// asynchronous 16-byte copies (cp.async) MM_STAGES - 1 slices ahead of the products; one elected thread
+// issues the MMAs and commits them to the slice's mbarrier, which frees the buffer for its next fill, and
+// the accumulator stays in 128 TMEM columns until the epilogue reads it back with tcgen05.ld. Every
+// mbarrier wait has an iteration bound after which the kernel records an error, drains its copies and
+// skips the epilogue.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -18,7 +20,8 @@ namespace vs {
 
 constexpr int MM_BM = 128, MM_BN = 128, MM_BK = 64, MM_THREADS = 128;
 constexpr int MM_STAGE_BYTES = (MM_BM + MM_BN) * MM_BK * 2;   // 32 KB
-constexpr int MM_SMEM = 2 * MM_STAGE_BYTES + 1024;           // two stages + 1 KB alignment slack
+constexpr int MM_STAGES = 4;                                 // shared-memory ring of K slices
+constexpr int MM_SMEM = MM_STAGES * MM_STAGE_BYTES + 1024;   // the ring + 1 KB alignment slack
 constexpr uint32_t MM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MM_BN >> 3) << 17) |
                               ((uint32_t)(MM_BM >> 4) << 24);  // F32 accumulate, BF16 A and B, K-major
 constexpr long long MM_WAIT_LIMIT = 1ll << 26;
@@ -59,9 +62,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(__cvta_generic_to_global(src)),
+               "r"(bytes) : "memory");
+}
+
 __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   extern __shared__ unsigned char mm_raw[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[MM_STAGES];
   __shared__ uint32_t tmem_base;
   unsigned char* st = (unsigned char*)(((uintptr_t)mm_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -72,8 +80,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+    for (int q = 0; q < MM_STAGES; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[q])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -81,32 +88,42 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int nk = (g.K + MM_BK - 1) / MM_BK;
-  bool ok = true;
-  for (int kb = 0; kb < nk; ++kb) {
-    const int s = kb & 1;
-    if (kb >= 2) {
-      const bool w = mbar_wait(smem_addr(&mbar[s]), (uint32_t)((kb - 2) >> 1) & 1u);
-      if (__syncthreads_or(!w)) { ok = false; break; }
-    }
-    unsigned char* sa = st + s * MM_STAGE_BYTES;
+  // copies of K slice kb into ring buffer kb % MM_STAGES (out-of-range chunks are filled with zeros)
+  auto fill = [&](int kb) {
+    unsigned char* sa = st + (kb % MM_STAGES) * MM_STAGE_BYTES;
     unsigned char* sb = sa + MM_BM * MM_BK * 2;
     const int kbase = kb * MM_BK;
-    for (int e = tid; e < MM_BM * 8; e += MM_THREADS) {
-      const int r = e >> 3, c = e & 7;
+#pragma unroll
+    for (int q = 0; q < MM_BM * 8 / MM_THREADS; ++q) {
+      const int e = tid + q * MM_THREADS, r = e >> 3, c = e & 7;
       const int gm = m0 + r, gk = kbase + 8 * c;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (gm < g.M && gk < g.K) val = *reinterpret_cast<const uint4*>(g.A + (int64_t)gm * g.lda + gk);
-      *reinterpret_cast<uint4*>(sa + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = val;
+      const bool in = gm < g.M && gk < g.K;
+      cp_async16(smem_addr(sa + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16),
+                 in ? (const void*)(g.A + (int64_t)gm * g.lda + gk) : (const void*)g.A, in ? 16u : 0u);
     }
-    for (int e = tid; e < MM_BN * 8; e += MM_THREADS) {
-      const int r = e >> 3, c = e & 7;
+#pragma unroll
+    for (int q = 0; q < MM_BN * 8 / MM_THREADS; ++q) {
+      const int e = tid + q * MM_THREADS, r = e >> 3, c = e & 7;
       const int gn = n0 + r, gk = kbase + 8 * c;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (gn < g.N && gk < g.K) val = *reinterpret_cast<const uint4*>(g.B + (int64_t)gn * g.ldb + gk);
-      *reinterpret_cast<uint4*>(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = val;
+      const bool in = gn < g.N && gk < g.K;
+      cp_async16(smem_addr(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16),
+                 in ? (const void*)(g.B + (int64_t)gn * g.ldb + gk) : (const void*)g.B, in ? 16u : 0u);
     }
+  };
+#pragma unroll
+  for (int p = 0; p < MM_STAGES - 1; ++p) {
+    if (p < nk) fill(p);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  bool ok = true;
+  for (int kb = 0; kb < nk; ++kb) {
+    // slice kb has landed (this thread's copies, then everyone's), visible to the tensor core's proxy
+    asm volatile("cp.async.wait_group %0;" ::"n"(MM_STAGES - 2) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    const int s = kb % MM_STAGES;
+    unsigned char* sa = st + s * MM_STAGE_BYTES;
+    unsigned char* sb = sa + MM_BM * MM_BK * 2;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -120,9 +137,22 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_addr(&mbar[s])));
     }
+    // refill the buffer of slice kb - 1 with slice kb + MM_STAGES - 1 once its products are done
+    const int nx = kb + MM_STAGES - 1;
+    if (nx < nk) {
+      if (kb >= 1) {
+        const int pb = kb - 1;
+        const bool w = mbar_wait(smem_addr(&mbar[pb % MM_STAGES]), (uint32_t)(pb / MM_STAGES) & 1u);
+        if (__syncthreads_or(!w)) { ok = false; break; }
+      }
+      fill(nx);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy left in flight, also after a timeout
   if (ok && nk > 0) {
-    const bool w = mbar_wait(smem_addr(&mbar[(nk - 1) & 1]), (uint32_t)((nk - 1) >> 1) & 1u);
+    const int lb = nk - 1;
+    const bool w = mbar_wait(smem_addr(&mbar[lb % MM_STAGES]), (uint32_t)(lb / MM_STAGES) & 1u);
     if (__syncthreads_or(!w)) ok = false;
   }
   if (!ok && tid == 0) atomicOr(g.err, ERR_MMA_TIMEOUT);
