@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
   if (ok) {
     const int r = warp * 32 + lane;
     const int gm = m0 + r;
+    // whole 16-column chunks with 16-byte aligned rows (dims are multiples of 16) take the vector path
+    const bool vec = (g.N % 16 == 0) && (!g.out_f32 || (g.ld_f32 % 4 == 0 && ((uintptr_t)g.out_f32 & 15) == 0)) &&
+                     (!g.out_bf || (g.ld_bf % 8 == 0 && ((uintptr_t)g.out_bf & 15) == 0)) &&
+                     (!g.bias || ((uintptr_t)g.bias & 15) == 0) &&
+                     (g.act != EPI_MASK || (g.ld_mask % 8 == 0 && ((uintptr_t)g.mask & 15) == 0));
     for (int c0 = 0; c0 < MM_BN; c0 += 16) {
       if (n0 + c0 >= g.N) break;  // uniform across the CTA
       uint32_t v[16];
@@ -171,19 +176,67 @@ __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (gm < g.M) {
+        const int gn0 = n0 + c0;
+        float x[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int gn = n0 + c0 + j;
-          if (gn >= g.N) break;
-          float x = __uint_as_float(v[j]);
-          if (g.bias) x += g.bias[gn];
-          if (g.act == EPI_RELU) x = fmaxf(x, 0.f);
-          if (g.act == EPI_MASK && !(__bfloat162float(g.mask[(int64_t)gm * g.ld_mask + gn]) > 0.f)) x = 0.f;
-          if (g.oscale) x = fmaf(x, g.oscale[gn], g.oshift[gn]);
-          if (g.out_f32) g.out_f32[(int64_t)gm * g.ld_f32 + gn] = x;
-          const __nv_bfloat16 b = __float2bfloat16_rn(x);
-          if (g.out_bf) g.out_bf[(int64_t)gm * g.ld_bf + gn] = b;
-          if (g.out_bfT) g.out_bfT[(int64_t)gn * g.ld_bfT + gm] = b;
+        for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[j]);
+        if (vec) {  // 16 whole, 16-element aligned columns: vector loads and stores of the row's chunk
+          if (g.bias) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(g.bias + gn0 + j);
+              x[j] += b4.x; x[j + 1] += b4.y; x[j + 2] += b4.z; x[j + 3] += b4.w;
+            }
+          }
+          if (g.act == EPI_RELU) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = fmaxf(x[j], 0.f);
+          }
+          if (g.act == EPI_MASK) {
+            __align__(16) __nv_bfloat16 mk[16];
+            const uint4* msrc = reinterpret_cast<const uint4*>(g.mask + (int64_t)gm * g.ld_mask + gn0);
+            *reinterpret_cast<uint4*>(mk) = msrc[0];
+            *reinterpret_cast<uint4*>(mk + 8) = msrc[1];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (!(__bfloat162float(mk[j]) > 0.f)) x[j] = 0.f;
+          }
+          if (g.oscale) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = fmaf(x[j], g.oscale[gn0 + j], g.oshift[gn0 + j]);
+          }
+          if (g.out_f32) {
+            float4* o = reinterpret_cast<float4*>(g.out_f32 + (int64_t)gm * g.ld_f32 + gn0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+          }
+          __align__(16) __nv_bfloat16 bv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) bv[j] = __float2bfloat16_rn(x[j]);
+          if (g.out_bf) {
+            uint4* o = reinterpret_cast<uint4*>(g.out_bf + (int64_t)gm * g.ld_bf + gn0);
+            o[0] = *reinterpret_cast<const uint4*>(bv);
+            o[1] = *reinterpret_cast<const uint4*>(bv + 8);
+          }
+          if (g.out_bfT) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) g.out_bfT[(int64_t)(gn0 + j) * g.ld_bfT + gm] = bv[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int gn = gn0 + j;
+            if (gn >= g.N) break;
+            float y = x[j];
+            if (g.bias) y += g.bias[gn];
+            if (g.act == EPI_RELU) y = fmaxf(y, 0.f);
+            if (g.act == EPI_MASK && !(__bfloat162float(g.mask[(int64_t)gm * g.ld_mask + gn]) > 0.f)) y = 0.f;
+            if (g.oscale) y = fmaf(y, g.oscale[gn], g.oshift[gn]);
+            if (g.out_f32) g.out_f32[(int64_t)gm * g.ld_f32 + gn] = y;
+            const __nv_bfloat16 b = __float2bfloat16_rn(y);
+            if (g.out_bf) g.out_bf[(int64_t)gm * g.ld_bf + gn] = b;
+            if (g.out_bfT) g.out_bfT[(int64_t)gn * g.ld_bfT + gm] = b;
+          }
         }
       }
     }
