@@ -78,6 +78,13 @@ typedef struct {
  * unchanged): an approximation of the all-pairs sum (the paper names FMM as the route to O(M) cost) whose
  * truncation error is below 3^-13 of a vesicle's density scale; FP32 with compensated accumulation. */
 #define VS_FLAG_FARFIELD_MULTIPOLE 16ull
+/* The FP32 far field sums over every ordered pair with one thread per target (k_farfield_f32, launch
+ * shape autotuned) instead of the default symmetric evaluation. The symmetric kernel (k_farfield_sym)
+ * visits each unordered pair of points of different vesicles once and adds both reactions (the
+ * Stokeslet is even in r), with deterministic chunked FP64 reduction; it runs when every vesicle has
+ * 32, 64 or 128 points and its per-chunk partial sums (16 bytes per point and group of 16 vesicles)
+ * fit in 4 GiB, the per-target kernel otherwise. The two agree to FP32 rounding. */
+#define VS_FLAG_FARFIELD_PER_TARGET 32ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */
@@ -165,14 +172,17 @@ vs_status vs_checkpoint_size(vs_suspension* s, int64_t* bytes);
 vs_status vs_checkpoint(vs_suspension* s, void* buf, int64_t cap);
 vs_status vs_restore(vs_suspension* s, const void* buf, int64_t size);
 
-/* FP32 far-field launch shape; the paper has no counterpart/* FP32 far-field launch shape; the paper has no counterpart (a tuning control). vs_create times the
- * far-field kernel in each of its launch shapes (threads per CTA x source points staged per chunk)
- * on the suspension's own sources and keeps the fastest, unless VS_FLAG_NO_AUTOTUNE is set; the
- * choice is cached per (device name, M, points, near mask) in the process, and in the text file
- * named by the environment variable VS_TUNE_CACHE when it is set. Every shape gives bitwise
- * identical velocities. set >= 0 selects shape `set` (captured step graphs are dropped), set < 0
- * leaves it. On return *index, *threads and *chunk (each may be null) describe the shape in use.
- * VS_ERR_INVALID_ARG for a null handle or set beyond the last shape. */
+/* Launch shape of the per-target FP32 far field (a tuning control; the paper has no counterpart).
+ * vs_create times the per-target kernel in each of its launch shapes (threads per CTA x source points
+ * staged per chunk) on the suspension's own sources and keeps the fastest, unless VS_FLAG_NO_AUTOTUNE
+ * is set or the symmetric kernel is in use (VS_FLAG_FARFIELD_PER_TARGET); the choice is cached per
+ * (device name, M, points, near mask) in the process, and in the text file named by the environment
+ * variable VS_TUNE_CACHE when it is set. Every shape gives bitwise identical velocities. set >= 0
+ * selects per-target shape `set` (leaving the symmetric kernel; captured step graphs are dropped),
+ * set < 0 leaves the choice. On return *index, *threads and *chunk (each may be null) describe the
+ * kernel in use: shape index, threads per CTA, source points staged per chunk; index -1 for the
+ * symmetric kernel (threads per CTA, points per chunk of vesicles). VS_ERR_INVALID_ARG for a null
+ * handle or set beyond the last shape. */
 vs_status vs_farfield_variant(vs_suspension* s, int32_t set, int32_t* index, int32_t* threads, int32_t* chunk);
 
 /* Per-kernel timing: while enabled, every kernel the handle launches is bracketed by CUDA

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "k_dense.cuh"
 #include "k_farfield.cuh"
+#include "k_farfield_sym.cuh"
 #include "k_geometry.cuh"
 #include "k_mlp.cuh"
 #include "k_mp.cuh"
@@ -304,6 +305,13 @@ struct vs_suspension {
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t graph_launches[4] = {0, 0, 0, 0};
   int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
+  // symmetric FP32 far field (k_farfield_sym): used when R > 0
+  struct {
+    int R = 0, nchunk = 0, ntile = 0, grid = 0;
+    int2* tiles = nullptr;
+    double2* part = nullptr;
+    unsigned* ctr = nullptr;
+  } ffs;
   std::string msg;
 };
 
@@ -534,6 +542,74 @@ FarFieldArgs far_field_args(vs_suspension* h) {
                       h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
 }
 
+// Symmetric FP32 far field: eligible when every vesicle has N = 32, 64 or 128 points and the chunk slots
+// (one double2 per point and chunk of FFS_V vesicles) fit in FFS_PART_MAX bytes; otherwise, and with
+// VS_FLAG_FARFIELD_PER_TARGET, the per-target kernel runs.
+constexpr size_t FFS_PART_MAX = size_t(4) << 30;
+
+FfSymArgs ffs_args(const vs_suspension* h) {
+  const Layout& L = h->L;
+  return FfSymArgs{L.P, L.M, L.nmax, h->ffs.nchunk, h->ffs.ntile, h->ffs.tiles, h->ffs.ctr,
+                   h->p.near_field ? 1 : 0, h->ffs.part, h->B.near_cnt, h->B.near_v, h->err};
+}
+
+template <int R>
+cudaError_t ffs_prepare(int* grid) {
+  const size_t smem = ffs_smem_bytes(32 * R);
+  cudaError_t e = cudaFuncSetAttribute(k_farfield_sym<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_farfield_sym<R>, 32 * FFS_W, smem)) != cudaSuccess)
+    return e;
+  *grid = sms * std::max(per_sm, 1);
+  return cudaSuccess;
+}
+
+cudaError_t ffs_setup(vs_suspension* h) {
+  const Layout& L = h->L;
+  h->ffs.R = 0;
+  const uint64_t off = VS_FLAG_FARFIELD_FP64 | VS_FLAG_FARFIELD_MULTIPOLE | VS_FLAG_FARFIELD_PER_TARGET;
+  if (L.M < 2 || (h->p.flags & off)) return cudaSuccess;
+  if (*std::min_element(L.N.begin(), L.N.end()) != L.nmax) return cudaSuccess;
+  const int R = L.nmax / 32;
+  if (L.nmax % 32 != 0 || !(R == 1 || R == 2 || R == 4)) return cudaSuccess;
+  const int nchunk = (L.M + FFS_V - 1) / FFS_V;
+  if ((size_t)nchunk * (size_t)L.P * sizeof(double2) > FFS_PART_MAX) return cudaSuccess;
+  std::vector<int2> tiles;
+  for (int i = 0; i < nchunk; ++i)  // whole tiles first, the half-empty diagonal ones last
+    for (int j = i + 1; j < nchunk; ++j) tiles.push_back(make_int2(i, j));
+  for (int i = 0; i < nchunk; ++i) tiles.push_back(make_int2(i, i));
+  cudaError_t e;
+  if ((e = dalloc(&h->ffs.tiles, (int64_t)tiles.size())) != cudaSuccess) return e;
+  if ((e = upload(h->ffs.tiles, tiles.data(), (int64_t)tiles.size(), h->stream)) != cudaSuccess) return e;
+  if ((e = dalloc(&h->ffs.part, (int64_t)nchunk * L.P)) != cudaSuccess) return e;
+  if ((e = dalloc(&h->ffs.ctr, 1)) != cudaSuccess) return e;
+  int grid = 0;
+  e = R == 1 ? ffs_prepare<1>(&grid) : R == 2 ? ffs_prepare<2>(&grid) : ffs_prepare<4>(&grid);
+  if (e != cudaSuccess) return e;
+  h->ffs.nchunk = nchunk;
+  h->ffs.ntile = (int)tiles.size();
+  h->ffs.grid = std::min(grid, h->ffs.ntile);
+  h->ffs.R = R;
+  return cudaStreamSynchronize(h->stream);
+}
+
+void launch_far_field_sym(vs_suspension* h) {
+  const FfSymArgs a = ffs_args(h);
+  const size_t smem = ffs_smem_bytes(32 * h->ffs.R);
+  cudaStream_t st = h->stream;
+  cudaMemsetAsync(h->ffs.ctr, 0, sizeof(unsigned), st);
+  if (a.near_mask) cudaMemsetAsync(h->B.near_cnt, 0, h->L.P * sizeof(int), st);
+  const int g = h->ffs.grid;
+  switch (h->ffs.R) {
+    case 1: k_farfield_sym<1><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
+    case 2: k_farfield_sym<2><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
+    default: k_farfield_sym<4><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
+  }
+}
+
 vs_status far_field(vs_suspension* h) {
   const Layout& L = h->L;
   if (L.M < 2) return VS_OK;
@@ -548,6 +624,11 @@ vs_status far_field(vs_suspension* h) {
     VS_LAUNCH(h, "k_farfield_mp", (k_farfield_mp<128, FF_MP_P, 1><<<grid, 128, 0, h->stream>>>(a, h->B.src,
                                                                                              h->B.centre32, h->B.h2,
                                                                                              h->B.mpcoef, h->B.mpa0)));
+  } else if (h->ffs.R > 0) {
+    VS_LAUNCH(h, "k_farfield_sym", launch_far_field_sym(h));
+    const FfSymArgs fa = ffs_args(h);
+    VS_LAUNCH(h, "k_farfield_sym_reduce",
+              k_farfield_sym_reduce<<<(int)((L.P + 255) / 256), 256, 0, h->stream>>>(fa, h->u));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -567,7 +648,9 @@ std::map<std::string, int>& tune_cache() {
 
 vs_status tune_far_field(vs_suspension* h) {
   const Layout& L = h->L;
-  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE))) return VS_OK;
+  if (L.M < 2 || h->ffs.R > 0 ||
+      (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE)))
+    return VS_OK;
   int dev = 0;
   VS_CK(h, cudaGetDevice(&dev), "autotune");
   cudaDeviceProp prop;
@@ -911,6 +994,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near); cudaFree(h->involved);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
+  cudaFree(h->ffs.tiles); cudaFree(h->ffs.part); cudaFree(h->ffs.ctr);
 }
 
 thread_local std::string g_create_msg;
@@ -997,6 +1081,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
   if (tension(h, h->u, 0) != VS_OK) return fail(VS_ERR_CUDA);
   VS_A(cudaGetLastError());
+  VS_A(ffs_setup(h));
   if (tune_far_field(h) != VS_OK) return fail(VS_ERR_CUDA);
   if (geometry(h, h->xy, true) != VS_OK) return fail(VS_ERR_CUDA);  // u back to u_inf after tuning
   h->cur = 0;
@@ -1114,9 +1199,16 @@ vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
 
 vs_status vs_farfield_variant(vs_suspension* h, int32_t set, int32_t* index, int32_t* threads, int32_t* chunk) {
   if (!h || set >= FF_NVARIANTS) return VS_ERR_INVALID_ARG;
-  if (set >= 0 && set != h->ff_variant) {
+  if (set >= 0 && (set != h->ff_variant || h->ffs.R > 0)) {
     h->ff_variant = set;
+    h->ffs.R = 0;  // an explicit per-target launch shape leaves the symmetric kernel
     drop_graphs(h);
+  }
+  if (h->ffs.R > 0) {
+    if (index) *index = -1;
+    if (threads) *threads = 32 * FFS_W;
+    if (chunk) *chunk = FFS_V * h->L.nmax;
+    return VS_OK;
   }
   if (index) *index = h->ff_variant;
   if (threads) *threads = FF_VARIANTS[h->ff_variant].threads;
