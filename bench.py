@@ -32,10 +32,18 @@ sys.path.insert(0, ROOT)
 METRIC = "vesicle-steps/s: hybrid vs plain BIE on one B300 at shape error <=1e-2"
 UNIT = "vesicle-steps/s"
 MUFU_PER_CLK_SM = 16      # special-function results per clock per SM (4 per sub-partition)
+ISSUE_LANES_PER_CLK_SM = 128  # 4 warp schedulers x 32 lanes: one warp instruction each per clock
 N_SM = 148
+# k_farfield_sym: arithmetic instructions per unordered pair of points (18 FP32 + lg2 + rcp: both reactions)
+FFS_INST_PER_PAIR = 20
 # DRAM bytes per point of one far-field launch: ncu dram__bytes of k_farfield_f32 on the 1200 x 64 dense
 # Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
 FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
+# DRAM bytes of one k_farfield_sym launch at 2000 x 64 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# one-pass capture of the bench workload: 3.48 MB read, 195.44 MB written, mostly the per-chunk partial sums
+# that do not stay in L2)
+FFS_DRAM_BYTES = 3.48e6 + 195.44e6
+FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 
 
 def parse():
@@ -238,7 +246,7 @@ def _time_steps(sus, n, stream):
 def long_run_arms(wl, args, stream):
     """Variants of the step against the plain step (all-pairs point sums) from the same state:
     * hybrid: learned relaxation on every other step, exact relaxation on the others and for vesicles in
-      near pairs or within three spacings of another vesicle; the network trained on the GPU on exact
+      near pairs or within four spacings of another vesicle; the network trained on the GPU on exact
       relaxation pairs of a differently seeded suspension (64 snapshots 15 steps apart);
     * farfield_multipole: the plain step with the vesicle-multipole far field;
     * hybrid_multipole: both.
@@ -289,7 +297,7 @@ def long_run_arms(wl, args, stream):
         if cfg.get("mode", 0) == 1:
             out[name]["net"] = net
             out[name]["exact_every"] = exact_every
-            out[name]["fallback"] = ("exact relaxation on every %d-th step and for vesicles within 3 spacings h of "
+            out[name]["fallback"] = ("exact relaxation on every %d-th step and for vesicles within 4 spacings h of "
                                      "another vesicle" % exact_every)
         if cfg.get("farfield_multipole"):
             out[name]["far_field"] = ("order-12 expansions about each vesicle's centre beyond three reach radii, "
@@ -401,6 +409,18 @@ def run_gpu(args):
                 "traffic_source": "ncu dram__bytes at 1200 x 64, scaled by points",
                 "peak_source": "16 MUFU/clk/SM x 148 SMs x median SM clock (derived)",
                 "share_of_step": dom_ms / total_prof}
+    elif dom_name.startswith("k_farfield_sym"):
+        # issue-bound: every instruction of the pair formula takes an issue slot (FP32 pipe ~80%, MUFU ~27%)
+        pairs = (float(wl.offsets[-1]) ** 2 - float(np.sum(wl.counts.astype(np.float64) ** 2))) / 2
+        mhz = clocks.get("sm_mhz") or 1920.0
+        peak_issue = ISSUE_LANES_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
+        achieved = FFS_INST_PER_PAIR * pairs / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "Tinst/s",
+                "frac": achieved / peak_issue, "traffic": FFS_DRAM_BYTES,
+                "traffic_source": FFS_DRAM_SOURCE,
+                "peak_source": "issue: 4 schedulers x 32 lanes x 148 SMs x median SM clock (derived); "
+                               "achieved counts 20 instructions per unordered pair (18 FP32 + lg2 + rcp)",
+                "share_of_step": dom_ms / total_prof}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "share_of_step": dom_ms / total_prof}
@@ -459,8 +479,12 @@ def run_gpu(args):
                 "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(wl, args, {"parallelism": "replicas" if world > 1 else "single GPU",
-                                               "farfield_launch": "%d threads x %d staged source points per CTA "
-                                                                  "(autotuned at create)" % (fv[1], fv[2])}
+                                               "farfield_launch": ("symmetric pair kernel: %d threads per CTA, "
+                                                                   "column chunks of %d points, persistent CTAs"
+                                                                   % (fv[1], fv[2])) if fv[0] < 0 else
+                                                                  ("per-target kernel: %d threads x %d staged source "
+                                                                   "points per CTA (autotuned at create)"
+                                                                   % (fv[1], fv[2]))}
                                     if not args.farfield_multipole else
                                     {"parallelism": "replicas" if world > 1 else "single GPU",
                                      "farfield": "fp32 vesicle multipole beyond three reach radii, point sums "

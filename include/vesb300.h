@@ -98,6 +98,8 @@ typedef struct {
   int32_t exact_every; /* hybrid only: every exact_every-th step (counting from 1) takes the exact
                           relaxation instead of the learned one; 0: never */
   uint64_t flags;    /* VS_FLAG_* */
+  double exact_gap;  /* hybrid only: a vesicle closer than exact_gap point spacings h = L/N (the larger of
+                        the two vesicles') to another vesicle relaxes exactly; 0 selects 4 */
 } vs_params;
 
 typedef struct vs_suspension vs_suspension;

@@ -22,7 +22,7 @@ points, u^n is carried to the new points by its trigonometric interpolant. Algor
 computes the tension before the correction and so do we. One far-field evaluation per step
 (Algorithm 1 needs u^n once). With Params.relax_net set, step 4 is the learned relaxation of the
 hybrid step (relax_learned), except for vesicles in a near pair this step (the target's owner or the
-source vesicle) or within HYBRID_EXACT_GAP spacings of another vesicle, and, with exact_every = m > 0,
+source vesicle) or within exact_gap (default HYBRID_EXACT_GAP) spacings of another vesicle, and, with exact_every = m > 0,
 on every m-th step: those relax exactly, the plain step serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
 too; here they keep the exact relaxation). Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
@@ -37,9 +37,12 @@ from .redistribute import redistribute
 from .spectral import Geometry, eval_interpolant, force
 
 
+HYBRID_EXACT_GAP = 4.0
+
+
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
-                 near_field=False, corr_tol=0.01, relax_net=None, exact_every=0):
+                 near_field=False, corr_tol=0.01, relax_net=None, exact_every=0, exact_gap=HYBRID_EXACT_GAP):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
@@ -47,6 +50,8 @@ class Params:
         # step; with exact_every = m > 0 every m-th step (counting from 1) relaxes exactly instead
         self.relax_net = relax_net
         self.exact_every = int(exact_every)
+        # in a learned step, vesicles within exact_gap spacings h of another vesicle relax exactly
+        self.exact_gap = float(exact_gap)
 
 
 def relax_learned(x, y, net):
@@ -146,7 +151,7 @@ class Suspension:
             owner = np.repeat(np.arange(len(self.xs)), [len(x) for x in self.xs])
             for t, v in self.near_pairs:
                 exact.update((int(owner[t]), int(v)))
-            exact.update(close_vesicles(self.xs, self.ys, HYBRID_EXACT_GAP))
+            exact.update(close_vesicles(self.xs, self.ys, p.exact_gap))
         nxs, nys, nsig, vel = [], [], [], []
         for v, (x, y) in enumerate(zip(self.xs, self.ys)):
             ux, uy = u[v]
@@ -162,9 +167,6 @@ class Suspension:
             nsig.append(sig)
             vel.append(np.concatenate([ux, uy]))
         self.xs, self.ys, self.sig, self.velocity = nxs, nys, nsig, vel
-
-
-HYBRID_EXACT_GAP = 3.0
 
 
 def close_vesicles(xs, ys, gap_h):

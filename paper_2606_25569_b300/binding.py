@@ -110,7 +110,8 @@ class VsError(RuntimeError):
 class VsParams(ctypes.Structure):
     _fields_ = [("kappa_b", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
                 ("corr_tol", ctypes.c_double), ("mode", ctypes.c_int32), ("near_field", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("exact_every", ctypes.c_int32), ("flags", ctypes.c_uint64)]
+                ("use_graph", ctypes.c_int32), ("exact_every", ctypes.c_int32), ("flags", ctypes.c_uint64),
+                ("exact_gap", ctypes.c_double)]
 
 
 class VsFlow(ctypes.Structure):
@@ -142,7 +143,7 @@ class Suspension:
     def __init__(self, xy, offsets, kappa=1.0, mu=1.0, dt=1e-4, corr_tol=0.01, flow_kind=0,
                  flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0,
                  use_graph=False, direct_fp64=False, autotune=True, tc_gemm=False, exact_every=0,
-                 farfield_multipole=False, farfield_per_target=False):
+                 farfield_multipole=False, farfield_per_target=False, exact_gap=0.0):
         L = lib()
         self._h = ctypes.c_void_p()
         xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -154,7 +155,7 @@ class Suspension:
                  | (VS_FLAG_FARFIELD_MULTIPOLE if farfield_multipole else 0)
                  | (VS_FLAG_FARFIELD_PER_TARGET if farfield_per_target else 0))
         p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0,
-                     int(exact_every), flags)
+                     int(exact_every), flags, float(exact_gap))
         f = VsFlow(int(flow_kind), 0, (ctypes.c_double * 4)(*[float(v) for v in flow_p]))
         st = L.vs_create(_ptr(xy), _ptr(off), self.M, ctypes.byref(p), ctypes.byref(f), _stream(stream),
                          ctypes.byref(self._h))

@@ -36,6 +36,11 @@
 
 namespace vs {
 
+#ifndef FFS_UNROLL
+#define FFS_UNROLL 16
+#endif
+constexpr int FFS_STEPS_UNROLLED = FFS_UNROLL;  // steps of the 32-step lane rotation unrolled together
+
 constexpr int FFS_V = 16;  // vesicles per chunk
 constexpr int FFS_W = 8;   // warps per CTA
 
@@ -73,7 +78,7 @@ __device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int la
                                          float (&mc)[R]) {
   const int from = (lane + 1) & 31;
   const float4* base = colB + lane;
-#pragma unroll 4
+#pragma unroll FFS_STEPS_UNROLLED
   for (int k = 0; k < 32; ++k) {
     float4 s[R];
 #pragma unroll

@@ -31,7 +31,7 @@ using namespace vs;
 
 // Hybrid steps relax exactly every vesicle within this many point spacings h = L/N (the larger of the two
 // vesicles') of another vesicle.
-constexpr double HYBRID_EXACT_GAP = 3.0;
+constexpr double HYBRID_EXACT_GAP = 4.0;  // default of vs_params.exact_gap
 constexpr int CORR_NEWTON_ITERS = 16;  // Newton steps on the KKT system (linear convergence with the FP32 Jacobian)
 
 namespace {
@@ -863,6 +863,8 @@ vs_status correction(vs_suspension* h) {
   return VS_OK;
 }
 
+double exact_gap(const vs_suspension* h) { return h->p.exact_gap > 0.0 ? h->p.exact_gap : HYBRID_EXACT_GAP; }
+
 // Hybrid steps use the learned relaxation except every exact_every-th step (counting from 1), which takes
 // the exact one.
 inline bool learned_step(const vs_suspension* h) {
@@ -897,13 +899,13 @@ vs_status step_once(vs_suspension* h) {
     if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
     if (h->p.near_field && M > 1) {
       // the plain step is the fallback of the learned one: vesicles in a near pair, or closer to another
-      // vesicle than HYBRID_EXACT_GAP spacings, relax exactly
+      // vesicle than exact_gap (default HYBRID_EXACT_GAP) spacings, relax exactly
       VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
       const int tgrid = (int)((L.P + 127) / 128);
       VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
                                                                                      h->B.near_v, h->involved));
       VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
-                                                                         HYBRID_EXACT_GAP, h->involved));
+                                                                         exact_gap(h), h->involved));
       if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
     }
   } else {
@@ -979,6 +981,7 @@ bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
   }
   if (p->mode != 0 && p->mode != 1) { msg = "mode must be 0 (plain) or 1 (hybrid)"; return false; }
   if (p->exact_every < 0) { msg = "exact_every must be >= 0"; return false; }
+  if (!(p->exact_gap >= 0.0) || !std::isfinite(p->exact_gap)) { msg = "exact_gap must be finite and >= 0"; return false; }
   if (f->kind < 0 || f->kind > 3) { msg = "unknown flow kind"; return false; }
   if ((f->kind == 2 || f->kind == 3) && !(f->p[1] != 0.0)) { msg = "flow length scale p[1] must be non-zero"; return false; }
   return true;

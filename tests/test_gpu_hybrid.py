@@ -182,8 +182,10 @@ def test_hybrid_near_pairs_fall_back_to_exact_relaxation():
     g.close()
 
 
-def test_hybrid_close_vesicles_relax_exactly():
-    # two vesicles about two spacings apart (no near pair, within three spacings) and a far one
+@pytest.mark.parametrize("gap", [3.0, 6.0])
+def test_hybrid_close_vesicles_relax_exactly(gap):
+    # two vesicles about two spacings apart (no near pair, within three spacings) and a third one, closer
+    # than six spacings to the others: exact_gap = 3 relaxes the first two exactly, 6 all three
     from .test_gpu_parity import _close_pair
     xs, ys = _close_pair(gap_h=2.0)
     N, M = 32, 3
@@ -192,10 +194,10 @@ def test_hybrid_close_vesicles_relax_exactly():
     rng = np.random.default_rng(9)
     params = init_params(dims, rng).astype(np.float32).astype(np.float64)
     scale = 2e-4
-    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0.0, 0.0, 0.0), near_field=True)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0.0, 0.0, 0.0), near_field=True, exact_gap=gap)
     o = OracleSuspension(xs, ys, Params(relax_net=(dims, params, scale, 15), **kw))
     from oracle.step import close_vesicles
-    assert close_vesicles(o.xs, o.ys, 3.0) == {0, 1}
+    assert close_vesicles(o.xs, o.ys, gap) == ({0, 1} if gap == 3.0 else {0, 1, 2})
     stream = torch.cuda.current_stream()
     net = binding.Mlp(dims, max_batch=M, stream=stream)
     net.set_params(params)
