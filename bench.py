@@ -233,6 +233,37 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def farfield_alone(stream, reps=10):
+    """The far-field sum alone on the 2000 x 128 box (256,000 sources and targets, all pairs of different
+    vesicles, no near mask) through vs_farfield_eval: the symmetric kernel (precision 0) and the per-target
+    kernel (precision 3), CUDA events over `reps` evaluations after 3 warm-up ones."""
+    import torch
+    from paper_2606_25569_b300 import binding
+    from paper_2606_25569_b300.workloads import farfield_box
+    wl, fx, fy = farfield_box()
+    off = wl.offsets
+    xy = torch.as_tensor(wl.flat_xy(), device="cuda")
+    f = torch.as_tensor(np.concatenate([np.concatenate([a, b]) for a, b in zip(fx, fy)]), device="cuda")
+    u = torch.empty(2 * int(off[-1]), dtype=torch.float64, device="cuda")
+    pairs = float(off[-1]) ** 2 - float(np.sum(wl.counts.astype(np.float64) ** 2))
+    out = {"workload": "far field alone: 2000 vesicles x 128 points in a 20 x 20 box, densities N(0,1)",
+           "ordered_pairs": pairs, "unit": "pairs/s"}
+    for name, prec in (("symmetric", 0), ("per_target", 3)):
+        plan = binding.FarFieldPlan(off, mu=1.0, near_mask=False, precision=prec, stream=stream)
+        for _ in range(3):
+            plan.eval(xy, f, u)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.eval(xy, f, u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        plan.close()
+        out[name] = {"ms": ms, "value": pairs / (ms * 1e-3)}
+    return out
+
+
 def _time_steps(sus, n, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -466,6 +497,7 @@ def run_gpu(args):
                   "ms_per_step": ms_ss, "value": world * wl.M / (ms_ss * 1e-3), "unit": UNIT,
                   "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
 
+    ff_alone = farfield_alone(stream) if rank == 0 else None
     arms = {}
     if rank == 0 and not args.no_hybrid:
         arms = long_run_arms(wl, args, stream)
@@ -493,6 +525,7 @@ def run_gpu(args):
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
                 "steady_state": steady, "hybrid": arms.get("hybrid"),
                 "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
+                "farfield_2000x128": ff_alone,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -234,8 +234,10 @@ void vs_destroy(vs_suspension* s);
  *   G = (1/4 pi mu)(-log|r| I + r r^T / |r|^2).
  * A plan holds the layout and its device buffers.
  *  offsets     host, M+1 int64 as in vs_create.
- *  precision   0: compensated FP32 (vesicle-relative coordinates), 1: FP64, 2: FP32 with vesicle
- *              multipole expansions for far source vesicles (VS_FLAG_FARFIELD_MULTIPOLE).
+ *  precision   0: compensated FP32 (vesicle-relative coordinates; the symmetric pair kernel when every
+ *              vesicle has 32, 64 or 128 points, see VS_FLAG_FARFIELD_PER_TARGET), 1: FP64, 2: FP32 with
+ *              vesicle multipole expansions for far source vesicles (VS_FLAG_FARFIELD_MULTIPOLE),
+ *              3: compensated FP32 with the per-target kernel whatever the point counts.
  * vs_farfield_eval takes DEVICE pointers in CSR blocks: xy (2P), f (2P); writes u (2P, device,
  * overwritten) on the plan's stream. Asynchronous.
  */

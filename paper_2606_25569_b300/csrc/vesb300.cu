@@ -274,6 +274,19 @@ struct vs_mlp {
   std::string msg;
 };
 
+// Symmetric FP32 far field (k_farfield_sym): tile list, tile counter and per-chunk partial sums; R = points
+// per lane (N / 32), 0 when the suspension or plan uses another far-field kernel.
+struct FfSymState {
+  int R = 0, nchunk = 0, ntile = 0, grid = 0;
+  int2* tiles = nullptr;
+  double2* part = nullptr;
+  unsigned* ctr = nullptr;
+  void release() {
+    cudaFree(tiles); cudaFree(part); cudaFree(ctr);
+    *this = FfSymState{};
+  }
+};
+
 struct vs_suspension {
   Layout L;
   DevLayout D;
@@ -305,13 +318,7 @@ struct vs_suspension {
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t graph_launches[4] = {0, 0, 0, 0};
   int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
-  // symmetric FP32 far field (k_farfield_sym): used when R > 0
-  struct {
-    int R = 0, nchunk = 0, ntile = 0, grid = 0;
-    int2* tiles = nullptr;
-    double2* part = nullptr;
-    unsigned* ctr = nullptr;
-  } ffs;
+  FfSymState ffs;                                  // symmetric FP32 far field, used when ffs.R > 0
   std::string msg;
 };
 
@@ -319,6 +326,7 @@ struct vs_farfield_plan {
   Layout L;
   DevLayout D;
   SourceBufs B;
+  FfSymState ffs;
   double mu = 1.0;
   int near_mask = 0, precision = 0;
   cudaStream_t stream = nullptr;
@@ -547,10 +555,8 @@ FarFieldArgs far_field_args(vs_suspension* h) {
 // VS_FLAG_FARFIELD_PER_TARGET, the per-target kernel runs.
 constexpr size_t FFS_PART_MAX = size_t(4) << 30;
 
-FfSymArgs ffs_args(const vs_suspension* h) {
-  const Layout& L = h->L;
-  return FfSymArgs{L.P, L.M, L.nmax, h->ffs.nchunk, h->ffs.ntile, h->ffs.tiles, h->ffs.ctr,
-                   h->p.near_field ? 1 : 0, h->ffs.part, h->B.near_cnt, h->B.near_v, h->err};
+FfSymArgs ffs_args(const FfSymState& f, const Layout& L, int near_mask, const SourceBufs& B, unsigned* err) {
+  return FfSymArgs{L.P, L.M, L.nmax, f.nchunk, f.ntile, f.tiles, f.ctr, near_mask, f.part, B.near_cnt, B.near_v, err};
 }
 
 template <int R>
@@ -567,11 +573,11 @@ cudaError_t ffs_prepare(int* grid) {
   return cudaSuccess;
 }
 
-cudaError_t ffs_setup(vs_suspension* h) {
-  const Layout& L = h->L;
-  h->ffs.R = 0;
-  const uint64_t off = VS_FLAG_FARFIELD_FP64 | VS_FLAG_FARFIELD_MULTIPOLE | VS_FLAG_FARFIELD_PER_TARGET;
-  if (L.M < 2 || (h->p.flags & off)) return cudaSuccess;
+// Sets f up for the layout when `wanted` and the layout is eligible (equal N of 32, 64 or 128, M >= 2,
+// partial sums within FFS_PART_MAX); leaves f.R = 0 otherwise.
+cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t st) {
+  f.R = 0;
+  if (!wanted || L.M < 2) return cudaSuccess;
   if (*std::min_element(L.N.begin(), L.N.end()) != L.nmax) return cudaSuccess;
   const int R = L.nmax / 32;
   if (L.nmax % 32 != 0 || !(R == 1 || R == 2 || R == 4)) return cudaSuccess;
@@ -582,32 +588,34 @@ cudaError_t ffs_setup(vs_suspension* h) {
     for (int j = i + 1; j < nchunk; ++j) tiles.push_back(make_int2(i, j));
   for (int i = 0; i < nchunk; ++i) tiles.push_back(make_int2(i, i));
   cudaError_t e;
-  if ((e = dalloc(&h->ffs.tiles, (int64_t)tiles.size())) != cudaSuccess) return e;
-  if ((e = upload(h->ffs.tiles, tiles.data(), (int64_t)tiles.size(), h->stream)) != cudaSuccess) return e;
-  if ((e = dalloc(&h->ffs.part, (int64_t)nchunk * L.P)) != cudaSuccess) return e;
-  if ((e = dalloc(&h->ffs.ctr, 1)) != cudaSuccess) return e;
+  if ((e = dalloc(&f.tiles, (int64_t)tiles.size())) != cudaSuccess) return e;
+  if ((e = upload(f.tiles, tiles.data(), (int64_t)tiles.size(), st)) != cudaSuccess) return e;
+  if ((e = dalloc(&f.part, (int64_t)nchunk * L.P)) != cudaSuccess) return e;
+  if ((e = dalloc(&f.ctr, 1)) != cudaSuccess) return e;
   int grid = 0;
   e = R == 1 ? ffs_prepare<1>(&grid) : R == 2 ? ffs_prepare<2>(&grid) : ffs_prepare<4>(&grid);
   if (e != cudaSuccess) return e;
-  h->ffs.nchunk = nchunk;
-  h->ffs.ntile = (int)tiles.size();
-  h->ffs.grid = std::min(grid, h->ffs.ntile);
-  h->ffs.R = R;
-  return cudaStreamSynchronize(h->stream);
+  f.nchunk = nchunk;
+  f.ntile = (int)tiles.size();
+  f.grid = std::min(grid, f.ntile);
+  f.R = R;
+  return cudaStreamSynchronize(st);
 }
 
-void launch_far_field_sym(vs_suspension* h) {
-  const FfSymArgs a = ffs_args(h);
-  const size_t smem = ffs_smem_bytes(32 * h->ffs.R);
-  cudaStream_t st = h->stream;
-  cudaMemsetAsync(h->ffs.ctr, 0, sizeof(unsigned), st);
-  if (a.near_mask) cudaMemsetAsync(h->B.near_cnt, 0, h->L.P * sizeof(int), st);
-  const int g = h->ffs.grid;
-  switch (h->ffs.R) {
-    case 1: k_farfield_sym<1><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
-    case 2: k_farfield_sym<2><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
-    default: k_farfield_sym<4><<<g, 32 * FFS_W, smem, st>>>(a, h->B.src, h->B.centre32, h->B.h2); break;
+// Zero the tile counter (and the near counts), then the pair kernel. u is added to by ffs_reduce.
+void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cudaStream_t st) {
+  const size_t smem = ffs_smem_bytes(32 * f.R);
+  cudaMemsetAsync(f.ctr, 0, sizeof(unsigned), st);
+  if (a.near_mask) cudaMemsetAsync(B.near_cnt, 0, a.P * sizeof(int), st);
+  switch (f.R) {
+    case 1: k_farfield_sym<1><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
+    case 2: k_farfield_sym<2><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
+    default: k_farfield_sym<4><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
   }
+}
+
+void ffs_reduce(const FfSymArgs& a, double* u, cudaStream_t st) {
+  k_farfield_sym_reduce<<<(int)((a.P + 255) / 256), 256, 0, st>>>(a, u);
 }
 
 vs_status far_field(vs_suspension* h) {
@@ -625,10 +633,9 @@ vs_status far_field(vs_suspension* h) {
                                                                                              h->B.centre32, h->B.h2,
                                                                                              h->B.mpcoef, h->B.mpa0)));
   } else if (h->ffs.R > 0) {
-    VS_LAUNCH(h, "k_farfield_sym", launch_far_field_sym(h));
-    const FfSymArgs fa = ffs_args(h);
-    VS_LAUNCH(h, "k_farfield_sym_reduce",
-              k_farfield_sym_reduce<<<(int)((L.P + 255) / 256), 256, 0, h->stream>>>(fa, h->u));
+    const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
+    VS_LAUNCH(h, "k_farfield_sym", ffs_launch(h->ffs, fa, h->B, h->stream));
+    VS_LAUNCH(h, "k_farfield_sym_reduce", ffs_reduce(fa, h->u, h->stream));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -997,7 +1004,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near); cudaFree(h->involved);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
-  cudaFree(h->ffs.tiles); cudaFree(h->ffs.part); cudaFree(h->ffs.ctr);
+  h->ffs.release();
 }
 
 thread_local std::string g_create_msg;
@@ -1084,7 +1091,8 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (build_operators(h, h->xy, 0, nullptr) != VS_OK) return fail(VS_ERR_CUDA);
   if (tension(h, h->u, 0) != VS_OK) return fail(VS_ERR_CUDA);
   VS_A(cudaGetLastError());
-  VS_A(ffs_setup(h));
+  VS_A(ffs_setup(h->ffs, L, !(h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_FARFIELD_MULTIPOLE |
+                                            VS_FLAG_FARFIELD_PER_TARGET)), h->stream));
   if (tune_far_field(h) != VS_OK) return fail(VS_ERR_CUDA);
   if (geometry(h, h->xy, true) != VS_OK) return fail(VS_ERR_CUDA);  // u back to u_inf after tuning
   h->cur = 0;
@@ -1370,11 +1378,12 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
     g_create_msg = h->msg;
     h->D.release();
     h->B.release();
+    h->ffs.release();
     cudaFree(h->err);
     delete h;
     return s;
   };
-  if (!(mu > 0) || precision < 0 || precision > 2) { h->msg = "mu must be > 0, precision 0, 1 or 2"; return fail(VS_ERR_INVALID_ARG); }
+  if (!(mu > 0) || precision < 0 || precision > 3) { h->msg = "mu must be > 0, precision 0 to 3"; return fail(VS_ERR_INVALID_ARG); }
   if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
   h->mu = mu;
   h->near_mask = near_mask ? 1 : 0;
@@ -1384,7 +1393,8 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
   if ((e = upload_layout(h->L, h->D, h->stream)) != cudaSuccess ||
       (e = h->B.alloc(h->L.P, h->L.M)) != cudaSuccess || (e = dalloc(&h->err, 1)) != cudaSuccess ||
       (e = cudaMemset(h->err, 0, sizeof(unsigned))) != cudaSuccess ||
-      (e = cudaMemset(h->B.near_cnt, 0, h->L.P * sizeof(int))) != cudaSuccess) {
+      (e = cudaMemset(h->B.near_cnt, 0, h->L.P * sizeof(int))) != cudaSuccess ||
+      (e = ffs_setup(h->ffs, h->L, precision == 0, h->stream)) != cudaSuccess) {
     cuda_fail(h->msg, e, "vs_farfield_plan_create");
     return fail(e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
   }
@@ -1409,6 +1419,10 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
     k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
     k_farfield_mp<128, FF_MP_P, 1><<<(int)((L.P + 127) / 128), 128, 0, h->stream>>>(a, h->B.src, h->B.centre32,
                                                                                     h->B.h2, h->B.mpcoef, h->B.mpa0);
+  } else if (h->ffs.R > 0) {
+    const FfSymArgs fa = ffs_args(h->ffs, L, h->near_mask, h->B, h->err);
+    ffs_launch(h->ffs, fa, h->B, h->stream);
+    ffs_reduce(fa, u, h->stream);
   } else {
     k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
   }
@@ -1437,6 +1451,7 @@ void vs_farfield_plan_destroy(vs_farfield_plan* h) {
   cudaStreamSynchronize(h->stream);
   h->D.release();
   h->B.release();
+  h->ffs.release();
   cudaFree(h->err);
   delete h;
 }

@@ -89,3 +89,21 @@ def test_symmetric_far_field_is_deterministic():
         g.close()
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
     assert runs[0][2] == runs[1][2] > 0
+
+
+def test_far_field_plan_symmetric_and_per_target_agree():
+    # vs_farfield_eval: precision 0 (symmetric kernel for equal N = 32/64/128) against 3 (per target), near mask on
+    xs, ys = _grid(37, 128, seed=12, close_pair=True)
+    rng = np.random.default_rng(12)
+    f = np.concatenate([np.concatenate([rng.standard_normal(len(x)), rng.standard_normal(len(x))]) for x in xs])
+    off = offsets(xs)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    out = {}
+    for prec in (0, 3):
+        plan = binding.FarFieldPlan(off, mu=0.7, near_mask=True, precision=prec)
+        u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+        plan.eval(dev(csr(xs, ys)), dev(f), u)
+        out[prec] = (u.cpu().numpy(), plan.counters())
+        plan.close()
+    assert _rel_l2(out[0][0], out[3][0]) <= 1e-5
+    assert out[0][1]["near_pairs"] == out[3][1]["near_pairs"] > 0
