@@ -303,11 +303,26 @@ struct GemmPrefetch<OpT32> {
   static constexpr bool value = false;
 };
 
+// Position of tile row (column) r in a shared-memory row of the k_bgemm operand tiles: the four rows
+// (columns) one thread multiplies, r, r + 16, r + 32, r + 48, sit side by side, so that one 16-byte (float)
+// or two (double) shared-memory loads fetch them.
+__device__ __forceinline__ int gperm(int r) { return 4 * (r & 15) + (r >> 4); }
+constexpr int GPAD = 4;  // row padding: rows of GT + GPAD elements stay 16-byte aligned
+
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
 template <class Op>
 __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ active) {
   using T = typename Op::T;
-  __shared__ T As[GK][GT + 1];
-  __shared__ T Bs[GK][GT + 1];
+  __shared__ __align__(16) T As[GK][GT + GPAD];
+  __shared__ __align__(16) T Bs[GK][GT + GPAD];
   const int v = op.c.vi.vid(blockIdx.z);
   if (active && !active[v]) return;
   const int N = op.c.vi.N[v];
@@ -345,8 +360,8 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int e = tid + 256 * q;
-      As[e % GK][e / GK] = ra[q];
-      Bs[e / GT][e % GT] = rb[q];
+      As[e % GK][gperm(e / GK)] = ra[q];
+      Bs[e / GT][gperm(e % GT)] = rb[q];
     }
   };
   constexpr bool PF = GemmPrefetch<Op>::value;
@@ -358,12 +373,12 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
       for (int e = tid; e < GK * GT; e += 256) {
         const int kk = e % GK, rr = e / GK;
         const int gi = r0 + rr, gk = k0 + kk;
-        As[kk][rr] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
+        As[kk][gperm(rr)] = (gi < m && gk < K) ? op.a(v, N, gi, gk) : T(0);
       }
       for (int e = tid; e < GK * GT; e += 256) {
         const int kk = e / GT, cc = e % GT;
         const int gj = c0 + cc, gk = k0 + kk;
-        Bs[kk][cc] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
+        Bs[kk][gperm(cc)] = (gj < n && gk < K) ? op.b(v, N, gk, gj) : T(0);
       }
     }
     __syncthreads();
@@ -373,10 +388,8 @@ __global__ void __launch_bounds__(256) k_bgemm(Op op, const int* __restrict__ ac
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
       T av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][tr + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tc + 16 * b];
+      ld4(&As[kk][4 * tr], av);  // rows tr + 16 a
+      ld4(&Bs[kk][4 * tc], bv);  // columns tc + 16 b
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
