@@ -516,6 +516,15 @@ __global__ void __launch_bounds__(256) k_lu_smem(Geo geo, unsigned* err, const i
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = As[e];
 }
 
+// Reciprocal of a Gauss-Jordan pivot: the hardware approximation (rcp.approx, within one unit in the last
+// place); the FP32 inverses only precondition refinement, and the IEEE division's longer sequence sat on
+// the critical path of every elimination step.
+__device__ __forceinline__ float gj_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // In-place FP32 inverse of the n x n matrix at geo (n <= 16 RA = TC RB) by Gauss-Jordan exchange steps
 // with partial pivoting: step k takes as pivot p the row not yet used with the largest |T[p][k]| (first
 // wins) and exchanges equation p with unknown k,
@@ -609,7 +618,7 @@ __device__ void gj_invert(const float* src, float* dst, int n, unsigned* err) {
       __syncthreads();
       float pv = colb[buf][pr * RA + pa];
       if (bad || !(pv != 0.f)) { bad = true; pv = 1.f; }
-      const float ip = 1.f / pv;
+      const float ip = gj_rcp(pv);
       float c[RA];
       float2 u[H];
       if constexpr (RA >= 4) {
@@ -663,6 +672,7 @@ __device__ void gj_invert(const float* src, float* dst, int n, unsigned* err) {
 // writes nothing (uniformly across the CTA), and the caller runs the pivoting elimination. Otherwise the
 // result is the inverse in place (inv[i][j] = T[i][j], no permutation).
 constexpr float GJ_NP_TOL = 1e-4f;
+
 template <int RA, int RB, int TC>
 __device__ bool gj_invert_np(const float* src, float* dst, int n) {
   static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB, "square grid of pairs");
@@ -727,7 +737,7 @@ __device__ bool gj_invert_np(const float* src, float* dst, int n) {
       __syncthreads();
       float pv = colb[buf][pr * RA + pa];
       if (!(fabsf(pv) > thr)) { ok = false; pv = 1.f; }
-      const float ip = 1.f / pv;
+      const float ip = gj_rcp(pv);
       float c[RA];
       float2 u[H];
       if constexpr (RA >= 4) {
@@ -787,10 +797,13 @@ struct DenseGeo32 {
   __device__ float* A(int v) const { return base + (int64_t)v * nn * nn; }
 };
 
+// CTAs per SM the register allocation must allow: 128-thread shapes (64 x 64 matrices) 5, else 2.
+#define GJ_MIN_CTAS(TC) ((TC) == 8 ? 5 : 2)
+
 // In-place inverse of matrix blockIdx.x of geo; fallbacks (may be null) counts the matrices that needed
 // the pivoting elimination.
 template <int RA, int RB, int TC, class Geo>
-__global__ void __launch_bounds__(16 * TC, 2) k_gj_inverse(Geo geo, unsigned* err, const int* __restrict__ active,
+__global__ void __launch_bounds__(16 * TC, GJ_MIN_CTAS(TC)) k_gj_inverse(Geo geo, unsigned* err, const int* __restrict__ active,
                                                            int* fallbacks) {
   const int v = geo.vid(blockIdx.x);
   if (active && !active[v]) return;
