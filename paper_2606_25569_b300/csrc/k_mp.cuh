@@ -29,7 +29,7 @@ constexpr int MP_MAXIT = 10;
 // CTA sizes of the refinement kernels: 128 threads when there are many vesicles per SM to hide the
 // memory latency, 256 when a few large vesicles leave the SMs short of work (mp_threads)
 constexpr int MP_THREADS = 128, MP_THREADS_WIDE = 256;
-constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10;
+constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10, MP_CONTRACT = 1e-3;
 enum : unsigned { ERR_REFINE = 32u };
 
 __device__ inline double block_max_abs(double v, double* red) {
@@ -118,8 +118,12 @@ __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols
 
 // Convergence test of a refinement: stop once the update is at the rounding floor of the residual
 // arithmetic, or has stopped shrinking after falling below MP_STALL of the iterate.
+// Stop when the update is below MP_FLOOR of the iterate; or below MP_STALL and either no longer shrinking
+// (rounding floor of the residual) or shrinking by MP_CONTRACT or more a step, in which case the error
+// left after it is about MP_CONTRACT times the update, under MP_FLOOR of the iterate (this saves the
+// step that would only confirm it).
 __device__ __forceinline__ bool mp_done(double upd, double prev, double top) {
-  return upd <= MP_FLOOR * top || (upd <= MP_STALL * top && upd >= 0.5 * prev);
+  return upd <= MP_FLOOR * top || (upd <= MP_STALL * top && (upd >= 0.5 * prev || upd <= MP_CONTRACT * prev));
 }
 
 __device__ inline void mp_load_geom(MpShared& sh, const double* tab, const double* sa, const double* tx,
