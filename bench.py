@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--farfield-multipole", action="store_true",
                     help="time the plain step with the vesicle-multipole far field (not the headline configuration)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
+    ap.add_argument("--no-farfield-alone", action="store_true", help="skip the far field alone on the 2000 x 128 box")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
@@ -497,7 +498,7 @@ def run_gpu(args):
                   "ms_per_step": ms_ss, "value": world * wl.M / (ms_ss * 1e-3), "unit": UNIT,
                   "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
 
-    ff_alone = farfield_alone(stream) if rank == 0 else None
+    ff_alone = farfield_alone(stream) if rank == 0 and not args.no_farfield_alone else None
     arms = {}
     if rank == 0 and not args.no_hybrid:
         arms = long_run_arms(wl, args, stream)
