@@ -107,3 +107,27 @@ def test_far_field_plan_symmetric_and_per_target_agree():
         plan.close()
     assert _rel_l2(out[0][0], out[3][0]) <= 1e-5
     assert out[0][1]["near_pairs"] == out[3][1]["near_pairs"] > 0
+
+
+@pytest.mark.parametrize("precision", [0, 3])
+def test_near_list_overflow_is_reported(precision):
+    # ten small circles pass within 0.001 of one point of a larger vesicle: that target has ten near source
+    # vesicles, more than a near list holds (8); both kernels flag the overflow (error bit 8)
+    rng = np.random.default_rng(3)
+    x0, y0 = vesicle_outline(32, 0.8, 1.0, 1e-2, rng, 0.0)
+    xs, ys = [x0], [y0]
+    th = 2 * np.pi * np.arange(32) / 32
+    for v in range(10):
+        phi = 2 * np.pi * v / 10
+        cx, cy = x0[0] + 0.051 * np.cos(phi), y0[0] + 0.051 * np.sin(phi)
+        xs.append(cx + 0.05 * np.cos(th + phi + np.pi))  # point 0 of each circle 0.001 from (x0[0], y0[0])
+        ys.append(cy + 0.05 * np.sin(th + phi + np.pi))
+    off = offsets(xs)
+    f = np.ones(2 * off[-1])
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    plan = binding.FarFieldPlan(off, mu=1.0, near_mask=True, precision=precision)
+    u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+    plan.eval(dev(csr(xs, ys)), dev(f), u)
+    c = plan.counters()
+    plan.close()
+    assert c["err"] & 8
