@@ -15,9 +15,9 @@
 //     y = Li32 r2, dx = Ai32 (r1 + dt T32 y), dsigma = y - W32 dx   (W32 = Li32 P B32,
 //     A32 = I - dt (B32 - T32 W32)): the exact block elimination of the FP32 system.
 // Li32 and Ai32 are explicit FP32 inverses (k_gj_inverse), so every correction is a few FP32 mat-vecs
-// that all warps share. Iterates are kept in FP64. Each refinement stops at the rounding floor of the
-// residual arithmetic (mp_done; at most MP_MAXIT steps); an update above MP_FAIL of the iterate at the
-// end sets ERR_REFINE.
+// that all warps share. Iterates are kept in FP64. Each refinement stops once the error estimated from its
+// contraction is below MP_LEFT of the iterate or its update reaches the rounding floor of the residual
+// arithmetic (mp_done; at most MP_MAXIT steps); an estimated error above MP_FAIL at the end sets ERR_REFINE.
 #pragma once
 #include "common.cuh"
 #include "k_dense.cuh"
@@ -29,7 +29,7 @@ constexpr int MP_MAXIT = 10;
 // CTA sizes of the refinement kernels: 128 threads when there are many vesicles per SM to hide the
 // memory latency, 256 when a few large vesicles leave the SMs short of work (mp_threads)
 constexpr int MP_THREADS = 128, MP_THREADS_WIDE = 256;
-constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10, MP_CONTRACT = 1e-3;
+constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10, MP_LEFT = 1e-13;
 enum : unsigned { ERR_REFINE = 32u };
 
 __device__ inline double block_max_abs(double v, double* red) {
@@ -116,14 +116,16 @@ __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols
   __syncthreads();
 }
 
-// Convergence test of a refinement: stop once the update is at the rounding floor of the residual
-// arithmetic, or has stopped shrinking after falling below MP_STALL of the iterate.
-// Stop when the update is below MP_FLOOR of the iterate; or below MP_STALL and either no longer shrinking
-// (rounding floor of the residual) or shrinking by MP_CONTRACT or more a step, in which case the error
-// left after it is about MP_CONTRACT times the update, under MP_FLOOR of the iterate (this saves the
-// step that would only confirm it).
+// Error left in the iterate after an update of size upd that followed one of size prev, for an iteration
+// that contracts at the observed rate upd / prev: upd^2 / prev (and at most upd).
+__device__ __forceinline__ double mp_left(double upd, double prev) { return fmin(upd, upd * (upd / prev)); }
+
+// Convergence test of a refinement: stop once the estimated error left is below MP_LEFT of the iterate
+// (with FP32 inverses contracting by about 3e-7 a step this is after the first residual step), or the
+// update is below MP_FLOOR, or has stopped shrinking after falling below MP_STALL (the rounding floor of
+// the residual arithmetic).
 __device__ __forceinline__ bool mp_done(double upd, double prev, double top) {
-  return upd <= MP_FLOOR * top || (upd <= MP_STALL * top && (upd >= 0.5 * prev || upd <= MP_CONTRACT * prev));
+  return mp_left(upd, prev) <= MP_LEFT * top || upd <= MP_FLOOR * top || (upd <= MP_STALL * top && upd >= 0.5 * prev);
 }
 
 __device__ inline void mp_load_geom(MpShared& sh, const double* tab, const double* sa, const double* tx,
@@ -232,7 +234,7 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
                            float2* w, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) { s[i] = 0.0; e[i] = g[i]; }
   __syncthreads();
-  double upd = 1e300, top = 0.0;
+  double upd = 1e300, top = 0.0, prev_upd = 1e300;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it > 0) {
       for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = df_of(s[i]);
@@ -255,9 +257,10 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
     const double prev = upd;
     upd = block_max_abs(du, sh.red);
     top = block_max_abs(sv, sh.red);
+    prev_upd = prev;
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
-  return upd <= MP_FAIL * top || top == 0.0;
+  return mp_left(upd, prev_upd) <= MP_FAIL * top || top == 0.0;
 }
 
 // X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s.
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
   const float* W32 = base32 + MatLayout::W * NN;
   const float* Ainv = base32 + ainv_sub * NN;  // Ai32
   const float2 mk = df_of(-kappa);
-  double upd = 1e300, top = 0.0;
+  double upd = 1e300, top = 0.0, prev_upd = 1e300;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it == 0) {
       for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r];
@@ -401,10 +404,11 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
     const double prev = upd;
     upd = block_max_abs(du, sh.red);
     top = block_max_abs(xv, sh.red);
+    prev_upd = prev;
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
   for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) xy_out[2 * o + r] = x[r] + cen[r < N ? 0 : 1];
-  if (!(upd <= MP_FAIL * top) && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
+  if (!(mp_left(upd, prev_upd) <= MP_FAIL * top) && threadIdx.x == 0) atomicOr(err, ERR_REFINE);
 }
 
 }  // namespace vs
