@@ -325,15 +325,18 @@ def long_run_arms(wl, args, stream):
         out[name] = {"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_timed": n}
         if prof:
             out[name]["far_field_ms_per_step"] = sum(v[0] for k, v in prof.items()
-                                                     if k in ("k_farfield_mp", "k_ff_moments")) / 2
+                                                     if k in ("k_ff_moments", "k_ff_local", "k_farfield_loc")) / 2
         if cfg.get("mode", 0) == 1:
             out[name]["net"] = net
             out[name]["exact_every"] = exact_every
             out[name]["fallback"] = ("exact relaxation on every %d-th step and for vesicles within 4 spacings h of "
                                      "another vesicle" % exact_every)
         if cfg.get("farfield_multipole"):
-            out[name]["far_field"] = ("order-12 expansions about each vesicle's centre beyond three reach radii, "
-                                      "point sums (with the near test) inside: an approximation of the all-pairs sum")
+            out[name]["far_field"] = ("order-12 vesicle expansions translated to local expansions about each target "
+                                      "vesicle's centre for vesicle pairs farther apart than three times the sum of "
+                                      "their reach radii; for the other pairs the expansion per target point beyond "
+                                      "three reach radii, point sums (with the near test) inside: an approximation of "
+                                      "the all-pairs sum")
     # shape error against the plain step from the same initial state
     plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
     runs = {name: make(cfg) for name, cfg in variants.items()}
@@ -520,8 +523,8 @@ def run_gpu(args):
                                                                    % (fv[1], fv[2]))}
                                     if not args.farfield_multipole else
                                     {"parallelism": "replicas" if world > 1 else "single GPU",
-                                     "farfield": "fp32 vesicle multipole beyond three reach radii, point sums "
-                                                 "inside (not the headline configuration)"}),
+                                     "farfield": "fp32 vesicle multipole and local expansions for separated "
+                                                 "vesicles, point sums inside (not the headline configuration)"}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
                 "steady_state": steady, "hybrid": arms.get("hybrid"),

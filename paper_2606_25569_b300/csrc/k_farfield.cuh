@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__
   if (k == 0) a0[v] = make_float2((float)sA[0].x, (float)sA[0].y);
 }
 
-// Horner evaluation of a far vesicle's expansion (coefficients c in shared memory, (h^2, reach^2, A0) in na)
+// Horner evaluation of a far vesicle's expansion (its coefficients c, (h^2, reach^2, A0) in na)
 // for E targets at once (q_e = (qx[e], qy[e]), |q_e|^2 = d2[e]): every coefficient load serves all E.
 template <int P, int E>
 __device__ __forceinline__ void mp_far(const float4* c, float4 na, const float* qx, const float* qy, const float* d2,
@@ -322,96 +322,6 @@ __device__ __forceinline__ bool mp_points(const FarFieldArgs& a, const float4* _
   ux = fmaf(hl2, lx, ax);
   uy = fmaf(hl2, ly, ay);
   return true;
-}
-
-// TPT consecutive targets per thread over every source vesicle in ascending order: the expansion for far
-// vesicles (one coefficient pass for all of a thread's targets when every one of them is far), the point
-// sum with the near test for the rest; per-vesicle results added with Neumaier compensation. The vesicles'
-// centres, reach and coefficients are staged through shared memory FF_MP_CHUNK vesicles at a time.
-constexpr int FF_MP_CHUNK = 32;
-template <int THREADS, int P, int TPT>
-__global__ void __launch_bounds__(THREADS) k_farfield_mp(FarFieldArgs a, const float4* __restrict__ src,
-                                                         const float4* __restrict__ centre32,
-                                                         const float2* __restrict__ h2,
-                                                         const float4* __restrict__ coef,
-                                                         const float2* __restrict__ a0) {
-  constexpr int NC = 2 * (P + 1);  // coefficient float4s per vesicle
-  __shared__ float4 scoef[FF_MP_CHUNK * NC];
-  __shared__ float4 scen[FF_MP_CHUNK];
-  __shared__ float4 sh2a0[FF_MP_CHUNK];  // (h^2, reach^2, A0.x, A0.y)
-  int64_t t[TPT];
-  int tv[TPT], ncnt[TPT];
-  float4 ts[TPT], tc[TPT];
-  float sx[TPT], cx[TPT], sy[TPT], cy[TPT];
-  bool any = false;
-#pragma unroll
-  for (int e = 0; e < TPT; ++e) {
-    t[e] = ((int64_t)blockIdx.x * THREADS + threadIdx.x) * TPT + e;
-    const bool ok = t[e] < a.P;
-    any |= ok;
-    tv[e] = ok ? a.owner[t[e]] : -1;
-    ts[e] = ok ? src[t[e]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    tc[e] = ok ? centre32[tv[e]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    sx[e] = cx[e] = sy[e] = cy[e] = 0.f;
-    ncnt[e] = 0;
-  }
-  for (int v0 = 0; v0 < a.M; v0 += FF_MP_CHUNK) {
-    const int nv = min(FF_MP_CHUNK, a.M - v0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nv * NC; e += THREADS) scoef[e] = coef[(int64_t)v0 * NC + e];
-    for (int e = threadIdx.x; e < nv; e += THREADS) {
-      scen[e] = centre32[v0 + e];
-      const float2 hh = h2[v0 + e], A = a0[v0 + e];
-      sh2a0[e] = make_float4(hh.x, hh.y, A.x, A.y);
-    }
-    __syncthreads();
-    if (!any) continue;
-    for (int l = 0; l < nv; ++l) {
-      const int sv = v0 + l;
-      const float4 sc = scen[l];
-      const float4 na = sh2a0[l];
-      float qx[TPT], qy[TPT], d2[TPT];
-      bool far_all = true;
-#pragma unroll
-      for (int e = 0; e < TPT; ++e) {
-        qx[e] = ((tc[e].x - sc.x) + (tc[e].z - sc.z)) + ts[e].x;
-        qy[e] = ((tc[e].y - sc.y) + (tc[e].w - sc.w)) + ts[e].y;
-        d2[e] = fmaf(qx[e], qx[e], qy[e] * qy[e]);
-        far_all = far_all && tv[e] >= 0 && sv != tv[e] && d2[e] > FF_MP_THETA2 * na.y;
-      }
-      if (far_all) {
-        float ux[TPT], uy[TPT];
-        mp_far<P, TPT>(scoef + l * NC, na, qx, qy, d2, ux, uy);
-#pragma unroll
-        for (int e = 0; e < TPT; ++e) {
-          neumaier_add(sx[e], cx[e], ux[e]);
-          neumaier_add(sy[e], cy[e], uy[e]);
-        }
-        continue;
-      }
-#pragma unroll
-      for (int e = 0; e < TPT; ++e) {
-        if (tv[e] < 0 || sv == tv[e]) continue;
-        float ux, uy;
-        if (d2[e] > FF_MP_THETA2 * na.y) {
-          mp_far<P, 1>(scoef + l * NC, na, &qx[e], &qy[e], &d2[e], &ux, &uy);
-        } else if (!mp_points(a, src, t[e], sv, qx[e], qy[e], d2[e], na, ncnt[e], ux, uy)) {
-          continue;
-        }
-        neumaier_add(sx[e], cx[e], ux);
-        neumaier_add(sy[e], cy[e], uy);
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < TPT; ++e) {
-    if (tv[e] < 0) continue;
-    const int64_t to = a.voff[tv[e]];
-    const int tN = (int)(a.voff[tv[e] + 1] - to);
-    a.u[2 * to + (t[e] - to)] += (double)sx[e] + (double)cx[e];
-    a.u[2 * to + tN + (t[e] - to)] += (double)sy[e] + (double)cy[e];
-    if (a.near_mask) a.near_cnt[t[e]] = ncnt[e] < MAX_NEAR ? ncnt[e] : MAX_NEAR;
-  }
 }
 
 }  // namespace vs

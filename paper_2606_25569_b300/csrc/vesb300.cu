@@ -17,6 +17,7 @@
 #include "k_dense.cuh"
 #include "k_farfield.cuh"
 #include "k_farfield_sym.cuh"
+#include "k_farfield_loc.cuh"
 #include "k_geometry.cuh"
 #include "k_mlp.cuh"
 #include "k_mp.cuh"
@@ -204,6 +205,9 @@ struct SourceBufs {
   float4* sdf = nullptr;
   float4* mpcoef = nullptr;  // multipole far field: per vesicle (FF_MP_P + 1) x 2 float4 coefficients
   float2* mpa0 = nullptr;    // and its total density A_0
+  float* mploc = nullptr;    // per target vesicle: local expansion of the separated sources
+  int* mpncnt = nullptr;     // and its list of the other source vesicles
+  int* mplist = nullptr;
   cudaError_t alloc(int64_t P, int M) {
     cudaError_t e;
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -215,6 +219,8 @@ struct SourceBufs {
     VS_TRY(dalloc(&area, M)); VS_TRY(dalloc(&length, M)); VS_TRY(dalloc(&g32, P));
     VS_TRY(dalloc(&sdf, 3 * P));
     VS_TRY(dalloc(&mpcoef, (int64_t)M * (FF_MP_P + 1) * 2)); VS_TRY(dalloc(&mpa0, M));
+    VS_TRY(dalloc(&mploc, (int64_t)M * ffl_floats(FF_MP_P))); VS_TRY(dalloc(&mpncnt, M));
+    VS_TRY(dalloc(&mplist, (int64_t)M * FFL_LIST));
 #undef VS_TRY
     return cudaSuccess;
   }
@@ -222,10 +228,11 @@ struct SourceBufs {
     cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
     cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32); cudaFree(sdf);
-    cudaFree(mpcoef); cudaFree(mpa0);
+    cudaFree(mpcoef); cudaFree(mpa0); cudaFree(mploc); cudaFree(mpncnt); cudaFree(mplist);
     *this = SourceBufs{};
   }
   GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32, sdf}; }
+  FfLocArgs loc(int M) const { return FfLocArgs{M, centre32, h2, mpcoef, mpa0, mploc, mpncnt, mplist}; }
   PointGeom pg() const { return PointGeom{sa, tx, ty}; }
 };
 
@@ -628,10 +635,9 @@ vs_status far_field(vs_suspension* h) {
   } else if (h->p.flags & VS_FLAG_FARFIELD_MULTIPOLE) {
     VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef,
                                                                                    h->B.mpa0));
-    const int grid = (int)((L.P + 127) / 128);
-    VS_LAUNCH(h, "k_farfield_mp", (k_farfield_mp<128, FF_MP_P, 1><<<grid, 128, 0, h->stream>>>(a, h->B.src,
-                                                                                             h->B.centre32, h->B.h2,
-                                                                                             h->B.mpcoef, h->B.mpa0)));
+    const FfLocArgs la = h->B.loc(L.M);
+    VS_LAUNCH(h, "k_ff_local", k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la));
+    VS_LAUNCH(h, "k_farfield_loc", k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src));
   } else if (h->ffs.R > 0) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
     VS_LAUNCH(h, "k_farfield_sym", ffs_launch(h->ffs, fa, h->B, h->stream));
@@ -1417,8 +1423,9 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
   } else if (h->precision == 2) {
     k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
-    k_farfield_mp<128, FF_MP_P, 1><<<(int)((L.P + 127) / 128), 128, 0, h->stream>>>(a, h->B.src, h->B.centre32,
-                                                                                    h->B.h2, h->B.mpcoef, h->B.mpa0);
+    const FfLocArgs la = h->B.loc(L.M);
+    k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la);
+    k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src);
   } else if (h->ffs.R > 0) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->near_mask, h->B, h->err);
     ffs_launch(h->ffs, fa, h->B, h->stream);

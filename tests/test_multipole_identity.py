@@ -3,7 +3,10 @@ with s_j the sources relative to the vesicle centre, g_j the weighted densities 
 Stokeslet sum over a vesicle's points at a target q far from it equals
     -A_0 log|q| + A_0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2
 (series in zeta from the moments A_k, B_k, D_k; the library's kernels use this form). Written out here in
-numpy and checked against the oracle's direct sum: the error decays like (R/|q|)^(P+1)."""
+numpy and checked against the oracle's direct sum: the error decays like (R/|q|)^(P+1). The translation to
+a local expansion about a far target vesicle's centre (k_ff_local, k_farfield_loc) is written out and
+checked the same way."""
+from math import comb
 import numpy as np
 
 from oracle.farfield import far_field, source_weights
@@ -43,3 +46,52 @@ def test_expansion_matches_direct_sum_of_a_far_vesicle():
         u = _expansion(s, g, (tx[0] - c[0]) + 1j * (ty[0] - c[1]), P)
         scale = np.sqrt(np.mean(np.abs(g) ** 2)) * N
         assert abs(u - (ux[0] + 1j * uy[0])) <= tol * scale, (dist, P, abs(u - (ux[0] + 1j * uy[0])) / scale)
+
+
+def _local(s, g, d, P):
+    """Local expansion about the target vesicle's centre of the source vesicle's expansion, d = c_A - c_B:
+    u(w) = C + H(w)/2 + conj(K(w))/2 + w conj(S(w))/2 (coefficients of w^0 .. w^P)."""
+    A = np.array([np.sum(g * s ** k) for k in range(P + 2)])
+    B = np.array([np.sum(g * np.conj(s) ** k) for k in range(P + 2)])
+    D = np.array([np.sum(np.conj(g) * s * np.conj(s) ** k) for k in range(P + 2)])
+    t = [0] + [A[k] / k if k <= P else 0 for k in range(1, P + 2)]
+    sa = [0] + [A[k - 1] for k in range(1, P + 2)]
+    e = [0] + [(np.conj(B[k]) / k if k <= P else 0) - np.conj(D[k - 1]) for k in range(1, P + 2)]
+    z = 1.0 / d
+
+    def loc(f):  # sum_k f_k (d + w)^-k = sum_m L_m w^m
+        return np.array([(-z) ** m * sum(comb(k + m - 1, m) * f[k] * z ** k for k in range(1, P + 2))
+                         for m in range(P + 1)])
+
+    ell = np.array([0] + [(-1) ** (m + 1) * z ** m / m for m in range(1, P + 1)])  # log(1 + w/d)
+    LS = loc(sa)
+    H = loc(t) - A[0] * ell
+    K = loc(e) + np.conj(d) * LS - np.conj(A[0]) * ell
+    C = -A[0] * np.log(abs(d)) + 0.5 * A[0]
+    return C, H, K, LS
+
+
+def test_local_expansion_matches_direct_sum_at_a_separated_vesicle():
+    rng = np.random.default_rng(5)
+    N, R, P = 64, 0.1, 12
+    xb, yb = vesicle_outline(N, 0.65, R, 1e-2, rng, 0.4)
+    xa, ya = vesicle_outline(N, 0.65, R, 1e-2, rng, 1.9)
+    fx, fy = rng.standard_normal(N), rng.standard_normal(N)
+    w, _ = source_weights([xb], [yb])
+    cb = np.array([xb.mean(), yb.mean()])
+    s = (xb - cb[0]) + 1j * (yb - cb[1])
+    g = (fx + 1j * fy) * w[0] / (4 * np.pi)
+    ca = np.array([xa.mean(), ya.mean()])
+    wa = (xa - ca[0]) + 1j * (ya - ca[1])
+    rho = np.abs(s).max() + np.abs(wa).max()
+    scale = np.sqrt(np.mean(np.abs(g) ** 2)) * N
+    # centre distance 3, 4 and 6 times the sum of the two radii (the kernels take 3 and more)
+    for sep, tol in ((3.0, 1e-9), (4.0, 1e-11), (6.0, 1e-13)):
+        d = sep * rho * np.exp(0.7j)
+        X, Y = xa - ca[0] + cb[0] + d.real, ya - ca[1] + cb[1] + d.imag
+        ux, uy, _ = far_field([xb, X], [yb, Y], [fx, np.zeros(N)], [fy, np.zeros(N)], 1.0, near_mask=False,
+                              targets=np.arange(N, 2 * N))
+        C, H, K, S = _local(s, g, d, P)
+        pw = wa[:, None] ** np.arange(P + 1)[None, :]
+        u = C + 0.5 * (pw @ H) + 0.5 * np.conj(pw @ K) + 0.5 * wa * np.conj(pw @ S)
+        assert np.max(np.abs(u - (ux + 1j * uy))) <= tol * scale, (sep, np.max(np.abs(u - (ux + 1j * uy))) / scale)
