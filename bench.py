@@ -333,7 +333,7 @@ def long_run_arms(wl, args, stream):
                                      "another vesicle" % exact_every)
         if cfg.get("farfield_multipole"):
             out[name]["far_field"] = ("order-12 vesicle expansions translated to local expansions about each target "
-                                      "vesicle's centre for vesicle pairs farther apart than three times the sum of "
+                                      "vesicle's centre for vesicle pairs farther apart than twice the sum of "
                                       "their reach radii; for the other pairs the expansion per target point beyond "
                                       "three reach radii, point sums (with the near test) inside: an approximation of "
                                       "the all-pairs sum")

@@ -74,11 +74,11 @@ typedef struct {
  * preconditioners and the same FP64-accurate results. At N <= 128 the FMA kernels are faster. */
 #define VS_FLAG_TC_GEMM 8ull
 /* Far field through vesicle multipole expansions (order 12 about each vesicle's centre): for vesicle pairs
- * whose centres are farther apart than three times the sum of their reach radii, translated into one local
+ * whose centres are farther apart than twice the sum of their reach radii, translated into one local
  * expansion about each target vesicle's centre (summed over those sources, evaluated once per target
  * point); for the other pairs the expansion per target point beyond three reach radii of the source, point
  * sums inside (near test and lists unchanged). An approximation of the all-pairs sum (the paper names FMM
- * as the route to O(M) cost) whose truncation error is below about 3^-13 of a vesicle's density scale;
+ * as the route to O(M) cost) whose truncation error is below about 1e-8 of a vesicle's density scale;
  * FP32 with compensated accumulation. */
 #define VS_FLAG_FARFIELD_MULTIPOLE 16ull
 /* The FP32 far field sums over every ordered pair with one thread per target (k_farfield_f32, launch

@@ -13,17 +13,17 @@
 // with C = sum_B (-A0 log|d| + A0/2), H = sum_B (L[T1] - A0 l), K = sum_B (L[E] + conj(d) L[S_A] - conj(A0) l),
 // S = sum_B L[S_A], l the log series: three power series of degree P per target vesicle (the translation
 // that fast multipole methods call multipole-to-local). A pair (A, B) takes this route when
-// |c_A - c_B| > 3 (reach_A + reach_B); the truncation error is then below about 3^-(P+1) of B's
-// contribution. The other source vesicles of A are listed (ascending) and summed per target point as
-// before: B's expansion where the point is beyond three reach radii of c_B, the point sum with the near
-// test inside.
+// |c_A - c_B| > 2 (reach_A + reach_B); the truncation error is then below about 2^-(P+1) of B's density
+// scale (measured on 64-point vesicles: 5e-9 at twice, 1e-11 at three times the summed radii). The other
+// source vesicles of A are listed (ascending) and summed per target point as before: B's expansion where
+// the point is beyond three reach radii of c_B, the point sum with the near test inside.
 #pragma once
 #include "k_farfield.cuh"
 
 namespace vs {
 
 constexpr int FFL_LIST = 128;     // listed (not separated) source vesicles per target vesicle
-constexpr float FFL_SEP2 = 9.0f;  // separated when |c_A - c_B|^2 > 9 (reach_A + reach_B)^2
+constexpr float FFL_SEP2 = 4.0f;  // separated when |c_A - c_B|^2 > 4 (reach_A + reach_B)^2
 
 // floats of one local expansion of order P: C, then H, K, S (P + 1 complex coefficients each)
 __host__ __device__ constexpr int ffl_floats(int P) { return 2 + 6 * (P + 1); }

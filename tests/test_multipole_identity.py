@@ -85,8 +85,8 @@ def test_local_expansion_matches_direct_sum_at_a_separated_vesicle():
     wa = (xa - ca[0]) + 1j * (ya - ca[1])
     rho = np.abs(s).max() + np.abs(wa).max()
     scale = np.sqrt(np.mean(np.abs(g) ** 2)) * N
-    # centre distance 3, 4 and 6 times the sum of the two radii (the kernels take 3 and more)
-    for sep, tol in ((3.0, 1e-9), (4.0, 1e-11), (6.0, 1e-13)):
+    # centre distance 2, 3, 4 and 6 times the sum of the two radii (the kernels take 2 and more)
+    for sep, tol in ((2.0, 2e-8), (3.0, 1e-9), (4.0, 1e-11), (6.0, 1e-13)):
         d = sep * rho * np.exp(0.7j)
         X, Y = xa - ca[0] + cb[0] + d.real, ya - ca[1] + cb[1] + d.imag
         ux, uy, _ = far_field([xb, X], [yb, Y], [fx, np.zeros(N)], [fy, np.zeros(N)], 1.0, near_mask=False,
