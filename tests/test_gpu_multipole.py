@@ -112,3 +112,36 @@ def test_multipole_far_field_uneven_vesicles_and_near_lists():
     err = np.linalg.norm(got[2] - ref) / np.linalg.norm(ref)
     print("uneven box, multipole: relative L2 error %.3e" % err)
     assert err <= 1e-5, err
+
+
+def test_multipole_far_field_with_an_overflowing_source_list():
+    # a large vesicle ringed by 220 small ones: more than 128 of them are too close to its centre for the
+    # local expansion, so its target points take the fallback over all source vesicles
+    from paper_2606_25569_b300.workloads import vesicle_outline
+    rng = np.random.default_rng(31)
+    x0, y0 = vesicle_outline(128, 0.9, 1.0, 1e-2, rng, 0.0)
+    xs, ys, Ns = [x0], [y0], [128]
+    for v in range(220):
+        ring, ang = 1.6 + 0.25 * (v % 4), 2 * np.pi * (v // 4) / 55 + 0.3 * (v % 4)
+        x, y = vesicle_outline(32, 0.8, 0.06, 1e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x + ring * np.cos(ang))
+        ys.append(y + ring * np.sin(ang))
+        Ns.append(32)
+    fx = [rng.standard_normal(n) for n in Ns]
+    fy = [rng.standard_normal(n) for n in Ns]
+    off = np.concatenate([[0], np.cumsum(Ns)]).astype(np.int64)
+    xy = np.concatenate([np.concatenate([a, b]) for a, b in zip(xs, ys)])
+    f = np.concatenate([np.concatenate([a, b]) for a, b in zip(fx, fy)])
+    plan = binding.FarFieldPlan(off, mu=1.0, near_mask=True, precision=2)
+    u = torch.empty(2 * off[-1], dtype=torch.float64, device="cuda")
+    plan.eval(_dev(xy), _dev(f), u)
+    got = u.cpu().numpy()
+    c = plan.counters()
+    plan.close()
+    ux, uy, near = far_field(xs, ys, fx, fy, 1.0, near_mask=True)
+    assert c["err"] == 0 and c["near_pairs"] == len(near)
+    ref = np.concatenate([np.concatenate([ux[off[v]:off[v + 1]], uy[off[v]:off[v + 1]]]) for v in range(len(Ns))])
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    err0 = np.linalg.norm(got[:256] - ref[:256]) / np.linalg.norm(ref[:256])
+    print("ring, multipole: relative L2 error %.3e (large vesicle %.3e)" % (err, err0))
+    assert err <= 1e-5 and err0 <= 1e-5, (err, err0)
