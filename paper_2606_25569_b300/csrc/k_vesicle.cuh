@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) k_corr_newton32(VesIndex vi, const double
                                                        double* __restrict__ xy, int* __restrict__ fired, unsigned* err) {
   extern __shared__ __align__(16) float Mg[];  // (2N)^2
   __shared__ double d[NMAX], zx[NMAX], zy[NMAX], gA[2 * NMAX], gL[2 * NMAX], r1[2 * NMAX], red[8];
-  __shared__ float dq[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX], f1[2 * NMAX];
+  __shared__ float dq[NMAX], qxx[NMAX], qxy[NMAX], qyy[NMAX];
   __shared__ float yv[3][2 * NMAX];
   __shared__ double sol[3];
   const int v = vi.vid(blockIdx.x);

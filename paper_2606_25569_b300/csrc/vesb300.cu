@@ -887,7 +887,7 @@ inline bool learned_step(const vs_suspension* h) {
 
 vs_status step_once(vs_suspension* h) {
   const Layout& L = h->L;
-  const int M = L.M, n = L.nmax;
+  const int M = L.M;
   const VesIndex vi = h->D.vi();
   vs_status st;
   const int cur = h->cur, nxt = 1 - h->cur;
