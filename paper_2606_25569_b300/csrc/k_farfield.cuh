@@ -189,16 +189,18 @@ constexpr int FF_MP_P = 12;            // expansion order
 constexpr float FF_MP_THETA2 = 9.0f;   // far when |q|^2 > 9 R_v^2
 
 // Moments of every vesicle: one CTA per vesicle, one thread per point; each thread forms s^k (k = 0..P+1)
-// by repeated products and its terms of A_k, B_k, D_k in FP64, and the block sums them (warp shuffles,
-// then the warps' partial sums in fixed order). coef[v][k - 1], k = 1..P+1: (A_k/k [k <= P], A_{k-1}) and
+// by repeated products and its terms of A_k, B_k, D_k in FP64 into shared memory (ffm_smem bytes), and one
+// thread per moment component sums them in point order. coef[v][k - 1], k = 1..P+1: (A_k/k [k <= P], A_{k-1}) and
 // (E_k, 0, 0) as float4 pairs; a0[v] = A_0.
+inline size_t ffm_smem(int P, int threads) { return (size_t)6 * (P + 2) * threads * sizeof(double); }
+
 template <int P>
 __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__ voff, const float4* __restrict__ src,
                                                      float4* __restrict__ coef, float2* __restrict__ a0) {
   constexpr int K = P + 2;
-  __shared__ double part[NMAX / 32][3 * K][2];
+  extern __shared__ double mvals[];  // [6 K][blockDim]: every thread's terms, summed per moment below
   __shared__ double2 sA[K], sB[K], sD[K];
-  const int v = blockIdx.x, j = threadIdx.x, lane = j & 31, w = j >> 5;
+  const int v = blockIdx.x, j = threadIdx.x, nt = blockDim.x;
   const int64_t o = voff[v], n = voff[v + 1] - o;
   double sx = 0.0, sy = 0.0, gx = 0.0, gy = 0.0;
   if (j < n) {
@@ -208,32 +210,27 @@ __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__
   double pr = 1.0, pi = 0.0;  // s^k
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double t[6];
-    t[0] = gx * pr - gy * pi;  // g s^k
-    t[1] = gx * pi + gy * pr;
-    t[2] = gx * pr + gy * pi;  // g conj(s)^k = g conj(s^k)
-    t[3] = gy * pr - gx * pi;
+    double* t = mvals + (6 * k) * nt + j;
+    t[0 * nt] = gx * pr - gy * pi;  // g s^k
+    t[1 * nt] = gx * pi + gy * pr;
+    t[2 * nt] = gx * pr + gy * pi;  // g conj(s)^k = g conj(s^k)
+    t[3 * nt] = gy * pr - gx * pi;
     const double wr = sx * pr + sy * pi, wi = sy * pr - sx * pi;  // s conj(s^k)
-    t[4] = gx * wr + gy * wi;  // conj(g) s conj(s^k)
-    t[5] = gx * wi - gy * wr;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      double x = t[e];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-      if (lane == 0) part[w][(e >> 1) * K + k][e & 1] = x;
-    }
+    t[4 * nt] = gx * wr + gy * wi;  // conj(g) s conj(s^k)
+    t[5 * nt] = gx * wi - gy * wr;
     const double nr = pr * sx - pi * sy;
     pi = pr * sy + pi * sx;
     pr = nr;
   }
   __syncthreads();
-  const int nw = blockDim.x >> 5;
-  for (int e = j; e < 3 * K; e += blockDim.x) {
-    double x = 0.0, y = 0.0;
-    for (int q = 0; q < nw; ++q) { x += part[q][e][0]; y += part[q][e][1]; }
-    const int set = e / K, k = e - set * K;
-    (set == 0 ? sA : set == 1 ? sB : sD)[k] = make_double2(x, y);
+  // one thread per moment component sums the points' terms in order (FP64 adds run at a low rate on this
+  // part: this takes far fewer of them than tree reductions of every term across the warp)
+  for (int e = j; e < 6 * K; e += nt) {
+    const double* row = mvals + (int64_t)e * nt;
+    double x = 0.0;
+    for (int q = 0; q < n; ++q) x += row[q];
+    const int k = e / 6, c = e - 6 * k;
+    reinterpret_cast<double*>((c >> 1) == 0 ? sA : (c >> 1) == 1 ? sB : sD)[2 * k + (c & 1)] = x;
   }
   __syncthreads();
   const int k = j;

@@ -633,8 +633,9 @@ vs_status far_field(vs_suspension* h) {
     const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
     VS_LAUNCH(h, "k_farfield_f64", k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N));
   } else if (h->p.flags & VS_FLAG_FARFIELD_MULTIPOLE) {
-    VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef,
-                                                                                   h->B.mpa0));
+    const int mt = ff_moment_threads(L);
+    VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(
+                                     h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0));
     const FfLocArgs la = h->B.loc(L.M);
     VS_LAUNCH(h, "k_ff_local", k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la));
     VS_LAUNCH(h, "k_farfield_loc", k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src));
@@ -1064,6 +1065,8 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpW32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpA32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpBlk32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  VS_A(cudaFuncSetAttribute(k_ff_moments<FF_MP_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)ffm_smem(FF_MP_P, NMAX)));
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
@@ -1400,7 +1403,9 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
       (e = h->B.alloc(h->L.P, h->L.M)) != cudaSuccess || (e = dalloc(&h->err, 1)) != cudaSuccess ||
       (e = cudaMemset(h->err, 0, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMemset(h->B.near_cnt, 0, h->L.P * sizeof(int))) != cudaSuccess ||
-      (e = ffs_setup(h->ffs, h->L, precision == 0, h->stream)) != cudaSuccess) {
+      (e = ffs_setup(h->ffs, h->L, precision == 0, h->stream)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_ff_moments<FF_MP_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ffm_smem(FF_MP_P, NMAX))) != cudaSuccess) {
     cuda_fail(h->msg, e, "vs_farfield_plan_create");
     return fail(e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
   }
@@ -1422,7 +1427,8 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
   if (h->precision == 1) {
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
   } else if (h->precision == 2) {
-    k_ff_moments<FF_MP_P><<<L.M, ff_moment_threads(L), 0, h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
+    const int mt = ff_moment_threads(L);
+    k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);
     const FfLocArgs la = h->B.loc(L.M);
     k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la);
     k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src);
