@@ -27,11 +27,13 @@
 // Precision: per (target, source vesicle) partial sums in FP32 as in k_farfield_f32, added to running
 // sums with Neumaier compensation (registers for the rows, shared memory for the columns). Tile (I, J)
 // writes the contributions of chunk J to the points of chunk I and those of chunk I to the points of
-// chunk J into slots part[J][.] and part[I][.] (each slot written exactly once, the compensated pair
-// rounded to one double); k_farfield_sym_reduce adds the slots of each point in chunk order in FP64.
+// chunk J into slots part[J][.] and part[I][.] (each slot written exactly once, as the compensated float
+// pair); k_farfield_sym_reduce adds the slots of each point in chunk order in double-float arithmetic
+// (FP64 adds run at 1/64 of the FP32 rate on this part).
 // The result is deterministic and independent of which CTA takes which tile; it differs from the
 // per-target kernel's by FP32 rounding only.
 #pragma once
+#include "dfloat.cuh"
 #include "k_farfield.cuh"
 
 namespace vs {
@@ -51,7 +53,8 @@ struct FfSymArgs {
   const int2* tiles;   // [ntile] (I, J), I <= J
   unsigned* tile_ctr;  // next tile; zero before each launch
   int near_mask;
-  double2* part;       // [nchunk][P]: velocity at each point from the vesicles of one chunk
+  float4* part;        // [nchunk][P]: velocity at each point from the vesicles of one chunk (x sum and
+                       // compensation, y sum and compensation)
   int* near_cnt;       // [P], zero before each launch when near_mask
   int* near_v;         // [P * MAX_NEAR]
   unsigned* err;
@@ -229,32 +232,32 @@ __global__ void __launch_bounds__(32 * FFS_W) k_farfield_sym(FfSymArgs a, const 
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            a.part[(int64_t)J * a.P + (int64_t)av * N + lane + 32 * r] =
-                make_double2((double)sxr[r] + (double)cxr[r], (double)syr[r] + (double)cyr[r]);
+            a.part[(int64_t)J * a.P + (int64_t)av * N + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
         }
       }
       __syncthreads();
     }
     for (int e = threadIdx.x; e < nJ * N; e += blockDim.x) {  // chunk I's contributions to chunk J's points
       const float4 v = acc[e];
-      a.part[(int64_t)I * a.P + p0 + e] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      a.part[(int64_t)I * a.P + p0 + e] = v;
     }
     __syncthreads();
   }
 }
 
-// u (CSR blocks [u_x(N), u_y(N)] per vesicle) += sum over chunks of part, in chunk order (FP64); near
+// u (CSR blocks [u_x(N), u_y(N)] per vesicle) += sum over chunks of part, in chunk order (double-float); near
 // counts clamped to MAX_NEAR and each near list sorted ascending.
 __global__ void __launch_bounds__(256) k_farfield_sym_reduce(FfSymArgs a, double* __restrict__ u) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
-  double sx = 0.0, sy = 0.0;
+  float2 ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
 #pragma unroll 8
   for (int K = 0; K < a.nchunk; ++K) {
-    const double2 v = a.part[(int64_t)K * a.P + p];
-    sx += v.x;
-    sy += v.y;
+    const float4 v = a.part[(int64_t)K * a.P + p];
+    ax = df_add(ax, make_float2(v.x, v.y));
+    ay = df_add(ay, make_float2(v.z, v.w));
   }
+  const double sx = (double)ax.x + (double)ax.y, sy = (double)ay.x + (double)ay.y;
   const int64_t v = p / a.N;
   const int64_t to = v * a.N;
   const int64_t loc = p - to;

@@ -286,7 +286,7 @@ struct vs_mlp {
 struct FfSymState {
   int R = 0, nchunk = 0, ntile = 0, grid = 0;
   int2* tiles = nullptr;
-  double2* part = nullptr;
+  float4* part = nullptr;
   unsigned* ctr = nullptr;
   void release() {
     cudaFree(tiles); cudaFree(part); cudaFree(ctr);
@@ -558,7 +558,7 @@ FarFieldArgs far_field_args(vs_suspension* h) {
 }
 
 // Symmetric FP32 far field: eligible when every vesicle has N = 32, 64 or 128 points and the chunk slots
-// (one double2 per point and chunk of FFS_V vesicles) fit in FFS_PART_MAX bytes; otherwise, and with
+// (one float4 per point and chunk of FFS_V vesicles) fit in FFS_PART_MAX bytes; otherwise, and with
 // VS_FLAG_FARFIELD_PER_TARGET, the per-target kernel runs.
 constexpr size_t FFS_PART_MAX = size_t(4) << 30;
 
@@ -589,7 +589,7 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
   const int R = L.nmax / 32;
   if (L.nmax % 32 != 0 || !(R == 1 || R == 2 || R == 4)) return cudaSuccess;
   const int nchunk = (L.M + FFS_V - 1) / FFS_V;
-  if ((size_t)nchunk * (size_t)L.P * sizeof(double2) > FFS_PART_MAX) return cudaSuccess;
+  if ((size_t)nchunk * (size_t)L.P * sizeof(float4) > FFS_PART_MAX) return cudaSuccess;
   std::vector<int2> tiles;
   for (int i = 0; i < nchunk; ++i)  // whole tiles first, the half-empty diagonal ones last
     for (int j = i + 1; j < nchunk; ++j) tiles.push_back(make_int2(i, j));
