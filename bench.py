@@ -40,9 +40,9 @@ FFS_INST_PER_PAIR = 20
 # Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
 FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 # DRAM bytes of one k_farfield_sym launch at 2000 x 64 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# one-pass capture of the bench workload: 3.48 MB read, 195.44 MB written, mostly the per-chunk partial sums
+# one-pass capture of the bench workload: 3.64 MB read, 195.51 MB written, mostly the per-chunk partial sums
 # that do not stay in L2)
-FFS_DRAM_BYTES = 3.48e6 + 195.44e6
+FFS_DRAM_BYTES = 3.64e6 + 195.51e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 
 
