@@ -1,5 +1,6 @@
 """Pins for oracle.step (Algorithm 1, Eqs. advection_disc, relaxation_disc, tension_disc)."""
 import numpy as np
+import pytest
 
 from oracle.correct import area_length
 from oracle.spectral import bending_energy
@@ -93,3 +94,53 @@ def test_close_vesicles_against_circles_at_known_gaps():
         xs = [np.cos(t), np.cos(t) + 2.0 + gap, far[0]]
         ys = [np.sin(t), np.sin(t), far[1]]
         assert close_vesicles(xs, ys, 3.0) == expect
+
+
+def _inextensibility_residual(x, y, sig, ux, uy, kappa, mu):
+    """Surface divergence X_s . d/ds of the total membrane velocity u + S[f(sigma)], relative to the
+    divergence of the velocity without tension. f is built by spectral.force (the force's definition,
+    Eq. elastic_force), S by the self-quadrature: neither goes through the Operators matrices that the
+    tension update solves with."""
+    from oracle.spectral import Geometry, d_s, force
+    from oracle.stokes import self_single_layer_matrix
+    g = Geometry(x, y)
+    N = len(x)
+    S = self_single_layer_matrix(x, y, mu)
+
+    def div(sigma):
+        fx, fy = force(x, y, sigma, kappa)
+        w = S @ np.concatenate([fx, fy]) + np.concatenate([ux, uy])
+        return g.tx * d_s(w[:N], g.sa) + g.ty * d_s(w[N:], g.sa)
+
+    return np.max(np.abs(div(sig))) / np.max(np.abs(div(np.zeros(N))))
+
+
+@pytest.mark.parametrize("flow", [(1, (1.0, 0.0, 0.0, 0.0)), (2, (1.0, 1.7, 0.0, 0.0))])
+def test_tension_makes_the_total_velocity_inextensible(flow):
+    # Eq. tension_disc: sigma is the Lagrange multiplier of inextensibility, so the velocity of the
+    # membrane under bending, the tension's own force and the background flow has zero surface
+    # divergence (Eq. inextensib). A sign error or a dropped background term in the update fails it.
+    from oracle.flows import background
+    from oracle.operators import Operators
+    from oracle.step import _tension
+    for N, seed in ((32, 6), (64, 7)):
+        x, y = _ves(N, seed, 0.3, -0.2, R=0.8)
+        ub = background(flow[0], flow[1], x, y)
+        sig = _tension(Operators(x, y, 1.3, 0.9), x, y, ub[0], ub[1], 1.3)
+        assert _inextensibility_residual(x, y, sig, ub[0], ub[1], 1.3, 0.9) < 1e-10
+
+
+@pytest.mark.parametrize("flow", [(1, (1.0, 0.0, 0.0, 0.0)), (2, (1.0, 1.7, 0.0, 0.0))])
+def test_initial_and_stepped_tension_keep_the_membrane_inextensible(flow):
+    # The suspension's sigma^0 (background velocity at X^0) and, for a single vesicle in a quiescent
+    # fluid, sigma^1 (velocity u^0 = 0) each make the total velocity inextensible at their own points.
+    from oracle.flows import background
+    x, y = _ves(32, 8)
+    s = Suspension([x], [y], Params(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=flow[0], flow_p=flow[1],
+                                    corr_tol=1.0))
+    ub = background(flow[0], flow[1], s.xs[0], s.ys[0])
+    assert _inextensibility_residual(s.xs[0], s.ys[0], s.sig[0], ub[0], ub[1], 1.0, 1.0) < 1e-10
+    q = Suspension([x], [y], Params(kappa=1.0, mu=1.0, dt=1e-3, corr_tol=1.0))
+    q.step()
+    z = np.zeros(32)
+    assert _inextensibility_residual(q.xs[0], q.ys[0], q.sig[0], z, z, 1.0, 1.0) < 1e-10
