@@ -27,7 +27,8 @@ computes the tension before the correction and so do we. One far-field evaluatio
 hybrid step (relax_learned), except for vesicles in a near pair this step (the target's owner or the
 source vesicle) or within exact_gap (default HYBRID_EXACT_GAP) spacings of another vesicle, and, with exact_every = m > 0,
 on every m-th step: those relax exactly, the plain step serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
-too; here they keep the exact relaxation). Initial tension (not given in the paper):
+too; here they keep the exact relaxation). With Params.flow_net set as well, steps 3 and 6 of every step
+take the learned advection and tension of oracle.learned (Eqs. advectionMap, advTenMap) for every vesicle. Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -45,7 +46,8 @@ HYBRID_EXACT_GAP = 4.0
 
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
-                 near_field=False, corr_tol=0.01, relax_net=None, exact_every=0, exact_gap=HYBRID_EXACT_GAP):
+                 near_field=False, corr_tol=0.01, relax_net=None, exact_every=0, exact_gap=HYBRID_EXACT_GAP,
+                 flow_net=None):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
@@ -55,6 +57,10 @@ class Params:
         self.exact_every = int(exact_every)
         # in a learned step, vesicles within exact_gap spacings h of another vesicle relax exactly
         self.exact_gap = float(exact_gap)
+        # (adv, ten, Kf, Kout), each network (dims, flat parameters, affine or None) or a function of the
+        # vesicle (x, y) giving its output row: with relax_net set, the
+        # advection and the tension of every step come from them (oracle.learned), for every vesicle
+        self.flow_net = flow_net
 
 
 def relax_learned(x, y, net):
@@ -80,6 +86,23 @@ def relax_learned(x, y, net):
     ddx, ddy = features_to_samples(scale * out[0, :feature_count(K)], K, N)
     dx, dy = destandardize_disp(ddx, ddy, fr)
     return np.concatenate([fourier_filter(xr + dx, kmax), fourier_filter(yr + dy, kmax)])
+
+
+def flow_row(x, y, net, kmax):
+    """The flow network's output row for the vesicle (x, y): its input is the relaxation network's, the
+    Fourier features (modes <= min(kmax, N/2 - 1)) of the standardised shape (bfloat16 operands as on the
+    tensor cores, input first rounded to float32)."""
+    from .mlp import forward
+    from .standardize import feature_count, fourier_features, standardize
+    if callable(net):  # any function of the vesicle giving its row (the pins pass the exact columns)
+        return net(x, y)
+    dims, params, affine = net
+    K = min(kmax, len(x) // 2 - 1)
+    xo, yo, _ = standardize(x, y)
+    inp = np.zeros((1, dims[0]))
+    inp[0, :feature_count(K)] = fourier_features(xo, yo, K)
+    out, _ = forward(params, dims, inp, bf16=True, affine=affine)
+    return out[0]
 
 
 def relax_exact(x, y, p):
@@ -143,6 +166,8 @@ class Suspension:
     def step(self):
         p = self.p
         self.nstep = getattr(self, "nstep", 0) + 1
+        # learned advection and tension in every step of a hybrid suspension with flow networks
+        flow = (p.flow_net, p.relax_net[3]) if p.relax_net is not None and p.flow_net is not None else None
         if p.relax_net is not None and p.exact_every > 0 and self.nstep % p.exact_every == 0:
             import copy
             p = copy.copy(p)
@@ -163,7 +188,7 @@ class Suspension:
                 import copy
                 pv = copy.copy(p)
                 pv.relax_net = None
-            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], pv)
+            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], pv, flow)
             self.corrections += int(fired)
             nxs.append(xc)
             nys.append(yc)
@@ -185,20 +210,31 @@ def close_vesicles(xs, ys, gap_h):
     return out
 
 
-def advance_vesicle(x, y, ux, uy, A0, L0, p):
+def advance_vesicle(x, y, ux, uy, A0, L0, p, flow=None):
     """Steps 3-7 of the module header for one vesicle at X^n = (x, y) given its velocity u^n = (ux, uy):
-    returns (x^{n+1}, y^{n+1}, sigma^{n+1}, correction fired)."""
+    returns (x^{n+1}, y^{n+1}, sigma^{n+1}, correction fired). flow = ((adv, ten, Kf, Kout), kmax): the
+    advection and the tension from the networks (oracle.learned)."""
     N = len(x)
     ubar = np.concatenate([ux, uy])
-    ops_n = Operators(x, y, p.kappa, p.mu)
-    zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
+    if flow is not None:
+        from .learned import advect_learned
+        (adv, ten, Kf, Kout), kmax = flow
+        zx, zy = advect_learned(x, y, ux, uy, p.dt, flow_row(x, y, adv, kmax), Kf, Kout)
+        zs = np.concatenate([zx, zy])
+    else:
+        ops_n = Operators(x, y, p.kappa, p.mu)
+        zs = np.concatenate([x, y]) + p.dt * ops_n.project(ubar)
     if p.relax_net is not None:
         z1 = relax_learned(zs[:N], zs[N:], p.relax_net)
     else:
         z1 = relax_exact(zs[:N], zs[N:], p)
     xr, yr, alpha = redistribute(z1[:N], z1[N:])
     uxr, uyr = eval_interpolant(ux, alpha), eval_interpolant(uy, alpha)
-    ops_r = Operators(xr, yr, p.kappa, p.mu)
-    sig = _tension(ops_r, xr, yr, uxr, uyr, p.kappa)
+    if flow is not None:
+        from .learned import tension_learned
+        sig = tension_learned(xr, yr, uxr, uyr, flow_row(xr, yr, ten, kmax), Kf, Kout)
+    else:
+        ops_r = Operators(xr, yr, p.kappa, p.mu)
+        sig = _tension(ops_r, xr, yr, uxr, uyr, p.kappa)
     xc, yc, fired, _ = _corr.correct(xr, yr, A0, L0, tol=p.corr_tol)
     return xc, yc, sig, fired
