@@ -20,7 +20,7 @@ import sys
 import tempfile
 import time
 
-# the oracle baseline runs single-threaded: pin BLAS threads before numpy loads
+# the oracle baseline runs one BLAS thread per process: pin BLAS threads before numpy loads
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -34,8 +34,10 @@ UNIT = "vesicle-steps/s"
 MUFU_PER_CLK_SM = 16      # special-function results per clock per SM (4 per sub-partition)
 ISSUE_LANES_PER_CLK_SM = 128  # 4 warp schedulers x 32 lanes: one warp instruction each per clock
 N_SM = 148
-# k_farfield_sym: arithmetic instructions per unordered pair of points (18 FP32 + lg2 + rcp: both reactions)
-FFS_INST_PER_PAIR = 20
+# k_farfield_sym: arithmetic instructions per unordered pair of points (19 FP32 + lg2 + rcp, both reactions;
+# one of the FP32 instructions scales the log argument by the pair's constant, which the FP32 accuracy bar
+# needs in dense suspensions)
+FFS_INST_PER_PAIR = 21
 # DRAM bytes per point of one far-field launch: ncu dram__bytes of k_farfield_f32 on the 1200 x 64 dense
 # Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
 FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
@@ -44,6 +46,8 @@ FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 # that do not stay in L2)
 FFS_DRAM_BYTES = 3.64e6 + 195.51e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
+# learned advection and tension: velocity modes expanded and column modes kept, training epochs
+FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 16, 30
 
 
 def parse():
@@ -60,6 +64,8 @@ def parse():
                     help="time the plain step with the vesicle-multipole far field (not the headline configuration)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the learned-relaxation (hybrid) arm")
     ap.add_argument("--no-farfield-alone", action="store_true", help="skip the far field alone on the 2000 x 128 box")
+    ap.add_argument("--no-near-arm", action="store_true", help="skip the plain step with near pairs")
+    ap.add_argument("--no-uneven-arm", action="store_true", help="skip the plain step with 32/64/128-point vesicles")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
@@ -167,43 +173,98 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------------------------------ oracle
-def oracle_sample(wl, n_ves=24, n_targets=2048, threads=1):
+_ORACLE_SOURCES = None
+
+
+def _oracle_init(xs, ys, fx, fy, mu):
+    """Worker set-up: every source point of the suspension with its density (for the far-field sample)."""
+    global _ORACLE_SOURCES
+    _ORACLE_SOURCES = (xs, ys, fx, fy, mu)
+
+
+def _oracle_vesicles(job):
+    """One oracle plain step of a sub-suspension (its own vesicles' mutual far field included); seconds."""
+    from oracle.step import Params, Suspension
+    xs, ys, pv = job
+    sub = Suspension(xs, ys, Params(**pv))
+    t0 = time.perf_counter()
+    sub.step()
+    return time.perf_counter() - t0
+
+
+def _oracle_targets(tg):
+    """The oracle's far field at the targets tg against every source; seconds."""
+    from oracle.farfield import far_field
+    xs, ys, fx, fy, mu = _ORACLE_SOURCES
+    t0 = time.perf_counter()
+    far_field(xs, ys, fx, fy, mu, near_mask=True, targets=tg)
+    return time.perf_counter() - t0
+
+
+def oracle_pool(wl, procs):
+    """A spawned pool of `procs` oracle processes holding the workload's sources and densities (the
+    forces of zero tension), started and warmed up (imports done); None for procs = 1."""
+    import multiprocessing as mp
+    from oracle.spectral import force
+    fx, fy = [], []
+    for x, y in zip(wl.xs, wl.ys):
+        a, b = force(x, y, np.zeros(len(x)), wl.kappa)
+        fx.append(a)
+        fy.append(b)
+    _oracle_init(wl.xs, wl.ys, fx, fy, wl.mu)
+    if procs == 1:
+        return None
+    pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(wl.xs, wl.ys, fx, fy, wl.mu))
+    pool.map(_oracle_targets, [np.arange(2) for _ in range(procs)])
+    return pool
+
+
+def oracle_sample(wl, n_ves=24, n_targets=2048, procs=1, pool=None):
     """Time the FP64 oracle on a bounded sample of the workload and extrapolate one full step.
 
-    Per-vesicle part: an oracle step of the first n_ves vesicles (their mutual far field is
-    included, negligible). Far field: n_targets sampled targets against all sources. Full step
-    time = M * t_vesicle + P * t_target.
+    Per-vesicle part: oracle steps of n_ves vesicles per process (each process a sub-suspension of
+    consecutive vesicles; their mutual far field is included, negligible). Far field: n_targets sampled
+    targets per process against all sources. With procs > 1 the processes (spawned, one BLAS thread each)
+    run at once on the host cores, and a part's time is the slowest process's. Full step time =
+    M * t_vesicle + P * t_target, t_vesicle and t_target the part's time over the units all processes
+    handled.
     """
-    import contextlib
+    P = int(sum(len(x) for x in wl.xs))
+    pv = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True)
+    stride = max(1, wl.M // (n_ves * procs))
+    jobs = []
+    for k in range(procs):
+        idx = [(k * n_ves + i) * stride % wl.M for i in range(n_ves)]
+        jobs.append(([wl.xs[i] for i in idx], [wl.ys[i] for i in idx], pv))
+    tg = np.linspace(0, P - 1, n_targets * procs).astype(np.int64)
+    tgs = [tg[k::procs] for k in range(procs)]
+    own = pool is None and procs > 1
+    if own or (procs == 1 and _ORACLE_SOURCES is None):
+        pool = oracle_pool(wl, procs)
     try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:  # BLAS threads are already pinned through the environment
-        def threadpool_limits(limits):
-            return contextlib.nullcontext()
-    from oracle.farfield import far_field
-    from oracle.spectral import force
-    from oracle.step import Params, Suspension
-    with threadpool_limits(limits=threads):
-        p = Params(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True)
-        sub = Suspension(wl.xs[:n_ves], wl.ys[:n_ves], p)
-        t0 = time.perf_counter()
-        sub.step()
-        t_v = (time.perf_counter() - t0) / n_ves
-        fx, fy = [], []
-        for x, y in zip(wl.xs, wl.ys):
-            a, b = force(x, y, np.zeros(len(x)), wl.kappa)
-            fx.append(a)
-            fy.append(b)
-        P = int(sum(len(x) for x in wl.xs))
-        tg = np.linspace(0, P - 1, n_targets).astype(np.int64)
-        t0 = time.perf_counter()
-        far_field(wl.xs, wl.ys, fx, fy, wl.mu, near_mask=True, targets=tg)
-        t_t = (time.perf_counter() - t0) / n_targets
+        if procs == 1:
+            t_v = _oracle_vesicles(jobs[0]) / n_ves
+            t_t = _oracle_targets(tgs[0]) / n_targets
+        else:
+            t_v = max(pool.map(_oracle_vesicles, jobs)) / (n_ves * procs)
+            t_t = max(pool.map(_oracle_targets, tgs)) / (n_targets * procs)
+    finally:
+        if own:
+            pool.close()
+            pool.join()
     full = wl.M * t_v + P * t_t
-    return {"value": wl.M / full, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "FP64 numpy oracle: plain step of %d of the %d vesicles + far field at %d of %d targets "
-                      "against all sources; one full step extrapolated linearly (%.1f s)" % (n_ves, wl.M, n_targets,
-                                                                                           P, full)}
+    return {"value": wl.M / full, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": "FP64 numpy oracle in %d process%s of one BLAS thread: plain steps of %d of the %d vesicles "
+                      "+ far field at %d of %d targets against all sources; one full step extrapolated linearly "
+                      "(%.1f s)" % (procs, "es" if procs > 1 else "", n_ves * procs, wl.M, n_targets * procs, P,
+                                    full)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ------------------------------------------------------------------------------------------ main
@@ -212,14 +273,19 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args)
+    procs = host_cores()
+    pool = oracle_pool(wl, procs)
     for _ in range(args.warmup):
-        oracle_sample(wl, n_ves=2, n_targets=64)
+        oracle_sample(wl, n_ves=1, n_targets=32, procs=procs, pool=pool)
     vals, times = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle_sample(wl, n_ves=2, n_targets=96)
+        r = oracle_sample(wl, n_ves=2, n_targets=96, procs=procs, pool=pool)
         times.append(time.perf_counter() - t0)
         vals.append(r["value"])
+    if pool is not None:
+        pool.close()
+        pool.join()
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.M / v, "higher_is_better": True,
@@ -227,9 +293,10 @@ def run_reference(args):
             "config": config_of(wl, args, {"impl": "FP64 CPU oracle (numpy), sampled", "mode": "plain BIE step",
                                            "farfield": "fp64 brute force (oracle)",
                                            "launch": "numpy on the host cores, one vesicle at a time"}),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: oracle plain step of 2 vesicles + far field at 96 targets "
-                                       "against all sources, extrapolated to the full step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "per step: %d processes (one per host core, one BLAS thread each), each an "
+                                       "oracle plain step of 2 vesicles + far field at 96 targets against all "
+                                       "sources, extrapolated to the full step" % procs},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -265,6 +332,69 @@ def farfield_alone(stream, reps=10):
     return out
 
 
+def _profile_steps(sus, n):
+    """Per-kernel CUDA-event times over n steps: {kernel: (ms, launches)}."""
+    sus.profile(True)
+    sus.step(n)
+    prof = sus.profile_read()
+    sus.profile(False)
+    return prof
+
+
+def near_field_arm(args, stream):
+    """The plain step on the dense Poiseuille suspension with every tenth vesicle moved to 0.7 spacings h
+    from its neighbour (workloads.poiseuille_dense, close_fraction 0.1): near pairs from the first step, so
+    the five-layer RBF correction (k_near_*) does work. Pairs that close are not resolved by the explicit
+    inter-vesicle coupling at the headline time step (their gaps jitter and the area/length correction
+    stops converging within about 15 steps), so this arm takes a time step ten times smaller. Reports the
+    near pairs of the first and the last step and the near-field kernels' time beside the step's."""
+    from paper_2606_25569_b300 import binding
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    wl = poiseuille_dense(args.M, args.N, seed=5, close_fraction=0.1, close_gap=0.7)
+    dt = wl.dt / 10
+    sus = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=dt, corr_tol=0.01,
+                             flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True)
+    sus.step(1)
+    sus.sync()
+    first = sus.counters()["near_pairs"]
+    sus.step(2)
+    sus.sync()
+    n = max(4, args.steps)
+    ms = _time_steps(sus, n, stream)
+    c = sus.counters()
+    prof = _profile_steps(sus, n)
+    c2 = sus.counters()
+    sus.close()
+    near_ms = {k: round(v[0] / n, 4) for k, v in prof.items() if k.startswith("k_near")}
+    return {"workload": wl.name + ", dt = headline dt / 10", "value": wl.M / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "steps_timed": n, "near_pairs_first_step": first,
+            "near_pairs_last_step": c2["near_pairs"], "corrections_total": c2["corrections"], "err": c2["err"],
+            "near_field_ms_per_step": round(sum(near_ms.values()), 4), "near_kernels_ms_per_step": near_ms}
+
+
+def uneven_arm(args, stream):
+    """The plain step on the dense Poiseuille lattice with vesicles of 32, 64 and 128 points in turn
+    (2000 vesicles, 149,333 points): the symmetric far field (vesicles in classes of 1, 2, 4 segments) against
+    the per-target kernel."""
+    from paper_2606_25569_b300 import binding
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    wl = poiseuille_dense(args.M, (32, 64, 128), seed=5)
+    out = {"workload": wl.name, "points": int(wl.offsets[-1]), "unit": UNIT}
+    for name, extra in (("symmetric", {}), ("per_target", {"farfield_per_target": True})):
+        sus = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                                 flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream,
+                                 use_graph=True, **extra)
+        sus.step(3)
+        sus.sync()
+        n = max(4, args.steps)
+        ms = _time_steps(sus, n, stream)
+        prof = _profile_steps(sus, n)
+        sus.close()
+        ff = sum(v[0] for k, v in prof.items() if k.startswith("k_farfield")) / n
+        out[name] = {"value": wl.M / (ms * 1e-3), "ms_per_step": ms, "far_field_ms_per_step": round(ff, 4)}
+    return out
+
+
 def _time_steps(sus, n, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,31 +411,55 @@ def long_run_arms(wl, args, stream):
       near pairs or within four spacings of another vesicle; the network trained on the GPU on exact
       relaxation pairs of a differently seeded suspension (64 snapshots 15 steps apart);
     * farfield_multipole: the plain step with the vesicle-multipole far field;
-    * hybrid_multipole: both.
+    * hybrid_multipole: both;
+    * hybrid_flow (and hybrid_flow_multipole): the hybrid step with the advection and the tension of every step
+      from two more networks (Sec. 3.2, Eqs. advectionMap and advTenMap), trained on exact columns of the
+      same snapshots.
     Each reports its throughput (CUDA events) and the mean over vesicles of the centred relative shape
     error (App. B) against the plain step after 10 .. args.hybrid_steps steps."""
     from paper_2606_25569_b300 import binding, train
     from paper_2606_25569_b300.workloads import poiseuille_dense
-    kmax, exact_every, width = 16, 2, 1024
+    kmax, exact_every, width, Kf, Kout = 16, 2, 1024, FLOW_KF, FLOW_KOUT
     t0 = time.time()
-    X, Y = train.relaxation_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 64, 15, stream, kmax)
+    X, Y, A, T = train.hybrid_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 64, 15, stream, kmax, Kf, Kout)
     t_data = time.time() - t0
-    r = train.train_relaxation(X, Y, hidden=(width, width, width), epochs=40, batch=1024, lr=1e-3, lr_min=1e-5,
-                               stream=stream, serve_batch=wl.M)
+    hid = (width, width, width)
+    r = train.train_relaxation(X, Y, hidden=hid, epochs=40, batch=1024, lr=1e-3, lr_min=1e-5, stream=stream,
+                               serve_batch=wl.M)
     t_train = time.time() - t0 - t_data
-    net = {"dims": r["dims"], "train_samples": int(X.shape[0]), "train_steps": r["steps"],
-           "holdout_rel_err_mean": float(np.mean(r["holdout_err"])), "data_seconds": round(t_data, 1),
-           "train_seconds": round(t_train, 1), "input_filter_kmax": kmax, "features": "Fourier, normalised"}
+    ra = train.train_relaxation(X, A, hidden=hid, epochs=FLOW_EPOCHS, batch=1024, lr=1e-3, lr_min=1e-5, beta=0.0,
+                                stream=stream, serve_batch=wl.M)
+    rt = train.train_relaxation(X, T, hidden=hid, epochs=FLOW_EPOCHS, batch=1024, lr=1e-3, lr_min=1e-5, beta=0.0,
+                                stream=stream, serve_batch=wl.M)
+    t_flow = time.time() - t0 - t_data - t_train
+    del X, Y, A, T
+    net = {"dims": r["dims"], "train_samples": int(r["train_err"].shape[0] + r["holdout_err"].shape[0]),
+           "train_steps": r["steps"], "holdout_rel_err_mean": float(np.mean(r["holdout_err"])),
+           "data_seconds": round(t_data, 1), "train_seconds": round(t_train, 1), "input_filter_kmax": kmax,
+           "features": "Fourier, normalised"}
+    flow_nets = {"advection": {"dims": ra["dims"], "holdout_rel_err_mean": float(np.mean(ra["holdout_err"])),
+                               "train_steps": ra["steps"]},
+                 "tension": {"dims": rt["dims"], "holdout_rel_err_mean": float(np.mean(rt["holdout_err"])),
+                             "train_steps": rt["steps"]},
+                 "velocity_modes_Kf": Kf, "column_modes_Kout": Kout, "train_seconds": round(t_flow, 1),
+                 "maps": "advection (I - M) psi_k and tension L^-1 P psi_k, L^-1 P B X in the standard frame "
+                         "(Eqs. advectionMap, advTenMap, S_sigma), learned in every step"}
     kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
               near_field=True, stream=stream, use_graph=True)
     variants = {"hybrid": dict(mode=1, exact_every=exact_every),
                 "farfield_multipole": dict(farfield_multipole=True),
-                "hybrid_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True)}
+                "hybrid_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True),
+                "hybrid_flow": dict(mode=1, exact_every=exact_every, flow=True),
+                "hybrid_flow_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True, flow=True)}
 
     def make(cfg):
+        cfg = dict(cfg)
+        flow = cfg.pop("flow", False)
         sus = binding.Suspension(wl.flat_xy(), wl.offsets, **cfg, **kw)
         if cfg.get("mode", 0) == 1:
             sus.set_network(r["net"], r["scale"], kmax)
+        if flow:
+            sus.set_flow_networks(ra["net"], rt["net"], Kf, Kout)
         return sus
 
     out = {}
@@ -326,6 +480,8 @@ def long_run_arms(wl, args, stream):
         if prof:
             out[name]["far_field_ms_per_step"] = sum(v[0] for k, v in prof.items()
                                                      if k in ("k_ff_moments", "k_ff_local", "k_farfield_loc")) / 2
+        if cfg.get("flow"):
+            out[name]["flow_networks"] = flow_nets
         if cfg.get("mode", 0) == 1:
             out[name]["net"] = net
             out[name]["exact_every"] = exact_every
@@ -368,6 +524,8 @@ def long_run_arms(wl, args, stream):
         if name in failed:
             out[name]["failed"] = failed[name]
     r["net"].close()
+    ra["net"].close()
+    rt["net"].close()
     return out
 
 
@@ -454,7 +612,7 @@ def run_gpu(args):
                 "frac": achieved / peak_issue, "traffic": FFS_DRAM_BYTES,
                 "traffic_source": FFS_DRAM_SOURCE,
                 "peak_source": "issue: 4 schedulers x 32 lanes x 148 SMs x median SM clock (derived); "
-                               "achieved counts 20 instructions per unordered pair (18 FP32 + lg2 + rcp)",
+                               "achieved counts 21 instructions per unordered pair (19 FP32 + lg2 + rcp)",
                 "share_of_step": dom_ms / total_prof}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
@@ -502,6 +660,8 @@ def run_gpu(args):
                   "corrections_per_step": (s.counters()["corrections"] - c0) / args.steps}
 
     ff_alone = farfield_alone(stream) if rank == 0 and not args.no_farfield_alone else None
+    near_arm = near_field_arm(args, stream) if rank == 0 and not args.no_near_arm else None
+    uneven = uneven_arm(args, stream) if rank == 0 and not args.no_uneven_arm else None
     arms = {}
     if rank == 0 and not args.no_hybrid:
         arms = long_run_arms(wl, args, stream)
@@ -509,7 +669,10 @@ def run_gpu(args):
             v["vs_plain"] = v["value"] / (value / world)  # both single-GPU throughputs
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(wl)
+        procs = host_cores()
+        cpu = oracle_sample(wl, procs=procs)
+        one = oracle_sample(wl, n_ves=8, n_targets=512)
+        cpu["single_core"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -529,7 +692,8 @@ def run_gpu(args):
                 "clocks": clocks, "kernel_ms_per_launch": breakdown, "kernel_ms_per_step": per_step,
                 "steady_state": steady, "hybrid": arms.get("hybrid"),
                 "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
-                "farfield_2000x128": ff_alone,
+                "hybrid_flow": arms.get("hybrid_flow"), "hybrid_flow_multipole": arms.get("hybrid_flow_multipole"),
+                "farfield_2000x128": ff_alone, "near_field": near_arm, "uneven": uneven,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -220,6 +220,39 @@ vs_status vs_set_network(vs_suspension* s, int32_t which, vs_mlp* net, double ou
  * on. Does not change the suspension's state. Asynchronous. */
 vs_status vs_relax(vs_suspension* s, const double* xy_in, double* xy_out);
 
+/*
+ * Learned advection and tension (Sec. 3.2: Eq. advectionMap X_u^k: X -> (I - M) e^{ik alpha}, Eq. advTenMap
+ * S_u^k: X -> L^{-1} P e^{ik alpha}, and S_sigma: X -> L^{-1} P B X; Table tab:networks). In each vesicle's
+ * standard frame (vs_standardize) the interaction velocity u is expanded in the real Fourier modes
+ * k = 0..Kf of each component: with its features f (a_0..a_Kf, b_1..b_Kf of x, then of y, as the network
+ * input of vs_set_network), u = sum_i f_i psi_i for modes <= Kf, psi_i one component equal to 1, 2 cos(k
+ * alpha) or -2 sin(k alpha). Two networks give, per vesicle, the columns of the maps at the standardised
+ * shape, each represented by its Fourier features up to Kout:
+ *   advection network: row = [ (I - M) psi_0 | (I - M) psi_1 | ... ], 2 (2 Kout + 1) floats per column,
+ *     zero-padded to flow_adv_width = 16 ceil((4 Kf + 2) 2 (2 Kout + 1) / 16);
+ *   tension network: row = [ L^{-1} P B X | L^{-1} P psi_0 | ... ], 2 Kout + 1 floats each, zero-padded to
+ *     flow_ten_width = 16 ceil((4 Kf + 3)(2 Kout + 1) / 16);
+ * both with the input of the relaxation network (its width and filter_kmax). (I - M) and L^{-1} P do not
+ * depend on the vesicle's size; L^{-1} P B X is that of the unit-length shape over L^2.
+ *
+ * vs_set_flow_networks: a hybrid suspension (mode 1) with these networks set takes, in every step, the
+ * advection X* = X^n + dt R^T shift(sum_i f_i Q_i) and the tension sigma^{n+1} = -shift(S_sigma) / L^2 -
+ * shift(sum_i f_i S_i) from them (modes of u above Kf dropped) instead of the exact operators, which it
+ * then no longer builds at X^n or X^{n+1} (only for the source vesicles of near pairs, whose near-field
+ * layers need them); the relaxation stays as vs_set_network and exact_every arrange. The relaxation
+ * network must be set first; adv and ten are borrowed, share the suspension's stream, have batch capacity
+ * >= M; Kf, Kout in [0, N/2 - 1]; both NULL removes them. Errors: VS_ERR_INVALID_ARG.
+ *
+ * vs_flow_maps: training data of the two networks from the exact operators. For the suspension's current
+ * points (equal N): xin (DEVICE FP32, M x W) = the network input (filter_kmax as for vs_set_network),
+ * adv (DEVICE FP32, M x flow_adv_width) and ten (DEVICE FP32, M x flow_ten_width) = the rows above, computed
+ * at each vesicle's standardised shape with the operators of the step (FP64-accurate). The suspension's
+ * state and its operator cache for the next step are left as they were. Synchronous; allocates scratch.
+ */
+vs_status vs_set_flow_networks(vs_suspension* s, vs_mlp* adv, vs_mlp* ten, int32_t Kf, int32_t Kout);
+vs_status vs_flow_maps(vs_suspension* s, int32_t Kf, int32_t Kout, int32_t filter_kmax, float* xin, float* adv,
+                       float* ten);
+
 /* Training pairs of the relaxation map: for DEVICE points xy_in (CSR blocks, equal N), xin (device
  * FP32, M x W) = the network input of vs_set_network's map and yout (device FP32, M x W) = the
  * features of (relax(xy_in) - xy_in) in each vesicle's standard frame, divided by out_scale; W and the
@@ -287,7 +320,7 @@ vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, in
 /*
  * Learned part (Sec. 3.2-3.4): a fully connected network (ReLU hidden layers, affine output)
  * evaluated and trained on the tensor cores with BF16 operands and FP32 accumulation.
- *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 4096]; d_L <= 1024.
+ *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 4096].
  *  max_batch   largest batch a call may pass.
  *  ncomp, beta the loss ||Yhat - Y||/||Y|| + beta ||D(Yhat - Y)||/||D Y|| averaged over the batch,
  *              D the periodic difference inside each of ncomp equal blocks of an output row
@@ -344,11 +377,17 @@ void vs_mlp_destroy(vs_mlp* m);
  * keeps all of its scratch in one static device array of fixed size that is part of the library
  * image, so it calls no cudaMalloc / cudaFree and no allocating library routine.
  *  offsets      host, M+1 int64 (as in vs_create); at most VS_STATIC_MAX_VESICLES vesicles and
- *               VS_STATIC_MAX_POINTS points in total; N_v even in [8, 128].
+ *               VS_STATIC_MAX_POINTS points in total; N_v even in [8, 128]. Validated on the host,
+ *               then copied to the device with cudaMemcpyAsync on cuda_stream: pageable memory may be
+ *               reused once the call returns; page-locked memory must stay unchanged until the stream
+ *               has executed the call.
  *  precision    0: compensated FP32, 1: FP64.
  *  xy, f        DEVICE, CSR blocks (2P doubles each); u DEVICE output (2P doubles, overwritten).
  *  cuda_stream  stream for all work (NULL = legacy default stream). Asynchronous.
- * Sizes beyond the limits, odd or out-of-range N, null pointers: VS_ERR_INVALID_ARG.
+ * Sizes beyond the limits, odd or out-of-range N, null pointers: VS_ERR_INVALID_ARG. A failed
+ * launch or copy: VS_ERR_CUDA. The kernels have no data-dependent error conditions here (the near
+ * test, whose list overflow is the far field's only one, is off), so there is no device error word
+ * to read back.
  * The scratch array (about 13 MB) is reserved on every GPU that loads the library until the
  * process exits. The first call on a device does a one-time set-up on that device (looks up the
  * array's device address and fills its tables with one kernel); make that first call outside

@@ -41,6 +41,10 @@ FUNCTIONS = {
     "vs_set_network": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double,
                                       ctypes.c_int32]),
     "vs_relax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_set_flow_networks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32]),
+    "vs_flow_maps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
     "vs_training_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, ctypes.c_int32]),
     "vs_checkpoint_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -229,6 +233,17 @@ class Suspension:
         self._check(lib().vs_set_network(self._h, int(which), net._h if net is not None else None, float(out_scale),
                                          int(filter_kmax)))
 
+    def set_flow_networks(self, adv, ten, Kf, Kout):
+        """Learned advection and tension (vs_set_flow_networks); None, None removes them."""
+        self._flow = (adv, ten)  # the library borrows them
+        self._check(lib().vs_set_flow_networks(self._h, adv._h if adv is not None else None,
+                                               ten._h if ten is not None else None, int(Kf), int(Kout)))
+
+    def flow_maps(self, Kf, Kout, filter_kmax, xin_dev, adv_dev, ten_dev):
+        """Training rows of the advection and tension networks at the current points (vs_flow_maps)."""
+        self._check(lib().vs_flow_maps(self._h, int(Kf), int(Kout), int(filter_kmax), _ptr(xin_dev), _ptr(adv_dev),
+                                       _ptr(ten_dev)))
+
     def relax(self, xy_in_dev, xy_out_dev):
         self._check(lib().vs_relax(self._h, _ptr(xy_in_dev), _ptr(xy_out_dev)))
 
@@ -332,6 +347,12 @@ def batched_inverse32(a_dev, out_dev, n, batch, stream=None):
     if st != 0:
         raise VsError(st, "vs_batched_inverse32 failed")
     return fb.value
+
+
+def flow_widths(Kf, Kout):
+    """Output widths (advection, tension) of the flow networks (vs_set_flow_networks)."""
+    nb, po = 4 * Kf + 2, 2 * Kout + 1
+    return (nb * 2 * po + 15) // 16 * 16, ((nb + 1) * po + 15) // 16 * 16
 
 
 def feature_width(N, kmax):

@@ -11,7 +11,11 @@
 // vesicle) the centre difference is formed once from float hi/lo splits, so |r| keeps relative
 // accuracy for close pairs in a large box. Per-vesicle partial sums are FP32 and are added to the
 // running total with Neumaier compensation. -log|r| = -(ln 2 / 2) log2(|r|^2), with lg2 and rcp on
-// the special-function unit.
+// the special-function unit. A vesicle's densities sum to (nearly) zero, so its terms g_j log|r_j|^2 nearly
+// cancel: each log argument is scaled by s = 2^-e, the power of two nearest below 1 / (|x_i - c_v|^2 +
+// reach_v^2), which keeps the logarithms and the FP32 partial sums small for a distant vesicle (the scaled
+// argument is near 1, where lg2 is most accurate), and e times the vesicle's density sum (summed in FP64) is
+// added once per (target, source vesicle).
 //
 // One thread per target; source vesicles are staged through shared memory in chunks of whole
 // vesicles (chunk boundaries precomputed on the host, at most CHUNK points each). THREADS and CHUNK
@@ -36,6 +40,14 @@ __device__ __forceinline__ float fast_rcp(float x) {
   return y;
 }
 
+// The power of two 2^-e with S 2^-e in [1, 2) (S > 0, normal), and e: a log-argument scale whose logarithm
+// is exact and whose product with |r|^2 is exact.
+__device__ __forceinline__ float pow2_scale(float S, float& e) {
+  const int ex = ((__float_as_int(S) >> 23) & 0xff) - 127;
+  e = (float)ex;
+  return __int_as_float((127 - ex) << 23);
+}
+
 __device__ __forceinline__ void neumaier_add(float& s, float& c, float p) {
   const float t = s + p;
   c += (fabsf(s) >= fabsf(p)) ? ((s - t) + p) : ((p - t) + s);
@@ -44,16 +56,17 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float p) {
 
 // Sum over the sources j0..j1-1 (shared memory) of one vesicle for the target at (qx, qy) in the
 // vesicle's frame; with MIN the smallest |r|^2 is tracked too.
+// The log arguments are scaled by sc (see k_farfield_f32).
 template <bool MIN>
-__device__ __forceinline__ void ff_sum(const float4* sh, int j0, int j1, float qx, float qy, float& ax, float& ay,
-                                       float& lx, float& ly, float& mn) {
+__device__ __forceinline__ void ff_sum(const float4* sh, int j0, int j1, float qx, float qy, float sc, float& ax,
+                                       float& ay, float& lx, float& ly, float& mn) {
 #pragma unroll 16
   for (int j = j0; j < j1; ++j) {
     const float4 s = sh[j];
     const float rx = qx - s.x, ry = qy - s.y;
     const float r2 = fmaf(rx, rx, ry * ry);
     if (MIN) mn = fminf(mn, r2);
-    const float lg = fast_lg2(r2);
+    const float lg = fast_lg2(r2 * sc);
     const float inv = fast_rcp(r2);
     lx = fmaf(lg, s.z, lx);
     ly = fmaf(lg, s.w, ly);
@@ -80,7 +93,8 @@ struct FarFieldArgs {
 template <int THREADS, int CHUNK>
 __global__ void __launch_bounds__(THREADS) k_farfield_f32(FarFieldArgs a, const float4* __restrict__ src,
                                                           const float4* __restrict__ centre32,
-                                                          const float2* __restrict__ h2) {
+                                                          const float2* __restrict__ h2,
+                                                          const float2* __restrict__ gsum) {
   __shared__ float4 sh[CHUNK];
   const int64_t t = (int64_t)blockIdx.x * THREADS + threadIdx.x;
   const bool valid = t < a.P;
@@ -105,19 +119,23 @@ __global__ void __launch_bounds__(THREADS) k_farfield_f32(FarFieldArgs a, const 
       const int j0 = (int)(a.voff[sv] - p0), j1 = (int)(a.voff[sv + 1] - p0);
       const float2 nr = h2[sv];
       // the minimum distance is only needed when the target lies within reach of the vesicle
-      const bool test = a.near_mask && fmaf(qx, qx, qy * qy) <= nr.y;
+      const float q2 = fmaf(qx, qx, qy * qy);
+      const bool test = a.near_mask && q2 <= nr.y;
+      float le;
+      const float ls = pow2_scale(q2 + nr.y, le);
       float ax = 0.f, ay = 0.f, lx = 0.f, ly = 0.f, mn = 3.0e38f;
       if (test)
-        ff_sum<true>(sh, j0, j1, qx, qy, ax, ay, lx, ly, mn);
+        ff_sum<true>(sh, j0, j1, qx, qy, ls, ax, ay, lx, ly, mn);
       else
-        ff_sum<false>(sh, j0, j1, qx, qy, ax, ay, lx, ly, mn);
+        ff_sum<false>(sh, j0, j1, qx, qy, ls, ax, ay, lx, ly, mn);
       if (test && mn <= nr.x) {
         if (ncnt < MAX_NEAR) a.near_v[t * MAX_NEAR + ncnt] = sv;
         else atomicOr(a.err, ERR_NEAR_OVERFLOW);
         ++ncnt;
       } else {
-        neumaier_add(sx, cx, fmaf(hl2, lx, ax));
-        neumaier_add(sy, cy, fmaf(hl2, ly, ay));
+        const float2 gs = gsum[sv];
+        neumaier_add(sx, cx, fmaf(hl2, fmaf(le, gs.x, lx), ax));
+        neumaier_add(sy, cy, fmaf(hl2, fmaf(le, gs.y, ly), ay));
       }
     }
   }

@@ -1,5 +1,4 @@
-// Symmetric evaluation of the all-pairs far-field single-layer sum (Sec. 2.2.2, Sec. 4.1, Algorithm 4)
-// for suspensions whose vesicles all have N = 32 R points.
+// Symmetric evaluation of the all-pairs far-field single-layer sum (Sec. 2.2.2, Sec. 4.1, Algorithm 4).
 //
 // The 2D Stokeslet is even in r: G(-r) = G(r), with G(r) g = -log|r| g + (r . g) r / |r|^2. So one
 // evaluation of the pair (x_i in vesicle A, X_j in vesicle B) gives both reactions: the velocity at x_i
@@ -7,16 +6,23 @@
 // unordered pair of distinct vesicles is visited once, which halves the special-function work of the
 // per-target kernel (k_farfield_f32) and cuts the FP32 work per ordered pair by about a third.
 //
-// Work decomposition. Vesicles are grouped in chunks of FFS_V; a tile is a pair of chunks (I, J), I <= J.
-// A CTA stages chunk J's points (the columns) in shared memory and its W warps take the row vesicles of
-// chunk I, one per warp. For a row vesicle A and a column vesicle B the lanes hold A's points
-// (lane + 32 r) in registers; at step k = 0..31 lane l pairs them with B's points ((l + k) mod 32) + 32 c,
-// read from a shared-memory copy in which each 32-point segment is stored twice so that the index never
-// wraps. The row reactions accumulate in place; the column reactions accumulate in registers that are
-// passed one lane down after every step, so that after 32 steps lane l holds the total for B's points
-// l + 32 c. Warps visit the column vesicles in a rotated order (warp w takes column (w + k) mod n_J at
-// iteration k, a barrier between iterations), so no two warps add into the same column accumulators at
-// once and every accumulator receives its terms in a fixed order.
+// Uneven point counts. Each vesicle is handled as R = 1, 2 or 4 segments of 32 points (its class: N <= 32,
+// <= 64, <= 128). Its sources are copied into a padded array of 32 R entries (k_ffs_pad); a padding entry
+// repeats the vesicle's first point with zero density, so it adds nothing as a source and changes no
+// distance minimum, and what is computed for it as a target is discarded. The kernel works in the
+// symmetric order, the vesicles sorted by class (4, 2, 1), cut into chunks of at most FFS_V vesicles of one
+// class; a tile is a pair of chunks (I, J), I <= J, so its rows are of class R_I >= R_J of its columns, and
+// each pair of classes has its own instantiation k_farfield_sym<R_I, R_J> and persistent launch.
+//
+// Work decomposition. A CTA stages chunk J's padded points (the columns) in shared memory and its W warps
+// take the row vesicles of chunk I, one per warp. For a row vesicle A and a column vesicle B the lanes
+// hold A's points (lane + 32 r) in registers; at step k = 0..31 lane l pairs them with B's points
+// ((l + k) mod 32) + 32 c, read from a shared-memory copy in which each 32-point segment is stored twice
+// so that the index never wraps. The row reactions accumulate in place; the column reactions accumulate
+// in registers that are passed one lane down after every step, so that after 32 steps lane l holds the
+// total for B's points l + 32 c. Warps visit the column vesicles in a rotated order (warp w takes column
+// (w + k) mod n_J at iteration k, a barrier between iterations), so no two warps add into the same column
+// accumulators at once and every accumulator receives its terms in a fixed order.
 //
 // Near pairs (Sec. 4.1, Algorithm 4): the minimum |r|^2 over B (for each target of A) and over A (for each
 // target of B) is tracked only when the two vesicles' reach circles overlap; a target with min |r|^2 <= h^2
@@ -24,14 +30,20 @@
 // atomics and sorted by the reduction kernel, so they equal the per-target kernel's (ascending source
 // vesicle, at most MAX_NEAR; more sets ERR_NEAR_OVERFLOW).
 //
+// Common logarithm: the densities of a vesicle sum to (nearly) zero, so its terms g_j log|r_j|^2 nearly
+// cancel. Each log argument is scaled by s = 2^-e, the power of two nearest below 1 / (|c_A - c_B|^2 +
+// reach_A^2 + reach_B^2), the same for both reactions of the pair: log2(|r|^2 s) is small for separated
+// vesicles, which keeps the FP32 partial sums small, and e times the source vesicle's density sum (summed in
+// FP64) is added once per pair (Sum_j g_j log2|r_j|^2 = Sum_j g_j log2(|r_j|^2 s) + e Sum_j g_j; the scaling
+// and e are exact).
+//
 // Precision: per (target, source vesicle) partial sums in FP32 as in k_farfield_f32, added to running
 // sums with Neumaier compensation (registers for the rows, shared memory for the columns). Tile (I, J)
 // writes the contributions of chunk J to the points of chunk I and those of chunk I to the points of
 // chunk J into slots part[J][.] and part[I][.] (each slot written exactly once, as the compensated float
 // pair); k_farfield_sym_reduce adds the slots of each point in chunk order in double-float arithmetic
-// (FP64 adds run at 1/64 of the FP32 rate on this part).
-// The result is deterministic and independent of which CTA takes which tile; it differs from the
-// per-target kernel's by FP32 rounding only.
+// (FP64 adds run at 1/64 of the FP32 rate on this part). The result is deterministic and independent of
+// which CTA takes which tile; it differs from the per-target kernel's by FP32 rounding only.
 #pragma once
 #include "dfloat.cuh"
 #include "k_farfield.cuh"
@@ -47,22 +59,37 @@ constexpr int FFS_V = 16;  // vesicles per chunk
 constexpr int FFS_W = 8;   // warps per CTA
 
 struct FfSymArgs {
-  int64_t P;           // points (targets = sources)
-  int M, N;            // vesicles, points per vesicle (all equal)
-  int nchunk, ntile;
-  const int2* tiles;   // [ntile] (I, J), I <= J
-  unsigned* tile_ctr;  // next tile; zero before each launch
+  int64_t P;            // real points (targets = sources)
+  int M;
+  int nchunk;
   int near_mask;
-  float4* part;        // [nchunk][P]: velocity at each point from the vesicles of one chunk (x sum and
-                       // compensation, y sum and compensation)
-  int* near_cnt;       // [P], zero before each launch when near_mask
-  int* near_v;         // [P * MAX_NEAR]
+  float4* part;         // [nchunk][P]: velocity at each point from the vesicles of one chunk (x sum and
+                        // compensation, y sum and compensation)
+  int* near_cnt;        // [P], zero before each launch when near_mask
+  int* near_v;          // [P * MAX_NEAR]
   unsigned* err;
+  // the symmetric order: position s holds vesicle vid[s]; classes (segments R) descending
+  const int* vid;       // [M]
+  const int64_t* poff;  // [M] first entry of s in the padded sources (32 R_s entries each)
+  const int64_t* roff;  // [M] first point of s in the point arrays
+  const int* nreal;     // [M] points of s
+  const int2* chunk;    // [nchunk] (first position, vesicles)
+  const float4* psrc;   // padded sources (x - c_v, y - c_v, g_x, g_y)
 };
 
-// Shared memory of one CTA (float4 units): the staged column chunk (2N per vesicle) and the
-// column accumulators (N per vesicle: sum_x, comp_x, sum_y, comp_y).
-inline size_t ffs_smem_bytes(int N) { return (size_t)FFS_V * 3 * N * sizeof(float4); }
+// The tiles of one pair of classes and their counter.
+struct FfSymTiles {
+  const int2* tiles;   // [ntile] (I, J), I <= J
+  int ntile;
+  unsigned* ctr;       // next tile; zero before each launch
+};
+
+// Shared memory of one CTA (float4 units): the staged column chunk (64 per segment: each 32-point
+// segment twice) and the column accumulators (32 per segment: sum_x, comp_x, sum_y, comp_y).
+inline size_t ffs_smem_bytes(int RC) { return (size_t)FFS_V * 3 * 32 * RC * sizeof(float4); }
+
+// Segments (of 32 points) of a vesicle of N points in the symmetric kernel.
+__host__ __device__ inline int ffs_segments(int N) { return N <= 32 ? 1 : N <= 64 ? 2 : 4; }
 
 __device__ __forceinline__ void ffs_near(const FfSymArgs& a, int64_t t, int v) {
   const int slot = atomicAdd(&a.near_cnt[t], 1);
@@ -72,31 +99,32 @@ __device__ __forceinline__ void ffs_near(const FfSymArgs& a, int64_t t, int v) {
 
 // One (row vesicle A, column vesicle B) pair: row targets (tx, ty) relative to B's centre with their own
 // densities rp.zw (and hl2 times them in gxs, gys); B's staged points at colB. Row partial sums in
-// lx..ay, column partial sums (log term already scaled) in ux, uy; minima when MIN.
-template <int R, bool MIN>
-__device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int lane, const float (&tx)[R],
-                                         const float (&ty)[R], const float4 (&rp)[R], const float (&gxs)[R],
-                                         const float (&gys)[R], float (&lx)[R], float (&ly)[R], float (&ax)[R],
-                                         float (&ay)[R], float (&mr)[R], float (&ux)[R], float (&uy)[R],
-                                         float (&mc)[R]) {
+// lx..ay, column partial sums (log term already scaled) in ux, uy; minima when MIN. The log arguments are
+// scaled by sc.
+template <int RR, int RC, bool MIN>
+__device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int lane, float sc, const float (&tx)[RR],
+                                         const float (&ty)[RR], const float4 (&rp)[RR], const float (&gxs)[RR],
+                                         const float (&gys)[RR], float (&lx)[RR], float (&ly)[RR], float (&ax)[RR],
+                                         float (&ay)[RR], float (&mr)[RR], float (&ux)[RC], float (&uy)[RC],
+                                         float (&mc)[RC]) {
   const int from = (lane + 1) & 31;
   const float4* base = colB + lane;
 #pragma unroll FFS_STEPS_UNROLLED
   for (int k = 0; k < 32; ++k) {
-    float4 s[R];
+    float4 s[RC];
 #pragma unroll
-    for (int c = 0; c < R; ++c) s[c] = base[c * 64 + k];
+    for (int c = 0; c < RC; ++c) s[c] = base[c * 64 + k];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < RR; ++r)
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
+      for (int c = 0; c < RC; ++c) {
         const float rx = tx[r] - s[c].x, ry = ty[r] - s[c].y;
         const float r2 = fmaf(rx, rx, ry * ry);
         if (MIN) {
           mr[r] = fminf(mr[r], r2);
           mc[c] = fminf(mc[c], r2);
         }
-        const float lg = fast_lg2(r2);
+        const float lg = fast_lg2(r2 * sc);
         const float inv = fast_rcp(r2);
         lx[r] = fmaf(lg, s[c].z, lx[r]);
         ly[r] = fmaf(lg, s[c].w, ly[r]);
@@ -110,7 +138,7 @@ __device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int la
         uy[c] = fmaf(qt, ry, uy[c]);
       }
 #pragma unroll
-    for (int c = 0; c < R; ++c) {
+    for (int c = 0; c < RC; ++c) {
       ux[c] = __shfl_sync(0xffffffffu, ux[c], from);
       uy[c] = __shfl_sync(0xffffffffu, uy[c], from);
       if (MIN) mc[c] = __shfl_sync(0xffffffffu, mc[c], from);
@@ -118,52 +146,76 @@ __device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int la
   }
 }
 
-// Persistent: each CTA takes tiles from a.tile_ctr until none are left. blockDim = 32 * FFS_W.
-template <int R>
-__global__ void __launch_bounds__(32 * FFS_W) k_farfield_sym(FfSymArgs a, const float4* __restrict__ src,
+// The symmetric order's per-vesicle data; with EQ (every vesicle of 32 R points, in index order) the
+// identity, computed instead of read.
+template <bool EQ, int R>
+struct FfsIdx {
+  static __device__ __forceinline__ int vid(const FfSymArgs& a, int s) { return EQ ? s : a.vid[s]; }
+  static __device__ __forceinline__ int64_t poff(const FfSymArgs& a, int s) { return EQ ? (int64_t)s * 32 * R : a.poff[s]; }
+  static __device__ __forceinline__ int64_t roff(const FfSymArgs& a, int s) { return EQ ? (int64_t)s * 32 * R : a.roff[s]; }
+  static __device__ __forceinline__ int nreal(const FfSymArgs& a, int s) { return EQ ? 32 * R : a.nreal[s]; }
+};
+
+// Persistent: each CTA takes tiles of its pair of classes (rows of RR segments, columns of RC) from t.ctr
+// until none are left. blockDim = 32 * FFS_W. EQ: all vesicles have 32 RR = 32 RC points (no padding).
+template <int RR, int RC, bool EQ>
+__global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_farfield_sym(FfSymArgs a, FfSymTiles t,
                                                              const float4* __restrict__ centre32,
-                                                             const float2* __restrict__ h2) {
-  constexpr int N = 32 * R;
+                                                             const float2* __restrict__ h2,
+                                                             const float2* __restrict__ gsum) {
+  constexpr int NC = 32 * RC;  // padded points of a column vesicle
+  using IR = FfsIdx<EQ, RR>;
+  using IC = FfsIdx<EQ, RC>;
   extern __shared__ float4 ffs_smem[];
   __shared__ int s_tile;
-  float4* col = ffs_smem;                  // [FFS_V][R][64]
-  float4* acc = ffs_smem + FFS_V * 2 * N;  // [FFS_V][N]
+  __shared__ int s_na[FFS_W];          // each warp's row vesicle: points and first point (read after the pair
+  __shared__ long long s_ao[FFS_W];    // loops, so that they hold no registers there), and its density sum
+  __shared__ float2 s_hga[FFS_W];      // times -ln(2)/2
+  float4* col = ffs_smem;                   // [FFS_V][RC][64]
+  float4* acc = ffs_smem + FFS_V * 2 * NC;  // [FFS_V][NC]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2: -log|r| = hl2 log2|r|^2
   for (;;) {
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.tile_ctr, 1u);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(t.ctr, 1u);
     __syncthreads();
-    const int t = s_tile;
-    if (t >= a.ntile) break;
-    const int2 tij = a.tiles[t];
+    const int ti = s_tile;
+    if (ti >= t.ntile) break;
+    const int2 tij = t.tiles[ti];
     const int I = tij.x, J = tij.y;
-    const int i0 = I * FFS_V, nI = min(FFS_V, a.M - i0);
-    const int j0 = J * FFS_V, nJ = min(FFS_V, a.M - j0);
+    const int2 cI = a.chunk[I], cJ = a.chunk[J];
+    const int nI = cI.y, nJ = cJ.y;
     const bool diag = I == J;
-    const int64_t p0 = (int64_t)j0 * N;
-    for (int e = threadIdx.x; e < nJ * 2 * N; e += blockDim.x) {
-      const int b = e / (2 * N), rem = e - b * 2 * N;
-      col[e] = src[p0 + b * N + 32 * (rem >> 6) + (rem & 31)];
+    for (int e = threadIdx.x; e < nJ * 2 * NC; e += blockDim.x) {
+      const int b = e / (2 * NC), rem = e - b * 2 * NC;
+      col[e] = a.psrc[IC::poff(a, cJ.x + b) + 32 * (rem >> 6) + (rem & 31)];
     }
-    for (int e = threadIdx.x; e < nJ * N; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = threadIdx.x; e < nJ * NC; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const bool rot = nJ >= FFS_W;
     const int K = rot ? nJ : nJ + FFS_W - 1;
     for (int r0 = 0; r0 < nI; r0 += FFS_W) {
       const int ai = r0 + w;
       const bool arow = ai < nI;
-      const int av = i0 + ai;
-      float4 rp[R];
-      float gxs[R], gys[R], sxr[R], cxr[R], syr[R], cyr[R];
+      const int as = cI.x + ai;
+      int av = 0;
+      float4 rp[RR];
+      float gxs[RR], gys[RR], sxr[RR], cxr[RR], syr[RR], cyr[RR];
       float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
       float2 ha = make_float2(0.f, 0.f);
       if (arow) {
+        av = IR::vid(a, as);
+        if (lane == 0) {
+          const float2 ga = gsum[av];
+          s_na[w] = IR::nreal(a, as);
+          s_ao[w] = IR::roff(a, as);
+          s_hga[w] = make_float2(hl2 * ga.x, hl2 * ga.y);
+        }
         ca = centre32[av];
         ha = h2[av];
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        rp[r] = arow ? src[(int64_t)av * N + lane + 32 * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int r = 0; r < RR; ++r) {
+        rp[r] = arow ? a.psrc[IR::poff(a, as) + lane + 32 * r] : make_float4(0.f, 0.f, 0.f, 0.f);
         gxs[r] = hl2 * rp[r].z;
         gys[r] = hl2 * rp[r].w;
         sxr[r] = cxr[r] = syr[r] = cyr[r] = 0.f;
@@ -173,44 +225,63 @@ __global__ void __launch_bounds__(32 * FFS_W) k_farfield_sym(FfSymArgs a, const 
         int bj = rot ? w + k : k - w;
         if (rot && bj >= nJ) bj -= nJ;
         if (arow && bj >= 0 && bj < nJ && (!diag || bj > ai)) {
-          const int bv = j0 + bj;
+          const int bs = cJ.x + bj;
+          const int bv = IC::vid(a, bs);
           const float4 cb = centre32[bv];
           const float2 hb = h2[bv];
           const float dx = (ca.x - cb.x) + (ca.z - cb.z), dy = (ca.y - cb.y) + (ca.w - cb.w);
-          float tx[R], ty[R], lx[R], ly[R], ax[R], ay[R], mr[R], ux[R], uy[R], mc[R];
+          // log-argument scale of the pair (its exponent is read back after the pair loop, so that it holds no
+          // register there)
+          float lsc;
+          const float sc = pow2_scale(fmaf(dx, dx, dy * dy) + (ha.y + hb.y), lsc);
+          float tx[RR], ty[RR], lx[RR], ly[RR], ax[RR], ay[RR], mr[RR], ux[RC], uy[RC], mc[RC];
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
+          for (int r = 0; r < RR; ++r) {
             tx[r] = dx + rp[r].x;
             ty[r] = dy + rp[r].y;
-            lx[r] = ly[r] = ax[r] = ay[r] = ux[r] = uy[r] = 0.f;
-            mr[r] = mc[r] = 3.0e38f;
+            lx[r] = ly[r] = ax[r] = ay[r] = 0.f;
+            mr[r] = 3.0e38f;
+          }
+#pragma unroll
+          for (int c = 0; c < RC; ++c) {
+            ux[c] = uy[c] = 0.f;
+            mc[c] = 3.0e38f;
           }
           // the minima are needed only when the reach circles of A and B overlap
           const float rs = reach_a + sqrtf(hb.y);
           const bool test = a.near_mask && fmaf(dx, dx, dy * dy) <= rs * rs;
-          const float4* colB = col + bj * 2 * N;
+          const float4* colB = col + bj * 2 * NC;
           if (test)
-            ffs_pair<R, true>(colB, lane, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+            ffs_pair<RR, RC, true>(colB, lane, sc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
           else
-            ffs_pair<R, false>(colB, lane, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+            ffs_pair<RR, RC, false>(colB, lane, sc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+          lsc = (float)(127 - ((__float_as_int(sc) >> 23) & 0xff));  // sc = 2^-lsc
+          const float2 gb = gsum[bv];
+          __syncwarp();
+          const int na = EQ ? 32 * RR : s_na[w];
+          const int64_t ao = s_ao[w];
 #pragma unroll
-          for (int r = 0; r < R; ++r) {  // targets of A, source vesicle B
+          for (int r = 0; r < RR; ++r) {  // targets of A, source vesicle B
+            if (lane + 32 * r >= na) continue;
             if (test && mr[r] <= hb.x) {
-              ffs_near(a, (int64_t)av * N + lane + 32 * r, bv);
+              ffs_near(a, ao + lane + 32 * r, bv);
             } else {
-              neumaier_add(sxr[r], cxr[r], fmaf(hl2, lx[r], ax[r]));
-              neumaier_add(syr[r], cyr[r], fmaf(hl2, ly[r], ay[r]));
+              neumaier_add(sxr[r], cxr[r], fmaf(hl2, fmaf(lsc, gb.x, lx[r]), ax[r]));
+              neumaier_add(syr[r], cyr[r], fmaf(hl2, fmaf(lsc, gb.y, ly[r]), ay[r]));
             }
           }
+          const int nb = IC::nreal(a, bs);
+          const float2 hga = s_hga[w];
 #pragma unroll
-          for (int c = 0; c < R; ++c) {  // targets of B, source vesicle A
+          for (int c = 0; c < RC; ++c) {  // targets of B, source vesicle A
+            if (lane + 32 * c >= nb) continue;
             if (test && mc[c] <= ha.x) {
-              ffs_near(a, (int64_t)bv * N + lane + 32 * c, av);
+              ffs_near(a, IC::roff(a, bs) + lane + 32 * c, av);
             } else {
-              float4& v = acc[bj * N + lane + 32 * c];
+              float4& v = acc[bj * NC + lane + 32 * c];
               float4 s = v;
-              neumaier_add(s.x, s.y, ux[c]);
-              neumaier_add(s.z, s.w, uy[c]);
+              neumaier_add(s.x, s.y, fmaf(lsc, hga.x, ux[c]));
+              neumaier_add(s.z, s.w, fmaf(lsc, hga.y, uy[c]));
               v = s;
             }
           }
@@ -218,10 +289,10 @@ __global__ void __launch_bounds__(32 * FFS_W) k_farfield_sym(FfSymArgs a, const 
         __syncthreads();
       }
       if (arow) {
-        if (diag) {  // chunk I = J: the row sums join the column accumulators of A's points
+        if (diag) {  // chunk I = J (so RR = RC): the row sums join the column accumulators of A's points
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float4& v = acc[ai * N + lane + 32 * r];
+          for (int r = 0; r < RR; ++r) {
+            float4& v = acc[ai * NC + lane + 32 * r];
             float4 s = v;
             neumaier_add(s.x, s.y, sxr[r]);
             s.y += cxr[r];
@@ -230,24 +301,42 @@ __global__ void __launch_bounds__(32 * FFS_W) k_farfield_sym(FfSymArgs a, const 
             v = s;
           }
         } else {
+          __syncwarp();
+          const int na = EQ ? 32 * RR : s_na[w];
+          const int64_t ao = s_ao[w];
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            a.part[(int64_t)J * a.P + (int64_t)av * N + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
+          for (int r = 0; r < RR; ++r)
+            if (lane + 32 * r < na)
+              a.part[(int64_t)J * a.P + ao + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
         }
       }
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < nJ * N; e += blockDim.x) {  // chunk I's contributions to chunk J's points
-      const float4 v = acc[e];
-      a.part[(int64_t)I * a.P + p0 + e] = v;
+    for (int e = threadIdx.x; e < nJ * NC; e += blockDim.x) {  // chunk I's contributions to chunk J's points
+      const int b = e / NC, i = e - b * NC;
+      if (i < IC::nreal(a, cJ.x + b)) a.part[(int64_t)I * a.P + IC::roff(a, cJ.x + b) + i] = acc[e];
     }
     __syncthreads();
   }
 }
 
+// Padded sources in the symmetric order: vesicle vid[s] into 32 R_s entries from poff[s], the entries past
+// its N points a copy of its first point with zero density. One CTA per vesicle.
+__global__ void __launch_bounds__(128) k_ffs_pad(FfSymArgs a, const float4* __restrict__ src, float4* __restrict__ psrc) {
+  const int s = blockIdx.x;
+  const int n = a.nreal[s], np = 32 * ffs_segments(n);
+  const int64_t o = a.roff[s];
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    float4 v = src[o + (i < n ? i : 0)];
+    if (i >= n) v.z = v.w = 0.f;
+    psrc[a.poff[s] + i] = v;
+  }
+}
+
 // u (CSR blocks [u_x(N), u_y(N)] per vesicle) += sum over chunks of part, in chunk order (double-float); near
 // counts clamped to MAX_NEAR and each near list sorted ascending.
-__global__ void __launch_bounds__(256) k_farfield_sym_reduce(FfSymArgs a, double* __restrict__ u) {
+__global__ void __launch_bounds__(256) k_farfield_sym_reduce(FfSymArgs a, const int32_t* __restrict__ owner,
+                                                             const int64_t* __restrict__ voff, double* __restrict__ u) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
   float2 ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
@@ -258,11 +347,12 @@ __global__ void __launch_bounds__(256) k_farfield_sym_reduce(FfSymArgs a, double
     ay = df_add(ay, make_float2(v.z, v.w));
   }
   const double sx = (double)ax.x + (double)ax.y, sy = (double)ay.x + (double)ay.y;
-  const int64_t v = p / a.N;
-  const int64_t to = v * a.N;
+  const int v = owner[p];
+  const int64_t to = voff[v];
+  const int64_t n = voff[v + 1] - to;
   const int64_t loc = p - to;
   u[2 * to + loc] += sx;
-  u[2 * to + a.N + loc] += sy;
+  u[2 * to + n + loc] += sy;
   if (a.near_mask) {
     const int c = min(a.near_cnt[p], MAX_NEAR);
     int* lst = a.near_v + p * MAX_NEAR;

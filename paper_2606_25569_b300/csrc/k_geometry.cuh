@@ -54,6 +54,8 @@ struct ForceOut {
   float2* h2;          // ((L_v/N_v)^2, reach^2) [M]: reach = (max_j |X_vj - c_v| + L_v/N_v)(1 + 1e-3), a
                        // bound beyond which no point of v is within L_v/N_v
   double* g64;         // FP64 copy of g, CSR blocks (for the FP64 far-field variant)
+  float2* gsum;        // sum_j g_j of each vesicle, summed in FP64 [M] (the FP32 far field adds the common
+                       // part of its logarithms once per vesicle pair with it)
 };
 
 __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __restrict__ xy,
@@ -150,13 +152,15 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
   }
   const double cx = cxs / N, cy = cys / N;
   const double rho2 = block_max(act ? (xs[i] - cx) * (xs[i] - cx) + (ys[i] - cy) * (ys[i] - cy) : 0.0, red);
+  const double c = sa * dal / (4.0 * VS_PI * mu);
+  const double gsx = block_sum(act ? fx * c : 0.0, red);
+  const double gsy = block_sum(act ? fy * c : 0.0, red);
   if (act) {
     fo.f[2 * o + i] = fx;
     fo.f[2 * o + N + i] = fy;
     const double2 ub = background_flow(flow, xs[i], ys[i]);
     fo.u[2 * o + i] = ub.x;
     fo.u[2 * o + N + i] = ub.y;
-    const double c = sa * dal / (4.0 * VS_PI * mu);
     fo.g64[2 * o + i] = fx * c;
     fo.g64[2 * o + N + i] = fy * c;
     fo.src[o + i] = make_float4((float)(xs[i] - cx), (float)(ys[i] - cy), (float)(fx * c), (float)(fy * c));
@@ -168,6 +172,7 @@ __global__ void __launch_bounds__(NMAX) k_geometry(VesIndex vi, const double* __
     const double h = length / N;
     const double reach = (sqrt(rho2) + h) * (1.0 + 1e-3);
     fo.h2[v] = make_float2((float)(h * h), (float)(reach * reach));
+    fo.gsum[v] = make_float2((float)gsx, (float)gsy);
   }
 }
 

@@ -18,6 +18,9 @@
 
 namespace vs {
 
+constexpr int MLP_MAX_OUT = 4096;  // widest output layer (the loss keeps one row of errors in shared memory)
+
+
 constexpr int MM_BM = 128, MM_BN = 128, MM_BK = 64, MM_THREADS = 128;
 constexpr int MM_STAGE_BYTES = (MM_BM + MM_BN) * MM_BK * 2;   // 32 KB
 constexpr int MM_STAGES = 4;                                 // shared-memory ring of K slices
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
                                                   int d, int ncomp, float beta, float* __restrict__ g_f32,
                                                   __nv_bfloat16* __restrict__ g_bf, __nv_bfloat16* __restrict__ g_bfT,
                                                   int Bp, float* __restrict__ loss_b) {
-  __shared__ float e[1024], de[1024];
+  __shared__ float e[MLP_MAX_OUT], de[MLP_MAX_OUT];
   __shared__ double red[4];
   const int b = blockIdx.x;
   const int tid = threadIdx.x;

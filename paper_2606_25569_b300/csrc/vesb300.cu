@@ -24,6 +24,7 @@
 #include "k_near.cuh"
 #include "k_selfmat.cuh"
 #include "k_standardize.cuh"
+#include "k_flow.cuh"
 #include "k_tcgemm.cuh"
 #include "k_vesicle.cuh"
 #include "tables.cuh"
@@ -197,6 +198,7 @@ struct SourceBufs {
   double2* centre = nullptr;
   float4* centre32 = nullptr;
   float2* h2 = nullptr;
+  float2* gsum = nullptr;
   int* near_cnt = nullptr;
   int* near_v = nullptr;
   double *sa = nullptr, *tx = nullptr, *ty = nullptr, *bx = nullptr, *by = nullptr;
@@ -213,6 +215,7 @@ struct SourceBufs {
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
     VS_TRY(dalloc(&f, 2 * P)); VS_TRY(dalloc(&g64, 2 * P)); VS_TRY(dalloc(&src, P));
     VS_TRY(dalloc(&centre, M)); VS_TRY(dalloc(&centre32, M)); VS_TRY(dalloc(&h2, M));
+    VS_TRY(dalloc(&gsum, M));
     VS_TRY(dalloc(&near_cnt, P)); VS_TRY(dalloc(&near_v, P * MAX_NEAR));
     VS_TRY(dalloc(&sa, P)); VS_TRY(dalloc(&tx, P)); VS_TRY(dalloc(&ty, P));
     VS_TRY(dalloc(&bx, P)); VS_TRY(dalloc(&by, P));
@@ -226,6 +229,7 @@ struct SourceBufs {
   }
   void release() {
     cudaFree(f); cudaFree(g64); cudaFree(src); cudaFree(centre); cudaFree(centre32); cudaFree(h2);
+    cudaFree(gsum);
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
     cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32); cudaFree(sdf);
     cudaFree(mpcoef); cudaFree(mpa0); cudaFree(mploc); cudaFree(mpncnt); cudaFree(mplist);
@@ -283,13 +287,26 @@ struct vs_mlp {
 
 // Symmetric FP32 far field (k_farfield_sym): tile list, tile counter and per-chunk partial sums; R = points
 // per lane (N / 32), 0 when the suspension or plan uses another far-field kernel.
+// Symmetric FP32 far field (k_farfield_sym): the symmetric order, chunks, and the tiles of each pair of
+// classes (rows of rr[k] segments, columns of rc[k]).
+constexpr int FFS_NPAIR = 6;
 struct FfSymState {
-  int R = 0, nchunk = 0, ntile = 0, grid = 0;
+  bool on = false;
+  bool padded = false;  // some N is not a multiple of 32 or the order is not the identity: k_ffs_pad runs
+  int nchunk = 0, npair = 0;
+  int rr[FFS_NPAIR] = {}, rc[FFS_NPAIR] = {}, ntile[FFS_NPAIR] = {}, grid[FFS_NPAIR] = {};
+  int64_t tile_off[FFS_NPAIR + 1] = {};
   int2* tiles = nullptr;
+  unsigned* ctr = nullptr;  // [FFS_NPAIR]
   float4* part = nullptr;
-  unsigned* ctr = nullptr;
+  float4* psrc = nullptr;   // padded sources (padded only)
+  int* vid = nullptr;
+  int64_t *poff = nullptr, *roff = nullptr;
+  int* nreal = nullptr;
+  int2* chunk = nullptr;
   void release() {
-    cudaFree(tiles); cudaFree(part); cudaFree(ctr);
+    cudaFree(tiles); cudaFree(ctr); cudaFree(part); cudaFree(psrc); cudaFree(vid); cudaFree(poff); cudaFree(roff);
+    cudaFree(nreal); cudaFree(chunk);
     *this = FfSymState{};
   }
 };
@@ -317,6 +334,9 @@ struct vs_suspension {
   struct vs_mlp* net = nullptr;    // learned relaxation map (hybrid mode), borrowed
   double net_scale = 1.0;
   int net_kmax = 0;
+  struct vs_mlp* flow_adv = nullptr;  // learned advection and tension columns (hybrid mode), borrowed
+  struct vs_mlp* flow_ten = nullptr;
+  int flow_kf = 0, flow_kout = 0;
   int cur = 0;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -325,7 +345,7 @@ struct vs_suspension {
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t graph_launches[4] = {0, 0, 0, 0};
   int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
-  FfSymState ffs;                                  // symmetric FP32 far field, used when ffs.R > 0
+  FfSymState ffs;                                  // symmetric FP32 far field, used when ffs.on
   std::string msg;
 };
 
@@ -513,7 +533,7 @@ inline GeomOut geom_active(GeomOut g, const int* active, const float4* logtab) {
 vs_status geometry(vs_suspension* h, const double* xy, bool with_force, const int* active = nullptr) {
   ForceOut fo{};
   if (with_force)
-    fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
+    fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64, h->B.gsum};
   VS_LAUNCH(h, "k_geometry", k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
                                              flow_dev(h->flow), geom_active(h->B.geom(), active, h->D.logtab), fo, nullptr));
   VS_CK(h, cudaGetLastError(), "geometry");
@@ -537,14 +557,15 @@ void launch_far_field_f32(const vs_suspension* h, int var, FarFieldArgs a) {
   const float4* src = h->B.src;
   const float4* c32 = h->B.centre32;
   const float2* h2 = h->B.h2;
+  const float2* gs = h->B.gsum;
   cudaStream_t st = h->stream;
   switch (var) {
-    case 0: k_farfield_f32<128, 2048><<<grid, 128, 0, st>>>(a, src, c32, h2); break;
-    case 1: k_farfield_f32<64, 2048><<<grid, 64, 0, st>>>(a, src, c32, h2); break;
-    case 2: k_farfield_f32<256, 2048><<<grid, 256, 0, st>>>(a, src, c32, h2); break;
-    case 3: k_farfield_f32<128, 1024><<<grid, 128, 0, st>>>(a, src, c32, h2); break;
-    case 4: k_farfield_f32<64, 1024><<<grid, 64, 0, st>>>(a, src, c32, h2); break;
-    default: k_farfield_f32<32, 1024><<<grid, 32, 0, st>>>(a, src, c32, h2); break;
+    case 0: k_farfield_f32<128, 2048><<<grid, 128, 0, st>>>(a, src, c32, h2, gs); break;
+    case 1: k_farfield_f32<64, 2048><<<grid, 64, 0, st>>>(a, src, c32, h2, gs); break;
+    case 2: k_farfield_f32<256, 2048><<<grid, 256, 0, st>>>(a, src, c32, h2, gs); break;
+    case 3: k_farfield_f32<128, 1024><<<grid, 128, 0, st>>>(a, src, c32, h2, gs); break;
+    case 4: k_farfield_f32<64, 1024><<<grid, 64, 0, st>>>(a, src, c32, h2, gs); break;
+    default: k_farfield_f32<32, 1024><<<grid, 32, 0, st>>>(a, src, c32, h2, gs); break;
   }
 }
 
@@ -557,72 +578,154 @@ FarFieldArgs far_field_args(vs_suspension* h) {
                       h->p.near_field ? 1 : 0, h->u, h->B.near_cnt, h->B.near_v, h->err};
 }
 
-// Symmetric FP32 far field: eligible when every vesicle has N = 32, 64 or 128 points and the chunk slots
-// (one float4 per point and chunk of FFS_V vesicles) fit in FFS_PART_MAX bytes; otherwise, and with
+// Symmetric FP32 far field: eligible when M >= 2 and the chunk slots (one float4 per point and chunk of at
+// most FFS_V vesicles) fit in an eighth of the device's memory; otherwise, and with
 // VS_FLAG_FARFIELD_PER_TARGET, the per-target kernel runs.
-constexpr size_t FFS_PART_MAX = size_t(4) << 30;
-
 FfSymArgs ffs_args(const FfSymState& f, const Layout& L, int near_mask, const SourceBufs& B, unsigned* err) {
-  return FfSymArgs{L.P, L.M, L.nmax, f.nchunk, f.ntile, f.tiles, f.ctr, near_mask, f.part, B.near_cnt, B.near_v, err};
+  return FfSymArgs{L.P, L.M, f.nchunk, near_mask, f.part, B.near_cnt, B.near_v, err,
+                   f.vid, f.poff, f.roff, f.nreal, f.chunk, f.padded ? f.psrc : B.src};
 }
 
-template <int R>
+template <int RR, int RC, bool EQ>
 cudaError_t ffs_prepare(int* grid) {
-  const size_t smem = ffs_smem_bytes(32 * R);
-  cudaError_t e = cudaFuncSetAttribute(k_farfield_sym<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = ffs_smem_bytes(RC);
+  cudaError_t e = cudaFuncSetAttribute(k_farfield_sym<RR, RC, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_farfield_sym<R>, 32 * FFS_W, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_farfield_sym<RR, RC, EQ>, 32 * FFS_W, smem)) !=
+      cudaSuccess)
     return e;
   *grid = sms * std::max(per_sm, 1);
   return cudaSuccess;
 }
 
-// Sets f up for the layout when `wanted` and the layout is eligible (equal N of 32, 64 or 128, M >= 2,
-// partial sums within FFS_PART_MAX); leaves f.R = 0 otherwise.
-cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t st) {
-  f.R = 0;
-  if (!wanted || L.M < 2) return cudaSuccess;
-  if (*std::min_element(L.N.begin(), L.N.end()) != L.nmax) return cudaSuccess;
-  const int R = L.nmax / 32;
-  if (L.nmax % 32 != 0 || !(R == 1 || R == 2 || R == 4)) return cudaSuccess;
-  const int nchunk = (L.M + FFS_V - 1) / FFS_V;
-  if ((size_t)nchunk * (size_t)L.P * sizeof(float4) > FFS_PART_MAX) return cudaSuccess;
-  std::vector<int2> tiles;
-  for (int i = 0; i < nchunk; ++i)  // whole tiles first, the half-empty diagonal ones last
-    for (int j = i + 1; j < nchunk; ++j) tiles.push_back(make_int2(i, j));
-  for (int i = 0; i < nchunk; ++i) tiles.push_back(make_int2(i, i));
-  cudaError_t e;
-  if ((e = dalloc(&f.tiles, (int64_t)tiles.size())) != cudaSuccess) return e;
-  if ((e = upload(f.tiles, tiles.data(), (int64_t)tiles.size(), st)) != cudaSuccess) return e;
-  if ((e = dalloc(&f.part, (int64_t)nchunk * L.P)) != cudaSuccess) return e;
-  if ((e = dalloc(&f.ctr, 1)) != cudaSuccess) return e;
-  int grid = 0;
-  e = R == 1 ? ffs_prepare<1>(&grid) : R == 2 ? ffs_prepare<2>(&grid) : ffs_prepare<4>(&grid);
-  if (e != cudaSuccess) return e;
-  f.nchunk = nchunk;
-  f.ntile = (int)tiles.size();
-  f.grid = std::min(grid, f.ntile);
-  f.R = R;
-  return cudaStreamSynchronize(st);
-}
-
-// Zero the tile counter (and the near counts), then the pair kernel. u is added to by ffs_reduce.
-void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cudaStream_t st) {
-  const size_t smem = ffs_smem_bytes(32 * f.R);
-  cudaMemsetAsync(f.ctr, 0, sizeof(unsigned), st);
-  if (a.near_mask) cudaMemsetAsync(B.near_cnt, 0, a.P * sizeof(int), st);
-  switch (f.R) {
-    case 1: k_farfield_sym<1><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
-    case 2: k_farfield_sym<2><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
-    default: k_farfield_sym<4><<<f.grid, 32 * FFS_W, smem, st>>>(a, B.src, B.centre32, B.h2); break;
+// The instantiated pairs of classes (row segments >= column segments); eq: equal N of 32, 64 or 128 in index
+// order (no padding, identity order).
+cudaError_t ffs_prepare(int rr, int rc, bool eq, int* grid) {
+  switch (rr * 8 + rc) {
+    case 4 * 8 + 4: return eq ? ffs_prepare<4, 4, true>(grid) : ffs_prepare<4, 4, false>(grid);
+    case 4 * 8 + 2: return ffs_prepare<4, 2, false>(grid);
+    case 4 * 8 + 1: return ffs_prepare<4, 1, false>(grid);
+    case 2 * 8 + 2: return eq ? ffs_prepare<2, 2, true>(grid) : ffs_prepare<2, 2, false>(grid);
+    case 2 * 8 + 1: return ffs_prepare<2, 1, false>(grid);
+    default: return eq ? ffs_prepare<1, 1, true>(grid) : ffs_prepare<1, 1, false>(grid);
   }
 }
 
-void ffs_reduce(const FfSymArgs& a, double* u, cudaStream_t st) {
-  k_farfield_sym_reduce<<<(int)((a.P + 255) / 256), 256, 0, st>>>(a, u);
+// Sets f up for the layout when `wanted` and the layout is eligible; leaves f.on false otherwise.
+cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t st) {
+  f.on = false;
+  if (!wanted || L.M < 2) return cudaSuccess;
+  // symmetric order: classes of 4, 2, 1 segments, vesicle index ascending inside a class
+  std::vector<int> vid;
+  for (int R : {4, 2, 1})
+    for (int v = 0; v < L.M; ++v)
+      if (ffs_segments(L.N[v]) == R) vid.push_back(v);
+  std::vector<int64_t> poff(L.M), roff(L.M);
+  std::vector<int> nreal(L.M), cls(L.M);
+  int64_t pp = 0;
+  bool padded = false;
+  for (int s = 0; s < L.M; ++s) {
+    const int v = vid[s];
+    cls[s] = ffs_segments(L.N[v]);
+    poff[s] = pp;
+    roff[s] = L.off[v];
+    nreal[s] = L.N[v];
+    pp += 32 * cls[s];
+    if (v != s || L.N[v] != 32 * cls[s]) padded = true;
+  }
+  std::vector<int2> chunk;
+  std::vector<int> ccls;
+  for (int s = 0; s < L.M;) {
+    int n = 0;
+    while (s + n < L.M && n < FFS_V && cls[s + n] == cls[s]) ++n;
+    chunk.push_back(make_int2(s, n));
+    ccls.push_back(cls[s]);
+    s += n;
+  }
+  const int nchunk = (int)chunk.size();
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e;
+  if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return e;
+  if ((size_t)nchunk * (size_t)L.P * sizeof(float4) > total_b / 8) return cudaSuccess;
+  // tiles per pair of classes: whole tiles first, the half-empty diagonal ones last
+  std::vector<int2> tiles;
+  int npair = 0;
+  const int pairs[FFS_NPAIR][2] = {{4, 4}, {4, 2}, {4, 1}, {2, 2}, {2, 1}, {1, 1}};
+  for (const auto& pr : pairs) {
+    const size_t t0 = tiles.size();
+    for (int i = 0; i < nchunk; ++i)
+      for (int j = i + 1; j < nchunk; ++j)
+        if (ccls[i] == pr[0] && ccls[j] == pr[1]) tiles.push_back(make_int2(i, j));
+    if (pr[0] == pr[1])
+      for (int i = 0; i < nchunk; ++i)
+        if (ccls[i] == pr[0]) tiles.push_back(make_int2(i, i));
+    if (tiles.size() == t0) continue;
+    f.rr[npair] = pr[0];
+    f.rc[npair] = pr[1];
+    f.tile_off[npair] = (int64_t)t0;
+    f.ntile[npair] = (int)(tiles.size() - t0);
+    int grid = 0;
+    if ((e = ffs_prepare(pr[0], pr[1], !padded, &grid)) != cudaSuccess) return e;
+    f.grid[npair] = std::min(grid, f.ntile[npair]);
+    ++npair;
+  }
+  f.tile_off[npair] = (int64_t)tiles.size();
+#define VS_TRY(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+  VS_TRY(dalloc(&f.tiles, (int64_t)tiles.size()));
+  VS_TRY(upload(f.tiles, tiles.data(), (int64_t)tiles.size(), st));
+  VS_TRY(dalloc(&f.part, (int64_t)nchunk * L.P));
+  VS_TRY(dalloc(&f.ctr, FFS_NPAIR));
+  VS_TRY(dalloc(&f.vid, L.M)); VS_TRY(upload(f.vid, vid.data(), L.M, st));
+  VS_TRY(dalloc(&f.poff, L.M)); VS_TRY(upload(f.poff, poff.data(), L.M, st));
+  VS_TRY(dalloc(&f.roff, L.M)); VS_TRY(upload(f.roff, roff.data(), L.M, st));
+  VS_TRY(dalloc(&f.nreal, L.M)); VS_TRY(upload(f.nreal, nreal.data(), L.M, st));
+  VS_TRY(dalloc(&f.chunk, nchunk)); VS_TRY(upload(f.chunk, chunk.data(), nchunk, st));
+  if (padded) VS_TRY(dalloc(&f.psrc, pp));
+#undef VS_TRY
+  f.padded = padded;
+  f.nchunk = nchunk;
+  f.npair = npair;
+  f.on = true;
+  return cudaStreamSynchronize(st);
+}
+
+// Zero the tile counters (and the near counts), pad the sources if needed, then one pair kernel per pair of
+// classes. u is added to by ffs_reduce.
+void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cudaStream_t st) {
+  cudaMemsetAsync(f.ctr, 0, FFS_NPAIR * sizeof(unsigned), st);
+  if (a.near_mask) cudaMemsetAsync(B.near_cnt, 0, a.P * sizeof(int), st);
+  if (f.padded) k_ffs_pad<<<a.M, 128, 0, st>>>(a, B.src, f.psrc);
+  for (int k = 0; k < f.npair; ++k) {
+    const FfSymTiles t{f.tiles + f.tile_off[k], f.ntile[k], f.ctr + k};
+    const size_t smem = ffs_smem_bytes(f.rc[k]);
+    const int g = f.grid[k], nt = 32 * FFS_W;
+    const float4* c32 = B.centre32;
+    const float2 *h2 = B.h2, *gs = B.gsum;
+    if (!f.padded) {  // equal N of 32, 64 or 128: a single pair of classes
+      switch (f.rr[k]) {
+        case 4: k_farfield_sym<4, 4, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+        case 2: k_farfield_sym<2, 2, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+        default: k_farfield_sym<1, 1, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      }
+      continue;
+    }
+    switch (f.rr[k] * 8 + f.rc[k]) {
+      case 4 * 8 + 4: k_farfield_sym<4, 4, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 4 * 8 + 2: k_farfield_sym<4, 2, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 4 * 8 + 1: k_farfield_sym<4, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 2 * 8 + 2: k_farfield_sym<2, 2, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 2 * 8 + 1: k_farfield_sym<2, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      default: k_farfield_sym<1, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+    }
+  }
+}
+
+void ffs_reduce(const FfSymArgs& a, const DevLayout& D, double* u, cudaStream_t st) {
+  k_farfield_sym_reduce<<<(int)((a.P + 255) / 256), 256, 0, st>>>(a, D.owner, D.off, u);
 }
 
 vs_status far_field(vs_suspension* h) {
@@ -639,10 +742,10 @@ vs_status far_field(vs_suspension* h) {
     const FfLocArgs la = h->B.loc(L.M);
     VS_LAUNCH(h, "k_ff_local", k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la));
     VS_LAUNCH(h, "k_farfield_loc", k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src));
-  } else if (h->ffs.R > 0) {
+  } else if (h->ffs.on) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
     VS_LAUNCH(h, "k_farfield_sym", ffs_launch(h->ffs, fa, h->B, h->stream));
-    VS_LAUNCH(h, "k_farfield_sym_reduce", ffs_reduce(fa, h->u, h->stream));
+    VS_LAUNCH(h, "k_farfield_sym_reduce", ffs_reduce(fa, h->D, h->u, h->stream));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -662,7 +765,7 @@ std::map<std::string, int>& tune_cache() {
 
 vs_status tune_far_field(vs_suspension* h) {
   const Layout& L = h->L;
-  if (L.M < 2 || h->ffs.R > 0 ||
+  if (L.M < 2 || h->ffs.on ||
       (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE)))
     return VS_OK;
   int dev = 0;
@@ -796,6 +899,62 @@ vs_status tension(vs_suspension* h, const double* u, int s) {
   return VS_OK;
 }
 
+// sigma_out = -L^{-1} P (B X + u) with the operators of slot s and the geometry in the SourceBufs.
+vs_status tension_into(vs_suspension* h, const double* u, int s, double* sigma_out) {
+  const VesIndex vi = h->D.vi();
+  const int M = h->L.M;
+  if (mixed(h)) {
+    MP_DISPATCH(h, "k_tension_mp", k_tension_mp, M, (vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
+                                                        h->scratch32, s, h->p.kappa_b, sigma_out, h->err));
+  } else {
+    VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
+                                                                 h->piv, h->p.kappa_b, sigma_out));
+  }
+  VS_CK(h, cudaGetLastError(), "tension");
+  return VS_OK;
+}
+
+// xo = xy + dt (I - M) u with the operators of slot s (Eq. advection_disc).
+vs_status advect_into(vs_suspension* h, const double* xy, const double* u, int s, double dt, double* xo) {
+  const VesIndex vi = h->D.vi();
+  const int M = h->L.M;
+  if (mixed(h)) {
+    MP_DISPATCH(h, "k_advect_mp", k_advect_mp, M, (vi, xy, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
+                                                      dt, xo, h->err));
+  } else {
+    VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, xy, u, h->B.pg(), h->D.tab, h->scratch, s, h->piv, dt,
+                                                               xo));
+  }
+  VS_CK(h, cudaGetLastError(), "advection");
+  return VS_OK;
+}
+
+// Learned advection (Eq. advectionMap): X* = X^n + dt (I - M) u with the network's columns at the
+// standardised X^n; or learned tension (Eq. advTenMap and S_sigma): sigma = -L^{-1} P (B X + u) at X.
+vs_status flow_learned(vs_suspension* h, bool ten, const double* xy, const double* u, double* out) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  const int W = feat_width(feat_kmax(h->net_kmax, L.nmax));
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, xy, h->D.tab, h->xin, W, h->frames,
+                                                                           h->net_kmax, true));
+  VS_CK(h, cudaGetLastError(), "standardise");
+  vs_mlp* net = ten ? h->flow_ten : h->flow_adv;
+  vs_status st = mlp_forward(net, h->xin, L.M, true);
+  if (st != VS_OK) { h->msg = "flow network forward failed"; return st; }
+  const int ld = net->dims.back();
+  if (ten) {
+    VS_LAUNCH(h, "k_flow_apply<tension>", k_flow_apply<true><<<L.M, NMAX, 0, h->stream>>>(
+                                              vi, u, h->frames, mlp_output(net), ld, h->flow_kf, h->flow_kout, h->D.tab,
+                                              0.0, nullptr, nullptr, out));
+  } else {
+    VS_LAUNCH(h, "k_flow_apply<advection>", k_flow_apply<false><<<L.M, NMAX, 0, h->stream>>>(
+                                                vi, u, h->frames, mlp_output(net), ld, h->flow_kf, h->flow_kout, h->D.tab,
+                                                h->p.dt, xy, out, nullptr));
+  }
+  VS_CK(h, cudaGetLastError(), "learned flow");
+  return VS_OK;
+}
+
 // Learned relaxation (VesNet's X_X map): X*_r = redistribute(X*),
 // X^{n+1} = lowpass_kmax(X*_r + destandardise(net(standardise(X*_r)))).
 vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
@@ -817,13 +976,19 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   return VS_OK;
 }
 
-// u += near-field correction of every (target, vesicle) pair the far field masked (Sec. 3.3).
-vs_status near_field(vs_suspension* h, int s) {
+// u += near-field correction of every (target, vesicle) pair the far field masked (Sec. 3.3). With
+// build_sources the operators of slot s are first built for the source vesicles that have near targets (a
+// step with learned advection and tension keeps no operators at X^n otherwise).
+vs_status near_field(vs_suspension* h, int s, bool build_sources = false) {
   const Layout& L = h->L;
   const VesIndex vi = h->D.vi();
   VS_CK(h, cudaMemsetAsync(h->has_near, 0, L.M * sizeof(int), h->stream), "near field");
   const int tgrid = (int)((L.P + 127) / 128);
   VS_LAUNCH(h, "k_near_mark", k_near_mark<<<tgrid, 128, 0, h->stream>>>(L.P, h->B.near_cnt, h->B.near_v, h->has_near));
+  if (build_sources) {
+    vs_status st = build_operators(h, h->xy, s, h->has_near);
+    if (st != VS_OK) return st;
+  }
   const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
   const size_t smem = 6 * (size_t)Nu * sizeof(double);
   VS_LAUNCH(h, "k_near_layers", k_near_layers<<<L.M, 256, smem, h->stream>>>(vi, h->has_near, h->xy, h->B.f, h->B.pg(),
@@ -877,6 +1042,9 @@ vs_status correction(vs_suspension* h) {
   return VS_OK;
 }
 
+// Hybrid suspension with the advection and tension networks set (vs_set_flow_networks).
+inline bool flow_learned_on(const vs_suspension* h) { return h->p.mode == 1 && h->flow_adv && h->flow_ten; }
+
 double exact_gap(const vs_suspension* h) { return h->p.exact_gap > 0.0 ? h->p.exact_gap : HYBRID_EXACT_GAP; }
 
 // Hybrid steps use the learned relaxation except every exact_every-th step (counting from 1), which takes
@@ -892,15 +1060,20 @@ vs_status step_once(vs_suspension* h) {
   const VesIndex vi = h->D.vi();
   vs_status st;
   const int cur = h->cur, nxt = 1 - h->cur;
+  // hybrid with flow networks: advection and tension learned in every step (Sec. 3.2), no operators at X^n
+  // or X^{n+1}
+  const bool lf = flow_learned_on(h);
   // (1) geometry + force at X^n, u = u_inf(X^n)
   if ((st = geometry(h, h->xy, true)) != VS_OK) return st;
   // (2) operators at X^n where the cache is stale (first step, or after a correction)
-  if ((st = build_operators(h, h->xy, cur, h->dirty)) != VS_OK) return st;
+  if (!lf && (st = build_operators(h, h->xy, cur, h->dirty)) != VS_OK) return st;
   // (3) u += far field (near pairs masked) + near-field correction
   if ((st = far_field(h)) != VS_OK) return st;
-  if (h->p.near_field && L.M > 1 && (st = near_field(h, cur)) != VS_OK) return st;
+  if (h->p.near_field && L.M > 1 && (st = near_field(h, cur, lf)) != VS_OK) return st;
   // (4) advection
-  if (mixed(h)) {
+  if (lf) {
+    if ((st = flow_learned(h, false, h->xy, h->u, h->xy_star)) != VS_OK) return st;
+  } else if (mixed(h)) {
     MP_DISPATCH(h, "k_advect_mp", k_advect_mp, M, (vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32,
                                                       cur, h->p.dt, h->xy_star, h->err));
   } else {
@@ -911,13 +1084,14 @@ vs_status step_once(vs_suspension* h) {
   // (5) relaxation at X*: exact (plain) or the learned map (hybrid)
   if (learned_step(h)) {
     if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
-    if (h->p.near_field && M > 1) {
+    if (M > 1) {
       // the plain step is the fallback of the learned one: vesicles in a near pair, or closer to another
       // vesicle than exact_gap (default HYBRID_EXACT_GAP) spacings, relax exactly
       VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
       const int tgrid = (int)((L.P + 127) / 128);
-      VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
-                                                                                     h->B.near_v, h->involved));
+      if (h->p.near_field)
+        VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
+                                                                                       h->B.near_v, h->involved));
       VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
                                                                          exact_gap(h), h->involved));
       if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
@@ -929,9 +1103,13 @@ vs_status step_once(vs_suspension* h) {
   VS_LAUNCH(h, "k_redistribute", k_redistribute<<<M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r));
   VS_CK(h, cudaGetLastError(), "redistribution");
   // (7) tension at the redistributed X^{n+1}; operators cached in slot nxt for the next step
-  if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
-  if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
-  if ((st = tension(h, h->u_r, nxt)) != VS_OK) return st;
+  if (lf) {
+    if ((st = flow_learned(h, true, h->xy, h->u_r, h->sigma)) != VS_OK) return st;
+  } else {
+    if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
+    if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
+    if ((st = tension(h, h->u_r, nxt)) != VS_OK) return st;
+  }
   // (8) area/length correction (Newton on the KKT system); marks the cached operators stale where it fires
   if ((st = correction(h)) != VS_OK) return st;
   h->cur = nxt;
@@ -1219,12 +1397,12 @@ vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
 
 vs_status vs_farfield_variant(vs_suspension* h, int32_t set, int32_t* index, int32_t* threads, int32_t* chunk) {
   if (!h || set >= FF_NVARIANTS) return VS_ERR_INVALID_ARG;
-  if (set >= 0 && (set != h->ff_variant || h->ffs.R > 0)) {
+  if (set >= 0 && (set != h->ff_variant || h->ffs.on)) {
     h->ff_variant = set;
-    h->ffs.R = 0;  // an explicit per-target launch shape leaves the symmetric kernel
+    h->ffs.on = false;  // an explicit per-target launch shape leaves the symmetric kernel
     drop_graphs(h);
   }
-  if (h->ffs.R > 0) {
+  if (h->ffs.on) {
     if (index) *index = -1;
     if (threads) *threads = 32 * FFS_W;
     if (chunk) *chunk = FFS_V * h->L.nmax;
@@ -1276,6 +1454,92 @@ vs_status vs_set_network(vs_suspension* h, int32_t which, vs_mlp* net, double ou
   h->net_scale = out_scale;
   h->net_kmax = filter_kmax;
   return VS_OK;
+}
+
+vs_status vs_set_flow_networks(vs_suspension* h, vs_mlp* adv, vs_mlp* ten, int32_t Kf, int32_t Kout) {
+  if (!h || (!adv) != (!ten)) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  if (!adv) {
+    drop_graphs(h);
+    h->flow_adv = h->flow_ten = nullptr;
+    std::vector<int> ones(L.M, 1);  // the operator cache at X^n was not kept while the networks were in use
+    VS_CK(h, cudaMemcpy(h->dirty, ones.data(), L.M * sizeof(int), cudaMemcpyHostToDevice), "flow networks");
+    return VS_OK;
+  }
+  if (!h->net) { h->msg = "set the relaxation network (vs_set_network) first: the flow networks share its input"; return VS_ERR_INVALID_ARG; }
+  if (Kf < 0 || Kout < 0 || Kf > L.nmax / 2 - 1 || Kout > L.nmax / 2 - 1) {
+    h->msg = "Kf and Kout must be in [0, N/2 - 1]";
+    return VS_ERR_INVALID_ARG;
+  }
+  const int W = feat_width(feat_kmax(h->net_kmax, L.nmax));
+  if (adv->dims.front() != W || ten->dims.front() != W || adv->dims.back() != flow_adv_width(Kf, Kout) ||
+      ten->dims.back() != flow_ten_width(Kf, Kout) || adv->Bcap < L.M || ten->Bcap < L.M) {
+    h->msg = "flow networks: input width that of the relaxation network, outputs flow_adv_width(Kf, Kout) and "
+             "flow_ten_width(Kf, Kout), batch capacity at least M";
+    return VS_ERR_INVALID_ARG;
+  }
+  if (adv->stream != h->stream || ten->stream != h->stream) {
+    h->msg = "networks and suspension must share one stream";
+    return VS_ERR_INVALID_ARG;
+  }
+  drop_graphs(h);
+  h->flow_adv = adv;
+  h->flow_ten = ten;
+  h->flow_kf = Kf;
+  h->flow_kout = Kout;
+  return VS_OK;
+}
+
+vs_status vs_flow_maps(vs_suspension* h, int32_t Kf, int32_t Kout, int32_t filter_kmax, float* xin, float* adv,
+                       float* ten) {
+  if (!h || !xin || !adv || !ten || filter_kmax < 0) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  for (int v = 0; v < L.M; ++v)
+    if (L.N[v] != L.nmax) { h->msg = "vs_flow_maps needs one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
+  if (Kf < 0 || Kout < 0 || Kf > L.nmax / 2 - 1 || Kout > L.nmax / 2 - 1) return VS_ERR_INVALID_ARG;
+  const VesIndex vi = h->D.vi();
+  const int M = L.M, nxt = 1 - h->cur;
+  const int W = feat_width(feat_kmax(filter_kmax, L.nmax));
+  const int la = flow_adv_width(Kf, Kout), lt = flow_ten_width(Kf, Kout);
+  const int ca = flow_col_adv(Kout), ct = flow_col_ten(Kout);
+  // inputs and frames at the current points, the standardised points into xy_next
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->D.tab, xin, W, h->frames,
+                                                                         filter_kmax, true));
+  VS_LAUNCH(h, "k_standard_points", k_standard_points<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->frames, h->xy_next));
+  VS_CK(h, cudaMemsetAsync(adv, 0, (size_t)M * la * sizeof(float), h->stream), "flow maps");
+  VS_CK(h, cudaMemsetAsync(ten, 0, (size_t)M * lt * sizeof(float), h->stream), "flow maps");
+  // the exact operators at the standardised shapes in slot nxt (the cache of slot cur is left alone)
+  vs_status st;
+  if ((st = geometry(h, h->xy_next, false)) != VS_OK) return st;
+  if ((st = build_operators(h, h->xy_next, nxt, nullptr)) != VS_OK) return st;
+  double *zero = nullptr, *ub = nullptr, *out = nullptr, *s0 = nullptr, *sb = nullptr;
+  cudaError_t e = dalloc(&zero, 2 * L.P);
+  if (e == cudaSuccess) e = dalloc(&ub, 2 * L.P);
+  if (e == cudaSuccess) e = dalloc(&out, 2 * L.P);
+  if (e == cudaSuccess) e = dalloc(&s0, L.P);
+  if (e == cudaSuccess) e = dalloc(&sb, L.P);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, 2 * L.P * sizeof(double), h->stream);
+  auto done = [&](vs_status r) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(zero); cudaFree(ub); cudaFree(out); cudaFree(s0); cudaFree(sb);
+    return r;
+  };
+  if (e != cudaSuccess) { cuda_fail(h->msg, e, "vs_flow_maps"); return done(VS_ERR_NOMEM); }
+  // S_sigma = L^{-1} P B X = -sigma(u = 0)
+  if ((st = tension_into(h, zero, nxt, s0)) != VS_OK) return done(st);
+  k_field_features<<<M, NMAX, 0, h->stream>>>(vi, s0, 1, h->D.tab, Kout, -1.0, false, ten, lt, 0);
+  for (int b = 0; b < flow_basis(Kf); ++b) {
+    k_basis_velocity<<<M, NMAX, 0, h->stream>>>(vi, h->D.tab, b, Kf, ub);
+    // (I - M) psi_b
+    if ((st = advect_into(h, zero, ub, nxt, 1.0, out)) != VS_OK) return done(st);
+    k_field_features<<<M, NMAX, 0, h->stream>>>(vi, out, 2, h->D.tab, Kout, 1.0, false, adv, la, b * ca);
+    // L^{-1} P psi_b = sigma(0) - sigma(psi_b)
+    if ((st = tension_into(h, ub, nxt, sb)) != VS_OK) return done(st);
+    k_field_features<<<M, NMAX, 0, h->stream>>>(vi, s0, 1, h->D.tab, Kout, 1.0, false, ten, lt, (b + 1) * ct);
+    k_field_features<<<M, NMAX, 0, h->stream>>>(vi, sb, 1, h->D.tab, Kout, -1.0, true, ten, lt, (b + 1) * ct);
+  }
+  VS_CK(h, cudaGetLastError(), "flow maps");
+  return done(VS_OK);
 }
 
 vs_status vs_relax(vs_suspension* h, const double* xy_in, double* xy_out) {
@@ -1416,7 +1680,7 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
 vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* f, double* u) {
   if (!h || !xy || !f || !u) return VS_ERR_INVALID_ARG;
   const Layout& L = h->L;
-  ForceOut fo{h->B.f, u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64};
+  ForceOut fo{h->B.f, u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64, h->B.gsum};
   FlowDev none{0, 0.0, 0.0};
   k_geometry<<<L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, nullptr, h->D.tab, 1.0, h->mu, none, h->B.geom(), fo, f);
   VS_CK(h, cudaGetLastError(), "far-field sources");
@@ -1432,12 +1696,13 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
     const FfLocArgs la = h->B.loc(L.M);
     k_ff_local<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la);
     k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src);
-  } else if (h->ffs.R > 0) {
+  } else if (h->ffs.on) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->near_mask, h->B, h->err);
     ffs_launch(h->ffs, fa, h->B, h->stream);
-    ffs_reduce(fa, u, h->stream);
+    ffs_reduce(fa, h->D, u, h->stream);
   } else {
-    k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2);
+    k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2,
+                                                                        h->B.gsum);
   }
   VS_CK(h, cudaGetLastError(), "far field");
   return VS_OK;
@@ -1709,8 +1974,8 @@ vs_status vs_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_batch,
       g_create_msg = "MLP widths must be multiples of 16 in [16, 4096]";
       return VS_ERR_INVALID_ARG;
     }
-  if (dims[nlayers] > 1024 || dims[nlayers] % ncomp != 0) {
-    g_create_msg = "output width must be <= 1024 and divisible by ncomp";
+  if (dims[nlayers] > MLP_MAX_OUT || dims[nlayers] % ncomp != 0) {
+    g_create_msg = "output width must be <= 4096 and divisible by ncomp";
     return VS_ERR_INVALID_ARG;
   }
   vs_mlp* h = new (std::nothrow) vs_mlp();
@@ -1956,7 +2221,8 @@ constexpr int64_t SF_SRC = SF_G64 + sf_align(16 * SF_MAX_P);
 constexpr int64_t SF_CENTRE = SF_SRC + sf_align(16 * SF_MAX_P);
 constexpr int64_t SF_CENTRE32 = SF_CENTRE + sf_align(16 * SF_MAX_M);
 constexpr int64_t SF_H2 = SF_CENTRE32 + sf_align(16 * SF_MAX_M);
-constexpr int64_t SF_BYTES = SF_H2 + sf_align(8 * SF_MAX_M);
+constexpr int64_t SF_GSUM = SF_H2 + sf_align(8 * SF_MAX_M);
+constexpr int64_t SF_BYTES = SF_GSUM + sf_align(8 * SF_MAX_M);
 
 __device__ __align__(256) static unsigned char g_ff_scratch[SF_BYTES];
 
@@ -2045,7 +2311,8 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
   double* al = (double*)(base + SF_AREA);
   const GeomOut g{geo, geo + SF_MAX_P, geo + 2 * SF_MAX_P, geo + 3 * SF_MAX_P, geo + 4 * SF_MAX_P, al, al + SF_MAX_M};
   const ForceOut fo{(double*)(base + SF_F), u, (float4*)(base + SF_SRC), (double2*)(base + SF_CENTRE),
-                    (float4*)(base + SF_CENTRE32), (float2*)(base + SF_H2), (double*)(base + SF_G64)};
+                    (float4*)(base + SF_CENTRE32), (float2*)(base + SF_H2), (double*)(base + SF_G64),
+                    (float2*)(base + SF_GSUM)};
   const FlowDev none{0, 0.0, 0.0};
   k_geometry<<<M, NMAX, 0, st>>>(vi, xy, nullptr, (const double*)(base + SF_TABLE), 1.0, mu, none, g, fo, f);
   if (M >= 2) {
@@ -2055,7 +2322,7 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
     if (precision == 1)
       k_farfield_f64<<<grid, FF_THREADS, 0, st>>>(a, xy, fo.g64, g.length, vi.N);
     else
-      k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, st>>>(a, fo.src, fo.centre32, fo.h2);
+      k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, st>>>(a, fo.src, fo.centre32, fo.h2, fo.gsum);
   }
   return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ERR_CUDA;
 }

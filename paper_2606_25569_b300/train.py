@@ -49,6 +49,38 @@ def relaxation_samples(wl, snapshots, every, stream, kmax, near_field=None, skip
     return X, Y
 
 
+def hybrid_samples(wl, snapshots, every, stream, kmax, Kf, Kout, near_field=None, skip=0):
+    """Training data of the hybrid step's three networks from one plain run: every `every` steps, each
+    vesicle's current shape gives the network input X (Fourier features up to kmax of the standardised shape),
+    the relaxation target R (vs_training_pairs), and the exact advection and tension columns A, T
+    (vs_flow_maps, modes <= Kf of the velocity, columns up to Kout). FP32 device tensors, snapshots * M
+    rows."""
+    import torch
+    nf = wl.near_field if near_field is None else near_field
+    s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=nf, stream=stream)
+    M, W = wl.M, binding.feature_width(len(wl.xs[0]), kmax)
+    la, lt = binding.flow_widths(Kf, Kout)
+    if skip:
+        s.step(skip)
+    X = torch.empty(snapshots * M, W, dtype=torch.float32, device="cuda")
+    R = torch.empty_like(X)
+    A = torch.empty(snapshots * M, la, dtype=torch.float32, device="cuda")
+    T = torch.empty(snapshots * M, lt, dtype=torch.float32, device="cuda")
+    X2 = torch.empty(M, W, dtype=torch.float32, device="cuda")
+    for k in range(snapshots):
+        rows = slice(k * M, (k + 1) * M)
+        xy = torch.as_tensor(s.positions(), device="cuda")
+        s.training_pairs(xy, X[rows], R[rows], 1.0, kmax)
+        s.flow_maps(Kf, Kout, kmax, X2, A[rows], T[rows])
+        s.sync()
+        if k + 1 < snapshots:
+            s.step(every)
+    s.sync()
+    s.close()
+    return X, R, A, T
+
+
 def relative_errors(net, X, Y, batch):
     """Per-sample ||Yhat - Y|| / ||Y|| of the network on (X, Y) (device tensors)."""
     import torch

@@ -164,10 +164,15 @@ def farfield_box(M=2000, N=128, seed=3, R=0.08, box=20.0):
     return Workload("far field %dx%d box %g" % (M, N, box), xs, ys), fxs, fys
 
 
-def poiseuille_dense(M=2000, N=64, seed=5, area_fraction=0.30, Cn=0.025, Ca=2.0):
+def poiseuille_dense(M=2000, N=64, seed=5, area_fraction=0.30, Cn=0.025, Ca=2.0, close_fraction=0.0, close_gap=0.5):
     """Dense Poiseuille suspension (Sec. 5.5): channel of width 1 (walls y = +-1/2),
     R = Cn W with W = 1/2, reduced area 0.65, u_max from Ca = 2 eta u_max R^3/(kappa W)
     (Sec. 5.3), dt = 0.01 W/u_max, jittered lattice with principal axes along x (Sec. 5.3).
+
+    N: points per vesicle, or a sequence of point counts taken in turn (a suspension of uneven N).
+    close_fraction: that fraction of the vesicles (every k-th) is moved along x towards its neighbour in the
+    same lattice row until the smallest gap between them is close_gap times the larger arclength spacing
+    h = L/N, so that the near-field rule (gap <= h) has pairs from the first step.
     """
     rng = np.random.default_rng(seed)
     W = 0.5
@@ -181,15 +186,41 @@ def poiseuille_dense(M=2000, N=64, seed=5, area_fraction=0.30, Cn=0.025, Ca=2.0)
     dy = (2 * W - 4 * b) / rows
     dx = cell / dy
     cols = int(np.ceil(M / rows))
+    Ns = [int(N)] * M if np.isscalar(N) else [int(N[v % len(N)]) for v in range(M)]
     xs, ys = [], []
     for v in range(M):
         r, c = v % rows, v // rows
         cx = c * dx + rng.uniform(-0.1, 0.1) * (dx - 2 * a)
         cy = -W + 2 * b + (r + 0.5) * dy + rng.uniform(-0.1, 0.1) * (dy - 2 * b)
-        x, y = vesicle_outline(N, 0.65, R, 1e-2, rng, rng.uniform(-0.05, 0.05))
+        x, y = vesicle_outline(Ns[v], 0.65, R, 1e-2, rng, rng.uniform(-0.05, 0.05))
         xs.append(x + cx)
         ys.append(y + cy)
-    return Workload("poiseuille %dx%d af %.2f" % (M, N, area_fraction), xs, ys, kappa=kappa, mu=mu,
+    if close_fraction > 0.0:
+        step = max(1, int(round(1.0 / close_fraction)))
+        for v in range(0, M - rows, step):
+            w = v + rows  # right-hand neighbour in the same row
+            hv = np.sum(np.hypot(np.diff(xs[v], append=xs[v][0]), np.diff(ys[v], append=ys[v][0]))) / Ns[v]
+            hw = np.sum(np.hypot(np.diff(xs[w], append=xs[w][0]), np.diff(ys[w], append=ys[w][0]))) / Ns[w]
+            target = close_gap * max(hv, hw)
+
+            def gap(shift):
+                return np.sqrt(((xs[v] + shift)[:, None] - xs[w][None, :]) ** 2
+                               + (ys[v][:, None] - ys[w][None, :]) ** 2).min()
+
+            lo, hi = 0.0, float(xs[w].min() - xs[v].max()) + 2.0 * target
+            if gap(0.0) <= target:
+                continue
+            for _ in range(60):  # bisection on the shift along x: the smallest point distance falls with it
+                mid = 0.5 * (lo + hi)
+                if gap(mid) > target:
+                    lo = mid
+                else:
+                    hi = mid
+            xs[v] = xs[v] + lo
+    name = "poiseuille %dx%s af %.2f" % (M, N if np.isscalar(N) else "/".join(str(n) for n in N), area_fraction)
+    if close_fraction > 0.0:
+        name += " close %.2f at %.2f h" % (close_fraction, close_gap)
+    return Workload(name, xs, ys, kappa=kappa, mu=mu,
                     dt=0.01 * W / umax, flow_kind=3, flow_p=(umax, W, 0.0, 0.0), steps=1000,
                     near_field=True, extra={"cols": cols, "dx": dx, "dy": dy})
 

@@ -1,13 +1,15 @@
 """GPU parity at the sizes of the five workloads, through the C ABI, against the FP64 oracle.
 
 * single vesicle, 32 points, 200 steps: the whole trajectory;
-* Taylor-Green batch, 64 x 128: whole steps (FP64 far field, so the FP64 bar applies to every point);
+* Taylor-Green batch, 64 x 128: whole steps (FP64 far field, so the FP64 bar applies to every point), and
+  the whole 500-step trajectory against the oracle's, stored under tests/golden/;
 * far field alone, 2000 x 128 in the 20 x 20 box: sampled targets, FP32 (1e-5) and FP64 (1e-10);
 * MLP on 128-point shapes (256 -> 512 x 3 -> 256), batch 4096: the forward pass;
 * dense Poiseuille, 2000 x 64, in the launch configuration the benchmark times (mixed precision, FP32
   far field, near-field correction on, CUDA-graph replay): the velocity u^n at sampled targets against
-  the oracle's brute-force far field (2e-5, see the test), and X^{n+1}, sigma^{n+1} of sampled vesicles
-  against the oracle's per-vesicle step given the same u^n (1e-10, 1e-8).
+  the oracle's brute-force far field at its own initial state (1e-5); with the FP64 far field,
+  X^{n+1}, sigma^{n+1} of sampled vesicles against the oracle's step of them (1e-10; sigma by
+  gpu_util.SIGMA_TOL).
 """
 import numpy as np
 import pytest
@@ -20,7 +22,8 @@ from oracle.step import Params, Suspension as OracleSuspension, advance_vesicle
 from paper_2606_25569_b300 import binding
 from paper_2606_25569_b300.workloads import farfield_box, poiseuille_dense, single_shear, taylor_green
 
-from .gpu_util import csr, offsets, rel_err_per_vesicle, split
+from .gpu_util import (check_network_output, csr, offsets, poiseuille_oracle_state, rel_err_per_vesicle, sigma_error,
+                       sigma_tolerance, split)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -30,15 +33,15 @@ def _dev(a, dtype=None):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
 
 
-def _compare(o, g, tol_x=1e-10, tol_s=1e-8):
+def _compare(o, g, tol_x=1e-10, tol_s=None):
+    """Positions per vesicle at tol_x; tension at tol_s (None: the FP64 tolerance of gpu_util.SIGMA_TOL)."""
     counts = [len(x) for x in o.xs]
     gx, gy = split(g.positions(), counts)
     ex = rel_err_per_vesicle(gx, gy, o.xs, o.ys)
-    sg = g.tension()
-    so = np.concatenate(o.sig)
-    es = np.max(np.abs(sg - so)) / np.max(np.abs(so))
+    es = sigma_error(g.tension(), o.sig)
+    print("positions %.3e, tension %.3e" % (ex, es))
     assert ex <= tol_x, ex
-    assert es <= tol_s, es
+    assert es <= sigma_tolerance(o.sig, tol_s), es
 
 
 def _pair(wl, fp64=True):
@@ -70,6 +73,39 @@ def test_taylor_green_64x128_steps():
         g.step()
         _compare(o, g)
     g.close()
+
+
+def test_taylor_green_64x128_500_steps_against_oracle_trajectory():
+    # the oracle's 500-step trajectory of the whole suspension, stored by tests/golden/
+    # make_taylor_green_trajectory.py (every eighth vesicle at nine steps); the library runs the same 500
+    # steps (FP64 far field) and is compared at each stored step, recording how the difference grows
+    import os
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "taylor_green_64x128_trajectory.npz"))
+    wl = taylor_green()
+    _, g = _pair(wl, fp64=True)
+    counts = list(wl.counts)
+    sample = [int(v) for v in ref["vesicles"]]
+    done = 0
+    rows = []
+    for k, n in enumerate(ref["steps"]):
+        g.step(int(n) - done)
+        done = int(n)
+        gx, gy = split(g.positions(), counts)
+        sg = g.tension()
+        off = wl.offsets
+        ox, oy, os_ = split(ref["xy"][k], [counts[v] for v in sample]) + ([],)
+        for i, v in enumerate(sample):
+            os_.append(ref["sigma"][k][sum(counts[u] for u in sample[:i]):][:counts[v]])
+        ex = rel_err_per_vesicle([gx[v] for v in sample], [gy[v] for v in sample], ox, oy)
+        es = sigma_error(np.concatenate([sg[off[v]:off[v + 1]] for v in sample]), os_)
+        rows.append((done, ex, es, g.counters()["corrections"], int(ref["corrections"][k])))
+    g.close()
+    for r in rows:
+        print("step %4d: positions %.3e, tension %.3e, corrections %d (oracle %d)" % r)
+    for done, ex, es, cg, co in rows:
+        assert cg == co, (done, cg, co)
+        assert ex <= 1e-10, (done, ex)
+        assert es <= sigma_tolerance([np.zeros(128)]), (done, es)
 
 
 # FP64: 1e-10, the stated FP64 bar (a sum of 256k random-sign terms loses a few digits to cancellation in
@@ -112,60 +148,66 @@ def test_mlp_forward_256x512x3_batch4096():
     net.sync()
     got = y.cpu().numpy().astype(np.float64)
     ref, _ = forward(p32, dims, X.astype(np.float64), bf16=True)
-    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err <= 1e-3, err
+    # hidden activations rounded to bfloat16 on both sides: relative L2 1e-3, 1e-2 per element (test_gpu_mlp)
+    check_network_output(got, ref, 1e-3, 1e-2, "network 256-512x3-256, batch 4096")
 
 
 def test_poiseuille_2000x64_bench_configuration_sampled():
-    wl = poiseuille_dense(2000, 64, seed=5)
+    # Every expected value comes from the oracle's own state (its redistribution and initial tension of the
+    # workload), never from the library's output.
+    wl, o, fx, fy = poiseuille_oracle_state()
+    p = o.p
+    off = wl.offsets
+    X, Y = np.concatenate(o.xs), np.concatenate(o.ys)
+    owner = np.repeat(np.arange(wl.M), wl.counts)
+    rng = np.random.default_rng(12)
+
+    # u^n of the launch configuration the benchmark times (FP32 far field, near-field correction, CUDA
+    # graph) at sampled targets: background flow + the oracle's brute-force far field, relative L2 1e-5
     stream = torch.cuda.current_stream()
-    g = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+    g = binding.Suspension(wl.flat_xy(), off, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
                            flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream,
                            use_graph=True)
-    counts = list(wl.counts)
-    off = wl.offsets
-    x0s, y0s = split(g.positions(), counts)
-    s0 = g.tension()
-    a0l0 = g.reference()
-    A0, L0 = a0l0[0], a0l0[1]
     g.step(1)
     g.sync()
     u0 = g.velocity()
-    x1s, y1s = split(g.positions(), counts)
-    s1 = g.tension()
     c = g.counters()
     g.close()
     assert c["err"] == 0
-
-    # u^n at sampled targets: background flow + brute-force far field of the oracle's forces
-    fx, fy = [], []
-    for v in range(wl.M):
-        a, b = force(x0s[v], y0s[v], s0[off[v]:off[v + 1]], wl.kappa)
-        fx.append(a)
-        fy.append(b)
-    rng = np.random.default_rng(12)
     tgt = np.sort(rng.choice(off[-1], 256, replace=False))
-    ux, uy, near = far_field(x0s, y0s, fx, fy, wl.mu, near_mask=True, targets=tgt)
+    ux, uy, near = far_field(o.xs, o.ys, fx, fy, wl.mu, near_mask=True, targets=tgt)
     assert not near  # the lattice starts with every gap wider than the near-field threshold
-    owner = np.repeat(np.arange(wl.M), wl.counts)
     loc = tgt - off[owner[tgt]]
-    X, Y = np.concatenate(x0s), np.concatenate(y0s)
     bx, by = background(wl.flow_kind, wl.flow_p, X[tgt], Y[tgt])
     gx = u0[2 * off[owner[tgt]] + loc] - bx
     gy = u0[2 * off[owner[tgt]] + wl.counts[owner[tgt]] + loc] - by
     err = np.sqrt(np.sum((gx - ux) ** 2 + (gy - uy) ** 2) / np.sum(ux ** 2 + uy ** 2))
     print("poiseuille 2000x64 far-field velocity: relative L2 error %.3e" % err)
-    # 2e-5 here, 1e-5 on the far-field workload above: in this dense suspension each source vesicle's 64
-    # terms nearly cancel (its densities sum to zero), so the FP32 rounding of each term (5.7e-6 by an
-    # FP32 emulation with FP64 sums) and of the 64-term sums leaves about 1.2e-5 of the far field
-    assert err <= 2e-5, err
+    assert err <= 1e-5, err
 
-    # one step of sampled vesicles given the same u^n
-    p = Params(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, flow_kind=wl.flow_kind, flow_p=wl.flow_p, corr_tol=0.01)
-    uxs, uys = split(u0, counts)
-    for v in rng.choice(wl.M, 16, replace=False):
-        xo, yo, so, _ = advance_vesicle(x0s[v], y0s[v], uxs[v], uys[v], A0[v], L0[v], p)
+    # one whole step of sampled vesicles (the same per-vesicle kernels, far field in FP64 so that the FP64
+    # bar applies): the oracle's u^n at their points, then its per-vesicle step
+    g = binding.Suspension(wl.flat_xy(), off, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, farfield_fp64=True,
+                           stream=stream, use_graph=True)
+    g.step(1)
+    g.sync()
+    x1s, y1s = split(g.positions(), list(wl.counts))
+    s1 = g.tension()
+    g.close()
+    sample = np.sort(rng.choice(wl.M, 16, replace=False))
+    pts = np.concatenate([np.arange(off[v], off[v + 1]) for v in sample])
+    ux, uy, near = far_field(o.xs, o.ys, fx, fy, wl.mu, near_mask=True, targets=pts)
+    assert not near
+    worst = [0.0, 0.0]
+    for i, v in enumerate(sample):
+        n = int(wl.counts[v])
+        bx, by = background(wl.flow_kind, wl.flow_p, o.xs[v], o.ys[v])
+        xo, yo, so, _ = advance_vesicle(o.xs[v], o.ys[v], ux[i * n:(i + 1) * n] + bx, uy[i * n:(i + 1) * n] + by,
+                                        o.A0[v], o.L0[v], p)
         ex = rel_err_per_vesicle([x1s[v]], [y1s[v]], [xo], [yo])
+        es = sigma_error(s1[off[v]:off[v + 1]], [so])
+        worst = [max(worst[0], ex), max(worst[1], es)]
         assert ex <= 1e-10, (v, ex)
-        es = np.max(np.abs(s1[off[v]:off[v + 1]] - so)) / np.max(np.abs(so))
-        assert es <= 1e-8, (v, es)
+        assert es <= sigma_tolerance([so]), (v, es)
+    print("poiseuille 2000x64 sampled vesicles after one step: positions %.3e, tension %.3e" % tuple(worst))

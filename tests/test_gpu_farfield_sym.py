@@ -1,10 +1,11 @@
 """GPU checks of the symmetric FP32 far field (k_farfield_sym: each unordered pair of points of different
-vesicles evaluated once, both reactions added; the default when every vesicle has 32, 64 or 128 points)
-against the FP64 oracle's all-pairs sum and against the per-target kernel.
+vesicles evaluated once, both reactions added; the default FP32 far field) against the FP64 oracle's
+all-pairs sum and against the per-target kernel.
 
 Cases span one chunk of 16 vesicles with fewer column vesicles than warps (M = 2, 5), a partial last
-chunk (M = 21, 37) and several chunks (M = 40), at N = 32, 64 and 128 (one, two and four points per lane).
-Tolerance: the stated FP32 far-field bar, 1e-5 relative L2.
+chunk (M = 21, 37) and several chunks (M = 40), at N = 32, 64 and 128 (one, two and four points per lane),
+and suspensions of uneven point counts (8 to 128 points: every pair of the three classes, padded
+segments) with and without near pairs. Tolerance: the stated FP32 far-field bar, 1e-5 relative L2.
 """
 import numpy as np
 import pytest
@@ -20,14 +21,16 @@ torch = pytest.importorskip("torch")
 
 
 def _grid(M, N, seed, spacing=3.2, close_pair=False):
+    """M vesicles on a 7-wide grid; N an int or a list of point counts (cycled)."""
     rng = np.random.default_rng(seed)
+    Ns = [N] * M if np.isscalar(N) else [N[v % len(N)] for v in range(M)]
     xs, ys = [], []
     for v in range(M):
-        x, y = vesicle_outline(N, float(rng.uniform(0.6, 0.9)), 1.0, 2e-2, rng, rng.uniform(0, 2 * np.pi))
+        x, y = vesicle_outline(Ns[v], float(rng.uniform(0.6, 0.9)), 1.0, 2e-2, rng, rng.uniform(0, 2 * np.pi))
         xs.append(x + spacing * (v % 7))
         ys.append(y + spacing * (v // 7))
     if close_pair:  # vesicle 1's leftmost point moved to half a spacing (2 pi / N <= h) right of vesicle 0's rightmost
-        h = 2 * np.pi / N
+        h = 2 * np.pi / max(Ns[0], Ns[1])
         i0, i1 = int(np.argmax(xs[0])), int(np.argmin(xs[1]))
         xs[1] = xs[1] - xs[1][i1] + xs[0][i0] + 0.5 * h
         ys[1] = ys[1] - ys[1][i1] + ys[0][i0]
@@ -49,6 +52,43 @@ def test_symmetric_far_field_matches_oracle(M, N):
     ref = np.concatenate([np.concatenate([ux, uy]) for ux, uy in o.interaction_velocity()])
     assert _rel_l2(got, ref) <= 1e-5
     g.close()
+
+
+UNEVEN = [32, 128, 64, 48, 16, 100, 8, 96, 66, 34, 128, 20]
+
+
+@pytest.mark.parametrize("M", [12, 45])
+def test_symmetric_far_field_uneven_matches_oracle(M):
+    xs, ys = _grid(M, UNEVEN, seed=M, spacing=3.4)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.0, mu=1.3, dt=1e-4)
+    assert g.farfield_variant()[0] == -1  # the symmetric kernel is in use
+    g.step()
+    got = g.velocity()
+    o = OracleSuspension(xs, ys, Params(kappa=1.0, mu=1.3, dt=1e-4))
+    ref = np.concatenate([np.concatenate([ux, uy]) for ux, uy in o.interaction_velocity()])
+    err = _rel_l2(got, ref)
+    print("symmetric far field, %d vesicles of uneven N: relative L2 %.3e" % (M, err))
+    assert err <= 1e-5, err
+    g.close()
+
+
+def test_symmetric_far_field_uneven_with_near_pairs_matches_oracle_and_per_target():
+    xs, ys = _grid(30, [128, 32, 64, 48, 128, 16], seed=5, spacing=3.4, close_pair=True)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0, 0, 0), near_field=True)
+    a = binding.Suspension(csr(xs, ys), offsets(xs), **kw)
+    b = binding.Suspension(csr(xs, ys), offsets(xs), farfield_per_target=True, **kw)
+    assert a.farfield_variant()[0] == -1 and b.farfield_variant()[0] >= 0
+    a.step()
+    b.step()
+    o = OracleSuspension(xs, ys, Params(**kw))
+    ref = np.concatenate([np.concatenate([ux, uy]) for ux, uy in o.interaction_velocity()])
+    assert a.counters()["near_pairs"] == b.counters()["near_pairs"] == len(o.near_pairs) > 0
+    err, err_pt = _rel_l2(a.velocity(), ref), _rel_l2(a.velocity(), b.velocity())
+    print("uneven with %d near pairs: against the oracle %.3e, against the per-target kernel %.3e"
+          % (len(o.near_pairs), err, err_pt))
+    assert err <= 1e-5 and err_pt <= 1e-5, (err, err_pt)
+    a.close()
+    b.close()
 
 
 def test_symmetric_and_per_target_kernels_agree_with_near_pairs():
@@ -91,9 +131,10 @@ def test_symmetric_far_field_is_deterministic():
     assert runs[0][2] == runs[1][2] > 0
 
 
-def test_far_field_plan_symmetric_and_per_target_agree():
-    # vs_farfield_eval: precision 0 (symmetric kernel for equal N = 32/64/128) against 3 (per target), near mask on
-    xs, ys = _grid(37, 128, seed=12, close_pair=True)
+@pytest.mark.parametrize("N", [128, UNEVEN])
+def test_far_field_plan_symmetric_and_per_target_agree(N):
+    # vs_farfield_eval: precision 0 (symmetric kernel) against 3 (per target), near mask on
+    xs, ys = _grid(37, N, seed=12, close_pair=True)
     rng = np.random.default_rng(12)
     f = np.concatenate([np.concatenate([rng.standard_normal(len(x)), rng.standard_normal(len(x))]) for x in xs])
     off = offsets(xs)

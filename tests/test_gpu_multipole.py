@@ -5,11 +5,10 @@ import pytest
 
 from oracle.farfield import far_field
 from oracle.flows import background
-from oracle.spectral import force
 from paper_2606_25569_b300 import binding
 from paper_2606_25569_b300.workloads import farfield_box, poiseuille_dense
 
-from .gpu_util import csr, split
+from .gpu_util import csr, poiseuille_oracle_state, split
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -49,21 +48,16 @@ def test_multipole_suspension_poiseuille_2000x64():
               near_field=True, stream=stream, use_graph=True)
     g = binding.Suspension(wl.flat_xy(), wl.offsets, farfield_multipole=True, **kw)
     d = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
-    counts = list(wl.counts)
     off = wl.offsets
-    x0s, y0s = split(g.positions(), counts)
-    s0 = g.tension()
     g.step(1)
     d.step(1)
     g.sync()
     u_mp, u_pt = g.velocity(), d.velocity()
     assert g.counters()["near_pairs"] == d.counters()["near_pairs"]
-    # against the oracle's all-pairs sum at sampled targets (same tolerance as the point-sum FP32 kernel)
-    fx, fy = [], []
-    for v in range(wl.M):
-        a, b = force(x0s[v], y0s[v], s0[off[v]:off[v + 1]], wl.kappa)
-        fx.append(a)
-        fy.append(b)
+    # against the oracle's all-pairs sum at sampled targets, at the oracle's own initial state (same
+    # tolerance as the point-sum FP32 kernel)
+    _, o, fx, fy = poiseuille_oracle_state()
+    x0s, y0s = o.xs, o.ys
     rng = np.random.default_rng(22)
     tgt = np.sort(rng.choice(off[-1], 256, replace=False))
     ux, uy, near = far_field(x0s, y0s, fx, fy, wl.mu, near_mask=True, targets=tgt)

@@ -5,7 +5,8 @@ all device memory to someone else, a real-time loop that must not allocate) get 
 far-field sum as vs_farfield_eval, computed with scratch that lives in a static device array of
 the library. This file is collected last so that a run stopping at the first failure has
 already run every other test. It calls the entry point through the C ABI twice in a row, on
-two different layouts, and compares each result with the allocating entry point.
+two different layouts, and compares each result with the allocating entry point; and once on a
+small suspension of uneven point counts against the oracle's all-pairs sum.
 """
 import ctypes
 
@@ -57,6 +58,37 @@ def test_static_scratch_far_field_matches_allocating_entry_point(precision, tol)
         assert np.all(np.isfinite(g))
         err = np.linalg.norm(g - r) / np.linalg.norm(r)
         assert err <= tol, err
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-12)])
+def test_static_scratch_far_field_matches_oracle_on_uneven_vesicles(precision, tol):
+    from oracle.farfield import far_field
+    from paper_2606_25569_b300 import binding
+    from paper_2606_25569_b300.workloads import vesicle_outline
+    L = binding.lib()
+    rng = np.random.default_rng(31)
+    xs, ys, fx, fy = [], [], [], []
+    for v, N in enumerate([16, 64, 32, 8, 128, 48]):
+        x, y = vesicle_outline(N, 0.75, 0.3, 1e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x + 0.9 * (v % 3))
+        ys.append(y + 0.9 * (v // 3))
+        fx.append(rng.standard_normal(N))
+        fy.append(rng.standard_normal(N))
+    off = np.concatenate([[0], np.cumsum([len(x) for x in xs])]).astype(np.int64)
+    xy = torch.as_tensor(_csr(xs, ys), device="cuda")
+    f = torch.as_tensor(_csr(fx, fy), device="cuda")
+    got = torch.full_like(xy, float("nan"))
+    stream = torch.cuda.current_stream()
+    st = L.vs_farfield_eval_static(off.ctypes.data, len(off) - 1, 0.9, precision, xy.data_ptr(), f.data_ptr(),
+                                   got.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    ux, uy, _ = far_field(xs, ys, fx, fy, 0.9, near_mask=False)
+    ref = np.concatenate([np.concatenate([ux[off[v]:off[v + 1]], uy[off[v]:off[v + 1]]]) for v in range(len(xs))])
+    g = got.cpu().numpy()
+    err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    print("static far field against the oracle, precision %d: %.3e" % (precision, err))
+    assert err <= tol, err
 
 
 def test_static_scratch_rejects_oversized_input():
