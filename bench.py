@@ -47,7 +47,7 @@ FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 FFS_DRAM_BYTES = 3.64e6 + 195.51e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 # learned advection and tension: velocity modes expanded and column modes kept, training epochs
-FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 16, 30
+FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
 
 
 def parse():

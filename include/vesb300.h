@@ -238,8 +238,10 @@ vs_status vs_relax(vs_suspension* s, const double* xy_in, double* xy_out);
  * vs_set_flow_networks: a hybrid suspension (mode 1) with these networks set takes, in every step, the
  * advection X* = X^n + dt R^T shift(sum_i f_i Q_i) and the tension sigma^{n+1} = -shift(S_sigma) / L^2 -
  * shift(sum_i f_i S_i) from them (modes of u above Kf dropped) instead of the exact operators, which it
- * then no longer builds at X^n or X^{n+1} (only for the source vesicles of near pairs, whose near-field
- * layers need them); the relaxation stays as vs_set_network and exact_every arrange. The relaxation
+ * then builds at X^n and X^{n+1} only for the vesicles of the hybrid fallback (in a near pair this step or
+ * within exact_gap spacings of another vesicle: those take the exact advection and tension) and for the
+ * source vesicles of near pairs (their near-field layers need them); the relaxation stays as
+ * vs_set_network and exact_every arrange. The relaxation
  * network must be set first; adv and ten are borrowed, share the suspension's stream, have batch capacity
  * >= M; Kf, Kout in [0, N/2 - 1]; both NULL removes them. Errors: VS_ERR_INVALID_ARG.
  *

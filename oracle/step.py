@@ -28,7 +28,8 @@ hybrid step (relax_learned), except for vesicles in a near pair this step (the t
 source vesicle) or within exact_gap (default HYBRID_EXACT_GAP) spacings of another vesicle, and, with exact_every = m > 0,
 on every m-th step: those relax exactly, the plain step serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
 too; here they keep the exact relaxation). With Params.flow_net set as well, steps 3 and 6 of every step
-take the learned advection and tension of oracle.learned (Eqs. advectionMap, advTenMap) for every vesicle. Initial tension (not given in the paper):
+take the learned advection and tension of oracle.learned (Eqs. advectionMap, advTenMap), except for the
+vesicles of that fallback set, which keep the exact ones. Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -173,9 +174,10 @@ class Suspension:
             p = copy.copy(p)
             p.relax_net = None
         u = self.interaction_velocity()
-        # in a learned step, vesicles in a near pair (as the target's owner or as the source) relax exactly
+        # in a learned step, vesicles in a near pair (as the target's owner or as the source) relax exactly; with
+        # the flow networks they also take the exact advection and tension, in every step
         exact = set()
-        if p.relax_net is not None:
+        if p.relax_net is not None or flow is not None:
             owner = np.repeat(np.arange(len(self.xs)), [len(x) for x in self.xs])
             for t, v in self.near_pairs:
                 exact.update((int(owner[t]), int(v)))
@@ -183,12 +185,13 @@ class Suspension:
         nxs, nys, nsig, vel = [], [], [], []
         for v, (x, y) in enumerate(zip(self.xs, self.ys)):
             ux, uy = u[v]
-            pv = p
+            pv, fv = p, flow
             if v in exact:
                 import copy
                 pv = copy.copy(p)
                 pv.relax_net = None
-            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], pv, flow)
+                fv = None
+            xc, yc, sig, fired = advance_vesicle(x, y, ux, uy, self.A0[v], self.L0[v], pv, fv)
             self.corrections += int(fired)
             nxs.append(xc)
             nys.append(yc)

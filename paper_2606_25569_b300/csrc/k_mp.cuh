@@ -270,11 +270,13 @@ __global__ void __launch_bounds__(THREADS) k_advect_mp(VesIndex vi, const double
                                                    const double* __restrict__ tx, const double* __restrict__ ty,
                                                    const double* __restrict__ tab,
                                                    const float* __restrict__ scratch32, int s, double dt,
-                                                   double* __restrict__ xy_out, unsigned* err) {
+                                                   double* __restrict__ xy_out, unsigned* err,
+                                                   const int* __restrict__ active = nullptr) {
   __shared__ MpShared sh;
   __shared__ float2 g[NMAX], e[NMAX];
   __shared__ double sg[NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);
@@ -299,11 +301,13 @@ __global__ void __launch_bounds__(THREADS) k_tension_mp(VesIndex vi, const doubl
                                                     const double* __restrict__ sa, const double* __restrict__ tx,
                                                     const double* __restrict__ ty, const double* __restrict__ tab,
                                                     const float* __restrict__ scratch32, int s, double kappa,
-                                                    double* __restrict__ sigma, unsigned* err) {
+                                                    double* __restrict__ sigma, unsigned* err,
+                                                    const int* __restrict__ active = nullptr) {
   __shared__ MpShared sh;
   __shared__ float2 g[NMAX], e[NMAX];
   __shared__ double sg[NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   mp_load_geom(sh, tab + vi.toff[v], sa, tx, ty, N, o);

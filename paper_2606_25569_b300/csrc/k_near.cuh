@@ -2,14 +2,19 @@
 //
 // For every source vesicle v with at least one near target (recorded by the far-field kernel):
 //  k_near_layers  the 5N layer points X + d h n, d in {-1, -1/2, 0, 1/2, 1}, and the exact
-//                 single layer S[X, f] there: on the curve S f with the cached self matrix, off the
-//                 curve the trapezoid rule on the curve upsampled by rho = ceil(sqrt(N)) (FP64);
+//                 single layer S[X, f] there: on the curve S f with the cached self matrix (FP64 sums),
+//                 off the curve the trapezoid rule on the curve upsampled by rho = ceil(sqrt(N)), in FP32
+//                 (the RBF that takes these values is FP32) with the far field's log scaling: each
+//                 target's log arguments scaled by a power of two near 1 / (|x - c|^2 + reach^2) and the
+//                 exponent times the density sum added once;
 //  k_near_rbf     (Phi + lam I) w = u_layers, Phi_ab = exp(-|x_a - x_b|^2 / (c h)^2), c = 2,
-//                 lam = 1e-3, by an FP32 Cholesky (the paper's precision) in the vesicle's scratch;
+//                 lam = 1e-3, by an FP32 Cholesky (the paper's precision): k_near_rbf_smem holds the
+//                 lower triangle in shared memory (5N <= 320), k_near_rbf works in the vesicle's scratch;
 //  k_near_apply   u(x_t) += sum_b phi(|x_t - x_b|) w_b for each near (target, vesicle) pair.
 #pragma once
 #include "common.cuh"
 #include "k_dense.cuh"
+#include "k_farfield.cuh"
 #include "k_vesicle.cuh"
 
 namespace vs {
@@ -103,7 +108,12 @@ struct NearBufs {
   float* phi;      // per vesicle at moff[v]: (5N)^2 floats
 };
 
-// Layer points and exact layer velocities. Dynamic shared memory: 12 * rho * N doubles.
+// Layer points and exact layer velocities. Dynamic shared memory: near_layers_smem(N) bytes.
+inline size_t near_layers_smem(int N) {
+  const int Nu = (int)std::ceil(std::sqrt((double)N)) * N;
+  return (size_t)Nu * sizeof(float4) + 2 * (size_t)Nu * sizeof(float);
+}
+
 __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __restrict__ has_near,
                                                      const double* __restrict__ xy, const double* __restrict__ f,
                                                      PointGeom g, const double* __restrict__ length,
@@ -111,70 +121,79 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
                                                      const double* __restrict__ scratch,
                                                      const float* __restrict__ scratch32, int s, double mu,
                                                      NearBufs nb) {
-  extern __shared__ double sm[];
+  extern __shared__ float4 smf[];
   const int v = vi.vid(blockIdx.x);
   if (!has_near[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int rho = near_rho(N), Nu = rho * N;
   const int tid = threadIdx.x;
-  double* cs = sm;            // cos(2 pi q / Nu)
-  double* sn = cs + Nu;       // sin(2 pi q / Nu)
-  double* xu = sn + Nu;
-  double* yu = xu + Nu;
-  double* gx = yu + Nu;
-  double* gy = gx + Nu;
-  __shared__ double cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
-  __shared__ double fl[2 * NMAX];
+  float4* src = smf;                  // upsampled points relative to the mean point, and g (Nu)
+  float* cs = (float*)(smf + Nu);     // cos(2 pi q / Nu)
+  float* sn = cs + Nu;                // sin(2 pi q / Nu)
+  __shared__ float cre[4][NMAX / 2 + 1], cim[4][NMAX / 2 + 1];
+  __shared__ double fl[2 * NMAX], gsum[2], cmean[2], red[8];
   const double* T = tab + vi.toff[v];
-  for (int q = tid; q < Nu; q += blockDim.x) sincospi(2.0 * q / Nu, &sn[q], &cs[q]);
+  for (int q = tid; q < Nu; q += blockDim.x) sincospif(2.f * q / Nu, &sn[q], &cs[q]);
   for (int r = tid; r < 2 * N; r += blockDim.x) fl[r] = f[2 * o + r];
-  // Fourier coefficients of x, y, f_x, f_y (k = 0..N/2)
+  // Fourier coefficients of x, y, f_x, f_y (k = 0..N/2), FP64 sums; the curve's relative to its mean point
   const int nk = N / 2 + 1;
   for (int e = tid; e < 4 * nk; e += blockDim.x) {
     const int comp = e / nk, k = e - comp * nk;
-    const double* src = (comp < 2) ? (xy + 2 * o + comp * N) : (f + 2 * o + (comp - 2) * N);
+    const double* sv = (comp < 2) ? (xy + 2 * o + comp * N) : (f + 2 * o + (comp - 2) * N);
     double re = 0.0, im = 0.0;
     int m = 0;
     for (int j = 0; j < N; ++j) {
-      re = fma(src[j], T[15 * N + m], re);
-      im = fma(-src[j], T[16 * N + m], im);
+      re = fma(sv[j], T[15 * N + m], re);
+      im = fma(-sv[j], T[16 * N + m], im);
       m += k;
       if (m >= N) m -= N;
     }
-    cre[comp][k] = re / N;
-    cim[comp][k] = im / N;
+    if (comp < 2 && k == 0) cmean[comp] = re / N;
+    cre[comp][k] = (comp < 2 && k == 0) ? 0.f : (float)(re / N);
+    cim[comp][k] = (float)(im / N);
   }
   __syncthreads();
-  // upsampled curve, its speed, and the scaled density g = f |X_alpha| (2 pi / Nu) / (4 pi mu)
-  const double cw = 2.0 * VS_PI / Nu / (4.0 * VS_PI * mu);
+  const double cx = cmean[0], cy = cmean[1];
+  // upsampled curve (relative to the mean point), its speed, and g = f |X_alpha| (2 pi / Nu) / (4 pi mu)
+  const float cw = (float)(2.0 * VS_PI / Nu / (4.0 * VS_PI * mu));
+  double gxs = 0.0, gys = 0.0;
+  float r2max = 0.f;
   for (int q = tid; q < Nu; q += blockDim.x) {
-    double val[4], dx = 0.0, dy = 0.0;
+    float val[4], dx = 0.f, dy = 0.f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) val[c] = cre[c][0];
     int idx = 0;
     for (int k = 1; k < N / 2; ++k) {
       idx += q;
       if (idx >= Nu) idx %= Nu;
-      const double ck = cs[idx], sk = sn[idx];
+      const float ck = cs[idx], sk = sn[idx];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) val[c] += 2.0 * (cre[c][k] * ck - cim[c][k] * sk);
-      dx -= 2.0 * k * (cre[0][k] * sk + cim[0][k] * ck);
-      dy -= 2.0 * k * (cre[1][k] * sk + cim[1][k] * ck);
+      for (int c = 0; c < 4; ++c) val[c] += 2.f * (cre[c][k] * ck - cim[c][k] * sk);
+      dx -= 2.f * k * (cre[0][k] * sk + cim[0][k] * ck);
+      dy -= 2.f * k * (cre[1][k] * sk + cim[1][k] * ck);
     }
     const int iN = (int)(((int64_t)q * (N / 2)) % Nu);
 #pragma unroll
     for (int c = 0; c < 4; ++c) val[c] += cre[c][N / 2] * cs[iN];
     dx -= cre[0][N / 2] * (N / 2) * sn[iN];
     dy -= cre[1][N / 2] * (N / 2) * sn[iN];
-    const double w = sqrt(dx * dx + dy * dy) * cw;
-    xu[q] = val[0];
-    yu[q] = val[1];
-    gx[q] = val[2] * w;
-    gy[q] = val[3] * w;
+    const float w = sqrtf(dx * dx + dy * dy) * cw;
+    src[q] = make_float4(val[0], val[1], val[2] * w, val[3] * w);
+    gxs += (double)(val[2] * w);
+    gys += (double)(val[3] * w);
+    r2max = fmaxf(r2max, val[0] * val[0] + val[1] * val[1]);
+  }
+  gxs = block_sum(gxs, red);
+  gys = block_sum(gys, red);
+  const double rmax = block_max((double)r2max, red);
+  if (tid == 0) {
+    gsum[0] = gxs;
+    gsum[1] = gys;
   }
   __syncthreads();
   const double h = length[v] / N;
+  const float reach2 = (float)(rmax + h * h);
   double* L = nb.layer + 30 * o;
   double* LX = L;
   double* LY = L + 5 * N;
@@ -185,6 +204,7 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
   const double* S = scratch + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN;
   const float* Sh = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN : nullptr;
   const float* Sl = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::SL) * NN : nullptr;
+  const float hl2 = -0.34657359027997264f;  // -ln(2)/2: -log|r| = hl2 log2|r|^2
   for (int e = tid; e < 5 * N; e += blockDim.x) {
     const int lay = e / N, j = e - lay * N;
     const double d = c_layer_d[lay] * h;
@@ -201,19 +221,132 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
         ax = fma(sx, fl[k], ax);
         ay = fma(sy, fl[k], ay);
       }
-    } else {
+    } else {  // off the curve: FP32 trapezoid sums on the upsampled curve
+      const float tx = (float)(px - cx), ty = (float)(py - cy);
+      float le;
+      const float sc = pow2_scale(fmaf(tx, tx, ty * ty) + reach2, le);
+      float lx = 0.f, ly = 0.f, qx = 0.f, qy = 0.f;
       for (int m = 0; m < Nu; ++m) {
-        const double rx = px - xu[m], ry = py - yu[m];
-        const double r2 = rx * rx + ry * ry;
-        const double lg = -0.5 * log(r2);
-        const double q = (rx * gx[m] + ry * gy[m]) / r2;
-        ax += lg * gx[m] + q * rx;
-        ay += lg * gy[m] + q * ry;
+        const float4 sm = src[m];
+        const float rx = tx - sm.x, ry = ty - sm.y;
+        const float r2 = fmaf(rx, rx, ry * ry);
+        const float lg = fast_lg2(r2 * sc);
+        const float q = fmaf(rx, sm.z, ry * sm.w) * fast_rcp(r2);
+        lx = fmaf(lg, sm.z, lx);
+        ly = fmaf(lg, sm.w, ly);
+        qx = fmaf(q, rx, qx);
+        qy = fmaf(q, ry, qy);
       }
+      ax = (double)hl2 * ((double)lx + (double)le * gsum[0]) + (double)qx;
+      ay = (double)hl2 * ((double)ly + (double)le * gsum[1]) + (double)qy;
     }
     UX[e] = ax;
     UY[e] = ay;
   }
+}
+
+// FP32 Cholesky of (Phi + lam I) and the two RBF weight vectors for 5N <= 320, the lower triangle held
+// packed in shared memory (row i at i (i + 1) / 2; dynamic shared memory near_rbf_smem(5N) bytes). One CTA
+// per near vesicle: the trailing update of step k by warps over rows and lanes over columns, the two
+// triangular solves by warp 0 (forward by rows, backward by columns, both reading rows of L).
+constexpr int NEAR_RBF_SMEM_N = 320;
+inline size_t near_rbf_smem(int n) { return ((size_t)n * (n + 1) / 2 + 3 * (size_t)n) * sizeof(float); }
+
+__global__ void __launch_bounds__(512) k_near_rbf_smem(VesIndex vi, const int* __restrict__ has_near,
+                                                       const double* __restrict__ length, NearBufs nb,
+                                                       unsigned* err) {
+  extern __shared__ float sA[];
+  __shared__ int bad;
+  const int v = vi.vid(blockIdx.x);
+  if (!has_near[v]) return;
+  const int N = vi.N[v];
+  const int n = 5 * N;
+  const int64_t o = vi.off[v];
+  float* colk = sA + (size_t)n * (n + 1) / 2;
+  float* y1 = colk + n;
+  float* y2 = y1 + n;
+  const double h = length[v] / N;
+  const float ie2 = (float)(1.0 / (NEAR_RBF_C * h * NEAR_RBF_C * h));
+  double* L = nb.layer + 30 * o;
+  const double* LX = L;
+  const double* LY = L + 5 * N;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  for (int i = wid; i < n; i += nw) {
+    float* row = sA + (size_t)i * (i + 1) / 2;
+    for (int j = lane; j <= i; j += 32) {
+      const float dx = (float)(LX[i] - LX[j]), dy = (float)(LY[i] - LY[j]);
+      float p = expf(-(dx * dx + dy * dy) * ie2);
+      if (i == j) p += (float)NEAR_RBF_NUGGET;
+      row[j] = p;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float dkk = sA[(size_t)k * (k + 1) / 2 + k];
+    const float d = dkk > 0.f ? sqrtf(dkk) : 1.f;
+    if (tid == 0 && !(dkk > 0.f)) bad = 1;
+    const float inv = 1.f / d;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+      float* a = sA + (size_t)i * (i + 1) / 2 + k;
+      const float l = *a * inv;
+      *a = l;
+      colk[i] = l;
+    }
+    __syncthreads();
+    if (tid == 0) sA[(size_t)k * (k + 1) / 2 + k] = d;
+    for (int i = k + 1 + wid; i < n; i += nw) {
+      const float li = colk[i];
+      float* row = sA + (size_t)i * (i + 1) / 2;
+      for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fmaf(-li, colk[j], row[j]);
+    }
+    __syncthreads();
+  }
+  if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
+  const double* UX = L + 10 * N;
+  const double* UY = L + 15 * N;
+  for (int i = tid; i < n; i += blockDim.x) { y1[i] = (float)UX[i]; y2[i] = (float)UY[i]; }
+  __syncthreads();
+  if (wid == 0) {
+    // forward L y = u: row i of L is contiguous
+    for (int i = 0; i < n; ++i) {
+      const float* row = sA + (size_t)i * (i + 1) / 2;
+      float s1 = 0.f, s2 = 0.f;
+      for (int k = lane; k < i; k += 32) {
+        s1 = fmaf(row[k], y1[k], s1);
+        s2 = fmaf(row[k], y2[k], s2);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      }
+      if (lane == 0) {
+        y1[i] = (y1[i] - s1) / row[i];
+        y2[i] = (y2[i] - s2) / row[i];
+      }
+      __syncwarp();
+    }
+    // backward L^T w = y by columns: w_i = y_i / L_ii, then y_k -= L_ik w_i for k < i (row i of L)
+    for (int i = n - 1; i >= 0; --i) {
+      const float* row = sA + (size_t)i * (i + 1) / 2;
+      const float w1 = y1[i] / row[i], w2 = y2[i] / row[i];
+      __syncwarp();
+      for (int k = lane; k < i; k += 32) {
+        y1[k] = fmaf(-row[k], w1, y1[k]);
+        y2[k] = fmaf(-row[k], w2, y2[k]);
+      }
+      if (lane == 0) {
+        y1[i] = w1;
+        y2[i] = w2;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double* WX = L + 20 * N;
+  double* WY = L + 25 * N;
+  for (int i = tid; i < n; i += blockDim.x) { WX[i] = y1[i]; WY[i] = y2[i]; }
 }
 
 // FP32 Cholesky of (Phi + lam I) and the two RBF weight vectors. One CTA per near vesicle.

@@ -13,14 +13,17 @@ struct PointGeom {
   const double* ty;
 };
 
-// X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s (Eq. advection_disc).
+// X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s (Eq. advection_disc);
+// with `active`, only the vesicles flagged there.
 __global__ void __launch_bounds__(256) k_advect(VesIndex vi, const double* __restrict__ xy,
                                                 const double* __restrict__ u,
                                                 PointGeom g, const double* __restrict__ tab,
                                                 const double* __restrict__ scratch, int s, const int* __restrict__ piv,
-                                                double dt, double* __restrict__ xy_out) {
+                                                double dt, double* __restrict__ xy_out,
+                                                const int* __restrict__ active = nullptr) {
   __shared__ double d[NMAX], u1[NMAX], u2[NMAX], b[2 * NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;
@@ -209,15 +212,17 @@ __global__ void __launch_bounds__(256) k_redistribute(VesIndex vi, const double*
   }
 }
 
-// sigma = -L^{-1} P (B X + u) at slot s (Eq. tension_disc), with B X = -kappa S X_ssss.
+// sigma = -L^{-1} P (B X + u) at slot s (Eq. tension_disc), with B X = -kappa S X_ssss; with `active`, only
+// the vesicles flagged there.
 __global__ void __launch_bounds__(256) k_tension(VesIndex vi, const double* __restrict__ bx,
                                                  const double* __restrict__ by, const double* __restrict__ u,
                                                  PointGeom g,
                                                  const double* __restrict__ tab, const double* __restrict__ scratch,
                                                  int s, const int* __restrict__ piv, double kappa,
-                                                 double* __restrict__ sigma) {
+                                                 double* __restrict__ sigma, const int* __restrict__ active = nullptr) {
   __shared__ double d[NMAX], b[2 * NMAX], w[2 * NMAX], rhs[NMAX];
   const int v = vi.vid(blockIdx.x);
+  if (active && !active[v]) return;
   const int N = vi.N[v];
   const int64_t o = vi.off[v];
   const int i = threadIdx.x;

@@ -900,30 +900,31 @@ vs_status tension(vs_suspension* h, const double* u, int s) {
 }
 
 // sigma_out = -L^{-1} P (B X + u) with the operators of slot s and the geometry in the SourceBufs.
-vs_status tension_into(vs_suspension* h, const double* u, int s, double* sigma_out) {
+vs_status tension_into(vs_suspension* h, const double* u, int s, double* sigma_out, const int* active = nullptr) {
   const VesIndex vi = h->D.vi();
   const int M = h->L.M;
   if (mixed(h)) {
     MP_DISPATCH(h, "k_tension_mp", k_tension_mp, M, (vi, h->B.bx, h->B.by, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab,
-                                                        h->scratch32, s, h->p.kappa_b, sigma_out, h->err));
+                                                        h->scratch32, s, h->p.kappa_b, sigma_out, h->err, active));
   } else {
     VS_LAUNCH(h, "k_tension", k_tension<<<M, 256, 0, h->stream>>>(vi, h->B.bx, h->B.by, u, h->B.pg(), h->D.tab, h->scratch, s,
-                                                                 h->piv, h->p.kappa_b, sigma_out));
+                                                                 h->piv, h->p.kappa_b, sigma_out, active));
   }
   VS_CK(h, cudaGetLastError(), "tension");
   return VS_OK;
 }
 
 // xo = xy + dt (I - M) u with the operators of slot s (Eq. advection_disc).
-vs_status advect_into(vs_suspension* h, const double* xy, const double* u, int s, double dt, double* xo) {
+vs_status advect_into(vs_suspension* h, const double* xy, const double* u, int s, double dt, double* xo,
+                      const int* active = nullptr) {
   const VesIndex vi = h->D.vi();
   const int M = h->L.M;
   if (mixed(h)) {
     MP_DISPATCH(h, "k_advect_mp", k_advect_mp, M, (vi, xy, u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s,
-                                                      dt, xo, h->err));
+                                                      dt, xo, h->err, active));
   } else {
     VS_LAUNCH(h, "k_advect", k_advect<<<M, 256, 0, h->stream>>>(vi, xy, u, h->B.pg(), h->D.tab, h->scratch, s, h->piv, dt,
-                                                               xo));
+                                                               xo, active));
   }
   VS_CK(h, cudaGetLastError(), "advection");
   return VS_OK;
@@ -989,13 +990,17 @@ vs_status near_field(vs_suspension* h, int s, bool build_sources = false) {
     vs_status st = build_operators(h, h->xy, s, h->has_near);
     if (st != VS_OK) return st;
   }
-  const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
-  const size_t smem = 6 * (size_t)Nu * sizeof(double);
+  const size_t smem = near_layers_smem(L.nmax);
   VS_LAUNCH(h, "k_near_layers", k_near_layers<<<L.M, 256, smem, h->stream>>>(vi, h->has_near, h->xy, h->B.f, h->B.pg(),
                                                                             h->B.length, h->D.tab, h->scratch,
                                                                             mixed(h) ? h->scratch32 : nullptr, s,
                                                                             h->p.mu, h->nb));
-  VS_LAUNCH(h, "k_near_rbf", k_near_rbf<<<L.M, 256, 0, h->stream>>>(vi, h->has_near, h->B.length, h->nb, h->err));
+  if (5 * L.nmax <= NEAR_RBF_SMEM_N) {
+    VS_LAUNCH(h, "k_near_rbf", k_near_rbf_smem<<<L.M, 512, near_rbf_smem(5 * L.nmax), h->stream>>>(
+                                   vi, h->has_near, h->B.length, h->nb, h->err));
+  } else {
+    VS_LAUNCH(h, "k_near_rbf", k_near_rbf<<<L.M, 256, 0, h->stream>>>(vi, h->has_near, h->B.length, h->nb, h->err));
+  }
   VS_LAUNCH(h, "k_near_apply", k_near_apply<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->D.off, h->D.N,
                                                                         h->B.near_cnt, h->B.near_v, h->xy,
                                                                         h->B.length, h->nb, h->u));
@@ -1070,9 +1075,26 @@ vs_status step_once(vs_suspension* h) {
   // (3) u += far field (near pairs masked) + near-field correction
   if ((st = far_field(h)) != VS_OK) return st;
   if (h->p.near_field && L.M > 1 && (st = near_field(h, cur, lf)) != VS_OK) return st;
+  // the plain step is the fallback of the learned one: vesicles in a near pair this step, or closer to another
+  // vesicle than exact_gap (default HYBRID_EXACT_GAP) spacings h, relax exactly in a learned step and, with
+  // the flow networks, take the exact advection and tension in every step
+  const bool fallback = M > 1 && (learned_step(h) || lf);
+  if (fallback) {
+    VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
+    const int tgrid = (int)((L.P + 127) / 128);
+    if (h->p.near_field)
+      VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
+                                                                                     h->B.near_v, h->involved));
+    VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
+                                                                       exact_gap(h), h->involved));
+  }
   // (4) advection
   if (lf) {
     if ((st = flow_learned(h, false, h->xy, h->u, h->xy_star)) != VS_OK) return st;
+    if (M > 1) {
+      if ((st = build_operators(h, h->xy, cur, h->involved)) != VS_OK) return st;
+      if ((st = advect_into(h, h->xy, h->u, cur, h->p.dt, h->xy_star, h->involved)) != VS_OK) return st;
+    }
   } else if (mixed(h)) {
     MP_DISPATCH(h, "k_advect_mp", k_advect_mp, M, (vi, h->xy, h->u, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32,
                                                       cur, h->p.dt, h->xy_star, h->err));
@@ -1084,18 +1106,7 @@ vs_status step_once(vs_suspension* h) {
   // (5) relaxation at X*: exact (plain) or the learned map (hybrid)
   if (learned_step(h)) {
     if ((st = relax_learned(h, h->xy_star, h->xy_next)) != VS_OK) return st;
-    if (M > 1) {
-      // the plain step is the fallback of the learned one: vesicles in a near pair, or closer to another
-      // vesicle than exact_gap (default HYBRID_EXACT_GAP) spacings, relax exactly
-      VS_CK(h, cudaMemsetAsync(h->involved, 0, M * sizeof(int), h->stream), "hybrid fallback");
-      const int tgrid = (int)((L.P + 127) / 128);
-      if (h->p.near_field)
-        VS_LAUNCH(h, "k_near_involved", k_near_involved<<<tgrid, 128, 0, h->stream>>>(L.P, h->D.owner, h->B.near_cnt,
-                                                                                       h->B.near_v, h->involved));
-      VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
-                                                                         exact_gap(h), h->involved));
-      if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
-    }
+    if (M > 1 && (st = relax_exact(h, h->xy_star, h->xy_next, nxt, h->involved)) != VS_OK) return st;
   } else {
     if ((st = relax_exact(h, h->xy_star, h->xy_next, nxt)) != VS_OK) return st;
   }
@@ -1105,6 +1116,11 @@ vs_status step_once(vs_suspension* h) {
   // (7) tension at the redistributed X^{n+1}; operators cached in slot nxt for the next step
   if (lf) {
     if ((st = flow_learned(h, true, h->xy, h->u_r, h->sigma)) != VS_OK) return st;
+    if (M > 1) {
+      if ((st = geometry(h, h->xy, false, h->involved)) != VS_OK) return st;
+      if ((st = build_operators(h, h->xy, nxt, h->involved)) != VS_OK) return st;
+      if ((st = tension_into(h, h->u_r, nxt, h->sigma, h->involved)) != VS_OK) return st;
+    }
   } else {
     if ((st = geometry(h, h->xy, false)) != VS_OK) return st;
     if ((st = build_operators(h, h->xy, nxt, nullptr)) != VS_OK) return st;
@@ -1253,9 +1269,11 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (h->p.near_field) {
     VS_A(dalloc(&h->nb.layer, 30 * L.P));
     VS_A(dalloc(&h->nb.phi, L.moff[L.M]));
-    const int Nu = (int)std::ceil(std::sqrt((double)L.nmax)) * L.nmax;
     VS_A(cudaFuncSetAttribute(k_near_layers, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(6 * (size_t)Nu * sizeof(double))));
+                              (int)near_layers_smem(L.nmax)));
+    if (5 * L.nmax <= NEAR_RBF_SMEM_N)
+      VS_A(cudaFuncSetAttribute(k_near_rbf_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)near_rbf_smem(5 * L.nmax)));
   }
   VS_A(cudaMemsetAsync(h->fired, 0, sizeof(int), h->stream));
   VS_A(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));

@@ -39,6 +39,9 @@ def rel_err_per_vesicle(xs_a, ys_a, xs_b, ys_b):
 # vesicles (and 5e-11..8e-11 at 64 points), spread over all of its modes. The two sides agree in X to
 # about 2e-13 after a step, so sigma is held to 1e-10 where N <= 32 and to 1e-9 where N >= 64.
 SIGMA_TOL, SIGMA_TOL_N64 = 1e-10, 1e-9
+# the same sensitivity per unit of relative position difference: 1.1e-10..6.0e-10 for 1e-13..2e-13, i.e. up
+# to about 3e3 on those vesicles
+SIGMA_PER_X = 5e3
 
 
 def sigma_error(sg, so_list):
@@ -48,11 +51,13 @@ def sigma_error(sg, so_list):
     return float(np.max(np.abs(sg - so)) / np.max(np.abs(so)))
 
 
-def sigma_tolerance(so_list, tol_s=None):
-    """tol_s, or the FP64 tolerance of SIGMA_TOL for the largest vesicle."""
+def sigma_tolerance(so_list, tol_s=None, ex=0.0):
+    """tol_s, or the FP64 tolerance of SIGMA_TOL for the largest vesicle; along a trajectory whose positions
+    differ by ex (relative), at least SIGMA_PER_X * ex (the sensitivity measured on the oracle, rounded up)."""
     if tol_s is not None:
         return tol_s
-    return SIGMA_TOL if max(len(s) for s in so_list) <= 32 else SIGMA_TOL_N64
+    base = SIGMA_TOL if max(len(s) for s in so_list) <= 32 else SIGMA_TOL_N64
+    return max(base, SIGMA_PER_X * ex)
 
 
 def _elementwise(got, ref):

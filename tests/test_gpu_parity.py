@@ -204,7 +204,12 @@ def test_near_field_step_matches_oracle():
         vx, vy = split(g.velocity(), counts)
         ref = np.concatenate(o.velocity)
         got = np.concatenate([np.concatenate([a, b]) for a, b in zip(vx, vy)])
-        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+        # FP32 layer sums and FP32 RBF Cholesky: the FP32 bar of 1e-5 in relative L2, 5e-5 of the largest
+        # velocity at any one point (as at 64 and 128 points)
+        l2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        mx = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        print("near field N=32: velocity relative L2 %.3e, max %.3e" % (l2, mx))
+        assert l2 <= 1e-5 and mx <= 5e-5, (l2, mx)
         _compare(o, g, tol_x=1e-8, tol_s=1e-4)
 
 
@@ -256,8 +261,8 @@ def test_near_field_at_64_and_128_points_matches_oracle(N):
     l2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     mx = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     print("near field N=%d: %d pairs, velocity relative L2 %.3e, max %.3e" % (N, len(o.near_pairs), l2, mx))
-    # the RBF systems are solved in FP32 (Cholesky, condition number about 3e4): the FP32 bar of 1e-5 in
-    # relative L2, and 5e-5 of the largest velocity at any one point
+    # the layer sums and the RBF systems are FP32 (Cholesky, condition number about 3e4): the FP32 bar of
+    # 1e-5 in relative L2, and 5e-5 of the largest velocity at any one point
     assert l2 <= 1e-5 and mx <= 5e-5, (l2, mx)
     _compare(o, g, tol_x=1e-8, tol_s=1e-4)
 
