@@ -42,9 +42,9 @@ FFS_INST_PER_PAIR = 21
 # Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
 FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 # DRAM bytes of one k_farfield_sym launch at 2000 x 64 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# one-pass capture of the bench workload: 3.64 MB read, 195.51 MB written, mostly the per-chunk partial sums
-# that do not stay in L2)
-FFS_DRAM_BYTES = 3.64e6 + 195.51e6
+# one-pass capture of the bench workload with chunks of 16 vesicles: 5.20 MB read, 197.19 MB written, mostly
+# the per-chunk partial sums that do not stay in L2)
+FFS_DRAM_READ, FFS_DRAM_WRITE = 5.20e6, 197.19e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 # learned advection and tension: velocity modes expanded and column modes kept, training epochs
 FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
@@ -608,9 +608,13 @@ def run_gpu(args):
         mhz = clocks.get("sm_mhz") or 1920.0
         peak_issue = ISSUE_LANES_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
         achieved = FFS_INST_PER_PAIR * pairs / (avg_ms * 1e-3) / 1e12
+        # the measured traffic is for chunks of 16 vesicles; its partial-sum writes scale with the chunk count
+        V = fv[2] // args.N if fv[0] < 0 else 16
+        traffic = FFS_DRAM_READ + FFS_DRAM_WRITE * 16.0 / V
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "Tinst/s",
-                "frac": achieved / peak_issue, "traffic": FFS_DRAM_BYTES,
-                "traffic_source": FFS_DRAM_SOURCE,
+                "frac": achieved / peak_issue, "traffic": traffic,
+                "traffic_source": FFS_DRAM_SOURCE + (", writes scaled from 16 to %d vesicles per chunk" % V
+                                                     if V != 16 else ""),
                 "peak_source": "issue: 4 schedulers x 32 lanes x 148 SMs x median SM clock (derived); "
                                "achieved counts 21 instructions per unordered pair (19 FP32 + lg2 + rcp)",
                 "share_of_step": dom_ms / total_prof}

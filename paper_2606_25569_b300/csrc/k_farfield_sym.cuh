@@ -55,7 +55,7 @@ namespace vs {
 #endif
 constexpr int FFS_STEPS_UNROLLED = FFS_UNROLL;  // steps of the 32-step lane rotation unrolled together
 
-constexpr int FFS_V = 16;  // vesicles per chunk
+constexpr int FFS_V = 16;  // vesicles per chunk (uneven point counts; equal N: 8, 16 or 32, autotuned)
 constexpr int FFS_W = 8;   // warps per CTA
 
 struct FfSymArgs {
@@ -86,7 +86,7 @@ struct FfSymTiles {
 
 // Shared memory of one CTA (float4 units): the staged column chunk (64 per segment: each 32-point
 // segment twice) and the column accumulators (32 per segment: sum_x, comp_x, sum_y, comp_y).
-inline size_t ffs_smem_bytes(int RC) { return (size_t)FFS_V * 3 * 32 * RC * sizeof(float4); }
+inline size_t ffs_smem_bytes(int RC, int V) { return (size_t)V * 3 * 32 * RC * sizeof(float4); }
 
 // Segments (of 32 points) of a vesicle of N points in the symmetric kernel.
 __host__ __device__ inline int ffs_segments(int N) { return N <= 32 ? 1 : N <= 64 ? 2 : 4; }
@@ -158,7 +158,8 @@ struct FfsIdx {
 
 // Persistent: each CTA takes tiles of its pair of classes (rows of RR segments, columns of RC) from t.ctr
 // until none are left. blockDim = 32 * FFS_W. EQ: all vesicles have 32 RR = 32 RC points (no padding).
-template <int RR, int RC, bool EQ>
+// V: vesicles per chunk.
+template <int RR, int RC, bool EQ, int V>
 __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_farfield_sym(FfSymArgs a, FfSymTiles t,
                                                              const float4* __restrict__ centre32,
                                                              const float2* __restrict__ h2,
@@ -171,8 +172,8 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
   __shared__ int s_na[FFS_W];          // each warp's row vesicle: points and first point (read after the pair
   __shared__ long long s_ao[FFS_W];    // loops, so that they hold no registers there), and its density sum
   __shared__ float2 s_hga[FFS_W];      // times -ln(2)/2
-  float4* col = ffs_smem;                   // [FFS_V][RC][64]
-  float4* acc = ffs_smem + FFS_V * 2 * NC;  // [FFS_V][NC]
+  float4* col = ffs_smem;               // [V][RC][64]
+  float4* acc = ffs_smem + V * 2 * NC;  // [V][NC]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2: -log|r| = hl2 log2|r|^2
   for (;;) {
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
           const int64_t ao = s_ao[w];
 #pragma unroll
           for (int r = 0; r < RR; ++r) {  // targets of A, source vesicle B
-            if (lane + 32 * r >= na) continue;
+            if (!EQ && lane + 32 * r >= na) continue;
             if (test && mr[r] <= hb.x) {
               ffs_near(a, ao + lane + 32 * r, bv);
             } else {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
           const float2 hga = s_hga[w];
 #pragma unroll
           for (int c = 0; c < RC; ++c) {  // targets of B, source vesicle A
-            if (lane + 32 * c >= nb) continue;
+            if (!EQ && lane + 32 * c >= nb) continue;
             if (test && mc[c] <= ha.x) {
               ffs_near(a, IC::roff(a, bs) + lane + 32 * c, av);
             } else {
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
           const int64_t ao = s_ao[w];
 #pragma unroll
           for (int r = 0; r < RR; ++r)
-            if (lane + 32 * r < na)
+            if (EQ || lane + 32 * r < na)
               a.part[(int64_t)J * a.P + ao + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
         }
       }

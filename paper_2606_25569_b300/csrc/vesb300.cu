@@ -292,6 +292,8 @@ struct vs_mlp {
 constexpr int FFS_NPAIR = 6;
 struct FfSymState {
   bool on = false;
+  int V = FFS_V;        // vesicles per chunk
+  int per_sm = 0;       // persistent CTAs per SM (0: as many as fit)
   bool padded = false;  // some N is not a multiple of 32 or the order is not the identity: k_ffs_pad runs
   int nchunk = 0, npair = 0;
   int rr[FFS_NPAIR] = {}, rc[FFS_NPAIR] = {}, ntile[FFS_NPAIR] = {}, grid[FFS_NPAIR] = {};
@@ -586,38 +588,55 @@ FfSymArgs ffs_args(const FfSymState& f, const Layout& L, int near_mask, const So
                    f.vid, f.poff, f.roff, f.nreal, f.chunk, f.padded ? f.psrc : B.src};
 }
 
-template <int RR, int RC, bool EQ>
-cudaError_t ffs_prepare(int* grid) {
-  const size_t smem = ffs_smem_bytes(RC);
-  cudaError_t e = cudaFuncSetAttribute(k_farfield_sym<RR, RC, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Persistent grid of one instantiation: CTAs per SM as many as fit, or per_sm when smaller.
+template <int RR, int RC, bool EQ, int V>
+cudaError_t ffs_prepare(int per_sm_want, int* grid) {
+  const size_t smem = ffs_smem_bytes(RC, V);
+  cudaError_t e = cudaFuncSetAttribute(k_farfield_sym<RR, RC, EQ, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_farfield_sym<RR, RC, EQ>, 32 * FFS_W, smem)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_farfield_sym<RR, RC, EQ, V>, 32 * FFS_W, smem)) !=
       cudaSuccess)
     return e;
-  *grid = sms * std::max(per_sm, 1);
+  per_sm = std::max(per_sm, 1);
+  if (per_sm_want > 0) per_sm = std::min(per_sm, per_sm_want);
+  *grid = sms * per_sm;
   return cudaSuccess;
 }
 
+template <int RR, int RC, bool EQ>
+cudaError_t ffs_prepare_v(int V, int per_sm, int* grid) {
+  return V == 8 ? ffs_prepare<RR, RC, EQ, 8>(per_sm, grid)
+                : V == 32 ? ffs_prepare<RR, RC, EQ, 32>(per_sm, grid) : ffs_prepare<RR, RC, EQ, 16>(per_sm, grid);
+}
+
 // The instantiated pairs of classes (row segments >= column segments); eq: equal N of 32, 64 or 128 in index
-// order (no padding, identity order).
-cudaError_t ffs_prepare(int rr, int rc, bool eq, int* grid) {
+// order (no padding, identity order), chunks of V = 8, 16 or 32 vesicles; otherwise V = 16.
+cudaError_t ffs_prepare(int rr, int rc, bool eq, int V, int per_sm, int* grid) {
+  if (eq) {
+    switch (rr) {
+      case 4: return ffs_prepare_v<4, 4, true>(V, per_sm, grid);
+      case 2: return ffs_prepare_v<2, 2, true>(V, per_sm, grid);
+      default: return ffs_prepare_v<1, 1, true>(V, per_sm, grid);
+    }
+  }
   switch (rr * 8 + rc) {
-    case 4 * 8 + 4: return eq ? ffs_prepare<4, 4, true>(grid) : ffs_prepare<4, 4, false>(grid);
-    case 4 * 8 + 2: return ffs_prepare<4, 2, false>(grid);
-    case 4 * 8 + 1: return ffs_prepare<4, 1, false>(grid);
-    case 2 * 8 + 2: return eq ? ffs_prepare<2, 2, true>(grid) : ffs_prepare<2, 2, false>(grid);
-    case 2 * 8 + 1: return ffs_prepare<2, 1, false>(grid);
-    default: return eq ? ffs_prepare<1, 1, true>(grid) : ffs_prepare<1, 1, false>(grid);
+    case 4 * 8 + 4: return ffs_prepare<4, 4, false, FFS_V>(per_sm, grid);
+    case 4 * 8 + 2: return ffs_prepare<4, 2, false, FFS_V>(per_sm, grid);
+    case 4 * 8 + 1: return ffs_prepare<4, 1, false, FFS_V>(per_sm, grid);
+    case 2 * 8 + 2: return ffs_prepare<2, 2, false, FFS_V>(per_sm, grid);
+    case 2 * 8 + 1: return ffs_prepare<2, 1, false, FFS_V>(per_sm, grid);
+    default: return ffs_prepare<1, 1, false, FFS_V>(per_sm, grid);
   }
 }
 
-// Sets f up for the layout when `wanted` and the layout is eligible; leaves f.on false otherwise.
-cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t st) {
-  f.on = false;
+// Sets f up for the layout when `wanted` and the layout is eligible; leaves f.on false otherwise. V: vesicles
+// per chunk (equal N only; 16 otherwise), per_sm: persistent CTAs per SM (0: as many as fit).
+cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t st, int V = FFS_V, int per_sm = 0) {
+  f.release();
   if (!wanted || L.M < 2) return cudaSuccess;
   // symmetric order: classes of 4, 2, 1 segments, vesicle index ascending inside a class
   std::vector<int> vid;
@@ -637,11 +656,12 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
     pp += 32 * cls[s];
     if (v != s || L.N[v] != 32 * cls[s]) padded = true;
   }
+  if (padded) V = FFS_V;
   std::vector<int2> chunk;
   std::vector<int> ccls;
   for (int s = 0; s < L.M;) {
     int n = 0;
-    while (s + n < L.M && n < FFS_V && cls[s + n] == cls[s]) ++n;
+    while (s + n < L.M && n < V && cls[s + n] == cls[s]) ++n;
     chunk.push_back(make_int2(s, n));
     ccls.push_back(cls[s]);
     s += n;
@@ -669,7 +689,7 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
     f.tile_off[npair] = (int64_t)t0;
     f.ntile[npair] = (int)(tiles.size() - t0);
     int grid = 0;
-    if ((e = ffs_prepare(pr[0], pr[1], !padded, &grid)) != cudaSuccess) return e;
+    if ((e = ffs_prepare(pr[0], pr[1], !padded, V, per_sm, &grid)) != cudaSuccess) return e;
     f.grid[npair] = std::min(grid, f.ntile[npair]);
     ++npair;
   }
@@ -687,6 +707,8 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
   if (padded) VS_TRY(dalloc(&f.psrc, pp));
 #undef VS_TRY
   f.padded = padded;
+  f.V = V;
+  f.per_sm = per_sm;
   f.nchunk = nchunk;
   f.npair = npair;
   f.on = true;
@@ -701,25 +723,30 @@ void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cu
   if (f.padded) k_ffs_pad<<<a.M, 128, 0, st>>>(a, B.src, f.psrc);
   for (int k = 0; k < f.npair; ++k) {
     const FfSymTiles t{f.tiles + f.tile_off[k], f.ntile[k], f.ctr + k};
-    const size_t smem = ffs_smem_bytes(f.rc[k]);
+    const size_t smem = ffs_smem_bytes(f.rc[k], f.V);
     const int g = f.grid[k], nt = 32 * FFS_W;
     const float4* c32 = B.centre32;
     const float2 *h2 = B.h2, *gs = B.gsum;
     if (!f.padded) {  // equal N of 32, 64 or 128: a single pair of classes
+#define VS_FFS_EQ(R)                                                                                          \
+  (f.V == 8 ? k_farfield_sym<R, R, true, 8><<<g, nt, smem, st>>>(a, t, c32, h2, gs)                           \
+            : f.V == 32 ? k_farfield_sym<R, R, true, 32><<<g, nt, smem, st>>>(a, t, c32, h2, gs)              \
+                        : k_farfield_sym<R, R, true, 16><<<g, nt, smem, st>>>(a, t, c32, h2, gs))
       switch (f.rr[k]) {
-        case 4: k_farfield_sym<4, 4, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-        case 2: k_farfield_sym<2, 2, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-        default: k_farfield_sym<1, 1, true><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+        case 4: VS_FFS_EQ(4); break;
+        case 2: VS_FFS_EQ(2); break;
+        default: VS_FFS_EQ(1); break;
       }
+#undef VS_FFS_EQ
       continue;
     }
     switch (f.rr[k] * 8 + f.rc[k]) {
-      case 4 * 8 + 4: k_farfield_sym<4, 4, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-      case 4 * 8 + 2: k_farfield_sym<4, 2, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-      case 4 * 8 + 1: k_farfield_sym<4, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-      case 2 * 8 + 2: k_farfield_sym<2, 2, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-      case 2 * 8 + 1: k_farfield_sym<2, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
-      default: k_farfield_sym<1, 1, false><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 4 * 8 + 4: k_farfield_sym<4, 4, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 4 * 8 + 2: k_farfield_sym<4, 2, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 4 * 8 + 1: k_farfield_sym<4, 1, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 2 * 8 + 2: k_farfield_sym<2, 2, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      case 2 * 8 + 1: k_farfield_sym<2, 1, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
+      default: k_farfield_sym<1, 1, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
     }
   }
 }
@@ -763,15 +790,74 @@ std::map<std::string, int>& tune_cache() {
   return c;
 }
 
+// Autotuner of the symmetric far field (equal point counts): chunk size V (8, 16, 32 vesicles) and persistent
+// CTAs per SM (as many as fit, or 2), each timed on the suspension's own sources (best of two launches after
+// one warm-up); cached as the per-target kernel's shapes are, under a key of its own.
+vs_status tune_symmetric(vs_suspension* h, const char* devname) {
+  const Layout& L = h->L;
+  char key[512];
+  snprintf(key, sizeof key, "sym|%s|M=%d|P=%lld|near=%d", devname, L.M, (long long)L.P, h->p.near_field ? 1 : 0);
+  for (char* c = key; *c; ++c)
+    if (*c == ' ') *c = '_';
+  auto& cache = tune_cache();
+  const char* path = std::getenv("VS_TUNE_CACHE");
+  if (!cache.count(key) && path) {
+    if (FILE* f = std::fopen(path, "r")) {
+      char k[512];
+      int var = 0;
+      while (std::fscanf(f, "%511s %d", k, &var) == 2)
+        if (var >= 0) cache[k] = var;
+      std::fclose(f);
+    }
+  }
+  const bool want = true;
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    VS_CK(h, ffs_setup(h->ffs, L, want, h->stream, it->second / 10, it->second % 10), "autotune");
+    return VS_OK;
+  }
+  cudaEvent_t e0, e1;
+  VS_CK(h, cudaEventCreate(&e0), "autotune");
+  VS_CK(h, cudaEventCreate(&e1), "autotune");
+  int best = FFS_V * 10;
+  float best_ms = 1e30f;
+  for (int V : {8, 16, 32})
+    for (int per_sm : {0, 2}) {
+      VS_CK(h, ffs_setup(h->ffs, L, want, h->stream, V, per_sm), "autotune");
+      const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
+      ffs_launch(h->ffs, fa, h->B, h->stream);
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        ffs_launch(h->ffs, fa, h->B, h->stream);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = V * 10 + per_sm; }
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  VS_CK(h, cudaGetLastError(), "autotune");
+  VS_CK(h, ffs_setup(h->ffs, L, want, h->stream, best / 10, best % 10), "autotune");
+  cache[key] = best;
+  if (path)
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d\n", key, best);
+      std::fclose(f);
+    }
+  return VS_OK;
+}
+
 vs_status tune_far_field(vs_suspension* h) {
   const Layout& L = h->L;
-  if (L.M < 2 || h->ffs.on ||
-      (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE)))
+  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE)))
     return VS_OK;
   int dev = 0;
   VS_CK(h, cudaGetDevice(&dev), "autotune");
   cudaDeviceProp prop;
   VS_CK(h, cudaGetDeviceProperties(&prop, dev), "autotune");
+  if (h->ffs.on) return h->ffs.padded ? VS_OK : tune_symmetric(h, prop.name);
   char key[512];
   snprintf(key, sizeof key, "%s|M=%d|P=%lld|near=%d", prop.name, L.M, (long long)L.P, h->p.near_field ? 1 : 0);
   for (char* c = key; *c; ++c)
@@ -1423,7 +1509,7 @@ vs_status vs_farfield_variant(vs_suspension* h, int32_t set, int32_t* index, int
   if (h->ffs.on) {
     if (index) *index = -1;
     if (threads) *threads = 32 * FFS_W;
-    if (chunk) *chunk = FFS_V * h->L.nmax;
+    if (chunk) *chunk = h->ffs.V * h->L.nmax;
     return VS_OK;
   }
   if (index) *index = h->ff_variant;
