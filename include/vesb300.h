@@ -39,7 +39,7 @@ typedef enum {
   VS_ERR_INVALID_ARG = 1,   /* bad sizes, layout, parameters or a null pointer */
   VS_ERR_CUDA = 2,          /* a CUDA call failed (no device, launch error) */
   VS_ERR_NOMEM = 3,         /* device allocation failed */
-  VS_ERR_NOT_CONVERGED = 4, /* area/length correction did not converge */
+  VS_ERR_NOT_CONVERGED = 4, /* area/length correction, or the implicit step's GMRES, did not converge */
   VS_ERR_UNSTABLE = 5,      /* non-finite state or a singular per-vesicle system */
   VS_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
   VS_ERR_NO_NETWORK = 7     /* reserved for the learned (hybrid) path */
@@ -94,7 +94,9 @@ typedef struct {
   double mu;         /* viscosity, > 0 */
   double dt;         /* time step, > 0 */
   double corr_tol;   /* relative area/length error that triggers the correction (Sec. 4.3: 0.01) */
-  int32_t mode;      /* 0: plain boundary-integral step, 1: hybrid (learned relaxation, vs_set_network) */
+  int32_t mode;      /* 0: plain boundary-integral step, 1: hybrid (learned relaxation, vs_set_network),
+                        2: fully implicit step (Sec. 2.2.3, Eq. time_step_sc1) solved by GMRES (vs_set_gmres);
+                        its operators are FP64 whatever VS_FLAG_DIRECT_FP64 says */
   int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
   int32_t use_graph; /* 1: replay each step from a captured CUDA graph (needs a non-NULL stream and
                         profiling off; otherwise steps are launched one kernel at a time) */
@@ -131,6 +133,31 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
  * Asynchronous: returns once the work is enqueued.
  */
 vs_status vs_step(vs_suspension* s, int32_t nsteps);
+
+/*
+ * Fully implicit step (mode 2; Sec. 2.2.3, Eq. time_step_sc1). With every operator at X^n and the
+ * density f = -kappa D_s^4 X^{n+1} + (sigma^{n+1} X_s)_s, the velocity U = S f + far field of f from the
+ * other vesicles (+ the near-field correction of f when near_field is set) satisfies
+ *   X^{n+1} - dt U = X^n + dt u_inf(X^n),   P U = -P u_inf(X^n)
+ * for all vesicles at once. vs_step solves it by restarted GMRES (right preconditioning with the exact
+ * per-vesicle solve of the same system without the other vesicles; two-pass classical Gram-Schmidt),
+ * starting from (X^n, sigma^n), until ||b - A z|| <= tol ||b|| by GMRES's own residual estimate; then
+ * redistributes X^{n+1} (Sec. 4.2; sigma^{n+1} evaluated at the new parameters by its trigonometric
+ * interpolant) and applies the area/length correction (Sec. 4.3). The far field of each product is the
+ * one the flags select, so with the FP32 far field the attainable residual is limited by its rounding.
+ * Each GMRES iteration reads one Hessenberg column on the host (the stream is synchronised), so vs_step
+ * returns after the work of mode-2 steps has finished and never uses CUDA graphs. vs_get_velocity is not
+ * defined in mode 2.
+ *  vs_set_gmres: tol > 0 (default 1e-10), 1 <= restart <= VS_GMRES_MAX_RESTART (default 30) Krylov vectors
+ *    per cycle, max_iter >= 1 (default 300) iterations per step; vs_step returns VS_ERR_NOT_CONVERGED
+ *    when a step needs more (the state is then not advanced past the failing solve). Device memory:
+ *    (restart + 6) * 3 P doubles, allocated by the first mode-2 step.
+ *  vs_gmres_stats: iterations and relative residual estimate of the last step, iterations over all
+ *    steps; any pointer may be NULL.
+ */
+#define VS_GMRES_MAX_RESTART 200
+vs_status vs_set_gmres(vs_suspension* s, double tol, int32_t restart, int32_t max_iter);
+vs_status vs_gmres_stats(const vs_suspension* s, int32_t* last_iters, double* last_residual, int64_t* total_iters);
 
 /* Wait for the handle's stream and report device-side errors of earlier steps. */
 vs_status vs_sync(vs_suspension* s);

@@ -26,6 +26,8 @@ FUNCTIONS = {
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "vs_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "vs_set_gmres": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
+    "vs_gmres_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_get_positions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_get_tension": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -232,6 +234,17 @@ class Suspension:
         self._net = net  # the library borrows it
         self._check(lib().vs_set_network(self._h, int(which), net._h if net is not None else None, float(out_scale),
                                          int(filter_kmax)))
+
+    def set_gmres(self, tol=1e-10, restart=30, max_iter=300):
+        """GMRES settings of the fully implicit step (mode 2, vs_set_gmres)."""
+        self._check(lib().vs_set_gmres(self._h, float(tol), int(restart), int(max_iter)))
+
+    def gmres_stats(self):
+        """(iterations of the last step, its relative residual estimate, iterations over all steps)."""
+        it, tot = ctypes.c_int32(), ctypes.c_int64()
+        res = ctypes.c_double()
+        self._check(lib().vs_gmres_stats(self._h, ctypes.byref(it), ctypes.byref(res), ctypes.byref(tot)))
+        return it.value, res.value, tot.value
 
     def set_flow_networks(self, adv, ten, Kf, Kout):
         """Learned advection and tension (vs_set_flow_networks); None, None removes them."""

@@ -19,6 +19,7 @@
 #include "k_farfield_sym.cuh"
 #include "k_farfield_loc.cuh"
 #include "k_geometry.cuh"
+#include "k_implicit.cuh"
 #include "k_mlp.cuh"
 #include "k_mp.cuh"
 #include "k_near.cuh"
@@ -313,6 +314,32 @@ struct FfSymState {
   }
 };
 
+// Restarted GMRES of the fully implicit step (mode 2): settings, device work vectors and statistics.
+struct GmresState {
+  double tol = 1e-10;        // relative residual ||b - A z|| / ||b|| to reach
+  int restart = 30;          // Krylov vectors per cycle
+  int max_iter = 300;        // iterations (matrix-vector products in cycles) per step
+  int64_t n = 0;             // 3 P
+  int G = 0;                 // CTAs of the vector kernels
+  int alloc_restart = 0;
+  double *V = nullptr;       // (restart + 1) x n Krylov basis
+  double *w = nullptr, *z = nullptr, *b = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double *part = nullptr;    // (restart + 1) x G partial dot products
+  double *hd = nullptr;      // Hessenberg column (restart + 2), then the first pass's coefficients
+  double *hd2 = nullptr;     // second Gram-Schmidt pass's coefficients / the update coefficients y
+  double *hh = nullptr;      // pinned host copy of a Hessenberg column (restart + 2)
+  int last_iters = 0;
+  double last_res = 0.0;
+  int64_t total_iters = 0;
+  void release() {
+    cudaFree(V); cudaFree(w); cudaFree(z); cudaFree(b); cudaFree(t1); cudaFree(t2); cudaFree(part);
+    cudaFree(hd); cudaFree(hd2);
+    if (hh) cudaFreeHost(hh);
+    V = w = z = b = t1 = t2 = part = hd = hd2 = hh = nullptr;
+    alloc_restart = 0;
+  }
+};
+
 struct vs_suspension {
   Layout L;
   DevLayout D;
@@ -348,6 +375,7 @@ struct vs_suspension {
   int64_t graph_launches[4] = {0, 0, 0, 0};
   int ff_variant = 0;                              // FP32 far-field launch shape (FF_VARIANTS)
   FfSymState ffs;                                  // symmetric FP32 far field, used when ffs.on
+  GmresState gm;                                   // fully implicit step (mode 2)
   std::string msg;
 };
 
@@ -497,7 +525,9 @@ inline bool mp_wide(const vs_suspension* h) { return h->L.nmax > 64 || h->L.M < 
   } while (0)
 
 // Mixed precision (default): FP32 operator products and factorisations refined in FP64.
-inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
+// FP32 factorisations with FP64 refinement, unless FP64 operators are asked for or the step is the fully
+// implicit one (its GMRES preconditioner uses the FP64 LU factors)
+inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64) && h->p.mode != 2; }
 
 // S, T, L at slot s for the geometry currently in the SourceBufs, then LU of L.
 vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* active) {
@@ -912,7 +942,24 @@ vs_status tune_far_field(vs_suspension* h) {
 vs_status mlp_forward(vs_mlp* h, const float* x, int batch, bool out_map);
 const float* mlp_output(const vs_mlp* h);
 
-// Exact relaxation (Eq. relaxation_disc) of the points xs into xo, operators built in slot s.
+// FP64 relaxation matrices with the operators of slot s and the geometry in the SourceBufs: D4, B,
+// W = L^{-1} P B and the LU of A = I - dt (B - T W) (Eq. relaxation_disc).
+vs_status relax_matrix_fp64(vs_suspension* h, int s) {
+  const int M = h->L.M, n = h->L.nmax;
+  const VesIndex vi = h->D.vi();
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
+  VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 0, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 1, h->p.kappa_b}, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
+  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<double><<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
+  VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
+  launch_lu(h, "k_lu<A>", LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, 2 * n, nullptr);
+  VS_CK(h, cudaGetLastError(), "relaxation matrix");
+  return VS_OK;
+}
+
 // Exact relaxation (Eq. relaxation_disc) of xs into xo with the operators at slot s; with active non-null
 // only the vesicles with active[v] != 0 are processed and written.
 vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s, const int* active = nullptr) {
@@ -957,14 +1004,8 @@ vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s, con
     VS_CK(h, cudaGetLastError(), "relaxation");
     return VS_OK;
   }
-  VS_LAUNCH(h, "k_bgemm<OpD2>", k_bgemm<OpD2><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD2{c}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpD4>", k_bgemm<OpD4><<<gemm_grid(n, n, M), 256, 0, h->stream>>>(OpD4{c}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 0, h->p.kappa_b}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpB>", k_bgemm<OpB><<<gemm_grid(2 * n, n, M), 256, 0, h->stream>>>(OpB{c, s, 1, h->p.kappa_b}, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpPB>", k_bgemm<OpPB><<<gemm_grid(n, 2 * n, M), 256, 0, h->stream>>>(OpPB{c}, nullptr));
-  VS_LAUNCH(h, "k_lu_solve_cols", k_lu_solve_cols<double><<<M, 2 * NMAX, 0, h->stream>>>(vi, h->scratch, s, h->piv, nullptr));
-  VS_LAUNCH(h, "k_bgemm<OpA>", k_bgemm<OpA><<<gemm_grid(2 * n, 2 * n, M), 256, 0, h->stream>>>(OpA{c, s, h->p.dt}, nullptr));
-  launch_lu(h, "k_lu<A>", LuGeo{vi, h->scratch, MatLayout::A, 2, 0, h->piv, 2}, 2 * n, nullptr);
+  vs_status st2 = relax_matrix_fp64(h, s);
+  if (st2 != VS_OK) return st2;
   VS_LAUNCH(h, "k_relax_solve", k_relax_solve<<<M, 256, 0, h->stream>>>(vi, xs, h->scratch, h->piv, xo, active));
   VS_CK(h, cudaGetLastError(), "relaxation");
   return VS_OK;
@@ -1219,6 +1260,195 @@ vs_status step_once(vs_suspension* h) {
   return VS_OK;
 }
 
+// ---- Fully implicit step (mode 2; Sec. 2.2.3, Eq. time_step_sc1), solved by restarted GMRES with the
+// block-diagonal (per-vesicle) preconditioner of k_implicit.cuh, right-preconditioned: the Krylov space is
+// built for A M^{-1} and the solution is z = z0 + M^{-1} V y. Gram-Schmidt is classical, applied twice
+// (CGS2) with batched dot products; the small Hessenberg least-squares problem (Givens rotations) runs on
+// the host, which reads one column per iteration.
+
+vs_status gmres_alloc(vs_suspension* h) {
+  GmresState& g = h->gm;
+  const int64_t n = 3 * h->L.P;
+  if (g.V && g.alloc_restart == g.restart && g.n == n) return VS_OK;
+  g.release();
+  g.n = n;
+  g.G = (int)std::min<int64_t>((n + GM_THREADS - 1) / GM_THREADS, 4 * 148);
+  const int m = g.restart;
+  VS_CK(h, dalloc(&g.V, (int64_t)(m + 1) * n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.w, n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.z, n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.b, n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.t1, n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.t2, n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.part, (int64_t)(m + 2) * g.G), "GMRES buffers");
+  VS_CK(h, dalloc(&g.hd, m + 2), "GMRES buffers");
+  VS_CK(h, dalloc(&g.hd2, m + 2), "GMRES buffers");
+  VS_CK(h, cudaMallocHost(&g.hh, (m + 2) * sizeof(double)), "GMRES buffers");
+  g.alloc_restart = m;
+  return VS_OK;
+}
+
+// q = A p: the density of p, its far field (and near-field correction) from the other vesicles, the self
+// single layer, then both lines of the system (operators of slot s at X^n).
+vs_status imp_matvec(vs_suspension* h, int s, const double* p, double* q) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  VS_LAUNCH(h, "k_imp_density", k_imp_density<<<L.M, NMAX, 0, h->stream>>>(vi, p, h->B.pg(), h->D.tab, h->p.kappa_b,
+                                                                           h->p.mu, h->B.f, h->B.g64, h->B.src,
+                                                                           h->B.gsum, h->u));
+  vs_status st;
+  if ((st = far_field(h)) != VS_OK) return st;
+  if (h->p.near_field && L.M > 1 && (st = near_field(h, s)) != VS_OK) return st;
+  VS_LAUNCH(h, "k_imp_apply", k_imp_apply<<<L.M, 256, 0, h->stream>>>(vi, p, h->B.f, h->u, h->B.pg(), h->D.tab,
+                                                                       h->scratch, s, h->p.dt, q));
+  VS_CK(h, cudaGetLastError(), "implicit matrix-vector product");
+  return VS_OK;
+}
+
+vs_status imp_precond(vs_suspension* h, int s, const double* r, double* out) {
+  VS_LAUNCH(h, "k_imp_precond", k_imp_precond<<<h->L.M, 256, 0, h->stream>>>(h->D.vi(), r, h->scratch, h->piv, s,
+                                                                             h->p.dt, out));
+  VS_CK(h, cudaGetLastError(), "implicit preconditioner");
+  return VS_OK;
+}
+
+// out[0..J) = <V_j, x> (norm_slot < 0), or out[norm_slot] = ||x|| (J = 1, V = x); with acc non-null the
+// results are also added to acc.
+vs_status gm_dots(vs_suspension* h, const double* V, int J, const double* x, double* out, double* acc,
+                  int norm_slot) {
+  GmresState& g = h->gm;
+  VS_LAUNCH(h, "k_gm_dots", k_gm_dots<<<g.G, GM_THREADS, 0, h->stream>>>(V, g.n, J, x, g.part));
+  VS_LAUNCH(h, "k_gm_reduce", k_gm_reduce<<<J, 32, 0, h->stream>>>(g.part, g.G, J, out, acc, norm_slot));
+  VS_CK(h, cudaGetLastError(), "GMRES dot products");
+  return VS_OK;
+}
+
+vs_status read_doubles(vs_suspension* h, const double* d, int n) {
+  VS_CK(h, cudaMemcpyAsync(h->gm.hh, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "GMRES readback");
+  VS_CK(h, cudaStreamSynchronize(h->stream), "GMRES readback");
+  return VS_OK;
+}
+
+// Solves A z = b for z (starting from the z in the state) to gm.tol; operators at slot s.
+vs_status gmres_solve(vs_suspension* h, int s) {
+  GmresState& g = h->gm;
+  const int m = g.restart;
+  const int64_t n = g.n;
+  vs_status st;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  // ||b||
+  if ((st = gm_dots(h, g.b, 1, g.b, g.hd, nullptr, 0)) != VS_OK) return st;
+  if ((st = read_doubles(h, g.hd, 1)) != VS_OK) return st;
+  const double bnorm = g.hh[0];
+  const double target = g.tol * (bnorm > 0.0 ? bnorm : 1.0);
+  int iters = 0;
+  double res = 0.0;
+  for (;;) {
+    // r = b - A z into V_0 (unnormalised), beta = ||r||
+    if ((st = imp_matvec(h, s, g.z, g.t1)) != VS_OK) return st;
+    VS_LAUNCH(h, "k_gm_sub", k_gm_sub<<<g.G, GM_THREADS, 0, h->stream>>>(g.b, g.t1, n, g.w));
+    if ((st = gm_dots(h, g.w, 1, g.w, g.hd, nullptr, 0)) != VS_OK) return st;
+    if ((st = read_doubles(h, g.hd, 1)) != VS_OK) return st;
+    const double beta = g.hh[0];
+    res = beta;
+    if (!std::isfinite(beta)) { h->msg = "non-finite GMRES residual"; return VS_ERR_UNSTABLE; }
+    if (beta <= target) break;
+    if (iters >= g.max_iter) break;
+    VS_LAUNCH(h, "k_gm_scale", k_gm_scale<<<g.G, GM_THREADS, 0, h->stream>>>(g.w, n, g.hd, g.V));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    bool done = false;
+    for (int j = 0; j < m && iters < g.max_iter; ++j) {
+      double* vj = g.V + (int64_t)j * n;
+      double* vn = g.V + (int64_t)(j + 1) * n;
+      if ((st = imp_precond(h, s, vj, g.t2)) != VS_OK) return st;
+      if ((st = imp_matvec(h, s, g.t2, g.w)) != VS_OK) return st;
+      // CGS2: h = V^T w, w -= V h, h2 = V^T w, w -= V h2, h += h2
+      if ((st = gm_dots(h, g.V, j + 1, g.w, g.hd, nullptr, -1)) != VS_OK) return st;
+      VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.V, n, j + 1, g.hd, -1.0, g.w));
+      if ((st = gm_dots(h, g.V, j + 1, g.w, g.hd2, g.hd, -1)) != VS_OK) return st;
+      VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.V, n, j + 1, g.hd2, -1.0, g.w));
+      if ((st = gm_dots(h, g.w, 1, g.w, g.hd, nullptr, j + 1)) != VS_OK) return st;
+      VS_LAUNCH(h, "k_gm_scale", k_gm_scale<<<g.G, GM_THREADS, 0, h->stream>>>(g.w, n, g.hd + j + 1, vn));
+      if ((st = read_doubles(h, g.hd, j + 2)) != VS_OK) return st;
+      ++iters;
+      k = j + 1;
+      // Givens rotations on column j
+      double* col = H.data() + (size_t)j * (m + 1);
+      for (int i = 0; i <= j + 1; ++i) col[i] = g.hh[i];
+      for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = col[j], b = col[j + 1];
+      const double r = std::hypot(a, b);
+      cs[j] = r > 0.0 ? a / r : 1.0;
+      sn[j] = r > 0.0 ? b / r : 0.0;
+      col[j] = r;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      res = std::fabs(gv[j + 1]);
+      if (!std::isfinite(res)) { h->msg = "non-finite GMRES residual"; return VS_ERR_UNSTABLE; }
+      if (res <= target || g.hh[j + 1] == 0.0) { done = true; break; }
+    }
+    // y = R^{-1} g (upper triangular k x k), z += M^{-1} V y
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int c = i + 1; c < k; ++c) acc -= H[(size_t)c * (m + 1) + i] * y[c];
+      const double d = H[(size_t)i * (m + 1) + i];
+      y[i] = d != 0.0 ? acc / d : 0.0;
+    }
+    for (int i = 0; i < k; ++i) g.hh[i] = y[i];
+    VS_CK(h, cudaMemcpyAsync(g.hd2, g.hh, k * sizeof(double), cudaMemcpyHostToDevice, h->stream), "GMRES update");
+    VS_CK(h, cudaMemsetAsync(g.t1, 0, n * sizeof(double), h->stream), "GMRES update");
+    VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.V, n, k, g.hd2, 1.0, g.t1));
+    if ((st = imp_precond(h, s, g.t1, g.t2)) != VS_OK) return st;
+    VS_LAUNCH(h, "k_gm_add", k_gm_add<<<g.G, GM_THREADS, 0, h->stream>>>(g.t2, n, g.z));
+    VS_CK(h, cudaGetLastError(), "GMRES update");
+    // the host buffer is reused by the next readback only after this copy has run
+    VS_CK(h, cudaStreamSynchronize(h->stream), "GMRES update");
+    if (done) break;
+  }
+  g.last_iters = iters;
+  g.last_res = res / (bnorm > 0.0 ? bnorm : 1.0);
+  g.total_iters += iters;
+  if (res > target) {
+    h->msg = "GMRES did not reach its tolerance within max_iter iterations";
+    return VS_ERR_NOT_CONVERGED;
+  }
+  return VS_OK;
+}
+
+vs_status step_implicit(vs_suspension* h) {
+  const Layout& L = h->L;
+  const VesIndex vi = h->D.vi();
+  const int s = 0;
+  vs_status st;
+  if ((st = gmres_alloc(h)) != VS_OK) return st;
+  GmresState& g = h->gm;
+  // geometry, centres and sources at X^n; every operator at X^n (Eq. time_step_sc1 discretises them there)
+  if ((st = geometry(h, h->xy, true)) != VS_OK) return st;
+  if ((st = build_operators(h, h->xy, s, nullptr)) != VS_OK) return st;
+  if ((st = relax_matrix_fp64(h, s)) != VS_OK) return st;
+  VS_LAUNCH(h, "k_imp_rhs", k_imp_rhs<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->B.pg(), h->D.tab, flow_dev(h->flow),
+                                                                   h->p.dt, g.b));
+  VS_LAUNCH(h, "k_imp_pack", k_imp_pack<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->sigma, g.z));
+  VS_CK(h, cudaGetLastError(), "implicit step");
+  if ((st = gmres_solve(h, s)) != VS_OK) return st;
+  // X^{n+1}, sigma^{n+1}; redistribution (sigma carried by the interpolant) and area/length correction
+  VS_LAUNCH(h, "k_imp_unpack", k_imp_unpack<<<L.M, NMAX, 0, h->stream>>>(vi, g.z, h->xy_next, h->u));
+  VS_LAUNCH(h, "k_redistribute", k_redistribute<<<L.M, 256, 0, h->stream>>>(vi, h->xy_next, h->u, h->D.tab, h->xy, h->u_r));
+  VS_LAUNCH(h, "k_imp_sigma", k_imp_sigma<<<L.M, NMAX, 0, h->stream>>>(vi, h->u_r, h->sigma));
+  VS_CK(h, cudaGetLastError(), "implicit step");
+  if ((st = correction(h)) != VS_OK) return st;
+  h->cur = 0;
+  h->steps += 1;
+  return VS_OK;
+}
+
 vs_status read_err(vs_suspension* h) {
   VS_CK(h, cudaStreamSynchronize(h->stream), "synchronize");
   unsigned e = 0;
@@ -1273,7 +1503,7 @@ bool params_ok(const vs_params* p, const vs_flow* f, std::string& msg) {
     msg = "kappa_b, mu, dt must be positive and corr_tol non-negative";
     return false;
   }
-  if (p->mode != 0 && p->mode != 1) { msg = "mode must be 0 (plain) or 1 (hybrid)"; return false; }
+  if (p->mode < 0 || p->mode > 2) { msg = "mode must be 0 (plain), 1 (hybrid) or 2 (fully implicit)"; return false; }
   if (p->exact_every < 0) { msg = "exact_every must be >= 0"; return false; }
   if (!(p->exact_gap >= 0.0) || !std::isfinite(p->exact_gap)) { msg = "exact_gap must be finite and >= 0"; return false; }
   if (f->kind < 0 || f->kind > 3) { msg = "unknown flow kind"; return false; }
@@ -1292,6 +1522,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
   h->ffs.release();
+  h->gm.release();
 }
 
 thread_local std::string g_create_msg;
@@ -1397,11 +1628,33 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
 
 vs_status vs_step(vs_suspension* h, int32_t nsteps) {
   if (!h || nsteps < 0) return VS_ERR_INVALID_ARG;
-  const bool graphs = h->p.use_graph && h->stream != nullptr && !h->prof.on;
+  // the implicit step reads GMRES's residual on the host every iteration: never captured in a graph
+  const bool implicit = h->p.mode == 2;
+  const bool graphs = !implicit && h->p.use_graph && h->stream != nullptr && !h->prof.on;
   for (int32_t k = 0; k < nsteps; ++k) {
-    const vs_status st = graphs ? step_graph(h) : step_once(h);
+    const vs_status st = implicit ? step_implicit(h) : graphs ? step_graph(h) : step_once(h);
     if (st != VS_OK) return st;
   }
+  return VS_OK;
+}
+
+vs_status vs_set_gmres(vs_suspension* h, double tol, int32_t restart, int32_t max_iter) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  if (!(tol > 0.0) || !std::isfinite(tol) || restart < 1 || restart > VS_GMRES_MAX_RESTART || max_iter < 1) {
+    h->msg = "GMRES needs tol > 0, 1 <= restart <= VS_GMRES_MAX_RESTART and max_iter >= 1";
+    return VS_ERR_INVALID_ARG;
+  }
+  h->gm.tol = tol;
+  h->gm.restart = restart;
+  h->gm.max_iter = max_iter;
+  return VS_OK;
+}
+
+vs_status vs_gmres_stats(const vs_suspension* h, int32_t* last_iters, double* last_residual, int64_t* total_iters) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  if (last_iters) *last_iters = h->gm.last_iters;
+  if (last_residual) *last_residual = h->gm.last_res;
+  if (total_iters) *total_iters = h->gm.total_iters;
   return VS_OK;
 }
 
