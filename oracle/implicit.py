@@ -15,6 +15,11 @@ system is solved directly here (numpy), where the paper uses preconditioned GMRE
 After the solve the step continues as the plain one: redistribution (Sec. 4.2) with sigma carried to the
 new points by its trigonometric interpolant, then the area/length correction (Sec. 4.3).
 
+With the near field on, the far-field sum excludes the (target, source vesicle) pairs of the near rule
+(oracle.farfield) and the near-field correction of the density (oracle.nearfield, linear in it) is added
+to U, as U_near^{n+1} of the printed equation; its matrix is assembled column by column from unit
+densities.
+
 Pins (tests/test_oracle_implicit.py): for one vesicle the implicit step equals the advection with the
 operators at X^n followed by the relaxation with the operators at X^n (an algebraic identity of the two
 schemes); two vesicles mirrored across an axis of a symmetric background flow stay mirrored; the velocity
@@ -23,6 +28,7 @@ of the solved state satisfies both lines of the equation.
 import numpy as np
 
 from . import correct as _corr
+from .farfield import far_field
 from .flows import background
 from .operators import Operators
 from .redistribute import redistribute
@@ -48,14 +54,40 @@ def force_matrix(ops, kappa):
     return np.block([[-kappa * D4, Z, ops.Ten[:N]], [Z, -kappa * D4, ops.Ten[N:]]])
 
 
-def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p):
+def near_blocks(xs, ys, mu):
+    """Near pairs of the far-field rule and, per source vesicle b with near targets, the dense map from
+    f_b = [f_x; f_y] (2 N_b) to the near-field correction at every point ([u_x over all points; u_y])."""
+    from .nearfield import near_correction
+    zero = [np.zeros(len(x)) for x in xs]
+    _, _, near = far_field(xs, ys, zero, zero, mu, near_mask=True)
+    P = sum(len(x) for x in xs)
+    blocks = {}
+    for b in sorted({v for _, v in near}):
+        pairs = [(t, v) for t, v in near if v == b]
+        Nb = len(xs[b])
+        Nmat = np.zeros((2 * P, 2 * Nb))
+        for c in range(2 * Nb):
+            fx = [np.zeros(len(x)) for x in xs]
+            fy = [np.zeros(len(x)) for x in xs]
+            (fx if c < Nb else fy)[b][c % Nb] = 1.0
+            cx, cy = near_correction(xs, ys, fx, fy, mu, pairs)
+            Nmat[:, c] = np.concatenate([cx, cy])
+        blocks[b] = Nmat
+    return near, blocks
+
+
+def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p, near_field=False):
     """X^{n+1}, sigma^{n+1} of Eq. time_step_sc1 for every vesicle (before redistribution)."""
     M = len(xs)
     Ns = [len(x) for x in xs]
     off = np.concatenate([[0], np.cumsum([3 * n for n in Ns])])
+    poff = np.concatenate([[0], np.cumsum(Ns)])
+    P = poff[-1]
     n_all = off[-1]
     ops = [Operators(x, y, kappa, mu) for x, y in zip(xs, ys)]
     F = [force_matrix(o, kappa) for o in ops]
+    near, blocks = near_blocks(xs, ys, mu) if near_field else ([], {})
+    near_set = set(near)
     A = np.zeros((n_all, n_all))
     b = np.zeros(n_all)
     for a in range(M):
@@ -65,7 +97,18 @@ def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p):
         # U_a = sum_b V_ab z_b with V_ab = G_ab F_b (G_aa = S_a)
         V = []
         for bb in range(M):
-            G = ops[a].S if bb == a else interaction_matrix(xs[a], ys[a], xs[bb], ys[bb], mu)
+            if bb == a:
+                G = ops[a].S
+            else:
+                G = interaction_matrix(xs[a], ys[a], xs[bb], ys[bb], mu)
+                # targets of a near b: the trapezoid rule is replaced by the near-field correction
+                for i in range(Na):
+                    if (poff[a] + i, bb) in near_set:
+                        G[i, :] = 0.0
+                        G[Na + i, :] = 0.0
+                if bb in blocks:
+                    rows = np.concatenate([np.arange(poff[a], poff[a + 1]), P + np.arange(poff[a], poff[a + 1])])
+                    G = G + blocks[bb][rows]
             V.append(G @ F[bb])
         rows_x = np.zeros((2 * Na, n_all))
         rows_s = np.zeros((Na, n_all))
@@ -100,7 +143,7 @@ class ImplicitSuspension:
 
     def step(self):
         p = self.p
-        sol = implicit_solve(self.xs, self.ys, p.kappa, p.mu, p.dt, p.flow_kind, p.flow_p)
+        sol = implicit_solve(self.xs, self.ys, p.kappa, p.mu, p.dt, p.flow_kind, p.flow_p, near_field=p.near_field)
         nxs, nys, nsig = [], [], []
         for v, (x1, y1, s1) in enumerate(sol):
             xr, yr, alpha = redistribute(x1, y1)
