@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-farfield-alone", action="store_true", help="skip the far field alone on the 2000 x 128 box")
     ap.add_argument("--no-near-arm", action="store_true", help="skip the plain step with near pairs")
     ap.add_argument("--no-uneven-arm", action="store_true", help="skip the plain step with 32/64/128-point vesicles")
+    ap.add_argument("--no-implicit-arm", action="store_true", help="skip the fully implicit (GMRES) step")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
@@ -395,6 +396,41 @@ def uneven_arm(args, stream):
     return out
 
 
+def implicit_arm(args, stream, tol=1e-8, multipole=False):
+    """The paper's ground-truth scheme on the headline suspension: the fully implicit step (Sec. 2.2.3,
+    Eq. time_step_sc1) solved by restarted flexible GMRES (30 vectors) with the per-vesicle FP32
+    preconditioner, every product through the symmetric far field (or the vesicle-multipole far field) and
+    the near-field rule. Reports the GMRES iterations per step and the kernels' shares beside the step time."""
+    from paper_2606_25569_b300 import binding
+    wl = workload(args)
+    sus = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                             flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, mode=2,
+                             farfield_multipole=multipole)
+    sus.set_gmres(tol=tol, restart=30, max_iter=600)
+    sus.step(1)
+    sus.sync()
+    n = max(3, min(args.steps, 5))
+    _, _, it0 = sus.gmres_stats()
+    l0 = sus.counters()["launches"]
+    ms = _time_steps(sus, n, stream)
+    last, res, it1 = sus.gmres_stats()
+    launches = sus.counters()["launches"] - l0
+    prof = _profile_steps(sus, 1)
+    _, _, it2 = sus.gmres_stats()
+    c = sus.counters()
+    sus.close()
+    tot = sum(v[0] for v in prof.values())
+    groups = {"far_field": "k_farfield", "near_field": "k_near", "gmres_vectors": "k_gm_", "products": "k_imp_"}
+    shares = {g: round(sum(v[0] for k, v in prof.items() if k.startswith(pfx)) / tot, 4) for g, pfx in groups.items()}
+    return {"workload": wl.name, "value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_timed": n,
+            "gmres": {"tol": tol, "restart": 30, "iterations_per_step": (it1 - it0) / n,
+                      "last_residual_estimate": res, "iterations_profiled_step": it2 - it1},
+            "gpu_launches_per_step": launches / n, "kernel_time_shares": shares, "corrections": c["corrections"],
+            "near_pairs_last_product": c["near_pairs"],
+            "far_field": ("fp32 vesicle multipole and local expansions for separated vesicles, point sums inside"
+                          if multipole else "fp32 symmetric pair kernel (as the plain step)")}
+
+
 def _time_steps(sus, n, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -666,11 +702,17 @@ def run_gpu(args):
     ff_alone = farfield_alone(stream) if rank == 0 and not args.no_farfield_alone else None
     near_arm = near_field_arm(args, stream) if rank == 0 and not args.no_near_arm else None
     uneven = uneven_arm(args, stream) if rank == 0 and not args.no_uneven_arm else None
+    implicit = implicit_arm(args, stream) if rank == 0 and not args.no_implicit_arm else None
+    if implicit:
+        implicit["plain_vs_implicit"] = (value / world) / implicit["value"]
+        implicit["multipole"] = implicit_arm(args, stream, multipole=True)
     arms = {}
     if rank == 0 and not args.no_hybrid:
         arms = long_run_arms(wl, args, stream)
         for v in arms.values():
             v["vs_plain"] = v["value"] / (value / world)  # both single-GPU throughputs
+            if implicit:
+                v["vs_implicit"] = v["value"] / implicit["value"]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         procs = host_cores()
@@ -697,7 +739,7 @@ def run_gpu(args):
                 "steady_state": steady, "hybrid": arms.get("hybrid"),
                 "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
                 "hybrid_flow": arms.get("hybrid_flow"), "hybrid_flow_multipole": arms.get("hybrid_flow_multipole"),
-                "farfield_2000x128": ff_alone, "near_field": near_arm, "uneven": uneven,
+                "farfield_2000x128": ff_alone, "near_field": near_arm, "uneven": uneven, "implicit": implicit,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -95,8 +95,7 @@ typedef struct {
   double dt;         /* time step, > 0 */
   double corr_tol;   /* relative area/length error that triggers the correction (Sec. 4.3: 0.01) */
   int32_t mode;      /* 0: plain boundary-integral step, 1: hybrid (learned relaxation, vs_set_network),
-                        2: fully implicit step (Sec. 2.2.3, Eq. time_step_sc1) solved by GMRES (vs_set_gmres);
-                        its operators are FP64 whatever VS_FLAG_DIRECT_FP64 says */
+                        2: fully implicit step (Sec. 2.2.3, Eq. time_step_sc1) solved by GMRES (vs_set_gmres) */
   int32_t near_field;/* 1: exclude near pairs (distance <= h of the source) from the far field */
   int32_t use_graph; /* 1: replay each step from a captured CUDA graph (needs a non-NULL stream and
                         profiling off; otherwise steps are launched one kernel at a time) */
@@ -139,8 +138,10 @@ vs_status vs_step(vs_suspension* s, int32_t nsteps);
  * density f = -kappa D_s^4 X^{n+1} + (sigma^{n+1} X_s)_s, the velocity U = S f + far field of f from the
  * other vesicles (+ the near-field correction of f when near_field is set) satisfies
  *   X^{n+1} - dt U = X^n + dt u_inf(X^n),   P U = -P u_inf(X^n)
- * for all vesicles at once. vs_step solves it by restarted GMRES (right preconditioning with the exact
- * per-vesicle solve of the same system without the other vesicles; two-pass classical Gram-Schmidt),
+ * for all vesicles at once. vs_step solves it by restarted flexible GMRES (right preconditioning with the
+ * per-vesicle solve of the same system without the other vesicles: FP32 explicit inverses, or the FP64 LU
+ * factors under VS_FLAG_DIRECT_FP64; the products with the system matrix are FP64 either way, apart from
+ * the far field the flags select; two-pass classical Gram-Schmidt),
  * starting from (X^n, sigma^n), until ||b - A z|| <= tol ||b|| by GMRES's own residual estimate; then
  * redistributes X^{n+1} (Sec. 4.2; sigma^{n+1} evaluated at the new parameters by its trigonometric
  * interpolant) and applies the area/length correction (Sec. 4.3). The far field of each product is the
@@ -151,7 +152,7 @@ vs_status vs_step(vs_suspension* s, int32_t nsteps);
  *  vs_set_gmres: tol > 0 (default 1e-10), 1 <= restart <= VS_GMRES_MAX_RESTART (default 30) Krylov vectors
  *    per cycle, max_iter >= 1 (default 300) iterations per step; vs_step returns VS_ERR_NOT_CONVERGED
  *    when a step needs more (the state is then not advanced past the failing solve). Device memory:
- *    (restart + 6) * 3 P doubles, allocated by the first mode-2 step.
+ *    (2 restart + 5) * 3 P doubles, allocated by the first mode-2 step.
  *  vs_gmres_stats: iterations and relative residual estimate of the last step, iterations over all
  *    steps; any pointer may be NULL.
  */

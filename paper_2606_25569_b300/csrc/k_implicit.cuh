@@ -1,5 +1,5 @@
 // Fully implicit step (Sec. 2.2.3, Eq. time_step_sc1): the coupled system of all vesicles, solved by
-// GMRES with a block-diagonal preconditioner (the paper's solver: preconditioned GMRES).
+// flexible GMRES with a block-diagonal preconditioner (the paper's solver: preconditioned GMRES).
 //
 // Unknowns per vesicle: z = [x(N), y(N), sigma(N)] at 3 off (the "3-block" layout). With every operator at
 // X^n, the density f = -kappa D_s^4 X + D_s(sigma X_s) is linear in z, the velocity is
@@ -14,7 +14,8 @@
 //   k_imp_pack      z0 = [X^n; sigma^n]
 //   k_imp_density   f of a vector p into the far field's source buffers (f, g64, src.zw, gsum), u = 0
 //   k_imp_apply     q = [p_X - dt (S f + u); P (S f + u)] (u: the far field + near field of f)
-//   k_imp_precond   the block-diagonal inverse above
+//   k_imp_precond   the block-diagonal inverse above from the FP64 LU factors (FP64 operators), or
+//   k_imp_precond32 from the FP32 explicit inverses of the mixed-precision path (an approximate inverse)
 //   k_imp_unpack    X^{n+1} and sigma^{n+1} (sigma into the first component of a velocity-shaped buffer,
 //                   which the redistribution carries to the new parameters)
 //   k_gm_*          GMRES vector kernels over n = 3P doubles (grid-stride; dot products per CTA then a
@@ -23,6 +24,7 @@
 #include "common.cuh"
 #include "k_dense.cuh"
 #include "k_geometry.cuh"
+#include "k_mp.cuh"
 #include "k_vesicle.cuh"
 
 namespace vs {
@@ -177,6 +179,31 @@ __global__ void __launch_bounds__(256) k_imp_precond(VesIndex vi, const double* 
     for (int k = 0; k < 2 * N; ++k) acc = fma(W[(int64_t)i * 2 * N + k], x[k], acc);
     out[3 * o + 2 * N + i] = t[i] - acc;
   }
+}
+
+// The same per-vesicle inverse from the FP32 operators of the mixed-precision path (explicit inverses Li32
+// of L and Ai32 of A, T32, W32 = Li32 P B32), all arithmetic in FP32: an approximate inverse, which the
+// flexible GMRES accepts as it stands (the products with A stay FP64).
+template <int THREADS, int COLS>
+__global__ void __launch_bounds__(THREADS) k_imp_precond32(VesIndex vi, const double* __restrict__ r,
+                                                           const float* __restrict__ scratch32, int s,
+                                                           int64_t ainv_sub, double dt, double* __restrict__ out) {
+  __shared__ __align__(16) float fs[NMAX], fy[NMAX], fw[NMAX], fr[2 * NMAX], fdx[2 * NMAX];
+  const int v = vi.vid(blockIdx.x);
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int64_t NN = (int64_t)N * N;
+  const MpMats m = mp_mats(vi, scratch32, v, s);
+  const float* base32 = scratch32 + vi.moff[v];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) fs[i] = (float)r[3 * o + 2 * N + i];
+  for (int q = threadIdx.x; q < 2 * N; q += blockDim.x) fr[q] = (float)r[3 * o + q];
+  __syncthreads();
+  matvec32f<COLS>(m.li, N, N, fs, fy, 1.f, false);
+  matvec32f<COLS>(m.t32, 2 * N, N, fy, fr, (float)dt, true);
+  matvec32f<COLS>(base32 + ainv_sub * NN, 2 * N, 2 * N, fr, fdx, 1.f, false);
+  matvec32f<COLS>(base32 + MatLayout::W * NN, N, 2 * N, fdx, fw, 1.f, false);
+  for (int q = threadIdx.x; q < 2 * N; q += blockDim.x) out[3 * o + q] = (double)fdx[q];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) out[3 * o + 2 * N + i] = (double)fy[i] - (double)fw[i];
 }
 
 __global__ void __launch_bounds__(NMAX) k_imp_unpack(VesIndex vi, const double* __restrict__ z,

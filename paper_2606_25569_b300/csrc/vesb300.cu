@@ -323,7 +323,9 @@ struct GmresState {
   int G = 0;                 // CTAs of the vector kernels
   int alloc_restart = 0;
   double *V = nullptr;       // (restart + 1) x n Krylov basis
-  double *w = nullptr, *z = nullptr, *b = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double *Z = nullptr;       // restart x n preconditioned basis vectors (flexible GMRES)
+  int64_t ainv = 0;          // FP32 inverse of the relaxation matrix in the FP32 scratch (mixed precision)
+  double *w = nullptr, *z = nullptr, *b = nullptr, *t1 = nullptr;
   double *part = nullptr;    // (restart + 1) x G partial dot products
   double *hd = nullptr;      // Hessenberg column (restart + 2), then the first pass's coefficients
   double *hd2 = nullptr;     // second Gram-Schmidt pass's coefficients / the update coefficients y
@@ -332,10 +334,10 @@ struct GmresState {
   double last_res = 0.0;
   int64_t total_iters = 0;
   void release() {
-    cudaFree(V); cudaFree(w); cudaFree(z); cudaFree(b); cudaFree(t1); cudaFree(t2); cudaFree(part);
+    cudaFree(V); cudaFree(Z); cudaFree(w); cudaFree(z); cudaFree(b); cudaFree(t1); cudaFree(part);
     cudaFree(hd); cudaFree(hd2);
     if (hh) cudaFreeHost(hh);
-    V = w = z = b = t1 = t2 = part = hd = hd2 = hh = nullptr;
+    V = Z = w = z = b = t1 = part = hd = hd2 = hh = nullptr;
     alloc_restart = 0;
   }
 };
@@ -525,9 +527,9 @@ inline bool mp_wide(const vs_suspension* h) { return h->L.nmax > 64 || h->L.M < 
   } while (0)
 
 // Mixed precision (default): FP32 operator products and factorisations refined in FP64.
-// FP32 factorisations with FP64 refinement, unless FP64 operators are asked for or the step is the fully
-// implicit one (its GMRES preconditioner uses the FP64 LU factors)
-inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64) && h->p.mode != 2; }
+// FP32 factorisations (refined in FP64, or preconditioning the implicit step's FP64 GMRES) unless FP64
+// operators are asked for
+inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
 
 // S, T, L at slot s for the geometry currently in the SourceBufs, then LU of L.
 vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* active) {
@@ -960,45 +962,62 @@ vs_status relax_matrix_fp64(vs_suspension* h, int s) {
   return VS_OK;
 }
 
+// FP32 relaxation matrices with the operators of slot s (FP32 copies) and the geometry in the SourceBufs:
+// D4, B, W = Li32 P B and the explicit FP32 inverse of A = I - dt (B - T W) (Eq. relaxation_disc); returns
+// where the inverse sits in the FP32 scratch (units of N^2), -1 on a launch error. With active non-null only
+// the flagged vesicles' matrices are formed (the 2 x 2 block path forms all).
+int64_t relax_matrix_32(vs_suspension* h, int s, const int* active) {
+  const int M = h->L.M, n = h->L.nmax;
+  const VesIndex vi = h->D.vi();
+  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
+  gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, active);
+  gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, active);
+  gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, active);
+  gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 1, h->p.kappa_b}, 2 * n, n, active);
+  gemm32(h, "k_bgemm<OpPB32>", OpPB32{c}, n, 2 * n, active);
+  gemm32(h, "k_bgemm<OpW32>", OpW32{c, s}, n, 2 * n, active);
+  gemm32(h, "k_bgemm<OpA32>", OpA32{c, s, h->p.dt}, 2 * n, 2 * n, active);
+  const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
+  const int64_t ainv = MatLayout::A;
+  if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, active)) {
+    // 2N beyond the register Gauss-Jordan: the 2 x 2 block (Schur complement) inverse in place,
+    // A = [A11 A12; A21 A22], X1 = A11^{-1}, Y = X1 A12, Z = A21 X1, S = A22 - A21 Y,
+    // A^{-1} = [X1 - C12 Z, C12; -S^{-1} Z, S^{-1}] with C12 = -Y S^{-1}; X1, Y, Z, S^{-1} in the free B block
+    const int64_t Bq = MatLayout::B;
+    const BlkView A11{MatLayout::A, 2, 0, 0}, A12{MatLayout::A, 2, 0, 1}, A21{MatLayout::A, 2, 1, 0},
+        A22{MatLayout::A, 2, 1, 1}, X1{Bq, 1, 0, 0}, Y{Bq + 1, 1, 0, 0}, Z{Bq + 2, 1, 0, 0}, Si{Bq + 3, 1, 0, 0};
+    const dim3 gcopy((n * n + 255) / 256, M);
+    VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, A11, X1));
+    launch_gj32(h, "k_gj_inverse<A11>", LuGeo32{vi, h->scratch32, Bq, 1, 0, h->piv32, 2}, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, X1, A12, Y, Y, 1.f, 0}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, X1, Z, Z, 1.f, 0}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, Y, Si, A22, -1.f, 1}, n, n, nullptr);
+    launch_gj32(h, "k_gj_inverse<S>", LuGeo32{vi, h->scratch32, Bq + 3, 1, 0, h->piv32, 2}, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Y, Si, A12, A12, -1.f, 0}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Si, Z, A21, A21, -1.f, 0}, n, n, nullptr);
+    gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, n, n, nullptr);
+    VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(h->msg, e, "relaxation matrix");
+    return -1;
+  }
+  return ainv;
+}
+
 // Exact relaxation (Eq. relaxation_disc) of xs into xo with the operators at slot s; with active non-null
 // only the vesicles with active[v] != 0 are processed and written.
 vs_status relax_exact(vs_suspension* h, const double* xs, double* xo, int s, const int* active = nullptr) {
   const Layout& L = h->L;
-  const int M = L.M, n = L.nmax;
+  const int M = L.M;
   const VesIndex vi = h->D.vi();
   vs_status st;
   if ((st = geometry(h, xs, false, active)) != VS_OK) return st;
   if ((st = build_operators(h, xs, s, active)) != VS_OK) return st;
-  OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
   if (mixed(h)) {
-    gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, active);
-    gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, active);
-    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, active);
-    gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 1, h->p.kappa_b}, 2 * n, n, active);
-    gemm32(h, "k_bgemm<OpPB32>", OpPB32{c}, n, 2 * n, active);
-    gemm32(h, "k_bgemm<OpW32>", OpW32{c, s}, n, 2 * n, active);
-    gemm32(h, "k_bgemm<OpA32>", OpA32{c, s, h->p.dt}, 2 * n, 2 * n, active);
-    const LuGeo32 ga{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2};
-    const int64_t ainv = MatLayout::A;
-    if (!launch_gj32(h, "k_gj_inverse<A>", ga, 2 * n, active)) {
-      // 2N beyond the register Gauss-Jordan: the 2 x 2 block (Schur complement) inverse in place,
-      // A = [A11 A12; A21 A22], X1 = A11^{-1}, Y = X1 A12, Z = A21 X1, S = A22 - A21 Y,
-      // A^{-1} = [X1 - C12 Z, C12; -S^{-1} Z, S^{-1}] with C12 = -Y S^{-1}; X1, Y, Z, S^{-1} in the free B block
-      const int64_t Bq = MatLayout::B;
-      const BlkView A11{MatLayout::A, 2, 0, 0}, A12{MatLayout::A, 2, 0, 1}, A21{MatLayout::A, 2, 1, 0},
-          A22{MatLayout::A, 2, 1, 1}, X1{Bq, 1, 0, 0}, Y{Bq + 1, 1, 0, 0}, Z{Bq + 2, 1, 0, 0}, Si{Bq + 3, 1, 0, 0};
-      const dim3 gcopy((n * n + 255) / 256, M);
-      VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, A11, X1));
-      launch_gj32(h, "k_gj_inverse<A11>", LuGeo32{vi, h->scratch32, Bq, 1, 0, h->piv32, 2}, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, X1, A12, Y, Y, 1.f, 0}, n, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, X1, Z, Z, 1.f, 0}, n, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A21, Y, Si, A22, -1.f, 1}, n, n, nullptr);
-      launch_gj32(h, "k_gj_inverse<S>", LuGeo32{vi, h->scratch32, Bq + 3, 1, 0, h->piv32, 2}, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Y, Si, A12, A12, -1.f, 0}, n, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, Si, Z, A21, A21, -1.f, 0}, n, n, nullptr);
-      gemm32(h, "k_bgemm<OpBlk32>", OpBlk32{c, A12, Z, A11, X1, -1.f, 1}, n, n, nullptr);
-      VS_LAUNCH(h, "k_blk_copy", k_blk_copy<<<gcopy, 256, 0, h->stream>>>(c, Si, A22));
-    }
+    const int64_t ainv = relax_matrix_32(h, s, active);
+    if (ainv < 0) return VS_ERR_CUDA;
     MP_DISPATCH(h, "k_relax_mp", k_relax_mp, M, (vi, xs, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->scratch32, s, ainv,
                                                     h->p.kappa_b, h->p.dt, xo, h->err, active));
     VS_CK(h, cudaGetLastError(), "relaxation");
@@ -1260,11 +1279,12 @@ vs_status step_once(vs_suspension* h) {
   return VS_OK;
 }
 
-// ---- Fully implicit step (mode 2; Sec. 2.2.3, Eq. time_step_sc1), solved by restarted GMRES with the
-// block-diagonal (per-vesicle) preconditioner of k_implicit.cuh, right-preconditioned: the Krylov space is
-// built for A M^{-1} and the solution is z = z0 + M^{-1} V y. Gram-Schmidt is classical, applied twice
-// (CGS2) with batched dot products; the small Hessenberg least-squares problem (Givens rotations) runs on
-// the host, which reads one column per iteration.
+// ---- Fully implicit step (mode 2; Sec. 2.2.3, Eq. time_step_sc1), solved by restarted flexible GMRES
+// with the block-diagonal (per-vesicle) preconditioner of k_implicit.cuh applied on the right: the Arnoldi
+// process runs on A M^{-1}, the preconditioned vectors z_j = M^{-1} v_j are kept and the solution is
+// z = z0 + Z y, so an approximate (FP32) M^{-1} costs iterations but no accuracy. Gram-Schmidt is
+// classical, applied twice (CGS2) with batched dot products; the small Hessenberg least-squares problem
+// (Givens rotations) runs on the host, which reads one column per iteration.
 
 vs_status gmres_alloc(vs_suspension* h) {
   GmresState& g = h->gm;
@@ -1275,11 +1295,11 @@ vs_status gmres_alloc(vs_suspension* h) {
   g.G = (int)std::min<int64_t>((n + GM_THREADS - 1) / GM_THREADS, 4 * 148);
   const int m = g.restart;
   VS_CK(h, dalloc(&g.V, (int64_t)(m + 1) * n), "GMRES buffers");
+  VS_CK(h, dalloc(&g.Z, (int64_t)m * n), "GMRES buffers");
   VS_CK(h, dalloc(&g.w, n), "GMRES buffers");
   VS_CK(h, dalloc(&g.z, n), "GMRES buffers");
   VS_CK(h, dalloc(&g.b, n), "GMRES buffers");
   VS_CK(h, dalloc(&g.t1, n), "GMRES buffers");
-  VS_CK(h, dalloc(&g.t2, n), "GMRES buffers");
   VS_CK(h, dalloc(&g.part, (int64_t)(m + 2) * g.G), "GMRES buffers");
   VS_CK(h, dalloc(&g.hd, m + 2), "GMRES buffers");
   VS_CK(h, dalloc(&g.hd2, m + 2), "GMRES buffers");
@@ -1306,8 +1326,13 @@ vs_status imp_matvec(vs_suspension* h, int s, const double* p, double* q) {
 }
 
 vs_status imp_precond(vs_suspension* h, int s, const double* r, double* out) {
-  VS_LAUNCH(h, "k_imp_precond", k_imp_precond<<<h->L.M, 256, 0, h->stream>>>(h->D.vi(), r, h->scratch, h->piv, s,
-                                                                             h->p.dt, out));
+  const VesIndex vi = h->D.vi();
+  if (mixed(h)) {
+    MP_DISPATCH(h, "k_imp_precond32", k_imp_precond32, h->L.M, (vi, r, h->scratch32, s, h->gm.ainv, h->p.dt, out));
+  } else {
+    VS_LAUNCH(h, "k_imp_precond", k_imp_precond<<<h->L.M, 256, 0, h->stream>>>(vi, r, h->scratch, h->piv, s, h->p.dt,
+                                                                               out));
+  }
   VS_CK(h, cudaGetLastError(), "implicit preconditioner");
   return VS_OK;
 }
@@ -1362,8 +1387,9 @@ vs_status gmres_solve(vs_suspension* h, int s) {
     for (int j = 0; j < m && iters < g.max_iter; ++j) {
       double* vj = g.V + (int64_t)j * n;
       double* vn = g.V + (int64_t)(j + 1) * n;
-      if ((st = imp_precond(h, s, vj, g.t2)) != VS_OK) return st;
-      if ((st = imp_matvec(h, s, g.t2, g.w)) != VS_OK) return st;
+      double* zj = g.Z + (int64_t)j * n;
+      if ((st = imp_precond(h, s, vj, zj)) != VS_OK) return st;
+      if ((st = imp_matvec(h, s, zj, g.w)) != VS_OK) return st;
       // CGS2: h = V^T w, w -= V h, h2 = V^T w, w -= V h2, h += h2
       if ((st = gm_dots(h, g.V, j + 1, g.w, g.hd, nullptr, -1)) != VS_OK) return st;
       VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.V, n, j + 1, g.hd, -1.0, g.w));
@@ -1394,7 +1420,7 @@ vs_status gmres_solve(vs_suspension* h, int s) {
       if (!std::isfinite(res)) { h->msg = "non-finite GMRES residual"; return VS_ERR_UNSTABLE; }
       if (res <= target || g.hh[j + 1] == 0.0) { done = true; break; }
     }
-    // y = R^{-1} g (upper triangular k x k), z += M^{-1} V y
+    // y = R^{-1} g (upper triangular k x k), z += Z y
     for (int i = k - 1; i >= 0; --i) {
       double acc = gv[i];
       for (int c = i + 1; c < k; ++c) acc -= H[(size_t)c * (m + 1) + i] * y[c];
@@ -1403,10 +1429,7 @@ vs_status gmres_solve(vs_suspension* h, int s) {
     }
     for (int i = 0; i < k; ++i) g.hh[i] = y[i];
     VS_CK(h, cudaMemcpyAsync(g.hd2, g.hh, k * sizeof(double), cudaMemcpyHostToDevice, h->stream), "GMRES update");
-    VS_CK(h, cudaMemsetAsync(g.t1, 0, n * sizeof(double), h->stream), "GMRES update");
-    VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.V, n, k, g.hd2, 1.0, g.t1));
-    if ((st = imp_precond(h, s, g.t1, g.t2)) != VS_OK) return st;
-    VS_LAUNCH(h, "k_gm_add", k_gm_add<<<g.G, GM_THREADS, 0, h->stream>>>(g.t2, n, g.z));
+    VS_LAUNCH(h, "k_gm_combine", k_gm_combine<<<g.G, GM_THREADS, 0, h->stream>>>(g.Z, n, k, g.hd2, 1.0, g.z));
     VS_CK(h, cudaGetLastError(), "GMRES update");
     // the host buffer is reused by the next readback only after this copy has run
     VS_CK(h, cudaStreamSynchronize(h->stream), "GMRES update");
@@ -1429,10 +1452,17 @@ vs_status step_implicit(vs_suspension* h) {
   vs_status st;
   if ((st = gmres_alloc(h)) != VS_OK) return st;
   GmresState& g = h->gm;
-  // geometry, centres and sources at X^n; every operator at X^n (Eq. time_step_sc1 discretises them there)
+  // geometry, centres and sources at X^n; every operator at X^n (Eq. time_step_sc1 discretises them there):
+  // the FP64 self matrix for the products, and the preconditioner's factors (FP64 LU or FP32 inverses)
   if ((st = geometry(h, h->xy, true)) != VS_OK) return st;
   if ((st = build_operators(h, h->xy, s, nullptr)) != VS_OK) return st;
-  if ((st = relax_matrix_fp64(h, s)) != VS_OK) return st;
+  if (mixed(h)) {
+    VS_LAUNCH(h, "k_self_matrix", k_self_matrix<<<self_grid(L.nmax, L.M), 256, 0, h->stream>>>(
+                                      vi, h->xy, h->B.sa, h->B.tx, h->B.ty, h->D.tab, h->p.mu, h->scratch, s, nullptr));
+    if ((g.ainv = relax_matrix_32(h, s, nullptr)) < 0) return VS_ERR_CUDA;
+  } else if ((st = relax_matrix_fp64(h, s)) != VS_OK) {
+    return st;
+  }
   VS_LAUNCH(h, "k_imp_rhs", k_imp_rhs<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->B.pg(), h->D.tab, flow_dev(h->flow),
                                                                    h->p.dt, g.b));
   VS_LAUNCH(h, "k_imp_pack", k_imp_pack<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->sigma, g.z));

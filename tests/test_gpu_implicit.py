@@ -4,7 +4,7 @@ against the oracle's dense solve (oracle.implicit).
 Tolerances. The coupled system is stiff: in the FP64 oracle itself a change of one input coordinate by
 1e-16 of itself moves X^{n+1} by 1.3e-10 and sigma^{n+1} by 5e-9 of its size (tests/test_oracle_implicit.py
 measures the mirror images to that level). The GPU path (GMRES to a relative residual of 1e-13, FP64 far
-field, FP64 operators) is held to 1e-9 in X and 1e-6 in sigma per step, and along five steps to five times
+field, FP64 products) is held to 1e-9 in X and 1e-6 in sigma per step, and along five steps to five times
 that; with the FP32 far field (relative error about 1e-5 of the interaction velocity, Sec. 4.1) to 1e-7 in
 X and 1e-4 in sigma.
 """
@@ -53,10 +53,12 @@ def _errors(o, g):
     return ex, es
 
 
+@pytest.mark.parametrize("direct", [False, True], ids=["fp32-preconditioner", "fp64-preconditioner"])
 @pytest.mark.parametrize("Ns,flow", [([32] * 5, (3, (1.0, 6.0, 0, 0))), ([32, 24, 48, 32, 16, 64], (1, (1.0, 0, 0, 0)))])
-def test_implicit_step_matches_oracle_fp64(Ns, flow):
+def test_implicit_step_matches_oracle_fp64(Ns, flow, direct):
+    # the preconditioner changes the iterations, not the solution (flexible GMRES, FP64 products)
     xs, ys = _cluster(Ns, 3)
-    o, g = _pair(xs, ys, 1e-3, flow[0], flow[1], farfield_fp64=True)
+    o, g = _pair(xs, ys, 1e-3, flow[0], flow[1], farfield_fp64=True, direct_fp64=direct)
     for k in range(5):
         o.step()
         g.step()
@@ -82,9 +84,9 @@ def test_implicit_step_matches_oracle_fp32_far_field():
 
 
 def test_single_vesicle_converges_in_one_iteration():
-    # with one vesicle the preconditioner is the exact inverse of the system
+    # with one vesicle the FP64 preconditioner is the exact inverse of the system
     xs, ys = _cluster([48], 5)
-    o, g = _pair(xs, ys, 2e-3, 1, (1.5, 0, 0, 0))
+    o, g = _pair(xs, ys, 2e-3, 1, (1.5, 0, 0, 0), direct_fp64=True)
     o.step()
     g.step()
     it, res, tot = g.gmres_stats()
@@ -105,3 +107,28 @@ def test_gmres_reports_non_convergence():
     assert np.array_equal(g.positions(), before)
     with pytest.raises(binding.VsError):
         g.set_gmres(tol=0.0)
+
+
+def test_implicit_step_with_near_field_matches_oracle():
+    # a close pair (gap about half a point spacing) and a third vesicle: U_near^{n+1} of Eq. time_step_sc1 by
+    # the near-field rule (Sec. 3.3) in every GMRES product. The GPU near field is FP32 (layer sums and the
+    # RBF solve; about 1e-5 of the correction), so X is held to 1e-7 and sigma to 1e-4 per step.
+    xs, ys = [], []
+    for v, (cx, cy, th) in enumerate(((-0.36, 0.0, 1.5), (0.36, 0.05, 1.5), (0.0, 1.4, 0.2))):
+        rng = np.random.default_rng(20 + v)
+        x, y = vesicle_outline(32, 0.7, 0.5, 5e-2, rng, th)
+        xs.append(x + cx)
+        ys.append(y + cy)
+    p = Params(kappa=KAPPA, mu=MU, dt=1e-3, flow_kind=1, flow_p=(1.0, 0, 0, 0), corr_tol=0.01, near_field=True)
+    o = ImplicitSuspension(xs, ys, p)
+    g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=KAPPA, mu=MU, dt=1e-3, corr_tol=0.01, flow_kind=1,
+                           flow_p=(1.0, 0, 0, 0), mode=2, near_field=True, farfield_fp64=True)
+    g.set_gmres(tol=1e-8, restart=30, max_iter=200)
+    for k in range(3):
+        o.step()
+        g.step()
+        ex, es = _errors(o, g)
+        it, res, _ = g.gmres_stats()
+        print("near field, step %d: X %.3e sigma %.3e, GMRES %d iterations, residual %.2e" % (k + 1, ex, es, it, res))
+        assert ex <= 1e-7 * (k + 1), ex
+        assert es <= 1e-4 * (k + 1), es
