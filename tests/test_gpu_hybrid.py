@@ -148,9 +148,10 @@ def test_trained_network_beats_the_step_without_it():
              res["train_seconds"]))
     held = res["holdout_err"]
     assert len(held) == M
-    # the same shapes without the network: zero displacement, relative error exactly 1
-    assert float(np.mean(held)) <= 0.5, float(np.mean(held))
-    assert float(np.median(held)) <= 0.5
+    # the same shapes without the network: zero displacement, relative error exactly 1; this seeded run
+    # measures a mean of 0.138 and a median of 0.129 (the bench's longer training reaches about 0.03)
+    assert float(np.mean(held)) <= 0.2, float(np.mean(held))
+    assert float(np.median(held)) <= 0.2
 
 
 def test_hybrid_near_pairs_fall_back_to_exact_relaxation():
