@@ -28,12 +28,25 @@ learned tension: sigma = -roll(S_sigma(alpha), j0) / L^2 - roll((sum_i f_i S_i)(
 exact_columns() computes the same outputs with the exact operators (oracle.operators) at the standardised
 shape: the targets the networks are trained to, and with them the learned maps reproduce the exact ones
 for velocities of modes <= K_f (pins in tests/test_oracle_learned.py).
+
+Learned near field (Sec. 3.3, Eq. NearFieldMap): N_X^k maps a shape to the single layer of the density
+e^{ik alpha} at the five layer points (oracle.nearfield), so that S[X, f] there is the sum over the density's
+Fourier modes. Readings: the same real basis psi_i (modes 0..K_f of each component) for the density; the
+layer velocities of each psi_i at the layers of the unit-length standardised shape, with mu = 1, as
+velocity features up to K_out per layer; one network per layer (row d = the nb columns of layer d,
+2 (2 K_out + 1) each). For a vesicle X = c + L R^T X^o the single layer transforms as
+    S[X, f](x) = L R^T S[X^o, R f](x^o) / mu - (L log L / (4 pi mu)) (integral of f over the unit curve),
+(the Stokeslet's -log|r| gains -log L under the scaling; the layer spacing h = L/N scales with the shape),
+so the learned layers are L R^T roll(sum_i c_i Q_d,i, j0) / mu plus that constant, c the features of
+roll(R f, -j0). The learned layers are those of the density's modes 0..K_f (f_K, the basis's span): the
+integral is that of f_K, by the quadrature each layer takes (the trapezoid rule on the N points for the
+layer on the curve, the smooth part of the self rule; on the upsampled curve for the others).
 """
 import numpy as np
 
 from .operators import Operators
-from .spectral import Geometry
-from .standardize import features_to_samples, fourier_features, standardize
+from .spectral import Geometry, upsample
+from .standardize import features_to_samples, fourier_features, fourier_filter, standardize
 
 
 def basis_count(Kf):
@@ -120,3 +133,51 @@ def tension_learned(x, y, ux, uy, ten_row, Kf, Kout):
     for i in range(basis_count(Kf)):
         g = g - f[i] * ten_row[(i + 1) * sw:(i + 2) * sw]
     return np.roll(scalar_samples(g, Kout, N), fr.j0)
+
+
+def near_columns(x, y, Kf, Kout):
+    """The N_X rows (one per layer) of the vesicle (x, y): exact layer velocities (oracle.nearfield, mu = 1)
+    of every basis density psi_i at the layers of its standardised shape, as velocity features up to Kout."""
+    from .nearfield import LAYERS, layer_velocities
+    xo, yo, _ = standardize(x, y)
+    N = len(x)
+    rows = [[] for _ in LAYERS]
+    for i in range(basis_count(Kf)):
+        psi = basis_field(i, Kf, N)
+        UX, UY = layer_velocities(xo, yo, psi[:N], psi[N:], 1.0)
+        for d in range(len(LAYERS)):
+            rows[d].append(fourier_features(UX[d * N:(d + 1) * N], UY[d * N:(d + 1) * N], Kout))
+    return [np.concatenate(r) for r in rows]
+
+
+def near_layers_learned(x, y, fx, fy, rows, Kf, Kout, mu):
+    """S[X, f] at the 5N layer points of (x, y) (layer-major, as oracle.nearfield.layer_velocities) from the
+    N_X rows (module header)."""
+    N = len(x)
+    _, _, fr = standardize(x, y)
+    g = Geometry(x, y)
+    L = g.length
+    vx, vy = velocity_to_frame(fx, fy, fr)
+    c = fourier_features(vx, vy, Kf)
+    cw = 2 * (2 * Kout + 1)
+    # integral of f over the unit-length curve, (1/L) times the quadrature of f ds: on the N points for the
+    # layer on the curve, on the curve upsampled as in oracle.nearfield for the others
+    from .nearfield import LAYERS, upsample_factor
+    rho = upsample_factor(N)
+    gu = Geometry(upsample(x, rho), upsample(y, rho))
+    fxk, fyk = fourier_filter(fx, Kf), fourier_filter(fy, Kf)
+    fxu, fyu = upsample(fxk, rho), upsample(fyk, rho)
+    tot = {True: (np.sum(fxk * g.sa) * 2.0 * np.pi / N / L, np.sum(fyk * g.sa) * 2.0 * np.pi / N / L),
+           False: (np.sum(fxu * gu.sa) * 2.0 * np.pi / (rho * N) / L, np.sum(fyu * gu.sa) * 2.0 * np.pi / (rho * N) / L)}
+    k0 = -L * np.log(L) / (4.0 * np.pi * mu)
+    UX, UY = [], []
+    for d, row in zip(LAYERS, rows):
+        tot_x, tot_y = tot[d == 0.0]
+        acc = np.zeros(cw)
+        for i in range(basis_count(Kf)):
+            acc = acc + c[i] * row[i * cw:(i + 1) * cw]
+        qx, qy = features_to_samples(acc, Kout, N)
+        px, py = velocity_from_frame(qx, qy, fr)
+        UX.append(L * px / mu + k0 * tot_x)
+        UY.append(L * py / mu + k0 * tot_y)
+    return np.concatenate(UX), np.concatenate(UY)

@@ -82,9 +82,10 @@ def rbf_eval(LX, LY, WX, WY, h, tx, ty):
     return Q @ WX, Q @ WY
 
 
-def near_correction(xs, ys, fxs, fys, mu, near_pairs):
+def near_correction(xs, ys, fxs, fys, mu, near_pairs, layers=None):
     """Velocity added at every point (flat over all points) by the near-field rule of the
-    sorted (target, source vesicle) pairs."""
+    sorted (target, source vesicle) pairs. layers(v) -> (UX, UY), when given, supplies source vesicle v's
+    layer velocities instead of step 2 (the learned near field, oracle.learned.near_layers_learned)."""
     P = sum(len(x) for x in xs)
     X = np.concatenate(xs)
     Y = np.concatenate(ys)
@@ -95,7 +96,7 @@ def near_correction(xs, ys, fxs, fys, mu, near_pairs):
         by_src.setdefault(v, []).append(t)
     for v, targets in sorted(by_src.items()):
         LX, LY, h = layer_points(xs[v], ys[v])
-        UX, UY = layer_velocities(xs[v], ys[v], fxs[v], fys[v], mu)
+        UX, UY = layer_velocities(xs[v], ys[v], fxs[v], fys[v], mu) if layers is None else layers(v)
         WX, WY = rbf_weights(LX, LY, UX, UY, h)
         t = np.array(targets)
         ax, ay = rbf_eval(LX, LY, WX, WY, h, X[t], Y[t])

@@ -29,7 +29,9 @@ source vesicle) or within exact_gap (default HYBRID_EXACT_GAP) spacings of anoth
 on every m-th step: those relax exactly, the plain step serving as the fallback of the learned one (reading: the paper's VesNet learns the near interactions
 too; here they keep the exact relaxation). With Params.flow_net set as well, steps 3 and 6 of every step
 take the learned advection and tension of oracle.learned (Eqs. advectionMap, advTenMap), except for the
-vesicles of that fallback set, which keep the exact ones. Initial tension (not given in the paper):
+vesicles of that fallback set, which keep the exact ones. With Params.near_net set as well (and the near
+field on), step 2's near-field layer velocities of every source vesicle come from the learned near field
+(oracle.learned.near_layers_learned, Sec. 3.3) in every step. Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -48,7 +50,7 @@ HYBRID_EXACT_GAP = 4.0
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
                  near_field=False, corr_tol=0.01, relax_net=None, exact_every=0, exact_gap=HYBRID_EXACT_GAP,
-                 flow_net=None):
+                 flow_net=None, near_net=None):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
@@ -62,6 +64,9 @@ class Params:
         # vesicle (x, y) giving its output row: with relax_net set, the
         # advection and the tension of every step come from them (oracle.learned), for every vesicle
         self.flow_net = flow_net
+        # (nets, Kf, Kout), nets the five layer networks (as flow_net's entries), layer order -h .. h: with
+        # relax_net set and the near field on, the near-field layer velocities come from them
+        self.near_net = near_net
 
 
 def relax_learned(x, y, net):
@@ -151,7 +156,16 @@ class Suspension:
         ux, uy, near = far_field(self.xs, self.ys, fx, fy, p.mu, near_mask=p.near_field)
         if p.near_field and near:
             from .nearfield import near_correction
-            cx, cy = near_correction(self.xs, self.ys, fx, fy, p.mu, near)
+            layers = None
+            if p.relax_net is not None and p.near_net is not None:
+                from .learned import near_layers_learned
+                nets, Kf, Kout = p.near_net
+                kmax = p.relax_net[3]
+
+                def layers(v):
+                    rows = [flow_row(self.xs[v], self.ys[v], net, kmax) for net in nets]
+                    return near_layers_learned(self.xs[v], self.ys[v], fx[v], fy[v], rows, Kf, Kout, p.mu)
+            cx, cy = near_correction(self.xs, self.ys, fx, fy, p.mu, near, layers=layers)
             ux = ux + cx
             uy = uy + cy
         self.near_pairs = near
