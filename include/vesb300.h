@@ -283,6 +283,34 @@ vs_status vs_set_flow_networks(vs_suspension* s, vs_mlp* adv, vs_mlp* ten, int32
 vs_status vs_flow_maps(vs_suspension* s, int32_t Kf, int32_t Kout, int32_t filter_kmax, float* xin, float* adv,
                        float* ten);
 
+/*
+ * Learned near field (Sec. 3.3, Eq. NearFieldMap: N_X^k maps a shape to the single layer of the density
+ * e^{ik alpha} at the five layer points X + d h n, d in {-1, -1/2, 0, 1/2, 1}). The density's Fourier features
+ * f (modes 0..Kf of each component, in the vesicle's standard frame, as for the flow networks) combine the
+ * columns of each layer: network d gives, per vesicle, the layer-d velocities of the nb = 4 Kf + 2 basis
+ * densities psi_i at the unit-length standardised shape with mu = 1, as velocity features up to Kout
+ * (2 (2 Kout + 1) floats per column, in basis order: flow_adv_width(Kf, Kout) outputs). The layer velocities
+ * are then those of the density's modes <= Kf, f_K:
+ *   S[X, f_K] = L R^T shift(sum_i f_i Q_d,i) / mu - (L log L / (4 pi mu)) I_d,
+ * I_d the integral of f_K over the unit-length curve by the layer's quadrature (the N points on the curve,
+ * the curve upsampled by ceil(sqrt(N)) off it); the RBF interpolation to the near targets is unchanged.
+ *
+ * vs_set_near_networks: a hybrid suspension (mode 1, created with near_field = 1) with these networks set
+ * takes the layer velocities of every near source vesicle from them in every step. nets: n = 5 borrowed
+ * networks, layer order as above (-h first); input width that of the relaxation network (set it first),
+ * batch capacity >= M, the suspension's stream; Kf, Kout in [0, N/2 - 1]. nets NULL removes them. Errors:
+ * VS_ERR_INVALID_ARG.
+ *
+ * vs_near_maps: training data of the five networks from the exact layer velocities. For the suspension's
+ * current points (equal N): xin (DEVICE FP32, M x W) = the network input (filter_kmax as for vs_set_network)
+ * and out (DEVICE FP32, 5 x M x flow_adv_width(Kf, Kout), layer-major) = the rows above (on-curve layer by
+ * the self rule, off-curve layers by FP32 sums on the upsampled curve, as the plain near field computes
+ * them). The suspension's state and its operator cache for the next step are left as they were.
+ * Synchronous; allocates scratch.
+ */
+vs_status vs_set_near_networks(vs_suspension* s, vs_mlp* const* nets, int32_t n, int32_t Kf, int32_t Kout);
+vs_status vs_near_maps(vs_suspension* s, int32_t Kf, int32_t Kout, int32_t filter_kmax, float* xin, float* out);
+
 /* Training pairs of the relaxation map: for DEVICE points xy_in (CSR blocks, equal N), xin (device
  * FP32, M x W) = the network input of vs_set_network's map and yout (device FP32, M x W) = the
  * features of (relax(xy_in) - xy_in) in each vesicle's standard frame, divided by out_scale; W and the

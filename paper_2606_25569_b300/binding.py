@@ -26,6 +26,10 @@ FUNCTIONS = {
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "vs_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "vs_set_near_networks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32]),
+    "vs_near_maps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "vs_set_gmres": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]),
     "vs_gmres_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -256,6 +260,21 @@ class Suspension:
         """Training rows of the advection and tension networks at the current points (vs_flow_maps)."""
         self._check(lib().vs_flow_maps(self._h, int(Kf), int(Kout), int(filter_kmax), _ptr(xin_dev), _ptr(adv_dev),
                                        _ptr(ten_dev)))
+
+    def set_near_networks(self, nets, Kf, Kout):
+        """Learned near-field layers (vs_set_near_networks): five networks, layer order -h .. h; None removes."""
+        if nets is None:
+            self._near = None
+            self._check(lib().vs_set_near_networks(self._h, None, 0, int(Kf), int(Kout)))
+            return
+        self._near = list(nets)  # the library borrows them
+        arr = (ctypes.c_void_p * len(nets))(*[n._h.value for n in nets])
+        self._check(lib().vs_set_near_networks(self._h, arr, len(nets), int(Kf), int(Kout)))
+
+    def near_maps(self, Kf, Kout, filter_kmax, xin_dev, out_dev):
+        """Training rows of the near-field networks at the current points (vs_near_maps): out_dev holds
+        5 x M x flow_adv_width(Kf, Kout) floats, layer-major."""
+        self._check(lib().vs_near_maps(self._h, int(Kf), int(Kout), int(filter_kmax), _ptr(xin_dev), _ptr(out_dev)))
 
     def relax(self, xy_in_dev, xy_out_dev):
         self._check(lib().vs_relax(self._h, _ptr(xy_in_dev), _ptr(xy_out_dev)))

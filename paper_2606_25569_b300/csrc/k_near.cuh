@@ -7,6 +7,13 @@
 //                 (the RBF that takes these values is FP32) with the far field's log scaling: each
 //                 target's log arguments scaled by a power of two near 1 / (|x - c|^2 + reach^2) and the
 //                 exponent times the density sum added once;
+//                 With the learned near field (Sec. 3.3, Eq. NearFieldMap; k_near_layers<true>) the layer
+//                 velocities come from the networks' rows instead: the density's Fourier features in the
+//                 vesicle's standard frame combine the columns of each layer (the layer velocities of the
+//                 basis densities at the unit-length standardised shape, mu = 1), and
+//                 S[X, f_K] = L R^T shift(sum_i c_i Q_d,i) / mu - (L log L / (4 pi mu)) I_d for the density's
+//                 modes <= Kf, f_K, I_d the integral of f_K over the unit-length curve by the layer's own
+//                 quadrature (the N points on the curve, the upsampled curve off it);
 //  k_near_rbf     (Phi + lam I) w = u_layers, Phi_ab = exp(-|x_a - x_b|^2 / (c h)^2), c = 2,
 //                 lam = 1e-3, by an FP32 Cholesky (the paper's precision): k_near_rbf_smem holds the
 //                 lower triangle in shared memory (5N <= 320), k_near_rbf works in the vesicle's scratch;
@@ -15,6 +22,7 @@
 #include "common.cuh"
 #include "k_dense.cuh"
 #include "k_farfield.cuh"
+#include "k_standardize.cuh"
 #include "k_vesicle.cuh"
 
 namespace vs {
@@ -108,19 +116,120 @@ struct NearBufs {
   float* phi;      // per vesicle at moff[v]: (5N)^2 floats
 };
 
+// The learned near field's inputs: one network output row per vesicle and layer (row v of layer d at
+// rows[d] + v ld: the nb = 4 Kf + 2 columns of velocity features up to Kout, 2 (2 Kout + 1) floats each) and
+// the standardisation frames of the same step.
+struct NearNets {
+  const float* rows[NEAR_LAYERS];
+  int64_t ld;
+  int Kf, Kout;
+  const StdFrame* frames;
+};
+
+// Learned layer velocities of vesicle v (all threads of the CTA; module header), written to UX, UY (5N each,
+// layer-major, the vesicle's own point labels): those of f_K, the density's modes <= Kf. gs = the upsampled
+// quadrature's density sums sum_q f_K,u |X'_u| (2 pi / Nu) / (4 pi mu), the off-curve layers' integral of f_K
+// times L / (4 pi mu).
+__device__ void near_learned_layers(const NearNets& nn, int v, int N, int64_t o, const double* T,
+                                    const double* __restrict__ f, PointGeom g, double L, double mu,
+                                    const double* gs, double* UX, double* UY) {
+  __shared__ double w[2][NMAX];
+  __shared__ double c[4 * (NMAX / 2) + 2];
+  __shared__ double gd[NEAR_LAYERS][2 * NMAX];
+  __shared__ double ic[2], red[8];
+  const int t = threadIdx.x;
+  const StdFrame fr = nn.frames[v];
+  // f in the frame: rotated and relabelled
+  for (int k = t; k < N; k += blockDim.x) {
+    const int i = (k + fr.j0) % N;
+    const double fx = f[2 * o + i], fy = f[2 * o + N + i];
+    w[0][k] = fr.ct * fx - fr.st * fy;
+    w[1][k] = fr.st * fx + fr.ct * fy;
+  }
+  __syncthreads();
+  // its features (modes <= Kf)
+  const int pf = 2 * nn.Kf + 1, nbasis = 2 * pf;
+  for (int e = t; e < nbasis; e += blockDim.x) {
+    const int cc = e / pf, r = e - cc * pf;
+    const int q = r <= nn.Kf ? r : r - nn.Kf;
+    const int off = r <= nn.Kf ? 15 * N : 16 * N;
+    double acc = 0.0;
+    int m = 0;
+    for (int j = 0; j < N; ++j) {
+      acc = fma(w[cc][j], T[off + m], acc);
+      m += q;
+      if (m >= N) m -= N;
+    }
+    c[e] = (r <= nn.Kf ? acc : -acc) / N;
+  }
+  __syncthreads();
+  // the integral of f_K (the density's modes <= Kf, synthesised from c and turned back to the vesicle's
+  // axes) over the curve by the N-point trapezoid rule, the on-curve layer's quadrature
+  double ax = 0.0, ay = 0.0;
+  for (int k = t; k < N; k += blockDim.x) {
+    double a = c[0], b = c[pf];
+    int m = 0;
+    for (int q = 1; q <= nn.Kf; ++q) {
+      m += k;
+      if (m >= N) m -= N;
+      const double cs = T[15 * N + m], sn = T[16 * N + m];
+      a += 2.0 * (c[q] * cs - c[nn.Kf + q] * sn);
+      b += 2.0 * (c[pf + q] * cs - c[pf + nn.Kf + q] * sn);
+    }
+    const double sa = g.sa[o + (k + fr.j0) % N];
+    ax += (fr.ct * a + fr.st * b) * sa;
+    ay += (-fr.st * a + fr.ct * b) * sa;
+  }
+  ax = block_sum(ax, red);
+  ay = block_sum(ay, red);
+  if (t == 0) { ic[0] = ax * (2.0 * VS_PI / N); ic[1] = ay * (2.0 * VS_PI / N); }
+  // each layer's velocity features: the columns combined
+  const int po = 2 * nn.Kout + 1, cw = 2 * po;
+  for (int e = t; e < NEAR_LAYERS * cw; e += blockDim.x) {
+    const int d = e / cw, k = e - d * cw;
+    const float* row = nn.rows[d] + (int64_t)v * nn.ld;
+    double acc = 0.0;
+    for (int i = 0; i < nbasis; ++i) acc = fma(c[i], (double)row[i * cw + k], acc);
+    gd[d][k] = acc;
+  }
+  __syncthreads();
+  // synthesis at frame label k, back to the vesicle's label and axes, scaled
+  const double sc = L / mu, k0 = -L * log(L) / (4.0 * VS_PI * mu);
+  const double iux = 4.0 * VS_PI * mu * gs[0] / L, iuy = 4.0 * VS_PI * mu * gs[1] / L;  // off-curve integrals
+  const double icx = ic[0] / L, icy = ic[1] / L;                                     // on-curve integrals
+  for (int e = t; e < NEAR_LAYERS * N; e += blockDim.x) {
+    const int d = e / N, k = e - d * N;
+    const double* G = gd[d];
+    double a = G[0], b = G[po];
+    int m = 0;
+    for (int q = 1; q <= nn.Kout; ++q) {
+      m += k;
+      if (m >= N) m -= N;
+      const double cs = T[15 * N + m], sn = T[16 * N + m];
+      a += 2.0 * (G[q] * cs - G[nn.Kout + q] * sn);
+      b += 2.0 * (G[po + q] * cs - G[po + nn.Kout + q] * sn);
+    }
+    const int i = (k + fr.j0) % N;
+    const bool on = d == NEAR_LAYERS / 2;
+    UX[d * N + i] = sc * (fr.ct * a + fr.st * b) + k0 * (on ? icx : iux);
+    UY[d * N + i] = sc * (-fr.st * a + fr.ct * b) + k0 * (on ? icy : iuy);
+  }
+}
+
 // Layer points and exact layer velocities. Dynamic shared memory: near_layers_smem(N) bytes.
 inline size_t near_layers_smem(int N) {
   const int Nu = (int)std::ceil(std::sqrt((double)N)) * N;
   return (size_t)Nu * sizeof(float4) + 2 * (size_t)Nu * sizeof(float);
 }
 
+template <bool LEARNED>
 __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __restrict__ has_near,
                                                      const double* __restrict__ xy, const double* __restrict__ f,
                                                      PointGeom g, const double* __restrict__ length,
                                                      const double* __restrict__ tab,
                                                      const double* __restrict__ scratch,
                                                      const float* __restrict__ scratch32, int s, double mu,
-                                                     NearBufs nb) {
+                                                     NearBufs nb, NearNets nn) {
   extern __shared__ float4 smf[];
   const int v = vi.vid(blockIdx.x);
   if (!has_near[v]) return;
@@ -154,6 +263,13 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
     cim[comp][k] = (float)(im / N);
   }
   __syncthreads();
+  if constexpr (LEARNED) {  // the learned layers are those of the density's modes <= Kf: truncate it
+    for (int e = tid; e < 2 * nk; e += blockDim.x) {
+      const int comp = 2 + e / nk, k = e - (comp - 2) * nk;
+      if (k > nn.Kf) { cre[comp][k] = 0.f; cim[comp][k] = 0.f; }
+    }
+    __syncthreads();
+  }
   const double cx = cmean[0], cy = cmean[1];
   // upsampled curve (relative to the mean point), its speed, and g = f |X_alpha| (2 pi / Nu) / (4 pi mu)
   const float cw = (float)(2.0 * VS_PI / Nu / (4.0 * VS_PI * mu));
@@ -205,6 +321,16 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
   const float* Sh = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN : nullptr;
   const float* Sl = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::SL) * NN : nullptr;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2: -log|r| = hl2 log2|r|^2
+  if constexpr (LEARNED) {
+    for (int e = tid; e < 5 * N; e += blockDim.x) {
+      const int lay = e / N, j = e - lay * N;
+      const double d = c_layer_d[lay] * h;
+      LX[e] = xy[2 * o + j] + d * g.ty[o + j];
+      LY[e] = xy[2 * o + N + j] - d * g.tx[o + j];
+    }
+    near_learned_layers(nn, v, N, o, T, f, g, length[v], mu, gsum, UX, UY);
+    return;
+  }
   for (int e = tid; e < 5 * N; e += blockDim.x) {
     const int lay = e / N, j = e - lay * N;
     const double d = c_layer_d[lay] * h;
@@ -242,6 +368,43 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
     }
     UX[e] = ax;
     UY[e] = ay;
+  }
+}
+
+// Row v, columns [col, col + 2 (2K + 1)) of `rows` = the velocity features (modes <= K; a_0..a_K, b_1..b_K
+// of x, then of y) of layer d's velocities in nb.layer, for the vesicles flagged in has_near (the training
+// rows of the learned near field: the layers of the standardised points, whose labels are the frame's).
+__global__ void __launch_bounds__(NMAX) k_layer_features(VesIndex vi, const int* __restrict__ has_near,
+                                                         const double* __restrict__ layer, int d,
+                                                         const double* __restrict__ tab, int K,
+                                                         float* __restrict__ rows, int64_t ld, int col) {
+  __shared__ double u[2][NMAX];
+  const int v = vi.vid(blockIdx.x);
+  if (!has_near[v]) return;
+  const int N = vi.N[v];
+  const int64_t o = vi.off[v];
+  const int t = threadIdx.x;
+  const double* T = tab + vi.toff[v];
+  const double* L = layer + 30 * o;
+  if (t < N) {
+    u[0][t] = L[10 * N + d * N + t];
+    u[1][t] = L[15 * N + d * N + t];
+  }
+  __syncthreads();
+  const int per = 2 * K + 1;
+  float* row = rows + (int64_t)v * ld + col;
+  for (int e = t; e < 2 * per; e += blockDim.x) {
+    const int c = e / per, r = e - c * per;
+    const int q = r <= K ? r : r - K;
+    const int off = r <= K ? 15 * N : 16 * N;
+    double acc = 0.0;
+    int m = 0;
+    for (int j = 0; j < N; ++j) {
+      acc = fma(u[c][j], T[off + m], acc);
+      m += q;
+      if (m >= N) m -= N;
+    }
+    row[e] = (float)((r <= K ? acc : -acc) / N);
   }
 }
 

@@ -368,6 +368,8 @@ struct vs_suspension {
   struct vs_mlp* flow_adv = nullptr;  // learned advection and tension columns (hybrid mode), borrowed
   struct vs_mlp* flow_ten = nullptr;
   int flow_kf = 0, flow_kout = 0;
+  struct vs_mlp* near_net[NEAR_LAYERS] = {};  // learned near-field layers (hybrid mode), borrowed
+  int near_kf = 0, near_kout = 0;
   int cur = 0;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -1123,24 +1125,47 @@ vs_status relax_learned(vs_suspension* h, const double* xs, double* xo) {
   return VS_OK;
 }
 
+// Hybrid suspension with the near-field networks set (vs_set_near_networks).
+inline bool near_learned_on(const vs_suspension* h) { return h->p.mode == 1 && h->near_net[0] != nullptr; }
+
 // u += near-field correction of every (target, vesicle) pair the far field masked (Sec. 3.3). With
 // build_sources the operators of slot s are first built for the source vesicles that have near targets (a
-// step with learned advection and tension keeps no operators at X^n otherwise).
+// step with learned advection and tension keeps no operators at X^n otherwise). With the near-field networks
+// set (hybrid mode) the layer velocities come from them, and no operators are needed.
 vs_status near_field(vs_suspension* h, int s, bool build_sources = false) {
   const Layout& L = h->L;
   const VesIndex vi = h->D.vi();
   VS_CK(h, cudaMemsetAsync(h->has_near, 0, L.M * sizeof(int), h->stream), "near field");
   const int tgrid = (int)((L.P + 127) / 128);
   VS_LAUNCH(h, "k_near_mark", k_near_mark<<<tgrid, 128, 0, h->stream>>>(L.P, h->B.near_cnt, h->B.near_v, h->has_near));
-  if (build_sources) {
-    vs_status st = build_operators(h, h->xy, s, h->has_near);
-    if (st != VS_OK) return st;
-  }
   const size_t smem = near_layers_smem(L.nmax);
-  VS_LAUNCH(h, "k_near_layers", k_near_layers<<<L.M, 256, smem, h->stream>>>(vi, h->has_near, h->xy, h->B.f, h->B.pg(),
-                                                                            h->B.length, h->D.tab, h->scratch,
-                                                                            mixed(h) ? h->scratch32 : nullptr, s,
-                                                                            h->p.mu, h->nb));
+  if (near_learned_on(h)) {
+    // learned layer velocities (Sec. 3.3, Eq. NearFieldMap): the networks take the relaxation network's input
+    const int W = feat_width(feat_kmax(h->net_kmax, L.nmax));
+    VS_LAUNCH(h, "k_standardize", k_standardize<<<L.M, NMAX, 0, h->stream>>>(vi, h->xy, h->D.tab, h->xin, W,
+                                                                             h->frames, h->net_kmax, true));
+    NearNets nn{};
+    for (int d = 0; d < NEAR_LAYERS; ++d) {
+      vs_status st = mlp_forward(h->near_net[d], h->xin, L.M, true);
+      if (st != VS_OK) { h->msg = "near-field network forward failed"; return st; }
+      nn.rows[d] = mlp_output(h->near_net[d]);
+    }
+    nn.ld = h->near_net[0]->dims.back();
+    nn.Kf = h->near_kf;
+    nn.Kout = h->near_kout;
+    nn.frames = h->frames;
+    VS_LAUNCH(h, "k_near_layers<learned>", k_near_layers<true><<<L.M, 256, smem, h->stream>>>(
+                                               vi, h->has_near, h->xy, h->B.f, h->B.pg(), h->B.length, h->D.tab,
+                                               h->scratch, nullptr, s, h->p.mu, h->nb, nn));
+  } else {
+    if (build_sources) {
+      vs_status st = build_operators(h, h->xy, s, h->has_near);
+      if (st != VS_OK) return st;
+    }
+    VS_LAUNCH(h, "k_near_layers", k_near_layers<false><<<L.M, 256, smem, h->stream>>>(
+                                      vi, h->has_near, h->xy, h->B.f, h->B.pg(), h->B.length, h->D.tab, h->scratch,
+                                      mixed(h) ? h->scratch32 : nullptr, s, h->p.mu, h->nb, NearNets{}));
+  }
   if (5 * L.nmax <= NEAR_RBF_SMEM_N) {
     VS_LAUNCH(h, "k_near_rbf", k_near_rbf_smem<<<L.M, 512, near_rbf_smem(5 * L.nmax), h->stream>>>(
                                    vi, h->has_near, h->B.length, h->nb, h->err));
@@ -1616,7 +1641,9 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (h->p.near_field) {
     VS_A(dalloc(&h->nb.layer, 30 * L.P));
     VS_A(dalloc(&h->nb.phi, L.moff[L.M]));
-    VS_A(cudaFuncSetAttribute(k_near_layers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VS_A(cudaFuncSetAttribute(k_near_layers<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)near_layers_smem(L.nmax)));
+    VS_A(cudaFuncSetAttribute(k_near_layers<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)near_layers_smem(L.nmax)));
     if (5 * L.nmax <= NEAR_RBF_SMEM_N)
       VS_A(cudaFuncSetAttribute(k_near_rbf_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1926,6 +1953,99 @@ vs_status vs_flow_maps(vs_suspension* h, int32_t Kf, int32_t Kout, int32_t filte
     k_field_features<<<M, NMAX, 0, h->stream>>>(vi, sb, 1, h->D.tab, Kout, -1.0, true, ten, lt, (b + 1) * ct);
   }
   VS_CK(h, cudaGetLastError(), "flow maps");
+  return done(VS_OK);
+}
+
+vs_status vs_set_near_networks(vs_suspension* h, vs_mlp* const* nets, int32_t n, int32_t Kf, int32_t Kout) {
+  if (!h) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  if (!nets) {
+    drop_graphs(h);
+    for (auto& p : h->near_net) p = nullptr;
+    return VS_OK;
+  }
+  if (n != NEAR_LAYERS) { h->msg = "the near field takes one network per layer (5)"; return VS_ERR_INVALID_ARG; }
+  if (!h->p.near_field || !h->nb.layer) {
+    h->msg = "near-field networks need a suspension created with near_field = 1";
+    return VS_ERR_INVALID_ARG;
+  }
+  if (!h->net) { h->msg = "set the relaxation network (vs_set_network) first: the near-field networks share its input"; return VS_ERR_INVALID_ARG; }
+  if (Kf < 0 || Kout < 0 || Kf > L.nmax / 2 - 1 || Kout > L.nmax / 2 - 1) {
+    h->msg = "Kf and Kout must be in [0, N/2 - 1]";
+    return VS_ERR_INVALID_ARG;
+  }
+  const int W = feat_width(feat_kmax(h->net_kmax, L.nmax));
+  for (int d = 0; d < NEAR_LAYERS; ++d) {
+    const vs_mlp* m = nets[d];
+    if (!m || m->dims.front() != W || m->dims.back() != flow_adv_width(Kf, Kout) || m->Bcap < L.M) {
+      h->msg = "near-field networks: input width that of the relaxation network, output flow_adv_width(Kf, Kout), "
+               "batch capacity at least M";
+      return VS_ERR_INVALID_ARG;
+    }
+    if (m->stream != h->stream) { h->msg = "networks and suspension must share one stream"; return VS_ERR_INVALID_ARG; }
+  }
+  drop_graphs(h);
+  for (int d = 0; d < NEAR_LAYERS; ++d) h->near_net[d] = nets[d];
+  h->near_kf = Kf;
+  h->near_kout = Kout;
+  return VS_OK;
+}
+
+vs_status vs_near_maps(vs_suspension* h, int32_t Kf, int32_t Kout, int32_t filter_kmax, float* xin, float* out) {
+  if (!h || !xin || !out || filter_kmax < 0) return VS_ERR_INVALID_ARG;
+  const Layout& L = h->L;
+  for (int v = 0; v < L.M; ++v)
+    if (L.N[v] != L.nmax) { h->msg = "vs_near_maps needs one point count for all vesicles"; return VS_ERR_INVALID_ARG; }
+  if (Kf < 0 || Kout < 0 || Kf > L.nmax / 2 - 1 || Kout > L.nmax / 2 - 1) return VS_ERR_INVALID_ARG;
+  const VesIndex vi = h->D.vi();
+  const int M = L.M, nxt = 1 - h->cur;
+  const int W = feat_width(feat_kmax(filter_kmax, L.nmax));
+  const int width = flow_adv_width(Kf, Kout), cw = flow_col_adv(Kout);
+  // inputs and frames at the current points, the standardised points into xy_next
+  VS_LAUNCH(h, "k_standardize", k_standardize<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->D.tab, xin, W, h->frames,
+                                                                         filter_kmax, true));
+  VS_LAUNCH(h, "k_standard_points", k_standard_points<<<M, NMAX, 0, h->stream>>>(vi, h->xy, h->frames, h->xy_next));
+  VS_CK(h, cudaMemsetAsync(out, 0, (size_t)NEAR_LAYERS * M * width * sizeof(float), h->stream), "near maps");
+  // the self matrix at the standardised shapes in slot nxt (the cache of slot cur is left alone), with mu = 1
+  // as the columns are defined
+  vs_status st;
+  const double mu = h->p.mu;
+  h->p.mu = 1.0;
+  st = geometry(h, h->xy_next, false);
+  if (st == VS_OK) st = build_operators(h, h->xy_next, nxt, nullptr);
+  h->p.mu = mu;
+  if (st != VS_OK) return st;
+  double *psi = nullptr, *layer = nullptr;
+  int* ones = nullptr;
+  cudaError_t e = dalloc(&psi, 2 * L.P);
+  if (e == cudaSuccess) e = dalloc(&layer, 30 * L.P);
+  if (e == cudaSuccess) e = dalloc(&ones, M);
+  if (e == cudaSuccess) {
+    std::vector<int> one(M, 1);
+    e = cudaMemcpyAsync(ones, one.data(), M * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  const size_t smem = near_layers_smem(L.nmax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_near_layers<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto done = [&](vs_status r) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(psi); cudaFree(layer); cudaFree(ones);
+    return r;
+  };
+  if (e != cudaSuccess) { cuda_fail(h->msg, e, "vs_near_maps"); return done(VS_ERR_NOMEM); }
+  const NearBufs nbuf{layer, nullptr};
+  for (int b = 0; b < flow_basis(Kf); ++b) {
+    k_basis_velocity<<<M, NMAX, 0, h->stream>>>(vi, h->D.tab, b, Kf, psi);
+    // the layer velocities of psi_b at the standardised shape, mu = 1
+    k_near_layers<false><<<M, 256, smem, h->stream>>>(vi, ones, h->xy_next, psi, h->B.pg(), h->B.length, h->D.tab,
+                                                      h->scratch, mixed(h) ? h->scratch32 : nullptr, nxt, 1.0, nbuf,
+                                                      NearNets{});
+    for (int d = 0; d < NEAR_LAYERS; ++d)
+      k_layer_features<<<M, NMAX, 0, h->stream>>>(vi, ones, layer, d, h->D.tab, Kout, out + (int64_t)d * M * width,
+                                                  width, b * cw);
+  }
+  VS_CK(h, cudaGetLastError(), "near maps");
   return done(VS_OK);
 }
 
