@@ -48,6 +48,9 @@ FFS_DRAM_READ, FFS_DRAM_WRITE = 5.20e6, 197.19e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 # learned advection and tension: velocity modes expanded and column modes kept, training epochs
 FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
+# learned near field: every density mode below the Nyquist one (the membrane force's high modes carry most of
+# the near-field correction: on the oracle, keeping modes <= 24 of a 64-point vesicle leaves 20% of it out)
+NEAR_SNAPSHOTS, NEAR_EPOCHS = 16, 40
 
 
 def parse():
@@ -67,6 +70,7 @@ def parse():
     ap.add_argument("--no-near-arm", action="store_true", help="skip the plain step with near pairs")
     ap.add_argument("--no-uneven-arm", action="store_true", help="skip the plain step with 32/64/128-point vesicles")
     ap.add_argument("--no-implicit-arm", action="store_true", help="skip the fully implicit (GMRES) step")
+    ap.add_argument("--no-near-learned-arm", action="store_true", help="skip the learned near field")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
@@ -431,6 +435,73 @@ def implicit_arm(args, stream, tol=1e-8, multipole=False):
                           if multipole else "fp32 symmetric pair kernel (as the plain step)")}
 
 
+def near_learned_arm(args, stream):
+    """The learned near field (Sec. 3.3, Eq. NearFieldMap) on the near-field arm's suspension: five layer
+    networks (one per layer, density modes and columns up to N/2 - 1) trained on the GPU on exact layer columns
+    (vs_near_maps) of 16 snapshots of a differently seeded dense suspension, then a hybrid suspension whose
+    relaxation stays exact every step (exact_every = 1: only the near field is learned) against the plain step
+    from the same state. Reports the interaction velocity's difference after the first step, throughput, and
+    the shape error after 10 .. 300 steps (at the arm's time step, a tenth of the headline's)."""
+    import torch
+    from paper_2606_25569_b300 import binding, train
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    N, kmax = args.N, 16
+    K = N // 2 - 1
+    t0 = time.time()
+    X, rows = train.near_samples(poiseuille_dense(M=args.M, N=N, seed=105), NEAR_SNAPSHOTS, 15, stream, kmax, K, K)
+    t_data = time.time() - t0
+    res = [train.train_relaxation(X, rows[d], hidden=(1024, 1024, 1024), epochs=NEAR_EPOCHS, batch=1024, lr=1e-3,
+                                  lr_min=1e-5, beta=0.0, stream=stream, serve_batch=args.M) for d in range(5)]
+    t_train = time.time() - t0 - t_data
+    del X, rows
+    W = binding.feature_width(N, kmax)
+    rel = binding.Mlp([W, W], max_batch=args.M, stream=stream)  # input width only: the relaxation stays exact
+    rel.set_params(np.zeros(W * W + W))
+    wl = poiseuille_dense(args.M, N, seed=5, close_fraction=0.1, close_gap=0.7)
+    kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt / 10, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
+              near_field=True, stream=stream, use_graph=True)
+    plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
+    learned = binding.Suspension(wl.flat_xy(), wl.offsets, mode=1, exact_every=1, **kw)
+    learned.set_network(rel, 1.0, kmax)
+    learned.set_near_networks([r["net"] for r in res], K, K)
+    plain.step(1)
+    learned.step(1)
+    up, ul = plain.velocity(), learned.velocity()
+    near_pairs = plain.counters()["near_pairs"]
+    du = {"relative_l2": float(np.linalg.norm(ul - up) / np.linalg.norm(up)),
+          "max_over_max": float(np.max(np.abs(ul - up)) / np.max(np.abs(up)))}
+    out = {"workload": wl.name + ", dt = headline dt / 10", "unit": UNIT, "near_pairs_first_step": near_pairs,
+           "nets": {"dims": res[0]["dims"], "density_modes_Kf": K, "column_modes_Kout": K,
+                    "holdout_rel_err_mean_by_layer": [float(np.mean(r["holdout_err"])) for r in res],
+                    "train_samples": int(res[0]["train_err"].shape[0] + res[0]["holdout_err"].shape[0]),
+                    "data_seconds": round(t_data, 1), "train_seconds": round(t_train, 1)},
+           "interaction_velocity_difference_first_step": du}
+    errs, done = {}, 1
+    for S in (10, 100, 300):
+        plain.step(S - done)
+        learned.step(S - done)
+        plain.sync()
+        learned.sync()
+        e, _ = train.centred_shape_error(learned.positions(), plain.positions(), wl.counts)
+        errs[str(S)] = float(np.mean(e))
+        done = S
+    out["shape_error_mean_by_step"] = errs
+    n = max(4, args.steps)
+    for name, sus in (("plain", plain), ("learned", learned)):
+        ms = _time_steps(sus, n, stream)
+        prof = _profile_steps(sus, n)
+        out[name] = {"value": wl.M / (ms * 1e-3), "ms_per_step": ms,
+                     "near_kernels_ms_per_step": round(sum(v[0] for k, v in prof.items() if k.startswith("k_near"))
+                                                       / n, 4)}
+        sus.close()
+    out["note"] = ("near_kernels_ms_per_step: the library's k_near_* launches (layers, RBF, apply); the learned "
+                   "run's five network forwards run on the networks' handles and count in ms_per_step only")
+    for r in res:
+        r["net"].close()
+    rel.close()
+    return out
+
+
 def _time_steps(sus, n, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -702,6 +773,7 @@ def run_gpu(args):
     ff_alone = farfield_alone(stream) if rank == 0 and not args.no_farfield_alone else None
     near_arm = near_field_arm(args, stream) if rank == 0 and not args.no_near_arm else None
     uneven = uneven_arm(args, stream) if rank == 0 and not args.no_uneven_arm else None
+    near_learned = near_learned_arm(args, stream) if rank == 0 and not args.no_near_learned_arm else None
     implicit = implicit_arm(args, stream) if rank == 0 and not args.no_implicit_arm else None
     if implicit:
         implicit["plain_vs_implicit"] = (value / world) / implicit["value"]
@@ -740,6 +812,7 @@ def run_gpu(args):
                 "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
                 "hybrid_flow": arms.get("hybrid_flow"), "hybrid_flow_multipole": arms.get("hybrid_flow_multipole"),
                 "farfield_2000x128": ff_alone, "near_field": near_arm, "uneven": uneven, "implicit": implicit,
+                "near_field_learned": near_learned,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -378,7 +378,7 @@ vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, in
 /*
  * Learned part (Sec. 3.2-3.4): a fully connected network (ReLU hidden layers, affine output)
  * evaluated and trained on the tensor cores with BF16 operands and FP32 accumulation.
- *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 4096].
+ *  dims        host, nlayers+1 widths d_0 .. d_L, each a multiple of 16 in [16, 16384].
  *  max_batch   largest batch a call may pass.
  *  ncomp, beta the loss ||Yhat - Y||/||Y|| + beta ||D(Yhat - Y)||/||D Y|| averaged over the batch,
  *              D the periodic difference inside each of ncomp equal blocks of an output row

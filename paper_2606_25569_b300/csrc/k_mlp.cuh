@@ -18,7 +18,7 @@
 
 namespace vs {
 
-constexpr int MLP_MAX_OUT = 4096;  // widest output layer (the loss keeps one row of errors in shared memory)
+constexpr int MLP_MAX_OUT = 16384;  // widest layer
 
 
 constexpr int MM_BM = 128, MM_BN = 128, MM_BK = 64, MM_THREADS = 128;
@@ -277,7 +277,6 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
                                                   int d, int ncomp, float beta, float* __restrict__ g_f32,
                                                   __nv_bfloat16* __restrict__ g_bf, __nv_bfloat16* __restrict__ g_bfT,
                                                   int Bp, float* __restrict__ loss_b) {
-  __shared__ float e[MLP_MAX_OUT], de[MLP_MAX_OUT];
   __shared__ double red[4];
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
@@ -298,20 +297,22 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
   } else {
     y = const_cast<float*>(yraw);
   }
-  double se = 0.0, sy = 0.0;
+  // errors e_j and periodic differences de_j = e_{next(j)} - e_j within each component's block, recomputed
+  // from global memory where needed (rows up to MLP_MAX_OUT wide)
+  const float* yh = yhat + (int64_t)b * d;
+  const float* yr = y + (int64_t)b * d;
+  auto err = [&](int j) { return yh[j] - yr[j]; };
+  auto nxt = [&](int j) { const int blk = j / n, k = j - blk * n; return blk * n + ((k + 1 == n) ? 0 : k + 1); };
+  auto prv = [&](int j) { const int blk = j / n, k = j - blk * n; return blk * n + ((k == 0) ? n - 1 : k - 1); };
+  double se = 0.0, sy = 0.0, sde = 0.0, sdy = 0.0;
   for (int j = tid; j < d; j += blockDim.x) {
-    const float t = y[(int64_t)b * d + j];
-    e[j] = yhat[(int64_t)b * d + j] - t;
-    se += (double)e[j] * e[j];
+    const float t = yr[j], e = err(j);
+    se += (double)e * e;
     sy += (double)t * t;
-  }
-  __syncthreads();
-  double sde = 0.0, sdy = 0.0;
-  for (int j = tid; j < d; j += blockDim.x) {
-    const int blk = j / n, k = j - blk * n, nx = blk * n + ((k + 1 == n) ? 0 : k + 1);
-    de[j] = e[nx] - e[j];
-    const float dy = y[(int64_t)b * d + nx] - y[(int64_t)b * d + j];
-    sde += (double)de[j] * de[j];
+    const int nx = nxt(j);
+    const float de = err(nx) - e;
+    const float dy = yr[nx] - t;
+    sde += (double)de * de;
     sdy += (double)dy * dy;
   }
   se = block_sum(se, red);
@@ -323,8 +324,9 @@ __global__ void __launch_bounds__(128) k_mlp_loss(const float* __restrict__ yhat
   const double c1 = ne > 0 ? 1.0 / (ne * ny * batch) : 0.0;
   const double c2 = nde > 0 ? beta / (nde * ndy * batch) : 0.0;
   for (int j = tid; j < d; j += blockDim.x) {
-    const int blk = j / n, k = j - blk * n, pv = blk * n + ((k == 0) ? n - 1 : k - 1);
-    const float gv = (float)(c1 * e[j] + c2 * ((double)de[pv] - de[j]));
+    const int pv = prv(j);
+    const float e = err(j), de = err(nxt(j)) - e, dep = e - err(pv);
+    const float gv = (float)(c1 * e + c2 * ((double)dep - de));
     g_f32[(int64_t)b * d + j] = gv;
     const __nv_bfloat16 bv = __float2bfloat16_rn(gv);
     g_bf[(int64_t)b * d + j] = bv;

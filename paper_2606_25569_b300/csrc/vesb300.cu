@@ -2477,12 +2477,12 @@ vs_status vs_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_batch,
     return VS_ERR_INVALID_ARG;
   }
   for (int l = 0; l <= nlayers; ++l)
-    if (dims[l] < 16 || dims[l] % 16 != 0 || dims[l] > 4096) {
-      g_create_msg = "MLP widths must be multiples of 16 in [16, 4096]";
+    if (dims[l] < 16 || dims[l] % 16 != 0 || dims[l] > MLP_MAX_OUT) {
+      g_create_msg = "MLP widths must be multiples of 16 in [16, 16384]";
       return VS_ERR_INVALID_ARG;
     }
-  if (dims[nlayers] > MLP_MAX_OUT || dims[nlayers] % ncomp != 0) {
-    g_create_msg = "output width must be <= 4096 and divisible by ncomp";
+  if (dims[nlayers] % ncomp != 0) {
+    g_create_msg = "output width must be divisible by ncomp";
     return VS_ERR_INVALID_ARG;
   }
   vs_mlp* h = new (std::nothrow) vs_mlp();

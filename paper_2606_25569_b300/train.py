@@ -81,6 +81,34 @@ def hybrid_samples(wl, snapshots, every, stream, kmax, Kf, Kout, near_field=None
     return X, R, A, T
 
 
+def near_samples(wl, snapshots, every, stream, kmax, Kf, Kout, skip=0):
+    """Training data of the five near-field layer networks from one plain run: every `every` steps, each
+    vesicle's current shape gives the network input X (as for the relaxation network) and the exact layer
+    columns of the basis densities (vs_near_maps, density modes <= Kf, columns up to Kout). FP32 device
+    tensors: X (snapshots * M rows) and a list of five (snapshots * M) x width tensors, layer order -h .. h."""
+    import torch
+    s = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
+                           flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream)
+    M, W = wl.M, binding.feature_width(len(wl.xs[0]), kmax)
+    width = binding.flow_widths(Kf, Kout)[0]
+    if skip:
+        s.step(skip)
+    X = torch.empty(snapshots * M, W, dtype=torch.float32, device="cuda")
+    rows = [torch.empty(snapshots * M, width, dtype=torch.float32, device="cuda") for _ in range(5)]
+    buf = torch.empty(5, M, width, dtype=torch.float32, device="cuda")
+    for k in range(snapshots):
+        sl = slice(k * M, (k + 1) * M)
+        s.near_maps(Kf, Kout, kmax, X[sl], buf)
+        for d in range(5):
+            rows[d][sl].copy_(buf[d])
+        s.sync()
+        if k + 1 < snapshots:
+            s.step(every)
+    s.sync()
+    s.close()
+    return X, rows
+
+
 def relative_errors(net, X, Y, batch):
     """Per-sample ||Yhat - Y|| / ||Y|| of the network on (X, Y) (device tensors)."""
     import torch

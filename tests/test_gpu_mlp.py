@@ -48,7 +48,7 @@ def _check_layers(g, go, dims, tol_l2, tol_elem, what):
         check_network_output(a, b, tol_l2, tol_elem, "%s, %s %d" % (what, "W" if i < len(gw) else "b", i % len(gw)))
 
 
-@pytest.mark.parametrize("dims", [[512, 256], [256, 1024]])
+@pytest.mark.parametrize("dims", [[512, 256], [256, 1024], [128, 8192]])
 def test_single_layer_matches_oracle_per_element(dims):
     # one tensor-core GEMM with its bias: forward and gradient element by element
     batch = 384
