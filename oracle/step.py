@@ -31,7 +31,8 @@ too; here they keep the exact relaxation). With Params.flow_net set as well, ste
 take the learned advection and tension of oracle.learned (Eqs. advectionMap, advTenMap), except for the
 vesicles of that fallback set, which keep the exact ones. With Params.near_net set as well (and the near
 field on), step 2's near-field layer velocities of every source vesicle come from the learned near field
-(oracle.learned.near_layers_learned, Sec. 3.3) in every step. Initial tension (not given in the paper):
+(oracle.learned.near_layers_learned, Sec. 3.3) in every step; otherwise, with Params.near_yz, step 2's near
+field is the Ying-Zorin evaluation (oracle.yingzorin) instead of the layers and the RBF. Initial tension (not given in the paper):
 sigma^0 = -L^{-1} P (B X^0 + u_inf(X^0)) after redistributing X^0, which also fixes A_0, L_0.
 """
 import numpy as np
@@ -50,7 +51,7 @@ HYBRID_EXACT_GAP = 4.0
 class Params:
     def __init__(self, kappa=1.0, mu=1.0, dt=1e-4, flow_kind=0, flow_p=(0.0, 0.0, 0.0, 0.0),
                  near_field=False, corr_tol=0.01, relax_net=None, exact_every=0, exact_gap=HYBRID_EXACT_GAP,
-                 flow_net=None, near_net=None):
+                 flow_net=None, near_net=None, near_yz=False):
         self.kappa, self.mu, self.dt = float(kappa), float(mu), float(dt)
         self.flow_kind, self.flow_p = int(flow_kind), tuple(float(v) for v in flow_p)
         self.near_field, self.corr_tol = bool(near_field), float(corr_tol)
@@ -67,6 +68,8 @@ class Params:
         # (nets, Kf, Kout), nets the five layer networks (as flow_net's entries), layer order -h .. h: with
         # relax_net set and the near field on, the near-field layer velocities come from them
         self.near_net = near_net
+        # the near field by the Ying-Zorin scheme (oracle.yingzorin) instead of the layers and the RBF
+        self.near_yz = bool(near_yz)
 
 
 def relax_learned(x, y, net):
@@ -165,7 +168,11 @@ class Suspension:
                 def layers(v):
                     rows = [flow_row(self.xs[v], self.ys[v], net, kmax) for net in nets]
                     return near_layers_learned(self.xs[v], self.ys[v], fx[v], fy[v], rows, Kf, Kout, p.mu)
-            cx, cy = near_correction(self.xs, self.ys, fx, fy, p.mu, near, layers=layers)
+            if p.near_yz and layers is None:
+                from .yingzorin import near_correction_yz
+                cx, cy = near_correction_yz(self.xs, self.ys, fx, fy, p.mu, near)
+            else:
+                cx, cy = near_correction(self.xs, self.ys, fx, fy, p.mu, near, layers=layers)
             ux = ux + cx
             uy = uy + cy
         self.near_pairs = near
