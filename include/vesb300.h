@@ -88,6 +88,14 @@ typedef struct {
  * 32, 64 or 128 points and its per-chunk partial sums (16 bytes per point and group of 16 vesicles)
  * fit in 4 GiB, the per-target kernel otherwise. The two agree to FP32 rounding. */
 #define VS_FLAG_FARFIELD_PER_TARGET 32ull
+/* Near field by the Ying-Zorin scheme (Sec. 2.2.2, the caption of Fig. fig:near-singular: the near-singular
+ * integration of the paper's BIEM ground truth) instead of the five layers and the RBF of Sec. 3.3: at each
+ * near target, the closest point x0 of the source curve's trigonometric interpolant (Newton, FP64), the
+ * on-curve single layer there (the self rule's values interpolated along the membrane), the single layer at
+ * six points x0 + s i h/4 n (i = 1..6, on the target's side s) by FP32 trapezoid sums on the curve upsampled
+ * by ceil(sqrt(N)), and the interpolating polynomial in the distance. Needs near_field = 1; the learned near
+ * field (vs_set_near_networks) takes precedence in a hybrid suspension. */
+#define VS_FLAG_NEAR_YZ 64ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */

@@ -14,6 +14,8 @@
 //                 S[X, f_K] = L R^T shift(sum_i c_i Q_d,i) / mu - (L log L / (4 pi mu)) I_d for the density's
 //                 modes <= Kf, f_K, I_d the integral of f_K over the unit-length curve by the layer's own
 //                 quadrature (the N points on the curve, the upsampled curve off it);
+//                 With the Ying-Zorin scheme (VS_FLAG_NEAR_YZ; k_near_layers<NEAR_YZ> + k_near_yz) the layers
+//                 and the RBF are replaced by the evaluation of Sec. 2.2.2 at each near target (k_near_yz).
 //  k_near_rbf     (Phi + lam I) w = u_layers, Phi_ab = exp(-|x_a - x_b|^2 / (c h)^2), c = 2,
 //                 lam = 1e-3, by an FP32 Cholesky (the paper's precision): k_near_rbf_smem holds the
 //                 lower triangle in shared memory (5N <= 320), k_near_rbf works in the vesicle's scratch;
@@ -222,7 +224,24 @@ inline size_t near_layers_smem(int N) {
   return (size_t)Nu * sizeof(float4) + 2 * (size_t)Nu * sizeof(float);
 }
 
-template <bool LEARNED>
+// What k_near_layers computes for each near source vesicle: the exact layer velocities, the learned ones, or
+// (NEAR_YZ) the per-vesicle data of the Ying-Zorin evaluation (k_near_yz).
+enum : int { NEAR_EXACT = 0, NEAR_LEARNED = 1, NEAR_YZ = 2 };
+
+// Ying-Zorin data of a source vesicle at 30 off[v] in nb.layer (doubles): the FP64 Fourier coefficients
+// (re, im; k = 0..N/2) of x, y and of the on-curve single layer u0 = S f (x and y components), then gsum_x,
+// gsum_y, the mean point (cx, cy) and reach^2, then the upsampled sources as float4 (x - cx, y - cy, g_x, g_y).
+struct YzLayout {
+  int N;
+  __host__ __device__ int cx() const { return 0; }
+  __host__ __device__ int cy() const { return N + 2; }
+  __host__ __device__ int ux() const { return 2 * N + 4; }
+  __host__ __device__ int uy() const { return 3 * N + 6; }
+  __host__ __device__ int misc() const { return 4 * N + 8; }
+  __host__ __device__ int src() const { return 4 * N + 16; }  // doubles; 16-byte aligned
+};
+
+template <int MODE>
 __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __restrict__ has_near,
                                                      const double* __restrict__ xy, const double* __restrict__ f,
                                                      PointGeom g, const double* __restrict__ length,
@@ -261,9 +280,14 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
     if (comp < 2 && k == 0) cmean[comp] = re / N;
     cre[comp][k] = (comp < 2 && k == 0) ? 0.f : (float)(re / N);
     cim[comp][k] = (float)(im / N);
+    if (MODE == NEAR_YZ && comp < 2) {
+      double* Y = nb.layer + 30 * o + (comp == 0 ? YzLayout{N}.cx() : YzLayout{N}.cy());
+      Y[2 * k] = re / N;
+      Y[2 * k + 1] = im / N;
+    }
   }
   __syncthreads();
-  if constexpr (LEARNED) {  // the learned layers are those of the density's modes <= Kf: truncate it
+  if constexpr (MODE == NEAR_LEARNED) {  // the learned layers are those of the density's modes <= Kf: truncate it
     for (int e = tid; e < 2 * nk; e += blockDim.x) {
       const int comp = 2 + e / nk, k = e - (comp - 2) * nk;
       if (k > nn.Kf) { cre[comp][k] = 0.f; cim[comp][k] = 0.f; }
@@ -321,7 +345,47 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
   const float* Sh = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::S) * NN : nullptr;
   const float* Sl = scratch32 ? scratch32 + vi.moff[v] + (MatLayout::slot(s) + MatLayout::SL) * NN : nullptr;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2: -log|r| = hl2 log2|r|^2
-  if constexpr (LEARNED) {
+  if constexpr (MODE == NEAR_YZ) {
+    // the on-curve single layer u0 = S f, its Fourier coefficients, the sums and the upsampled sources
+    __shared__ double u0[2 * NMAX];
+    for (int r = tid; r < 2 * N; r += blockDim.x) {
+      double a = 0.0;
+      for (int k = 0; k < 2 * N; ++k) {
+        const int64_t e = (int64_t)r * 2 * N + k;
+        a = fma(Sh ? (double)Sh[e] + (double)Sl[e] : S[e], fl[k], a);
+      }
+      u0[r] = a;
+    }
+    __syncthreads();
+    const YzLayout lay{N};
+    double* Yv = nb.layer + 30 * o;
+    for (int e = tid; e < 2 * nk; e += blockDim.x) {
+      const int comp = e / nk, k = e - comp * nk;
+      double re = 0.0, im = 0.0;
+      int m = 0;
+      for (int j = 0; j < N; ++j) {
+        re = fma(u0[comp * N + j], T[15 * N + m], re);
+        im = fma(-u0[comp * N + j], T[16 * N + m], im);
+        m += k;
+        if (m >= N) m -= N;
+      }
+      double* C = Yv + (comp == 0 ? lay.ux() : lay.uy());
+      C[2 * k] = re / N;
+      C[2 * k + 1] = im / N;
+    }
+    if (tid == 0) {
+      double* mi = Yv + lay.misc();
+      mi[0] = gsum[0];
+      mi[1] = gsum[1];
+      mi[2] = cx;
+      mi[3] = cy;
+      mi[4] = (double)reach2;
+    }
+    float4* so = reinterpret_cast<float4*>(Yv + lay.src());
+    for (int q = tid; q < Nu; q += blockDim.x) so[q] = src[q];
+    return;
+  }
+  if constexpr (MODE == NEAR_LEARNED) {
     for (int e = tid; e < 5 * N; e += blockDim.x) {
       const int lay = e / N, j = e - lay * N;
       const double d = c_layer_d[lay] * h;
@@ -368,6 +432,157 @@ __global__ void __launch_bounds__(256) k_near_layers(VesIndex vi, const int* __r
     }
     UX[e] = ax;
     UY[e] = ay;
+  }
+}
+
+// Ying-Zorin evaluation (Sec. 2.2.2, Fig. fig:near-singular; the near-singular scheme of the paper's BIEM
+// ground truth): for every near (target, source vesicle) pair, u += S[X_v, f_v](x) by
+//  1. the closest point x0 = X(alpha0) of the source's trigonometric interpolant (Newton on
+//     (X - x) . X' = 0 from the nearest point, FP64);
+//  2. the on-curve single layer at alpha0 from the Fourier coefficients of u0 = S f;
+//  3. the single layer at x0 + s i beta h n, i = 1..YZ_M (s: the target's side), by FP32 trapezoid sums on
+//     the upsampled curve with the far field's log scaling;
+//  4. the interpolating polynomial in the distance t = |x - x0| (Lagrange form, FP64).
+// One warp per target point (grid-stride over targets); the lanes split the modes and the upsampled sources.
+constexpr int YZ_M = 6;
+constexpr double YZ_BETA = 0.25;
+constexpr int YZ_NEWTON = 30;
+
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// X, X', X'' of the interpolant with coefficients C (re, im pairs, k = 0..N/2) at alpha: each lane sums its
+// modes, the warp adds them (all lanes get the totals). The Nyquist mode enters the value only.
+__device__ inline void yz_curve(const double* C, int N, double a, double& v, double& d1, double& d2) {
+  const int lane = threadIdx.x & 31;
+  double sv = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int k = lane; k <= N / 2; k += 32) {
+    double sn, cs;
+    sincos(k * a, &sn, &cs);
+    const double re = C[2 * k], im = C[2 * k + 1];
+    const double c = re * cs - im * sn;  // Re(c_k e^{ik a})
+    if (k == 0) {
+      sv += re;
+    } else if (k == N / 2) {
+      sv += re * cs;
+    } else {
+      sv += 2.0 * c;
+      s1 += -2.0 * k * (re * sn + im * cs);
+      s2 += -2.0 * (double)k * k * c;
+    }
+  }
+  v = warp_sum_all(sv);
+  d1 = warp_sum_all(s1);
+  d2 = warp_sum_all(s2);
+}
+
+__global__ void __launch_bounds__(128) k_near_yz(int64_t P, const int32_t* __restrict__ owner,
+                                                 const int64_t* __restrict__ off, const int32_t* __restrict__ Nv,
+                                                 const int* __restrict__ near_cnt, const int* __restrict__ near_v,
+                                                 const double* __restrict__ xy, const double* __restrict__ length,
+                                                 const double* __restrict__ layer, double* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < P; t += warps) {
+    const int cnt = min(near_cnt[t], MAX_NEAR);
+    if (cnt == 0) continue;
+    const int a = owner[t];
+    const int64_t oa = off[a];
+    const int Na = Nv[a];
+    const int ia = (int)(t - oa);
+    const double px = xy[2 * oa + ia], py = xy[2 * oa + Na + ia];
+    double ax = 0.0, ay = 0.0;
+    for (int c = 0; c < cnt; ++c) {
+      const int v = near_v[t * MAX_NEAR + c];
+      const int N = Nv[v];
+      const int64_t o = off[v];
+      const YzLayout lay{N};
+      const double* Y = layer + 30 * o;
+      // 1. the nearest of the N points, then Newton on the interpolant
+      double best = 1e300;
+      int jb = 0;
+      for (int j = lane; j < N; j += 32) {
+        const double dx = xy[2 * o + j] - px, dy = xy[2 * o + N + j] - py;
+        const double d2 = dx * dx + dy * dy;
+        if (d2 < best) { best = d2; jb = j; }
+      }
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, s);
+        const int oj = __shfl_xor_sync(0xffffffffu, jb, s);
+        if (ob < best || (ob == best && oj < jb)) { best = ob; jb = oj; }
+      }
+      double al = 2.0 * VS_PI * jb / N;
+      double X, X1, X2, Yc, Y1, Y2;
+      for (int it = 0; it < YZ_NEWTON; ++it) {
+        yz_curve(Y + lay.cx(), N, al, X, X1, X2);
+        yz_curve(Y + lay.cy(), N, al, Yc, Y1, Y2);
+        const double g = (X - px) * X1 + (Yc - py) * Y1;
+        const double gp = X1 * X1 + Y1 * Y1 + (X - px) * X2 + (Yc - py) * Y2;
+        const double step = g / gp;
+        al -= step;
+        if (fabs(step) < 1e-15) break;
+      }
+      yz_curve(Y + lay.cx(), N, al, X, X1, X2);
+      yz_curve(Y + lay.cy(), N, al, Yc, Y1, Y2);
+      const double sp = sqrt(X1 * X1 + Y1 * Y1);
+      const double nx = Y1 / sp, ny = -X1 / sp;
+      const double sd = ((px - X) * nx + (py - Yc) * ny) >= 0.0 ? 1.0 : -1.0;
+      const double tq = sqrt((px - X) * (px - X) + (py - Yc) * (py - Yc));
+      // 2. the on-curve value at alpha0
+      double vx[YZ_M + 1], vy[YZ_M + 1], d;
+      yz_curve(Y + lay.ux(), N, al, vx[0], d, d);
+      yz_curve(Y + lay.uy(), N, al, vy[0], d, d);
+      // 3. the points along the normal: FP32 trapezoid sums on the upsampled curve
+      const double* mi = Y + lay.misc();
+      const double gsx = mi[0], gsy = mi[1], cx = mi[2], cy = mi[3];
+      const float reach2 = (float)mi[4];
+      const float4* src = reinterpret_cast<const float4*>(Y + lay.src());
+      const int Nu = near_rho(N) * N;
+      const double h = length[v] / N;
+      const float hl2 = -0.34657359027997264f;
+#pragma unroll
+      for (int i = 1; i <= YZ_M; ++i) {
+        const double di = sd * i * YZ_BETA * h;
+        const float tx = (float)(X + di * nx - cx), ty = (float)(Yc + di * ny - cy);
+        float le;
+        const float sc = pow2_scale(fmaf(tx, tx, ty * ty) + reach2, le);
+        float lx = 0.f, ly = 0.f, qx = 0.f, qy = 0.f;
+        for (int m = lane; m < Nu; m += 32) {
+          const float4 sm = src[m];
+          const float rx = tx - sm.x, ry = ty - sm.y;
+          const float r2 = fmaf(rx, rx, ry * ry);
+          const float lg = fast_lg2(r2 * sc);
+          const float q = fmaf(rx, sm.z, ry * sm.w) * fast_rcp(r2);
+          lx = fmaf(lg, sm.z, lx);
+          ly = fmaf(lg, sm.w, ly);
+          qx = fmaf(q, rx, qx);
+          qy = fmaf(q, ry, qy);
+        }
+        const double Lx = warp_sum_all((double)lx), Ly = warp_sum_all((double)ly);
+        const double Qx = warp_sum_all((double)qx), Qy = warp_sum_all((double)qy);
+        vx[i] = (double)hl2 * (Lx + (double)le * gsx) + Qx;
+        vy[i] = (double)hl2 * (Ly + (double)le * gsy) + Qy;
+      }
+      // 4. Lagrange interpolation at t in units of beta h
+      const double tt = tq / (YZ_BETA * h);
+#pragma unroll
+      for (int i = 0; i <= YZ_M; ++i) {
+        double w = 1.0;
+#pragma unroll
+        for (int j = 0; j <= YZ_M; ++j)
+          if (j != i) w *= (tt - j) / (double)(i - j);
+        ax = fma(w, vx[i], ax);
+        ay = fma(w, vy[i], ay);
+      }
+    }
+    if (lane == 0) {
+      u[2 * oa + ia] += ax;
+      u[2 * oa + Na + ia] += ay;
+    }
   }
 }
 

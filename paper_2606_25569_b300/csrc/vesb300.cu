@@ -1154,15 +1154,31 @@ vs_status near_field(vs_suspension* h, int s, bool build_sources = false) {
     nn.Kf = h->near_kf;
     nn.Kout = h->near_kout;
     nn.frames = h->frames;
-    VS_LAUNCH(h, "k_near_layers<learned>", k_near_layers<true><<<L.M, 256, smem, h->stream>>>(
+    VS_LAUNCH(h, "k_near_layers<learned>", k_near_layers<NEAR_LEARNED><<<L.M, 256, smem, h->stream>>>(
                                                vi, h->has_near, h->xy, h->B.f, h->B.pg(), h->B.length, h->D.tab,
                                                h->scratch, nullptr, s, h->p.mu, h->nb, nn));
+  } else if (h->p.flags & VS_FLAG_NEAR_YZ) {
+    // Ying-Zorin evaluation at each near target (Sec. 2.2.2) instead of the layers and the RBF
+    if (build_sources) {
+      vs_status st = build_operators(h, h->xy, s, h->has_near);
+      if (st != VS_OK) return st;
+    }
+    VS_LAUNCH(h, "k_near_layers<yz>", k_near_layers<NEAR_YZ><<<L.M, 256, smem, h->stream>>>(
+                                          vi, h->has_near, h->xy, h->B.f, h->B.pg(), h->B.length, h->D.tab,
+                                          h->scratch, mixed(h) ? h->scratch32 : nullptr, s, h->p.mu, h->nb,
+                                          NearNets{}));
+    const int yg = (int)std::min<int64_t>((L.P + 3) / 4, 148 * 32);
+    VS_LAUNCH(h, "k_near_yz", k_near_yz<<<yg, 128, 0, h->stream>>>(L.P, h->D.owner, h->D.off, h->D.N, h->B.near_cnt,
+                                                                   h->B.near_v, h->xy, h->B.length, h->nb.layer,
+                                                                   h->u));
+    VS_CK(h, cudaGetLastError(), "near field");
+    return VS_OK;
   } else {
     if (build_sources) {
       vs_status st = build_operators(h, h->xy, s, h->has_near);
       if (st != VS_OK) return st;
     }
-    VS_LAUNCH(h, "k_near_layers", k_near_layers<false><<<L.M, 256, smem, h->stream>>>(
+    VS_LAUNCH(h, "k_near_layers", k_near_layers<NEAR_EXACT><<<L.M, 256, smem, h->stream>>>(
                                       vi, h->has_near, h->xy, h->B.f, h->B.pg(), h->B.length, h->D.tab, h->scratch,
                                       mixed(h) ? h->scratch32 : nullptr, s, h->p.mu, h->nb, NearNets{}));
   }
@@ -1641,9 +1657,11 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (h->p.near_field) {
     VS_A(dalloc(&h->nb.layer, 30 * L.P));
     VS_A(dalloc(&h->nb.phi, L.moff[L.M]));
-    VS_A(cudaFuncSetAttribute(k_near_layers<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VS_A(cudaFuncSetAttribute(k_near_layers<NEAR_EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)near_layers_smem(L.nmax)));
-    VS_A(cudaFuncSetAttribute(k_near_layers<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VS_A(cudaFuncSetAttribute(k_near_layers<NEAR_LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)near_layers_smem(L.nmax)));
+    VS_A(cudaFuncSetAttribute(k_near_layers<NEAR_YZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)near_layers_smem(L.nmax)));
     if (5 * L.nmax <= NEAR_RBF_SMEM_N)
       VS_A(cudaFuncSetAttribute(k_near_rbf_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2027,7 +2045,7 @@ vs_status vs_near_maps(vs_suspension* h, int32_t Kf, int32_t Kout, int32_t filte
   }
   const size_t smem = near_layers_smem(L.nmax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_near_layers<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_near_layers<NEAR_EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   auto done = [&](vs_status r) {
     cudaStreamSynchronize(h->stream);
     cudaFree(psi); cudaFree(layer); cudaFree(ones);
@@ -2038,7 +2056,7 @@ vs_status vs_near_maps(vs_suspension* h, int32_t Kf, int32_t Kout, int32_t filte
   for (int b = 0; b < flow_basis(Kf); ++b) {
     k_basis_velocity<<<M, NMAX, 0, h->stream>>>(vi, h->D.tab, b, Kf, psi);
     // the layer velocities of psi_b at the standardised shape, mu = 1
-    k_near_layers<false><<<M, 256, smem, h->stream>>>(vi, ones, h->xy_next, psi, h->B.pg(), h->B.length, h->D.tab,
+    k_near_layers<NEAR_EXACT><<<M, 256, smem, h->stream>>>(vi, ones, h->xy_next, psi, h->B.pg(), h->B.length, h->D.tab,
                                                       h->scratch, mixed(h) ? h->scratch32 : nullptr, nxt, 1.0, nbuf,
                                                       NearNets{});
     for (int d = 0; d < NEAR_LAYERS; ++d)

@@ -427,3 +427,33 @@ def test_circle_makes_the_tension_system_singular_and_is_reported():
     xs, ys = [R * np.cos(t)], [R * np.sin(t)]
     with pytest.raises(binding.VsError, match="NOT_CONVERGED"):
         binding.Suspension(csr(xs, ys), offsets(xs), kappa=1.3, mu=1.0, dt=1e-2, corr_tol=0.01, flow_kind=0)
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_near_field_ying_zorin_matches_oracle(N):
+    # the near field by the Ying-Zorin scheme (Sec. 2.2.2): closest point, on-curve value, FP32 sums at the
+    # interpolation points (relative error about 1e-7 of the single layer there), FP64 interpolation
+    from oracle.step import Suspension as OS
+    xs, ys = _close_pair(N=N)
+    kw = dict(kappa=1.0, mu=0.9, dt=1e-3, flow_kind=1, flow_p=(0.5, 0, 0, 0), near_field=True)
+    o = OS(xs, ys, Params(near_yz=True, **kw))
+    r = OS(xs, ys, Params(**kw))
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, near_yz=True, **kw)
+    u_o = o.interaction_velocity()
+    u_r = r.interaction_velocity()
+    assert o.near_pairs
+    g.step()
+    ug = g.velocity()
+    counts = [len(x) for x in xs]
+    uo = np.concatenate([np.concatenate(v) for v in u_o])
+    ur = np.concatenate([np.concatenate(v) for v in u_r])
+    err = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+    diff = np.max(np.abs(ur - uo)) / np.max(np.abs(uo))
+    print("Ying-Zorin near field N=%d: GPU against the oracle %.2e (RBF scheme against Ying-Zorin %.2e)"
+          % (N, err, diff))
+    assert err <= 1e-6
+    assert diff >= 100 * err
+    # and the step that follows
+    o.step()
+    gx, gy = split(g.positions(), counts)
+    assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-9
