@@ -371,10 +371,33 @@ def near_field_arm(args, stream):
     c2 = sus.counters()
     sus.close()
     near_ms = {k: round(v[0] / n, 4) for k, v in prof.items() if k.startswith("k_near")}
-    return {"workload": wl.name + ", dt = headline dt / 10", "value": wl.M / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms, "steps_timed": n, "near_pairs_first_step": first,
-            "near_pairs_last_step": c2["near_pairs"], "corrections_total": c2["corrections"], "err": c2["err"],
-            "near_field_ms_per_step": round(sum(near_ms.values()), 4), "near_kernels_ms_per_step": near_ms}
+    out = {"workload": wl.name + ", dt = headline dt / 10", "value": wl.M / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms, "steps_timed": n, "near_pairs_first_step": first,
+           "near_pairs_last_step": c2["near_pairs"], "corrections_total": c2["corrections"], "err": c2["err"],
+           "near_field_ms_per_step": round(sum(near_ms.values()), 4), "near_kernels_ms_per_step": near_ms}
+    # the same suspension with the Ying-Zorin near field (Sec. 2.2.2), and the two schemes' interaction
+    # velocities from the same initial state
+    yz = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=dt, corr_tol=0.01,
+                            flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, use_graph=True,
+                            near_yz=True)
+    rbf = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=dt, corr_tol=0.01,
+                             flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream)
+    yz.step(1)
+    rbf.step(1)
+    uy_, ur_ = yz.velocity(), rbf.velocity()
+    rbf.close()
+    yz.step(2)
+    yz.sync()
+    ms_yz = _time_steps(yz, n, stream)
+    prof = _profile_steps(yz, n)
+    yz.close()
+    out["ying_zorin"] = {"value": wl.M / (ms_yz * 1e-3), "ms_per_step": ms_yz,
+                         "near_kernels_ms_per_step": {k: round(v[0] / n, 4) for k, v in prof.items()
+                                                      if k.startswith("k_near")},
+                         "rbf_against_ying_zorin_first_step": {
+                             "relative_l2": float(np.linalg.norm(ur_ - uy_) / np.linalg.norm(uy_)),
+                             "max_over_max": float(np.max(np.abs(ur_ - uy_)) / np.max(np.abs(uy_)))}}
+    return out
 
 
 def uneven_arm(args, stream):
