@@ -17,8 +17,8 @@ new points by its trigonometric interpolant, then the area/length correction (Se
 
 With the near field on, the far-field sum excludes the (target, source vesicle) pairs of the near rule
 (oracle.farfield) and the near-field correction of the density (oracle.nearfield, linear in it) is added
-to U, as U_near^{n+1} of the printed equation; its matrix is assembled column by column from unit
-densities.
+to U, as U_near^{n+1} of the printed equation (with Params.near_yz the Ying-Zorin evaluation, the ground
+truth's own near-singular scheme); its matrix is assembled column by column from unit densities.
 
 Pins (tests/test_oracle_implicit.py): for one vesicle the implicit step equals the advection with the
 operators at X^n followed by the relaxation with the operators at X^n (an algebraic identity of the two
@@ -54,10 +54,13 @@ def force_matrix(ops, kappa):
     return np.block([[-kappa * D4, Z, ops.Ten[:N]], [Z, -kappa * D4, ops.Ten[N:]]])
 
 
-def near_blocks(xs, ys, mu):
+def near_blocks(xs, ys, mu, yz=False):
     """Near pairs of the far-field rule and, per source vesicle b with near targets, the dense map from
-    f_b = [f_x; f_y] (2 N_b) to the near-field correction at every point ([u_x over all points; u_y])."""
+    f_b = [f_x; f_y] (2 N_b) to the near-field correction at every point ([u_x over all points; u_y]); yz: by
+    the Ying-Zorin evaluation (oracle.yingzorin) instead of the layers and the RBF."""
     from .nearfield import near_correction
+    from .yingzorin import near_correction_yz
+    correction = near_correction_yz if yz else near_correction
     zero = [np.zeros(len(x)) for x in xs]
     _, _, near = far_field(xs, ys, zero, zero, mu, near_mask=True)
     P = sum(len(x) for x in xs)
@@ -70,13 +73,13 @@ def near_blocks(xs, ys, mu):
             fx = [np.zeros(len(x)) for x in xs]
             fy = [np.zeros(len(x)) for x in xs]
             (fx if c < Nb else fy)[b][c % Nb] = 1.0
-            cx, cy = near_correction(xs, ys, fx, fy, mu, pairs)
+            cx, cy = correction(xs, ys, fx, fy, mu, pairs)
             Nmat[:, c] = np.concatenate([cx, cy])
         blocks[b] = Nmat
     return near, blocks
 
 
-def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p, near_field=False):
+def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p, near_field=False, near_yz=False):
     """X^{n+1}, sigma^{n+1} of Eq. time_step_sc1 for every vesicle (before redistribution)."""
     M = len(xs)
     Ns = [len(x) for x in xs]
@@ -86,7 +89,7 @@ def implicit_solve(xs, ys, kappa, mu, dt, flow_kind, flow_p, near_field=False):
     n_all = off[-1]
     ops = [Operators(x, y, kappa, mu) for x, y in zip(xs, ys)]
     F = [force_matrix(o, kappa) for o in ops]
-    near, blocks = near_blocks(xs, ys, mu) if near_field else ([], {})
+    near, blocks = near_blocks(xs, ys, mu, near_yz) if near_field else ([], {})
     near_set = set(near)
     A = np.zeros((n_all, n_all))
     b = np.zeros(n_all)
@@ -143,7 +146,8 @@ class ImplicitSuspension:
 
     def step(self):
         p = self.p
-        sol = implicit_solve(self.xs, self.ys, p.kappa, p.mu, p.dt, p.flow_kind, p.flow_p, near_field=p.near_field)
+        sol = implicit_solve(self.xs, self.ys, p.kappa, p.mu, p.dt, p.flow_kind, p.flow_p, near_field=p.near_field,
+                             near_yz=p.near_yz)
         nxs, nys, nsig = [], [], []
         for v, (x1, y1, s1) in enumerate(sol):
             xr, yr, alpha = redistribute(x1, y1)

@@ -109,20 +109,23 @@ def test_gmres_reports_non_convergence():
         g.set_gmres(tol=0.0)
 
 
-def test_implicit_step_with_near_field_matches_oracle():
+@pytest.mark.parametrize("yz", [False, True], ids=["layers-rbf", "ying-zorin"])
+def test_implicit_step_with_near_field_matches_oracle(yz):
     # a close pair (gap about half a point spacing) and a third vesicle: U_near^{n+1} of Eq. time_step_sc1 by
-    # the near-field rule (Sec. 3.3) in every GMRES product. The GPU near field is FP32 (layer sums and the
-    # RBF solve; about 1e-5 of the correction), so X is held to 1e-7 and sigma to 1e-4 per step.
+    # the near-field rule (Sec. 3.3, or the Ying-Zorin evaluation of Sec. 2.2.2) in every GMRES product. The
+    # GPU near field is FP32 (layer sums and the RBF solve, about 1e-5 of the correction; the Ying-Zorin sums
+    # about 1e-7), so X is held to 1e-7 and sigma to 1e-4 per step.
     xs, ys = [], []
     for v, (cx, cy, th) in enumerate(((-0.36, 0.0, 1.5), (0.36, 0.05, 1.5), (0.0, 1.4, 0.2))):
         rng = np.random.default_rng(20 + v)
         x, y = vesicle_outline(32, 0.7, 0.5, 5e-2, rng, th)
         xs.append(x + cx)
         ys.append(y + cy)
-    p = Params(kappa=KAPPA, mu=MU, dt=1e-3, flow_kind=1, flow_p=(1.0, 0, 0, 0), corr_tol=0.01, near_field=True)
+    p = Params(kappa=KAPPA, mu=MU, dt=1e-3, flow_kind=1, flow_p=(1.0, 0, 0, 0), corr_tol=0.01, near_field=True,
+               near_yz=yz)
     o = ImplicitSuspension(xs, ys, p)
     g = binding.Suspension(csr(xs, ys), offsets(xs), kappa=KAPPA, mu=MU, dt=1e-3, corr_tol=0.01, flow_kind=1,
-                           flow_p=(1.0, 0, 0, 0), mode=2, near_field=True, farfield_fp64=True)
+                           flow_p=(1.0, 0, 0, 0), mode=2, near_field=True, farfield_fp64=True, near_yz=yz)
     g.set_gmres(tol=1e-8, restart=30, max_iter=200)
     for k in range(3):
         o.step()

@@ -144,3 +144,36 @@ def test_near_field_solution_satisfies_both_lines():
     # and differs from the solution without the near field
     plain = implicit_solve(xs, ys, KAPPA, MU, dt, kind, fp)
     assert max(np.max(np.abs(a[2] - b[2])) for a, b in zip(sol, plain)) > 1e-6
+
+
+def test_near_field_ying_zorin_solution_satisfies_both_lines():
+    # as above with the Ying-Zorin evaluation as U_near^{n+1} (the ground truth's near-singular scheme)
+    from oracle.yingzorin import near_correction_yz
+    xs, ys = [], []
+    for v, (cx, cy) in enumerate(((-0.36, 0.0), (0.36, 0.05), (0.0, 1.4))):
+        x, y = _ves(32, 20 + v, cx, cy, R=0.5, theta=1.5 if v < 2 else 0.2)
+        xs.append(x)
+        ys.append(y)
+    dt, kind, fp = 1e-3, 1, (1.0, 0, 0, 0)
+    sol = implicit_solve(xs, ys, KAPPA, MU, dt, kind, fp, near_field=True, near_yz=True)
+    ops = [Operators(x, y, KAPPA, MU) for x, y in zip(xs, ys)]
+    fx, fy = [], []
+    for o, (x1, y1, s1) in zip(ops, sol):
+        f = force_matrix(o, KAPPA) @ np.concatenate([x1, y1, s1])
+        fx.append(f[:o.N])
+        fy.append(f[o.N:])
+    ux, uy, near = far_field(xs, ys, fx, fy, MU, near_mask=True)
+    assert near
+    cx, cy = near_correction_yz(xs, ys, fx, fy, MU, near)
+    ux, uy = ux + cx, uy + cy
+    off = 0
+    for v, (o, (x1, y1, s1)) in enumerate(zip(ops, sol)):
+        N = o.N
+        ub = np.concatenate(background(kind, fp, xs[v], ys[v]))
+        U = o.S @ np.concatenate([fx[v], fy[v]]) + np.concatenate([ux[off:off + N], uy[off:off + N]]) + ub
+        off += N
+        r1 = np.concatenate([x1, y1]) - np.concatenate([xs[v], ys[v]]) - dt * U
+        z = np.concatenate([x1, y1, s1])
+        mag = np.abs(o.S) @ (np.abs(force_matrix(o, KAPPA)) @ np.abs(z))
+        assert np.max(np.abs(r1)) <= 1e-12 * dt * np.max(mag), np.max(np.abs(r1))
+        assert np.max(np.abs(o.P @ U)) <= 1e-15 * np.max(np.abs(o.P) @ mag)
