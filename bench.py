@@ -427,12 +427,12 @@ def implicit_arm(args, stream, tol=1e-8, multipole=False):
     """The paper's ground-truth scheme on the headline suspension: the fully implicit step (Sec. 2.2.3,
     Eq. time_step_sc1) solved by restarted flexible GMRES (30 vectors) with the per-vesicle FP32
     preconditioner, every product through the symmetric far field (or the vesicle-multipole far field) and
-    the near-field rule. Reports the GMRES iterations per step and the kernels' shares beside the step time."""
+    the Ying-Zorin near field (the ground truth's near-singular scheme, Sec. 2.2.2). Reports the GMRES iterations per step and the kernels' shares beside the step time."""
     from paper_2606_25569_b300 import binding
     wl = workload(args)
     sus = binding.Suspension(wl.flat_xy(), wl.offsets, kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01,
                              flow_kind=wl.flow_kind, flow_p=wl.flow_p, near_field=True, stream=stream, mode=2,
-                             farfield_multipole=multipole)
+                             farfield_multipole=multipole, near_yz=True)
     sus.set_gmres(tol=tol, restart=30, max_iter=600)
     sus.step(1)
     sus.sync()
