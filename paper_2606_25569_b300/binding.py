@@ -88,6 +88,25 @@ FUNCTIONS = {
     "vs_mlp_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "vs_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_mlp_destroy": (None, [ctypes.c_void_p]),
+    "vs_ivnet_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_ivnet_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_ivnet_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_ivnet_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_ivnet_set_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "vs_ivnet_fit_affine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_double]),
+    "vs_ivnet_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "vs_ivnet_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "vs_ivnet_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_ivnet_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "vs_ivnet_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "vs_ivnet_destroy": (None, [ctypes.c_void_p]),
+    "vs_feature_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_standardize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_self_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
@@ -477,6 +496,86 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+class Ivnet:
+    """vs_ivnet: the paper's IVNet (Sec. 3.4.2) on the BF16 tensor-core GEMMs, with the paper's loss and AdamW.
+    Samples are rows [x(N), y(N)]."""
+
+    def __init__(self, N, C, nblocks, max_batch, beta=1.0, stream=None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        st = L.vs_ivnet_create(int(N), int(C), int(nblocks), int(max_batch), float(beta), _stream(stream),
+                               ctypes.byref(self._h))
+        if st != 0:
+            raise VsError(st, L.vs_ivnet_last_error(None).decode())
+        n = ctypes.c_int64()
+        self._check(L.vs_ivnet_num_params(self._h, ctypes.byref(n)))
+        self.nparam = n.value
+        self.N, self.C, self.nblocks = N, C, nblocks
+
+    def _check(self, st):
+        if st != 0:
+            raise VsError(st, lib().vs_ivnet_last_error(self._h).decode())
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().vs_ivnet_set_params(self._h, _ptr(p), len(p)))
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        self._check(lib().vs_ivnet_get_params(self._h, _ptr(p), len(p)))
+        return p
+
+    def set_affine(self, in_shift=None, in_scale=None, out_shift=None, out_scale=None):
+        arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+               for a in (in_shift, in_scale, out_shift, out_scale)]
+        for a in arr:
+            if a is not None and a.shape != (2 * self.N,):
+                raise ValueError("affine map of width %d expected" % (2 * self.N))
+        self._check(lib().vs_ivnet_set_affine(self._h, *[None if a is None else _ptr(a) for a in arr]))
+
+    def fit_affine(self, x_dev, y_dev, rows, rel_floor=0.0):
+        self._check(lib().vs_ivnet_fit_affine(self._h, _ptr(x_dev), _ptr(y_dev), int(rows), float(rel_floor)))
+
+    def forward(self, x_dev, y_dev, batch):
+        self._check(lib().vs_ivnet_forward(self._h, _ptr(x_dev), int(batch), _ptr(y_dev)))
+
+    def loss_grad(self, x_dev, y_dev, batch, want_grad=True):
+        loss = ctypes.c_float()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grad else None
+        self._check(lib().vs_ivnet_loss_grad(self._h, _ptr(x_dev), _ptr(y_dev), int(batch), ctypes.byref(loss),
+                                             _ptr(g) if want_grad else None, self.nparam))
+        return loss.value, g
+
+    def train_step(self, x_dev, y_dev, batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01,
+                   want_loss=False):
+        opt = VsAdamW(lr, beta1, beta2, eps, weight_decay)
+        loss = ctypes.c_float()
+        self._check(lib().vs_ivnet_train_step(self._h, _ptr(x_dev), _ptr(y_dev), int(batch), ctypes.byref(opt),
+                                              ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def sync(self):
+        self._check(lib().vs_ivnet_sync(self._h))
+
+    def close(self):
+        if self._h:
+            lib().vs_ivnet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def feature_points(feat_dev, rows, ld, N, K, out_dev, stream=None):
+    """vs_feature_points: samples [x(N), y(N)] of Fourier feature rows (device FP32)."""
+    st = lib().vs_feature_points(_ptr(feat_dev), int(rows), int(ld), int(N), int(K), _ptr(out_dev), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_feature_points failed")
 
 
 def standardize(xy_dev, offsets, kmax, xin_dev, frames_dev, stream=None):

@@ -20,6 +20,7 @@
 #include "k_farfield_loc.cuh"
 #include "k_geometry.cuh"
 #include "k_implicit.cuh"
+#include "k_ivnet.cuh"
 #include "k_mlp.cuh"
 #include "k_mp.cuh"
 #include "k_near.cuh"
@@ -2851,3 +2852,6 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
   }
   return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ERR_CUDA;
 }
+
+// IVNet (the paper's network architecture) on the MLP part's tensor-core GEMM.
+#include "ivnet_host.cuh"
