@@ -51,6 +51,8 @@ FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
 # learned near field: every density mode below the Nyquist one (the membrane force's high modes carry most of
 # the near-field correction: on the oracle, keeping modes <= 24 of a 64-point vesicle leaves 20% of it out)
 NEAR_SNAPSHOTS, NEAR_EPOCHS = 16, 40
+# IVNet relaxation map: C channels, n_b blocks (0.43 M parameters; the paper's relaxation network has 0.6 M)
+IV_C, IV_NB, IV_EPOCHS = 64, 8, 40
 
 
 def parse():
@@ -71,6 +73,7 @@ def parse():
     ap.add_argument("--no-uneven-arm", action="store_true", help="skip the plain step with 32/64/128-point vesicles")
     ap.add_argument("--no-implicit-arm", action="store_true", help="skip the fully implicit (GMRES) step")
     ap.add_argument("--no-near-learned-arm", action="store_true", help="skip the learned near field")
+    ap.add_argument("--no-ivnet-arm", action="store_true", help="skip the IVNet relaxation map")
     ap.add_argument("--hybrid-steps", type=int, default=1000, help="steps over which the hybrid shape error is taken")
     ap.add_argument("--burn-in", type=int, default=300, help="steps before the steady-state measurement (0: skip)")
     return ap.parse_args()
@@ -458,6 +461,61 @@ def implicit_arm(args, stream, tol=1e-8, multipole=False):
                           if multipole else "fp32 symmetric pair kernel (as the plain step)")}
 
 
+def ivnet_arm(args, stream):
+    """IVNet (Sec. 3.4.2, Fig. fig:net: the paper's architecture) against the MLP as the relaxation map: both
+    trained on the GPU on the same 128 k exact relaxation pairs (64 snapshots of a differently seeded dense
+    suspension), IVNet on point rows, the MLP on Fourier features; the held-out relative error of the
+    displacement compared in point space, and the forward time at the suspension's batch."""
+    import torch
+    from paper_2606_25569_b300 import train
+    from paper_2606_25569_b300.workloads import poiseuille_dense
+    N, kmax, M = args.N, 16, args.M
+    t0 = time.time()
+    X, Y = train.relaxation_samples(poiseuille_dense(M=M, N=N, seed=105), 64, 15, stream, kmax)
+    Xp, Yp = train.to_points(X, N, kmax), train.to_points(Y, N, kmax)
+    t_data = time.time() - t0
+    rm = train.train_relaxation(X, Y, hidden=(1024, 1024, 1024), epochs=40, batch=1024, lr=1e-3, lr_min=1e-5,
+                                stream=stream, serve_batch=M)
+    ri = train.train_ivnet(Xp, Yp, N, C=IV_C, nb=IV_NB, epochs=IV_EPOCHS, batch=1024, lr=1e-3, lr_min=1e-5,
+                           stream=stream, serve_batch=M)
+    n = X.shape[0]
+    ntr = n - int(round(0.1 * n))
+    # the MLP's held-out predictions in point space
+    pred = torch.empty_like(Y[ntr:])
+    for a in range(0, n - ntr, 1024):
+        b = min(a + 1024, n - ntr)
+        rm["net"].forward(X[ntr + a:ntr + b], pred[a:b], b - a)
+    rm["net"].sync()
+    pp, yp = train.to_points(pred, N, kmax), Yp[ntr:]
+    mlp_pts = (torch.linalg.norm(pp - yp, dim=1) / torch.linalg.norm(yp, dim=1)).cpu().numpy()
+
+    def fwd_ms(net, x, width):
+        y = torch.empty(M, width, dtype=torch.float32, device="cuda")
+        net.forward(x[:M], y, M)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            net.forward(x[:M], y, M)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 20
+
+    out = {"samples": n, "data_seconds": round(t_data, 1),
+           "mlp": {"dims": rm["dims"], "params": int(sum(a * b + b for a, b in zip(rm["dims"][:-1], rm["dims"][1:]))),
+                   "holdout_rel_err_mean": float(np.mean(mlp_pts)),
+                   "holdout_rel_err_features": float(np.mean(rm["holdout_err"])),
+                   "train_seconds": round(rm["train_seconds"], 1), "forward_ms_batch_M": fwd_ms(rm["net"], X, X.shape[1])},
+           "ivnet": {"channels": IV_C, "blocks": IV_NB, "levels": 2, "params": int(ri["params"]),
+                     "holdout_rel_err_mean": float(np.mean(ri["holdout_err"])), "train_steps": ri["steps"],
+                     "train_seconds": round(ri["train_seconds"], 1), "forward_ms_batch_M": fwd_ms(ri["net"], Xp, 2 * N)},
+           "epochs": 40, "batch": 1024,
+           "note": "held-out relative error of the relaxation displacement at the N points (the MLP's feature "
+                   "output converted to points); the MLP's own feature-space error beside it"}
+    rm["net"].close()
+    ri["net"].close()
+    return out
+
+
 def near_learned_arm(args, stream):
     """The learned near field (Sec. 3.3, Eq. NearFieldMap) on the near-field arm's suspension: five layer
     networks (one per layer, density modes and columns up to N/2 - 1) trained on the GPU on exact layer columns
@@ -797,6 +855,7 @@ def run_gpu(args):
     near_arm = near_field_arm(args, stream) if rank == 0 and not args.no_near_arm else None
     uneven = uneven_arm(args, stream) if rank == 0 and not args.no_uneven_arm else None
     near_learned = near_learned_arm(args, stream) if rank == 0 and not args.no_near_learned_arm else None
+    ivnet = ivnet_arm(args, stream) if rank == 0 and not args.no_ivnet_arm else None
     implicit = implicit_arm(args, stream) if rank == 0 and not args.no_implicit_arm else None
     if implicit:
         implicit["plain_vs_implicit"] = (value / world) / implicit["value"]
@@ -835,7 +894,7 @@ def run_gpu(args):
                 "farfield_multipole": arms.get("farfield_multipole"), "hybrid_multipole": arms.get("hybrid_multipole"),
                 "hybrid_flow": arms.get("hybrid_flow"), "hybrid_flow_multipole": arms.get("hybrid_flow_multipole"),
                 "farfield_2000x128": ff_alone, "near_field": near_arm, "uneven": uneven, "implicit": implicit,
-                "near_field_learned": near_learned,
+                "near_field_learned": near_learned, "ivnet_relaxation": ivnet,
                 "corrections": c["corrections"], "near_pairs_last_step": c["near_pairs"]}
         print(json.dumps(line))
     s.close()

@@ -435,30 +435,33 @@ const char* vs_mlp_last_error(const vs_mlp* m);
 void vs_mlp_destroy(vs_mlp* m);
 
 /*
- * IVNet (Sec. 3.4.2, Fig. fig:net), the paper's network, for periodic 1D signals: a sample is a vesicle's N
- * points as rows [x(N), y(N)] (in and out, 2N floats). Architecture: a lifting convolution (k = 3, 2 -> C
+ * IVNet (Sec. 3.4.2, Fig. fig:net), the paper's network, for periodic 1D signals: a sample is in_channels
+ * signals of a vesicle's N points (rows [s_0(N), s_1(N), ...], in_channels N floats: [x(N), y(N)] for two)
+ * and the output two (rows [x(N), y(N)]). Architecture: a lifting convolution (k = 3, in_channels -> C
  * channels), nblocks blocks of two stride-2 restriction levels (each two paths of C/2 channels, dilations 1
  * and 2, concatenated), two periodic linear interpolations by 2 each followed by a convolution (k = 3),
- * a mixing convolution (k = 1) added to the block's input, and a projection (k = 1, C -> 2); ReLU after
+ * the interpolations added to the descent's finer signals (r1, then the block's input), a mixing
+ * convolution (k = 1) added to the block's input, and a projection (k = 1, C -> 2); ReLU after
  * every convolution but the mixing ones and the projection; all convolutions circular. Every convolution
  * runs as a BF16 tensor-core GEMM of its gathered input columns (FP32 accumulation). Loss, affine maps
  * and AdamW as for vs_mlp (ncomp = 2).
- *  vs_ivnet_create: N a multiple of 4 in [8, 128], C a multiple of 32 in [32, 1024], nblocks >= 1,
- *    max_batch >= 1, beta >= 0 (the loss's derivative weight), stream as for vs_mlp_create.
+ *  vs_ivnet_create: N a multiple of 4 in [8, 128], in_channels in [1, 16], C a multiple of 32 in [32, 1024],
+ *    nblocks >= 1, max_batch >= 1, beta >= 0 (the loss's derivative weight), stream as for vs_mlp_create.
  *  Parameters (host FP32, vs_ivnet_num_params of them): per convolution in the order lift, (R_1^1, R_1^2,
  *    R_2^1, R_2^2, I_1, I_2, C_m) per block, projection: W (C_out x C_in x k, row-major) then b (C_out).
  *    set also clears the AdamW moments.
- *  vs_ivnet_set_affine / vs_ivnet_fit_affine: per-feature maps of inputs and outputs (2N each) as for
- *    vs_mlp_set_affine / vs_mlp_fit_affine.
- *  vs_ivnet_forward: x, y DEVICE FP32 rows (batch x 2N), batch <= max_batch; asynchronous.
+ *  vs_ivnet_set_affine / vs_ivnet_fit_affine: per-feature maps of inputs (in_channels N) and outputs (2N) as
+ *    for vs_mlp_set_affine / vs_mlp_fit_affine.
+ *  vs_ivnet_forward: x (batch x in_channels N), y (batch x 2N) DEVICE FP32 rows, batch <= max_batch;
+ *    asynchronous.
  *  vs_ivnet_loss_grad: loss (host) and, with grad non-NULL, the gradient (host, n = num_params); synchronous.
  *  vs_ivnet_train_step: one AdamW step on (x, y); loss (host) or NULL (then asynchronous).
  * vs_feature_points: samples of signals given by Fourier feature rows (modes <= K, the relaxation network's
  * layout, row stride ld) as rows [x(N), y(N)]; DEVICE FP32; asynchronous on cuda_stream.
  */
 typedef struct vs_ivnet vs_ivnet;
-vs_status vs_ivnet_create(int32_t N, int32_t C, int32_t nblocks, int32_t max_batch, float beta, void* cuda_stream,
-                          vs_ivnet** out);
+vs_status vs_ivnet_create(int32_t N, int32_t in_channels, int32_t C, int32_t nblocks, int32_t max_batch, float beta,
+                          void* cuda_stream, vs_ivnet** out);
 vs_status vs_ivnet_num_params(const vs_ivnet* net, int64_t* n);
 vs_status vs_ivnet_set_params(vs_ivnet* net, const float* params, int64_t n);
 vs_status vs_ivnet_get_params(vs_ivnet* net, float* params, int64_t n);

@@ -88,8 +88,8 @@ FUNCTIONS = {
     "vs_mlp_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "vs_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vs_mlp_destroy": (None, [ctypes.c_void_p]),
-    "vs_ivnet_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
-                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_ivnet_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_ivnet_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vs_ivnet_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_ivnet_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -502,17 +502,17 @@ class Ivnet:
     """vs_ivnet: the paper's IVNet (Sec. 3.4.2) on the BF16 tensor-core GEMMs, with the paper's loss and AdamW.
     Samples are rows [x(N), y(N)]."""
 
-    def __init__(self, N, C, nblocks, max_batch, beta=1.0, stream=None):
+    def __init__(self, N, C, nblocks, max_batch, beta=1.0, stream=None, in_channels=2):
         L = lib()
         self._h = ctypes.c_void_p()
-        st = L.vs_ivnet_create(int(N), int(C), int(nblocks), int(max_batch), float(beta), _stream(stream),
-                               ctypes.byref(self._h))
+        st = L.vs_ivnet_create(int(N), int(in_channels), int(C), int(nblocks), int(max_batch), float(beta),
+                               _stream(stream), ctypes.byref(self._h))
         if st != 0:
             raise VsError(st, L.vs_ivnet_last_error(None).decode())
         n = ctypes.c_int64()
         self._check(L.vs_ivnet_num_params(self._h, ctypes.byref(n)))
         self.nparam = n.value
-        self.N, self.C, self.nblocks = N, C, nblocks
+        self.N, self.C, self.nblocks, self.in_channels = N, C, nblocks, in_channels
 
     def _check(self, st):
         if st != 0:
@@ -530,9 +530,9 @@ class Ivnet:
     def set_affine(self, in_shift=None, in_scale=None, out_shift=None, out_scale=None):
         arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float32)
                for a in (in_shift, in_scale, out_shift, out_scale)]
-        for a in arr:
-            if a is not None and a.shape != (2 * self.N,):
-                raise ValueError("affine map of width %d expected" % (2 * self.N))
+        for a, d in zip(arr, (self.in_channels, self.in_channels, 2, 2)):
+            if a is not None and a.shape != (d * self.N,):
+                raise ValueError("affine map of width %d expected" % (d * self.N))
         self._check(lib().vs_ivnet_set_affine(self._h, *[None if a is None else _ptr(a) for a in arr]))
 
     def fit_affine(self, x_dev, y_dev, rows, rel_floor=0.0):

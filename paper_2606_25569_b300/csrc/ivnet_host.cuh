@@ -7,7 +7,7 @@
 // the oracle (per convolution W (C_out x C_in x k) then b).
 
 struct vs_ivnet {
-  int N = 0, C = 0, nb = 0, Bcap = 0;
+  int N = 0, C = 0, nb = 0, Bcap = 0, nch = 2;  // nch input signals of N points
   float beta = 1.f;
   std::vector<IvConv> cv;
   std::vector<int64_t> woff, boff;  // padded flat layout
@@ -20,11 +20,11 @@ struct vs_ivnet {
   std::vector<float*> r1, r2, u1, i1, u2, i2, cm;        // per block
   float *y16 = nullptr, *yrows = nullptr;
   float *gh = nullptr, *gi2 = nullptr, *gu2 = nullptr, *gi1 = nullptr, *gu1 = nullptr, *gr2 = nullptr, *gr1 = nullptr;
-  float *gm = nullptr, *dcol = nullptr, *dy16 = nullptr, *part = nullptr;
+  float *gm = nullptr, *dcol = nullptr, *dy16 = nullptr, *part = nullptr, *wpart = nullptr;
   __nv_bfloat16 *gb = nullptr, *gbT = nullptr;
   float *g32 = nullptr, *ynorm = nullptr, *loss_b = nullptr, *loss = nullptr;
   __nv_bfloat16 *lbf = nullptr, *lbfT = nullptr;
-  float* aff = nullptr;   // [in_shift 2N | in_scale 2N | out_shift 2N | out_scale 2N | 1/out_scale 2N]
+  float* aff = nullptr;   // [in_shift nch N | in_scale nch N | out_shift 2N | out_scale 2N | 1/out_scale 2N]
   double* stats = nullptr;
   bool has_in = false, has_out = false;
   unsigned* err = nullptr;
@@ -34,7 +34,8 @@ struct vs_ivnet {
 
 namespace {
 
-constexpr int IV_PARTS = 64;  // row chunks of the deterministic column sums
+constexpr int IV_PARTS = 512;  // row chunks of the deterministic column sums
+constexpr int IV_KCHUNK = 1024;  // rows per split of the weight-gradient GEMM (split K)
 
 // column sums of a rows x cols FP32 matrix: per-chunk partial sums, then the chunks in order
 __global__ void k_iv_colsum_part(const float* __restrict__ G, int64_t rows, int cols, float* __restrict__ part) {
@@ -68,12 +69,12 @@ void ivnet_free(vs_ivnet* h) {
   for (auto* vec : {&h->r1, &h->r2, &h->u1, &h->i1, &h->u2, &h->i2, &h->cm})
     for (auto* p : *vec) F(p);
   F(h->y16); F(h->yrows); F(h->gh); F(h->gi2); F(h->gu2); F(h->gi1); F(h->gu1); F(h->gr2); F(h->gr1);
-  F(h->gm); F(h->dcol); F(h->dy16); F(h->part); F(h->gb); F(h->gbT); F(h->g32); F(h->ynorm); F(h->loss_b);
+  F(h->gm); F(h->dcol); F(h->dy16); F(h->part); F(h->wpart); F(h->gb); F(h->gbT); F(h->g32); F(h->ynorm); F(h->loss_b);
   F(h->loss); F(h->lbf); F(h->lbfT); F(h->aff); F(h->stats); F(h->err);
 }
 
-vs_status iv_gemm(vs_ivnet* h, const GemmArgs& a) {
-  const dim3 grid((a.N + MM_BN - 1) / MM_BN, (a.M + MM_BM - 1) / MM_BM);
+vs_status iv_gemm(vs_ivnet* h, const GemmArgs& a, int splits = 1) {
+  const dim3 grid((a.N + MM_BN - 1) / MM_BN, (a.M + MM_BM - 1) / MM_BM, splits);
   k_gemm_bf16<<<grid, MM_THREADS, MM_SMEM, h->stream>>>(a);
   VS_CK(h, cudaGetLastError(), "ivnet gemm");
   return VS_OK;
@@ -96,7 +97,8 @@ vs_status iv_conv(vs_ivnet* h, int j, const float* src, int64_t ldx, int n_in, f
                   bool train) {
   const IvConv& c = h->cv[j];
   const int64_t M = (int64_t)Bp * (n_in / c.s);
-  k_iv_gather<<<iv_grid(M * c.kp), 256, 0, h->stream>>>(src, ldx, Bp, n_in, c, h->col[j], train ? h->colT[j] : nullptr);
+  k_iv_gather<<<iv_grid(M * c.kp), 256, 0, h->stream>>>(src, (int)ldx, Bp, n_in, c, h->col[j]);
+  if (train) k_iv_gatherT<<<iv_grid(M * c.kp), 256, 0, h->stream>>>(src, (int)ldx, Bp, n_in, c, h->colT[j]);
   GemmArgs a = gemm_args(h->col[j], c.kp, h->Wb[j], c.kp, (int)M, c.coutp, c.kp, h->err);
   a.bias = h->w + h->boff[j];
   a.act = (j == 0 || (j < (int)h->cv.size() - 1 && (j - 1) % 7 != 6)) ? EPI_RELU : EPI_NONE;
@@ -107,19 +109,20 @@ vs_status iv_conv(vs_ivnet* h, int j, const float* src, int64_t ldx, int n_in, f
 
 vs_status iv_forward(vs_ivnet* h, const float* x, int batch, bool out_map, bool train) {
   const int Bp = round_up(batch, MM_BM), N = h->N, C = h->C, hc = C / 2;
-  k_iv_rows_in<<<iv_grid((int64_t)Bp * N * 2), 256, 0, h->stream>>>(x, batch, Bp, N, h->has_in ? h->aff : nullptr,
-                                                                     h->aff + 2 * N, h->x0);
+  const int di = h->nch * N;
+  k_iv_rows_in<<<iv_grid((int64_t)Bp * di), 256, 0, h->stream>>>(x, batch, Bp, N, h->nch, h->has_in ? h->aff : nullptr,
+                                                                 h->aff + di, h->x0);
   vs_status st;
-  if ((st = iv_conv(h, 0, h->x0, 2, N, h->hs[0], C, Bp, train)) != VS_OK) return st;
+  if ((st = iv_conv(h, 0, h->x0, h->nch, N, h->hs[0], C, Bp, train)) != VS_OK) return st;
   for (int b = 0; b < h->nb; ++b) {
     const int j = 1 + 7 * b;
     if ((st = iv_conv(h, j, h->hs[b], C, N, h->r1[b], C, Bp, train)) != VS_OK) return st;
     if ((st = iv_conv(h, j + 1, h->hs[b], C, N, h->r1[b] + hc, C, Bp, train)) != VS_OK) return st;
     if ((st = iv_conv(h, j + 2, h->r1[b], C, N / 2, h->r2[b], C, Bp, train)) != VS_OK) return st;
     if ((st = iv_conv(h, j + 3, h->r1[b], C, N / 2, h->r2[b] + hc, C, Bp, train)) != VS_OK) return st;
-    k_iv_up<<<iv_grid((int64_t)Bp * N / 2 * C), 256, 0, h->stream>>>(h->r2[b], Bp, N / 4, C, h->u1[b]);
+    k_iv_up<<<iv_grid((int64_t)Bp * N / 2 * C), 256, 0, h->stream>>>(h->r2[b], h->r1[b], Bp, N / 4, C, h->u1[b]);
     if ((st = iv_conv(h, j + 4, h->u1[b], C, N / 2, h->i1[b], C, Bp, train)) != VS_OK) return st;
-    k_iv_up<<<iv_grid((int64_t)Bp * N * C), 256, 0, h->stream>>>(h->i1[b], Bp, N / 2, C, h->u2[b]);
+    k_iv_up<<<iv_grid((int64_t)Bp * N * C), 256, 0, h->stream>>>(h->i1[b], h->hs[b], Bp, N / 2, C, h->u2[b]);
     if ((st = iv_conv(h, j + 5, h->u2[b], C, N, h->i2[b], C, Bp, train)) != VS_OK) return st;
     if ((st = iv_conv(h, j + 6, h->i2[b], C, N, h->cm[b], C, Bp, train)) != VS_OK) return st;
     k_iv_add<<<iv_grid((int64_t)Bp * N * C), 256, 0, h->stream>>>(h->hs[b], h->cm[b], (int64_t)Bp * N * C, h->hs[b + 1]);
@@ -127,8 +130,8 @@ vs_status iv_forward(vs_ivnet* h, const float* x, int batch, bool out_map, bool 
   const int jl = (int)h->cv.size() - 1;
   if ((st = iv_conv(h, jl, h->hs[h->nb], C, N, h->y16, 16, Bp, train)) != VS_OK) return st;
   const bool om = out_map && h->has_out;
-  k_iv_rows_out<<<iv_grid((int64_t)batch * 2 * N), 256, 0, h->stream>>>(h->y16, batch, N, om ? h->aff + 6 * N : nullptr,
-                                                                          om ? h->aff + 4 * N : nullptr, h->yrows);
+  k_iv_rows_out<<<iv_grid((int64_t)batch * 2 * N), 256, 0, h->stream>>>(h->y16, batch, N, om ? h->aff + 2 * di + 2 * N : nullptr,
+                                                                          om ? h->aff + 2 * di : nullptr, h->yrows);
   VS_CK(h, cudaGetLastError(), "ivnet forward");
   return VS_OK;
 }
@@ -141,11 +144,16 @@ vs_status iv_back(vs_ivnet* h, int j, const float* g, int64_t ldg, const float* 
   const IvConv& c = h->cv[j];
   const int64_t M = (int64_t)Bp * (n_in / c.s);
   k_iv_grad<<<iv_grid(M * c.coutp), 256, 0, h->stream>>>(g, ldg, post, M, c.coutp, h->gm, h->gb, h->gbT);
+  // the weight gradient: K = M rows split into chunks of IV_KCHUNK, partial products summed in order
+  const int S = (int)((M + IV_KCHUNK - 1) / IV_KCHUNK);
   GemmArgs a = gemm_args(h->gbT, M, h->colT[j], M, c.coutp, c.kp, (int)M, h->err);
-  a.out_f32 = h->g + h->woff[j];
+  a.out_f32 = h->wpart;
   a.ld_f32 = c.kp;
-  vs_status st = iv_gemm(h, a);
+  a.kchunk = IV_KCHUNK;
+  a.split_ld = (int64_t)c.coutp * c.kp;
+  vs_status st = iv_gemm(h, a, S);
   if (st != VS_OK) return st;
+  k_iv_splitsum<<<iv_grid(a.split_ld), 256, 0, h->stream>>>(h->wpart, S, a.split_ld, h->g + h->woff[j]);
   k_iv_colsum_part<<<dim3((c.coutp + 127) / 128, IV_PARTS), 128, 0, h->stream>>>(h->gm, M, c.coutp, h->part);
   k_iv_colsum_final<<<(c.coutp + 127) / 128, 128, 0, h->stream>>>(h->part, c.coutp, h->g + h->boff[j]);
   if (dsrc) {
@@ -165,9 +173,9 @@ vs_status iv_zero(vs_ivnet* h, float* p, int64_t n) {
 }
 
 vs_status iv_backward(vs_ivnet* h, const float* y, int batch) {
-  const int Bp = round_up(batch, MM_BM), N = h->N, C = h->C, hc = C / 2, d = 2 * N;
-  const float* ysh = h->has_out ? h->aff + 4 * N : nullptr;
-  k_mlp_loss<<<Bp, 128, 0, h->stream>>>(h->yrows, y, ysh, h->aff + 8 * N, h->ynorm, batch, d, 2, h->beta, h->g32,
+  const int Bp = round_up(batch, MM_BM), N = h->N, C = h->C, hc = C / 2, d = 2 * N, di = h->nch * N;
+  const float* ysh = h->has_out ? h->aff + 2 * di : nullptr;
+  k_mlp_loss<<<Bp, 128, 0, h->stream>>>(h->yrows, y, ysh, h->aff + 2 * di + 4 * N, h->ynorm, batch, d, 2, h->beta, h->g32,
                                         h->lbf, h->lbfT, Bp, h->loss_b);
   k_mean<<<1, 32, 0, h->stream>>>(h->loss_b, batch, h->loss);
   k_iv_rows_grad<<<iv_grid((int64_t)Bp * N * 16), 256, 0, h->stream>>>(h->g32, Bp, N, h->dy16);
@@ -184,13 +192,16 @@ vs_status iv_backward(vs_ivnet* h, const float* y, int batch) {
     if ((st = iv_back(h, j + 6, h->gh, C, nullptr, h->gi2, C, N, Bp)) != VS_OK) return st;
     if ((st = iv_zero(h, h->gu2, full)) != VS_OK) return st;
     if ((st = iv_back(h, j + 5, h->gi2, C, h->i2[b], h->gu2, C, N, Bp)) != VS_OK) return st;
+    // u2 = up(i1) + h_b: the skip's gradient goes to h_b
+    k_iv_add<<<iv_grid(full), 256, 0, h->stream>>>(h->gh, h->gu2, full, h->gh);
     if ((st = iv_zero(h, h->gi1, half)) != VS_OK) return st;
     k_iv_up_T<<<iv_grid(half), 256, 0, h->stream>>>(h->gu2, Bp, N / 2, C, h->gi1);
     if ((st = iv_zero(h, h->gu1, half)) != VS_OK) return st;
     if ((st = iv_back(h, j + 4, h->gi1, C, h->i1[b], h->gu1, C, N / 2, Bp)) != VS_OK) return st;
     if ((st = iv_zero(h, h->gr2, quarter)) != VS_OK) return st;
     k_iv_up_T<<<iv_grid(quarter), 256, 0, h->stream>>>(h->gu1, Bp, N / 4, C, h->gr2);
-    if ((st = iv_zero(h, h->gr1, half)) != VS_OK) return st;
+    // u1 = up(r2) + r1: the skip's gradient starts r1's
+    VS_CK(h, cudaMemcpyAsync(h->gr1, h->gu1, half * sizeof(float), cudaMemcpyDeviceToDevice, h->stream), "ivnet");
     if ((st = iv_back(h, j + 2, h->gr2, C, h->r2[b], h->gr1, C, N / 2, Bp)) != VS_OK) return st;
     if ((st = iv_back(h, j + 3, h->gr2 + hc, C, h->r2[b] + hc, h->gr1, C, N / 2, Bp)) != VS_OK) return st;
     if ((st = iv_back(h, j, h->gr1, C, h->r1[b], h->gh, C, N, Bp)) != VS_OK) return st;
@@ -236,25 +247,31 @@ void iv_unpad(const vs_ivnet* h, const std::vector<float>& q, float* p) {
 
 extern "C" {
 
-vs_status vs_ivnet_create(int32_t N, int32_t C, int32_t nblocks, int32_t max_batch, float beta, void* cuda_stream,
-                          vs_ivnet** out) {
+vs_status vs_ivnet_create(int32_t N, int32_t in_channels, int32_t C, int32_t nblocks, int32_t max_batch, float beta,
+                          void* cuda_stream, vs_ivnet** out) {
   if (!out) return VS_ERR_INVALID_ARG;
   *out = nullptr;
   if (N < 8 || N > NMAX || N % 4 != 0 || C < 32 || C > 1024 || C % 32 != 0 || nblocks < 1 || max_batch < 1 ||
-      !(beta >= 0.f)) {
-    g_create_msg = "IVNet needs N a multiple of 4 in [8, 128], C a multiple of 32 in [32, 1024], nblocks >= 1";
+      in_channels < 1 || in_channels > 16 || !(beta >= 0.f)) {
+    g_create_msg = "IVNet needs N a multiple of 4 in [8, 128], 1 to 16 input signals, C a multiple of 32 in "
+                   "[32, 1024], nblocks >= 1";
+    return VS_ERR_INVALID_ARG;
+  }
+  if ((int64_t)round_up(max_batch, MM_BM) * N * round_up(3 * C, 16) >= (1ll << 31)) {
+    g_create_msg = "IVNet: max_batch x N x 3C must stay below 2^31 (32-bit column indices)";
     return VS_ERR_INVALID_ARG;
   }
   vs_ivnet* h = new (std::nothrow) vs_ivnet();
   if (!h) return VS_ERR_NOMEM;
   h->N = N; h->C = C; h->nb = nblocks; h->Bcap = round_up(max_batch, MM_BM); h->beta = beta;
+  h->nch = in_channels;
   h->stream = (cudaStream_t)cuda_stream;
   const int hc = C / 2;
   auto add = [&](int ci, int co, int k, int s, int d) {
     IvConv c{ci, co, k, s, d, round_up(ci * k, 16), std::max(16, round_up(co, 16))};
     h->cv.push_back(c);
   };
-  add(2, C, 3, 1, 1);
+  add(in_channels, C, 3, 1, 1);
   for (int b = 0; b < nblocks; ++b) {
     add(C, hc, 3, 2, 1); add(C, hc, 3, 2, 2); add(C, hc, 3, 2, 1); add(C, hc, 3, 2, 2);
     add(C, C, 3, 1, 1); add(C, C, 3, 1, 1); add(C, C, 1, 1, 1);
@@ -294,7 +311,7 @@ vs_status vs_ivnet_create(int32_t N, int32_t C, int32_t nblocks, int32_t max_bat
     mk = std::max(mk, M * c.kp);
     mc = std::max(mc, M * c.coutp);
   }
-  VS_I(dalloc(&h->x0, B * N * 2));
+  VS_I(dalloc(&h->x0, B * N * in_channels));
   for (int b = 0; b <= nblocks; ++b) { float* p; VS_I(dalloc(&p, full)); h->hs.push_back(p); }
   for (int b = 0; b < nblocks; ++b) {
     float* p;
@@ -311,17 +328,23 @@ vs_status vs_ivnet_create(int32_t N, int32_t C, int32_t nblocks, int32_t max_bat
   VS_I(dalloc(&h->gu1, full / 2)); VS_I(dalloc(&h->gr2, full / 4)); VS_I(dalloc(&h->gr1, full / 2));
   VS_I(dalloc(&h->gm, mc)); VS_I(dalloc(&h->gb, mc)); VS_I(dalloc(&h->gbT, mc)); VS_I(dalloc(&h->dcol, mk));
   VS_I(dalloc(&h->dy16, B * N * 16)); VS_I(dalloc(&h->part, (int64_t)IV_PARTS * std::max(C, 16)));
+  int64_t wmax = 0;
+  for (const IvConv& c : h->cv) wmax = std::max(wmax, (int64_t)c.coutp * c.kp);
+  VS_I(dalloc(&h->wpart, wmax * ((B * N + IV_KCHUNK - 1) / IV_KCHUNK)));
   VS_I(dalloc(&h->g32, B * 2 * N)); VS_I(dalloc(&h->ynorm, B * 2 * N)); VS_I(dalloc(&h->loss_b, B));
   VS_I(dalloc(&h->loss, 1)); VS_I(dalloc(&h->lbf, B * 2 * N)); VS_I(dalloc(&h->lbfT, B * 2 * N));
-  VS_I(dalloc(&h->aff, 10 * (int64_t)N)); VS_I(dalloc(&h->stats, 4 * (int64_t)N)); VS_I(dalloc(&h->err, 1));
+  const int64_t di = (int64_t)in_channels * N;
+  VS_I(dalloc(&h->aff, 2 * di + 6 * (int64_t)N)); VS_I(dalloc(&h->stats, 2 * std::max(di, 2 * (int64_t)N)));
+  VS_I(dalloc(&h->err, 1));
   VS_I(cudaMemset(h->err, 0, sizeof(unsigned)));
   VS_I(cudaMemset(h->w, 0, h->npad * sizeof(float)));
   VS_I(cudaMemset(h->m, 0, h->npad * sizeof(float)));
   VS_I(cudaMemset(h->v, 0, h->npad * sizeof(float)));
   VS_I(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM));
   {
-    std::vector<float> a(10 * (size_t)N, 0.f);
-    for (int i = 0; i < 2 * N; ++i) { a[2 * N + i] = 1.f; a[6 * N + i] = 1.f; a[8 * N + i] = 1.f; }
+    std::vector<float> a(2 * di + 6 * (size_t)N, 0.f);
+    for (int i = 0; i < di; ++i) a[di + i] = 1.f;
+    for (int i = 0; i < 2 * N; ++i) { a[2 * di + 2 * N + i] = 1.f; a[2 * di + 4 * N + i] = 1.f; }
     VS_I(cudaMemcpy(h->aff, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
 #undef VS_I
@@ -362,16 +385,18 @@ vs_status vs_ivnet_get_params(vs_ivnet* h, float* p, int64_t n) {
 vs_status vs_ivnet_set_affine(vs_ivnet* h, const float* in_shift, const float* in_scale, const float* out_shift,
                               const float* out_scale) {
   if (!h) return VS_ERR_INVALID_ARG;
-  const int d = 2 * h->N;
-  std::vector<float> a(5 * (size_t)d);
-  for (int j = 0; j < d; ++j) {
+  const int di = h->nch * h->N, d = 2 * h->N;
+  std::vector<float> a(2 * (size_t)di + 3 * (size_t)d);
+  for (int j = 0; j < di; ++j) {
     a[j] = in_shift ? in_shift[j] : 0.f;
-    a[d + j] = in_scale ? in_scale[j] : 1.f;
-    a[2 * d + j] = out_shift ? out_shift[j] : 0.f;
+    a[di + j] = in_scale ? in_scale[j] : 1.f;
+  }
+  for (int j = 0; j < d; ++j) {
+    a[2 * di + j] = out_shift ? out_shift[j] : 0.f;
     const float t = out_scale ? out_scale[j] : 1.f;
     if (!(t != 0.f) || !std::isfinite(t)) return VS_ERR_INVALID_ARG;
-    a[3 * d + j] = t;
-    a[4 * d + j] = 1.f / t;
+    a[2 * di + d + j] = t;
+    a[2 * di + 2 * d + j] = 1.f / t;
   }
   for (float x : a)
     if (!std::isfinite(x)) return VS_ERR_INVALID_ARG;
@@ -384,21 +409,24 @@ vs_status vs_ivnet_set_affine(vs_ivnet* h, const float* in_shift, const float* i
 
 vs_status vs_ivnet_fit_affine(vs_ivnet* h, const float* x, const float* y, int32_t rows, double rel_floor) {
   if (!h || !x || !y || rows < 1 || !(rel_floor >= 0.0)) return VS_ERR_INVALID_ARG;
-  const int d = 2 * h->N;
-  std::vector<double> st(2 * (size_t)d);
+  const int dims[2] = {h->nch * h->N, 2 * h->N};
+  const int dmx = std::max(dims[0], dims[1]);
+  std::vector<double> st(2 * (size_t)dmx);
   std::vector<float> sh[2], sc[2];
   for (int pass = 0; pass < 2; ++pass) {
-    k_colstats<<<(d + 127) / 128, 128, 0, h->stream>>>(pass ? y : x, rows, d, h->stats, h->stats + d);
+    const int d = dims[pass];
+    k_colstats<<<(d + 127) / 128, 128, 0, h->stream>>>(pass ? y : x, rows, d, h->stats, h->stats + dmx);
     VS_CK(h, cudaGetLastError(), "fit affine");
-    VS_CK(h, cudaMemcpyAsync(st.data(), h->stats, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "fit affine");
+    VS_CK(h, cudaMemcpyAsync(st.data(), h->stats, 2 * dmx * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+          "fit affine");
     VS_CK(h, cudaStreamSynchronize(h->stream), "fit affine");
     double sdmax = 0.0;
     for (int j = 0; j < d; ++j)
-      if (std::isfinite(st[d + j])) sdmax = std::max(sdmax, st[d + j]);
+      if (std::isfinite(st[dmx + j])) sdmax = std::max(sdmax, st[dmx + j]);
     sh[pass].resize(d);
     sc[pass].resize(d);
     for (int j = 0; j < d; ++j) {
-      const double sd = std::max(st[d + j], rel_floor * sdmax);
+      const double sd = std::max(st[dmx + j], rel_floor * sdmax);
       const bool flat = !(sd > 0.0) || !std::isfinite(sd);
       sh[pass][j] = (float)st[j];
       sc[pass][j] = flat ? 1.f : (float)(pass ? sd : 1.0 / sd);

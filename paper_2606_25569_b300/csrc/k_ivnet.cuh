@@ -6,11 +6,13 @@
 // row-major FP32, rows b n + p; the batch is padded to a multiple of 128 with zero samples.
 //
 // Kernels (grid-stride over their elements):
-//   k_iv_rows_in    network input rows [x(N), y(N)] (per-feature input map in FP32) -> signal (N, 2)
-//   k_iv_gather     columns col[(b n_out + p) Kp + c k + t] = bf16(x[b, (s p + d (t - (k-1)/2)) mod n_in, c])
-//                   and their transpose (K-major over the rows, for the weight gradient)
+//   k_iv_rows_in    network input rows [s_0(N), s_1(N), ...] (per-feature input map in FP32) -> signal (N, nch)
+//   k_iv_gather     columns col[(b n_out + p) Kp + c k + t] = bf16(x[b, (s p + d (t - (k-1)/2)) mod n_in, c]);
+//                   k_iv_gatherT their transpose (K-major over the rows, for the weight gradient)
 //   k_iv_scatter    adjoint of the gather: dx[b, q, c] += sum over (p, t) reaching q of dcol[b n_out + p, c k + t]
-//   k_iv_up         periodic linear interpolation by 2 along positions; k_iv_up_T its adjoint (added)
+//   k_iv_up         periodic linear interpolation by 2 along positions plus the finer level's signal (the
+//                   prolongated coarse correction of the V-cycle); k_iv_up_T the interpolation's adjoint (added)
+//   k_iv_splitsum   the weight gradient from the split-K GEMM's partial products, in order
 //   k_iv_add        y = a + b (the residual stream)
 //   k_iv_rows_out   projection output (channels 0, 1 of a 16-channel signal) -> rows [x(N), y(N)], with the
 //                   output map when given; k_iv_rows_grad the loss gradient rows -> that signal's gradient
@@ -23,17 +25,18 @@
 
 namespace vs {
 
-__global__ void k_iv_rows_in(const float* __restrict__ x, int batch, int Bp, int N, const float* __restrict__ shift,
-                             const float* __restrict__ scale, float* __restrict__ sig) {
-  const int64_t n = (int64_t)Bp * N * 2;
+__global__ void k_iv_rows_in(const float* __restrict__ x, int batch, int Bp, int N, int nch,
+                             const float* __restrict__ shift, const float* __restrict__ scale,
+                             float* __restrict__ sig) {
+  const int64_t n = (int64_t)Bp * N * nch;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e & 1);
-    const int64_t r = e >> 1;
+    const int c = (int)(e % nch);
+    const int64_t r = e / nch;
     const int b = (int)(r / N), p = (int)(r - (int64_t)b * N);
     float v = 0.f;
     if (b < batch) {
       const int f = c * N + p;
-      v = x[(int64_t)b * 2 * N + f];
+      v = x[(int64_t)b * nch * N + f];
       if (shift) v = __fmul_rn(__fsub_rn(v, shift[f]), scale[f]);
     }
     sig[e] = v;
@@ -45,27 +48,37 @@ struct IvConv {
   int kp, coutp;  // padded K (multiple of 16) and output channels (at least 16)
 };
 
-// col (M x kp, row-major) and, when colT is non-null, colT (kp x M); M = Bp n_out
-__global__ void k_iv_gather(const float* __restrict__ x, int64_t ldx, int Bp, int n_in, IvConv cv,
-                            __nv_bfloat16* __restrict__ col, __nv_bfloat16* __restrict__ colT) {
+// the gathered input of column j of row m (M = Bp n_out rows; zero in the padding columns)
+__device__ __forceinline__ float iv_col(const float* __restrict__ x, int ldx, int n_in, int n_out, const IvConv& cv,
+                                        int m, int j) {
+  if (j >= cv.cin * cv.k) return 0.f;
+  const int c = j / cv.k, t = j - c * cv.k;
+  const int b = m / n_out, p = m - b * n_out;
+  int q = (cv.s * p + cv.d * (t - (cv.k - 1) / 2)) % n_in;
+  if (q < 0) q += n_in;
+  return x[((int64_t)b * n_in + q) * ldx + c];
+}
+
+// col (M x kp, row-major); 32-bit indices (M kp < 2^31, checked at create)
+__global__ void k_iv_gather(const float* __restrict__ x, int ldx, int Bp, int n_in, IvConv cv,
+                            __nv_bfloat16* __restrict__ col) {
   const int n_out = n_in / cv.s;
-  const int64_t M = (int64_t)Bp * n_out;
-  const int64_t n = M * cv.kp;
-  const int half = (cv.k - 1) / 2;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = e / cv.kp;
-    const int j = (int)(e - m * cv.kp);
-    float v = 0.f;
-    if (j < cv.cin * cv.k) {
-      const int c = j / cv.k, t = j - c * cv.k;
-      const int b = (int)(m / n_out), p = (int)(m - (int64_t)b * n_out);
-      int q = (cv.s * p + cv.d * (t - half)) % n_in;
-      if (q < 0) q += n_in;
-      v = x[((int64_t)b * n_in + q) * ldx + c];
-    }
-    const __nv_bfloat16 bv = __float2bfloat16_rn(v);
-    col[e] = bv;
-    if (colT) colT[(int64_t)j * M + m] = bv;
+  const int n = Bp * n_out * cv.kp;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int m = e / cv.kp;
+    col[e] = __float2bfloat16_rn(iv_col(x, ldx, n_in, n_out, cv, m, e - m * cv.kp));
+  }
+}
+
+// colT (kp x M): the columns K-major over the rows (the weight gradient's operand), written in order
+__global__ void k_iv_gatherT(const float* __restrict__ x, int ldx, int Bp, int n_in, IvConv cv,
+                             __nv_bfloat16* __restrict__ colT) {
+  const int n_out = n_in / cv.s;
+  const int M = Bp * n_out;
+  const int n = M * cv.kp;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int j = e / M;
+    colT[e] = __float2bfloat16_rn(iv_col(x, ldx, n_in, n_out, cv, e - j * M, j));
   }
 }
 
@@ -91,8 +104,9 @@ __global__ void k_iv_scatter(const float* __restrict__ dcol, int Bp, int n_in, I
   }
 }
 
-// y (2n positions) = up(x) (n positions), C channels, contiguous
-__global__ void k_iv_up(const float* __restrict__ x, int Bp, int n, int C, float* __restrict__ y) {
+// y (2n positions) = up(x) (n positions) + skip (2n positions, or null), C channels, contiguous
+__global__ void k_iv_up(const float* __restrict__ x, const float* __restrict__ skip, int Bp, int n, int C,
+                        float* __restrict__ y) {
   const int64_t total = (int64_t)Bp * 2 * n * C;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % C);
@@ -100,12 +114,9 @@ __global__ void k_iv_up(const float* __restrict__ x, int Bp, int n, int C, float
     const int b = (int)(r / (2 * n)), p = (int)(r - (int64_t)b * 2 * n);
     const int q = p >> 1;
     const float a = x[((int64_t)b * n + q) * C + c];
-    if (p & 1) {
-      const float a1 = x[((int64_t)b * n + (q + 1 == n ? 0 : q + 1)) * C + c];
-      y[e] = 0.5f * (a + a1);
-    } else {
-      y[e] = a;
-    }
+    float v = a;
+    if (p & 1) v = 0.5f * (a + x[((int64_t)b * n + (q + 1 == n ? 0 : q + 1)) * C + c]);
+    y[e] = skip ? v + skip[e] : v;
   }
 }
 
@@ -119,6 +130,14 @@ __global__ void k_iv_up_T(const float* __restrict__ dy, int Bp, int n, int C, fl
     const int64_t base = (int64_t)b * 2 * n;
     const int pm = (q == 0) ? 2 * n - 1 : 2 * q - 1;
     dx[e] += dy[(base + 2 * q) * C + c] + 0.5f * dy[(base + 2 * q + 1) * C + c] + 0.5f * dy[(base + pm) * C + c];
+  }
+}
+
+__global__ void k_iv_splitsum(const float* __restrict__ part, int S, int64_t n, float* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < S; ++z) s += part[(int64_t)z * n + e];
+    out[e] = s;
   }
 }
 

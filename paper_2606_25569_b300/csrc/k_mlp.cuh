@@ -47,6 +47,9 @@ struct GemmArgs {
   const __nv_bfloat16* mask; int64_t ld_mask;
   const float* oscale; const float* oshift;  // [N] each, or both null
   unsigned* err;
+  // split K (kchunk > 0): CTA z of gridDim.z takes K range [z kchunk, (z + 1) kchunk) and writes its partial
+  // product to out_f32 + z split_ld (no bias, activation or BF16 outputs)
+  int kchunk; int64_t split_ld;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -71,6 +74,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 }
 
 __global__ void __launch_bounds__(MM_THREADS) k_gemm_bf16(GemmArgs g) {
+  if (g.kchunk > 0) {
+    const int k0 = blockIdx.z * g.kchunk;
+    g.A += k0;
+    g.B += k0;
+    g.K = min(g.K - k0, g.kchunk);
+    g.out_f32 += blockIdx.z * g.split_ld;
+  }
   extern __shared__ unsigned char mm_raw[];
   __shared__ __align__(8) uint64_t mbar[MM_STAGES];
   __shared__ uint32_t tmem_base;

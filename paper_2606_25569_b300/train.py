@@ -25,6 +25,91 @@ def he_uniform(dims, rng):
     return np.concatenate(ws + bs).astype(np.float32)
 
 
+def ivnet_convs(C, nb, cin=2):
+    """(C_in, C_out, k) of IVNet's convolutions in vs_ivnet's parameter order."""
+    h = C // 2
+    out = [(cin, C, 3)]
+    for _ in range(nb):
+        out += [(C, h, 3)] * 4 + [(C, C, 3), (C, C, 3), (C, C, 1)]
+    return out + [(C, 2, 1)]
+
+
+def ivnet_he_uniform(C, nb, rng, cin=2):
+    """Initial flat parameters of vs_ivnet: He-uniform weights (fan-in C_in k), zero biases, and zero weights
+    in the mixing convolutions, so that every block starts as the identity on its residual stream (without
+    it the residual sums grow block by block: the first loss of an 8-block network was 197 against 1.4)."""
+    out = []
+    convs = ivnet_convs(C, nb, cin)
+    for j, (ci, co, k) in enumerate(convs):
+        lim = np.sqrt(6.0 / (ci * k))
+        mixing = 0 < j < len(convs) - 1 and (j - 1) % 7 == 6
+        out += [np.zeros(co * ci * k) if mixing else rng.uniform(-lim, lim, co * ci * k), np.zeros(co)]
+    return np.concatenate(out).astype(np.float32)
+
+
+def to_points(F, N, kmax):
+    """Fourier feature rows (modes <= min(kmax, N/2 - 1), vs_training_pairs' layout) -> point rows
+    [x(N), y(N)] (vs_feature_points)."""
+    import torch
+    K = min(kmax, N // 2 - 1)
+    out = torch.empty(F.shape[0], 2 * N, dtype=torch.float32, device="cuda")
+    binding.feature_points(F.contiguous(), F.shape[0], F.shape[1], N, K, out)
+    return out
+
+
+def split_points(F, N, kmax, k_split):
+    """Fourier feature rows -> point rows of four signals [x_low(N), y_low(N), x_high(N), y_high(N)]: the modes
+    <= k_split and the modes above it (to kmax) as separate signals, each normalised on its own by the network's
+    input map (the high modes are ~1e-2 of the shape, below a bfloat16 input's resolution next to it)."""
+    import torch
+    K = min(kmax, N // 2 - 1)
+    per = 2 * K + 1
+    r = np.arange(per)
+    mode = np.where(r <= K, r, r - K)
+    low = np.zeros(F.shape[1], dtype=np.float32)
+    for c in range(2):
+        low[c * per:(c + 1) * per] = (mode <= k_split)
+    low_t = torch.as_tensor(low, device="cuda")
+    lo = to_points(F * low_t, N, kmax)
+    hi = to_points(F * (1.0 - low_t) * (torch.arange(F.shape[1], device="cuda") < 2 * per), N, kmax)
+    return torch.cat([lo, hi], dim=1).contiguous()
+
+
+def train_ivnet(X, Y, N, C=64, nb=4, epochs=40, batch=1024, lr=1e-3, lr_min=1e-5, beta=0.1, holdout=0.1, seed=0,
+                stream=None, serve_batch=0, rel_floor=1e-3, cin=2):
+    """IVNet (Sec. 3.4.2) on point rows (X, Y) [x(N), y(N)]: normalised features (vs_ivnet_fit_affine), AdamW
+    from lr decaying on a cosine to lr_min, the last `holdout` fraction held out (as train_relaxation)."""
+    import torch
+    n = X.shape[0]
+    nh = int(round(holdout * n))
+    ntr = n - nh
+    net = binding.Ivnet(N, C, nb, max_batch=max(batch, serve_batch), beta=beta, stream=stream, in_channels=cin)
+    net.set_params(ivnet_he_uniform(C, nb, np.random.default_rng(seed), cin))
+    net.fit_affine(X[:ntr].contiguous(), Y[:ntr].contiguous(), ntr, rel_floor)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    hist = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    for ep in range(epochs):
+        lr_ep = lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * ep / max(1, epochs)))
+        perm = torch.randperm(ntr, device="cuda", generator=gen)
+        Xs, Ys = X[perm].contiguous(), Y[perm].contiguous()
+        for a in range(0, ntr - batch + 1, batch):
+            want = (a == 0)
+            lo = net.train_step(Xs[a:a + batch], Ys[a:a + batch], batch, lr=lr_ep, want_loss=want)
+            steps += 1
+            if want:
+                hist.append(lo)
+    net.sync()
+    t_train = time.perf_counter() - t0
+    err_tr = relative_errors(net, X[:ntr], Y[:ntr], batch)
+    err_ho = relative_errors(net, X[ntr:], Y[ntr:], batch) if nh else np.array([])
+    return {"net": net, "params": net.nparam, "history": hist, "train_err": err_tr, "holdout_err": err_ho,
+            "train_seconds": t_train, "steps": steps}
+
+
 def relaxation_samples(wl, snapshots, every, stream, kmax, near_field=None, skip=0):
     """(X, Y): FP32 device tensors (snapshots * M, W) of network inputs and raw targets (Fourier
     features up to mode kmax, W = binding.feature_width), taken every `every` steps after `skip`

@@ -66,23 +66,26 @@ def test_forward_and_gradient_match_oracle(N, C, nb, batch, tol):
     net.close()
 
 
-def test_affine_maps_match_oracle():
+@pytest.mark.parametrize("cin", [2, 4])
+def test_affine_maps_match_oracle(cin):
     N, C, nb, batch = 32, 32, 2, 160
-    p, X, Y = _data(N, C, nb, batch, 2)
-    rng = np.random.default_rng(3)
+    rng = np.random.default_rng(2)
+    p = ov.init_params(C, nb, rng, cin).astype(np.float32).astype(np.float64)
+    X = rng.standard_normal((batch, cin * N)).astype(np.float32).astype(np.float64)
+    Y = rng.standard_normal((batch, 2 * N)).astype(np.float32).astype(np.float64)
     aff = tuple(a.astype(np.float32).astype(np.float64) for a in (
-        0.3 * rng.standard_normal(2 * N), rng.uniform(0.5, 3.0, 2 * N), 0.2 * rng.standard_normal(2 * N),
+        0.3 * rng.standard_normal(cin * N), rng.uniform(0.5, 3.0, cin * N), 0.2 * rng.standard_normal(2 * N),
         rng.uniform(0.05, 2.0, 2 * N)))
-    net = binding.Ivnet(N, C, nb, max_batch=batch, beta=0.5)
+    net = binding.Ivnet(N, C, nb, max_batch=batch, beta=0.5, in_channels=cin)
     net.set_params(p)
     net.set_affine(*aff)
     y = torch.empty(batch, 2 * N, dtype=torch.float32, device="cuda")
     net.forward(_dev(X), y, batch)
     net.sync()
-    ref, _ = ov.forward(p, C, nb, X, bf16=True, affine=aff)
+    ref, _ = ov.forward(p, C, nb, X, bf16=True, affine=aff, cin=cin)
     check_network_output(y.cpu().numpy().astype(np.float64), ref, DEEP_L2, DEEP_ELEM, "IVNet forward with maps")
     loss, g = net.loss_grad(_dev(X), _dev(Y), batch)
-    lo, go = ov.loss_and_gradient(p, C, nb, X, Y, beta=0.5, bf16=True, affine=aff)
+    lo, go = ov.loss_and_gradient(p, C, nb, X, Y, beta=0.5, bf16=True, affine=aff, cin=cin)
     assert abs(loss - lo) <= 1e-4 * abs(lo)
     check_network_output(np.asarray(g, np.float64), go, DEEP_L2, DEEP_ELEM, "IVNet gradient with maps")
     net.close()
