@@ -685,21 +685,36 @@ def long_run_arms(wl, args, stream):
     plain = binding.Suspension(wl.flat_xy(), wl.offsets, **kw)
     runs = {name: make(cfg) for name, cfg in variants.items()}
     errs = {name: {} for name in variants}
+    windows = {name: {} for name in variants}
+    plain_windows = {}
     failed = {}
     done = 0
+    import torch
     for S in sorted({min(k, args.hybrid_steps) for k in (10, 100, 300, 500, 800, 1000, args.hybrid_steps)}):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         plain.step(S - done)
+        e1.record(stream)
         plain.sync()
+        plain_windows["%d-%d" % (done, S)] = {"ms_per_step": e0.elapsed_time(e1) / (S - done)}
         ref = plain.positions()
         for name, sus in runs.items():
             if name in failed:
                 continue
             try:
+                c0 = sus.hybrid_counters()
+                e0.record(stream)
                 sus.step(S - done)
+                e1.record(stream)
                 sus.sync()
             except Exception as ex:  # a non-finite state ends that comparison
                 failed[name] = "step %d..%d: %s" % (done, S, ex)
                 continue
+            c1 = sus.hybrid_counters()
+            tests = c1["fallback_steps"] - c0["fallback_steps"]
+            windows[name]["%d-%d" % (done, S)] = {
+                "ms_per_step": e0.elapsed_time(e1) / (S - done),
+                "exact_fraction": ((c1["exact_vesicles"] - c0["exact_vesicles"]) / (tests * wl.M)) if tests else None}
             e, _ = train.centred_shape_error(sus.positions(), ref, wl.counts)
             errs[name][str(S)] = float(np.mean(e))
         done = S
@@ -708,7 +723,15 @@ def long_run_arms(wl, args, stream):
         sus.close()
         last = errs[name].get(str(args.hybrid_steps))
         out[name].update({"shape_error_mean_by_step": errs[name], "after_steps": args.hybrid_steps,
-                          "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2)})
+                          "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2),
+                          "windows": windows[name], "plain_windows": plain_windows})
+        # throughput over the last window of the long run (both arms timed on the same steps)
+        if windows[name]:
+            key = list(windows[name])[-1]
+            w = windows[name][key]
+            out[name]["late_window"] = {"steps": key, "value": wl.M / (w["ms_per_step"] * 1e-3), "unit": UNIT,
+                                        "ms_per_step": w["ms_per_step"], "exact_fraction": w["exact_fraction"],
+                                        "vs_plain": plain_windows[key]["ms_per_step"] / w["ms_per_step"]}
         if name in failed:
             out[name]["failed"] = failed[name]
     r["net"].close()

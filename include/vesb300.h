@@ -199,6 +199,15 @@ vs_status vs_get_device_ptrs(const vs_suspension* s, const double** xy, const do
  * [4] kernels launched by this handle so far. Synchronises. */
 vs_status vs_get_counters(vs_suspension* s, int64_t* out5);
 
+/* Fallback statistics of the hybrid step (Algorithm 1 with the learned maps of Sec. 3.2-3.3; the plain
+ * step is the learned step's fallback and judge). out3 (3 int64, host): [0] steps so far whose
+ * relaxation was the learned map; [1] steps that ran the fallback test (learned relaxation steps, and
+ * every step when the advection and tension networks are set); [2] vesicles that took the exact step
+ * in those steps (in a near pair, or within exact_gap spacings h of another vesicle), summed over
+ * them, so that [2] / ([1] M) is the mean fraction of vesicles stepped exactly. Zero outside hybrid
+ * mode and for one vesicle. Synchronises. */
+vs_status vs_get_hybrid_counters(vs_suspension* s, int64_t* out3);
+
 /*
  * Checkpoint and resume (no counterpart in the paper). A checkpoint holds what a later run needs to
  * continue bit for bit: positions, tension, A_0 and L_0, the step count and the correction counter, with

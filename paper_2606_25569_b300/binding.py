@@ -40,6 +40,7 @@ FUNCTIONS = {
     "vs_get_reference": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "vs_get_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_get_hybrid_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vs_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "vs_farfield_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p]),
@@ -239,6 +240,13 @@ class Suspension:
         self._check(lib().vs_get_counters(self._h, _ptr(out)))
         return {"steps": int(out[0]), "corrections": int(out[1]), "near_pairs": int(out[2]), "err": int(out[3]),
                 "launches": int(out[4])}
+
+    def hybrid_counters(self):
+        """Hybrid fallback statistics: learned relaxation steps, steps with the fallback test, and vesicles
+        stepped exactly in them (summed over those steps)."""
+        out = np.zeros(3, dtype=np.int64)
+        self._check(lib().vs_get_hybrid_counters(self._h, _ptr(out)))
+        return {"learned_steps": int(out[0]), "fallback_steps": int(out[1]), "exact_vesicles": int(out[2])}
 
     def profile(self, enable):
         self._check(lib().vs_profile(self._h, 1 if enable else 0))

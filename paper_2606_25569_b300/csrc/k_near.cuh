@@ -113,6 +113,23 @@ __global__ void __launch_bounds__(128) k_proximity(VesIndex vi, const double* __
   if (threadIdx.x == 0 && hit) involved[a] = 1;
 }
 
+// Hybrid fallback statistics (one CTA): acc[0] += number of vesicles flagged for the exact step, acc[1] += 1.
+__global__ void __launch_bounds__(256) k_count_flags(int M, const int* __restrict__ flag,
+                                                      unsigned long long* __restrict__ acc) {
+  __shared__ int part[8];
+  int c = 0;
+  for (int v = threadIdx.x; v < M; v += blockDim.x) c += flag[v] != 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    acc[0] += (unsigned long long)t;
+    acc[1] += 1ull;
+  }
+}
+
 struct NearBufs {
   double* layer;   // per vesicle at 30 off[v]: LX, LY, UX, UY, WX, WY (5N each)
   float* phi;      // per vesicle at moff[v]: (5N)^2 floats

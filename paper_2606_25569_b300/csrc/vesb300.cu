@@ -358,6 +358,8 @@ struct vs_suspension {
   unsigned* err = nullptr;
   int* has_near = nullptr;
   int* involved = nullptr;         // vesicles in a near pair this step (hybrid: they relax exactly)
+  unsigned long long* fb_acc = nullptr;  // [0] vesicles taking the exact fallback, summed over steps; [1] steps
+  int64_t learned_steps = 0;       // steps whose relaxation was the learned map
   NearBufs nb{nullptr, nullptr};
   double* corr = nullptr;          // correction state (6 N + 16 doubles per vesicle)
   int *cactive = nullptr, *cpiv = nullptr;
@@ -1275,6 +1277,7 @@ vs_status step_once(vs_suspension* h) {
                                                                                      h->B.near_v, h->involved));
     VS_LAUNCH(h, "k_proximity", k_proximity<<<M, 128, 0, h->stream>>>(vi, h->xy, h->B.centre, h->B.h2, M,
                                                                        exact_gap(h), h->involved));
+    VS_LAUNCH(h, "k_count_flags", k_count_flags<<<1, 256, 0, h->stream>>>(M, h->involved, h->fb_acc));
   }
   // (4) advection
   if (lf) {
@@ -1590,7 +1593,7 @@ void free_suspension(vs_suspension* h) {
   cudaFree(h->xy); cudaFree(h->xy_star); cudaFree(h->xy_next); cudaFree(h->sigma); cudaFree(h->u);
   cudaFree(h->u_r); cudaFree(h->A0); cudaFree(h->L0); cudaFree(h->scratch); cudaFree(h->piv);
   cudaFree(h->scratch32); cudaFree(h->piv32);
-  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near); cudaFree(h->involved);
+  cudaFree(h->dirty); cudaFree(h->fired); cudaFree(h->err); cudaFree(h->has_near); cudaFree(h->involved); cudaFree(h->fb_acc);
   cudaFree(h->nb.layer); cudaFree(h->nb.phi); cudaFree(h->xin); cudaFree(h->frames);
   cudaFree(h->corr); cudaFree(h->cactive); cudaFree(h->cpiv);
   h->ffs.release();
@@ -1636,6 +1639,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(dalloc(&h->dirty, L.M)); VS_A(dalloc(&h->fired, 1)); VS_A(dalloc(&h->err, 1));
   VS_A(dalloc(&h->has_near, L.M));
   VS_A(dalloc(&h->involved, L.M));
+  VS_A(dalloc(&h->fb_acc, 2));
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
@@ -1669,6 +1673,7 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
                                 (int)near_rbf_smem(5 * L.nmax)));
   }
   VS_A(cudaMemsetAsync(h->fired, 0, sizeof(int), h->stream));
+  VS_A(cudaMemsetAsync(h->fb_acc, 0, 2 * sizeof(unsigned long long), h->stream));
   VS_A(cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
   VS_A(cudaMemsetAsync(h->sigma, 0, L.P * sizeof(double), h->stream));
   VS_A(cudaMemsetAsync(h->u, 0, 2 * L.P * sizeof(double), h->stream));
@@ -1708,8 +1713,10 @@ vs_status vs_step(vs_suspension* h, int32_t nsteps) {
   const bool implicit = h->p.mode == 2;
   const bool graphs = !implicit && h->p.use_graph && h->stream != nullptr && !h->prof.on;
   for (int32_t k = 0; k < nsteps; ++k) {
+    const bool learned = learned_step(h);
     const vs_status st = implicit ? step_implicit(h) : graphs ? step_graph(h) : step_once(h);
     if (st != VS_OK) return st;
+    h->learned_steps += learned;
   }
   return VS_OK;
 }
@@ -1825,6 +1832,17 @@ vs_status vs_get_counters(vs_suspension* h, int64_t* out4) {
   out4[2] = pairs;
   out4[3] = e;
   out4[4] = h->launches;
+  return VS_OK;
+}
+
+vs_status vs_get_hybrid_counters(vs_suspension* h, int64_t* out3) {
+  if (!h || !out3) return VS_ERR_INVALID_ARG;
+  VS_CK(h, cudaStreamSynchronize(h->stream), "hybrid counters");
+  unsigned long long acc[2] = {0ull, 0ull};
+  VS_CK(h, cudaMemcpy(acc, h->fb_acc, sizeof acc, cudaMemcpyDeviceToHost), "hybrid counters");
+  out3[0] = h->learned_steps;
+  out3[1] = (int64_t)acc[1];
+  out3[2] = (int64_t)acc[0];
   return VS_OK;
 }
 

@@ -204,10 +204,14 @@ def test_hybrid_close_vesicles_relax_exactly(gap):
     net.set_params(params)
     g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, stream=stream, mode=1, **kw)
     g.set_network(net, scale, 15)
+    exact = 0
     for _ in range(2):
+        exact += len(close_vesicles(o.xs, o.ys, gap))  # decided at X^n, as in the step
         o.step()
         g.step()
         assert len(o.near_pairs) == 0
         gx, gy = split(g.positions(), [N] * M)
         assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-8
+    # the library's fallback statistics count the same vesicles
+    assert g.hybrid_counters() == {"learned_steps": 2, "fallback_steps": 2, "exact_vesicles": exact}
     g.close()
