@@ -32,19 +32,20 @@ sys.path.insert(0, ROOT)
 METRIC = "vesicle-steps/s: hybrid vs plain BIE on one B300 at shape error <=1e-2"
 UNIT = "vesicle-steps/s"
 MUFU_PER_CLK_SM = 16      # special-function results per clock per SM (4 per sub-partition)
-ISSUE_LANES_PER_CLK_SM = 128  # 4 warp schedulers x 32 lanes: one warp instruction each per clock
+FP32_LANES_PER_CLK_SM = 128  # FP32 lane operations per clock per SM (4 sub-partitions x 32 lanes; single and
+                             # paired float2 instructions alike)
 N_SM = 148
-# k_farfield_sym: arithmetic instructions per unordered pair of points (19 FP32 + lg2 + rcp, both reactions;
-# one of the FP32 instructions scales the log argument by the pair's constant, which the FP32 accuracy bar
-# needs in dense suspensions)
-FFS_INST_PER_PAIR = 21
+# k_farfield_sym: FP32 lane operations per unordered pair of points, both reactions (r 2, |r|^2 2, row
+# reaction 7, column reaction 7), besides lg2 and rcp on the special-function unit; the log argument's
+# per-pair scale rides on the coordinates and costs none
+FFS_FP32_PER_PAIR = 18
 # DRAM bytes per point of one far-field launch: ncu dram__bytes of k_farfield_f32 on the 1200 x 64 dense
 # Poiseuille suspension (2.82 MB for 76,800 points; sources, centres and outputs, every re-read hits L2)
 FF_DRAM_BYTES_PER_POINT = 2.82e6 / 76800
 # DRAM bytes of one k_farfield_sym launch at 2000 x 64 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
-# one-pass capture of the bench workload with chunks of 16 vesicles: 5.20 MB read, 197.19 MB written, mostly
+# one-pass capture of the bench workload with chunks of 16 vesicles: 3.19 MB read, 195.51 MB written, mostly
 # the per-chunk partial sums that do not stay in L2)
-FFS_DRAM_READ, FFS_DRAM_WRITE = 5.20e6, 197.19e6
+FFS_DRAM_READ, FFS_DRAM_WRITE = 3.19e6, 195.51e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 # learned advection and tension: velocity modes expanded and column modes kept, training epochs
 FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
@@ -814,20 +815,20 @@ def run_gpu(args):
                 "peak_source": "16 MUFU/clk/SM x 148 SMs x median SM clock (derived)",
                 "share_of_step": dom_ms / total_prof}
     elif dom_name.startswith("k_farfield_sym"):
-        # issue-bound: every instruction of the pair formula takes an issue slot (FP32 pipe ~80%, MUFU ~27%)
+        # FP32-pipe bound (paired float2 instructions; the special-function unit carries lg2 and rcp beside it)
         pairs = (float(wl.offsets[-1]) ** 2 - float(np.sum(wl.counts.astype(np.float64) ** 2))) / 2
         mhz = clocks.get("sm_mhz") or 1920.0
-        peak_issue = ISSUE_LANES_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
-        achieved = FFS_INST_PER_PAIR * pairs / (avg_ms * 1e-3) / 1e12
+        peak_fp32 = FP32_LANES_PER_CLK_SM * N_SM * mhz * 1e6 / 1e12
+        achieved = FFS_FP32_PER_PAIR * pairs / (avg_ms * 1e-3) / 1e12
         # the measured traffic is for chunks of 16 vesicles; its partial-sum writes scale with the chunk count
         V = fv[2] // args.N if fv[0] < 0 else 16
         traffic = FFS_DRAM_READ + FFS_DRAM_WRITE * 16.0 / V
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_issue, "unit": "Tinst/s",
-                "frac": achieved / peak_issue, "traffic": traffic,
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_fp32,
+                "unit": "T FP32 lane-ops/s", "frac": achieved / peak_fp32, "traffic": traffic,
                 "traffic_source": FFS_DRAM_SOURCE + (", writes scaled from 16 to %d vesicles per chunk" % V
                                                      if V != 16 else ""),
-                "peak_source": "issue: 4 schedulers x 32 lanes x 148 SMs x median SM clock (derived); "
-                               "achieved counts 21 instructions per unordered pair (19 FP32 + lg2 + rcp)",
+                "peak_source": "FP32 pipe: 128 lanes per clock per SM x 148 SMs x median SM clock (derived); "
+                               "achieved counts 18 FP32 lane operations per unordered pair of points",
                 "share_of_step": dom_ms / total_prof}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,

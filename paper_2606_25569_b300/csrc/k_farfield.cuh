@@ -48,6 +48,16 @@ __device__ __forceinline__ float pow2_scale(float S, float& e) {
   return __int_as_float((127 - ex) << 23);
 }
 
+// The same with e even, and t = 2^(-e/2): scaling both points of a pair by t scales |r|^2 by 2^-e exactly
+// (powers of two commute with rounding), so the log argument needs no multiply of its own, while the
+// Stokeslet's (r . g) r / |r|^2 does not change at all.
+__device__ __forceinline__ float pow2_scale_even(float S, float& t) {
+  int ex = ((__float_as_int(S) >> 23) & 0xff) - 127;
+  ex -= ex & 1;  // down to even (two's complement: -3 -> -4)
+  t = __int_as_float((127 - ex / 2) << 23);
+  return __int_as_float((127 - ex) << 23);
+}
+
 __device__ __forceinline__ void neumaier_add(float& s, float& c, float p) {
   const float t = s + p;
   c += (fabsf(s) >= fabsf(p)) ? ((s - t) + p) : ((p - t) + s);

@@ -31,11 +31,12 @@
 // vesicle, at most MAX_NEAR; more sets ERR_NEAR_OVERFLOW).
 //
 // Common logarithm: the densities of a vesicle sum to (nearly) zero, so its terms g_j log|r_j|^2 nearly
-// cancel. Each log argument is scaled by s = 2^-e, the power of two nearest below 1 / (|c_A - c_B|^2 +
-// reach_A^2 + reach_B^2), the same for both reactions of the pair: log2(|r|^2 s) is small for separated
-// vesicles, which keeps the FP32 partial sums small, and e times the source vesicle's density sum (summed in
-// FP64) is added once per pair (Sum_j g_j log2|r_j|^2 = Sum_j g_j log2(|r_j|^2 s) + e Sum_j g_j; the scaling
-// and e are exact).
+// cancel. Each log argument is scaled by s = 2^-e, the power of two with even exponent at or below
+// 1 / (|c_A - c_B|^2 + reach_A^2 + reach_B^2), the same for both reactions of the pair: log2(|r|^2 s) is small
+// for separated vesicles, which keeps the FP32 partial sums small, and e times the source vesicle's density
+// sum (summed in FP64) is added once per pair (Sum_j g_j log2|r_j|^2 = Sum_j g_j log2(|r_j|^2 s) + e Sum_j g_j;
+// the scaling and e are exact). The scaling is applied to the coordinates (both points of a pair times
+// 2^(-e/2)), which leaves (r . g) r / |r|^2 unchanged bit for bit and costs no operation per pair.
 //
 // Precision: per (target, source vesicle) partial sums in FP32 as in k_farfield_f32, added to running
 // sums with Neumaier compensation (registers for the rows, shared memory for the columns). Tile (I, J)
@@ -97,12 +98,14 @@ __device__ __forceinline__ void ffs_near(const FfSymArgs& a, int64_t t, int v) {
   else atomicOr(a.err, ERR_NEAR_OVERFLOW);
 }
 
-// One (row vesicle A, column vesicle B) pair: row targets (tx, ty) relative to B's centre with their own
-// densities rp.zw (and hl2 times them in gxs, gys); B's staged points at colB. Row partial sums in
-// lx..ay, column partial sums (log term already scaled) in ux, uy; minima when MIN. The log arguments are
-// scaled by sc.
+// One (row vesicle A, column vesicle B) pair: row targets (tx, ty) relative to B's centre, times t, with
+// their own densities rp.zw (and hl2 times them in gxs, gys); B's staged points at colB, taken times t.
+// Row partial sums in lx..ay, column partial sums (log term already scaled) in ux, uy; minima of the
+// scaled |r|^2 when MIN. Both points of a pair scaled by t = 2^(-e/2) put the log argument |r|^2 2^-e
+// into range without a multiply (pow2_scale_even); r is taken as source minus target (the pair terms
+// are even in r).
 template <int RR, int RC, bool MIN>
-__device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int lane, float sc, const float (&tx)[RR],
+__device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int lane, float t, const float (&tx)[RR],
                                          const float (&ty)[RR], const float4 (&rp)[RR], const float (&gxs)[RR],
                                          const float (&gys)[RR], float (&lx)[RR], float (&ly)[RR], float (&ax)[RR],
                                          float (&ay)[RR], float (&mr)[RR], float (&ux)[RC], float (&uy)[RC],
@@ -118,13 +121,13 @@ __device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int la
     for (int r = 0; r < RR; ++r)
 #pragma unroll
       for (int c = 0; c < RC; ++c) {
-        const float rx = tx[r] - s[c].x, ry = ty[r] - s[c].y;
+        const float rx = fmaf(s[c].x, t, -tx[r]), ry = fmaf(s[c].y, t, -ty[r]);
         const float r2 = fmaf(rx, rx, ry * ry);
         if (MIN) {
           mr[r] = fminf(mr[r], r2);
           mc[c] = fminf(mc[c], r2);
         }
-        const float lg = fast_lg2(r2 * sc);
+        const float lg = fast_lg2(r2);
         const float inv = fast_rcp(r2);
         lx[r] = fmaf(lg, s[c].z, lx[r]);
         ly[r] = fmaf(lg, s[c].w, ly[r]);
@@ -146,6 +149,101 @@ __device__ __forceinline__ void ffs_pair(const float4* __restrict__ colB, int la
   }
 }
 
+// ffs_pair for RC even in Blackwell's two-lane FP32 instructions (add, multiply and fma of float2: two FP32
+// operations in one issue slot, at the same lane rate as single ones). The one-lane form is issue-bound (the
+// FP32 pipe is busy in about two issue slots of three); here the column segments 2p and 2p + 1 go through
+// the same instructions as the two halves of float2 values, which halves the issue slots of the FP32 work,
+// so that the FP32 pipe and the special-function unit, not the issue, become the limits. The column layout
+// is paired accordingly: colB[(2p + h) 64 + k] holds point
+// k mod 32 of both segments, h = 0: (x_2p, x_2p+1, y_2p, y_2p+1), h = 1: (g_x 2p, g_x 2p+1, g_y 2p, g_y 2p+1).
+// Coordinates scaled by t as in ffs_pair. The row sums are kept per half and added at the end.
+template <int RR, int RC, bool MIN>
+__device__ __forceinline__ void ffs_pair2(const float4* __restrict__ colB, int lane, float t, const float (&tx)[RR],
+                                          const float (&ty)[RR], const float4 (&rp)[RR], const float (&gxs)[RR],
+                                          const float (&gys)[RR], float (&lx)[RR], float (&ly)[RR], float (&ax)[RR],
+                                          float (&ay)[RR], float (&mr)[RR], float (&ux)[RC], float (&uy)[RC],
+                                          float (&mc)[RC]) {
+  static_assert(RC % 2 == 0, "paired columns");
+  constexpr int RP = RC / 2;
+  const int from = (lane + 1) & 31;
+  const float4* base = colB + lane;
+  float2 ntx[RR], nty[RR], rz[RR], rw[RR], gx2[RR], gy2[RR], lx2[RR], ly2[RR], ax2[RR], ay2[RR], ux2[RP], uy2[RP];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    ntx[r] = make_float2(-tx[r], -tx[r]);
+    nty[r] = make_float2(-ty[r], -ty[r]);
+    rz[r] = make_float2(rp[r].z, rp[r].z);
+    rw[r] = make_float2(rp[r].w, rp[r].w);
+    gx2[r] = make_float2(gxs[r], gxs[r]);
+    gy2[r] = make_float2(gys[r], gys[r]);
+    lx2[r] = ly2[r] = ax2[r] = ay2[r] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int p = 0; p < RP; ++p) ux2[p] = uy2[p] = make_float2(0.f, 0.f);
+  const float2 t2 = make_float2(t, t);
+#pragma unroll FFS_STEPS_UNROLLED
+  for (int k = 0; k < 32; ++k) {
+    float2 sx[RP], sy[RP], sz[RP], sw[RP];
+#pragma unroll
+    for (int p = 0; p < RP; ++p) {
+      const float4 q0 = base[(2 * p) * 64 + k], q1 = base[(2 * p + 1) * 64 + k];
+      sx[p] = make_float2(q0.x, q0.y);
+      sy[p] = make_float2(q0.z, q0.w);
+      sz[p] = make_float2(q1.x, q1.y);
+      sw[p] = make_float2(q1.z, q1.w);
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int p = 0; p < RP; ++p) {
+        const float2 rx = __ffma2_rn(sx[p], t2, ntx[r]), ry = __ffma2_rn(sy[p], t2, nty[r]);
+        const float2 r2 = __ffma2_rn(rx, rx, __fmul2_rn(ry, ry));
+        if (MIN) {
+          mr[r] = fminf(mr[r], fminf(r2.x, r2.y));
+          mc[2 * p] = fminf(mc[2 * p], r2.x);
+          mc[2 * p + 1] = fminf(mc[2 * p + 1], r2.y);
+        }
+        const float2 lg = make_float2(fast_lg2(r2.x), fast_lg2(r2.y));
+        const float2 inv = make_float2(fast_rcp(r2.x), fast_rcp(r2.y));
+        lx2[r] = __ffma2_rn(lg, sz[p], lx2[r]);
+        ly2[r] = __ffma2_rn(lg, sw[p], ly2[r]);
+        const float2 q = __fmul2_rn(__ffma2_rn(rx, sz[p], __fmul2_rn(ry, sw[p])), inv);
+        ax2[r] = __ffma2_rn(q, rx, ax2[r]);
+        ay2[r] = __ffma2_rn(q, ry, ay2[r]);
+        ux2[p] = __ffma2_rn(lg, gx2[r], ux2[p]);
+        uy2[p] = __ffma2_rn(lg, gy2[r], uy2[p]);
+        const float2 qt = __fmul2_rn(__ffma2_rn(rx, rz[r], __fmul2_rn(ry, rw[r])), inv);
+        ux2[p] = __ffma2_rn(qt, rx, ux2[p]);
+        uy2[p] = __ffma2_rn(qt, ry, uy2[p]);
+      }
+#pragma unroll
+    for (int p = 0; p < RP; ++p) {
+      ux2[p].x = __shfl_sync(0xffffffffu, ux2[p].x, from);
+      ux2[p].y = __shfl_sync(0xffffffffu, ux2[p].y, from);
+      uy2[p].x = __shfl_sync(0xffffffffu, uy2[p].x, from);
+      uy2[p].y = __shfl_sync(0xffffffffu, uy2[p].y, from);
+      if (MIN) {
+        mc[2 * p] = __shfl_sync(0xffffffffu, mc[2 * p], from);
+        mc[2 * p + 1] = __shfl_sync(0xffffffffu, mc[2 * p + 1], from);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    lx[r] = lx2[r].x + lx2[r].y;
+    ly[r] = ly2[r].x + ly2[r].y;
+    ax[r] = ax2[r].x + ax2[r].y;
+    ay[r] = ay2[r].x + ay2[r].y;
+  }
+#pragma unroll
+  for (int p = 0; p < RP; ++p) {
+    ux[2 * p] = ux2[p].x;
+    ux[2 * p + 1] = ux2[p].y;
+    uy[2 * p] = uy2[p].x;
+    uy[2 * p + 1] = uy2[p].y;
+  }
+}
+
 // The symmetric order's per-vesicle data; with EQ (every vesicle of 32 R points, in index order) the
 // identity, computed instead of read.
 template <bool EQ, int R>
@@ -156,11 +254,16 @@ struct FfsIdx {
   static __device__ __forceinline__ int nreal(const FfSymArgs& a, int s) { return EQ ? 32 * R : a.nreal[s]; }
 };
 
+// CTAs per SM the register allocation must allow (256 threads each): 3 for the one-lane pair loop of small
+// classes (80 registers), else 2 (the paired loop of 2 x 2 segments needs 128 registers without spills; at
+// 80 registers it spilled and ran 2% slower on the dense 2000 x 64 layout).
+#define FFS_MIN_CTAS(RR, RC) (((RR) <= 2 && (RC) <= 2 && (RC) % 2 == 1) ? 3 : 2)
+
 // Persistent: each CTA takes tiles of its pair of classes (rows of RR segments, columns of RC) from t.ctr
 // until none are left. blockDim = 32 * FFS_W. EQ: all vesicles have 32 RR = 32 RC points (no padding).
 // V: vesicles per chunk.
 template <int RR, int RC, bool EQ, int V>
-__global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_farfield_sym(FfSymArgs a, FfSymTiles t,
+__global__ void __launch_bounds__(32 * FFS_W, FFS_MIN_CTAS(RR, RC)) k_farfield_sym(FfSymArgs a, FfSymTiles t,
                                                              const float4* __restrict__ centre32,
                                                              const float2* __restrict__ h2,
                                                              const float2* __restrict__ gsum) {
@@ -188,7 +291,14 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
     const bool diag = I == J;
     for (int e = threadIdx.x; e < nJ * 2 * NC; e += blockDim.x) {
       const int b = e / (2 * NC), rem = e - b * 2 * NC;
-      col[e] = a.psrc[IC::poff(a, cJ.x + b) + 32 * (rem >> 6) + (rem & 31)];
+      if constexpr (RC % 2 == 0) {  // paired segments (ffs_pair2)
+        const int blk = rem >> 6;
+        const int64_t o = IC::poff(a, cJ.x + b) + 64 * (blk >> 1) + (rem & 31);
+        const float4 s0 = a.psrc[o], s1 = a.psrc[o + 32];
+        col[e] = (blk & 1) ? make_float4(s0.z, s1.z, s0.w, s1.w) : make_float4(s0.x, s1.x, s0.y, s1.y);
+      } else {
+        col[e] = a.psrc[IC::poff(a, cJ.x + b) + 32 * (rem >> 6) + (rem & 31)];
+      }
     }
     for (int e = threadIdx.x; e < nJ * NC; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -233,13 +343,13 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
           const float dx = (ca.x - cb.x) + (ca.z - cb.z), dy = (ca.y - cb.y) + (ca.w - cb.w);
           // log-argument scale of the pair (its exponent is read back after the pair loop, so that it holds no
           // register there)
-          float lsc;
-          const float sc = pow2_scale(fmaf(dx, dx, dy * dy) + (ha.y + hb.y), lsc);
+          float tsc;
+          const float sc = pow2_scale_even(fmaf(dx, dx, dy * dy) + (ha.y + hb.y), tsc);
           float tx[RR], ty[RR], lx[RR], ly[RR], ax[RR], ay[RR], mr[RR], ux[RC], uy[RC], mc[RC];
 #pragma unroll
           for (int r = 0; r < RR; ++r) {
-            tx[r] = dx + rp[r].x;
-            ty[r] = dy + rp[r].y;
+            tx[r] = (dx + rp[r].x) * tsc;
+            ty[r] = (dy + rp[r].y) * tsc;
             lx[r] = ly[r] = ax[r] = ay[r] = 0.f;
             mr[r] = 3.0e38f;
           }
@@ -252,11 +362,18 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
           const float rs = reach_a + sqrtf(hb.y);
           const bool test = a.near_mask && fmaf(dx, dx, dy * dy) <= rs * rs;
           const float4* colB = col + bj * 2 * NC;
-          if (test)
-            ffs_pair<RR, RC, true>(colB, lane, sc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
-          else
-            ffs_pair<RR, RC, false>(colB, lane, sc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
-          lsc = (float)(127 - ((__float_as_int(sc) >> 23) & 0xff));  // sc = 2^-lsc
+          if constexpr (RC % 2 == 0) {
+            if (test)
+              ffs_pair2<RR, RC, true>(colB, lane, tsc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+            else
+              ffs_pair2<RR, RC, false>(colB, lane, tsc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+          } else {
+            if (test)
+              ffs_pair<RR, RC, true>(colB, lane, tsc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+            else
+              ffs_pair<RR, RC, false>(colB, lane, tsc, tx, ty, rp, gxs, gys, lx, ly, ax, ay, mr, ux, uy, mc);
+          }
+          const float lsc = (float)(127 - ((__float_as_int(sc) >> 23) & 0xff));  // sc = 2^-lsc
           const float2 gb = gsum[bv];
           __syncwarp();
           const int na = EQ ? 32 * RR : s_na[w];
@@ -264,7 +381,7 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
 #pragma unroll
           for (int r = 0; r < RR; ++r) {  // targets of A, source vesicle B
             if (!EQ && lane + 32 * r >= na) continue;
-            if (test && mr[r] <= hb.x) {
+            if (test && mr[r] <= hb.x * sc) {  // minima of the scaled |r|^2
               ffs_near(a, ao + lane + 32 * r, bv);
             } else {
               neumaier_add(sxr[r], cxr[r], fmaf(hl2, fmaf(lsc, gb.x, lx[r]), ax[r]));
@@ -276,7 +393,7 @@ __global__ void __launch_bounds__(32 * FFS_W, (RR <= 2 && RC <= 2) ? 3 : 2) k_fa
 #pragma unroll
           for (int c = 0; c < RC; ++c) {  // targets of B, source vesicle A
             if (!EQ && lane + 32 * c >= nb) continue;
-            if (test && mc[c] <= ha.x) {
+            if (test && mc[c] <= ha.x * sc) {
               ffs_near(a, IC::roff(a, bs) + lane + 32 * c, av);
             } else {
               float4& v = acc[bj * NC + lane + 32 * c];
