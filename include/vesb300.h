@@ -96,6 +96,12 @@ typedef struct {
  * by ceil(sqrt(N)), and the interpolating polynomial in the distance. Needs near_field = 1; the learned near
  * field (vs_set_near_networks) takes precedence in a hybrid suspension. */
 #define VS_FLAG_NEAR_YZ 64ull
+/* Form the FP32 operator products of the mixed-precision path (T, L, and the relaxation's W and A) with one
+ * batched GEMM launch per product over all vesicles instead of the default fused kernels, which form each
+ * vesicle's chain of products in shared memory with one CTA per vesicle (vesicles of at most 64 points; larger
+ * ones always take the batched launches). Both give FP32-quality preconditioners and the same FP64-accurate
+ * results. */
+#define VS_FLAG_OPS_BATCHED 128ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */

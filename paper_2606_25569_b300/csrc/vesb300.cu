@@ -18,6 +18,7 @@
 #include "k_farfield.cuh"
 #include "k_farfield_sym.cuh"
 #include "k_farfield_loc.cuh"
+#include "k_fused.cuh"
 #include "k_geometry.cuh"
 #include "k_implicit.cuh"
 #include "k_ivnet.cuh"
@@ -535,6 +536,11 @@ inline bool mp_wide(const vs_suspension* h) { return h->L.nmax > 64 || h->L.M < 
 // FP32 factorisations (refined in FP64, or preconditioning the implicit step's FP64 GMRES) unless FP64
 // operators are asked for
 inline bool mixed(const vs_suspension* h) { return !(h->p.flags & VS_FLAG_DIRECT_FP64); }
+// FP32 operator products by the fused per-vesicle kernels (k_fused.cuh; vesicles of at most 64 points) instead
+// of one batched GEMM launch per product
+inline bool fused(const vs_suspension* h) {
+  return mixed(h) && h->L.nmax <= FZ && !(h->p.flags & (VS_FLAG_TC_GEMM | VS_FLAG_OPS_BATCHED));
+}
 
 // S, T, L at slot s for the geometry currently in the SourceBufs, then LU of L.
 vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* active) {
@@ -549,7 +555,10 @@ vs_status build_operators(vs_suspension* h, const double* xy, int s, const int* 
                                                                       h->D.tab, h->p.mu, h->scratch, s, active));
   }
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
-  if (mixed(h)) {
+  if (fused(h)) {
+    VS_LAUNCH(h, "k_fused_tl", k_fused_tl<<<M, FUSED_THREADS, fz_tl_smem(), h->stream>>>(c, s, active));
+    launch_gj32(h, "k_gj_inverse<L>", LuGeo32{vi, h->scratch32, MatLayout::slot(s) + MatLayout::L, 1, 0, h->piv32, s}, n, active);
+  } else if (mixed(h)) {
     gemm32(h, "k_bgemm<OpT32>", OpT32{c, s}, 2 * n, n, active);
     gemm32(h, "k_bgemm<OpL32>", OpL32{c, s}, n, n, active);
     static_assert(NMAX <= 128, "the FP32 inverse of L is formed in registers");
@@ -975,6 +984,17 @@ int64_t relax_matrix_32(vs_suspension* h, int s, const int* active) {
   const int M = h->L.M, n = h->L.nmax;
   const VesIndex vi = h->D.vi();
   OpCtx c{vi, h->D.tab, h->B.sa, h->B.tx, h->B.ty, h->scratch, h->scratch32, h->D.tab32, h->B.g32};
+  if (fused(h)) {
+    VS_LAUNCH(h, "k_fused_relax", k_fused_relax<<<M, FUSED_THREADS, fz_relax_smem(), h->stream>>>(
+                                      c, s, (float)h->p.kappa_b, (float)h->p.dt, active));
+    launch_gj32(h, "k_gj_inverse<A>", LuGeo32{vi, h->scratch32, MatLayout::A, 2, 0, h->piv32, 2}, 2 * n, active);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cuda_fail(h->msg, e, "relaxation matrix");
+      return -1;
+    }
+    return MatLayout::A;
+  }
   gemm32(h, "k_bgemm<OpD2_32>", OpD2_32{c}, n, n, active);
   gemm32(h, "k_bgemm<OpD4_32>", OpD4_32{c}, n, n, active);
   gemm32(h, "k_bgemm<OpB32>", OpB32{c, s, 0, h->p.kappa_b}, 2 * n, n, active);
@@ -1643,6 +1663,8 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(cudaFuncSetAttribute(k_lu_smem<LuGeo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_SMEM_MAX));
   VS_A(cudaFuncSetAttribute(k_corr_newton32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4));
+  VS_A(cudaFuncSetAttribute(k_fused_tl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fz_tl_smem()));
+  VS_A(cudaFuncSetAttribute(k_fused_relax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fz_relax_smem()));
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpT32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpD2_32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));

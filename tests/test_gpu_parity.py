@@ -330,6 +330,30 @@ def test_tensor_core_and_fma_operator_products_agree(Ns):
     b.close()
 
 
+@pytest.mark.parametrize("Ns", [[64, 62, 50, 34, 26, 18, 10, 64], [32, 32, 16, 8]])
+def test_fused_operator_products_match_batched_and_oracle(Ns):
+    # the FP32 preconditioners formed per vesicle in shared memory (k_fused_tl, k_fused_relax; N x N blocks
+    # embedded in 64 x 64, point counts not multiples of 4 included) and by one batched GEMM launch per product
+    # (VS_FLAG_OPS_BATCHED) lead to the same FP64-accurate steps, and those match the oracle
+    xs, ys = _mixed(Ns, 12, spacing=2.6)
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=2, flow_p=(5.0, 8.0, 0, 0), corr_tol=0.01)
+    o = OracleSuspension(xs, ys, Params(**kw))
+    a = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, **kw)
+    b = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, ops_batched=True, **kw)
+    counts = [len(x) for x in xs]
+    for k in range(3):
+        o.step()
+        a.step()
+        b.step()
+        _compare(o, a)
+    ax, ay = split(a.positions(), counts)
+    bx, by = split(b.positions(), counts)
+    assert rel_err_per_vesicle(ax, ay, bx, by) <= 1e-12
+    assert np.max(np.abs(a.tension() - b.tension())) <= 1e-10 * np.max(np.abs(b.tension()))
+    a.close()
+    b.close()
+
+
 def test_set_state_keeps_operators_of_unchanged_vesicles():
     # vs_set_state only invalidates the cached operators of vesicles whose points changed; rebuilding the
     # others would give the same bits, so a suspension whose every vesicle was invalidated must agree
