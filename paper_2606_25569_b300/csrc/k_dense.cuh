@@ -788,6 +788,155 @@ __device__ bool gj_invert_np(const float* src, float* dst, int n) {
   return true;
 }
 
+// The same elimination two exchange steps per barrier (n even): steps k and k + 1 exchange equations k, k + 1
+// with unknowns k, k + 1 at once through the 2 x 2 pivot block P = T[K][K] (K = {k, k + 1}),
+//   T[K][K] <- Q = P^{-1},  T[K][j] <- -Q T[K][j],  T[i][K] <- T[i][K] Q,  T[i][j] <- T[i][j] - T[i][K] Q T[K][j],
+// which equals the two single steps in exact arithmetic (the block pivot's Schur complement). The owners of
+// columns k, k + 1 and rows k, k + 1 publish them before one barrier; every thread forms Q from the four pivot
+// entries and updates its entries with two paired FMAs each. The pivots the single steps would take, P00 and
+// P11 - P10 P01 / P00, are held to the same threshold (GJ_NP_TOL max|A|); a smaller one ends the attempt as in
+// gj_invert_np. Half the barriers of gj_invert_np, whose steps are bound by the barrier and the pivot's latency
+// rather than by the FP32 work.
+template <int RA, int RB, int TC>
+__device__ bool gj_invert_np2(const float* src, float* dst, int n) {
+  static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB && TC % 2 == 0, "square grid of pairs");
+  constexpr int NP = 16 * RA, H = RB / 2, NW = 16 * TC / 32;
+  __shared__ __align__(16) float colb[2][2][NP], rowb[2][2][NP];
+  __shared__ float wmax[NW];
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  float2 T[RA][H];
+  float mx = 0.f;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
+      T[a][h].x = (i < n && j0 < n) ? src[(int64_t)i * n + j0] : 0.f;
+      T[a][h].y = (i < n && j1 < n) ? src[(int64_t)i * n + j1] : 0.f;
+      mx = fmaxf(mx, fmaxf(fabsf(T[a][h].x), fabsf(T[a][h].y)));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = mx;
+  __syncthreads();
+  mx = wmax[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) mx = fmaxf(mx, wmax[w]);
+  const float thr = GJ_NP_TOL * mx;
+  bool ok = mx > 0.f;
+#pragma unroll
+  for (int kb = 0; kb < RB; ++kb) {
+#pragma unroll 1
+    for (int kc = 0; kc < TC; kc += 2) {
+      const int k = TC * kb + kc;  // even: rows k, k + 1 share a (pa), columns k, k + 1 share b (kb)
+      if (k >= n) break;
+      const int buf = (k >> 1) & 1;
+      const int pr = k & 15, pa = k >> 4;
+      if (tc == kc || tc == kc + 1) {  // column k or k + 1
+        float* cb = colb[buf][tc - kc];
+        float cv[RA];
+#pragma unroll
+        for (int a = 0; a < RA; ++a) cv[a] = (kb & 1) ? T[a][kb >> 1].y : T[a][kb >> 1].x;
+        if constexpr (RA >= 4) {
+#pragma unroll
+          for (int a = 0; a < RA; a += 4)
+            *reinterpret_cast<float4*>(&cb[tr * RA + a]) = make_float4(cv[a], cv[a + 1], cv[a + 2], cv[a + 3]);
+        } else {
+          *reinterpret_cast<float2*>(&cb[tr * RA]) = make_float2(cv[0], cv[1]);
+        }
+      }
+      if (tr == pr || tr == pr + 1) {  // row k or k + 1
+        float* rb = rowb[buf][tr - pr];
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+          if (a == pa) {
+            if constexpr (H == 1) {
+              *reinterpret_cast<float2*>(&rb[tc * RB]) = T[a][0];
+            } else {
+#pragma unroll
+              for (int h = 0; h < H; h += 2)
+                *reinterpret_cast<float4*>(&rb[tc * RB + 2 * h]) =
+                    make_float4(T[a][h].x, T[a][h].y, T[a][h + 1].x, T[a][h + 1].y);
+            }
+          }
+      }
+      __syncthreads();
+      const float p00 = colb[buf][0][pr * RA + pa], p10 = colb[buf][0][(pr + 1) * RA + pa];
+      const float p01 = colb[buf][1][pr * RA + pa], p11 = colb[buf][1][(pr + 1) * RA + pa];
+      float t1 = p00;
+      if (!(fabsf(t1) > thr)) { ok = false; t1 = 1.f; }
+      const float i1 = gj_rcp(t1);
+      float t2 = fmaf(-p10 * i1, p01, p11);
+      if (!(fabsf(t2) > thr)) { ok = false; t2 = 1.f; }
+      const float id = i1 * gj_rcp(t2);  // 1 / det P
+      const float q00 = p11 * id, q01 = -p01 * id, q10 = -p10 * id, q11 = p00 * id;
+      float c0[RA], c1[RA];
+      if constexpr (RA >= 4) {
+#pragma unroll
+        for (int a = 0; a < RA; a += 4) {
+          const float4 w0 = *reinterpret_cast<const float4*>(&colb[buf][0][tr * RA + a]);
+          const float4 w1 = *reinterpret_cast<const float4*>(&colb[buf][1][tr * RA + a]);
+          c0[a] = w0.x; c0[a + 1] = w0.y; c0[a + 2] = w0.z; c0[a + 3] = w0.w;
+          c1[a] = w1.x; c1[a + 1] = w1.y; c1[a + 2] = w1.z; c1[a + 3] = w1.w;
+        }
+      } else {
+        const float2 w0 = *reinterpret_cast<const float2*>(&colb[buf][0][tr * RA]);
+        const float2 w1 = *reinterpret_cast<const float2*>(&colb[buf][1][tr * RA]);
+        c0[0] = w0.x; c0[1] = w0.y;
+        c1[0] = w1.x; c1[1] = w1.y;
+      }
+      float2 u0[H], u1[H];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const float2 r0 = *reinterpret_cast<const float2*>(&rowb[buf][0][tc * RB + 2 * h]);
+        const float2 r1 = *reinterpret_cast<const float2*>(&rowb[buf][1][tc * RB + 2 * h]);
+        u0[h] = __ffma2_rn(make_float2(q01, q01), r1, __fmul2_rn(make_float2(q00, q00), r0));
+        u1[h] = __ffma2_rn(make_float2(q11, q11), r1, __fmul2_rn(make_float2(q10, q10), r0));
+      }
+      // columns k, k + 1: T[i][K] Q through the same update
+      if (tc == kc) {
+        if (kb & 1) { u0[kb >> 1].y = 1.f - q00; u1[kb >> 1].y = -q10; }
+        else { u0[kb >> 1].x = 1.f - q00; u1[kb >> 1].x = -q10; }
+      } else if (tc == kc + 1) {
+        if (kb & 1) { u0[kb >> 1].y = -q01; u1[kb >> 1].y = 1.f - q11; }
+        else { u0[kb >> 1].x = -q01; u1[kb >> 1].x = 1.f - q11; }
+      }
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          T[a][h] = __ffma2_rn(make_float2(-c0[a], -c0[a]), u0[h], T[a][h]);
+          T[a][h] = __ffma2_rn(make_float2(-c1[a], -c1[a]), u1[h], T[a][h]);
+        }
+      if (tr == pr || tr == pr + 1) {  // rows k, k + 1: -Q T[K][j], and Q in columns k, k + 1
+        const bool second = tr != pr;
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+          if (a == pa) {
+#pragma unroll
+            for (int h = 0; h < H; ++h) T[a][h] = second ? make_float2(-u1[h].x, -u1[h].y) : make_float2(-u0[h].x, -u0[h].y);
+            if (tc == kc || tc == kc + 1) {
+              const float qv = second ? (tc == kc ? q10 : q11) : (tc == kc ? q00 : q01);
+              if (kb & 1) T[a][kb >> 1].y = qv; else T[a][kb >> 1].x = qv;
+            }
+          }
+      }
+    }
+  }
+  __syncthreads();
+  if (!ok) return false;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = tr + 16 * a, j0 = tc + 2 * TC * h, j1 = j0 + TC;
+      if (i < n && j0 < n) dst[(int64_t)i * n + j0] = T[a][h].x;
+      if (i < n && j1 < n) dst[(int64_t)i * n + j1] = T[a][h].y;
+    }
+  __syncthreads();
+  return true;
+}
+
 // A dense batch of n x n row-major FP32 matrices, matrix v at base + v n^2.
 struct DenseGeo32 {
   float* base;
@@ -808,7 +957,8 @@ __global__ void __launch_bounds__(16 * TC, GJ_MIN_CTAS(TC)) k_gj_inverse(Geo geo
   const int v = geo.vid(blockIdx.x);
   if (active && !active[v]) return;
   float* A = geo.A(v);
-  if (!gj_invert_np<RA, RB, TC>(A, A, geo.n(v))) {
+  const int n = geo.n(v);
+  if (!((n % 2 == 0) ? gj_invert_np2<RA, RB, TC>(A, A, n) : gj_invert_np<RA, RB, TC>(A, A, n))) {
     if (fallbacks && threadIdx.x == 0) atomicAdd(fallbacks, 1);
     gj_invert<RA, RB, TC>(A, A, geo.n(v), err);
   }
