@@ -84,9 +84,12 @@ typedef struct {
 /* The FP32 far field sums over every ordered pair with one thread per target (k_farfield_f32, launch
  * shape autotuned) instead of the default symmetric evaluation. The symmetric kernel (k_farfield_sym)
  * visits each unordered pair of points of different vesicles once and adds both reactions (the
- * Stokeslet is even in r), with deterministic chunked FP64 reduction; it runs when every vesicle has
- * 32, 64 or 128 points and its per-chunk partial sums (16 bytes per point and group of 16 vesicles)
- * fit in 4 GiB, the per-target kernel otherwise. The two agree to FP32 rounding. */
+ * Stokeslet is even in r), with a deterministic chunked double-float reduction, for any point counts
+ * (vesicles padded to 32, 64 or 128 points). Its partial sums take 16 bytes per point and chunk of
+ * vesicles; beyond a budget (1/8 of the device memory, or the byte count in the environment variable
+ * VS_FFS_SLOT_BYTES, read when the suspension or plan is created) the chunks are taken in groups that
+ * fit it, one group pair at a time (the same sums, their double-float grouping aside), and below four
+ * slots a point the per-target kernel runs. The two kernels agree to FP32 rounding. */
 #define VS_FLAG_FARFIELD_PER_TARGET 32ull
 /* Near field by the Ying-Zorin scheme (Sec. 2.2.2, the caption of Fig. fig:near-singular: the near-singular
  * integration of the paper's BIEM ground truth) instead of the five layers and the RBF of Sec. 3.3: at each

@@ -64,8 +64,9 @@ struct FfSymArgs {
   int M;
   int nchunk;
   int near_mask;
-  float4* part;         // [nchunk][P]: velocity at each point from the vesicles of one chunk (x sum and
-                        // compensation, y sum and compensation)
+  float4* part;         // [slots][P]: velocity at each point from the vesicles of one chunk (x sum and
+                        // compensation, y sum and compensation); chunk K writes slot K % slots
+  int slots;            // nchunk (one pass), or the group size S of the phased evaluation
   int* near_cnt;        // [P], zero before each launch when near_mask
   int* near_v;          // [P * MAX_NEAR]
   unsigned* err;
@@ -425,14 +426,14 @@ __global__ void __launch_bounds__(32 * FFS_W, FFS_MIN_CTAS(RR, RC)) k_farfield_s
 #pragma unroll
           for (int r = 0; r < RR; ++r)
             if (EQ || lane + 32 * r < na)
-              a.part[(int64_t)J * a.P + ao + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
+              a.part[(int64_t)(J % a.slots) * a.P + ao + lane + 32 * r] = make_float4(sxr[r], cxr[r], syr[r], cyr[r]);
         }
       }
       __syncthreads();
     }
     for (int e = threadIdx.x; e < nJ * NC; e += blockDim.x) {  // chunk I's contributions to chunk J's points
       const int b = e / NC, i = e - b * NC;
-      if (i < IC::nreal(a, cJ.x + b)) a.part[(int64_t)I * a.P + IC::roff(a, cJ.x + b) + i] = acc[e];
+      if (i < IC::nreal(a, cJ.x + b)) a.part[(int64_t)(I % a.slots) * a.P + IC::roff(a, cJ.x + b) + i] = acc[e];
     }
     __syncthreads();
   }
@@ -485,6 +486,54 @@ __global__ void __launch_bounds__(256) k_farfield_sym_reduce(FfSymArgs a, const 
     }
     a.near_cnt[p] = c;
   }
+}
+
+// Phased evaluation (partial-sum memory bounded by S slots per point instead of one per chunk): the chunks form
+// groups of S consecutive chunks, and phase (g_a, g_b), g_a <= g_b, runs the tiles (I, J) with I in g_a and J in
+// g_b. In it a point of group g_a receives from the chunks of g_b only (slot J % S, each written once) and a
+// point of g_b from those of g_a, so one set of S slots serves the phase; this kernel then adds the phase's
+// slots of those points to u in slot order (double-float, as k_farfield_sym_reduce), the phases in a fixed
+// order, so the result is deterministic. pchunk: the chunk of each point; n_a, n_b: chunks in g_a and g_b.
+__global__ void __launch_bounds__(256) k_ffs_reduce_phase(FfSymArgs a, const int32_t* __restrict__ owner,
+                                                          const int64_t* __restrict__ voff,
+                                                          const int* __restrict__ pchunk, int ga, int gb, int na,
+                                                          int nb, double* __restrict__ u) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  const int g = pchunk[p] / a.slots;
+  if (g != ga && g != gb) return;
+  const int n = (g == ga) ? nb : na;  // the slots written for this point: the chunks of the other group
+  float2 ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
+  for (int K = 0; K < n; ++K) {
+    const float4 v = a.part[(int64_t)K * a.P + p];
+    ax = df_add(ax, make_float2(v.x, v.y));
+    ay = df_add(ay, make_float2(v.z, v.w));
+  }
+  const int v = owner[p];
+  const int64_t to = voff[v];
+  const int64_t nv = voff[v + 1] - to;
+  const int64_t loc = p - to;
+  u[2 * to + loc] += (double)ax.x + (double)ax.y;
+  u[2 * to + nv + loc] += (double)ay.x + (double)ay.y;
+}
+
+// After the last phase: near counts clamped to MAX_NEAR and each near list sorted ascending (as in
+// k_farfield_sym_reduce).
+__global__ void __launch_bounds__(256) k_ffs_near_sort(FfSymArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  const int c = min(a.near_cnt[p], MAX_NEAR);
+  int* lst = a.near_v + p * MAX_NEAR;
+  for (int i = 1; i < c; ++i) {
+    const int x = lst[i];
+    int j = i - 1;
+    while (j >= 0 && lst[j] > x) {
+      lst[j + 1] = lst[j];
+      --j;
+    }
+    lst[j + 1] = x;
+  }
+  a.near_cnt[p] = c;
 }
 
 }  // namespace vs

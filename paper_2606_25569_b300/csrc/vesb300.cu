@@ -298,11 +298,17 @@ struct FfSymState {
   int V = FFS_V;        // vesicles per chunk
   int per_sm = 0;       // persistent CTAs per SM (0: as many as fit)
   bool padded = false;  // some N is not a multiple of 32 or the order is not the identity: k_ffs_pad runs
-  int nchunk = 0, npair = 0;
-  int rr[FFS_NPAIR] = {}, rc[FFS_NPAIR] = {}, ntile[FFS_NPAIR] = {}, grid[FFS_NPAIR] = {};
-  int64_t tile_off[FFS_NPAIR + 1] = {};
+  int nchunk = 0;
+  int slots = 0;        // partial-sum slots per point: nchunk, or the group size S of the phased evaluation
+  bool phased = false;
+  // one persistent launch per pair of classes with tiles, per phase (one phase when not phased)
+  struct Launch { int rr, rc, ntile, grid; int64_t tile_off; };
+  struct Phase { int first, count, ga, gb, na, nb; };
+  std::vector<Launch> launch;
+  std::vector<Phase> phase;
   int2* tiles = nullptr;
-  unsigned* ctr = nullptr;  // [FFS_NPAIR]
+  unsigned* ctr = nullptr;  // [launch.size()]
+  int* pchunk = nullptr;    // chunk of each point (phased only)
   float4* part = nullptr;
   float4* psrc = nullptr;   // padded sources (padded only)
   int* vid = nullptr;
@@ -311,7 +317,7 @@ struct FfSymState {
   int2* chunk = nullptr;
   void release() {
     cudaFree(tiles); cudaFree(ctr); cudaFree(part); cudaFree(psrc); cudaFree(vid); cudaFree(poff); cudaFree(roff);
-    cudaFree(nreal); cudaFree(chunk);
+    cudaFree(nreal); cudaFree(chunk); cudaFree(pchunk);
     *this = FfSymState{};
   }
 };
@@ -630,7 +636,7 @@ FarFieldArgs far_field_args(vs_suspension* h) {
 // most FFS_V vesicles) fit in an eighth of the device's memory; otherwise, and with
 // VS_FLAG_FARFIELD_PER_TARGET, the per-target kernel runs.
 FfSymArgs ffs_args(const FfSymState& f, const Layout& L, int near_mask, const SourceBufs& B, unsigned* err) {
-  return FfSymArgs{L.P, L.M, f.nchunk, near_mask, f.part, B.near_cnt, B.near_v, err,
+  return FfSymArgs{L.P, L.M, f.nchunk, near_mask, f.part, f.slots, B.near_cnt, B.near_v, err,
                    f.vid, f.poff, f.roff, f.nreal, f.chunk, f.padded ? f.psrc : B.src};
 }
 
@@ -716,35 +722,55 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
   size_t free_b = 0, total_b = 0;
   cudaError_t e;
   if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return e;
-  if ((size_t)nchunk * (size_t)L.P * sizeof(float4) > total_b / 8) return cudaSuccess;
-  // tiles per pair of classes: whole tiles first, the half-empty diagonal ones last
-  std::vector<int2> tiles;
-  int npair = 0;
-  const int pairs[FFS_NPAIR][2] = {{4, 4}, {4, 2}, {4, 1}, {2, 2}, {2, 1}, {1, 1}};
-  for (const auto& pr : pairs) {
-    const size_t t0 = tiles.size();
-    for (int i = 0; i < nchunk; ++i)
-      for (int j = i + 1; j < nchunk; ++j)
-        if (ccls[i] == pr[0] && ccls[j] == pr[1]) tiles.push_back(make_int2(i, j));
-    if (pr[0] == pr[1])
-      for (int i = 0; i < nchunk; ++i)
-        if (ccls[i] == pr[0]) tiles.push_back(make_int2(i, i));
-    if (tiles.size() == t0) continue;
-    f.rr[npair] = pr[0];
-    f.rc[npair] = pr[1];
-    f.tile_off[npair] = (int64_t)t0;
-    f.ntile[npair] = (int)(tiles.size() - t0);
-    int grid = 0;
-    if ((e = ffs_prepare(pr[0], pr[1], !padded, V, per_sm, &grid)) != cudaSuccess) return e;
-    f.grid[npair] = std::min(grid, f.ntile[npair]);
-    ++npair;
+  // partial-sum memory: one slot (16 bytes a point) per chunk within the budget (1/8 of the device memory, or
+  // VS_FFS_SLOT_BYTES), else the phased evaluation with groups of S chunks; fewer than 4 slots: none
+  size_t budget = total_b / 8;
+  if (const char* sb = std::getenv("VS_FFS_SLOT_BYTES")) budget = (size_t)std::strtoull(sb, nullptr, 10);
+  const size_t per_slot = (size_t)L.P * sizeof(float4);
+  int S = nchunk;
+  if ((size_t)nchunk * per_slot > budget) {
+    S = (int)std::min<size_t>(budget / per_slot, (size_t)nchunk);
+    if (S < 4) return cudaSuccess;
   }
-  f.tile_off[npair] = (int64_t)tiles.size();
+  const int G = (nchunk + S - 1) / S;
+  // tiles per (phase, pair of classes): whole tiles first, the half-empty diagonal ones last
+  std::vector<int2> tiles;
+  const int pairs[FFS_NPAIR][2] = {{4, 4}, {4, 2}, {4, 1}, {2, 2}, {2, 1}, {1, 1}};
+  int grid_of[FFS_NPAIR] = {};
+  for (int k = 0; k < FFS_NPAIR; ++k)
+    if ((e = ffs_prepare(pairs[k][0], pairs[k][1], !padded, V, per_sm, &grid_of[k])) != cudaSuccess) return e;
+  for (int ga = 0; ga < G; ++ga)
+    for (int gb = ga; gb < G; ++gb) {
+      const int a0 = ga * S, a1 = std::min(nchunk, a0 + S), b0 = gb * S, b1 = std::min(nchunk, b0 + S);
+      FfSymState::Phase ph{(int)f.launch.size(), 0, ga, gb, a1 - a0, b1 - b0};
+      for (int k = 0; k < FFS_NPAIR; ++k) {
+        const size_t t0 = tiles.size();
+        for (int i = a0; i < a1; ++i)
+          for (int j = std::max(b0, i + 1); j < b1; ++j)
+            if (ccls[i] == pairs[k][0] && ccls[j] == pairs[k][1]) tiles.push_back(make_int2(i, j));
+        if (ga == gb && pairs[k][0] == pairs[k][1])
+          for (int i = a0; i < a1; ++i)
+            if (ccls[i] == pairs[k][0]) tiles.push_back(make_int2(i, i));
+        if (tiles.size() == t0) continue;
+        const int nt = (int)(tiles.size() - t0);
+        f.launch.push_back(FfSymState::Launch{pairs[k][0], pairs[k][1], nt, std::min(grid_of[k], nt), (int64_t)t0});
+        ++ph.count;
+      }
+      f.phase.push_back(ph);
+    }
 #define VS_TRY(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
   VS_TRY(dalloc(&f.tiles, (int64_t)tiles.size()));
   VS_TRY(upload(f.tiles, tiles.data(), (int64_t)tiles.size(), st));
-  VS_TRY(dalloc(&f.part, (int64_t)nchunk * L.P));
-  VS_TRY(dalloc(&f.ctr, FFS_NPAIR));
+  VS_TRY(dalloc(&f.part, (int64_t)S * L.P));
+  VS_TRY(dalloc(&f.ctr, (int64_t)f.launch.size()));
+  if (S < nchunk) {  // the chunk of every point, for the phased reduction
+    std::vector<int> pchunk(L.P);
+    for (int c = 0; c < nchunk; ++c)
+      for (int q = chunk[c].x; q < chunk[c].x + chunk[c].y; ++q)
+        for (int i = 0; i < nreal[q]; ++i) pchunk[roff[q] + i] = c;
+    VS_TRY(dalloc(&f.pchunk, L.P));
+    VS_TRY(upload(f.pchunk, pchunk.data(), L.P, st));
+  }
   VS_TRY(dalloc(&f.vid, L.M)); VS_TRY(upload(f.vid, vid.data(), L.M, st));
   VS_TRY(dalloc(&f.poff, L.M)); VS_TRY(upload(f.poff, poff.data(), L.M, st));
   VS_TRY(dalloc(&f.roff, L.M)); VS_TRY(upload(f.roff, roff.data(), L.M, st));
@@ -756,21 +782,20 @@ cudaError_t ffs_setup(FfSymState& f, const Layout& L, bool wanted, cudaStream_t 
   f.V = V;
   f.per_sm = per_sm;
   f.nchunk = nchunk;
-  f.npair = npair;
+  f.slots = S;
+  f.phased = S < nchunk;
   f.on = true;
   return cudaStreamSynchronize(st);
 }
 
-// Zero the tile counters (and the near counts), pad the sources if needed, then one pair kernel per pair of
-// classes. u is added to by ffs_reduce.
-void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cudaStream_t st) {
-  cudaMemsetAsync(f.ctr, 0, FFS_NPAIR * sizeof(unsigned), st);
-  if (a.near_mask) cudaMemsetAsync(B.near_cnt, 0, a.P * sizeof(int), st);
-  if (f.padded) k_ffs_pad<<<a.M, 128, 0, st>>>(a, B.src, f.psrc);
-  for (int k = 0; k < f.npair; ++k) {
-    const FfSymTiles t{f.tiles + f.tile_off[k], f.ntile[k], f.ctr + k};
-    const size_t smem = ffs_smem_bytes(f.rc[k], f.V);
-    const int g = f.grid[k], nt = 32 * FFS_W;
+// The pair kernels of one phase: one persistent launch per pair of classes with tiles in it.
+void ffs_launch_phase(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, int ph, cudaStream_t st) {
+  const FfSymState::Phase& P = f.phase[ph];
+  for (int k = P.first; k < P.first + P.count; ++k) {
+    const FfSymState::Launch& l = f.launch[k];
+    const FfSymTiles t{f.tiles + l.tile_off, l.ntile, f.ctr + k};
+    const size_t smem = ffs_smem_bytes(l.rc, f.V);
+    const int g = l.grid, nt = 32 * FFS_W;
     const float4* c32 = B.centre32;
     const float2 *h2 = B.h2, *gs = B.gsum;
     if (!f.padded) {  // equal N of 32, 64 or 128: a single pair of classes
@@ -778,7 +803,7 @@ void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cu
   (f.V == 8 ? k_farfield_sym<R, R, true, 8><<<g, nt, smem, st>>>(a, t, c32, h2, gs)                           \
             : f.V == 32 ? k_farfield_sym<R, R, true, 32><<<g, nt, smem, st>>>(a, t, c32, h2, gs)              \
                         : k_farfield_sym<R, R, true, 16><<<g, nt, smem, st>>>(a, t, c32, h2, gs))
-      switch (f.rr[k]) {
+      switch (l.rr) {
         case 4: VS_FFS_EQ(4); break;
         case 2: VS_FFS_EQ(2); break;
         default: VS_FFS_EQ(1); break;
@@ -786,7 +811,7 @@ void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cu
 #undef VS_FFS_EQ
       continue;
     }
-    switch (f.rr[k] * 8 + f.rc[k]) {
+    switch (l.rr * 8 + l.rc) {
       case 4 * 8 + 4: k_farfield_sym<4, 4, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
       case 4 * 8 + 2: k_farfield_sym<4, 2, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
       case 4 * 8 + 1: k_farfield_sym<4, 1, false, FFS_V><<<g, nt, smem, st>>>(a, t, c32, h2, gs); break;
@@ -797,8 +822,27 @@ void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, cu
   }
 }
 
-void ffs_reduce(const FfSymArgs& a, const DevLayout& D, double* u, cudaStream_t st) {
-  k_farfield_sym_reduce<<<(int)((a.P + 255) / 256), 256, 0, st>>>(a, D.owner, D.off, u);
+// Zero the tile counters (and the near counts), pad the sources if needed, then the pair kernels; u is added to
+// by ffs_reduce (one pass), or here phase by phase (phased: each phase's slots are reduced before the next
+// phase writes them), the near lists sorted after the last phase.
+void ffs_launch(const FfSymState& f, const FfSymArgs& a, const SourceBufs& B, const DevLayout& D, double* u,
+                cudaStream_t st) {
+  cudaMemsetAsync(f.ctr, 0, f.launch.size() * sizeof(unsigned), st);
+  if (a.near_mask) cudaMemsetAsync(B.near_cnt, 0, a.P * sizeof(int), st);
+  if (f.padded) k_ffs_pad<<<a.M, 128, 0, st>>>(a, B.src, f.psrc);
+  const int rg = (int)((a.P + 255) / 256);
+  for (int ph = 0; ph < (int)f.phase.size(); ++ph) {
+    ffs_launch_phase(f, a, B, ph, st);
+    if (f.phased) {
+      const FfSymState::Phase& P = f.phase[ph];
+      k_ffs_reduce_phase<<<rg, 256, 0, st>>>(a, D.owner, D.off, f.pchunk, P.ga, P.gb, P.na, P.nb, u);
+    }
+  }
+  if (f.phased && a.near_mask) k_ffs_near_sort<<<rg, 256, 0, st>>>(a);
+}
+
+void ffs_reduce(const FfSymState& f, const FfSymArgs& a, const DevLayout& D, double* u, cudaStream_t st) {
+  if (!f.phased) k_farfield_sym_reduce<<<(int)((a.P + 255) / 256), 256, 0, st>>>(a, D.owner, D.off, u);
 }
 
 vs_status far_field(vs_suspension* h) {
@@ -817,8 +861,8 @@ vs_status far_field(vs_suspension* h) {
     VS_LAUNCH(h, "k_farfield_loc", k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src));
   } else if (h->ffs.on) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
-    VS_LAUNCH(h, "k_farfield_sym", ffs_launch(h->ffs, fa, h->B, h->stream));
-    VS_LAUNCH(h, "k_farfield_sym_reduce", ffs_reduce(fa, h->D, h->u, h->stream));
+    VS_LAUNCH(h, "k_farfield_sym", ffs_launch(h->ffs, fa, h->B, h->D, h->u, h->stream));
+    VS_LAUNCH(h, "k_farfield_sym_reduce", ffs_reduce(h->ffs, fa, h->D, h->u, h->stream));
   } else {
     VS_LAUNCH(h, "k_farfield_f32", launch_far_field_f32(h, h->ff_variant, a));
   }
@@ -871,10 +915,10 @@ vs_status tune_symmetric(vs_suspension* h, const char* devname) {
     for (int per_sm : {0, 2}) {
       VS_CK(h, ffs_setup(h->ffs, L, want, h->stream, V, per_sm), "autotune");
       const FfSymArgs fa = ffs_args(h->ffs, L, h->p.near_field ? 1 : 0, h->B, h->err);
-      ffs_launch(h->ffs, fa, h->B, h->stream);
+      ffs_launch(h->ffs, fa, h->B, h->D, h->u, h->stream);
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, h->stream);
-        ffs_launch(h->ffs, fa, h->B, h->stream);
+        ffs_launch(h->ffs, fa, h->B, h->D, h->u, h->stream);
         cudaEventRecord(e1, h->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -2264,8 +2308,8 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
     k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src);
   } else if (h->ffs.on) {
     const FfSymArgs fa = ffs_args(h->ffs, L, h->near_mask, h->B, h->err);
-    ffs_launch(h->ffs, fa, h->B, h->stream);
-    ffs_reduce(fa, h->D, u, h->stream);
+    ffs_launch(h->ffs, fa, h->B, h->D, u, h->stream);
+    ffs_reduce(h->ffs, fa, h->D, u, h->stream);
   } else {
     k_farfield_f32<FF_THREADS, FF_CHUNK><<<grid, FF_THREADS, 0, h->stream>>>(a, h->B.src, h->B.centre32, h->B.h2,
                                                                         h->B.gsum);

@@ -172,3 +172,41 @@ def test_near_list_overflow_is_reported(precision):
     c = plan.counters()
     plan.close()
     assert c["err"] & 8
+
+
+@pytest.mark.parametrize("N,slots", [(32, 4), (UNEVEN, 5)])
+def test_phased_symmetric_far_field_matches_one_pass(N, slots, monkeypatch):
+    # partial-sum memory bounded to `slots` chunk slots a point (VS_FFS_SLOT_BYTES below one slot per chunk):
+    # the chunks are taken in groups of that many, phase by phase (each group pair's tiles, then their slots
+    # reduced). The far field equals the one-pass evaluation's up to the grouping of the double-float sums,
+    # with the same near pairs, and matches the oracle; the same through a far-field plan
+    xs, ys = _grid(150, N, seed=21, close_pair=True)
+    off = offsets(xs)
+    P = int(off[-1])
+    kw = dict(kappa=1.0, mu=1.0, dt=1e-3, flow_kind=1, flow_p=(0.5, 0, 0, 0), near_field=True, autotune=False)
+    a = binding.Suspension(csr(xs, ys), off, **kw)
+    monkeypatch.setenv("VS_FFS_SLOT_BYTES", str(slots * P * 16))
+    b = binding.Suspension(csr(xs, ys), off, **kw)
+    rng = np.random.default_rng(3)
+    f = np.concatenate([np.concatenate([rng.standard_normal(len(x)), rng.standard_normal(len(x))]) for x in xs])
+    dev = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+    plan_b = binding.FarFieldPlan(off, mu=0.7, near_mask=True, precision=0)
+    monkeypatch.delenv("VS_FFS_SLOT_BYTES")
+    plan_a = binding.FarFieldPlan(off, mu=0.7, near_mask=True, precision=0)
+    assert a.farfield_variant()[0] == -1 and b.farfield_variant()[0] == -1
+    a.step()
+    b.step()
+    o = OracleSuspension(xs, ys, Params(**{k: v for k, v in kw.items() if k != "autotune"}))
+    ref = np.concatenate([np.concatenate([ux, uy]) for ux, uy in o.interaction_velocity()])
+    d, e = _rel_l2(b.velocity(), a.velocity()), _rel_l2(b.velocity(), ref)
+    print("phased against one pass %.3e, against the oracle %.3e" % (d, e))
+    assert d <= 1e-12 and e <= 1e-5
+    assert a.counters()["near_pairs"] == b.counters()["near_pairs"] == len(o.near_pairs) > 0
+    ua = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+    ub = torch.empty_like(ua)
+    plan_a.eval(dev(csr(xs, ys)), dev(f), ua)
+    plan_b.eval(dev(csr(xs, ys)), dev(f), ub)
+    assert _rel_l2(ub.cpu().numpy(), ua.cpu().numpy()) <= 1e-12
+    assert plan_a.counters()["near_pairs"] == plan_b.counters()["near_pairs"] > 0
+    for h in (a, b, plan_a, plan_b):
+        h.close()
