@@ -788,15 +788,12 @@ __device__ bool gj_invert_np(const float* src, float* dst, int n) {
   return true;
 }
 
-// The same elimination two exchange steps per barrier (n even): steps k and k + 1 exchange equations k, k + 1
-// with unknowns k, k + 1 at once through the 2 x 2 pivot block P = T[K][K] (K = {k, k + 1}),
-//   T[K][K] <- Q = P^{-1},  T[K][j] <- -Q T[K][j],  T[i][K] <- T[i][K] Q,  T[i][j] <- T[i][j] - T[i][K] Q T[K][j],
-// which equals the two single steps in exact arithmetic (the block pivot's Schur complement). The owners of
-// columns k, k + 1 and rows k, k + 1 publish them before one barrier; every thread forms Q from the four pivot
-// entries and updates its entries with two paired FMAs each. The pivots the single steps would take, P00 and
-// P11 - P10 P01 / P00, are held to the same threshold (GJ_NP_TOL max|A|); a smaller one ends the attempt as in
-// gj_invert_np. Half the barriers of gj_invert_np, whose steps are bound by the barrier and the pivot's latency
-// rather than by the FP32 work.
+// The same elimination two exchange steps per barrier (n even): the owners of columns k, k + 1 and rows k, k + 1
+// publish them before one barrier, and every thread applies both steps to its entries at once, step k + 1's
+// pivot row and column taken as step k leaves them (computed locally from the four published vectors), so the
+// result is that of the two single steps. The pivots P00 and P11 - P10 P01 / P00 are held to the same
+// threshold (GJ_NP_TOL max|A|); a smaller one ends the attempt as in gj_invert_np. Half the barriers of
+// gj_invert_np, whose steps are bound by the barrier and the pivot's latency rather than by the FP32 work.
 template <int RA, int RB, int TC>
 __device__ bool gj_invert_np2(const float* src, float* dst, int n) {
   static_assert(RB % 2 == 0 && RA % 2 == 0 && RA <= 8 && 16 * RA == TC * RB && TC % 2 == 0, "square grid of pairs");
@@ -866,10 +863,14 @@ __device__ bool gj_invert_np2(const float* src, float* dst, int n) {
       float t1 = p00;
       if (!(fabsf(t1) > thr)) { ok = false; t1 = 1.f; }
       const float i1 = gj_rcp(t1);
-      float t2 = fmaf(-p10 * i1, p01, p11);
+      const float a01 = p01 * i1, a10 = p10 * i1;
+      float t2 = fmaf(-a10, p01, p11);  // the pivot of step k + 1 after step k
       if (!(fabsf(t2) > thr)) { ok = false; t2 = 1.f; }
-      const float id = i1 * gj_rcp(t2);  // 1 / det P
-      const float q00 = p11 * id, q01 = -p01 * id, q10 = -p10 * id, q11 = p00 * id;
+      const float i2 = gj_rcp(t2);
+      // the two steps in their sequential form: column k + 1 and row k + 1 as step k leaves them,
+      //   c1'_i = c1_i - c0_i p01 / p00,  r1'_j = r1_j - p10 r0_j / p00,
+      // then T_ij -= c0_i r0_j / p00 + c1'_i r1'_j / t2 (the block inverse's explicit form would amplify
+      // rounding by |P| / t2 where the second pivot is small)
       float c0[RA], c1[RA];
       if constexpr (RA >= 4) {
 #pragma unroll
@@ -885,38 +886,42 @@ __device__ bool gj_invert_np2(const float* src, float* dst, int n) {
         c0[0] = w0.x; c0[1] = w0.y;
         c1[0] = w1.x; c1[1] = w1.y;
       }
+#pragma unroll
+      for (int a = 0; a < RA; ++a) c1[a] = (tr == pr && a == pa) ? -a01 : fmaf(-c0[a], a01, c1[a]);
       float2 u0[H], u1[H];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const float2 r0 = *reinterpret_cast<const float2*>(&rowb[buf][0][tc * RB + 2 * h]);
         const float2 r1 = *reinterpret_cast<const float2*>(&rowb[buf][1][tc * RB + 2 * h]);
-        u0[h] = __ffma2_rn(make_float2(q01, q01), r1, __fmul2_rn(make_float2(q00, q00), r0));
-        u1[h] = __ffma2_rn(make_float2(q11, q11), r1, __fmul2_rn(make_float2(q10, q10), r0));
+        u0[h] = __fmul2_rn(make_float2(i1, i1), r0);
+        u1[h] = __fmul2_rn(make_float2(i2, i2), __ffma2_rn(make_float2(-a10, -a10), r0, r1));
       }
-      // columns k, k + 1: T[i][K] Q through the same update
-      if (tc == kc) {
-        if (kb & 1) { u0[kb >> 1].y = 1.f - q00; u1[kb >> 1].y = -q10; }
-        else { u0[kb >> 1].x = 1.f - q00; u1[kb >> 1].x = -q10; }
-      } else if (tc == kc + 1) {
-        if (kb & 1) { u0[kb >> 1].y = -q01; u1[kb >> 1].y = 1.f - q11; }
-        else { u0[kb >> 1].x = -q01; u1[kb >> 1].x = 1.f - q11; }
+      // columns k, k + 1 through the same update: (u0, u1) there = (1 - i1, a10 i2) and (a01, 1 - i2)
+      const bool ck = tc == kc, ck1 = tc == kc + 1;
+      float2 m0 = u0[kb >> 1], m1 = u1[kb >> 1];
+      if (ck || ck1) {
+        const float v0 = ck ? 1.f - i1 : a01, v1 = ck ? a10 * i2 : 1.f - i2;
+        if (kb & 1) { m0.y = v0; m1.y = v1; } else { m0.x = v0; m1.x = v1; }
       }
 #pragma unroll
       for (int a = 0; a < RA; ++a)
 #pragma unroll
         for (int h = 0; h < H; ++h) {
-          T[a][h] = __ffma2_rn(make_float2(-c0[a], -c0[a]), u0[h], T[a][h]);
-          T[a][h] = __ffma2_rn(make_float2(-c1[a], -c1[a]), u1[h], T[a][h]);
+          const float2 e0 = (h == (kb >> 1)) ? m0 : u0[h], e1 = (h == (kb >> 1)) ? m1 : u1[h];
+          T[a][h] = __ffma2_rn(make_float2(-c0[a], -c0[a]), e0, T[a][h]);
+          T[a][h] = __ffma2_rn(make_float2(-c1[a], -c1[a]), e1, T[a][h]);
         }
-      if (tr == pr || tr == pr + 1) {  // rows k, k + 1: -Q T[K][j], and Q in columns k, k + 1
+      if (tr == pr || tr == pr + 1) {  // rows k, k + 1 as the two exchange steps leave them
         const bool second = tr != pr;
 #pragma unroll
         for (int a = 0; a < RA; ++a)
           if (a == pa) {
 #pragma unroll
-            for (int h = 0; h < H; ++h) T[a][h] = second ? make_float2(-u1[h].x, -u1[h].y) : make_float2(-u0[h].x, -u0[h].y);
-            if (tc == kc || tc == kc + 1) {
-              const float qv = second ? (tc == kc ? q10 : q11) : (tc == kc ? q00 : q01);
+            for (int h = 0; h < H; ++h)
+              T[a][h] = second ? make_float2(-u1[h].x, -u1[h].y)
+                               : __ffma2_rn(make_float2(a01, a01), u1[h], make_float2(-u0[h].x, -u0[h].y));
+            if (ck || ck1) {
+              const float qv = second ? (ck ? -a10 * i2 : i2) : (ck ? fmaf(a01 * a10, i2, i1) : -a01 * i2);
               if (kb & 1) T[a][kb >> 1].y = qv; else T[a][kb >> 1].x = qv;
             }
           }

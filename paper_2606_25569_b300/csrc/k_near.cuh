@@ -642,10 +642,114 @@ __global__ void __launch_bounds__(NMAX) k_layer_features(VesIndex vi, const int*
 
 // FP32 Cholesky of (Phi + lam I) and the two RBF weight vectors for 5N <= 320, the lower triangle held
 // packed in shared memory (row i at i (i + 1) / 2; dynamic shared memory near_rbf_smem(5N) bytes). One CTA
-// per near vesicle: the trailing update of step k by warps over rows and lanes over columns, the two
-// triangular solves by warp 0 (forward by rows, backward by columns, both reading rows of L).
+// per near vesicle, right-looking and blocked by panels of RBF_NB columns: warp 0 factors the panel's
+// diagonal block (a column a lane, in registers), one thread a row solves the panel below it against that
+// block (also copied, transposed, to a panel buffer), and the trailing triangle takes the panel's
+// rank-RBF_NB update in 4 x 4 register tiles; three barriers a panel instead of two a column. The
+// triangular solves go by the same panels (warp 0 the diagonal block, every thread a row of the update
+// below or above it), and one step of iterative refinement follows (the residual with Phi formed again),
+// which removes the factorisation's rounding growth from the weights. The coordinate differences are taken
+// in float pairs (hi + lo of each layer point relative to the first), accurate to FP32 in the difference.
 constexpr int NEAR_RBF_SMEM_N = 320;
-inline size_t near_rbf_smem(int n) { return ((size_t)n * (n + 1) / 2 + 3 * (size_t)n) * sizeof(float); }
+constexpr int RBF_NB = 16;  // panel width
+// The packed triangle (n (n + 1) / 2 floats, rounded up to a multiple of 4), then the panel buffer
+// (RBF_NB rows of rbf_ld(n) floats; in the solves: the coordinates and the vectors).
+__host__ __device__ inline int rbf_ld(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline size_t rbf_tri(int n) { return ((size_t)n * (n + 1) / 2 + 3) & ~(size_t)3; }
+inline size_t near_rbf_smem(int n) { return (rbf_tri(n) + (size_t)RBF_NB * rbf_ld(n)) * sizeof(float); }
+
+__device__ __forceinline__ float rbf_phi(const float* c, int ld, int i, int j, float ie2) {
+  // c: x hi, x lo, y hi, y lo rows of ld floats
+  const float dx = (c[i] - c[j]) + (c[ld + i] - c[ld + j]);
+  const float dy = (c[2 * ld + i] - c[2 * ld + j]) + (c[3 * ld + i] - c[3 * ld + j]);
+  float p = expf(-(dx * dx + dy * dy) * ie2);
+  if (i == j) p += (float)NEAR_RBF_NUGGET;
+  return p;
+}
+
+// The layer points relative to the first as float pairs into c (four rows of ld floats).
+__device__ __forceinline__ void rbf_coords(const double* LX, const double* LY, int n, int ld, float* c) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = LX[i] - LX[0], y = LY[i] - LY[0];
+    const float xh = (float)x, yh = (float)y;
+    c[i] = xh;
+    c[ld + i] = (float)(x - (double)xh);
+    c[2 * ld + i] = yh;
+    c[3 * ld + i] = (float)(y - (double)yh);
+  }
+}
+
+// Solves L L^T z = b in place for two vectors (b1, b2 in shared memory), L packed in sA, by panels of RBF_NB:
+// forward, then backward; all threads of the CTA (two barriers a panel and direction).
+__device__ void rbf_solve2(const float* sA, int n, float* b1, float* b2) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c0 = 0; c0 < n; c0 += RBF_NB) {  // forward: L y = b
+    const int w = min(RBF_NB, n - c0), c1 = c0 + w;
+    if (wid == 0) {  // lane r: row c0 + r of the diagonal block; y_t broadcast as it is found
+      const int i = c0 + lane;
+      const float* row = sA + (size_t)i * (i + 1) / 2 + c0;
+      float a1 = lane < w ? b1[i] : 0.f, a2 = lane < w ? b2[i] : 0.f;
+      const float dii = lane < w ? row[lane] : 1.f;
+#pragma unroll
+      for (int t = 0; t < RBF_NB; ++t) {
+        if (t >= w) break;
+        if (lane == t) { a1 /= dii; a2 /= dii; }
+        const float y1 = __shfl_sync(0xffffffffu, a1, t), y2 = __shfl_sync(0xffffffffu, a2, t);
+        if (lane > t && lane < w) {
+          const float l = row[t];
+          a1 = fmaf(-l, y1, a1);
+          a2 = fmaf(-l, y2, a2);
+        }
+      }
+      if (lane < w) { b1[i] = a1; b2[i] = a2; }
+    }
+    __syncthreads();
+    for (int i = c1 + tid; i < n; i += blockDim.x) {
+      const float* row = sA + (size_t)i * (i + 1) / 2 + c0;
+      float s1 = b1[i], s2 = b2[i];
+      for (int t = 0; t < w; ++t) {
+        s1 = fmaf(-row[t], b1[c0 + t], s1);
+        s2 = fmaf(-row[t], b2[c0 + t], s2);
+      }
+      b1[i] = s1;
+      b2[i] = s2;
+    }
+    __syncthreads();
+  }
+  const int last = ((n - 1) / RBF_NB) * RBF_NB;
+  for (int c0 = last; c0 >= 0; c0 -= RBF_NB) {  // backward: L^T z = y
+    const int w = min(RBF_NB, n - c0), c1 = c0 + w;
+    if (wid == 0) {  // lane j: unknown c0 + j; z_i broadcast as it is found, from the last row up
+      const int j = c0 + lane;
+      float a1 = lane < w ? b1[j] : 0.f, a2 = lane < w ? b2[j] : 0.f;
+      const float djj = lane < w ? sA[(size_t)j * (j + 1) / 2 + j] : 1.f;
+#pragma unroll
+      for (int t = RBF_NB - 1; t >= 0; --t) {
+        if (t >= w) continue;
+        if (lane == t) { a1 /= djj; a2 /= djj; }
+        const float z1 = __shfl_sync(0xffffffffu, a1, t), z2 = __shfl_sync(0xffffffffu, a2, t);
+        if (lane < t) {  // L[c0 + t][c0 + lane]
+          const float l = sA[(size_t)(c0 + t) * (c0 + t + 1) / 2 + c0 + lane];
+          a1 = fmaf(-l, z1, a1);
+          a2 = fmaf(-l, z2, a2);
+        }
+      }
+      if (lane < w) { b1[j] = a1; b2[j] = a2; }
+    }
+    __syncthreads();
+    for (int k = tid; k < c0; k += blockDim.x) {  // earlier unknowns: y_k -= sum_i L[i][k] z_i
+      float s1 = b1[k], s2 = b2[k];
+      for (int t = 0; t < w; ++t) {
+        const float l = sA[(size_t)(c0 + t) * (c0 + t + 1) / 2 + k];
+        s1 = fmaf(-l, b1[c0 + t], s1);
+        s2 = fmaf(-l, b2[c0 + t], s2);
+      }
+      b1[k] = s1;
+      b2[k] = s2;
+    }
+    __syncthreads();
+  }
+}
 
 __global__ void __launch_bounds__(512) k_near_rbf_smem(VesIndex vi, const int* __restrict__ has_near,
                                                        const double* __restrict__ length, NearBufs nb,
@@ -657,9 +761,8 @@ __global__ void __launch_bounds__(512) k_near_rbf_smem(VesIndex vi, const int* _
   const int N = vi.N[v];
   const int n = 5 * N;
   const int64_t o = vi.off[v];
-  float* colk = sA + (size_t)n * (n + 1) / 2;
-  float* y1 = colk + n;
-  float* y2 = y1 + n;
+  float* Pt = sA + rbf_tri(n);  // [RBF_NB][ld]: the panel's rows below its diagonal block, transposed
+  const int ld = rbf_ld(n);
   const double h = length[v] / N;
   const float ie2 = (float)(1.0 / (NEAR_RBF_C * h * NEAR_RBF_C * h));
   double* L = nb.layer + 30 * o;
@@ -667,81 +770,151 @@ __global__ void __launch_bounds__(512) k_near_rbf_smem(VesIndex vi, const int* _
   const double* LY = L + 5 * N;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) bad = 0;
+  rbf_coords(LX, LY, n, ld, Pt);
+  __syncthreads();
   for (int i = wid; i < n; i += nw) {
     float* row = sA + (size_t)i * (i + 1) / 2;
-    for (int j = lane; j <= i; j += 32) {
-      const float dx = (float)(LX[i] - LX[j]), dy = (float)(LY[i] - LY[j]);
-      float p = expf(-(dx * dx + dy * dy) * ie2);
-      if (i == j) p += (float)NEAR_RBF_NUGGET;
-      row[j] = p;
-    }
+    for (int j = lane; j <= i; j += 32) row[j] = rbf_phi(Pt, ld, i, j, ie2);
   }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const float dkk = sA[(size_t)k * (k + 1) / 2 + k];
-    const float d = dkk > 0.f ? sqrtf(dkk) : 1.f;
-    if (tid == 0 && !(dkk > 0.f)) bad = 1;
-    const float inv = 1.f / d;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-      float* a = sA + (size_t)i * (i + 1) / 2 + k;
-      const float l = *a * inv;
-      *a = l;
-      colk[i] = l;
+  for (int c0 = 0; c0 < n; c0 += RBF_NB) {
+    const int w = min(RBF_NB, n - c0), c1 = c0 + w, m = n - c1;
+    if (wid == 0) {  // diagonal block: lane c holds column c0 + c (rows c0 + r, r >= c)
+      float a[RBF_NB];
+#pragma unroll
+      for (int r = 0; r < RBF_NB; ++r)
+        a[r] = (lane < w && r < w && r >= lane) ? sA[(size_t)(c0 + r) * (c0 + r + 1) / 2 + c0 + lane] : 0.f;
+#pragma unroll
+      for (int k = 0; k < RBF_NB; ++k) {
+        if (k >= w) break;
+        const float dkk = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(dkk > 0.f) && lane == 0) bad = 1;
+        const float d = dkk > 0.f ? sqrtf(dkk) : 1.f;
+        if (lane == k) {
+          const float inv = 1.f / d;
+#pragma unroll
+          for (int r = 0; r < RBF_NB; ++r) a[r] = (r == k) ? d : (r > k ? a[r] * inv : a[r]);
+        }
+        // column j = lane > k: a[r] -= L[r][k] L[j][k] for r >= j (column k sits in lane k; L[j][k] arrives
+        // at r == j, before the first r it is needed for)
+        float ljk = 0.f;
+#pragma unroll
+        for (int r = 0; r < RBF_NB; ++r) {
+          const float lrk = __shfl_sync(0xffffffffu, a[r], k);
+          if (r == lane) ljk = lrk;
+          if (lane > k && lane < w && r >= lane) a[r] = fmaf(-lrk, ljk, a[r]);
+        }
+      }
+      if (lane < w)
+#pragma unroll
+        for (int r = 0; r < RBF_NB; ++r)
+          if (r < w && r >= lane) sA[(size_t)(c0 + r) * (c0 + r + 1) / 2 + c0 + lane] = a[r];
     }
     __syncthreads();
-    if (tid == 0) sA[(size_t)k * (k + 1) / 2 + k] = d;
-    for (int i = k + 1 + wid; i < n; i += nw) {
-      const float li = colk[i];
-      float* row = sA + (size_t)i * (i + 1) / 2;
-      for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fmaf(-li, colk[j], row[j]);
+    if (m == 0) break;
+    // the panel below the diagonal block: row i solves L[i][c0..c1) L_kk^T = A[i][c0..c1)
+    for (int q = tid; q < m; q += blockDim.x) {
+      const int i = c1 + q;
+      float* row = sA + (size_t)i * (i + 1) / 2 + c0;
+      float x[RBF_NB];
+#pragma unroll
+      for (int j = 0; j < RBF_NB; ++j) {
+        if (j >= w) break;
+        float acc = row[j];
+        const float* lj = sA + (size_t)(c0 + j) * (c0 + j + 1) / 2 + c0;  // row c0 + j of the diagonal block
+#pragma unroll
+        for (int t = 0; t < RBF_NB; ++t)
+          if (t < j) acc = fmaf(-x[t], lj[t], acc);
+        x[j] = acc / lj[j];
+      }
+#pragma unroll
+      for (int j = 0; j < RBF_NB; ++j)
+        if (j < w) {
+          row[j] = x[j];
+          Pt[j * ld + q] = x[j];
+        }
+    }
+    __syncthreads();
+    // trailing triangle: A[i][j] -= sum_t L[i][t] L[j][t] over the panel columns t, tiles of 4 x 4 (tile I >= J)
+    const int mb = (m + 3) >> 2;
+    const int ntile = mb * (mb + 1) / 2;
+    for (int t = tid; t < ntile; t += blockDim.x) {
+      int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while (I * (I + 1) / 2 > t) --I;
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      const int J = t - I * (I + 1) / 2;
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int u = 0; u < w; ++u) {  // entries past m in the last tile are stale and only reach discarded sums
+        const float4 pi = *reinterpret_cast<const float4*>(&Pt[u * ld + 4 * I]);
+        const float4 pj = *reinterpret_cast<const float4*>(&Pt[u * ld + 4 * J]);
+        const float vi[4] = {pi.x, pi.y, pi.z, pi.w}, vj[4] = {pj.x, pj.y, pj.z, pj.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(vi[a], vj[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = c1 + 4 * I + a;
+        if (4 * I + a >= m) continue;
+        float* row = sA + (size_t)i * (i + 1) / 2;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = c1 + 4 * J + b;
+          if (4 * J + b < m && j <= i) row[j] -= acc[a][b];
+        }
+      }
     }
     __syncthreads();
   }
   if (bad && tid == 0) atomicOr(err, ERR_PIVOT);
+  // the panel buffer now holds the coordinates (4 ld), the weights (2 ld) and the residuals (2 ld)
+  float* crd = Pt;
+  float* w1 = Pt + 4 * ld;
+  float* w2 = w1 + ld;
+  float* r1 = w2 + ld;
+  float* r2 = r1 + ld;
   const double* UX = L + 10 * N;
   const double* UY = L + 15 * N;
-  for (int i = tid; i < n; i += blockDim.x) { y1[i] = (float)UX[i]; y2[i] = (float)UY[i]; }
+  rbf_coords(LX, LY, n, ld, crd);
+  for (int i = tid; i < n; i += blockDim.x) { w1[i] = (float)UX[i]; w2[i] = (float)UY[i]; }
   __syncthreads();
-  if (wid == 0) {
-    // forward L y = u: row i of L is contiguous
-    for (int i = 0; i < n; ++i) {
-      const float* row = sA + (size_t)i * (i + 1) / 2;
-      float s1 = 0.f, s2 = 0.f;
-      for (int k = lane; k < i; k += 32) {
-        s1 = fmaf(row[k], y1[k], s1);
-        s2 = fmaf(row[k], y2[k], s2);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-      }
-      if (lane == 0) {
-        y1[i] = (y1[i] - s1) / row[i];
-        y2[i] = (y2[i] - s2) / row[i];
-      }
-      __syncwarp();
+  rbf_solve2(sA, n, w1, w2);
+  // refinement: r = u - (Phi + lam I) w with the same FP32 Phi formed again, its products and sums
+  // compensated (the exact product error by fma, Neumaier sums, lanes combined in FP64), w += (L L^T)^{-1} r
+  for (int i = wid; i < n; i += nw) {
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    for (int j = lane; j < n; j += 32) {
+      const float p = rbf_phi(crd, ld, i, j, ie2);
+      const float q1 = p * w1[j], q2 = p * w2[j];
+      c1 += fmaf(p, w1[j], -q1);
+      c2 += fmaf(p, w2[j], -q2);
+      neumaier_add(s1, c1, q1);
+      neumaier_add(s2, c2, q2);
     }
-    // backward L^T w = y by columns: w_i = y_i / L_ii, then y_k -= L_ik w_i for k < i (row i of L)
-    for (int i = n - 1; i >= 0; --i) {
-      const float* row = sA + (size_t)i * (i + 1) / 2;
-      const float w1 = y1[i] / row[i], w2 = y2[i] / row[i];
-      __syncwarp();
-      for (int k = lane; k < i; k += 32) {
-        y1[k] = fmaf(-row[k], w1, y1[k]);
-        y2[k] = fmaf(-row[k], w2, y2[k]);
-      }
-      if (lane == 0) {
-        y1[i] = w1;
-        y2[i] = w2;
-      }
-      __syncwarp();
+    double d1 = (double)s1 + (double)c1, d2 = (double)s2 + (double)c2;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+    }
+    if (lane == 0) {
+      r1[i] = (float)(UX[i] - d1);
+      r2[i] = (float)(UY[i] - d2);
     }
   }
   __syncthreads();
+  rbf_solve2(sA, n, r1, r2);
   double* WX = L + 20 * N;
   double* WY = L + 25 * N;
-  for (int i = tid; i < n; i += blockDim.x) { WX[i] = y1[i]; WY[i] = y2[i]; }
+  for (int i = tid; i < n; i += blockDim.x) {
+    WX[i] = (double)w1[i] + (double)r1[i];
+    WY[i] = (double)w2[i] + (double)r2[i];
+  }
 }
 
 // FP32 Cholesky of (Phi + lam I) and the two RBF weight vectors. One CTA per near vesicle.
