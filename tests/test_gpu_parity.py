@@ -481,3 +481,36 @@ def test_near_field_ying_zorin_matches_oracle(N):
     o.step()
     gx, gy = split(g.positions(), counts)
     assert rel_err_per_vesicle(gx, gy, o.xs, o.ys) <= 1e-9
+
+
+@pytest.mark.parametrize("yz", [True, False])
+def test_two_vesicles_sliding_past_each_other_in_shear(yz):
+    # the two-vesicle shear interaction: vesicles on neighbouring streamlines of u = (y, 0), the upper one
+    # behind and a fraction of a spacing above the lower one's top, slide past each other in near contact;
+    # 30 steps with the near field (Ying-Zorin or layers + RBF) on both sides, FP64 far field. The near
+    # velocities' FP32 parts (the Ying-Zorin sums, the RBF solve) set the tolerance (measured 2.7e-10 and
+    # 2.8e-9)
+    from oracle.spectral import Geometry
+    rng = np.random.default_rng(17)
+    N = 32
+    x0, y0 = vesicle_outline(N, 0.7, 1.0, 1e-2, rng, 0.0)
+    x1, y1 = vesicle_outline(N, 0.7, 1.0, 1e-2, rng, 0.0)
+    h = Geometry(x0, y0).h
+    x1 = x1 - 1.2
+    y1 = y1 + (y0.max() - y1.min()) + 0.6 * h
+    xs, ys = [x0, x1], [y0, y1]
+    kw = dict(kappa=1.0, mu=1.0, dt=2e-3, flow_kind=1, flow_p=(1.0, 0, 0, 0), near_field=True)
+    o = OracleSuspension(xs, ys, Params(near_yz=yz, **kw))
+    g = binding.Suspension(csr(xs, ys), offsets(xs), farfield_fp64=True, near_yz=yz, **kw)
+    near_steps, worst = 0, 0.0
+    for k in range(30):
+        o.step()
+        g.step()
+        near_steps += len(o.near_pairs) > 0
+        gx, gy = split(g.positions(), [N, N])
+        worst = max(worst, rel_err_per_vesicle(gx, gy, o.xs, o.ys))
+    print("two vesicles in shear (%s): %d of 30 steps with near pairs, worst position difference %.2e"
+          % ("Ying-Zorin" if yz else "RBF", near_steps, worst))
+    assert near_steps >= 20
+    assert worst <= (1e-9 if yz else 1e-8), worst
+    g.close()
