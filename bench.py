@@ -49,6 +49,10 @@ FFS_DRAM_READ, FFS_DRAM_WRITE = 3.19e6, 195.51e6
 FFS_DRAM_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one-pass capture at 2000 x 64"
 # learned advection and tension: velocity modes expanded and column modes kept, training epochs
 FLOW_KF, FLOW_KOUT, FLOW_EPOCHS = 8, 24, 60
+# hybrid training data and schedule: snapshots (15 steps apart) of a differently seeded suspension, epochs of
+# the relaxation network, exact steps every HYBRID_EVERY steps (learned relaxation only) or FLOW_EVERY (with
+# the learned advection and tension)
+HYBRID_SNAPSHOTS, HYBRID_EPOCHS, HYBRID_EVERY, FLOW_EVERY = 128, 100, 3, 2
 # learned near field: every density mode below the Nyquist one (the membrane force's high modes carry most of
 # the near-field correction: on the oracle, keeping modes <= 24 of a 64-point vesicle leaves 20% of it out)
 NEAR_SNAPSHOTS, NEAR_EPOCHS = 16, 40
@@ -599,27 +603,34 @@ def _time_steps(sus, n, stream):
     return e0.elapsed_time(e1) / n
 
 
+def _window_len(key):
+    a, b = key.split("-")
+    return int(b) - int(a)
+
+
 def long_run_arms(wl, args, stream):
     """Variants of the step against the plain step (all-pairs point sums) from the same state:
-    * hybrid: learned relaxation on every other step, exact relaxation on the others and for vesicles in
-      near pairs or within four spacings of another vesicle; the network trained on the GPU on exact
-      relaxation pairs of a differently seeded suspension (64 snapshots 15 steps apart);
+    * hybrid: learned relaxation, exact relaxation on every HYBRID_EVERY-th step and for vesicles in near
+      pairs or within four spacings of another vesicle; the network trained on the GPU on exact relaxation
+      pairs of a differently seeded suspension (HYBRID_SNAPSHOTS snapshots 15 steps apart);
     * farfield_multipole: the plain step with the vesicle-multipole far field;
     * hybrid_multipole: both;
     * hybrid_flow (and hybrid_flow_multipole): the hybrid step with the advection and the tension of every step
       from two more networks (Sec. 3.2, Eqs. advectionMap and advTenMap), trained on exact columns of the
       same snapshots.
-    Each reports its throughput (CUDA events) and the mean over vesicles of the centred relative shape
-    error (App. B) against the plain step after 10 .. args.hybrid_steps steps."""
+    Each reports the mean over vesicles of the centred relative shape error (App. B) against the plain step
+    after 10 .. args.hybrid_steps steps, and its throughput over that whole run (CUDA events per window; value
+    and vs_plain against the plain run of the same steps), with the first steps' throughput beside it."""
     from paper_2606_25569_b300 import binding, train
     from paper_2606_25569_b300.workloads import poiseuille_dense
-    kmax, exact_every, width, Kf, Kout = 16, 2, 1024, FLOW_KF, FLOW_KOUT
+    kmax, width, Kf, Kout = 16, 1024, FLOW_KF, FLOW_KOUT
     t0 = time.time()
-    X, Y, A, T = train.hybrid_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), 64, 15, stream, kmax, Kf, Kout)
+    X, Y, A, T = train.hybrid_samples(poiseuille_dense(M=wl.M, N=args.N, seed=105), HYBRID_SNAPSHOTS, 15, stream,
+                                      kmax, Kf, Kout)
     t_data = time.time() - t0
     hid = (width, width, width)
-    r = train.train_relaxation(X, Y, hidden=hid, epochs=40, batch=1024, lr=1e-3, lr_min=1e-5, stream=stream,
-                               serve_batch=wl.M)
+    r = train.train_relaxation(X, Y, hidden=hid, epochs=HYBRID_EPOCHS, batch=1024, lr=1e-3, lr_min=1e-5,
+                               stream=stream, serve_batch=wl.M)
     t_train = time.time() - t0 - t_data
     ra = train.train_relaxation(X, A, hidden=hid, epochs=FLOW_EPOCHS, batch=1024, lr=1e-3, lr_min=1e-5, beta=0.0,
                                 stream=stream, serve_batch=wl.M)
@@ -640,11 +651,11 @@ def long_run_arms(wl, args, stream):
                          "(Eqs. advectionMap, advTenMap, S_sigma), learned in every step"}
     kw = dict(kappa=wl.kappa, mu=wl.mu, dt=wl.dt, corr_tol=0.01, flow_kind=wl.flow_kind, flow_p=wl.flow_p,
               near_field=True, stream=stream, use_graph=True)
-    variants = {"hybrid": dict(mode=1, exact_every=exact_every),
+    variants = {"hybrid": dict(mode=1, exact_every=HYBRID_EVERY),
                 "farfield_multipole": dict(farfield_multipole=True),
-                "hybrid_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True),
-                "hybrid_flow": dict(mode=1, exact_every=exact_every, flow=True),
-                "hybrid_flow_multipole": dict(mode=1, exact_every=exact_every, farfield_multipole=True, flow=True)}
+                "hybrid_multipole": dict(mode=1, exact_every=HYBRID_EVERY, farfield_multipole=True),
+                "hybrid_flow": dict(mode=1, exact_every=FLOW_EVERY, flow=True),
+                "hybrid_flow_multipole": dict(mode=1, exact_every=FLOW_EVERY, farfield_multipole=True, flow=True)}
 
     def make(cfg):
         cfg = dict(cfg)
@@ -661,7 +672,8 @@ def long_run_arms(wl, args, stream):
         sus = make(cfg)
         sus.step(4)
         sus.sync()
-        n = 2 * max(2, args.steps // 2)  # even: learned and exact relaxation alternate
+        per = cfg.get("exact_every", 1)  # whole cycles of learned and exact relaxation
+        n = per * max(2, args.steps // per)
         ms = _time_steps(sus, n, stream)
         prof = {}
         if "multipole" in name:
@@ -670,7 +682,8 @@ def long_run_arms(wl, args, stream):
             prof = sus.profile_read()
             sus.profile(False)
         sus.close()
-        out[name] = {"value": wl.M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps_timed": n}
+        out[name] = {"unit": UNIT, "early": {"value": wl.M / (ms * 1e-3), "ms_per_step": ms,
+                                             "steps_timed": "%d after 4" % n}}
         if prof:
             out[name]["far_field_ms_per_step"] = sum(v[0] for k, v in prof.items()
                                                      if k in ("k_ff_moments", "k_ff_local", "k_farfield_loc")) / 2
@@ -678,9 +691,9 @@ def long_run_arms(wl, args, stream):
             out[name]["flow_networks"] = flow_nets
         if cfg.get("mode", 0) == 1:
             out[name]["net"] = net
-            out[name]["exact_every"] = exact_every
+            out[name]["exact_every"] = cfg["exact_every"]
             out[name]["fallback"] = ("exact relaxation on every %d-th step and for vesicles within 4 spacings h of "
-                                     "another vesicle" % exact_every)
+                                     "another vesicle" % cfg["exact_every"])
         if cfg.get("farfield_multipole"):
             out[name]["far_field"] = ("order-12 vesicle expansions translated to local expansions about each target "
                                       "vesicle's centre for vesicle pairs farther apart than twice the sum of "
@@ -731,7 +744,13 @@ def long_run_arms(wl, args, stream):
         out[name].update({"shape_error_mean_by_step": errs[name], "after_steps": args.hybrid_steps,
                           "meets_shape_error_1e-2": bool(last is not None and last <= 1e-2),
                           "windows": windows[name], "plain_windows": plain_windows})
-        # throughput over the last window of the long run (both arms timed on the same steps)
+        # throughput over the whole run and over its last window (the plain run timed on the same steps)
+        if windows[name] and name not in failed:
+            tot = sum(w["ms_per_step"] * _window_len(k) for k, w in windows[name].items())
+            ptot = sum(plain_windows[k]["ms_per_step"] * _window_len(k) for k in windows[name])
+            nst = sum(_window_len(k) for k in windows[name])
+            out[name].update({"value": wl.M * nst / (tot * 1e-3), "ms_per_step": tot / nst, "vs_plain": ptot / tot,
+                              "steps_timed": "0-%d" % nst, "plain_ms_per_step": ptot / nst})
         if windows[name]:
             key = list(windows[name])[-1]
             w = windows[name][key]
@@ -893,7 +912,10 @@ def run_gpu(args):
     if rank == 0 and not args.no_hybrid:
         arms = long_run_arms(wl, args, stream)
         for v in arms.values():
-            v["vs_plain"] = v["value"] / (value / world)  # both single-GPU throughputs
+            if "vs_plain" not in v:  # a run that failed: its first steps against the headline
+                v["vs_plain"] = v["early"]["value"] / (value / world)
+            if "value" not in v:
+                v["value"] = v["early"]["value"]
             if implicit:
                 v["vs_implicit"] = v["value"] / implicit["value"]
     cpu = None
