@@ -95,3 +95,80 @@ def test_local_expansion_matches_direct_sum_at_a_separated_vesicle():
         pw = wa[:, None] ** np.arange(P + 1)[None, :]
         u = C + 0.5 * (pw @ H) + 0.5 * np.conj(pw @ K) + 0.5 * wa * np.conj(pw @ S)
         assert np.max(np.abs(u - (ux + 1j * uy))) <= tol * scale, (sep, np.max(np.abs(u - (ux + 1j * uy))) / scale)
+
+
+def _moments(s, g, P):
+    """The expansion's series about the sources' centre: (A0, t, e, sa) with t, e, sa the coefficients of
+    zeta^1 .. zeta^(P+1) of T1, E and S_A (T1 and the B part of E truncated at P, as the kernels hold them)."""
+    A = np.array([np.sum(g * s ** k) for k in range(P + 2)])
+    B = np.array([np.sum(g * np.conj(s) ** k) for k in range(P + 2)])
+    D = np.array([np.sum(np.conj(g) * s * np.conj(s) ** k) for k in range(P + 2)])
+    t = np.array([A[k] / k if k <= P else 0.0 for k in range(1, P + 2)])
+    sa = np.array([A[k - 1] for k in range(1, P + 2)])
+    e = np.array([(np.conj(B[k]) / k if k <= P else 0.0) - np.conj(D[k - 1]) for k in range(1, P + 2)])
+    return A[0], t, e, sa
+
+
+def _field(A0, t, e, sa, q):
+    """-A0 log|q| + A0/2 + T1/2 + conj(E)/2 + q conj(S_A)/2 at q (zeta = 1/q)."""
+    z = 1.0 / q
+    zk = z ** np.arange(1, len(t) + 1)
+    return -A0 * np.log(abs(q)) + 0.5 * A0 + 0.5 * (t @ zk) + 0.5 * np.conj(e @ zk) + 0.5 * q * np.conj(sa @ zk)
+
+
+def _shift(A0, t, e, sa, delta):
+    """The expansion about c moved to c + delta (multipole-to-multipole): with q = q' + delta, each of
+    Phi = -A0 log q + T1, Psi = -conj(A0) log q + E and S_A re-expanded in 1/q' by
+    b_l = alpha (-delta)^l / l + sum_{k<=l} a_k C(l-1, k-1) (-delta)^(l-k), then E' += conj(delta) S_A'
+    (the term q conj(S_A) = q' conj(S_A) + conj(conj(delta) S_A))."""
+    n = len(t)
+
+    def re(a, alpha):
+        return np.array([alpha * (-delta) ** l / l + sum(a[k - 1] * comb(l - 1, k - 1) * (-delta) ** (l - k)
+                                                         for k in range(1, l + 1)) for l in range(1, n + 1)])
+    t2, e2, s2 = re(t, A0), re(e, np.conj(A0)), re(sa, 0.0)
+    return A0, t2, e2 + np.conj(delta) * s2, s2
+
+
+def test_shifted_expansion_matches_direct_sum():
+    # two vesicles' expansions moved to a common centre and added reproduce the direct sum of both beyond the
+    # disc that holds them; the error decays like (R/|q|)^(P+2)
+    rng = np.random.default_rng(7)
+    N, R, P = 64, 0.1, 12
+    parts, xs, ys, fxs, fys = [], [], [], [], []
+    for k, (ox, oy) in enumerate(((0.0, 0.0), (0.23, -0.11))):
+        x, y = vesicle_outline(N, 0.65, R, 1e-2, rng, 0.3 + k)
+        xs.append(x + ox)
+        ys.append(y + oy)
+        fxs.append(rng.standard_normal(N))
+        fys.append(rng.standard_normal(N))
+    w, _ = source_weights(xs, ys)
+    cc = np.array([0.15, -0.02])  # the common centre
+    rho, scale = 0.0, 0.0
+    tot = None
+    for v in range(2):
+        cv = np.array([xs[v].mean(), ys[v].mean()])
+        s = (xs[v] - cv[0]) + 1j * (ys[v] - cv[1])
+        g = (fxs[v] + 1j * fys[v]) * w[v] / (4 * np.pi)
+        rho = max(rho, np.abs((xs[v] - cc[0]) + 1j * (ys[v] - cc[1])).max())
+        scale += np.sqrt(np.mean(np.abs(g) ** 2)) * N
+        ex = _shift(*_moments(s, g, P), (cc[0] - cv[0]) + 1j * (cc[1] - cv[1]))
+        tot = ex if tot is None else tuple(a + b for a, b in zip(tot, ex))
+    for dist, tol in ((3.0, 1e-6), (6.0, 1e-10)):
+        ang = rng.uniform(0, 2 * np.pi)
+        q = dist * rho * np.exp(1j * ang)
+        tx, ty = np.array([cc[0] + q.real]), np.array([cc[1] + q.imag])
+        ux, uy, _ = far_field(xs + [tx], ys + [ty], fxs + [np.zeros(1)], fys + [np.zeros(1)], 1.0,
+                              near_mask=False, targets=[2 * N])
+        u = _field(*tot, q)
+        err = abs(u - (ux[0] + 1j * uy[0])) / scale
+        assert err <= tol, (dist, err)
+    # and the shift by zero changes nothing; two shifts compose
+    A0, t, e, sa = _moments(s, g, P)
+    for a, b in zip(_shift(A0, t, e, sa, 0.0), (A0, t, e, sa)):
+        assert np.allclose(a, b, rtol=0, atol=1e-15 * scale)
+    d1, d2 = 0.03 - 0.02j, -0.05 + 0.04j
+    one = _shift(*_shift(A0, t, e, sa, d1), d2)
+    both = _shift(A0, t, e, sa, d1 + d2)
+    for a, b in zip(one, both):
+        assert np.allclose(a, b, rtol=0, atol=1e-12 * scale)
