@@ -847,12 +847,19 @@ def run_gpu(args):
         # the measured traffic is for chunks of 16 vesicles; its partial-sum writes scale with the chunk count
         V = fv[2] // args.N if fv[0] < 0 else 16
         traffic = FFS_DRAM_READ + FFS_DRAM_WRITE * 16.0 / V
+        # measured beside the derived peak: paired FMA chains alone, and the pair loop's own instruction mix
+        # (registers only), both through the library's probe on this GPU
+        ffma2, _ = binding.fp32_rate(0, stream=torch.cuda.current_stream())
+        mix, _ = binding.fp32_rate(1, stream=torch.cuda.current_stream())
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak_fp32,
                 "unit": "T FP32 lane-ops/s", "frac": achieved / peak_fp32, "traffic": traffic,
                 "traffic_source": FFS_DRAM_SOURCE + (", writes scaled from 16 to %d vesicles per chunk" % V
                                                      if V != 16 else ""),
                 "peak_source": "FP32 pipe: 128 lanes per clock per SM x 148 SMs x median SM clock (derived); "
                                "achieved counts 18 FP32 lane operations per unordered pair of points",
+                "measured": {"ffma2_chains": ffma2, "frac_of_ffma2_chains": achieved / ffma2,
+                             "pair_mix_registers_only": mix, "frac_of_pair_mix": achieved / mix,
+                             "source": "vs_fp32_rate probes, 2 CTAs of 256 threads per SM, CUDA events"},
                 "share_of_step": dom_ms / total_prof}
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,

@@ -392,6 +392,18 @@ vs_status vs_batched_inverse32(const float* a, float* a_inv, int32_t n, int32_t 
                                void* cuda_stream);
 
 /*
+ * FP32 throughput probe: the measured denominator of the symmetric far field's roofline (its work is FP32
+ * arithmetic, Sec. 2.2.2's all-pairs sum). Runs a register-only kernel, two CTAs of 256 threads per SM (the
+ * far field's residency), after one warm-up launch: mix 0 times independent chains of paired FMAs (the
+ * FP32 pipe's own limit), mix 1 the arithmetic of the far field's paired pair loop without its loads and
+ * lane exchanges (per two pairs 18 paired FP32 instructions, 2 lg2 and 2 rcp: the ceiling of that
+ * instruction mix). iters: loop rounds (1 .. 2^20; about 2048 take a few ms). tera_lane_ops (host): FP32
+ * lane operations per second / 1e12 from CUDA events on cuda_stream; ms (host, may be NULL): the timed
+ * launch. Synchronous; VS_ERR_INVALID_ARG for another mix or iters out of range.
+ */
+vs_status vs_fp32_rate(int32_t mix, int32_t iters, double* tera_lane_ops, double* ms, void* cuda_stream);
+
+/*
  * Standardisation of every vesicle for the networks (Sec. 3.4.1): centroid, principal axis along
  * +y, unit length, cyclic relabelling so that point 0 is the right-most upward crossing of the x
  * axis, Fourier filter keeping modes |k| <= kmax (< N/2). xy: device CSR blocks. xin: device FP32, row v =

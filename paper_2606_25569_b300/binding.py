@@ -71,6 +71,7 @@ FUNCTIONS = {
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_batched_inverse32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "vs_fp32_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                      ctypes.c_void_p, ctypes.c_void_p]),
     "vs_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -410,6 +411,16 @@ def batched_inverse32(a_dev, out_dev, n, batch, stream=None):
     if st != 0:
         raise VsError(st, "vs_batched_inverse32 failed")
     return fb.value
+
+
+def fp32_rate(mix, iters=2048, stream=None):
+    """vs_fp32_rate: (T FP32 lane-ops/s, ms) of the register-only probe (mix 0 paired FMA chains, mix 1 the far
+    field's paired pair arithmetic)."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib().vs_fp32_rate(int(mix), int(iters), ctypes.byref(r), ctypes.byref(ms), _stream(stream))
+    if st != 0:
+        raise VsError(st, "vs_fp32_rate failed")
+    return r.value, ms.value
 
 
 def flow_widths(Kf, Kout):

@@ -25,6 +25,7 @@
 #include "k_mlp.cuh"
 #include "k_mp.cuh"
 #include "k_near.cuh"
+#include "k_probe.cuh"
 #include "k_selfmat.cuh"
 #include "k_standardize.cuh"
 #include "k_flow.cuh"
@@ -2370,6 +2371,40 @@ vs_status vs_batched_inverse32(const float* a, float* a_inv, int32_t n, int32_t 
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA;
   if (fallbacks) *fallbacks = hf;
   return (he & ERR_PIVOT) ? VS_ERR_UNSTABLE : VS_OK;
+}
+
+vs_status vs_fp32_rate(int32_t mix, int32_t iters, double* tera_lane_ops, double* ms, void* cuda_stream) {
+  if ((mix != 0 && mix != 1) || iters < 1 || iters > (1 << 20) || !tera_lane_ops) return VS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = 2 * sms;  // 16 warps per SM, the symmetric far field's residency
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = dalloc(&out, (int64_t)blocks * threads);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // mix 0: 8 chains of 2 lanes per step; mix 1: PROBE_ROWS pair-pairs of 18 paired instructions per step
+  const int steps = mix == 0 ? 4 * iters : iters;
+  float t = 0.f;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    cudaEventRecord(e0, s);
+    if (mix == 0) k_probe_ffma2<<<blocks, threads, 0, s>>>(out, steps);
+    else k_probe_pair<<<blocks, threads, 0, s>>>(out, steps);
+    cudaEventRecord(e1, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA;
+  const double lanes = (double)blocks * threads * steps * (mix == 0 ? 16.0 : PROBE_ROWS * 36.0);
+  *tera_lane_ops = lanes / (t * 1e-3) / 1e12;
+  if (ms) *ms = t;
+  return VS_OK;
 }
 
 vs_status vs_standardize(const double* xy, const int64_t* offsets, int32_t M, int32_t kmax, float* xin,

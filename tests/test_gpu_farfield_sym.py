@@ -210,3 +210,20 @@ def test_phased_symmetric_far_field_matches_one_pass(N, slots, monkeypatch):
     assert plan_a.counters()["near_pairs"] == plan_b.counters()["near_pairs"] > 0
     for h in (a, b, plan_a, plan_b):
         h.close()
+
+
+def test_fp32_rate_probes_bound_the_far_field():
+    # the probes that measure the far field's FP32 denominators: paired FMA chains run near the FP32 pipe's
+    # 128 lanes per clock per SM (at most ~2.1 GHz), the pair loop's instruction mix no faster than that, and the
+    # symmetric far field itself (loads and lane exchanges added) no faster than its own instruction mix
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ffma2, ms0 = binding.fp32_rate(0)
+    mix, ms1 = binding.fp32_rate(1)
+    assert ms0 > 0 and ms1 > 0
+    nominal = 128 * sms * 2.1e9 / 1e12
+    assert 0.3 * nominal < ffma2 <= 1.02 * nominal, (ffma2, nominal)
+    assert 0.2 * nominal < mix <= 1.02 * ffma2, (mix, ffma2)
+    for bad in ((2, 16), (0, 0), (1, 1 << 21)):
+        with pytest.raises(binding.VsError):
+            binding.fp32_rate(*bad)
