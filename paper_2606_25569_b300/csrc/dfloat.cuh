@@ -59,6 +59,16 @@ struct Dot2 {
 };
 
 
+// sqrt(a) in double-float (a.x > 0 and normal): the FP32 root y0 = sqrt(a.x) plus one Newton correction
+// (a - y0^2) / (2 y0) whose residual is formed exactly (y0^2 = p + e by the FMA, a.x - p exact as the two are
+// within a factor of two) and summed with a.y in FP32 (Karp and Markstein, ACM TOMS 23, 1997); about 47 bits.
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+  const float y0 = __fsqrt_rn(a.x);
+  const float p = __fmul_rn(y0, y0), e = fmaf(y0, y0, -p);
+  const float r = __fsub_rn(__fadd_rn(__fsub_rn(a.x, p), a.y), e);
+  return fast_two_sum(y0, __fmul_rn(r, __fmul_rn(0.5f, __frcp_rn(y0))));
+}
+
 // 1/a in double-float: the FP32 reciprocal refined by one Newton step carried out in double-float
 __device__ __forceinline__ float2 df_rcp(float2 a) {
   const float2 y0 = make_float2(__frcp_rn(a.x), 0.f);

@@ -589,8 +589,9 @@ vs_status geometry(vs_suspension* h, const double* xy, bool with_force, const in
   ForceOut fo{};
   if (with_force)
     fo = ForceOut{h->B.f, h->u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64, h->B.gsum};
-  VS_LAUNCH(h, "k_geometry", k_geometry<<<h->L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b, h->p.mu,
-                                             flow_dev(h->flow), geom_active(h->B.geom(), active, h->D.logtab), fo, nullptr));
+  VS_LAUNCH(h, "k_geometry", launch_geometry(h->L.M, h->L.nmax, h->stream, h->D.vi(), xy, h->sigma, h->D.tab, h->p.kappa_b,
+                                             h->p.mu, flow_dev(h->flow), geom_active(h->B.geom(), active, h->D.logtab),
+                                             fo, nullptr));
   VS_CK(h, cudaGetLastError(), "geometry");
   return VS_OK;
 }
@@ -2293,7 +2294,7 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
   const Layout& L = h->L;
   ForceOut fo{h->B.f, u, h->B.src, h->B.centre, h->B.centre32, h->B.h2, h->B.g64, h->B.gsum};
   FlowDev none{0, 0.0, 0.0};
-  k_geometry<<<L.M, NMAX, 0, h->stream>>>(h->D.vi(), xy, nullptr, h->D.tab, 1.0, h->mu, none, h->B.geom(), fo, f);
+  launch_geometry(L.M, L.nmax, h->stream, h->D.vi(), xy, nullptr, h->D.tab, 1.0, h->mu, none, h->B.geom(), fo, f);
   VS_CK(h, cudaGetLastError(), "far-field sources");
   if (L.M < 2) return VS_OK;
   FarFieldArgs a{L.P, L.M, h->D.owner, h->D.off, h->D.chunk, (int)L.chunk.size() - 1, h->near_mask, u,
@@ -2457,7 +2458,7 @@ vs_status vs_self_matrices(const double* xy, const int64_t* offsets, int32_t M, 
   if (e == cudaSuccess) e = B.alloc(L.P, L.M);
   if (e == cudaSuccess) {
     FlowDev none{0, 0.0, 0.0};
-    k_geometry<<<M, NMAX, 0, s>>>(D.vi(), xy, nullptr, D.tab, 1.0, mu, none, B.geom(), ForceOut{}, nullptr);
+    launch_geometry(M, L.nmax, s, D.vi(), xy, nullptr, D.tab, 1.0, mu, none, B.geom(), ForceOut{}, nullptr);
     const int n = L.nmax;
     k_self_matrix<<<self_grid(n, M), 256, 0, s>>>(D.vi(), xy, B.sa, B.tx, B.ty, D.tab, mu, S_out, 0, nullptr);
     e = cudaGetLastError();
@@ -2959,7 +2960,7 @@ extern "C" vs_status vs_farfield_eval_static(const int64_t* offsets, int32_t M, 
                     (float4*)(base + SF_CENTRE32), (float2*)(base + SF_H2), (double*)(base + SF_G64),
                     (float2*)(base + SF_GSUM)};
   const FlowDev none{0, 0.0, 0.0};
-  k_geometry<<<M, NMAX, 0, st>>>(vi, xy, nullptr, (const double*)(base + SF_TABLE), 1.0, mu, none, g, fo, f);
+  k_geometry<1><<<M, NMAX, 0, st>>>(vi, xy, nullptr, (const double*)(base + SF_TABLE), 1.0, mu, none, g, fo, f);
   if (M >= 2) {
     FarFieldArgs a{P, M, (const int32_t*)(base + SF_OWNER), off, (const int32_t*)(base + SF_CHUNK), nchunk, 0, u,
                    nullptr, nullptr, (unsigned*)(base + SF_ERR)};
