@@ -29,18 +29,20 @@ constexpr int MP_MAXIT = 10;
 // CTA sizes of the refinement kernels: 128 threads when there are many vesicles per SM to hide the
 // memory latency, 256 when a few large vesicles leave the SMs short of work (mp_threads)
 constexpr int MP_THREADS = 128, MP_THREADS_WIDE = 256;
-constexpr double MP_FLOOR = 1e-14, MP_STALL = 1e-11, MP_FAIL = 1e-10, MP_LEFT = 1e-13;
+constexpr float MP_FLOOR = 1e-14f, MP_STALL = 1e-11f, MP_FAIL = 1e-10f, MP_LEFT = 1e-13f;
 enum : unsigned { ERR_REFINE = 32u };
 
-__device__ inline double block_max_abs(double v, double* red) {
-  v = fabs(v);
+// Block-wide maximum of |v| in FP32 (the stop rule's magnitudes; the FP64 pipe runs at 1/64 of the FP32
+// rate on this part); red holds one float per warp. All threads get it.
+__device__ inline float block_max_absf(float v, float* red) {
+  v = fabsf(v);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double m = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+  float m = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
   return m;
 }
 
@@ -48,6 +50,7 @@ struct MpShared {
   float2 d[NMAX], is[NMAX], tx[NMAX], ty[NMAX];   // D_alpha circulant, 1/|X_alpha|, x_s, y_s
   float2 u0[2 * NMAX], u1[2 * NMAX], u2[2 * NMAX]; // double-float work vectors
   double red[8];
+  float redf[8];
   __align__(16) float f0[2 * NMAX];                // FP32 corrections
   __align__(16) float f1[2 * NMAX];
 };
@@ -118,14 +121,16 @@ __device__ inline void matvec32f(const float* __restrict__ M, int rows, int cols
 
 // Error left in the iterate after an update of size upd that followed one of size prev, for an iteration
 // that contracts at the observed rate upd / prev: upd^2 / prev (and at most upd).
-__device__ __forceinline__ double mp_left(double upd, double prev) { return fmin(upd, upd * (upd / prev)); }
+__device__ __forceinline__ float mp_left(float upd, float prev) { return fminf(upd, upd * (upd / prev)); }
 
 // Convergence test of a refinement: stop once the estimated error left is below MP_LEFT of the iterate
 // (with FP32 inverses contracting by about 3e-7 a step this is after the first residual step), or the
 // update is below MP_FLOOR, or has stopped shrinking after falling below MP_STALL (the rounding floor of
 // the residual arithmetic).
-__device__ __forceinline__ bool mp_done(double upd, double prev, double top) {
-  return mp_left(upd, prev) <= MP_LEFT * top || upd <= MP_FLOOR * top || (upd <= MP_STALL * top && upd >= 0.5 * prev);
+// The magnitudes are FP32 maxima of the FP32 corrections; the iterate's size `top` is taken from the first
+// correction (the iterate starts at zero, and later corrections change it by a few 1e-7 of itself).
+__device__ __forceinline__ bool mp_done(float upd, float prev, float top) {
+  return mp_left(upd, prev) <= MP_LEFT * top || upd <= MP_FLOOR * top || (upd <= MP_STALL * top && upd >= 0.5f * prev);
 }
 
 __device__ inline void mp_load_geom(MpShared& sh, const double* tab, const double* sa, const double* tx,
@@ -234,7 +239,7 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
                            float2* w, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) { s[i] = 0.0; e[i] = g[i]; }
   __syncthreads();
-  double upd = 1e300, top = 0.0, prev_upd = 1e300;
+  float upd = 3e38f, top = 0.f, prev_upd = 3e38f;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it > 0) {
       for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = df_of(s[i]);
@@ -248,19 +253,18 @@ __device__ bool mp_solve_L(MpShared& sh, const MpMats& m, const float2* g, doubl
     for (int i = threadIdx.x; i < N; i += blockDim.x) sh.f1[i] = e[i].x;
     __syncthreads();
     matvec32f<COLS>(m.li, N, N, sh.f1, sh.f0, 1.f, false);
-    double du = 0.0, sv = 0.0;
+    float du = 0.f;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       s[i] += (double)sh.f0[i];
-      du = fmax(du, fabs((double)sh.f0[i]));
-      sv = fmax(sv, fabs(s[i]));
+      du = fmaxf(du, fabsf(sh.f0[i]));
     }
-    const double prev = upd;
-    upd = block_max_abs(du, sh.red);
-    top = block_max_abs(sv, sh.red);
+    const float prev = upd;
+    upd = block_max_absf(du, sh.redf);
+    if (it == 0) top = upd;  // s = the first correction
     prev_upd = prev;
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
-  return mp_left(upd, prev_upd) <= MP_FAIL * top || top == 0.0;
+  return mp_left(upd, prev_upd) <= MP_FAIL * top || top == 0.f;
 }
 
 // X* = X^n + dt (u - T L^{-1} P u): (I - M^n) u with the operators cached at slot s.
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
   const float* W32 = base32 + MatLayout::W * NN;
   const float* Ainv = base32 + ainv_sub * NN;  // Ai32
   const float2 mk = df_of(-kappa);
-  double upd = 1e300, top = 0.0, prev_upd = 1e300;
+  float upd = 3e38f, top = 0.f, prev_upd = 3e38f;
   for (int it = 0; it < MP_MAXIT; ++it) {
     if (it == 0) {
       for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) r1[r] = b[r];
@@ -398,16 +402,15 @@ __global__ void __launch_bounds__(THREADS) k_relax_mp(VesIndex vi, const double*
     matvec32f<COLS>(m.t32, 2 * N, N, fy, fr, (float)dt, true);
     matvec32f<COLS>(Ainv, 2 * N, 2 * N, fr, fdx, 1.f, false);
     matvec32f<COLS>(W32, N, 2 * N, fdx, fw, 1.f, false);
-    double du = 0.0, xv = 0.0;
+    float du = 0.f;
     for (int r = threadIdx.x; r < 2 * N; r += blockDim.x) {
       x[r] += (double)fdx[r];
-      du = fmax(du, fabs((double)fdx[r]));
-      xv = fmax(xv, fabs(x[r]));
+      du = fmaxf(du, fabsf(fdx[r]));
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) sg[i] += (double)fy[i] - (double)fw[i];
-    const double prev = upd;
-    upd = block_max_abs(du, sh.red);
-    top = block_max_abs(xv, sh.red);
+    const float prev = upd;
+    upd = block_max_absf(du, sh.redf);
+    if (it == 0) top = upd;  // x = the first correction
     prev_upd = prev;
     if (it > 0 && mp_done(upd, prev, top)) break;
   }
