@@ -53,7 +53,12 @@ __device__ __forceinline__ void fz_gemm(const float* __restrict__ A, int lda, co
       for (int i = 0; i < 8; ++i) {
         const float ai = kk == 0 ? av[i].x : kk == 1 ? av[i].y : kk == 2 ? av[i].z : av[i].w;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) acc[i][j] = fmaf(ai, bv[j], acc[i][j]);
+        for (int j = 0; j < NB; j += 2) {  // paired FP32 FMAs (each lane rounded as fmaf)
+          const float2 c = __ffma2_rn(make_float2(ai, ai), make_float2(bv[j], bv[j + 1]),
+                                      make_float2(acc[i][j], acc[i][j + 1]));
+          acc[i][j] = c.x;
+          acc[i][j + 1] = c.y;
+        }
       }
     }
   }
