@@ -433,6 +433,9 @@ def uneven_arm(args, stream):
         sus.close()
         ff = sum(v[0] for k, v in prof.items() if k.startswith("k_farfield")) / n
         out[name] = {"value": wl.M / (ms * 1e-3), "ms_per_step": ms, "far_field_ms_per_step": round(ff, 4)}
+        if name == "symmetric":
+            kms = {k: round(v[0] / n, 4) for k, v in prof.items()}
+            out[name]["kernel_ms_per_step"] = dict(sorted(kms.items(), key=lambda kv: -kv[1]))
     return out
 
 
