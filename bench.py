@@ -347,7 +347,42 @@ def farfield_alone(stream, reps=10):
         plan.close()
         out[name] = {"ms": ms, "value": pairs / (ms * 1e-3)}
     out["symmetric_phased"]["slots"] = "32 chunk slots a point (16 B each) instead of 125: 4 groups, 10 phases"
+    out["multipole_scaling"] = multipole_scaling(stream)
     return out
+
+
+def multipole_scaling(stream, reps=5):
+    """The multipole far field alone at growing vesicle counts (64-point vesicles in a box of the 2000 x 128
+    box's vesicle density): vesicle by vesicle (precision 2: every vesicle pair tested and translated, O(M^2))
+    against the cluster tree (precision 4: O(M log M) translations), ms per evaluation and the two results'
+    relative difference."""
+    import torch
+    from paper_2606_25569_b300 import binding
+    from paper_2606_25569_b300.workloads import farfield_box
+    res = {}
+    for M in (2000, 8000, 16000):
+        wl, fx, fy = farfield_box(M=M, N=64, seed=13, box=20.0 * np.sqrt(M / 2000.0))
+        xy = torch.as_tensor(wl.flat_xy(), device="cuda")
+        f = torch.as_tensor(np.concatenate([np.concatenate([a, b]) for a, b in zip(fx, fy)]), device="cuda")
+        row, got = {}, {}
+        for name, prec in (("vesicle_pairs", 2), ("tree", 4)):
+            plan = binding.FarFieldPlan(wl.offsets, mu=1.0, near_mask=False, precision=prec, stream=stream)
+            u = torch.empty_like(xy)
+            for _ in range(3):
+                plan.eval(xy, f, u)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                plan.eval(xy, f, u)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name + "_ms"] = round(e0.elapsed_time(e1) / reps, 4)
+            got[name] = u.cpu().numpy()
+            plan.close()
+        row["relative_difference"] = float(np.linalg.norm(got["tree"] - got["vesicle_pairs"]) /
+                                           np.linalg.norm(got["vesicle_pairs"]))
+        res["%dx64" % M] = row
+    return res
 
 
 def _profile_steps(sus, n):

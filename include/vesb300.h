@@ -105,6 +105,16 @@ typedef struct {
  * ones always take the batched launches). Both give FP32-quality preconditioners and the same FP64-accurate
  * results. */
 #define VS_FLAG_OPS_BATCHED 128ull
+/* Multipole far field through a cluster tree (Sec. 4.1 and Sec. 4.5 name the fast multipole method as the
+ * route to a far-field cost linear in the number of vesicles): a quadtree of the vesicle centres (rebuilt on
+ * the device every evaluation; boxes of at most 8 vesicles at the leaves), every box's order-12 expansion
+ * about the mean of its vesicles' centres shifted exactly from its members' (multipole-to-multipole), and
+ * for each target vesicle a walk from the root that translates whole boxes farther than twice the summed
+ * radii into its local expansion, as VS_FLAG_FARFIELD_MULTIPOLE does vesicle by vesicle. The point sums and
+ * their near test are those of VS_FLAG_FARFIELD_MULTIPOLE; the results agree with it to the expansions'
+ * truncation error, at O(M log M) translations instead of O(M^2). At most 16384 vesicles
+ * (VS_ERR_INVALID_ARG beyond); takes precedence over VS_FLAG_FARFIELD_MULTIPOLE. */
+#define VS_FLAG_FARFIELD_TREE 256ull
 
 typedef struct {
   double kappa_b;    /* bending modulus, > 0 */
@@ -357,7 +367,9 @@ void vs_destroy(vs_suspension* s);
  *  precision   0: compensated FP32 (vesicle-relative coordinates; the symmetric pair kernel when every
  *              vesicle has 32, 64 or 128 points, see VS_FLAG_FARFIELD_PER_TARGET), 1: FP64, 2: FP32 with
  *              vesicle multipole expansions for far source vesicles (VS_FLAG_FARFIELD_MULTIPOLE),
- *              3: compensated FP32 with the per-target kernel whatever the point counts.
+ *              3: compensated FP32 with the per-target kernel whatever the point counts, 4: as 2 with
+ *              the expansions of whole clusters of vesicles from a tree (VS_FLAG_FARFIELD_TREE; at most
+ *              16384 vesicles).
  * vs_farfield_eval takes DEVICE pointers in CSR blocks: xy (2P), f (2P); writes u (2P, device,
  * overwritten) on the plan's stream. Asynchronous.
  */

@@ -19,6 +19,7 @@ VS_FLAG_FARFIELD_MULTIPOLE = 16
 VS_FLAG_FARFIELD_PER_TARGET = 32
 VS_FLAG_NEAR_YZ = 64
 VS_FLAG_OPS_BATCHED = 128
+VS_FLAG_FARFIELD_TREE = 256
 
 STATUS = {0: "VS_OK", 1: "VS_ERR_INVALID_ARG", 2: "VS_ERR_CUDA", 3: "VS_ERR_NOMEM",
           4: "VS_ERR_NOT_CONVERGED", 5: "VS_ERR_UNSTABLE", 6: "VS_ERR_TIMEOUT", 7: "VS_ERR_NO_NETWORK"}
@@ -177,6 +178,7 @@ class Suspension:
                  flow_p=(0.0, 0.0, 0.0, 0.0), near_field=False, farfield_fp64=False, stream=None, mode=0,
                  use_graph=False, direct_fp64=False, autotune=True, tc_gemm=False, exact_every=0,
                  farfield_multipole=False, farfield_per_target=False, exact_gap=0.0, near_yz=False,
+                 farfield_tree=False,
                  ops_batched=False):
         L = lib()
         self._h = ctypes.c_void_p()
@@ -187,6 +189,7 @@ class Suspension:
         flags = ((VS_FLAG_FARFIELD_FP64 if farfield_fp64 else 0) | (VS_FLAG_DIRECT_FP64 if direct_fp64 else 0)
                  | (0 if autotune else VS_FLAG_NO_AUTOTUNE) | (VS_FLAG_TC_GEMM if tc_gemm else 0)
                  | (VS_FLAG_FARFIELD_MULTIPOLE if farfield_multipole else 0)
+                 | (VS_FLAG_FARFIELD_TREE if farfield_tree else 0)
                  | (VS_FLAG_FARFIELD_PER_TARGET if farfield_per_target else 0)
                  | (VS_FLAG_NEAR_YZ if near_yz else 0) | (VS_FLAG_OPS_BATCHED if ops_batched else 0))
         p = VsParams(kappa, mu, dt, corr_tol, int(mode), 1 if near_field else 0, 1 if use_graph else 0,

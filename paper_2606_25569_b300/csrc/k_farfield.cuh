@@ -222,9 +222,32 @@ constexpr float FF_MP_THETA2 = 9.0f;   // far when |q|^2 > 9 R_v^2
 // (E_k, 0, 0) as float4 pairs; a0[v] = A_0.
 inline size_t ffm_smem(int P, int threads) { return (size_t)6 * (P + 2) * threads * sizeof(double); }
 
+// Coefficients (k = 1..P+1; thread k) and A_0 (thread 0) of an expansion from its moments A, B, D (K = P + 2
+// of each), written for one vesicle or cluster: coef points at its 2 (P + 1) float4.
+template <int P>
+__device__ __forceinline__ void ffm_coef(int k, const double2* sA, const double2* sB, const double2* sD,
+                                         float4* __restrict__ coef, float2* __restrict__ a0) {
+  if (k >= 1 && k <= P + 1) {
+    const double ik = 1.0 / k;
+    const double2 c1 = (k <= P) ? make_double2(sA[k].x * ik, sA[k].y * ik) : make_double2(0.0, 0.0);
+    const double2 cA = sA[k - 1];
+    double er = -sD[k - 1].x, ei = sD[k - 1].y;  // -conj(D_{k-1})
+    if (k <= P) {
+      er += sB[k].x * ik;   // conj(B_k)/k
+      ei -= sB[k].y * ik;
+    }
+    float4* c = coef + (k - 1) * 2;
+    c[0] = make_float4((float)c1.x, (float)c1.y, (float)cA.x, (float)cA.y);
+    c[1] = make_float4((float)er, (float)ei, 0.f, 0.f);
+  }
+  if (k == 0) *a0 = make_float2((float)sA[0].x, (float)sA[0].y);
+}
+
+// raw (optional): the moments themselves, [M][3 K] double2 (A_0..A_{K-1}, B_..., D_...), for the cluster tree.
 template <int P>
 __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__ voff, const float4* __restrict__ src,
-                                                     float4* __restrict__ coef, float2* __restrict__ a0) {
+                                                     float4* __restrict__ coef, float2* __restrict__ a0,
+                                                     double2* __restrict__ raw = nullptr) {
   constexpr int K = P + 2;
   extern __shared__ double mvals[];  // [6 K][blockDim]: every thread's terms, summed per moment below
   __shared__ double2 sA[K], sB[K], sD[K];
@@ -261,21 +284,9 @@ __global__ void __launch_bounds__(NMAX) k_ff_moments(const int64_t* __restrict__
     reinterpret_cast<double*>((c >> 1) == 0 ? sA : (c >> 1) == 1 ? sB : sD)[2 * k + (c & 1)] = x;
   }
   __syncthreads();
-  const int k = j;
-  if (k >= 1 && k <= P + 1) {
-    const double ik = 1.0 / k;
-    const double2 c1 = (k <= P) ? make_double2(sA[k].x * ik, sA[k].y * ik) : make_double2(0.0, 0.0);
-    const double2 cA = sA[k - 1];
-    double er = -sD[k - 1].x, ei = sD[k - 1].y;  // -conj(D_{k-1})
-    if (k <= P) {
-      er += sB[k].x * ik;   // conj(B_k)/k
-      ei -= sB[k].y * ik;
-    }
-    float4* c = coef + ((int64_t)v * (P + 1) + (k - 1)) * 2;
-    c[0] = make_float4((float)c1.x, (float)c1.y, (float)cA.x, (float)cA.y);
-    c[1] = make_float4((float)er, (float)ei, 0.f, 0.f);
-  }
-  if (k == 0) a0[v] = make_float2((float)sA[0].x, (float)sA[0].y);
+  ffm_coef<P>(j, sA, sB, sD, coef + (int64_t)v * (P + 1) * 2, a0 + v);
+  if (raw)
+    for (int e = j; e < 3 * K; e += nt) raw[(int64_t)v * 3 * K + e] = e < K ? sA[e] : e < 2 * K ? sB[e - K] : sD[e - 2 * K];
 }
 
 // Horner evaluation of a far vesicle's expansion (its coefficients c, (h^2, reach^2, A0) in na)

@@ -52,92 +52,86 @@ __device__ __forceinline__ bool ffl_separated(float4 ca, float ra, float4 cb, fl
   return fmaf(dx, dx, dy * dy) > FFL_SEP2 * s * s;
 }
 
-// One CTA of 128 threads per target vesicle A: thread j translates the separated source vesicles j, j + 128,
-// ... into its own partial local expansion; the partials are summed across the CTA in a fixed order. Then
-// the source vesicles that are not separated are listed in ascending order.
+// Adds to acc (C, H, K, S as in ffl_floats) the local expansion about a target centre c_A of one source
+// expansion (coefficients cf, total density A0) about c_B, d = (dx, dy) = c_A - c_B: the multipole-to-local
+// translation written out above.
 template <int P>
-__global__ void __launch_bounds__(128) k_ff_local(FfLocArgs a) {
-  constexpr int NT = P + 1, NF = ffl_floats(P);
+__device__ __forceinline__ void ffl_translate(float* acc, float dx, float dy, const float4* __restrict__ cf,
+                                              float2 A0) {
+  constexpr int NT = P + 1;
   constexpr int OH = 2, OK = 2 + 2 * NT, OS = 2 + 4 * NT;
-  __shared__ float part[4][NF];
-  __shared__ int wcount[4];
-  const int A = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float hl2 = -0.34657359027997264f;  // -ln(2)/2
-  const float4 ca = a.centre32[A];
-  const float ra = sqrtf(a.h2[A].y);
-  float acc[NF];
+  const float dd = fmaf(dx, dx, dy * dy);
+  const float id = 1.f / dd;
+  const float zr = dx * id, zi = -dy * id;  // zeta = 1/d
+  float pr[NT + 1], pi[NT + 1];             // zeta^k
+  pr[0] = 1.f;
+  pi[0] = 0.f;
 #pragma unroll
-  for (int i = 0; i < NF; ++i) acc[i] = 0.f;
-  for (int B = tid; B < a.M; B += 128) {
-    float dx, dy;
-    if (B == A || !ffl_separated(ca, ra, a.centre32[B], sqrtf(a.h2[B].y), dx, dy)) continue;
-    const float dd = fmaf(dx, dx, dy * dy);
-    const float id = 1.f / dd;
-    const float zr = dx * id, zi = -dy * id;  // zeta = 1/d
-    float pr[NT + 1], pi[NT + 1];             // zeta^k
-    pr[0] = 1.f;
-    pi[0] = 0.f;
+  for (int k = 1; k <= NT; ++k) {
+    pr[k] = pr[k - 1] * zr - pi[k - 1] * zi;
+    pi[k] = pr[k - 1] * zi + pi[k - 1] * zr;
+  }
+  // constant: -A0 log|d| + A0/2
+  const float ld = hl2 * fast_lg2(dd);
+  acc[0] = fmaf(A0.x, ld + 0.5f, acc[0]);
+  acc[1] = fmaf(A0.y, ld + 0.5f, acc[1]);
+#pragma unroll
+  for (int sigma = 0; sigma < 3; ++sigma) {  // T1, E, S_A
+    float gr[NT + 1], gi[NT + 1];            // f_k zeta^k
 #pragma unroll
     for (int k = 1; k <= NT; ++k) {
-      pr[k] = pr[k - 1] * zr - pi[k - 1] * zi;
-      pi[k] = pr[k - 1] * zi + pi[k - 1] * zr;
+      const float4 c = cf[(k - 1) * 2 + (sigma == 1 ? 1 : 0)];
+      const float fr = sigma == 2 ? c.z : c.x, fi = sigma == 2 ? c.w : c.y;
+      gr[k] = fr * pr[k] - fi * pi[k];
+      gi[k] = fr * pi[k] + fi * pr[k];
     }
-    const float4* cf = a.coef + (int64_t)B * 2 * NT;
-    const float2 A0 = a.a0[B];
-    // constant: -A0 log|d| + A0/2
-    const float ld = hl2 * fast_lg2(dd);
-    acc[0] = fmaf(A0.x, ld + 0.5f, acc[0]);
-    acc[1] = fmaf(A0.y, ld + 0.5f, acc[1]);
+    float mr = 1.f, mi = 0.f;  // (-zeta)^m
 #pragma unroll
-    for (int sigma = 0; sigma < 3; ++sigma) {  // T1, E, S_A
-      float gr[NT + 1], gi[NT + 1];            // f_k zeta^k
+    for (int m = 0; m < NT; ++m) {
+      float sr = 0.f, si = 0.f;
 #pragma unroll
       for (int k = 1; k <= NT; ++k) {
-        const float4 c = cf[(k - 1) * 2 + (sigma == 1 ? 1 : 0)];
-        const float fr = sigma == 2 ? c.z : c.x, fi = sigma == 2 ? c.w : c.y;
-        gr[k] = fr * pr[k] - fi * pi[k];
-        gi[k] = fr * pi[k] + fi * pr[k];
+        const float b = ffl_binom(k + m - 1, m);
+        sr = fmaf(b, gr[k], sr);
+        si = fmaf(b, gi[k], si);
       }
-      float mr = 1.f, mi = 0.f;  // (-zeta)^m
-#pragma unroll
-      for (int m = 0; m < NT; ++m) {
-        float sr = 0.f, si = 0.f;
-#pragma unroll
-        for (int k = 1; k <= NT; ++k) {
-          const float b = ffl_binom(k + m - 1, m);
-          sr = fmaf(b, gr[k], sr);
-          si = fmaf(b, gi[k], si);
+      const float lr = sr * mr - si * mi, li = sr * mi + si * mr;  // L_m
+      if (sigma == 0) {  // H += L[T1] - A0 l_m, l_m = -(-zeta)^m / m
+        acc[OH + 2 * m] += lr;
+        acc[OH + 2 * m + 1] += li;
+        if (m > 0) {
+          const float im = 1.f / m;
+          acc[OH + 2 * m] = fmaf(im, A0.x * mr - A0.y * mi, acc[OH + 2 * m]);
+          acc[OH + 2 * m + 1] = fmaf(im, A0.x * mi + A0.y * mr, acc[OH + 2 * m + 1]);
         }
-        const float lr = sr * mr - si * mi, li = sr * mi + si * mr;  // L_m
-        if (sigma == 0) {  // H += L[T1] - A0 l_m, l_m = -(-zeta)^m / m
-          acc[OH + 2 * m] += lr;
-          acc[OH + 2 * m + 1] += li;
-          if (m > 0) {
-            const float im = 1.f / m;
-            acc[OH + 2 * m] = fmaf(im, A0.x * mr - A0.y * mi, acc[OH + 2 * m]);
-            acc[OH + 2 * m + 1] = fmaf(im, A0.x * mi + A0.y * mr, acc[OH + 2 * m + 1]);
-          }
-        } else if (sigma == 1) {  // K += L[E] - conj(A0) l_m
-          acc[OK + 2 * m] += lr;
-          acc[OK + 2 * m + 1] += li;
-          if (m > 0) {
-            const float im = 1.f / m;
-            acc[OK + 2 * m] = fmaf(im, A0.x * mr + A0.y * mi, acc[OK + 2 * m]);
-            acc[OK + 2 * m + 1] = fmaf(im, A0.x * mi - A0.y * mr, acc[OK + 2 * m + 1]);
-          }
-        } else {  // S += L[S_A]; K += conj(d) L[S_A]
-          acc[OS + 2 * m] += lr;
-          acc[OS + 2 * m + 1] += li;
-          acc[OK + 2 * m] = fmaf(dx, lr, fmaf(dy, li, acc[OK + 2 * m]));
-          acc[OK + 2 * m + 1] = fmaf(dx, li, fmaf(-dy, lr, acc[OK + 2 * m + 1]));
+      } else if (sigma == 1) {  // K += L[E] - conj(A0) l_m
+        acc[OK + 2 * m] += lr;
+        acc[OK + 2 * m + 1] += li;
+        if (m > 0) {
+          const float im = 1.f / m;
+          acc[OK + 2 * m] = fmaf(im, A0.x * mr + A0.y * mi, acc[OK + 2 * m]);
+          acc[OK + 2 * m + 1] = fmaf(im, A0.x * mi - A0.y * mr, acc[OK + 2 * m + 1]);
         }
-        const float nr = -(mr * zr - mi * zi), ni = -(mr * zi + mi * zr);
-        mr = nr;
-        mi = ni;
+      } else {  // S += L[S_A]; K += conj(d) L[S_A]
+        acc[OS + 2 * m] += lr;
+        acc[OS + 2 * m + 1] += li;
+        acc[OK + 2 * m] = fmaf(dx, lr, fmaf(dy, li, acc[OK + 2 * m]));
+        acc[OK + 2 * m + 1] = fmaf(dx, li, fmaf(-dy, lr, acc[OK + 2 * m + 1]));
       }
+      const float nr = -(mr * zr - mi * zi), ni = -(mr * zi + mi * zr);
+      mr = nr;
+      mi = ni;
     }
   }
-  // sum over the CTA: lanes, then warps in order
+}
+
+// Sum of the CTA's partial local expansions (lanes, then warps in order), stored for target vesicle A.
+template <int P>
+__device__ __forceinline__ void ffl_store(const float* acc, float* __restrict__ loc) {
+  constexpr int NF = ffl_floats(P);
+  __shared__ float part[4][NF];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
     float v = acc[i];
@@ -146,8 +140,28 @@ __global__ void __launch_bounds__(128) k_ff_local(FfLocArgs a) {
     if (lane == 0) part[wid][i] = v;
   }
   __syncthreads();
-  for (int i = tid; i < NF; i += 128)
-    a.loc[(int64_t)A * NF + i] = ((part[0][i] + part[1][i]) + part[2][i]) + part[3][i];
+  for (int i = tid; i < NF; i += 128) loc[i] = ((part[0][i] + part[1][i]) + part[2][i]) + part[3][i];
+}
+
+// Target vesicle A against every source vesicle (128 threads): thread j translates the separated source
+// vesicles j, j + 128, ... into its own partial local expansion; the partials are summed across the CTA in
+// a fixed order. Then the source vesicles that are not separated are listed in ascending order.
+template <int P>
+__device__ __forceinline__ void ffl_local_all(const FfLocArgs& a, int A) {
+  constexpr int NT = P + 1, NF = ffl_floats(P);
+  __shared__ int wcount[4];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const float4 ca = a.centre32[A];
+  const float ra = sqrtf(a.h2[A].y);
+  float acc[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) acc[i] = 0.f;
+  for (int B = tid; B < a.M; B += 128) {
+    float dx, dy;
+    if (B == A || !ffl_separated(ca, ra, a.centre32[B], sqrtf(a.h2[B].y), dx, dy)) continue;
+    ffl_translate<P>(acc, dx, dy, a.coef + (int64_t)B * 2 * NT, a.a0[B]);
+  }
+  ffl_store<P>(acc, a.loc + (int64_t)A * NF);
   // list of the source vesicles that are not separated, ascending
   int base = 0;
   for (int B0 = 0; B0 < a.M; B0 += 128) {
@@ -165,6 +179,12 @@ __global__ void __launch_bounds__(128) k_ff_local(FfLocArgs a) {
     base += wcount[0] + wcount[1] + wcount[2] + wcount[3];
   }
   if (tid == 0) a.ncnt[A] = base;
+}
+
+// One CTA of 128 threads per target vesicle: ffl_local_all.
+template <int P>
+__global__ void __launch_bounds__(128) k_ff_local(FfLocArgs a) {
+  ffl_local_all<P>(a, blockIdx.x);
 }
 
 // One CTA of 128 threads per target vesicle, a thread per target point: the local expansion of the

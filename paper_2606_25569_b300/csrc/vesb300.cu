@@ -18,6 +18,7 @@
 #include "k_farfield.cuh"
 #include "k_farfield_sym.cuh"
 #include "k_farfield_loc.cuh"
+#include "k_fftree.cuh"
 #include "k_fused.cuh"
 #include "k_geometry.cuh"
 #include "k_implicit.cuh"
@@ -214,6 +215,31 @@ struct SourceBufs {
   float* mploc = nullptr;    // per target vesicle: local expansion of the separated sources
   int* mpncnt = nullptr;     // and its list of the other source vesicles
   int* mplist = nullptr;
+  // cluster tree of the multipole far field (k_fftree.cuh), allocated when it is used
+  double2 *vraw = nullptr, *t_cen = nullptr, *t_raw = nullptr;
+  int *t_order = nullptr, *t_owner = nullptr, *t_lstart = nullptr, *t_parent = nullptr, *t_first = nullptr;
+  int *t_nchild = nullptr;
+  int2* t_range = nullptr;
+  float4 *t_cen32 = nullptr, *t_coef = nullptr;
+  float* t_rad = nullptr;
+  float2* t_a0 = nullptr;
+  int64_t t_max = 0;
+  cudaError_t alloc_tree(int M) {
+    cudaError_t e;
+#define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+    t_max = tree_max_boxes(M);
+    VS_TRY(dalloc(&vraw, (size_t)M * 3 * TREE_K)); VS_TRY(dalloc(&t_order, M)); VS_TRY(dalloc(&t_owner, M));
+    VS_TRY(dalloc(&t_lstart, TREE_LMAX + 2)); VS_TRY(dalloc(&t_range, t_max)); VS_TRY(dalloc(&t_parent, t_max));
+    VS_TRY(dalloc(&t_first, t_max)); VS_TRY(dalloc(&t_nchild, t_max)); VS_TRY(dalloc(&t_cen, t_max));
+    VS_TRY(dalloc(&t_cen32, t_max)); VS_TRY(dalloc(&t_rad, t_max)); VS_TRY(dalloc(&t_raw, t_max * 3 * TREE_K));
+    VS_TRY(dalloc(&t_coef, t_max * 2 * (FF_MP_P + 1))); VS_TRY(dalloc(&t_a0, t_max));
+#undef VS_TRY
+    return cudaSuccess;
+  }
+  FfTreeArgs tree(int M) const {
+    return FfTreeArgs{M, t_max, centre, centre32, h2, vraw, t_order, t_owner, t_lstart, t_range, t_parent, t_first,
+                      t_nchild, t_cen, t_cen32, t_rad, t_raw, t_coef, t_a0};
+  }
   cudaError_t alloc(int64_t P, int M) {
     cudaError_t e;
 #define VS_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
@@ -237,6 +263,9 @@ struct SourceBufs {
     cudaFree(near_cnt); cudaFree(near_v); cudaFree(sa); cudaFree(tx); cudaFree(ty); cudaFree(bx);
     cudaFree(by); cudaFree(area); cudaFree(length); cudaFree(g32); cudaFree(sdf);
     cudaFree(mpcoef); cudaFree(mpa0); cudaFree(mploc); cudaFree(mpncnt); cudaFree(mplist);
+    cudaFree(vraw); cudaFree(t_order); cudaFree(t_owner); cudaFree(t_lstart); cudaFree(t_range); cudaFree(t_parent);
+    cudaFree(t_first); cudaFree(t_nchild); cudaFree(t_cen); cudaFree(t_cen32); cudaFree(t_rad); cudaFree(t_raw);
+    cudaFree(t_coef); cudaFree(t_a0);
     *this = SourceBufs{};
   }
   GeomOut geom() const { return GeomOut{sa, tx, ty, bx, by, area, length, g32, sdf}; }
@@ -627,6 +656,8 @@ void launch_far_field_f32(const vs_suspension* h, int var, FarFieldArgs a) {
 
 // k_ff_moments: one thread per point of the largest vesicle, whole warps
 inline int ff_moment_threads(const Layout& L) { return (L.nmax + 31) / 32 * 32; }
+// k_tree_moments: CTAs striding over the boxes of a level (a level holds fewer than M boxes)
+inline int tree_moment_grid(int M) { return std::min(M, 4 * 148); }
 
 FarFieldArgs far_field_args(vs_suspension* h) {
   const Layout& L = h->L;
@@ -854,6 +885,18 @@ vs_status far_field(vs_suspension* h) {
   if (h->p.flags & VS_FLAG_FARFIELD_FP64) {
     const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
     VS_LAUNCH(h, "k_farfield_f64", k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, h->xy, h->B.g64, h->B.length, h->D.N));
+  } else if (h->p.flags & VS_FLAG_FARFIELD_TREE) {
+    const int mt = ff_moment_threads(L);
+    const FfTreeArgs t = h->B.tree(L.M);
+    VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(
+                                     h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0, h->B.vraw));
+    VS_LAUNCH(h, "k_tree_build", k_tree_build<<<1, TREE_THREADS, tree_build_smem(L.M), h->stream>>>(t));
+    VS_LAUNCH(h, "k_tree_moments", k_tree_moments<<<tree_moment_grid(L.M), TM_THREADS, 0, h->stream>>>(t, 0, 1));
+    for (int l = TREE_LMAX - 1; l >= 0; --l)
+      VS_LAUNCH(h, "k_tree_moments", k_tree_moments<<<tree_moment_grid(L.M), TM_THREADS, 0, h->stream>>>(t, l, 0));
+    const FfLocArgs la = h->B.loc(L.M);
+    VS_LAUNCH(h, "k_ff_local_tree", k_ff_local_tree<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la, t));
+    VS_LAUNCH(h, "k_farfield_loc", k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src));
   } else if (h->p.flags & VS_FLAG_FARFIELD_MULTIPOLE) {
     const int mt = ff_moment_threads(L);
     VS_LAUNCH(h, "k_ff_moments", k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(
@@ -943,7 +986,8 @@ vs_status tune_symmetric(vs_suspension* h, const char* devname) {
 
 vs_status tune_far_field(vs_suspension* h) {
   const Layout& L = h->L;
-  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE)))
+  if (L.M < 2 || (h->p.flags & (VS_FLAG_FARFIELD_FP64 | VS_FLAG_NO_AUTOTUNE | VS_FLAG_FARFIELD_MULTIPOLE |
+                                VS_FLAG_FARFIELD_TREE)))
     return VS_OK;
   int dev = 0;
   VS_CK(h, cudaGetDevice(&dev), "autotune");
@@ -1687,6 +1731,10 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   if (!xy) { h->msg = "null xy"; return fail(VS_ERR_INVALID_ARG); }
   if (!params_ok(params, flow, h->msg)) return fail(VS_ERR_INVALID_ARG);
   if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
+  if ((params->flags & VS_FLAG_FARFIELD_TREE) && M > TREE_MAX_M) {
+    h->msg = "the cluster tree takes at most 16384 vesicles";
+    return fail(VS_ERR_INVALID_ARG);
+  }
   for (int64_t i = 0; i < 2 * h->L.P; ++i)
     if (!std::isfinite(xy[i])) { h->msg = "non-finite input point"; return fail(VS_ERR_INVALID_ARG); }
   h->p = *params;
@@ -1722,6 +1770,11 @@ vs_status vs_create(const double* xy, const int64_t* offsets, int32_t M, const v
   VS_A(cudaFuncSetAttribute(k_bgemm_tc<OpBlk32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   VS_A(cudaFuncSetAttribute(k_ff_moments<FF_MP_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)ffm_smem(FF_MP_P, NMAX)));
+  if (h->p.flags & VS_FLAG_FARFIELD_TREE) {
+    VS_A(h->B.alloc_tree(L.M));
+    VS_A(cudaFuncSetAttribute(k_tree_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tree_build_smem(TREE_MAX_M)));
+  }
   VS_A(dalloc(&h->corr, 6 * L.P + 16 * (int64_t)L.M));
   VS_A(dalloc(&h->cactive, L.M));
   VS_A(dalloc(&h->cpiv, 2 * L.P + 2 * (int64_t)L.M));
@@ -2268,7 +2321,8 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
     delete h;
     return s;
   };
-  if (!(mu > 0) || precision < 0 || precision > 3) { h->msg = "mu must be > 0, precision 0 to 3"; return fail(VS_ERR_INVALID_ARG); }
+  if (!(mu > 0) || precision < 0 || precision > 4) { h->msg = "mu must be > 0, precision 0 to 4"; return fail(VS_ERR_INVALID_ARG); }
+  if (precision == 4 && M > TREE_MAX_M) { h->msg = "the cluster tree takes at most 16384 vesicles"; return fail(VS_ERR_INVALID_ARG); }
   if (!build_layout(offsets, M, h->L, h->msg)) return fail(VS_ERR_INVALID_ARG);
   h->mu = mu;
   h->near_mask = near_mask ? 1 : 0;
@@ -2281,7 +2335,10 @@ vs_status vs_farfield_plan_create(const int64_t* offsets, int32_t M, double mu, 
       (e = cudaMemset(h->B.near_cnt, 0, h->L.P * sizeof(int))) != cudaSuccess ||
       (e = ffs_setup(h->ffs, h->L, precision == 0, h->stream)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(k_ff_moments<FF_MP_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ffm_smem(FF_MP_P, NMAX))) != cudaSuccess) {
+                                (int)ffm_smem(FF_MP_P, NMAX))) != cudaSuccess ||
+      (precision == 4 && (e = h->B.alloc_tree(h->L.M)) != cudaSuccess) ||
+      (precision == 4 && (e = cudaFuncSetAttribute(k_tree_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)tree_build_smem(TREE_MAX_M))) != cudaSuccess)) {
     cuda_fail(h->msg, e, "vs_farfield_plan_create");
     return fail(e == cudaErrorMemoryAllocation ? VS_ERR_NOMEM : VS_ERR_CUDA);
   }
@@ -2302,6 +2359,17 @@ vs_status vs_farfield_eval(vs_farfield_plan* h, const double* xy, const double* 
   const int grid = (int)((L.P + FF_THREADS - 1) / FF_THREADS);
   if (h->precision == 1) {
     k_farfield_f64<<<grid, FF_THREADS, 0, h->stream>>>(a, xy, h->B.g64, h->B.length, h->D.N);
+  } else if (h->precision == 4) {
+    const int mt = ff_moment_threads(L);
+    const FfTreeArgs t = h->B.tree(L.M);
+    k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0,
+                                                                        h->B.vraw);
+    k_tree_build<<<1, TREE_THREADS, tree_build_smem(L.M), h->stream>>>(t);
+    k_tree_moments<<<tree_moment_grid(L.M), TM_THREADS, 0, h->stream>>>(t, 0, 1);
+    for (int l = TREE_LMAX - 1; l >= 0; --l) k_tree_moments<<<tree_moment_grid(L.M), TM_THREADS, 0, h->stream>>>(t, l, 0);
+    const FfLocArgs la = h->B.loc(L.M);
+    k_ff_local_tree<FF_MP_P><<<L.M, 128, 0, h->stream>>>(la, t);
+    k_farfield_loc<FF_MP_P><<<L.M, 128, 0, h->stream>>>(a, la, h->B.src);
   } else if (h->precision == 2) {
     const int mt = ff_moment_threads(L);
     k_ff_moments<FF_MP_P><<<L.M, mt, ffm_smem(FF_MP_P, mt), h->stream>>>(h->D.off, h->B.src, h->B.mpcoef, h->B.mpa0);

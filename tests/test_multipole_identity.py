@@ -5,7 +5,8 @@ Stokeslet sum over a vesicle's points at a target q far from it equals
 (series in zeta from the moments A_k, B_k, D_k; the library's kernels use this form). Written out here in
 numpy and checked against the oracle's direct sum: the error decays like (R/|q|)^(P+1). The translation to
 a local expansion about a far target vesicle's centre (k_ff_local, k_farfield_loc) is written out and
-checked the same way."""
+checked the same way, and so are the cluster tree's exact shift of raw moments from the members of a box to
+its centre (k_tree_moments) and the expansion of a whole cluster."""
 from math import comb
 import numpy as np
 
@@ -172,3 +173,82 @@ def test_shifted_expansion_matches_direct_sum():
     both = _shift(A0, t, e, sa, d1 + d2)
     for a, b in zip(one, both):
         assert np.allclose(a, b, rtol=0, atol=1e-12 * scale)
+
+
+def _raw_moments(s, g, K):
+    A = np.array([np.sum(g * s ** k) for k in range(K)])
+    B = np.array([np.sum(g * np.conj(s) ** k) for k in range(K)])
+    D = np.array([np.sum(np.conj(g) * s * np.conj(s) ** k) for k in range(K)])
+    return A, B, D
+
+
+def _shift_raw(A, B, D, delta):
+    """Moments about a new centre from those about the old one, delta = old centre - new centre."""
+    K = len(A)
+    A2, B2, D2 = (np.zeros(K, complex) for _ in range(3))
+    for k in range(K):
+        for j in range(k + 1):
+            c = comb(k, j)
+            A2[k] += c * delta ** (k - j) * A[j]
+            B2[k] += c * np.conj(delta) ** (k - j) * B[j]
+            D2[k] += c * np.conj(delta) ** (k - j) * (D[j] + delta * np.conj(A[j]))
+    return A2, B2, D2
+
+
+def test_cluster_moments_follow_exactly_from_the_members():
+    # the cluster tree's multipole-to-multipole shift: moments of three vesicles about their own centres,
+    # shifted to the cluster centre and added, equal the moments of all their points about that centre
+    rng = np.random.default_rng(12)
+    K = 14
+    pts, gs, tot = [], [], [np.zeros(K, complex) for _ in range(3)]
+    centres = [0.3 + 0.1j, -0.2 + 0.25j, 0.05 - 0.3j]
+    cc = np.mean(centres)
+    for c in centres:
+        x, y = vesicle_outline(64, 0.7, 0.1, 1e-2, rng, rng.uniform(0, 2 * np.pi))
+        s = (x - x.mean()) + 1j * (y - y.mean())
+        g = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+        pts.append(s + c)
+        gs.append(g)
+        for t, m in zip(tot, _shift_raw(*_raw_moments(s, g, K), c - cc)):
+            t += m
+    direct = _raw_moments(np.concatenate(pts) - cc, np.concatenate(gs), K)
+    for t, d in zip(tot, direct):
+        assert np.max(np.abs(t - d) / (np.abs(d) + 1e-300)) <= 1e-11
+
+
+def test_cluster_expansion_matches_direct_sum_beyond_twice_its_radius():
+    # the expansion of a whole cluster (three vesicles) about its centre, from the shifted moments, against
+    # the oracle's direct sum at a target beyond twice the cluster's radius
+    rng = np.random.default_rng(4)
+    xs, ys, fx, fy = [], [], [], []
+    for c in (0.0 + 0.0j, 0.35 + 0.1j, 0.1 + 0.4j):
+        x, y = vesicle_outline(64, 0.7, 0.1, 1e-2, rng, rng.uniform(0, 2 * np.pi))
+        xs.append(x - x.mean() + c.real)
+        ys.append(y - y.mean() + c.imag)
+        fx.append(rng.standard_normal(64))
+        fy.append(rng.standard_normal(64))
+    w, _ = source_weights(xs, ys)
+    cen = [complex(x.mean(), y.mean()) for x, y in zip(xs, ys)]
+    cc = np.mean(cen)
+    K, P = 14, 12
+    tot = [np.zeros(K, complex) for _ in range(3)]
+    for v in range(3):
+        s = (xs[v] + 1j * ys[v]) - cen[v]
+        g = (fx[v] + 1j * fy[v]) * w[v] / (4 * np.pi)
+        for t, m in zip(tot, _shift_raw(*_raw_moments(s, g, K), cen[v] - cc)):
+            t += m
+    allp = np.concatenate([x + 1j * y for x, y in zip(xs, ys)])
+    radius = np.max(np.abs(allp - cc))
+    q = 2.2 * radius * np.exp(1j * 0.7)
+    ux, uy, _ = far_field(xs + [np.array([cc.real + q.real])], ys + [np.array([cc.imag + q.imag])],
+                          fx + [np.zeros(1)], fy + [np.zeros(1)], 1.0, near_mask=False, targets=[3 * 64])
+    # the expansion from the cluster moments (same series as _expansion, moments given)
+    A, B, D = tot
+    z = 1.0 / q
+    T1 = sum(A[k] / k * z ** k for k in range(1, P + 1))
+    SA = sum(A[k - 1] * z ** k for k in range(1, P + 2))
+    E = sum(((np.conj(B[k]) / k) if k <= P else 0.0) * z ** k - np.conj(D[k - 1]) * z ** k for k in range(1, P + 2))
+    u = -A[0] * np.log(abs(q)) + 0.5 * A[0] + 0.5 * T1 + 0.5 * np.conj(E) + 0.5 * q * np.conj(SA)
+    scale = np.sqrt(np.mean(np.abs(np.concatenate([(a + 1j * b) * wv for a, b, wv in zip(fx, fy, w)])) ** 2)) \
+        * 3 * 64 / (4 * np.pi)
+    assert abs(u - (ux[0] + 1j * uy[0])) <= 1e-3 * scale, abs(u - (ux[0] + 1j * uy[0])) / scale
