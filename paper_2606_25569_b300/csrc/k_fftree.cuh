@@ -214,6 +214,23 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_build(FfTreeArgs t) {
   for (int l = level + 2 + tid; l <= TREE_LMAX + 1; l += TREE_THREADS) t.lstart[l] = le;
 }
 
+// Binomial coefficients C(k, j), k, j < TREE_K, fixed at compile time (exact in FP64): the shifts below read
+// them instead of dividing in FP64, whose long latency at 1/64 of the FP32 rate sat on each box's critical path.
+struct TreeBinom {
+  double c[TREE_K][TREE_K];
+};
+__host__ __device__ constexpr TreeBinom tree_binom_table() {
+  TreeBinom t{};
+  for (int k = 0; k < TREE_K; ++k)
+    for (int j = 0; j < TREE_K; ++j) {
+      double c = j <= k ? 1.0 : 0.0;
+      for (int i = 1; i <= j && j <= k; ++i) c = c * (k - j + i) / i;
+      t.c[k][j] = c;
+    }
+  return t;
+}
+__constant__ TreeBinom c_tree_binom = tree_binom_table();
+
 // Moments, centre and radius of boxes from their members: with leaves set, every leaf box of the tree at
 // once (its members are vesicles, whose moments are known); otherwise the internal boxes of one level, deepest
 // level first. One CTA per box (grid-stride), a thread per (member, moment) so that the FP64 shifts of up to
@@ -227,9 +244,11 @@ __global__ void __launch_bounds__(TM_THREADS) k_tree_moments(FfTreeArgs t, int l
   __shared__ double2 part[MC][NO];
   __shared__ double2 mc[MC];
   __shared__ double mr[MC], mw[MC];
+  __shared__ double bn[K][K];
   __shared__ double2 cen;
   const int b0 = leaves ? 0 : t.lstart[level], b1 = leaves ? t.lstart[TREE_LMAX + 1] : t.lstart[level + 1];
   const int tid = threadIdx.x;
+  for (int e = tid; e < K * K; e += blockDim.x) bn[e / K][e % K] = c_tree_binom.c[e / K][e % K];
 
   for (int b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
     const int nc = t.nchild[b];
@@ -281,7 +300,6 @@ __global__ void __launch_bounds__(TM_THREADS) k_tree_moments(FfTreeArgs t, int l
       const double wr = dr, wi = kind == 0 ? di : -di;   // delta or conj(delta)
       // sum_j C(k, j) w^(k - j) X_j, with X_j = A_j, B_j, or D_j + delta conj(A_j)
       double pr = 1.0, pi = 0.0;  // w^(k - j), from j = k down to 0
-      double bin = 1.0;           // C(k, j)
       for (int j = k; j >= 0; --j) {
         double xr, xi;
         if (kind == 0) {
@@ -295,12 +313,12 @@ __global__ void __launch_bounds__(TM_THREADS) k_tree_moments(FfTreeArgs t, int l
           xr = d.x + (dr * a.x + di * a.y);  // delta conj(A_j)
           xi = d.y + (di * a.x - dr * a.y);
         }
-        sr += bin * (pr * xr - pi * xi);
-        si += bin * (pr * xi + pi * xr);
+        const double c = bn[k][j];
+        sr = fma(c, pr * xr - pi * xi, sr);
+        si = fma(c, pr * xi + pi * xr, si);
         const double nr = pr * wr - pi * wi;
         pi = pr * wi + pi * wr;
         pr = nr;
-        bin = bin * (double)j / (double)(k - j + 1);
       }
     }
     part[ml][o] = make_double2(sr, si);
